@@ -1,0 +1,229 @@
+// TEST INFRASTRUCTURE ONLY (see dgfv_oracle.h).  Reference-element operators.
+#include "basis.hpp"
+
+#include <cmath>
+#include <stdexcept>
+
+namespace ora {
+
+namespace {
+
+using ld = long double;
+
+// Legendre polynomial P_n(x) and its derivative by the three-term recurrence
+//   k P_k = (2k-1) x P_{k-1} - (k-1) P_{k-2},   P'_k = P'_{k-2} + (2k-1) P_{k-1}.
+void legendre(int n, ld x, ld& P, ld& dP) {
+    if (n == 0) { P = 1; dP = 0; return; }
+    ld p0 = 1, p1 = x, d0 = 0, d1 = 1;
+    for (int k = 2; k <= n; ++k) {
+        ld p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+        ld d2 = d0 + (2 * k - 1) * p1;
+        p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+    }
+    P = p1; dP = d1;
+}
+
+// Roots of P_n (Legendre-Gauss nodes) by Newton's method, ascending, and the
+// Gauss weights w = 2 / ((1 - x^2) P_n'(x)^2).
+void gauss_legendre(int n, std::vector<ld>& x, std::vector<ld>& w) {
+    const ld pi = 3.14159265358979323846264338327950288L;
+    x.assign(n, 0); w.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        ld xi = -std::cos(pi * (i + 0.75L) / (n + 0.5L));
+        for (int it = 0; it < 200; ++it) {
+            ld P, dP;
+            legendre(n, xi, P, dP);
+            ld dx = P / dP;
+            xi -= dx;
+            if (std::fabs((double)dx) < 1e-19) break;
+        }
+        ld P, dP;
+        legendre(n, xi, P, dP);
+        x[i] = xi;
+        w[i] = 2 / ((1 - xi * xi) * dP * dP);
+    }
+}
+
+// Lagrange polynomial l_j of the nodes x, evaluated at xi.
+ld lagrange(const std::vector<ld>& x, int j, ld xi) {
+    ld r = 1;
+    for (int m = 0; m < (int)x.size(); ++m)
+        if (m != j) r *= (xi - x[m]) / (x[j] - x[m]);
+    return r;
+}
+
+// Derivative of the Lagrange polynomial l_j at xi (product rule).
+ld lagrange_deriv(const std::vector<ld>& x, int j, ld xi) {
+    ld s = 0;
+    for (int k = 0; k < (int)x.size(); ++k) {
+        if (k == j) continue;
+        ld t = 1 / (x[j] - x[k]);
+        for (int m = 0; m < (int)x.size(); ++m)
+            if (m != j && m != k) t *= (xi - x[m]) / (x[j] - x[m]);
+        s += t;
+    }
+    return s;
+}
+
+// Orthonormal Legendre polynomial sqrt((2m+1)/2) P_m.
+ld legendre_orthonormal(int m, ld x) {
+    ld P, dP;
+    legendre(m, x, P, dP);
+    return std::sqrt((2 * m + 1) / (ld)2) * P;
+}
+
+// Inverse of a square matrix by Gauss-Jordan elimination with partial pivoting.
+std::vector<ld> invert(std::vector<ld> A, int n) {
+    std::vector<ld> B(n * n, 0);
+    for (int i = 0; i < n; ++i) B[i * n + i] = 1;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs((double)A[r * n + c]) > std::fabs((double)A[piv * n + c])) piv = r;
+        if (A[piv * n + c] == 0) throw std::runtime_error("singular matrix");
+        for (int k = 0; k < n; ++k) {
+            std::swap(A[c * n + k], A[piv * n + k]);
+            std::swap(B[c * n + k], B[piv * n + k]);
+        }
+        ld d = A[c * n + c];
+        for (int k = 0; k < n; ++k) { A[c * n + k] /= d; B[c * n + k] /= d; }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            ld f = A[r * n + c];
+            if (f == 0) continue;
+            for (int k = 0; k < n; ++k) {
+                A[r * n + k] -= f * A[c * n + k];
+                B[r * n + k] -= f * B[c * n + k];
+            }
+        }
+    }
+    return B;
+}
+
+std::vector<double> to_double(const std::vector<ld>& a) {
+    return std::vector<double>(a.begin(), a.end());
+}
+
+std::vector<ld> nodes_ld(int N) {
+    std::vector<ld> x, w;
+    gauss_legendre(N + 1, x, w);
+    return x;
+}
+
+// (N_to+1) x (N_from+1) interpolation matrix l^{from}_j(x^{to}_i).
+std::vector<ld> interp_ld(int N_from, int N_to) {
+    std::vector<ld> xf = nodes_ld(N_from), xt = nodes_ld(N_to);
+    int nf = N_from + 1, nt = N_to + 1;
+    std::vector<ld> M(nt * nf);
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < nf; ++j) M[i * nf + j] = lagrange(xf, j, xt[i]);
+    return M;
+}
+
+std::vector<ld> leg_vandermonde_ld(int N) {
+    int n = N + 1;
+    std::vector<ld> x = nodes_ld(N), V(n * n);
+    for (int i = 0; i < n; ++i)
+        for (int m = 0; m < n; ++m) V[i * n + m] = legendre_orthonormal(m, x[i]);
+    return V;
+}
+
+std::vector<ld> dg2fv_ld(int N, int n_fv) {
+    int n = N + 1;
+    std::vector<ld> x, w;
+    gauss_legendre(n, x, w);  // exact for the degree-N integrand
+    ld l = (ld)2 / n_fv;
+    std::vector<ld> A(n_fv * n);
+    for (int s = 0; s < n_fv; ++s) {
+        ld a = -1 + s * l;
+        for (int j = 0; j < n; ++j) {
+            // (1/l) * integral over [a, a+l] of l_j  =  (1/2) sum_q w_q l_j(a + (l/2)(x_q+1))
+            ld sum = 0;
+            for (int q = 0; q < n; ++q) sum += w[q] * lagrange(x, j, a + l / 2 * (x[q] + 1));
+            A[s * n + j] = sum / 2;
+        }
+    }
+    return A;
+}
+
+}  // namespace
+
+Basis1D make_basis(int N) {
+    if (N < 0 || N > 15) throw std::runtime_error("degree out of range");
+    Basis1D b;
+    b.N = N;
+    b.n = N + 1;
+    const int n = b.n;
+    std::vector<ld> x, w;
+    gauss_legendre(n, x, w);
+    b.x = to_double(x);
+    b.w = to_double(w);
+    std::vector<ld> D(n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) D[i * n + j] = lagrange_deriv(x, j, x[i]);
+    b.D = to_double(D);
+    b.Dhat.assign(n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) b.Dhat[i * n + j] = (double)(-(w[j] / w[i]) * D[j * n + i]);
+    b.lm.resize(n); b.lp.resize(n); b.lhm.resize(n); b.lhp.resize(n);
+    for (int j = 0; j < n; ++j) {
+        ld a = lagrange(x, j, -1), c = lagrange(x, j, 1);
+        b.lm[j] = (double)a;
+        b.lp[j] = (double)c;
+        b.lhm[j] = (double)(a / w[j]);
+        b.lhp[j] = (double)(c / w[j]);
+    }
+    return b;
+}
+
+std::vector<double> vmap(int N_from, int N_to) {
+    if (N_from <= N_to) return to_double(interp_ld(N_from, N_to));
+    // L2 projection onto degree N_to: expand in orthonormal Legendre modes
+    // (inverse Vandermonde of the finer degree), keep modes 0..N_to, evaluate
+    // the truncated series on the coarser nodes.
+    int nf = N_from + 1, nt = N_to + 1;
+    std::vector<ld> Vinv = invert(leg_vandermonde_ld(N_from), nf);
+    std::vector<ld> xt = nodes_ld(N_to);
+    std::vector<ld> M(nt * nf, 0);
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < nf; ++j) {
+            ld s = 0;
+            for (int m = 0; m <= N_to; ++m) s += legendre_orthonormal(m, xt[i]) * Vinv[m * nf + j];
+            M[i * nf + j] = s;
+        }
+    return to_double(M);
+}
+
+std::vector<double> dg2fv(int N, int n_fv) { return to_double(dg2fv_ld(N, n_fv)); }
+
+std::vector<double> fv2dg(int N, int n_fv) {
+    // Pseudo-inverse through the normal equations, (A^T A)^{-1} A^T; A has full
+    // column rank whenever n_fv >= N+1.
+    int n = N + 1;
+    if (n_fv < n) throw std::runtime_error("n_fv < N+1: DG->FV map not injective");
+    std::vector<ld> A = dg2fv_ld(N, n_fv);
+    std::vector<ld> AtA(n * n, 0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            ld s = 0;
+            for (int r = 0; r < n_fv; ++r) s += A[r * n + i] * A[r * n + j];
+            AtA[i * n + j] = s;
+        }
+    std::vector<ld> inv = invert(AtA, n);
+    std::vector<ld> P(n * n_fv, 0);
+    for (int i = 0; i < n; ++i)
+        for (int r = 0; r < n_fv; ++r) {
+            ld s = 0;
+            for (int k = 0; k < n; ++k) s += inv[i * n + k] * A[r * n + k];
+            P[i * n_fv + r] = s;
+        }
+    return to_double(P);
+}
+
+std::vector<double> leg_vandermonde(int N) { return to_double(leg_vandermonde_ld(N)); }
+
+std::vector<double> leg_vandermonde_inv(int N) {
+    return to_double(invert(leg_vandermonde_ld(N), N + 1));
+}
+
+}  // namespace ora

@@ -1,0 +1,44 @@
+// Reference-element operators of the DGSEM and of the DG <-> FV mappings.
+//
+// TEST INFRASTRUCTURE ONLY (see dgfv_oracle.h).  Everything here is computed
+// in long double from the defining formulas and rounded to double at the end.
+//
+//   Sec. 3.1.1: Legendre-Gauss nodes/weights, Lagrange basis (Eq. 18
+//               langrange_basis), derivative matrix D, weighted derivative
+//               matrix Dhat and l_hat = l/omega (Eq. 24 dgsem_abbrev).
+//   Sec. 3.2:   V^{N->M} (interpolation for N<M, L2 projection for N>M),
+//               V^{DG->FV} (sub-cell integration), V^{FV->DG} (pseudo-inverse).
+//   Sec. 3.4:   Legendre Vandermonde V_Leg (orthonormal Legendre modes).
+#ifndef DGFV_ORACLE_BASIS_HPP
+#define DGFV_ORACLE_BASIS_HPP
+
+#include <vector>
+
+namespace ora {
+
+struct Basis1D {
+    int N = 0;                 // polynomial degree
+    int n = 0;                 // number of nodes, N+1
+    std::vector<double> x, w;  // Legendre-Gauss nodes (ascending) and weights
+    std::vector<double> D;     // D[i*n+j] = l_j'(x_i)
+    std::vector<double> Dhat;  // Dhat[i*n+j] = -(w_j / w_i) * D[j*n+i]   (reading of Eq. 24)
+    std::vector<double> lm, lp;    // l_j(-1), l_j(+1)
+    std::vector<double> lhm, lhp;  // l_j(-1)/w_j, l_j(+1)/w_j
+};
+
+Basis1D make_basis(int N);
+
+// (N_to+1) x (N_from+1): interpolation if N_from <= N_to, L2 projection otherwise.
+std::vector<double> vmap(int N_from, int N_to);
+// n_fv x (N+1): mean value of the degree-N interpolant over each of n_fv equal sub-cells.
+std::vector<double> dg2fv(int N, int n_fv);
+// (N+1) x n_fv: Moore-Penrose pseudo-inverse of dg2fv(N, n_fv).
+std::vector<double> fv2dg(int N, int n_fv);
+// (N+1) x (N+1): V[i*n+m] = sqrt((2m+1)/2) P_m(x_i) on the LG nodes of degree N.
+std::vector<double> leg_vandermonde(int N);
+// Inverse of leg_vandermonde(N) (Gauss-Jordan elimination).
+std::vector<double> leg_vandermonde_inv(int N);
+
+}  // namespace ora
+
+#endif

@@ -1,0 +1,949 @@
+// Plain FP64 CPU oracle of the hp-adaptive hybrid DG/FV operator
+// (arXiv 2502.19342).  TEST INFRASTRUCTURE ONLY (see dgfv_oracle.h): only the
+// tests, the smoke check and the benchmark's CPU-baseline leg use it.
+//
+// The right-hand side follows the paper's steps in order, with plain loops:
+//   1. face values of every element: DG traces u(+-1) = sum_i l_i(+-1) u_i
+//      (LG nodes, Sec. 3.1.1); FV elements expose their boundary sub-cell means;
+//   2. FV sub-cell elements (Sec. 3.1.2): minmod TVD reconstruction of
+//      (rho_k, v, p), central-difference gradients, sub-cell Riemann and
+//      viscous fluxes on interior sub-cell faces;
+//   3. BR1 lifting interface value U* = (u- + u+)/2 (Eq. 19), on the lower
+//      degree at p-interfaces and on DG data at DG/FV interfaces (Sec. 3.2.2);
+//   4. lifting (Eq. 23) and volume integral (Eq. 22) of DG elements;
+//   5. face flux F* = F^c*(u-,u+) + (F^v(u-,g-) + F^v(u+,g+))/2 (Eqs. 20, 21)
+//      on the higher degree at p-interfaces and on FV data at DG/FV
+//      interfaces, mapped back to each side (Sec. 3.2.1, 3.2.2);
+//   6. surface integral and the 1/J scaling (Eqs. 22, 26).
+// Readings of the paper where it is silent or garbled are marked "Reading".
+#include "dgfv_oracle.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+#include <utility>
+#include <vector>
+
+#include "basis.hpp"
+#include "physics.hpp"
+
+using namespace ora;
+using std::vector;
+
+namespace {
+
+// ------------------------------------------------------------------ mesh
+struct Elem {
+    int dom = 0;
+    int idx[3] = {0, 0, 0};
+    int N = 1;        // DG degree (kept while the element is FV)
+    bool fv = false;  // FV sub-cell element
+    int n = 2;        // points per direction: N+1 (DG) or n_fv (FV)
+    int64_t off = 0;  // offset of the element's block in the state
+    int nb[6];        // neighbour across face f (0:-x 1:+x 2:-y 3:+y 4:-z 5:+z)
+    double h[3];      // element size
+};
+
+struct Ops {  // reference operators, built once per problem before any parallel loop
+    std::map<int, Basis1D> basis;
+    std::map<std::pair<int, int>, vector<double>> vm;  // (from,to) -> V^{from->to}
+    std::map<int, vector<double>> d2f, f2d;            // per DG degree
+    std::map<int, vector<double>> vleg_inv;
+    const Basis1D& B(int N) const { return basis.at(N); }
+};
+
+struct Problem {
+    Phys ph;
+    int V = 6;
+    int nfv = 2;
+    int riemann = 0;
+    vector<Elem> el;
+    int64_t size = 0;
+    Ops ops;
+};
+
+Problem make_problem(const oracle_problem* p, bool need_ops = true) {
+    if (!p || p->n_domains <= 0 || p->n_species < 1 || p->n_species > MAXSP || p->n_fv < 1)
+        throw std::runtime_error("bad problem");
+    Problem P;
+    P.ph.nk = p->n_species;
+    for (int k = 0; k < p->n_species; ++k) {
+        P.ph.gamma[k] = p->gamma[k];
+        P.ph.R[k] = p->Rgas[k];
+        P.ph.cv[k] = p->Rgas[k] / (p->gamma[k] - 1.0);
+        P.ph.cp[k] = p->gamma[k] * P.ph.cv[k];
+        P.ph.mu[k] = p->mu[k];
+        P.ph.pr[k] = p->Pr[k];
+        P.ph.D[k] = p->Dk[k];
+    }
+    P.V = P.ph.V();
+    P.nfv = p->n_fv;
+    P.riemann = p->riemann;
+    int64_t e0 = 0;
+    for (int d = 0; d < p->n_domains; ++d) {
+        const int nx = p->dims[3 * d], ny = p->dims[3 * d + 1], nz = p->dims[3 * d + 2];
+        if (nx < 1 || ny < 1 || nz < 1) throw std::runtime_error("bad domain");
+        double h[3];
+        for (int a = 0; a < 3; ++a)
+            h[a] = (p->hi[3 * d + a] - p->lo[3 * d + a]) / p->dims[3 * d + a];
+        const int dims[3] = {nx, ny, nz};
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    Elem E;
+                    E.dom = d;
+                    E.idx[0] = i; E.idx[1] = j; E.idx[2] = k;
+                    for (int a = 0; a < 3; ++a) E.h[a] = h[a];
+                    for (int f = 0; f < 6; ++f) {
+                        int q[3] = {i, j, k};
+                        int a = f / 2;
+                        q[a] = (q[a] + (f % 2 ? 1 : -1) + dims[a]) % dims[a];
+                        E.nb[f] = (int)(e0 + q[0] + nx * (q[1] + ny * q[2]));
+                    }
+                    P.el.push_back(E);
+                }
+        e0 += (int64_t)nx * ny * nz;
+    }
+    for (size_t e = 0; e < P.el.size(); ++e) {
+        Elem& E = P.el[e];
+        E.N = p->N[e];
+        E.fv = p->fv[e] != 0;
+        if (E.N < 1 || E.N > 15) throw std::runtime_error("bad degree");
+        E.n = E.fv ? P.nfv : E.N + 1;
+        E.off = P.size;
+        P.size += (int64_t)P.V * E.n * E.n * E.n;
+    }
+    if (need_ops) {
+        std::vector<int> degs;
+        for (auto& E : P.el) degs.push_back(E.N);
+        std::sort(degs.begin(), degs.end());
+        degs.erase(std::unique(degs.begin(), degs.end()), degs.end());
+        for (int N : degs) {
+            P.ops.basis[N] = make_basis(N);
+            P.ops.vleg_inv[N] = leg_vandermonde_inv(N);
+            if (P.nfv >= N + 1) {
+                P.ops.d2f[N] = dg2fv(N, P.nfv);
+                P.ops.f2d[N] = fv2dg(N, P.nfv);
+            }
+            for (int M : degs) P.ops.vm[{N, M}] = vmap(N, M);
+        }
+        for (auto& E : P.el)
+            if (E.fv && P.nfv < E.N + 1) throw std::runtime_error("n_fv < N+1 for an FV element");
+    }
+    return P;
+}
+
+// Node index of the point with coordinate m along direction d and transverse
+// coordinates (a, b) (in increasing axis order).
+inline int node_index(int n, int d, int m, int a, int b) {
+    if (d == 0) return m + n * (a + n * b);
+    if (d == 1) return a + n * (m + n * b);
+    return a + n * (b + n * m);
+}
+
+// Apply the tensor-product map M (nout x nin) in both face directions to a
+// face field of nvar variables stored as in[var*nin^2 + a + nin*b]
+// (first along a, then along b).
+template <class T>
+vector<T> map_face(const vector<T>& in, int nvar, int nin, int nout, const vector<double>& M) {
+    vector<T> tmp((size_t)nvar * nout * nin, T(0.0));
+    for (int v = 0; v < nvar; ++v)
+        for (int bi = 0; bi < nin; ++bi)
+            for (int ao = 0; ao < nout; ++ao) {
+                T s = T(0.0);
+                for (int ai = 0; ai < nin; ++ai)
+                    s = s + T(M[ao * nin + ai]) * in[(size_t)v * nin * nin + ai + nin * bi];
+                tmp[(size_t)v * nout * nin + ao + nout * bi] = s;
+            }
+    vector<T> out((size_t)nvar * nout * nout, T(0.0));
+    for (int v = 0; v < nvar; ++v)
+        for (int bo = 0; bo < nout; ++bo)
+            for (int ao = 0; ao < nout; ++ao) {
+                T s = T(0.0);
+                for (int bi = 0; bi < nin; ++bi)
+                    s = s + T(M[bo * nin + bi]) * tmp[(size_t)v * nout * nin + ao + nout * bi];
+                out[(size_t)v * nout * nout + ao + nout * bo] = s;
+            }
+    return out;
+}
+
+// V^{N_from -> N_to} on a face field; the identity when the degrees agree.
+template <class T>
+vector<T> map_face_deg(const Problem& P, const vector<T>& in, int nvar, int N_from, int N_to) {
+    if (N_from == N_to) return in;
+    return map_face(in, nvar, N_from + 1, N_to + 1, P.ops.vm.at({N_from, N_to}));
+}
+
+// Apply the tensor-product map M (nout x nin) in all three directions to a
+// volume field of nvar variables (one direction at a time).
+template <class T>
+vector<T> map_volume(const T* in, int nvar, int nin, int nout, const vector<double>& M) {
+    vector<T> a((size_t)nvar * nout * nin * nin, T(0.0));
+    for (int v = 0; v < nvar; ++v)
+        for (int k = 0; k < nin; ++k)
+            for (int j = 0; j < nin; ++j)
+                for (int i = 0; i < nout; ++i) {
+                    T s = T(0.0);
+                    for (int m = 0; m < nin; ++m)
+                        s = s + T(M[i * nin + m]) * in[(size_t)v * nin * nin * nin + m + nin * (j + nin * k)];
+                    a[(size_t)v * nout * nin * nin + i + nout * (j + nin * k)] = s;
+                }
+    vector<T> b((size_t)nvar * nout * nout * nin, T(0.0));
+    for (int v = 0; v < nvar; ++v)
+        for (int k = 0; k < nin; ++k)
+            for (int j = 0; j < nout; ++j)
+                for (int i = 0; i < nout; ++i) {
+                    T s = T(0.0);
+                    for (int m = 0; m < nin; ++m)
+                        s = s + T(M[j * nin + m]) * a[(size_t)v * nout * nin * nin + i + nout * (m + nin * k)];
+                    b[(size_t)v * nout * nout * nin + i + nout * (j + nout * k)] = s;
+                }
+    vector<T> c((size_t)nvar * nout * nout * nout, T(0.0));
+    for (int v = 0; v < nvar; ++v)
+        for (int k = 0; k < nout; ++k)
+            for (int j = 0; j < nout; ++j)
+                for (int i = 0; i < nout; ++i) {
+                    T s = T(0.0);
+                    for (int m = 0; m < nin; ++m)
+                        s = s + T(M[k * nin + m]) * b[(size_t)v * nout * nout * nin + i + nout * (j + nout * m)];
+                    c[(size_t)v * nout * nout * nout + i + nout * (j + nout * k)] = s;
+                }
+    return c;
+}
+
+template <class T>
+struct ElemWork {
+    vector<T> face_u[6];    // DG: trace of u; FV: boundary sub-cell means      (V x n^2)
+    vector<T> face_layer[6];  // DG: V^{DG->FV} sub-cell means of the boundary layer (V x n_fv^2)
+    vector<T> face_rec[6];  // FV: reconstructed face state at the element face (V x n^2)
+    vector<T> face_g[6];    // DG: trace of the lifted gradient; FV: boundary-cell gradient (3V x n^2)
+    vector<T> ustar[6];     // DG: lifting interface value U*                  (V x n^2)
+    vector<T> flux[6];      // outward normal flux F*.n on the element's own representation (V x n^2)
+    vector<T> div;          // volume (DG) or interior sub-cell face (FV) part of -R  (V x n^3)
+};
+
+// Face flux at one point: F* = F^c*(uL,uR) + (F^v(uL,gL) + F^v(uR,gR))/2 in +x_d direction.
+template <class T>
+void point_flux(const Problem& P, const T* uL, const T* gL, const T* uR, const T* gR, int d, T* F) {
+    const int V = P.V;
+    T Fc[MAXV], FvL[MAXV], FvR[MAXV];
+    Prim<T> sL, sR;
+    cons_to_prim(P.ph, uL, sL);
+    cons_to_prim(P.ph, uR, sR);
+    riemann(P.ph, P.riemann, uL, sL, uR, sR, d, Fc);
+    flux_visc(P.ph, uL, gL, sL, d, FvL);
+    flux_visc(P.ph, uR, gR, sR, d, FvR);
+    for (int v = 0; v < V; ++v) F[v] = Fc[v] + T(0.5) * (FvL[v] + FvR[v]);
+}
+
+template <class T>
+T minmod(T a, T b) {
+    // minmod(a,b) = 0 if a b <= 0, else the argument of smaller magnitude (a on ties)
+    if (val(a) * val(b) <= 0.0) return T(0.0);
+    return std::fabs(val(a)) <= std::fabs(val(b)) ? a : b;
+}
+
+template <class T>
+void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
+    const int V = P.V, nfv = P.nfv;
+    const int nel = (int)P.el.size();
+    vector<ElemWork<T>> W(nel);
+
+    // ---- step 1: face values of every element
+#pragma omp parallel for schedule(dynamic, 16) if (parallel)
+    for (int e = 0; e < nel; ++e) {
+        const Elem& E = P.el[e];
+        const int n = E.n;
+        const T* u = U + E.off;
+        for (int f = 0; f < 6; ++f) {
+            const int d = f / 2, s = f % 2;
+            vector<T> fu((size_t)V * n * n, T(0.0));
+            for (int v = 0; v < V; ++v)
+                for (int b = 0; b < n; ++b)
+                    for (int a = 0; a < n; ++a) {
+                        T val_ = T(0.0);
+                        if (E.fv) {
+                            val_ = u[(size_t)v * n * n * n + node_index(n, d, s ? n - 1 : 0, a, b)];
+                        } else {
+                            const vector<double>& l = s ? P.ops.B(E.N).lp : P.ops.B(E.N).lm;
+                            for (int m = 0; m < n; ++m)
+                                val_ = val_ + T(l[m]) * u[(size_t)v * n * n * n + node_index(n, d, m, a, b)];
+                        }
+                        fu[(size_t)v * n * n + a + n * b] = val_;
+                    }
+            W[e].face_u[f] = fu;
+            // the boundary layer of sub-cell means that an FV neighbour sees:
+            // V^{DG->FV} in all three directions, keeping the sub-cells next to face f
+            if (!E.fv && P.nfv >= n) {
+                const vector<double>& A = P.ops.d2f.at(E.N);
+                const int row = s ? P.nfv - 1 : 0;
+                vector<T> q((size_t)V * n * n, T(0.0));
+                for (int v = 0; v < V; ++v)
+                    for (int b = 0; b < n; ++b)
+                        for (int a = 0; a < n; ++a) {
+                            T t = T(0.0);
+                            for (int m = 0; m < n; ++m)
+                                t = t + T(A[row * n + m]) * u[(size_t)v * n * n * n + node_index(n, d, m, a, b)];
+                            q[(size_t)v * n * n + a + n * b] = t;
+                        }
+                W[e].face_layer[f] = map_face(q, V, n, P.nfv, A);
+            }
+        }
+    }
+
+    // ---- step 2: FV sub-cell elements (Sec. 3.1.2)
+#pragma omp parallel for schedule(dynamic, 1) if (parallel)
+    for (int e = 0; e < nel; ++e) {
+        const Elem& E = P.el[e];
+        if (!E.fv) continue;
+        const int n = nfv, n3 = n * n * n;
+        const double l = 2.0 / n;  // sub-cell size in reference coordinates
+        const T* u = U + E.off;
+        // Reading: the value beyond the element boundary is the neighbour's
+        // face-adjacent sub-cell mean: an FV neighbour's own, or, for a DG
+        // neighbour, its solution mapped to sub-cell means by V^{DG->FV}
+        // (Sec. 3.2.1: the DG side is transformed to the FV representation).
+        vector<T> nbval[6];
+        double nbdist[6];
+        for (int f = 0; f < 6; ++f) {
+            const Elem& Q = P.el[E.nb[f]];
+            nbval[f] = Q.fv ? W[E.nb[f]].face_u[f ^ 1] : W[E.nb[f]].face_layer[f ^ 1];
+            nbdist[f] = l;
+        }
+        // primitive reconstruction variables of every sub-cell and of the neighbour values
+        vector<T> w((size_t)V * n3);
+        for (int c = 0; c < n3; ++c) {
+            T uc[MAXV], wc[MAXV];
+            for (int v = 0; v < V; ++v) uc[v] = u[(size_t)v * n3 + c];
+            cons_to_recvars(P.ph, uc, wc);
+            for (int v = 0; v < V; ++v) w[(size_t)v * n3 + c] = wc[v];
+        }
+        vector<T> nbw[6];
+        for (int f = 0; f < 6; ++f) {
+            nbw[f].resize((size_t)V * n * n);
+            for (int p = 0; p < n * n; ++p) {
+                T uc[MAXV], wc[MAXV];
+                for (int v = 0; v < V; ++v) uc[v] = nbval[f][(size_t)v * n * n + p];
+                cons_to_recvars(P.ph, uc, wc);
+                for (int v = 0; v < V; ++v) nbw[f][(size_t)v * n * n + p] = wc[v];
+            }
+        }
+        // reconstructed states at the two faces of every cell along every direction
+        // recm[d], recp[d]: conservative state at the cell's -d and +d face (V x n^3)
+        vector<T> recm[3], recp[3];
+        // central-difference gradient of the conservative variables (3V x n^3)
+        vector<T> grad((size_t)3 * V * n3, T(0.0));
+        for (int d = 0; d < 3; ++d) {
+            recm[d].assign((size_t)V * n3, T(0.0));
+            recp[d].assign((size_t)V * n3, T(0.0));
+            for (int b = 0; b < n; ++b)
+                for (int a = 0; a < n; ++a)
+                    for (int m = 0; m < n; ++m) {
+                        const int c = node_index(n, d, m, a, b);
+                        const int p = a + n * b;
+                        const int cl = m > 0 ? node_index(n, d, m - 1, a, b) : -1;
+                        const int cr = m < n - 1 ? node_index(n, d, m + 1, a, b) : -1;
+                        const double dl = cl >= 0 ? l : nbdist[2 * d];
+                        const double dr = cr >= 0 ? l : nbdist[2 * d + 1];
+                        T wm[MAXV], wp[MAXV];
+                        for (int v = 0; v < V; ++v) {
+                            T wc = w[(size_t)v * n3 + c];
+                            T wl = cl >= 0 ? w[(size_t)v * n3 + cl] : nbw[2 * d][(size_t)v * n * n + p];
+                            T wr = cr >= 0 ? w[(size_t)v * n3 + cr] : nbw[2 * d + 1][(size_t)v * n * n + p];
+                            // second-order TVD reconstruction with the minmod limiter
+                            T slope = minmod((wc - wl) / T(dl), (wr - wc) / T(dr));
+                            wm[v] = wc - slope * T(l / 2);
+                            wp[v] = wc + slope * T(l / 2);
+                            // viscous terms: central differences of the conservative sub-cell means
+                            T ucl = cl >= 0 ? u[(size_t)v * n3 + cl] : nbval[2 * d][(size_t)v * n * n + p];
+                            T ucr = cr >= 0 ? u[(size_t)v * n3 + cr] : nbval[2 * d + 1][(size_t)v * n * n + p];
+                            grad[((size_t)d * V + v) * n3 + c] = (ucr - ucl) / T(dl + dr) * T(2.0 / E.h[d]);
+                        }
+                        T um[MAXV], up[MAXV];
+                        recvars_to_cons(P.ph, wm, um);
+                        recvars_to_cons(P.ph, wp, up);
+                        for (int v = 0; v < V; ++v) {
+                            recm[d][(size_t)v * n3 + c] = um[v];
+                            recp[d][(size_t)v * n3 + c] = up[v];
+                        }
+                    }
+        }
+        // interior sub-cell faces: F* = F^c*(rec-, rec+) + (F^v(rec-, g-) + F^v(rec+, g+))/2;
+        // div accumulates sum over faces of (outward flux) * |face| / |cell| = (n/h_d) F.n
+        vector<T> div((size_t)V * n3, T(0.0));
+        for (int d = 0; d < 3; ++d) {
+            const T scale = T(n / E.h[d]);
+            for (int b = 0; b < n; ++b)
+                for (int a = 0; a < n; ++a)
+                    for (int m = 0; m + 1 < n; ++m) {
+                        const int cL = node_index(n, d, m, a, b), cR = node_index(n, d, m + 1, a, b);
+                        T uL[MAXV], uR[MAXV], gL[3 * MAXV], gR[3 * MAXV], F[MAXV];
+                        for (int v = 0; v < V; ++v) {
+                            uL[v] = recp[d][(size_t)v * n3 + cL];
+                            uR[v] = recm[d][(size_t)v * n3 + cR];
+                        }
+                        for (int dd = 0; dd < 3; ++dd)
+                            for (int v = 0; v < V; ++v) {
+                                gL[dd * V + v] = grad[((size_t)dd * V + v) * n3 + cL];
+                                gR[dd * V + v] = grad[((size_t)dd * V + v) * n3 + cR];
+                            }
+                        point_flux(P, uL, gL, uR, gR, d, F);
+                        for (int v = 0; v < V; ++v) {
+                            div[(size_t)v * n3 + cL] = div[(size_t)v * n3 + cL] + scale * F[v];
+                            div[(size_t)v * n3 + cR] = div[(size_t)v * n3 + cR] - scale * F[v];
+                        }
+                    }
+        }
+        W[e].div = div;
+        // element-face states and boundary-cell gradients for the coupling
+        for (int f = 0; f < 6; ++f) {
+            const int d = f / 2, s = f % 2;
+            vector<T> fr((size_t)V * n * n), fg((size_t)3 * V * n * n);
+            for (int b = 0; b < n; ++b)
+                for (int a = 0; a < n; ++a) {
+                    const int c = node_index(n, d, s ? n - 1 : 0, a, b);
+                    for (int v = 0; v < V; ++v)
+                        fr[(size_t)v * n * n + a + n * b] = s ? recp[d][(size_t)v * n3 + c] : recm[d][(size_t)v * n3 + c];
+                    for (int dv = 0; dv < 3 * V; ++dv)
+                        fg[(size_t)dv * n * n + a + n * b] = grad[(size_t)dv * n3 + c];
+                }
+            W[e].face_rec[f] = fr;
+            W[e].face_g[f] = fg;
+        }
+    }
+
+    // ---- step 3: BR1 lifting interface value U* = (u- + u+)/2 (Eq. 19)
+#pragma omp parallel for schedule(dynamic, 16) if (parallel)
+    for (int e = 0; e < nel; ++e) {
+        const Elem& E = P.el[e];
+        if (E.fv) continue;
+        for (int f = 0; f < 6; ++f) {
+            const Elem& Q = P.el[E.nb[f]];
+            const vector<T>& mine = W[e].face_u[f];
+            vector<T> us;
+            if (Q.fv) {
+                // Sec. 3.2.2: FV side mapped to the DG element's polynomial data by V^{FV->DG}
+                vector<T> other = map_face(W[E.nb[f]].face_rec[f ^ 1], V, nfv, E.n, P.ops.f2d.at(E.N));
+                us.resize(mine.size());
+                for (size_t i = 0; i < mine.size(); ++i) us[i] = T(0.5) * (mine[i] + other[i]);
+            } else {
+                // Sec. 3.2.2: lifting flux on the lower degree, interpolated back up
+                const int Nm = std::min(E.N, Q.N);
+                vector<T> a = map_face_deg(P, mine, V, E.N, Nm);
+                vector<T> b = map_face_deg(P, W[E.nb[f]].face_u[f ^ 1], V, Q.N, Nm);
+                vector<T> avg(a.size());
+                for (size_t i = 0; i < a.size(); ++i) avg[i] = T(0.5) * (a[i] + b[i]);
+                us = map_face_deg(P, avg, V, Nm, E.N);
+            }
+            W[e].ustar[f] = us;
+        }
+    }
+
+    // ---- step 4: lifting (Eq. 23) and volume integral (Eq. 22) of DG elements.
+    // Cartesian elements: J = hx hy hz / 8, metric terms J dxi_d/dx_d = J (2/h_d),
+    // so contravariant quantities divided by J carry the factor 2/h_d.
+    // Reading (Eq. 23): the lifted variable is the gradient, g^d = +(1/J)[...].
+    // Reading (Eq. 24): Dhat_ij = -(w_j/w_i) D_ji.
+#pragma omp parallel for schedule(dynamic, 4) if (parallel)
+    for (int e = 0; e < nel; ++e) {
+        const Elem& E = P.el[e];
+        if (E.fv) continue;
+        const int n = E.n, n3 = n * n * n;
+        const Basis1D& B = P.ops.B(E.N);
+        const T* u = U + E.off;
+        vector<T> g((size_t)3 * V * n3, T(0.0));
+        for (int d = 0; d < 3; ++d) {
+            const T metric = T(2.0 / E.h[d]);
+            for (int v = 0; v < V; ++v)
+                for (int b = 0; b < n; ++b)
+                    for (int a = 0; a < n; ++a)
+                        for (int i = 0; i < n; ++i) {
+                            T s = T(0.0);
+                            for (int m = 0; m < n; ++m)
+                                s = s + T(B.Dhat[i * n + m]) * u[(size_t)v * n3 + node_index(n, d, m, a, b)];
+                            const int p = a + n * b;
+                            s = s + T(B.lhp[i]) * W[e].ustar[2 * d + 1][(size_t)v * n * n + p]
+                                  - T(B.lhm[i]) * W[e].ustar[2 * d][(size_t)v * n * n + p];
+                            g[((size_t)d * V + v) * n3 + node_index(n, d, i, a, b)] = metric * s;
+                        }
+        }
+        // fluxes at the nodes
+        vector<T> F((size_t)3 * V * n3);
+        for (int c = 0; c < n3; ++c) {
+            T uc[MAXV], gc[3 * MAXV], Fc[MAXV], Fv[MAXV];
+            for (int v = 0; v < V; ++v) uc[v] = u[(size_t)v * n3 + c];
+            for (int dv = 0; dv < 3 * V; ++dv) gc[dv] = g[(size_t)dv * n3 + c];
+            Prim<T> s;
+            cons_to_prim(P.ph, uc, s);
+            for (int d = 0; d < 3; ++d) {
+                flux_conv(P.ph, uc, s, d, Fc);
+                flux_visc(P.ph, uc, gc, s, d, Fv);
+                for (int v = 0; v < V; ++v) F[((size_t)d * V + v) * n3 + c] = Fc[v] + Fv[v];
+            }
+        }
+        // volume integral sum_m Ftilde_m Dhat_im / J
+        vector<T> div((size_t)V * n3, T(0.0));
+        for (int d = 0; d < 3; ++d) {
+            const T metric = T(2.0 / E.h[d]);
+            for (int v = 0; v < V; ++v)
+                for (int b = 0; b < n; ++b)
+                    for (int a = 0; a < n; ++a)
+                        for (int i = 0; i < n; ++i) {
+                            T s = T(0.0);
+                            for (int m = 0; m < n; ++m)
+                                s = s + T(B.Dhat[i * n + m]) * F[((size_t)d * V + v) * n3 + node_index(n, d, m, a, b)];
+                            const int c = node_index(n, d, i, a, b);
+                            div[(size_t)v * n3 + c] = div[(size_t)v * n3 + c] + metric * s;
+                        }
+        }
+        W[e].div = div;
+        // traces of the lifted gradient on the six faces
+        for (int f = 0; f < 6; ++f) {
+            const int d = f / 2, s = f % 2;
+            const vector<double>& lb = s ? B.lp : B.lm;
+            vector<T> fg((size_t)3 * V * n * n, T(0.0));
+            for (int dv = 0; dv < 3 * V; ++dv)
+                for (int b = 0; b < n; ++b)
+                    for (int a = 0; a < n; ++a) {
+                        T t = T(0.0);
+                        for (int m = 0; m < n; ++m) t = t + T(lb[m]) * g[(size_t)dv * n3 + node_index(n, d, m, a, b)];
+                        fg[(size_t)dv * n * n + a + n * b] = t;
+                    }
+            W[e].face_g[f] = fg;
+        }
+    }
+
+    // ---- step 5: face fluxes; every face is visited once, from its lower element L
+    for (int e = 0; e < nel; ++e)
+        for (int f = 0; f < 6; ++f) W[e].flux[f].clear();
+#pragma omp parallel for schedule(dynamic, 16) if (parallel)
+    for (int e = 0; e < nel; ++e) {
+        for (int d = 0; d < 3; ++d) {
+            const int eL = e, eR = P.el[e].nb[2 * d + 1];
+            const int fL = 2 * d + 1, fR = 2 * d;
+            const Elem &L = P.el[eL], &Rr = P.el[eR];
+            // common representation (Sec. 3.2.1): max degree, or FV data if either side is FV
+            vector<T> uL, gL, uR, gR;
+            int nc;
+            const bool common_fv = L.fv || Rr.fv;
+            if (!common_fv) {
+                const int Nc = std::max(L.N, Rr.N);
+                nc = Nc + 1;
+                uL = map_face_deg(P, W[eL].face_u[fL], V, L.N, Nc);
+                gL = map_face_deg(P, W[eL].face_g[fL], 3 * V, L.N, Nc);
+                uR = map_face_deg(P, W[eR].face_u[fR], V, Rr.N, Nc);
+                gR = map_face_deg(P, W[eR].face_g[fR], 3 * V, Rr.N, Nc);
+            } else {
+                nc = nfv;
+                if (L.fv) {
+                    uL = W[eL].face_rec[fL];
+                    gL = W[eL].face_g[fL];
+                } else {
+                    uL = map_face(W[eL].face_u[fL], V, L.n, nc, P.ops.d2f.at(L.N));
+                    gL = map_face(W[eL].face_g[fL], 3 * V, L.n, nc, P.ops.d2f.at(L.N));
+                }
+                if (Rr.fv) {
+                    uR = W[eR].face_rec[fR];
+                    gR = W[eR].face_g[fR];
+                } else {
+                    uR = map_face(W[eR].face_u[fR], V, Rr.n, nc, P.ops.d2f.at(Rr.N));
+                    gR = map_face(W[eR].face_g[fR], 3 * V, Rr.n, nc, P.ops.d2f.at(Rr.N));
+                }
+            }
+            const int np = nc * nc;
+            vector<T> Fc((size_t)V * np);
+            for (int p = 0; p < np; ++p) {
+                T a[MAXV], b[MAXV], ga[3 * MAXV], gb[3 * MAXV], F[MAXV];
+                for (int v = 0; v < V; ++v) { a[v] = uL[(size_t)v * np + p]; b[v] = uR[(size_t)v * np + p]; }
+                for (int dv = 0; dv < 3 * V; ++dv) { ga[dv] = gL[(size_t)dv * np + p]; gb[dv] = gR[(size_t)dv * np + p]; }
+                point_flux(P, a, ga, b, gb, d, F);
+                for (int v = 0; v < V; ++v) Fc[(size_t)v * np + p] = F[v];
+            }
+            // back to each side's native representation (projection / V^{FV->DG})
+            auto back = [&](const Elem& S) -> vector<T> {
+                if (!common_fv) return map_face_deg(P, Fc, V, nc - 1, S.N);
+                if (S.fv) return Fc;
+                return map_face(Fc, V, nc, S.n, P.ops.f2d.at(S.N));
+            };
+            vector<T> FLs = back(L), FRs = back(Rr);
+            for (auto& x : FRs) x = -x;  // outward normal of the upper element is -x_d
+            W[eL].flux[fL] = FLs;
+            W[eR].flux[fR] = FRs;
+        }
+    }
+
+    // ---- step 6: surface integral and -1/J (Eqs. 22, 26)
+#pragma omp parallel for schedule(dynamic, 16) if (parallel)
+    for (int e = 0; e < nel; ++e) {
+        const Elem& E = P.el[e];
+        const int n = E.n, n3 = n * n * n;
+        vector<T> div = W[e].div;
+        if (!E.fv) {
+            const Basis1D& B = P.ops.B(E.N);
+            for (int d = 0; d < 3; ++d) {
+                const T metric = T(2.0 / E.h[d]);
+                for (int v = 0; v < V; ++v)
+                    for (int b = 0; b < n; ++b)
+                        for (int a = 0; a < n; ++a)
+                            for (int i = 0; i < n; ++i) {
+                                const int c = node_index(n, d, i, a, b), p = a + n * b;
+                                T s = T(B.lhp[i]) * W[e].flux[2 * d + 1][(size_t)v * n * n + p]
+                                    + T(B.lhm[i]) * W[e].flux[2 * d][(size_t)v * n * n + p];
+                                div[(size_t)v * n3 + c] = div[(size_t)v * n3 + c] + metric * s;
+                            }
+            }
+        } else {
+            for (int d = 0; d < 3; ++d) {
+                const T scale = T(n / E.h[d]);
+                for (int s = 0; s < 2; ++s)
+                    for (int v = 0; v < V; ++v)
+                        for (int b = 0; b < n; ++b)
+                            for (int a = 0; a < n; ++a) {
+                                const int c = node_index(n, d, s ? n - 1 : 0, a, b);
+                                div[(size_t)v * n3 + c] = div[(size_t)v * n3 + c] + scale * W[e].flux[2 * d + s][(size_t)v * n * n + a + n * b];
+                            }
+            }
+        }
+        for (int i = 0; i < V * n3; ++i) R[E.off + i] = -div[i];
+    }
+}
+
+// ------------------------------------------------------------------ time step, Sec. 3.3
+// Reading: alpha_RK = beta_RK = 1; lambda^c / dx -> sum_d (|v_d| + c)/dx_d;
+// delta^v = max(4/3 mu/rho, kappa mu/(Pr rho), max_k D_k) with sum_d 1/dx_d^2;
+// DG: dx_d = h_d and the factor (2N+1); FV: dx_d = h_d/n_fv and factor 1.
+void time_step(const Problem& P, const double* U, double cfl_c, double cfl_v, double out[3]) {
+    double mc = INFINITY, mv = INFINITY;
+    double maxD = 0.0;
+    bool viscous = false;
+    for (int k = 0; k < P.ph.nk; ++k) {
+        maxD = std::max(maxD, P.ph.D[k]);
+        if (P.ph.mu[k] != 0.0 || P.ph.D[k] != 0.0) viscous = true;
+    }
+    for (const Elem& E : P.el) {
+        const int n3 = E.n * E.n * E.n;
+        const double fac = E.fv ? 1.0 : (2.0 * E.N + 1.0);
+        double dx[3];
+        for (int d = 0; d < 3; ++d) dx[d] = E.fv ? E.h[d] / P.nfv : E.h[d];
+        for (int c = 0; c < n3; ++c) {
+            double uc[MAXV];
+            for (int v = 0; v < P.V; ++v) uc[v] = U[E.off + (int64_t)v * n3 + c];
+            Prim<double> s;
+            cons_to_prim(P.ph, uc, s);
+            double lam = 0.0;
+            for (int d = 0; d < 3; ++d) lam += (std::fabs(s.v[d]) + s.c) / dx[d];
+            mc = std::min(mc, cfl_c / (lam * fac));
+            if (viscous) {
+                double dv = std::max(4.0 / 3.0 * s.mu / s.rho, s.kappa * s.mu / (s.pr * s.rho));
+                dv = std::max(dv, maxD);
+                double sdx = 0.0;
+                for (int d = 0; d < 3; ++d) sdx += 1.0 / (dx[d] * dx[d]);
+                mv = std::min(mv, cfl_v / (dv * sdx * fac));
+            }
+        }
+    }
+    out[1] = mc;
+    out[2] = mv;
+    out[0] = viscous ? 1.0 / (1.0 / mc + 1.0 / mv) : mc;
+}
+
+// ------------------------------------------------------------------ SSP-RK3 (Shu-Osher)
+//   U1 = U0 + dt R(U0);  U2 = 3/4 U0 + 1/4 (U1 + dt R(U1));  U3 = 1/3 U0 + 2/3 (U2 + dt R(U2))
+template <class Rhs>
+void ssp_rk3_step(int64_t n, double* U, double dt, Rhs rhs) {
+    static const double a[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double b[3] = {1.0, 0.25, 2.0 / 3.0};
+    vector<double> U0(U, U + n), Us(U, U + n), Rv(n);
+    for (int s = 0; s < 3; ++s) {
+        rhs(Us.data(), Rv.data());
+        for (int64_t i = 0; i < n; ++i) Us[i] = a[s] * U0[i] + b[s] * (Us[i] + dt * Rv[i]);
+    }
+    std::copy(Us.begin(), Us.end(), U);
+}
+
+// ------------------------------------------------------------------ indicator, Sec. 3.4
+// Reading: orthonormal Legendre modes; fit over m = 0..N; w_m floored at 1e-300
+// before the logarithm; I = min over the three directions of |sigma|;
+// FV elements are mapped to their DG degree by V^{FV->DG} first.
+double modal_indicator(const vector<double>& q, int N, const vector<double>& Vinv) {
+    const int n = N + 1;
+    vector<double> qm = map_volume(q.data(), 1, n, n, Vinv);  // Legendre coefficients
+    double total = 0.0;
+    for (int i = 0; i < n * n * n; ++i) total += qm[i] * qm[i];
+    double I = INFINITY;
+    for (int d = 0; d < 3; ++d) {
+        vector<double> y(n);
+        for (int m = 0; m < n; ++m) {
+            double E = 0.0;
+            for (int b = 0; b < n; ++b)
+                for (int a = 0; a < n; ++a) {
+                    double c = qm[node_index(n, d, m, a, b)];
+                    E += c * c;
+                }
+            double w = total > 0.0 ? E / total : 0.0;
+            y[m] = std::log(std::max(w, 1e-300));
+        }
+        // least-squares fit of log w_m = log c - sigma m  (Eq. 34)
+        double mbar = 0.0, ybar = 0.0;
+        for (int m = 0; m < n; ++m) { mbar += m; ybar += y[m]; }
+        mbar /= n; ybar /= n;
+        double sxy = 0.0, sxx = 0.0;
+        for (int m = 0; m < n; ++m) { sxy += (m - mbar) * (y[m] - ybar); sxx += (m - mbar) * (m - mbar); }
+        double sigma = -sxy / sxx;
+        I = std::min(I, std::fabs(sigma));
+    }
+    return I;
+}
+
+void indicator(const Problem& P, const double* U, double* Ip, double* Ih) {
+    const int nel = (int)P.el.size(), nk = P.ph.nk;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int e = 0; e < nel; ++e) {
+        const Elem& E = P.el[e];
+        const int n = E.N + 1, n3 = n * n * n;
+        vector<double> u;
+        if (E.fv) {
+            u = map_volume(U + E.off, P.V, P.nfv, n, P.ops.f2d.at(E.N));
+        } else {
+            u.assign(U + E.off, U + E.off + (int64_t)P.V * n3);
+        }
+        vector<double> rho(n3), pr(n3), Y[MAXSP];
+        for (int k = 0; k < nk; ++k) Y[k].resize(n3);
+        for (int c = 0; c < n3; ++c) {
+            double uc[MAXV];
+            for (int v = 0; v < P.V; ++v) uc[v] = u[(size_t)v * n3 + c];
+            Prim<double> s;
+            cons_to_prim(P.ph, uc, s);
+            rho[c] = s.rho;
+            pr[c] = s.p;
+            for (int k = 0; k < nk; ++k) Y[k][c] = s.Y[k];
+        }
+        const vector<double>& Vinv = P.ops.vleg_inv.at(E.N);
+        Ip[e] = modal_indicator(rho, E.N, Vinv);
+        double ih = modal_indicator(pr, E.N, Vinv);
+        for (int k = 0; k + 1 < nk; ++k) ih = std::min(ih, modal_indicator(Y[k], E.N, Vinv));
+        Ih[e] = ih;
+    }
+}
+
+}  // namespace
+
+// ==================================================================== C ABI
+extern "C" {
+
+int64_t oracle_state_size(const oracle_problem* p) {
+    try { return make_problem(p, false).size; } catch (...) { return -1; }
+}
+
+int oracle_elem_offsets(const oracle_problem* p, int64_t* off) {
+    try {
+        Problem P = make_problem(p, false);
+        for (size_t e = 0; e < P.el.size(); ++e) off[e] = P.el[e].off;
+        return 0;
+    } catch (...) { return -1; }
+}
+
+int oracle_eval_rhs(const oracle_problem* p, const double* U, double* R) {
+    try {
+        Problem P = make_problem(p);
+        eval_rhs_t<double>(P, U, R);
+        return 0;
+    } catch (...) { return -1; }
+}
+
+int oracle_eval_rhs_jvp(const oracle_problem* p, const double* U, const double* dU, double* R, double* dR) {
+    try {
+        Problem P = make_problem(p);
+        vector<Dual> u(P.size), r(P.size);
+        for (int64_t i = 0; i < P.size; ++i) u[i] = Dual(U[i], dU[i]);
+        eval_rhs_t<Dual>(P, u.data(), r.data());
+        for (int64_t i = 0; i < P.size; ++i) { R[i] = r[i].v; dR[i] = r[i].d; }
+        return 0;
+    } catch (...) { return -1; }
+}
+
+int oracle_count_flops(const oracle_problem* p, const double* U, double* out) {
+    try {
+        Problem P = make_problem(p);
+        vector<Counted> u(P.size), r(P.size);
+        for (int64_t i = 0; i < P.size; ++i) u[i] = Counted(U[i]);
+        flop_counter() = FlopCounter();
+        eval_rhs_t<Counted>(P, u.data(), r.data(), false);
+        out[0] = flop_counter().add;
+        out[1] = flop_counter().mul;
+        out[2] = flop_counter().div;
+        out[3] = flop_counter().sqrt;
+        out[4] = 0.0;
+        return 0;
+    } catch (...) { return -1; }
+}
+
+int oracle_dt(const oracle_problem* p, const double* U, double cfl_c, double cfl_v, double* out3) {
+    try {
+        Problem P = make_problem(p, false);
+        time_step(P, U, cfl_c, cfl_v, out3);
+        return 0;
+    } catch (...) { return -1; }
+}
+
+int oracle_rk3(const oracle_problem* p, double* U, int n_steps, double dt_fixed, double cfl_c,
+               double cfl_v, double* dts) {
+    try {
+        Problem P = make_problem(p);
+        for (int it = 0; it < n_steps; ++it) {
+            double dt = dt_fixed;
+            if (!(dt > 0.0)) {
+                double o[3];
+                time_step(P, U, cfl_c, cfl_v, o);
+                dt = o[0];
+            }
+            if (dts) dts[it] = dt;
+            ssp_rk3_step(P.size, U, dt, [&](const double* x, double* r) { eval_rhs_t<double>(P, x, r); });
+        }
+        return 0;
+    } catch (...) { return -1; }
+}
+
+double oracle_rk3_scalar_linear(double lambda, double dt, double u0) {
+    double u = u0;
+    ssp_rk3_step(1, &u, dt, [&](const double* x, double* r) { r[0] = lambda * x[0]; });
+    return u;
+}
+
+int oracle_indicator(const oracle_problem* p, const double* U, double* Ip, double* Ih) {
+    try {
+        Problem P = make_problem(p);
+        indicator(P, U, Ip, Ih);
+        return 0;
+    } catch (...) { return -1; }
+}
+
+// Reading of the threshold rule (values are configuration): DG -> FV when
+// I_h < T_fv_on; FV -> DG when I_h > T_fv_off; a DG element that stays DG
+// moves to N+1 when I_p < T_ref and to N-1 when I_p > T_crs, within
+// [N_min, N_max], one level per call.
+int oracle_adapt_decide(const oracle_problem* p, const double* Ip, const double* Ih, const double* thr,
+                        int N_min, int N_max, int8_t* N_new, uint8_t* fv_new) {
+    try {
+        Problem P = make_problem(p, false);
+        for (size_t e = 0; e < P.el.size(); ++e) {
+            const Elem& E = P.el[e];
+            int N = E.N;
+            bool fv = E.fv;
+            if (fv) {
+                if (Ih[e] > thr[1]) fv = false;
+            } else if (Ih[e] < thr[0]) {
+                fv = true;
+            } else if (Ip[e] < thr[2] && N < N_max) {
+                N = N + 1;
+            } else if (Ip[e] > thr[3] && N > N_min) {
+                N = N - 1;
+            }
+            N_new[e] = (int8_t)N;
+            fv_new[e] = fv ? 1 : 0;
+        }
+        return 0;
+    } catch (...) { return -1; }
+}
+
+int oracle_remap(const oracle_problem* p_old, const int8_t* N_new, const uint8_t* fv_new,
+                 const double* U_old, double* U_new) {
+    try {
+        Problem Po = make_problem(p_old, false);
+        oracle_problem pn = *p_old;
+        pn.N = N_new;
+        pn.fv = fv_new;
+        Problem Pn = make_problem(&pn, false);
+        const int V = Po.V;
+        for (size_t e = 0; e < Po.el.size(); ++e) {
+            const Elem &A = Po.el[e], &B = Pn.el[e];
+            const double* src = U_old + A.off;
+            double* dst = U_new + B.off;
+            vector<double> out;
+            if (A.fv == B.fv && A.n == B.n) {
+                out.assign(src, src + (int64_t)V * A.n * A.n * A.n);
+            } else if (!A.fv && !B.fv) {
+                out = map_volume(src, V, A.n, B.n, vmap(A.N, B.N));      // V^{N->N~}
+            } else if (!A.fv && B.fv) {
+                out = map_volume(src, V, A.n, B.n, dg2fv(A.N, Po.nfv));  // V^{DG->FV}
+            } else {
+                out = map_volume(src, V, A.n, B.n, fv2dg(B.N, Po.nfv));  // V^{FV->DG}
+            }
+            std::copy(out.begin(), out.end(), dst);
+        }
+        return 0;
+    } catch (...) { return -1; }
+}
+
+int oracle_basis(int N, double* x, double* w, double* D, double* Dhat, double* l_minus, double* l_plus) {
+    try {
+        Basis1D b = make_basis(N);
+        std::copy(b.x.begin(), b.x.end(), x);
+        std::copy(b.w.begin(), b.w.end(), w);
+        std::copy(b.D.begin(), b.D.end(), D);
+        std::copy(b.Dhat.begin(), b.Dhat.end(), Dhat);
+        std::copy(b.lm.begin(), b.lm.end(), l_minus);
+        std::copy(b.lp.begin(), b.lp.end(), l_plus);
+        return 0;
+    } catch (...) { return -1; }
+}
+
+int oracle_vmap(int N_from, int N_to, double* M) {
+    try { auto m = vmap(N_from, N_to); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }
+}
+int oracle_dg2fv(int N, int n_fv, double* M) {
+    try { auto m = dg2fv(N, n_fv); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }
+}
+int oracle_fv2dg(int N, int n_fv, double* M) {
+    try { auto m = fv2dg(N, n_fv); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }
+}
+int oracle_leg_vandermonde(int N, double* V) {
+    try { auto m = leg_vandermonde(N); std::copy(m.begin(), m.end(), V); return 0; } catch (...) { return -1; }
+}
+
+static Phys phys_only(const oracle_problem* p) {
+    Phys ph;
+    ph.nk = p->n_species;
+    for (int k = 0; k < ph.nk; ++k) {
+        ph.gamma[k] = p->gamma[k];
+        ph.R[k] = p->Rgas[k];
+        ph.cv[k] = p->Rgas[k] / (p->gamma[k] - 1.0);
+        ph.cp[k] = p->gamma[k] * ph.cv[k];
+        ph.mu[k] = p->mu[k];
+        ph.pr[k] = p->Pr[k];
+        ph.D[k] = p->Dk[k];
+    }
+    return ph;
+}
+
+int oracle_flux(const oracle_problem* p, const double* u, const double* g, int dir, double* Fc, double* Fv) {
+    Phys ph = phys_only(p);
+    Prim<double> s;
+    cons_to_prim(ph, u, s);
+    flux_conv(ph, u, s, dir, Fc);
+    flux_visc(ph, u, g, s, dir, Fv);
+    return 0;
+}
+
+int oracle_riemann(const oracle_problem* p, const double* uL, const double* uR, int dir, double* F) {
+    Phys ph = phys_only(p);
+    Prim<double> sL, sR;
+    cons_to_prim(ph, uL, sL);
+    cons_to_prim(ph, uR, sR);
+    riemann(ph, p->riemann, uL, sL, uR, sR, dir, F);
+    return 0;
+}
+
+int oracle_primitives(const oracle_problem* p, const double* u, double* out) {
+    Phys ph = phys_only(p);
+    Prim<double> s;
+    cons_to_prim(ph, u, s);
+    out[0] = s.rho; out[1] = s.p; out[2] = s.temp; out[3] = s.c; out[4] = s.kappa;
+    out[5] = s.cv; out[6] = s.cp; out[7] = s.mu; out[8] = s.lam;
+    for (int k = 0; k < ph.nk; ++k) out[9 + k] = s.Y[k];
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+/*
+ * Plain FP64 CPU oracle of the hp-adaptive hybrid DG/FV right-hand side
+ * U_t = R(U) for the multi-component compressible Navier-Stokes equations
+ * (Mossier, Kopper, Keim, Beck, Munz; arXiv 2502.19342).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package's smoke check
+ * and the benchmark's CPU-baseline leg may load this library.  It shares no
+ * code with the CUDA path and is written for readability, not speed.
+ *
+ * Conventions (shared with the CUDA path by specification, not by code):
+ *   - State ordering per point: rho_1..rho_Nk, rho*v_x, rho*v_y, rho*v_z, rho*E
+ *     (V = Nk + 4 conserved variables; rho = sum_k rho_k).
+ *   - Elements are ordered domain by domain, x fastest:
+ *     e = first_element(domain) + ix + nx*(iy + ny*iz).
+ *   - Element-contiguous state: U[off_e + v*n^3 + i + n*(j + n*k)] with
+ *     n = N_e + 1 for DG elements and n = N_FV for FV elements; off_e is the
+ *     exclusive prefix sum of V*n_e^3.
+ *   - All domains are periodic Cartesian boxes.
+ */
+#ifndef DGFV_ORACLE_H
+#define DGFV_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int n_domains;
+    const int32_t* dims;   /* 3 per domain: nx, ny, nz                   */
+    const double* lo;      /* 3 per domain: lower corner                 */
+    const double* hi;      /* 3 per domain: upper corner                 */
+    int n_fv;              /* FV sub-cells per direction (global)        */
+    int n_species;         /* Nk, 1..3                                   */
+    const double* gamma;   /* per species ratio of heat capacities       */
+    const double* Rgas;    /* per species specific gas constant          */
+    const double* mu;      /* per species dynamic viscosity              */
+    const double* Pr;      /* per species Prandtl number                 */
+    const double* Dk;      /* per species diffusion coefficient          */
+    int riemann;           /* 0 = local Lax-Friedrichs, 1 = Roe + Harten-Hyman */
+    const int8_t* N;       /* per element DG degree (kept while FV)      */
+    const uint8_t* fv;     /* per element: 1 = FV sub-cell element       */
+} oracle_problem;
+
+/* 0 on success, negative on a malformed problem. */
+int64_t oracle_state_size(const oracle_problem* p);
+int oracle_elem_offsets(const oracle_problem* p, int64_t* off);
+
+/* Semi-discrete right-hand side R(U), Sec. 3.1-3.2. */
+int oracle_eval_rhs(const oracle_problem* p, const double* U, double* R);
+
+/* Forward-mode directional derivative dR = R'(U) dU (dual numbers). */
+int oracle_eval_rhs_jvp(const oracle_problem* p, const double* U, const double* dU,
+                        double* R, double* dR);
+
+/* Floating-point operation count of one evaluation of R(U), counted on the
+ * oracle's own arithmetic: out[0] add/sub, out[1] mul, out[2] div, out[3] sqrt,
+ * out[4] other (abs, min/max compares are not counted). */
+int oracle_count_flops(const oracle_problem* p, const double* U, double* out);
+
+/* Time step of Sec. 3.3 (out: dt, min dt_c, min dt_v). */
+int oracle_dt(const oracle_problem* p, const double* U, double cfl_c, double cfl_v,
+              double* out3);
+
+/* n_steps SSP-RK3 steps in place; dt_fixed > 0 uses that step, otherwise the
+ * CFL step of Sec. 3.3 recomputed from U at the start of every step.
+ * dts (optional, n_steps entries) receives the steps taken. */
+int oracle_rk3(const oracle_problem* p, double* U, int n_steps, double dt_fixed,
+               double cfl_c, double cfl_v, double* dts);
+
+/* One SSP-RK3 step of the scalar ODE u' = lambda*u, through the same stage
+ * combination routine as oracle_rk3 (test hook for the stage coefficients). */
+double oracle_rk3_scalar_linear(double lambda, double dt, double u0);
+
+/* Modal indicator of Sec. 3.4 per element: Ip = I(rho), Ih = min(I(p), I(Y_k)). */
+int oracle_indicator(const oracle_problem* p, const double* U, double* Ip, double* Ih);
+
+/* Adaptation decision per element from Ip, Ih and thresholds
+ * thr = {T_fv_on, T_fv_off, T_ref, T_crs}; writes the new N and FV flags. */
+int oracle_adapt_decide(const oracle_problem* p, const double* Ip, const double* Ih,
+                        const double* thr, int N_min, int N_max,
+                        int8_t* N_new, uint8_t* fv_new);
+
+/* State re-layout for new degrees / FV flags (Sec. 3.2 mappings). */
+int oracle_remap(const oracle_problem* p_old, const int8_t* N_new, const uint8_t* fv_new,
+                 const double* U_old, double* U_new);
+
+/* Reference-element operators (for pins). Matrices are row-major. */
+int oracle_basis(int N, double* x, double* w, double* D, double* Dhat,
+                 double* l_minus, double* l_plus);
+int oracle_vmap(int N_from, int N_to, double* M);          /* (N_to+1) x (N_from+1) */
+int oracle_dg2fv(int N, int n_fv, double* M);              /* n_fv x (N+1)          */
+int oracle_fv2dg(int N, int n_fv, double* M);              /* (N+1) x n_fv          */
+int oracle_leg_vandermonde(int N, double* V);              /* V[i][m] = Lhat_m(x_i) */
+
+/* Pointwise physics (for pins): convective and viscous flux in direction
+ * dir of state u (V) and conservative gradient g (3*V, g[d*V+v] = du_v/dx_d). */
+int oracle_flux(const oracle_problem* p, const double* u, const double* g, int dir,
+                double* Fc, double* Fv);
+int oracle_riemann(const oracle_problem* p, const double* uL, const double* uR, int dir,
+                   double* F);
+int oracle_primitives(const oracle_problem* p, const double* u, double* out);
+/* out: rho, p, T, c, kappa, cv, cp, mu, lambda, Y_1..Y_Nk */
+
+#ifdef __cplusplus
+}
+#endif
+#endif

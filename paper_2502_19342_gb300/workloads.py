@@ -1,0 +1,324 @@
+"""Seeded synthetic workloads: meshes, degree / FV patterns and initial states.
+
+This module only builds inputs.  It holds no step of the right-hand side: the
+one piece of physics here is the ideal-gas mixture relation used to turn an
+initial (rho_k, v, p) field into conserved variables, which is how each
+workload's initial condition is specified.  It is shared by the tests, the
+benchmark and the CPU oracle's callers; it imports neither the CUDA binding
+nor the oracle.
+
+A *problem* is a plain dict (see ``make_problem``); states are flat float64
+arrays in the element-contiguous layout
+
+    U[off_e + v*n^3 + i + n*(j + n*k)],  n = N_e+1 (DG) or n_fv (FV),
+
+with variables (rho_1..rho_Nk, rho v_x, rho v_y, rho v_z, rho E) and elements
+ordered domain by domain, x fastest.
+"""
+import math
+
+import numpy as np
+
+# Universal gas constant in the nondimensional units of every workload.
+R_UNIVERSAL = 1.0
+
+AIR = dict(gamma=1.4, M=29.0)
+HEAVY = dict(gamma=1.249, M=3.5 * 29.0)  # density ratio 3.5 to air at equal p, T
+CO2 = dict(gamma=1.3, M=44.0)
+HELIUM = dict(gamma=1.67, M=4.0)
+
+
+def species_set(specs, mu=0.0, Pr=0.72, Sc=1.0, rho_ref=1.0):
+    """Species property arrays; D_k = mu / (Sc rho_ref) (constant, Sec. 2)."""
+    n = len(specs)
+    return dict(
+        gamma=np.array([s["gamma"] for s in specs], float),
+        Rgas=np.array([R_UNIVERSAL / s["M"] for s in specs], float),
+        mu=np.full(n, float(mu)),
+        Pr=np.full(n, float(Pr)),
+        Dk=np.full(n, float(mu) / (Sc * rho_ref)),
+    )
+
+
+def make_problem(domains, species, n_fv, N, fv=None, riemann=0):
+    """domains: list of (dims(3), lo(3), hi(3)); species: dict from species_set."""
+    dims = np.array([d[0] for d in domains], np.int32).reshape(-1, 3)
+    lo = np.array([d[1] for d in domains], float).reshape(-1, 3)
+    hi = np.array([d[2] for d in domains], float).reshape(-1, 3)
+    n_elem = int(np.prod(dims, axis=1).sum())
+    N = np.broadcast_to(np.asarray(N, np.int8), (n_elem,)).copy()
+    fv = np.zeros(n_elem, np.uint8) if fv is None else np.broadcast_to(np.asarray(fv, np.uint8), (n_elem,)).copy()
+    p = dict(dims=dims, lo=lo, hi=hi, n_fv=int(n_fv), riemann=int(riemann), N=N, fv=fv)
+    p.update({k: np.array(v, float) for k, v in species.items()})
+    return p
+
+
+def n_elements(prob):
+    return int(np.prod(prob["dims"], axis=1).sum())
+
+
+def n_vars(prob):
+    return len(prob["gamma"]) + 4
+
+
+def points_per_dir(prob):
+    return np.where(prob["fv"] != 0, prob["n_fv"], prob["N"].astype(np.int64) + 1)
+
+
+def offsets(prob):
+    n = points_per_dir(prob)
+    sizes = n_vars(prob) * n ** 3
+    off = np.zeros(len(n), np.int64)
+    off[1:] = np.cumsum(sizes)[:-1]
+    return off, int(sizes.sum())
+
+
+def n_dofs(prob):
+    """Degrees of freedom: nodes of DG elements plus sub-cells of FV elements."""
+    return int((points_per_dir(prob) ** 3).sum())
+
+
+def element_index(prob):
+    """Per element: domain id, integer position (3), lower corner (3), size h (3)."""
+    dom, pos, corner, h = [], [], [], []
+    for d, (dm, lo, hi) in enumerate(zip(prob["dims"], prob["lo"], prob["hi"])):
+        nx, ny, nz = (int(x) for x in dm)
+        hd = (hi - lo) / dm
+        k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        ijk = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)
+        dom.append(np.full(len(ijk), d))
+        pos.append(ijk)
+        corner.append(lo + ijk * hd)
+        h.append(np.broadcast_to(hd, ijk.shape))
+    return np.concatenate(dom), np.concatenate(pos), np.concatenate(corner), np.concatenate(h)
+
+
+def _ref_points(n, is_fv):
+    """Reference coordinates of the points of one direction: LG nodes (numpy's
+    Gauss-Legendre rule) for DG, sub-cell centres for FV."""
+    if is_fv:
+        return -1.0 + (np.arange(n) + 0.5) * (2.0 / n)
+    return np.polynomial.legendre.leggauss(n)[0]
+
+
+def build_state(prob, prim_fn, chunk=4096):
+    """Evaluate prim_fn(x, y, z) -> (rho_k list, (vx, vy, vz), p) at every point
+    and convert to the conserved variables with the ideal-gas mixture law
+    (rho E = p / (kappa_mix - 1) + rho |v|^2 / 2)."""
+    nk = len(prob["gamma"])
+    V = nk + 4
+    cv = prob["Rgas"] / (prob["gamma"] - 1.0)
+    cp = prob["gamma"] * cv
+    off, size = offsets(prob)
+    U = np.zeros(size)
+    _, _, corner, h = element_index(prob)
+    npd = points_per_dir(prob)
+    fv = prob["fv"] != 0
+    for n in np.unique(npd):
+        for isfv in (False, True):
+            sel = np.nonzero((npd == n) & (fv == isfv))[0]
+            if len(sel) == 0:
+                continue
+            r = _ref_points(int(n), isfv)
+            kk, jj, ii = np.meshgrid(r, r, r, indexing="ij")
+            ref = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1)  # (n^3, 3), x fastest
+            for s in range(0, len(sel), chunk):
+                es = sel[s:s + chunk]
+                X = corner[es][:, None, :] + (ref[None, :, :] + 1.0) * 0.5 * h[es][:, None, :]
+                rk, vel, p = prim_fn(X[..., 0], X[..., 1], X[..., 2])
+                rk = [np.broadcast_to(q, X.shape[:2]) for q in rk]
+                vel = [np.broadcast_to(q, X.shape[:2]) for q in vel]
+                p = np.broadcast_to(p, X.shape[:2])
+                rho = sum(rk)
+                cvm = sum(rk[k] * cv[k] for k in range(nk)) / rho
+                cpm = sum(rk[k] * cp[k] for k in range(nk)) / rho
+                kap = cpm / cvm
+                fields = list(rk) + [rho * vel[0], rho * vel[1], rho * vel[2],
+                                     p / (kap - 1.0) + 0.5 * rho * (vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2)]
+                blk = np.stack(fields, axis=1)  # (ne, V, n^3)
+                n3 = int(n) ** 3
+                idx = off[es][:, None] + np.arange(V * n3)[None, :]
+                U[idx.ravel()] = blk.reshape(len(es), V * n3).ravel()
+    return U
+
+
+def constant_state(prob, rho_k, v, p):
+    return build_state(prob, lambda x, y, z: ([np.full(x.shape, r) for r in rho_k], v, np.full(x.shape, p)))
+
+
+# ----------------------------------------------------------------- random patterns
+def random_degrees(n_elem, lo, hi, seed):
+    rng = np.random.default_rng(seed)
+    return rng.integers(lo, hi + 1, size=n_elem).astype(np.int8)
+
+
+def random_fv(n_elem, frac, seed):
+    rng = np.random.default_rng(seed + 7919)
+    return (rng.random(n_elem) < frac).astype(np.uint8)
+
+
+def smooth_random_state(prob, seed, amp=0.05, rho0=1.0, p0=1.0, vel=(0.3, -0.2, 0.1)):
+    """Smooth periodic random-phase state (low Fourier modes of each domain box)."""
+    rng = np.random.default_rng(seed + 104729)
+    nk = len(prob["gamma"])
+    modes = [(a, b, c) for a in range(0, 2) for b in range(0, 2) for c in range(0, 2) if (a, b, c) != (0, 0, 0)]
+    ph = rng.uniform(0, 2 * np.pi, size=(nk + 4, len(modes)))
+    lo0, hi0 = prob["lo"][0], prob["hi"][0]
+    L = hi0 - lo0
+
+    def wave(x, y, z, q):
+        s = 0.0
+        for m, (a, b, c) in enumerate(modes):
+            s = s + np.cos(2 * np.pi * (a * (x - lo0[0]) / L[0] + b * (y - lo0[1]) / L[1] + c * (z - lo0[2]) / L[2]) + ph[q, m])
+        return s / len(modes)
+
+    def fn(x, y, z):
+        Y1 = 0.5 + 0.3 * wave(x, y, z, 0)
+        fr = [Y1] + [(1.0 - Y1) / (nk - 1)] * (nk - 1) if nk > 1 else [1.0 + 0 * x]
+        rho = rho0 * (1.0 + amp * wave(x, y, z, 1))
+        rk = [rho * f for f in fr]
+        v = [vel[i] + amp * wave(x, y, z, 2 + i) for i in range(3)]
+        p = p0 * (1.0 + amp * wave(x, y, z, 5))
+        return rk, v, p
+
+    return build_state(prob, fn)
+
+
+# ----------------------------------------------------------------- paper-shaped workloads
+def plain_tiny(seed=0, riemann=0):
+    """3D periodic [0,1]^3, 4x4x4 elements, uniform N=3, two species
+    (gamma 1.4 / M 29 and gamma 1.67 / M 4), viscosity 1e-3, Pr 0.72, Sc 1.
+    Uniform velocity (1, 0.5, 0.25) at p = 1, Y_1 = 0.5 + 0.4 sin(2 pi x) sin(2 pi y),
+    density 1 + 1e-3 * (8 random-phase cosine modes)."""
+    sp = species_set([AIR, HELIUM], mu=1e-3, Pr=0.72, Sc=1.0)
+    prob = make_problem([((4, 4, 4), (0, 0, 0), (1, 1, 1))], sp, n_fv=4, N=3, riemann=riemann)
+    rng = np.random.default_rng(seed)
+    ks = [(a, b, c) for a in (1, 2) for b in (1, 2) for c in (1, 2)]
+    ph = rng.uniform(0, 2 * np.pi, len(ks))
+
+    def fn(x, y, z):
+        Y1 = 0.5 + 0.4 * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
+        rho = 1.0 + 1e-3 * sum(np.cos(2 * np.pi * (a * x + b * y + c * z) + ph[m]) for m, (a, b, c) in enumerate(ks))
+        return [rho * Y1, rho * (1 - Y1)], (1.0, 0.5, 0.25), np.ones_like(x)
+
+    return prob, build_state(prob, fn)
+
+
+SHOCK_MACH = 1.5
+
+
+def _post_shock(gamma, Ms, rho1=1.0, p1=1.0):
+    """Rankine-Hugoniot state behind a shock of Mach Ms moving into gas at rest."""
+    r = (gamma + 1) * Ms ** 2 / ((gamma - 1) * Ms ** 2 + 2)
+    pr = 1 + 2 * gamma / (gamma + 1) * (Ms ** 2 - 1)
+    c1 = math.sqrt(gamma * p1 / rho1)
+    u2 = Ms * c1 * (1 - 1 / r)
+    return rho1 * r, p1 * pr, u2
+
+
+def hp_shock(seed=0, nel=(16, 16, 16), riemann=0, mu=1e-4):
+    """[0,2]x[0,1]x[0,1], periodic, 16^3 elements, N drawn from {2..6},
+    N_FV = 7; a Mach 1.5 planar shock in air at x = 0.4 moving +x towards a
+    bubble (r = 0.2, centre (0.8, 0.5, 0.5)) of the heavy species (density
+    ratio 3.5), interface smoothed over 2 node spacings of degree 4."""
+    sp = species_set([AIR, HEAVY], mu=mu)
+    n_elem = nel[0] * nel[1] * nel[2]
+    N = random_degrees(n_elem, 2, 6, seed)
+    prob = make_problem([(nel, (0, 0, 0), (2, 1, 1))], sp, n_fv=7, N=N, riemann=riemann)
+    rho2, p2, u2 = _post_shock(AIR["gamma"], SHOCK_MACH)
+    T0 = 1.0 / (1.0 * sp["Rgas"][0])  # air at rho = p = 1
+    width = 2 * (1.0 / nel[1]) / 5.0
+    xs = 0.4
+
+    def fn(x, y, z):
+        r = np.sqrt((x - 0.8) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2)
+        Yb = 0.5 * (1 - np.tanh((r - 0.2) / width))
+        s = 0.5 * (1 - np.tanh((x - xs) / width))  # 1 behind the shock
+        Rm = (1 - Yb) * sp["Rgas"][0] + Yb * sp["Rgas"][1]
+        p = 1.0 + s * (p2 - 1.0)
+        rho_pre = 1.0 / (Rm * T0)
+        rho = rho_pre * (1 - s) + rho2 * s
+        vx = s * u2
+        return [rho * (1 - Yb), rho * Yb], (vx, 0.0 * x, 0.0 * x), p
+
+    return prob, build_state(prob, fn)
+
+
+def _fourier_coeffs(rng, kmax, spectrum, solenoidal):
+    k1 = np.arange(-kmax, kmax + 1)
+    KX, KY, KZ = np.meshgrid(k1, k1, k1, indexing="ij")
+    kk = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)
+    mask = (kk > 0) & (kk <= kmax)
+    amp = np.where(mask, np.sqrt(spectrum(np.maximum(kk, 1e-12)) / (4 * np.pi * np.maximum(kk, 1) ** 2)), 0.0)
+    ncomp = 3 if solenoidal else 1
+    c = (rng.standard_normal((ncomp,) + kk.shape) + 1j * rng.standard_normal((ncomp,) + kk.shape)) * amp
+    if solenoidal:
+        kv = np.stack([KX, KY, KZ]).astype(float)
+        kn = np.where(kk > 0, kk, 1.0)
+        dot = (c * kv).sum(0) / kn ** 2
+        c = c - dot[None] * kv
+    return k1, c
+
+
+def _eval_fourier(k1, c, X, Y, Z, L=2 * np.pi):
+    """Real part of sum_k c_k exp(i 2pi/L k.x) at points (X, Y, Z) of shape (ne, n^3)."""
+    w = 2 * np.pi / L
+    ex = np.exp(1j * w * X[..., None] * k1)  # (ne, P, K)
+    ey = np.exp(1j * w * Y[..., None] * k1)
+    ez = np.exp(1j * w * Z[..., None] * k1)
+    out = []
+    for comp in c:
+        t = np.einsum("epk,ijk->epij", ez, comp, optimize=True)
+        t = np.einsum("epj,epij->epi", ey, t, optimize=True)
+        out.append(np.real(np.einsum("epi,epi->ep", ex, t, optimize=True)))
+    return out
+
+
+def turbulence(seed=0, nel=(48, 48, 48), riemann=0, mu=5e-4, Mt=0.3, k0=4.0, kmax=8):
+    """Periodic [0,2pi]^3, 48^3 elements, N drawn from {1..7}, 3 species
+    (gamma 1.4/1.3/1.67, M 29/44/4), N_FV = 8.  Random-phase solenoidal
+    velocity with E(k) ~ k^4 exp(-2 (k/k0)^2), k0 = 4, scaled to turbulent Mach
+    0.3; species blobs from thresholded Gaussian random fields smoothed by tanh
+    over about 2 node spacings; p = 1 and uniform temperature."""
+    sp = species_set([AIR, CO2, HELIUM], mu=mu)
+    n_elem = nel[0] * nel[1] * nel[2]
+    N = random_degrees(n_elem, 1, 7, seed)
+    L = 2 * np.pi
+    prob = make_problem([(nel, (0, 0, 0), (L, L, L))], sp, n_fv=8, N=N, riemann=riemann)
+    rng = np.random.default_rng(seed + 1)
+    k1, cu = _fourier_coeffs(rng, kmax, lambda k: k ** 4 * np.exp(-2 * (k / k0) ** 2), True)
+    _, cb1 = _fourier_coeffs(rng, 3, lambda k: np.exp(-(k / 2.0) ** 2), False)
+    _, cb2 = _fourier_coeffs(rng, 3, lambda k: np.exp(-(k / 2.0) ** 2), False)
+    T0 = 1.0 / sp["Rgas"][0]
+    c0 = math.sqrt(1.4)
+    # normalise the velocity to the turbulent Mach number with a coarse sample
+    g = np.linspace(0, L, 24, endpoint=False)
+    gx, gy, gz = np.meshgrid(g, g, g, indexing="ij")
+    vs = _eval_fourier(k1, cu, gx.reshape(1, -1), gy.reshape(1, -1), gz.reshape(1, -1))
+    urms = math.sqrt(np.mean(vs[0] ** 2 + vs[1] ** 2 + vs[2] ** 2))
+    vscale = Mt * c0 / urms
+    b1s = _eval_fourier(np.arange(-3, 4), cb1, gx.reshape(1, -1), gy.reshape(1, -1), gz.reshape(1, -1))[0]
+    b2s = _eval_fourier(np.arange(-3, 4), cb2, gx.reshape(1, -1), gy.reshape(1, -1), gz.reshape(1, -1))[0]
+    s1, s2 = b1s.std(), b2s.std()
+    h = L / nel[0]
+    width = 2 * h / 5.0
+
+    def fn(x, y, z):
+        v = _eval_fourier(k1, cu, x, y, z)
+        g1 = _eval_fourier(np.arange(-3, 4), cb1, x, y, z)[0] / s1
+        g2 = _eval_fourier(np.arange(-3, 4), cb2, x, y, z)[0] / s2
+        # unit-slope-normalised level sets, smoothed over ~2 node spacings
+        b1 = 0.5 * (1 + np.tanh(g1 / (width * 1.5)))
+        b2 = 0.5 * (1 + np.tanh(g2 / (width * 1.5)))
+        Y2 = 0.6 * b1 * (1 - b2)
+        Y3 = 0.6 * b2
+        Y1 = 1.0 - Y2 - Y3
+        Rm = Y1 * sp["Rgas"][0] + Y2 * sp["Rgas"][1] + Y3 * sp["Rgas"][2]
+        rho = 1.0 / (Rm * T0)
+        return [rho * Y1, rho * Y2, rho * Y3], tuple(vscale * q for q in v), np.ones_like(x)
+
+    return prob, build_state(prob, fn, chunk=1024)
+
+
+# Indicator thresholds {T_fv_on, T_fv_off, T_ref, T_crs} (configuration values).
+THRESHOLDS = (1.0, 1.6, 3.0, 7.0)

@@ -1,0 +1,270 @@
+"""Pins of the oracle's pointwise physics (Sec. 2) and Riemann solvers
+(Sec. 3.1.1) against closed forms, symmetries and a textbook Roe solver."""
+import numpy as np
+import pytest
+
+from paper_2502_19342_gb300 import workloads as W
+
+
+def _prob(nk, riemann=0, mu=1e-2, D=3e-3, Pr=(0.72, 0.7, 0.68)):
+    specs = [W.AIR, W.CO2, W.HELIUM][:nk]
+    sp = W.species_set(specs, mu=mu)
+    sp["Pr"] = np.array(Pr[:nk])
+    sp["Dk"] = np.array([D, 2 * D, 0.5 * D][:nk])
+    sp["mu"] = np.array([mu, 0.7 * mu, 1.3 * mu][:nk])
+    sp["riemann"] = riemann
+    return sp
+
+
+def _state(rng, nk, rho=(0.6, 0.3, 0.2), v=None, p=1.3, prob=None):
+    rk = np.array(rho[:nk]) * (1 + 0.1 * rng.random(nk))
+    v = rng.standard_normal(3) * 0.4 if v is None else np.asarray(v, float)
+    rhot = rk.sum()
+    cv = prob["Rgas"] / (prob["gamma"] - 1)
+    kap = (rk @ (prob["gamma"] * cv)) / (rk @ cv)
+    rE = p / (kap - 1) + 0.5 * rhot * v @ v
+    return np.concatenate([rk, rhot * v, [rE]])
+
+
+def test_single_species_reduces_to_gamma_law(oracle):
+    prob = _prob(1)
+    u = np.array([1.3, 0.4, -0.2, 0.1, 3.0])
+    s = oracle.primitives(prob, u)
+    g, R = prob["gamma"][0], prob["Rgas"][0]
+    p = (g - 1) * (u[4] - 0.5 * (u[1] ** 2 + u[2] ** 2 + u[3] ** 2) / u[0])
+    assert abs(s["p"] - p) < 1e-14
+    assert abs(s["T"] - p / (u[0] * R)) < 1e-12
+    assert abs(s["c"] - np.sqrt(g * p / u[0])) < 1e-14
+    assert abs(s["kappa"] - g) < 1e-15
+
+
+def test_identical_species_equal_single_species(oracle):
+    p1 = _prob(1)
+    p2 = dict(p1)
+    for k in ("gamma", "Rgas", "mu", "Pr", "Dk"):
+        p2[k] = np.array([p1[k][0], p1[k][0]])
+    rng = np.random.default_rng(3)
+    u1 = _state(rng, 1, prob=p1)
+    u2 = np.concatenate([[0.3 * u1[0], 0.7 * u1[0]], u1[1:]])
+    g1 = rng.standard_normal(3 * 5)
+    # split the density gradient between the two (identical) species
+    g2 = np.zeros(3 * 6)
+    for d in range(3):
+        g2[d * 6 + 0] = 0.3 * g1[d * 5]
+        g2[d * 6 + 1] = 0.7 * g1[d * 5]
+        g2[d * 6 + 2:d * 6 + 6] = g1[d * 5 + 1:d * 5 + 5]
+    for d in range(3):
+        Fc1, Fv1 = oracle.flux(p1, u1, g1, d)
+        Fc2, Fv2 = oracle.flux(p2, u2, g2, d)
+        np.testing.assert_allclose(Fc2[0] + Fc2[1], Fc1[0], rtol=1e-14)
+        np.testing.assert_allclose(Fc2[2:], Fc1[1:], rtol=1e-14, atol=1e-15)
+        np.testing.assert_allclose(Fv2[0] + Fv2[1], Fv1[0], atol=1e-15)
+        np.testing.assert_allclose(Fv2[2:], Fv1[1:], rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("nk", [1, 2, 3])
+def test_species_diffusion_fluxes_sum_to_zero(oracle, nk):
+    prob = _prob(nk)
+    rng = np.random.default_rng(nk)
+    for _ in range(5):
+        u = _state(rng, nk, prob=prob)
+        g = rng.standard_normal(3 * (nk + 4))
+        for d in range(3):
+            _, Fv = oracle.flux(prob, u, g, d)
+            assert abs(Fv[:nk].sum()) < 1e-15
+
+
+def _permute(u, g, nk, perm):
+    """Relabel the axes: new axis perm[i] carries old axis i."""
+    V = nk + 4
+    u2 = u.copy()
+    for i in range(3):
+        u2[nk + perm[i]] = u[nk + i]
+    g2 = np.zeros_like(g)
+    for d in range(3):
+        gd = g[d * V:(d + 1) * V].copy()
+        gd2 = gd.copy()
+        for i in range(3):
+            gd2[nk + perm[i]] = gd[nk + i]
+        g2[perm[d] * V:(perm[d] + 1) * V] = gd2
+    return u2, g2
+
+
+@pytest.mark.parametrize("perm", [(1, 2, 0), (2, 0, 1), (1, 0, 2), (0, 2, 1)])
+def test_fluxes_are_covariant_under_axis_relabelling(oracle, perm):
+    nk = 3
+    prob = _prob(nk)
+    rng = np.random.default_rng(11)
+    u = _state(rng, nk, prob=prob)
+    g = rng.standard_normal(3 * (nk + 4))
+    u2, g2 = _permute(u, g, nk, perm)
+    for d in range(3):
+        Fc, Fv = oracle.flux(prob, u, g, d)
+        Fc2, Fv2 = oracle.flux(prob, u2, g2, perm[d])
+        Fc_p, _ = _permute(Fc, np.zeros(3 * (nk + 4)), nk, perm)
+        Fv_p, _ = _permute(Fv, np.zeros(3 * (nk + 4)), nk, perm)
+        np.testing.assert_allclose(Fc2, Fc_p, rtol=1e-14, atol=1e-15)
+        np.testing.assert_allclose(Fv2, Fv_p, rtol=1e-13, atol=1e-15)
+
+
+def test_viscous_flux_closed_forms(oracle):
+    nk = 2
+    prob = _prob(nk, D=2e-3)
+    prob["Dk"] = np.array([2e-3, 2e-3])
+    mu = prob["mu"]
+    rk = np.array([0.7, 0.5])
+    rho = rk.sum()
+    Y = rk / rho
+    p = 1.1
+    cv = prob["Rgas"] / (prob["gamma"] - 1)
+    cp = prob["gamma"] * cv
+    cvm, cpm = Y @ cv, Y @ cp
+    kap = cpm / cvm
+    u = np.concatenate([rk, [0, 0, 0], [p / (kap - 1)]])
+    V = nk + 4
+    mum = Y @ mu
+    prm = Y @ prob["Pr"]
+    T = p / (rho * (cpm - cvm))
+    # shear: only d(rho v_y)/dx = a
+    g = np.zeros(3 * V)
+    a = 0.37
+    g[0 * V + nk + 1] = a
+    _, Fx = oracle.flux(prob, u, g, 0)
+    _, Fy = oracle.flux(prob, u, g, 1)
+    assert abs(Fx[nk + 1] - (-mum * a / rho)) < 1e-16
+    assert abs(Fy[nk + 0] - (-mum * a / rho)) < 1e-16
+    # dilatation: only d(rho v_x)/dx = a: tau_xx = 4/3 mu a/rho, tau_yy = -2/3 mu a/rho
+    g = np.zeros(3 * V)
+    g[0 * V + nk + 0] = a
+    _, Fx = oracle.flux(prob, u, g, 0)
+    _, Fy = oracle.flux(prob, u, g, 1)
+    assert abs(Fx[nk] - (-4.0 / 3.0 * mum * a / rho)) < 1e-15
+    assert abs(Fy[nk + 1] - (2.0 / 3.0 * mum * a / rho)) < 1e-15
+    # heat conduction at rest: only d(rho E)/dz = q -> grad T = q/(rho cv)
+    g = np.zeros(3 * V)
+    q = 0.21
+    g[2 * V + nk + 3] = q
+    _, Fz = oracle.flux(prob, u, g, 2)
+    lam = mum * cpm / prm
+    assert abs(Fz[nk + 3] - (-lam * q / (rho * cvm))) < 1e-15  # F^v = q_h = -lambda grad T
+    # Fickian diffusion at rest and fixed rho: d(rho_1)/dy = s = -d(rho_2)/dy,
+    # equal D: J_1 = -D s; q_d = (cp_1 - cp_2) T J_1 plus heat conduction from grad c_v.
+    g = np.zeros(3 * V)
+    s = 0.3
+    g[1 * V + 0] = s
+    g[1 * V + 1] = -s
+    _, Fy = oracle.flux(prob, u, g, 1)
+    D = prob["Dk"][0]
+    assert abs(Fy[0] - (-D * s)) < 1e-16
+    assert abs(Fy[1] - (D * s)) < 1e-16
+    dYdy = s / rho
+    dTdy = -T * (cv[0] - cv[1]) * dYdy / cvm
+    expected_E = -lam * dTdy + (cp[0] - cp[1]) * T * (-D * s)
+    assert abs(Fy[nk + 3] - expected_E) < 1e-14
+
+
+def _mirror(u, nk, d):
+    m = u.copy()
+    m[nk + d] = -m[nk + d]
+    return m
+
+
+@pytest.mark.parametrize("riemann", [0, 1])
+@pytest.mark.parametrize("nk", [1, 2, 3])
+def test_riemann_consistency_and_mirror_symmetry(oracle, riemann, nk):
+    prob = _prob(nk, riemann=riemann)
+    rng = np.random.default_rng(5 + nk)
+    for _ in range(4):
+        uL = _state(rng, nk, prob=prob, p=1.0 + rng.random())
+        uR = _state(rng, nk, prob=prob, p=1.0 + rng.random())
+        for d in range(3):
+            Fc, _ = oracle.flux(prob, uL, np.zeros(3 * (nk + 4)), d)
+            np.testing.assert_allclose(oracle.riemann(prob, uL, uL, d), Fc, rtol=1e-13, atol=1e-14)
+            # reflecting the normal: F*(uL,uR) = -M F*(M uR, M uL)
+            F = oracle.riemann(prob, uL, uR, d)
+            Fm = oracle.riemann(prob, _mirror(uR, nk, d), _mirror(uL, nk, d), d)
+            np.testing.assert_allclose(F, -_mirror(Fm, nk, d), rtol=1e-12, atol=1e-13)
+
+
+def _textbook_roe(uL, uR, gamma, d, hh=True):
+    """Single-gas Roe flux with Harten-Hyman fix (standard textbook form)."""
+    def prim(u):
+        rho = u[0]
+        v = u[1:4] / rho
+        p = (gamma - 1) * (u[4] - 0.5 * rho * v @ v)
+        return rho, v, p
+
+    def flux(u):
+        rho, v, p = prim(u)
+        F = u * v[d]
+        F[1 + d] += p
+        F[4] += p * v[d]
+        return F
+
+    rL, vL, pL = prim(uL)
+    rR, vR, pR = prim(uR)
+    HL = (uL[4] + pL) / rL
+    HR = (uR[4] + pR) / rR
+    sL, sR = np.sqrt(rL), np.sqrt(rR)
+    v = (sL * vL + sR * vR) / (sL + sR)
+    H = (sL * HL + sR * HR) / (sL + sR)
+    a = np.sqrt((gamma - 1) * (H - 0.5 * v @ v))
+    rt = sL * sR
+    dp, drho, dv = pR - pL, rR - rL, vR - vL
+    un = v[d]
+    n = np.zeros(3)
+    n[d] = 1
+    waves = []
+    a1 = (dp - rt * a * dv[d]) / (2 * a * a)
+    waves.append((un - a, a1, np.concatenate([[1], v - a * n, [H - un * a]])))
+    a2 = drho - dp / (a * a)
+    waves.append((un, a2, np.concatenate([[1], v, [0.5 * v @ v]])))
+    for t in range(3):
+        if t == d:
+            continue
+        et = np.zeros(3)
+        et[t] = 1
+        waves.append((un, rt * dv[t], np.concatenate([[0], et, [v[t]]])))
+    a5 = (dp + rt * a * dv[d]) / (2 * a * a)
+    waves.append((un + a, a5, np.concatenate([[1], v + a * n, [H + un * a]])))
+    cL, cR = np.sqrt(gamma * pL / rL), np.sqrt(gamma * pR / rR)
+    lam_side = {0: (vL[d] - cL, vR[d] - cR), len(waves) - 1: (vL[d] + cL, vR[d] + cR)}
+    diss = np.zeros(5)
+    for i, (lam, al, K) in enumerate(waves):
+        aa = abs(lam)
+        if hh and i in lam_side:
+            lL, lR = lam_side[i]
+            delta = max(0.0, lam - lL, lR - lam)
+            if aa < delta:
+                aa = delta
+        diss += aa * al * K
+    return 0.5 * (flux(uL) + flux(uR)) - 0.5 * diss
+
+
+def test_roe_single_species_equals_textbook(oracle):
+    prob = _prob(1, riemann=1)
+    g = prob["gamma"][0]
+    rng = np.random.default_rng(9)
+    for case in range(8):
+        uL = _state(rng, 1, prob=prob, p=1.0 + rng.random())
+        uR = _state(rng, 1, prob=prob, p=0.5 + rng.random())
+        if case == 0:  # transonic rarefaction: exercises the entropy fix
+            uL = _state(rng, 1, v=(-0.2, 0.1, 0), prob=prob, p=3.0)
+            uR = _state(rng, 1, v=(1.6, 0.1, 0), prob=prob, p=0.3)
+        for d in range(3):
+            np.testing.assert_allclose(oracle.riemann(prob, uL, uR, d), _textbook_roe(uL, uR, g, d),
+                                       rtol=1e-12, atol=1e-13)
+
+
+def test_llf_textbook_form(oracle):
+    prob = _prob(2, riemann=0)
+    rng = np.random.default_rng(2)
+    uL = _state(rng, 2, prob=prob)
+    uR = _state(rng, 2, prob=prob, p=0.6)
+    for d in range(3):
+        FL, _ = oracle.flux(prob, uL, np.zeros(18), d)
+        FR, _ = oracle.flux(prob, uR, np.zeros(18), d)
+        sL, sR = oracle.primitives(prob, uL), oracle.primitives(prob, uR)
+        smax = max(abs(uL[2 + d] / sL["rho"]) + sL["c"], abs(uR[2 + d] / sR["rho"]) + sR["c"])
+        np.testing.assert_allclose(oracle.riemann(prob, uL, uR, d), 0.5 * (FL + FR) - 0.5 * smax * (uR - uL),
+                                   rtol=1e-14, atol=1e-15)
