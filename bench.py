@@ -1,0 +1,322 @@
+"""Throughput benchmark of the hp-adaptive hybrid DG/FV right-hand side.
+
+Workload (default): the turbulent multi-component decay case -- 48^3 periodic
+elements on [0, 2 pi]^3, degrees N in {1..7} (seeded, then driven by the modal
+indicator), 3 species, N_FV = 8, viscous, local Lax-Friedrichs.  One bench
+step is one adaptation cycle: the modal indicator + remap followed by 10
+SSP-RK3 steps (each: CFL time step + 3 evaluations of R(U)), i.e. 30 RK stages.
+
+Metric: DOF-stage updates per second (a DOF is a DG node or an FV sub-cell).
+  value     device-resident throughput, CUDA events around K timed steps
+  e2e       the same through the C ABI with the state copied host->device
+            before and device->host after every step (pinned host memory)
+  roofline  the dominant kernel's algorithmic FP64 flops per launch / its
+            measured launch time, against the FP64 peak derived from the SM
+            count and clock; algorithmic flops per DOF come from the oracle's
+            counting run on a sample mesh of the same degree distribution
+  cpu_baseline  the CPU oracle on a sample of the workload (all host cores)
+
+--impl reference runs the CPU oracle as the reference arm on a bounded sample.
+Multi-GPU: every rank runs its own replica of the workload (no collective).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+STEPS_PER_CYCLE = 10
+STAGES_PER_STEP = 3
+# FP64 peak from the unit count and clock of a GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+SMS, DFMA_PER_CLK, SM_MHZ_MAX = 152, 2, 2070.0
+FP64_PEAK_TFLOPS = SMS * DFMA_PER_CLK * 2 * SM_MHZ_MAX * 1e6 / 1e12
+KERNEL_STEP = {"prolong": 1, "fv": 2, "face_lift": 3, "dg_volume": 4, "face_flux": 5, "surface": 6}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--nel", type=int, default=48, help="elements per direction")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def workload(nel):
+    from paper_2502_19342_gb300 import workloads as W
+    # all elements start at N = 4; the modal indicator moves them within 1..7
+    # and to FV sub-cells from the first (warm-up) adaptation on
+    prob, U = W.turbulence(seed=0, nel=(nel, nel, nel), N0=4)
+    return prob, U
+
+
+WORKLOAD_NAME = ("turbulent multi-component decay, 48^3 elements on [0,2pi]^3, N in 1..7 driven by the modal "
+                 "indicator from N=4, FV sub-cells N_FV=8, 3 species, viscous, LLF")
+
+
+def sample_problem(prob, nel_s, seed=5):
+    """A periodic nel_s^3 mesh with the same distribution of degrees and FV
+    elements as `prob` (for the oracle's flop count and the CPU baseline)."""
+    from paper_2502_19342_gb300 import workloads as W
+    rng = np.random.default_rng(seed)
+    n = nel_s ** 3
+    idx = rng.integers(0, len(prob["N"]), n)
+    L = prob["hi"][0] - prob["lo"][0]
+    s = dict(prob)
+    s["dims"] = np.array([[nel_s] * 3], np.int32)
+    s["lo"] = prob["lo"][:1].copy()
+    s["hi"] = (prob["lo"][0] + L * nel_s / prob["dims"][0]).reshape(1, 3)
+    s["N"] = prob["N"][idx].copy()
+    s["fv"] = prob["fv"][idx].copy()
+    # the same smooth random state recipe on the sample box
+    return s, W.smooth_random_state(s, seed, amp=0.05)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, gpu):
+        self.gpu, self.rows, self.proc = gpu, [], None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def flops_per_dof(prob):
+    """Algorithmic flops per DOF-stage, total and per step of R(U), counted by
+    the oracle on a 10^3 sample with the same degree/FV distribution."""
+    import oracle
+    from paper_2502_19342_gb300 import workloads as W
+    s, Us = sample_problem(prob, 10)
+    f = oracle.count_flops(s, Us)
+    dofs = W.n_dofs(s)
+    per_step = {k: sum(v.values()) / dofs for k, v in f["steps"].items()}
+    return sum(per_step.values()), per_step
+
+
+def cpu_baseline(prob, budget_s=12.0):
+    """Oracle R(U) on a 12^3 sample of the workload, all host cores."""
+    import oracle
+    from paper_2502_19342_gb300 import workloads as W
+    s, Us = sample_problem(prob, 12)
+    oracle.eval_rhs(s, Us)  # warm (builds the library)
+    dofs = W.n_dofs(s)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.eval_rhs(s, Us)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s or reps >= 50:
+            break
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": dofs * reps / dt, "unit": "DOF-stage/s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} evaluations of R(U) on a 12^3-element sample ({dofs} DOFs) with the workload's "
+                      f"degree/FV distribution, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    prob, _ = workload(args.nel)
+    import oracle
+    from paper_2502_19342_gb300 import workloads as W
+    s, Us = sample_problem(prob, 8)
+    dofs = W.n_dofs(s)
+    oracle.eval_rhs(s, Us)
+    for _ in range(args.warmup):
+        oracle.eval_rhs(s, Us)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.eval_rhs(s, Us)
+    dt = time.perf_counter() - t0
+    v = dofs * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": "DOF-stage updates/s (FP64 RHS, hp-mixed)", "value": v,
+            "unit": "DOF-stage/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME + "; reference arm: CPU oracle, one R(U) per step on an "
+                                                  "8^3-element sample of the same degree distribution",
+                       "l2": "n/a (host)"},
+            "cpu_baseline": {"value": v, "unit": "DOF-stage/s", "cores": cores, "kind": "oracle",
+                             "sample": f"one R(U) per step on an 8^3 sample ({dofs} DOFs)"},
+            "e2e": {"value": v, "unit": "DOF-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def cycle(ctx):
+    st = ctx.adapt()
+    ctx.rk_steps(STEPS_PER_CYCLE, -1.0, want_dt=False)
+    dofs = st["mean_dofs"] * ctx.n_elem
+    return dofs * STEPS_PER_CYCLE * STAGES_PER_STEP, st
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2502_19342_gb300 import dgfv, workloads as W
+
+    prob, U = workload(args.nel)
+    ctx = dgfv.Context(prob, N_min=1, N_max=7, opts=dict(cfl_c=0.5, cfl_v=0.5, thresholds=W.THRESHOLDS))
+    ctx.set_state(torch.from_numpy(U).cuda())
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        cycle(ctx)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ------------------------------------------------------------ timed region (device-resident)
+    ctx.profile_enable(True)
+    units = 0.0
+    pattern = []
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            u, st = cycle(ctx)
+            units += u
+            pattern.append(st)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    t = torch.tensor([ms], device="cuda")
+    tot_units = torch.tensor([units], device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot_units, op=dist.ReduceOp.SUM)
+    ms = float(t.item())
+    value = float(tot_units.item()) / (ms * 1e-3)
+
+    # ------------------------------------------------------------ end to end through the C ABI, host buffers
+    e2e = None
+    if not args.no_e2e:
+        cap = ctx.n_elem * ctx.V * 512
+        host = torch.empty(cap, dtype=torch.float64).pin_memory()
+        n = ctx.state_size
+        ctx.get_state_host(host[:n])
+        e_units, h2d, d2h = 0.0, 0, 0
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            n = ctx.state_size
+            ctx.set_state_host(host[:n])
+            h2d += 8 * n
+            u, _ = cycle(ctx)
+            e_units += u
+            n = ctx.state_size
+            ctx.get_state_host(host[:n])
+            d2h += 8 * n
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        e2e = {"value": e_units / (ems * 1e-3), "unit": "DOF-stage/s",
+               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)}
+
+    if rank == 0:
+        # roofline of the dominant kernel
+        per_dof, per_step = flops_per_dof(prob)
+        main_k = max((k for k in KERNEL_STEP if prof[k][1] > 0), key=lambda k: prof[k][0])
+        kms, kl = prof[main_k]
+        dofs_per_launch = units / (args.steps * STEPS_PER_CYCLE * STAGES_PER_STEP)
+        achieved = per_step[KERNEL_STEP[main_k]] * dofs_per_launch / (kms / kl * 1e-3) / 1e12
+        probe = dgfv.probe_dfma(1 << 14) / 1e12
+        roof = {"bound": "alu", "kernel": main_k, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 1.26 TFLOP/s)",
+                "dfma_probe_tflops": probe,
+                "flops_per_dof": {"total": per_dof, main_k: per_step[KERNEL_STEP[main_k]]},
+                "whole_rhs_tflops": per_dof * units / (ms * 1e-3) / 1e12}
+        cpu = None if args.no_cpu else cpu_baseline(prob)
+        launches = int(sum(v[1] for v in prof.values()))
+        last = pattern[-1]
+        line = {"metric": "DOF-stage updates/s (FP64 RHS, hp-mixed)", "value": value, "unit": "DOF-stage/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD_NAME, "elements": ctx.n_elem,
+                           "step": "adapt + 10 SSP-RK3 steps (30 stages), CFL 0.5",
+                           "dofs_last_step": int(last["mean_dofs"] * ctx.n_elem), "fv_elements": last["n_fv"],
+                           "degree_histogram": last["hist"], "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (state ~1.2 GB)"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
+                "clocks": clk.summary()}
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * dgfv -- FP64 CUDA implementation (sm_103a) of the per-stage right-hand side
+ * U_t = R(U) of the hp-adaptive hybrid discontinuous-Galerkin / finite-volume
+ * operator for the compressible multi-component Navier-Stokes equations
+ * (Mossier, Kopper, Keim, Beck, Munz: "Tackling Compressible Turbulent
+ * Multi-Component Flows with Dynamic hp-Adaptation", arXiv 2502.19342).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Mesh      One or more independent periodic Cartesian boxes ("domains").
+ *           Elements are numbered domain by domain, x fastest:
+ *           e = first_element(domain) + ix + nx*(iy + ny*iz).
+ * Degrees   Each element has a DG degree N_e in [N_min, N_max] (1..7) and a
+ *           flag is_fv_e; an FV element keeps N_e for its return to DG.
+ * State     Conserved variables per point, V = Nk + 4:
+ *           (rho_1..rho_Nk, rho v_x, rho v_y, rho v_z, rho E).
+ *           Element-contiguous structure of arrays, FP64:
+ *               U[off_e + v*n^3 + i + n*(j + n*k)]
+ *           with n = N_e + 1 Legendre-Gauss nodes (DG) or n = N_FV sub-cell
+ *           means (FV) per direction and off_e the exclusive prefix sum of
+ *           V*n_e^3 (dgfv_state_layout).
+ * Memory    Arguments named d_* are device pointers owned by the caller; the
+ *           library never frees them.  The library owns only its scratch
+ *           (face buffers, stage buffers, tables), allocated in
+ *           dgfv_init_mesh at the capacity of the worst case (every element at
+ *           N_max or FV), so no later call allocates device memory.
+ * Streams   Every call that takes `stream` (a cudaStream_t, NULL = legacy
+ *           default stream) enqueues its work on it and returns without
+ *           synchronising, except where a host result is requested.
+ * Errors    Every call returns dgfv_status.  Kernels never trap: a detected
+ *           problem (non-finite state, a wait that timed out) sets a device
+ *           status word that the next synchronising call (or
+ *           dgfv_sync_status) reports.  dgfv_last_error gives the message.
+ * Threads   One context is used by one host thread and one stream at a time.
+ */
+#ifndef DGFV_H
+#define DGFV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgfv_ctx dgfv_ctx;
+
+typedef enum {
+    DGFV_OK = 0,
+    DGFV_ERR_ARG = -1,          /* invalid argument (null, out of range, size mismatch) */
+    DGFV_ERR_CUDA = -2,         /* a CUDA runtime call failed                            */
+    DGFV_ERR_OOM = -3,          /* device allocation failed                              */
+    DGFV_ERR_NONPHYSICAL = -4,  /* density or pressure <= 0 detected                      */
+    DGFV_ERR_NONFINITE = -5,    /* NaN or Inf detected in an updated state               */
+    DGFV_ERR_TIMEOUT = -6,      /* a bounded device wait gave up                          */
+    DGFV_ERR_STATE = -7         /* call order (e.g. rk_step before set_state)             */
+} dgfv_status;
+
+typedef enum { DGFV_RIEMANN_LLF = 0, DGFV_RIEMANN_ROE_HH = 1 } dgfv_riemann;
+
+/* Mesh: n_domains periodic boxes; arrays have 3 entries per domain. */
+typedef struct {
+    int n_domains;
+    const int32_t* dims;  /* nx, ny, nz per domain (>= 1)               */
+    const double* lo;     /* lower corner per domain                    */
+    const double* hi;     /* upper corner per domain (hi > lo)          */
+    int N_min, N_max;     /* degree bounds, 1 <= N_min <= N_max <= 7    */
+    int N_fv;             /* FV sub-cells per direction, N_max+1 <= N_fv <= 8 */
+} dgfv_mesh_desc;
+
+/* Species (Sec. 2): constant properties, ideal-gas mixture, 1 <= n_species <= 3. */
+typedef struct {
+    int n_species;
+    double gamma[3];  /* ratio of heat capacities                   */
+    double Rgas[3];   /* specific gas constant                      */
+    double mu[3];     /* dynamic viscosity                          */
+    double Pr[3];     /* Prandtl number                             */
+    double D[3];      /* Fickian diffusion coefficient              */
+} dgfv_phys;
+
+typedef struct {
+    int riemann;        /* dgfv_riemann                                        */
+    double cfl_c;       /* convective CFL number (Sec. 3.3)                    */
+    double cfl_v;       /* viscous CFL number (Sec. 3.3)                       */
+    double T_fv_on;     /* DG -> FV when I_h < T_fv_on (Sec. 3.4)              */
+    double T_fv_off;    /* FV -> DG when I_h > T_fv_off                        */
+    double T_ref;       /* N -> N+1 when I_p < T_ref                           */
+    double T_crs;       /* N -> N-1 when I_p > T_crs                           */
+} dgfv_opts;
+
+typedef struct {
+    int64_t n_fv;           /* FV elements after the call                      */
+    int64_t hist[8];        /* DG elements per degree N (index N) after        */
+    int64_t n_changed;      /* elements whose degree or type changed           */
+    int64_t n_near;         /* elements whose indicator lies within 1e-10 of a
+                               threshold that decided them                     */
+    double mean_dofs;       /* mean DOFs (nodes or sub-cells) per element      */
+} dgfv_adapt_stats;
+
+/* Creates a context for the mesh, species and options.  All elements start at
+ * degree N_min, DG.  Allocates every device buffer the context will need.
+ * Errors: DGFV_ERR_ARG, DGFV_ERR_OOM, DGFV_ERR_CUDA. */
+int dgfv_init_mesh(dgfv_ctx** ctx, const dgfv_mesh_desc* mesh, const dgfv_phys* phys,
+                   const dgfv_opts* opts);
+
+/* Number of elements of the mesh. */
+int64_t dgfv_num_elements(const dgfv_ctx* ctx);
+
+/* Sets the degree N[e] and FV flag is_fv[e] of every element (host arrays of
+ * dgfv_num_elements entries).  With remap_state != 0 the context's state is
+ * mapped to the new pattern (V^{N->M}, V^{DG->FV}, V^{FV->DG}, Sec. 3.2);
+ * otherwise the state becomes undefined until dgfv_set_state.  Synchronises.
+ * Errors: DGFV_ERR_ARG (degree out of [N_min, N_max]). */
+int dgfv_set_degrees(dgfv_ctx* ctx, const int8_t* N, const uint8_t* is_fv, int remap_state);
+
+/* Current degrees and FV flags (host arrays, may be NULL). Synchronises. */
+int dgfv_get_degrees(dgfv_ctx* ctx, int8_t* N, uint8_t* is_fv);
+
+/* Size of one state in doubles and the device array of the n_elem element
+ * offsets (owned by the context; valid until the pattern changes). */
+int dgfv_state_layout(dgfv_ctx* ctx, int64_t* n_doubles, const int64_t** d_elem_offsets);
+
+/* Copies n doubles (must equal the layout size) into / out of the context's
+ * state.  d_U is device memory, or host memory for the *_host variants
+ * (which synchronise the stream). */
+int dgfv_set_state(dgfv_ctx* ctx, const double* d_U, int64_t n, void* stream);
+int dgfv_get_state(dgfv_ctx* ctx, double* d_U, int64_t n, void* stream);
+int dgfv_set_state_host(dgfv_ctx* ctx, const double* h_U, int64_t n, void* stream);
+int dgfv_get_state_host(dgfv_ctx* ctx, double* h_U, int64_t n, void* stream);
+
+/* R = R(U), Eqs. 22 (DG, semidiscrete), 23 (lifting), 26 (FV,
+ * semidiscrete_fv), with the interface coupling of Sec. 3.2.1-3.2.2.
+ * d_U, d_R: caller-owned device arrays in the current layout; they must not
+ * alias.  Allocates nothing. */
+int dgfv_eval_rhs(dgfv_ctx* ctx, const double* d_U, double* d_R, void* stream);
+
+/* Time step of Sec. 3.3 for the state d_U: out3 (host) = {dt, min dt_c,
+ * min dt_v}.  Synchronises the stream. */
+int dgfv_compute_dt(dgfv_ctx* ctx, const double* d_U, double* out3, void* stream);
+
+/* One SSP-RK3 step (Shu-Osher) of the context's state.  dt > 0 uses that
+ * step; dt <= 0 uses the CFL step of Sec. 3.3 computed on the device from
+ * the state at the start of the step.  dt_used (host, may be NULL) receives
+ * the step taken, which synchronises the stream; with NULL the call does not
+ * synchronise.  Errors: DGFV_ERR_STATE before the first set_state. */
+int dgfv_rk_step(dgfv_ctx* ctx, double dt, double* dt_used, void* stream);
+
+/* n_steps SSP-RK3 steps captured once as a CUDA graph per degree pattern and
+ * replayed; same dt semantics as dgfv_rk_step (dt_used = last step). */
+int dgfv_rk_steps(dgfv_ctx* ctx, int n_steps, double dt, double* dt_used, void* stream);
+
+/* Modal indicator of Sec. 3.4 on the state d_U: per element I_p = I(rho),
+ * I_h = min(I(p), I(Y_k)) (device arrays of n_elem doubles, may be NULL) and
+ * the decision code (device array of n_elem bytes, may be NULL):
+ * 0 keep, 1 DG->FV, 2 FV->DG, 3 N+1, 4 N-1. */
+int dgfv_indicator(dgfv_ctx* ctx, const double* d_U, double* d_Ip, double* d_Ih,
+                   uint8_t* d_decision, void* stream);
+
+/* Indicator on the context's state, decisions, remap of the state to the new
+ * pattern (Sec. 3.2 mappings).  Synchronises.  stats may be NULL. */
+int dgfv_adapt(dgfv_ctx* ctx, dgfv_adapt_stats* stats, void* stream);
+
+/* Kernel timing for measurements.  With on != 0 every launch of the
+ * library's kernels is bracketed by CUDA events on its stream, and
+ * dgfv_rk_steps launches the stages directly instead of replaying its graph.
+ * dgfv_profile_read synchronises and returns, per kernel in the order
+ *   0 prolong, 1 fv, 2 face_lift, 3 dg_volume, 4 face_flux, 5 surface,
+ *   6 dt, 7 indicator, 8 remap,
+ * the summed milliseconds and the number of launches since the last
+ * dgfv_profile_enable, and the number of kernels written (at most cap). */
+int dgfv_profile_enable(dgfv_ctx* ctx, int on);
+int dgfv_profile_read(dgfv_ctx* ctx, double* ms, int64_t* launches, int cap);
+
+/* Device status word: DGFV_OK or the first error a kernel recorded; clears it. */
+int dgfv_sync_status(dgfv_ctx* ctx, void* stream);
+
+const char* dgfv_status_string(int status);
+const char* dgfv_last_error(const dgfv_ctx* ctx);
+void dgfv_destroy(dgfv_ctx* ctx);
+
+/* Operator bank entries, for checks against an independent computation:
+ * which = 0 nodes, 1 weights, 2 Dhat (n x n), 3 l(-1), 4 l(+1),
+ * 5 V^{N->M} ((M+1) x (N+1)), 6 V^{DG->FV} (N_fv x (N+1)),
+ * 7 V^{FV->DG} ((N+1) x N_fv), 8 inverse Legendre Vandermonde.
+ * Copies the row-major matrix to host memory `out` of `cap` doubles and
+ * returns the number of entries, or a negative status. */
+int64_t dgfv_bank_entry(dgfv_ctx* ctx, int which, int N, int M, double* out, int64_t cap);
+
+/* Peak FP64 throughput probe: a kernel of independent DFMA chains; returns
+ * achieved FMA-flops per second (2 per DFMA) over `iters` iterations.
+ * Synchronises. */
+double dgfv_probe_dfma(int iters, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -48,6 +48,7 @@ def lib():
         L.oracle_elem_offsets.argtypes = [P, _i64p]
         L.oracle_eval_rhs.argtypes = [P, _dp, _dp]
         L.oracle_eval_rhs_jvp.argtypes = [P, _dp, _dp, _dp, _dp]
+        L.oracle_eval_rhs_extended.argtypes = [P, _dp, _dp]
         L.oracle_count_flops.argtypes = [P, _dp, _dp]
         L.oracle_dt.argtypes = [P, _dp, C.c_double, C.c_double, _dp]
         L.oracle_rk3.argtypes = [P, _dp, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
@@ -132,6 +133,15 @@ def eval_rhs(prob, U):
     return R
 
 
+def eval_rhs_extended(prob, U):
+    """R(U) evaluated in long double arithmetic (rounding-error reference)."""
+    b = _Bound(prob)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    R = np.zeros_like(U)
+    _check(lib().oracle_eval_rhs_extended(b.ref, _ptr(U, _dp), _ptr(R, _dp)), "eval_rhs_extended")
+    return R
+
+
 def eval_rhs_jvp(prob, U, dU):
     b = _Bound(prob)
     U = np.ascontiguousarray(U, dtype=np.float64)
@@ -142,13 +152,20 @@ def eval_rhs_jvp(prob, U, dU):
     return R, dR
 
 
+STEPS = {1: "face values", 2: "FV sub-cells", 3: "lifting value", 4: "DG lifting + volume",
+         5: "face flux", 6: "surface"}
+
+
 def count_flops(prob, U):
-    """Counted operations of one R(U): dict add, mul, div, sqrt."""
+    """Counted operations of one R(U): dict add, mul, div, sqrt, and 'steps':
+    {step: {add, mul, div, sqrt}} for the six steps of the evaluation."""
     b = _Bound(prob)
     U = np.ascontiguousarray(U, dtype=np.float64)
-    out = np.zeros(5)
+    out = np.zeros(40)
     _check(lib().oracle_count_flops(b.ref, _ptr(U, _dp), _ptr(out, _dp)), "count_flops")
-    return {"add": out[0], "mul": out[1], "div": out[2], "sqrt": out[3]}
+    keys = ("add", "mul", "div", "sqrt")
+    steps = {s: dict(zip(keys, out[8 + 4 * s:12 + 4 * s])) for s in range(1, 7)}
+    return {"add": out[0], "mul": out[1], "div": out[2], "sqrt": out[3], "steps": steps}
 
 
 def dt(prob, U, cfl_c, cfl_v):

@@ -252,6 +252,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
     vector<ElemWork<T>> W(nel);
 
     // ---- step 1: face values of every element
+    flop_counter().phase = 1;
 #pragma omp parallel for schedule(dynamic, 16) if (parallel)
     for (int e = 0; e < nel; ++e) {
         const Elem& E = P.el[e];
@@ -276,7 +277,10 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
             W[e].face_u[f] = fu;
             // the boundary layer of sub-cell means that an FV neighbour sees:
             // V^{DG->FV} in all three directions, keeping the sub-cells next to face f
-            if (!E.fv && P.nfv >= n) {
+            // (counted with the FV step, which is where it is needed)
+            const bool fv_neighbour = P.el[E.nb[f]].fv;
+            if (!E.fv && fv_neighbour && !parallel) flop_counter().phase = 2;
+            if (!E.fv && fv_neighbour) {
                 const vector<double>& A = P.ops.d2f.at(E.N);
                 const int row = s ? P.nfv - 1 : 0;
                 vector<T> q((size_t)V * n * n, T(0.0));
@@ -290,10 +294,12 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
                         }
                 W[e].face_layer[f] = map_face(q, V, n, P.nfv, A);
             }
+            if (!parallel) flop_counter().phase = 1;
         }
     }
 
     // ---- step 2: FV sub-cell elements (Sec. 3.1.2)
+    flop_counter().phase = 2;
 #pragma omp parallel for schedule(dynamic, 1) if (parallel)
     for (int e = 0; e < nel; ++e) {
         const Elem& E = P.el[e];
@@ -415,6 +421,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
     }
 
     // ---- step 3: BR1 lifting interface value U* = (u- + u+)/2 (Eq. 19)
+    flop_counter().phase = 3;
 #pragma omp parallel for schedule(dynamic, 16) if (parallel)
     for (int e = 0; e < nel; ++e) {
         const Elem& E = P.el[e];
@@ -442,6 +449,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
     }
 
     // ---- step 4: lifting (Eq. 23) and volume integral (Eq. 22) of DG elements.
+    flop_counter().phase = 4;
     // Cartesian elements: J = hx hy hz / 8, metric terms J dxi_d/dx_d = J (2/h_d),
     // so contravariant quantities divided by J carry the factor 2/h_d.
     // Reading (Eq. 23): the lifted variable is the gradient, g^d = +(1/J)[...].
@@ -516,6 +524,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
     }
 
     // ---- step 5: face fluxes; every face is visited once, from its lower element L
+    flop_counter().phase = 5;
     for (int e = 0; e < nel; ++e)
         for (int f = 0; f < 6; ++f) W[e].flux[f].clear();
 #pragma omp parallel for schedule(dynamic, 16) if (parallel)
@@ -575,6 +584,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
     }
 
     // ---- step 6: surface integral and -1/J (Eqs. 22, 26)
+    flop_counter().phase = 6;
 #pragma omp parallel for schedule(dynamic, 16) if (parallel)
     for (int e = 0; e < nel; ++e) {
         const Elem& E = P.el[e];
@@ -608,6 +618,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
         }
         for (int i = 0; i < V * n3; ++i) R[E.off + i] = -div[i];
     }
+    flop_counter().phase = 0;
 }
 
 // ------------------------------------------------------------------ time step, Sec. 3.3
@@ -664,9 +675,14 @@ void ssp_rk3_step(int64_t n, double* U, double dt, Rhs rhs) {
 }
 
 // ------------------------------------------------------------------ indicator, Sec. 3.4
-// Reading: orthonormal Legendre modes; fit over m = 0..N; w_m floored at 1e-300
-// before the logarithm; I = min over the three directions of |sigma|;
-// FV elements are mapped to their DG degree by V^{FV->DG} first.
+// Reading: orthonormal Legendre modes; fit over m = 0..N; I = min over the three
+// directions of |sigma|; FV elements are mapped to their DG degree by V^{FV->DG}
+// first.  The energy fractions w_m are floored at W_FLOOR = 1e-24 before the
+// logarithm: modal coefficients of FP64 nodal data carry round-off of about
+// 1e-15 of the largest one, i.e. energy fractions near 1e-30, so every fraction
+// below the floor is round-off and the fit of a field resolved to round-off
+// does not depend on it.
+constexpr double W_FLOOR = 1e-24;
 double modal_indicator(const vector<double>& q, int N, const vector<double>& Vinv) {
     const int n = N + 1;
     vector<double> qm = map_volume(q.data(), 1, n, n, Vinv);  // Legendre coefficients
@@ -683,7 +699,7 @@ double modal_indicator(const vector<double>& q, int N, const vector<double>& Vin
                     E += c * c;
                 }
             double w = total > 0.0 ? E / total : 0.0;
-            y[m] = std::log(std::max(w, 1e-300));
+            y[m] = std::log(std::max(w, W_FLOOR));
         }
         // least-squares fit of log w_m = log c - sigma m  (Eq. 34)
         double mbar = 0.0, ybar = 0.0;
@@ -753,6 +769,16 @@ int oracle_eval_rhs(const oracle_problem* p, const double* U, double* R) {
     } catch (...) { return -1; }
 }
 
+int oracle_eval_rhs_extended(const oracle_problem* p, const double* U, double* R) {
+    try {
+        Problem P = make_problem(p);
+        vector<long double> u(U, U + P.size), r(P.size);
+        eval_rhs_t<long double>(P, u.data(), r.data());
+        for (int64_t i = 0; i < P.size; ++i) R[i] = (double)r[i];
+        return 0;
+    } catch (...) { return -1; }
+}
+
 int oracle_eval_rhs_jvp(const oracle_problem* p, const double* U, const double* dU, double* R, double* dR) {
     try {
         Problem P = make_problem(p);
@@ -776,6 +802,9 @@ int oracle_count_flops(const oracle_problem* p, const double* U, double* out) {
         out[2] = flop_counter().div;
         out[3] = flop_counter().sqrt;
         out[4] = 0.0;
+        // per step of the right-hand side: out[8 + 4*step + {add, mul, div, sqrt}], steps 1..6
+        for (int ph = 0; ph < 8; ++ph)
+            for (int k = 0; k < 4; ++k) out[8 + 4 * ph + k] = flop_counter().by_phase[ph][k];
         return 0;
     } catch (...) { return -1; }
 }

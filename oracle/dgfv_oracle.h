@@ -50,13 +50,20 @@ int oracle_elem_offsets(const oracle_problem* p, int64_t* off);
 /* Semi-discrete right-hand side R(U), Sec. 3.1-3.2. */
 int oracle_eval_rhs(const oracle_problem* p, const double* U, double* R);
 
+/* The same R(U) evaluated in long double (the reference-element operators
+ * stay the double ones): measures the double evaluation's own rounding error. */
+int oracle_eval_rhs_extended(const oracle_problem* p, const double* U, double* R);
+
 /* Forward-mode directional derivative dR = R'(U) dU (dual numbers). */
 int oracle_eval_rhs_jvp(const oracle_problem* p, const double* U, const double* dU,
                         double* R, double* dR);
 
 /* Floating-point operation count of one evaluation of R(U), counted on the
- * oracle's own arithmetic: out[0] add/sub, out[1] mul, out[2] div, out[3] sqrt,
- * out[4] other (abs, min/max compares are not counted). */
+ * oracle's own arithmetic (abs and comparisons are not counted):
+ * out[0] add/sub, out[1] mul, out[2] div, out[3] sqrt, out[4] unused, and per
+ * step s = 1..6 of the evaluation (face values, FV sub-cells, lifting value,
+ * DG lifting and volume integral, face fluxes, surface integral)
+ * out[8 + 4*s + {0,1,2,3}].  out must hold 40 doubles. */
 int oracle_count_flops(const oracle_problem* p, const double* U, double* out);
 
 /* Time step of Sec. 3.3 (out: dt, min dt_c, min dt_v). */

@@ -19,6 +19,12 @@ inline double val(double a) { return a; }
 inline double sqrt_(double a) { return std::sqrt(a); }
 inline double abs_(double a) { return std::fabs(a); }
 
+// ---------------------------------------------------------------- long double
+// (extended precision: a rounding-error reference for the double instantiation)
+inline double val(long double a) { return (double)a; }
+inline long double sqrt_(long double a) { return std::sqrt(a); }
+inline long double abs_(long double a) { return std::fabs(a); }
+
 // ---------------------------------------------------------------- Dual
 struct Dual {
     double v = 0.0, d = 0.0;
@@ -50,6 +56,8 @@ inline Dual abs_(Dual a) { return a.v < 0.0 ? -a : a; }
 // ---------------------------------------------------------------- Counted
 struct FlopCounter {
     double add = 0, mul = 0, div = 0, sqrt = 0;
+    int phase = 0;            // step of the right-hand side being counted (0..7)
+    double by_phase[8][4] = {};  // add, mul, div, sqrt per step
 };
 // The counting run is single threaded; one global counter suffices.
 inline FlopCounter& flop_counter() {
@@ -61,11 +69,16 @@ struct Counted {
     Counted() = default;
     Counted(double x) : v(x) {}
 };
-inline Counted operator+(Counted a, Counted b) { flop_counter().add += 1; return {a.v + b.v}; }
-inline Counted operator-(Counted a, Counted b) { flop_counter().add += 1; return {a.v - b.v}; }
+inline void count_op(int cat) {
+    FlopCounter& c = flop_counter();
+    (&c.add)[cat] += 1;
+    c.by_phase[c.phase][cat] += 1;
+}
+inline Counted operator+(Counted a, Counted b) { count_op(0); return {a.v + b.v}; }
+inline Counted operator-(Counted a, Counted b) { count_op(0); return {a.v - b.v}; }
 inline Counted operator-(Counted a) { return {-a.v}; }
-inline Counted operator*(Counted a, Counted b) { flop_counter().mul += 1; return {a.v * b.v}; }
-inline Counted operator/(Counted a, Counted b) { flop_counter().div += 1; return {a.v / b.v}; }
+inline Counted operator*(Counted a, Counted b) { count_op(1); return {a.v * b.v}; }
+inline Counted operator/(Counted a, Counted b) { count_op(2); return {a.v / b.v}; }
 inline Counted& operator+=(Counted& a, Counted b) { a = a + b; return a; }
 inline Counted& operator-=(Counted& a, Counted b) { a = a - b; return a; }
 inline Counted& operator*=(Counted& a, Counted b) { a = a * b; return a; }
@@ -74,7 +87,7 @@ inline bool operator>(Counted a, Counted b) { return a.v > b.v; }
 inline bool operator<=(Counted a, Counted b) { return a.v <= b.v; }
 inline bool operator>=(Counted a, Counted b) { return a.v >= b.v; }
 inline double val(Counted a) { return a.v; }
-inline Counted sqrt_(Counted a) { flop_counter().sqrt += 1; return {std::sqrt(a.v)}; }
+inline Counted sqrt_(Counted a) { count_op(3); return {std::sqrt(a.v)}; }
 inline Counted abs_(Counted a) { return {std::fabs(a.v)}; }
 
 }  // namespace ora

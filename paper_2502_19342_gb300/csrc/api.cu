@@ -1,0 +1,743 @@
+// C ABI of the dgfv library (include/dgfv.h): context, mesh tables, element
+// layout, work tiles, face lists, stage sequencing and CUDA-graph replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dgfv.h"
+#include "bank.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace dgfv;
+
+namespace {
+
+struct TileSet {
+    std::vector<int32_t> first, count, items;
+    std::vector<uint8_t> n;
+    int32_t *d_first = nullptr, *d_count = nullptr, *d_items = nullptr;
+    uint8_t* d_n = nullptr;
+    int ntiles = 0;
+    size_t smem = 0;
+    Tiles view() const { return Tiles{d_first, d_count, d_n, d_items}; }
+};
+
+struct FaceList {
+    std::vector<int32_t> ids;
+    int32_t* d = nullptr;
+    int count = 0;
+};
+
+enum Kernel { K_PROLONG = 0, K_FV, K_LIFT, K_VOLUME, K_FLUX, K_SURFACE, K_DT, K_INDICATOR, K_REMAP, K_COUNT };
+
+struct Profiler {
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[K_COUNT];
+    size_t used[K_COUNT] = {};
+};
+
+}  // namespace
+
+struct dgfv_ctx {
+    int dev = 0;
+    int nk = 2, V = 6;
+    DevPhys ph{};
+    dgfv_opts opts{};
+    int N_min = 1, N_max = 1, nfv = 2;
+    int n_elem = 0, n_faces = 0;
+    std::vector<int32_t> nb;
+    std::vector<double> rh;
+    std::vector<int32_t> faceL, faceR;
+    std::vector<uint8_t> faceD;
+    // current pattern and layout
+    std::vector<uint8_t> N, fv, npts;
+    std::vector<int64_t> off, fo;
+    int64_t n_state = 0, n_fpts = 0;
+    int64_t cap_state = 0, cap_fpts = 0;
+    // device tables (current and previous pattern, for the remap)
+    uint8_t *d_n = nullptr, *d_N = nullptr, *d_fv = nullptr;
+    int64_t *d_off = nullptr, *d_fo = nullptr;
+    uint8_t *d_n_old = nullptr, *d_N_old = nullptr, *d_fv_old = nullptr;
+    int64_t* d_off_old = nullptr;
+    int32_t* d_nb = nullptr;
+    double* d_rh = nullptr;
+    int32_t *d_faceL = nullptr, *d_faceR = nullptr;
+    uint8_t* d_faceD = nullptr;
+    double* d_bank = nullptr;
+    BankIdx bi{};
+    // buffers
+    double *d_fu = nullptr, *d_fg = nullptr, *d_flux = nullptr, *d_flift = nullptr, *d_frec = nullptr;
+    double *d_rtmp = nullptr, *d_U = nullptr, *d_Us = nullptr;
+    double *d_dt3 = nullptr, *d_partial = nullptr;
+    double *d_Ip = nullptr, *d_Ih = nullptr;
+    uint8_t* d_dec = nullptr;
+    int* d_status = nullptr;
+    TileSet all, dg, fvt;
+    FaceList lift, flux;
+    int n_fv_elems = 0;
+    bool state_valid = false;
+    std::string err;
+    // graph of one RK step
+    cudaGraphExec_t graph = nullptr;
+    bool graph_valid = false;
+    double graph_dt = 0.0;
+    cudaStream_t graph_stream = nullptr;
+    Profiler prof;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+int fail(dgfv_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(c, DGFV_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+int dalloc(dgfv_ctx* c, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return fail(c, DGFV_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    c->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return DGFV_OK;
+}
+
+#define TRY(x)                 \
+    do {                       \
+        int r_ = (x);          \
+        if (r_ != DGFV_OK) return r_; \
+    } while (0)
+
+Params params(const dgfv_ctx* c) {
+    Params P{};
+    P.ph = c->ph;
+    P.t = Tables{c->d_n, c->d_N, c->d_fv, c->d_off, c->d_fo, c->d_nb, c->d_rh};
+    P.b = Buffers{c->d_fu, c->d_fg, c->d_flux, c->d_flift, c->d_frec, c->d_rtmp};
+    P.bank = c->d_bank;
+    P.bi = c->bi;
+    P.nfv = c->nfv;
+    P.status = c->d_status;
+    return P;
+}
+
+// Brackets one kernel launch with events when profiling is on.
+struct Timed {
+    dgfv_ctx* c;
+    int k;
+    cudaStream_t s;
+    Timed(dgfv_ctx* c_, int k_, cudaStream_t s_) : c(c_), k(k_), s(s_) {
+        if (!c->prof.on) return;
+        auto& pool = c->prof.ev[k];
+        if (c->prof.used[k] == pool.size()) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            pool.emplace_back(a, b);
+        }
+        cudaEventRecord(pool[c->prof.used[k]].first, s);
+    }
+    ~Timed() {
+        if (!c->prof.on) return;
+        cudaEventRecord(c->prof.ev[k][c->prof.used[k]].second, s);
+        c->prof.used[k]++;
+    }
+};
+
+int build_bank(dgfv_ctx* c) {
+    std::vector<double> bank;
+    auto put = [&](const std::vector<double>& v) {
+        const int32_t o = (int32_t)bank.size();
+        bank.insert(bank.end(), v.begin(), v.end());
+        return o;
+    };
+    std::memset(&c->bi, 0, sizeof(c->bi));
+    for (int n = c->N_min + 1; n <= c->N_max + 1; ++n) {
+        Bank1D b = make_bank(n);
+        c->bi.dhat[n] = put(b.Dhat);
+        c->bi.lm[n] = put(b.lm);
+        c->bi.lp[n] = put(b.lp);
+        c->bi.lhm[n] = put(b.lhm);
+        c->bi.lhp[n] = put(b.lhp);
+        c->bi.vinv[n] = put(b.vinv);
+        c->bi.d2f[n] = put(make_dg2fv(n, c->nfv));
+        c->bi.f2d[n] = put(make_fv2dg(n, c->nfv));
+        for (int m = c->N_min + 1; m <= c->N_max + 1; ++m) c->bi.vm[n][m] = put(make_vmap(n, m));
+    }
+    TRY(dalloc(c, &c->d_bank, bank.size()));
+    CK(cudaMemcpy(c->d_bank, bank.data(), bank.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return DGFV_OK;
+}
+
+int upload_tiles(dgfv_ctx* c, TileSet& t) {
+    t.ntiles = (int)t.first.size();
+    if (t.ntiles == 0) return DGFV_OK;
+    CK(cudaMemcpy(t.d_first, t.first.data(), t.ntiles * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(t.d_count, t.count.data(), t.ntiles * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(t.d_n, t.n.data(), t.ntiles * sizeof(uint8_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(t.d_items, t.items.data(), t.items.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    return DGFV_OK;
+}
+
+// Group items by their point count n (ascending) and cut each group into tiles
+// of at most per_tile(n) items.
+template <class Sel, class Per>
+void make_tiles(const dgfv_ctx* c, TileSet& t, Sel sel, Per per_tile) {
+    t.first.clear(); t.count.clear(); t.items.clear(); t.n.clear();
+    for (int n = 1; n <= MAXP; ++n) {
+        std::vector<int32_t> group;
+        for (int e = 0; e < c->n_elem; ++e)
+            if (c->npts[e] == n && sel(e)) group.push_back(e);
+        if (group.empty()) continue;
+        const int per = std::max(1, per_tile(n));
+        for (size_t s = 0; s < group.size(); s += per) {
+            const int cnt = (int)std::min<size_t>(per, group.size() - s);
+            t.first.push_back((int32_t)t.items.size());
+            t.count.push_back(cnt);
+            t.n.push_back((uint8_t)n);
+            t.items.insert(t.items.end(), group.begin() + s, group.begin() + s + cnt);
+        }
+    }
+}
+
+// Elements per volume tile: about 256 nodes per CTA.
+int volume_per_tile(int n) { return std::max(1, 256 / (n * n * n)); }
+
+int apply_layout(dgfv_ctx* c) {
+    const int ne = c->n_elem;
+    c->npts.resize(ne);
+    c->off.resize(ne);
+    c->fo.resize(ne);
+    int64_t so = 0, fpo = 0;
+    c->n_fv_elems = 0;
+    for (int e = 0; e < ne; ++e) {
+        const int n = c->fv[e] ? c->nfv : c->N[e] + 1;
+        c->npts[e] = (uint8_t)n;
+        c->off[e] = so;
+        c->fo[e] = fpo;
+        so += (int64_t)c->V * n * n * n;
+        fpo += 6LL * n * n;
+        c->n_fv_elems += c->fv[e] ? 1 : 0;
+    }
+    c->n_state = so;
+    c->n_fpts = fpo;
+    CK(cudaMemcpy(c->d_n, c->npts.data(), ne, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_N, c->N.data(), ne, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_fv, c->fv.data(), ne, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_off, c->off.data(), ne * sizeof(int64_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_fo, c->fo.data(), ne * sizeof(int64_t), cudaMemcpyHostToDevice));
+    // tiles
+    make_tiles(c, c->all, [](int) { return true; }, [](int n) { return std::max(1, 512 / (n * n * n)); });
+    make_tiles(c, c->dg, [&](int e) { return !c->fv[e]; }, volume_per_tile);
+    make_tiles(c, c->fvt, [&](int e) { return c->fv[e] != 0; }, [](int) { return 1; });
+    size_t sm = 0;
+    for (int t = 0; t < (int)c->dg.first.size(); ++t)
+        sm = std::max(sm, volume_smem_bytes(c->nk, c->dg.n[t], c->dg.count[t]));
+    c->dg.smem = sm;
+    TRY(upload_tiles(c, c->all));
+    TRY(upload_tiles(c, c->dg));
+    TRY(upload_tiles(c, c->fvt));
+    // face lists: lifting needs a DG side; every face has a flux
+    c->lift.ids.clear();
+    c->flux.ids.clear();
+    for (int f = 0; f < c->n_faces; ++f) {
+        c->flux.ids.push_back(f);
+        if (!(c->fv[c->faceL[f]] && c->fv[c->faceR[f]])) c->lift.ids.push_back(f);
+    }
+    c->lift.count = (int)c->lift.ids.size();
+    c->flux.count = (int)c->flux.ids.size();
+    if (c->lift.count)
+        CK(cudaMemcpy(c->lift.d, c->lift.ids.data(), c->lift.count * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (c->flux.count)
+        CK(cudaMemcpy(c->flux.d, c->flux.ids.data(), c->flux.count * sizeof(int32_t), cudaMemcpyHostToDevice));
+    c->graph_valid = false;
+    return DGFV_OK;
+}
+
+int alloc_tiles(dgfv_ctx* c, TileSet& t) {
+    TRY(dalloc(c, &t.d_first, c->n_elem));
+    TRY(dalloc(c, &t.d_count, c->n_elem));
+    TRY(dalloc(c, &t.d_n, c->n_elem));
+    TRY(dalloc(c, &t.d_items, c->n_elem));
+    return DGFV_OK;
+}
+
+// One evaluation of R on Uin; the surface kernel writes mode 0: out = R, or
+// mode 1: out = a*U0 + b*(Uin + dt*R).
+void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out, int mode, double a, double b,
+                   cudaStream_t s) {
+    const Params P = params(c);
+    const Faces F{c->d_faceL, c->d_faceR, c->d_faceD};
+    { Timed t(c, K_PROLONG, s); launch_prolong(c->nk, P, c->all.view(), c->all.ntiles, Uin, s); }
+    if (c->n_fv_elems) { Timed t(c, K_FV, s); launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, Uin, s); }
+    if (c->ph.viscous) { Timed t(c, K_LIFT, s); launch_face_lift(c->nk, P, F, c->lift.d, c->lift.count, s); }
+    if (c->dg.ntiles) { Timed t(c, K_VOLUME, s); launch_dg_volume(c->nk, P, c->dg.view(), c->dg.ntiles, c->dg.smem, Uin, s); }
+    { Timed t(c, K_FLUX, s); launch_face_flux(c->nk, P, F, c->flux.d, c->flux.count, s); }
+    { Timed t(c, K_SURFACE, s); launch_surface(c->nk, P, c->all.view(), c->all.ntiles, Uin, U0, out, mode, a, b, c->d_dt3, s); }
+}
+
+void enqueue_rk_step(dgfv_ctx* c, double dt, cudaStream_t s) {
+    const Params P = params(c);
+    if (dt > 0.0) {
+        launch_set_scalar(c->d_dt3, dt, s);
+    } else {
+        Timed t(c, K_DT, s);
+        launch_dt(c->nk, P, c->all.view(), c->all.ntiles, c->d_U, c->opts.cfl_c, c->opts.cfl_v, c->d_partial,
+                  c->d_dt3, s);
+    }
+    // SSP-RK3 (Shu-Osher): U1 = U + dt R(U); U2 = 3/4 U + 1/4 (U1 + dt R(U1));
+    // U <- 1/3 U + 2/3 (U2 + dt R(U2)).
+    enqueue_stage(c, c->d_U, c->d_U, c->d_Us, 1, 0.0, 1.0, s);
+    enqueue_stage(c, c->d_Us, c->d_U, c->d_Us, 1, 0.75, 0.25, s);
+    enqueue_stage(c, c->d_Us, c->d_U, c->d_U, 1, 1.0 / 3.0, 2.0 / 3.0, s);
+}
+
+int set_pattern(dgfv_ctx* c, const int8_t* N, const uint8_t* fv, bool remap, cudaStream_t s) {
+    for (int e = 0; e < c->n_elem; ++e) {
+        if (N[e] < c->N_min || N[e] > c->N_max)
+            return fail(c, DGFV_ERR_ARG, "degree out of [N_min, N_max] at element " + std::to_string(e));
+    }
+    if (remap && c->state_valid) {
+        CK(cudaMemcpyAsync(c->d_n_old, c->d_n, c->n_elem, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(c->d_N_old, c->d_N, c->n_elem, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(c->d_fv_old, c->d_fv, c->n_elem, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(c->d_off_old, c->d_off, c->n_elem * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    for (int e = 0; e < c->n_elem; ++e) {
+        c->N[e] = (uint8_t)N[e];
+        c->fv[e] = fv ? (fv[e] ? 1 : 0) : 0;
+    }
+    TRY(apply_layout(c));
+    if (remap && c->state_valid) {
+        const Params P = params(c);
+        Timed t(c, K_REMAP, s);
+        launch_remap(P, c->d_n_old, c->d_N_old, c->d_fv_old, c->d_off_old, c->d_n, c->d_N, c->d_fv, c->d_off, c->V,
+                     c->n_elem, c->d_U, c->d_Us, s);
+        CK(cudaGetLastError());
+        std::swap(c->d_U, c->d_Us);
+        CK(cudaStreamSynchronize(s));
+    } else {
+        c->state_valid = false;
+    }
+    return DGFV_OK;
+}
+
+int read_status(dgfv_ctx* c, cudaStream_t s) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (st != 0) {
+        const int zero = 0;
+        CK(cudaMemcpyAsync(c->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        return fail(c, st, std::string("device reported: ") + dgfv_status_string(st));
+    }
+    return DGFV_OK;
+}
+
+}  // namespace
+
+// =============================================================================== C ABI
+extern "C" {
+
+const char* dgfv_status_string(int s) {
+    switch (s) {
+        case DGFV_OK: return "ok";
+        case DGFV_ERR_ARG: return "invalid argument";
+        case DGFV_ERR_CUDA: return "CUDA error";
+        case DGFV_ERR_OOM: return "out of device memory";
+        case DGFV_ERR_NONPHYSICAL: return "non-physical state (density or pressure <= 0)";
+        case DGFV_ERR_NONFINITE: return "non-finite value in the state";
+        case DGFV_ERR_TIMEOUT: return "bounded device wait timed out";
+        case DGFV_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+const char* dgfv_last_error(const dgfv_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void dgfv_destroy(dgfv_ctx* c) {
+    if (!c) return;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (int k = 0; k < K_COUNT; ++k)
+        for (auto& e : c->prof.ev[k]) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+    for (void* p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* phys, const dgfv_opts* opts) {
+    if (!out || !mesh || !phys || !opts) return DGFV_ERR_ARG;
+    *out = nullptr;
+    if (mesh->n_domains < 1 || !mesh->dims || !mesh->lo || !mesh->hi) return DGFV_ERR_ARG;
+    if (mesh->N_min < 1 || mesh->N_max > 7 || mesh->N_min > mesh->N_max) return DGFV_ERR_ARG;
+    if (mesh->N_fv < mesh->N_max + 1 || mesh->N_fv > MAXP) return DGFV_ERR_ARG;
+    if (phys->n_species < 1 || phys->n_species > 3) return DGFV_ERR_ARG;
+    int64_t ne = 0;
+    for (int d = 0; d < mesh->n_domains; ++d) {
+        for (int a = 0; a < 3; ++a) {
+            if (mesh->dims[3 * d + a] < 1 || !(mesh->hi[3 * d + a] > mesh->lo[3 * d + a])) return DGFV_ERR_ARG;
+        }
+        ne += (int64_t)mesh->dims[3 * d] * mesh->dims[3 * d + 1] * mesh->dims[3 * d + 2];
+    }
+    if (ne > (1LL << 30)) return DGFV_ERR_ARG;
+    dgfv_ctx* c = new (std::nothrow) dgfv_ctx();
+    if (!c) return DGFV_ERR_OOM;
+    auto cleanup = [&](int r) {
+        dgfv_destroy(c);
+        return r;
+    };
+    if (cudaGetDevice(&c->dev) != cudaSuccess) return cleanup(DGFV_ERR_CUDA);
+    c->nk = phys->n_species;
+    c->V = c->nk + 4;
+    c->opts = *opts;
+    c->N_min = mesh->N_min;
+    c->N_max = mesh->N_max;
+    c->nfv = mesh->N_fv;
+    c->ph.nk = c->nk;
+    c->ph.riemann = opts->riemann == DGFV_RIEMANN_ROE_HH ? 1 : 0;
+    c->ph.viscous = 0;
+    c->ph.maxD = 0.0;
+    for (int k = 0; k < c->nk; ++k) {
+        if (!(phys->gamma[k] > 1.0) || !(phys->Rgas[k] > 0.0) || phys->mu[k] < 0 || phys->D[k] < 0 ||
+            !(phys->Pr[k] > 0))
+            return cleanup(DGFV_ERR_ARG);
+        c->ph.cv[k] = phys->Rgas[k] / (phys->gamma[k] - 1.0);
+        c->ph.cp[k] = phys->gamma[k] * c->ph.cv[k];
+        c->ph.mu[k] = phys->mu[k];
+        c->ph.pr[k] = phys->Pr[k];
+        c->ph.D[k] = phys->D[k];
+        c->ph.maxD = std::max(c->ph.maxD, phys->D[k]);
+        if (phys->mu[k] != 0.0 || phys->D[k] != 0.0) c->ph.viscous = 1;
+    }
+    c->n_elem = (int)ne;
+    c->nb.resize(6 * ne);
+    c->rh.resize(3 * ne);
+    int64_t e0 = 0;
+    for (int dm = 0; dm < mesh->n_domains; ++dm) {
+        const int dims[3] = {mesh->dims[3 * dm], mesh->dims[3 * dm + 1], mesh->dims[3 * dm + 2]};
+        double rh[3];
+        for (int a = 0; a < 3; ++a) rh[a] = 2.0 * dims[a] / (mesh->hi[3 * dm + a] - mesh->lo[3 * dm + a]);
+        for (int k = 0; k < dims[2]; ++k)
+            for (int j = 0; j < dims[1]; ++j)
+                for (int i = 0; i < dims[0]; ++i) {
+                    const int64_t e = e0 + i + (int64_t)dims[0] * (j + (int64_t)dims[1] * k);
+                    const int ijk[3] = {i, j, k};
+                    for (int f = 0; f < 6; ++f) {
+                        int q[3] = {i, j, k};
+                        const int a = f / 2;
+                        q[a] = (ijk[a] + ((f & 1) ? 1 : -1) + dims[a]) % dims[a];
+                        c->nb[6 * e + f] = (int32_t)(e0 + q[0] + (int64_t)dims[0] * (q[1] + (int64_t)dims[1] * q[2]));
+                    }
+                    for (int a = 0; a < 3; ++a) c->rh[3 * e + a] = rh[a];
+                    for (int a = 0; a < 3; ++a) {  // face towards +a, owned by the lower element
+                        c->faceL.push_back((int32_t)e);
+                        c->faceR.push_back(c->nb[6 * e + 2 * a + 1]);
+                        c->faceD.push_back((uint8_t)a);
+                    }
+                }
+        e0 += (int64_t)dims[0] * dims[1] * dims[2];
+    }
+    c->n_faces = (int)c->faceL.size();
+    // capacity: every element at the largest point count
+    const int nmax = std::max(c->N_max + 1, c->nfv);
+    c->cap_state = ne * (int64_t)c->V * nmax * nmax * nmax;
+    c->cap_fpts = ne * 6LL * nmax * nmax;
+    int r = DGFV_OK;
+#define A_(p, n)                                 \
+    if ((r = dalloc(c, &(p), (size_t)(n))) != DGFV_OK) return cleanup(r);
+    A_(c->d_n, ne) A_(c->d_N, ne) A_(c->d_fv, ne) A_(c->d_off, ne) A_(c->d_fo, ne)
+    A_(c->d_n_old, ne) A_(c->d_N_old, ne) A_(c->d_fv_old, ne) A_(c->d_off_old, ne)
+    A_(c->d_nb, 6 * ne) A_(c->d_rh, 3 * ne)
+    A_(c->d_faceL, c->n_faces) A_(c->d_faceR, c->n_faces) A_(c->d_faceD, c->n_faces)
+    A_(c->d_fu, c->cap_fpts * c->V) A_(c->d_fg, c->cap_fpts * 3 * c->V) A_(c->d_flux, c->cap_fpts * c->V)
+    A_(c->d_flift, c->cap_fpts * c->V) A_(c->d_frec, c->cap_fpts * c->V)
+    A_(c->d_rtmp, c->cap_state) A_(c->d_U, c->cap_state) A_(c->d_Us, c->cap_state)
+    A_(c->d_dt3, 4) A_(c->d_partial, 2 * ne + 2) A_(c->d_Ip, ne) A_(c->d_Ih, ne) A_(c->d_dec, ne)
+    A_(c->d_status, 1) A_(c->lift.d, c->n_faces) A_(c->flux.d, c->n_faces)
+#undef A_
+    if ((r = alloc_tiles(c, c->all)) != DGFV_OK) return cleanup(r);
+    if ((r = alloc_tiles(c, c->dg)) != DGFV_OK) return cleanup(r);
+    if ((r = alloc_tiles(c, c->fvt)) != DGFV_OK) return cleanup(r);
+    if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) return cleanup(DGFV_ERR_CUDA);
+    if (cudaMemcpy(c->d_nb, c->nb.data(), c->nb.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_rh, c->rh.data(), c->rh.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_faceL, c->faceL.data(), c->n_faces * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_faceR, c->faceR.data(), c->n_faces * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_faceD, c->faceD.data(), c->n_faces, cudaMemcpyHostToDevice) != cudaSuccess)
+        return cleanup(DGFV_ERR_CUDA);
+    try {
+        if ((r = build_bank(c)) != DGFV_OK) return cleanup(r);
+    } catch (...) {
+        return cleanup(DGFV_ERR_ARG);
+    }
+    c->N.assign(ne, (uint8_t)c->N_min);
+    c->fv.assign(ne, 0);
+    if ((r = apply_layout(c)) != DGFV_OK) return cleanup(r);
+    *out = c;
+    return DGFV_OK;
+}
+
+int64_t dgfv_num_elements(const dgfv_ctx* c) { return c ? c->n_elem : -1; }
+
+int dgfv_set_degrees(dgfv_ctx* c, const int8_t* N, const uint8_t* is_fv, int remap_state) {
+    if (!c || !N) return DGFV_ERR_ARG;
+    return set_pattern(c, N, is_fv, remap_state != 0, nullptr);
+}
+
+int dgfv_get_degrees(dgfv_ctx* c, int8_t* N, uint8_t* is_fv) {
+    if (!c) return DGFV_ERR_ARG;
+    for (int e = 0; e < c->n_elem; ++e) {
+        if (N) N[e] = (int8_t)c->N[e];
+        if (is_fv) is_fv[e] = c->fv[e];
+    }
+    return DGFV_OK;
+}
+
+int dgfv_state_layout(dgfv_ctx* c, int64_t* n_doubles, const int64_t** d_elem_offsets) {
+    if (!c) return DGFV_ERR_ARG;
+    if (n_doubles) *n_doubles = c->n_state;
+    if (d_elem_offsets) *d_elem_offsets = c->d_off;
+    return DGFV_OK;
+}
+
+static int copy_state(dgfv_ctx* c, void* dst, const void* src, int64_t n, cudaMemcpyKind kind, void* stream,
+                      bool sync) {
+    if (!c || (!dst && n > 0) || (!src && n > 0)) return DGFV_ERR_ARG;
+    if (n != c->n_state) return fail(c, DGFV_ERR_ARG, "state size does not match the layout");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(double), kind, s));
+    if (sync) CK(cudaStreamSynchronize(s));
+    return DGFV_OK;
+}
+
+int dgfv_set_state(dgfv_ctx* c, const double* d_U, int64_t n, void* stream) {
+    int r = copy_state(c, c ? c->d_U : nullptr, d_U, n, cudaMemcpyDeviceToDevice, stream, false);
+    if (r == DGFV_OK) c->state_valid = true;
+    return r;
+}
+
+int dgfv_get_state(dgfv_ctx* c, double* d_U, int64_t n, void* stream) {
+    if (c && !c->state_valid) return fail(c, DGFV_ERR_STATE, "no state set");
+    return copy_state(c, d_U, c ? c->d_U : nullptr, n, cudaMemcpyDeviceToDevice, stream, false);
+}
+
+int dgfv_set_state_host(dgfv_ctx* c, const double* h_U, int64_t n, void* stream) {
+    int r = copy_state(c, c ? c->d_U : nullptr, h_U, n, cudaMemcpyHostToDevice, stream, true);
+    if (r == DGFV_OK) c->state_valid = true;
+    return r;
+}
+
+int dgfv_get_state_host(dgfv_ctx* c, double* h_U, int64_t n, void* stream) {
+    if (c && !c->state_valid) return fail(c, DGFV_ERR_STATE, "no state set");
+    return copy_state(c, h_U, c ? c->d_U : nullptr, n, cudaMemcpyDeviceToHost, stream, true);
+}
+
+int dgfv_eval_rhs(dgfv_ctx* c, const double* d_U, double* d_R, void* stream) {
+    if (!c || !d_U || !d_R) return DGFV_ERR_ARG;
+    if (d_U == d_R) return fail(c, DGFV_ERR_ARG, "d_U and d_R alias");
+    cudaStream_t s = (cudaStream_t)stream;
+    enqueue_stage(c, d_U, d_U, d_R, 0, 0.0, 0.0, s);
+    CK(cudaGetLastError());
+    return DGFV_OK;
+}
+
+int dgfv_compute_dt(dgfv_ctx* c, const double* d_U, double* out3, void* stream) {
+    if (!c || !d_U || !out3) return DGFV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_dt(c->nk, params(c), c->all.view(), c->all.ntiles, d_U, c->opts.cfl_c, c->opts.cfl_v, c->d_partial,
+              c->d_dt3, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out3, c->d_dt3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return DGFV_OK;
+}
+
+int dgfv_rk_step(dgfv_ctx* c, double dt, double* dt_used, void* stream) {
+    if (!c) return DGFV_ERR_ARG;
+    if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "rk_step before set_state");
+    cudaStream_t s = (cudaStream_t)stream;
+    enqueue_rk_step(c, dt, s);
+    CK(cudaGetLastError());
+    if (dt_used) {
+        CK(cudaMemcpyAsync(dt_used, c->d_dt3, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return read_status(c, s);
+    }
+    return DGFV_OK;
+}
+
+int dgfv_rk_steps(dgfv_ctx* c, int n_steps, double dt, double* dt_used, void* stream) {
+    if (!c || n_steps < 0) return DGFV_ERR_ARG;
+    if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "rk_steps before set_state");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->prof.on) {
+        for (int i = 0; i < n_steps; ++i) enqueue_rk_step(c, dt, s);
+        CK(cudaGetLastError());
+    } else if (!c->graph_valid || c->graph_dt != dt || c->graph_stream != s) {
+        if (c->graph) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
+        cudaStream_t cs;
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        enqueue_rk_step(c, dt, cs);
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return fail(c, DGFV_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(c, DGFV_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        c->graph_valid = true;
+        c->graph_dt = dt;
+        c->graph_stream = s;
+    }
+    if (!c->prof.on)
+        for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(c->graph, s));
+    if (dt_used) {
+        CK(cudaMemcpyAsync(dt_used, c->d_dt3, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return read_status(c, s);
+    }
+    return DGFV_OK;
+}
+
+int dgfv_indicator(dgfv_ctx* c, const double* d_U, double* d_Ip, double* d_Ih, uint8_t* d_decision, void* stream) {
+    if (!c || !d_U) return DGFV_ERR_ARG;
+    const double thr[4] = {c->opts.T_fv_on, c->opts.T_fv_off, c->opts.T_ref, c->opts.T_crs};
+    Timed t(c, K_INDICATOR, (cudaStream_t)stream);
+    launch_indicator(c->nk, params(c), d_U, c->n_elem, d_Ip, d_Ih, d_decision, thr, c->N_min, c->N_max,
+                     (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return DGFV_OK;
+}
+
+int dgfv_adapt(dgfv_ctx* c, dgfv_adapt_stats* stats, void* stream) {
+    if (!c) return DGFV_ERR_ARG;
+    if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "adapt before set_state");
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(dgfv_indicator(c, c->d_U, c->d_Ip, c->d_Ih, c->d_dec, stream));
+    std::vector<uint8_t> dec(c->n_elem);
+    std::vector<double> Ip(c->n_elem), Ih(c->n_elem);
+    CK(cudaMemcpyAsync(dec.data(), c->d_dec, c->n_elem, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(Ip.data(), c->d_Ip, c->n_elem * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(Ih.data(), c->d_Ih, c->n_elem * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int8_t> Nn(c->n_elem);
+    std::vector<uint8_t> fn(c->n_elem);
+    int64_t changed = 0, near = 0;
+    const double T[4] = {c->opts.T_fv_on, c->opts.T_fv_off, c->opts.T_ref, c->opts.T_crs};
+    for (int e = 0; e < c->n_elem; ++e) {
+        int N = c->N[e];
+        int f = c->fv[e];
+        switch (dec[e]) {
+            case 1: f = 1; break;
+            case 2: f = 0; break;
+            case 3: N = N + 1; break;
+            case 4: N = N - 1; break;
+            default: break;
+        }
+        Nn[e] = (int8_t)N;
+        fn[e] = (uint8_t)f;
+        changed += dec[e] != 0;
+        bool nr = std::fabs(Ih[e] - (c->fv[e] ? T[1] : T[0])) < 1e-10;
+        if (!c->fv[e]) nr = nr || std::fabs(Ip[e] - T[2]) < 1e-10 || std::fabs(Ip[e] - T[3]) < 1e-10;
+        near += nr;
+    }
+    if (changed) TRY(set_pattern(c, Nn.data(), fn.data(), true, s));
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        int64_t dofs = 0;
+        for (int e = 0; e < c->n_elem; ++e) {
+            if (c->fv[e]) stats->n_fv++;
+            else stats->hist[c->N[e]]++;
+            dofs += (int64_t)c->npts[e] * c->npts[e] * c->npts[e];
+        }
+        stats->n_changed = changed;
+        stats->n_near = near;
+        stats->mean_dofs = (double)dofs / c->n_elem;
+    }
+    return read_status(c, s);
+}
+
+int dgfv_profile_enable(dgfv_ctx* c, int on) {
+    if (!c) return DGFV_ERR_ARG;
+    CK(cudaDeviceSynchronize());
+    c->prof.on = on != 0;
+    for (int k = 0; k < K_COUNT; ++k) c->prof.used[k] = 0;
+    return DGFV_OK;
+}
+
+int dgfv_profile_read(dgfv_ctx* c, double* ms, int64_t* launches, int cap) {
+    if (!c || cap < 0) return DGFV_ERR_ARG;
+    CK(cudaDeviceSynchronize());
+    const int nk = std::min<int>(cap, K_COUNT);
+    for (int k = 0; k < nk; ++k) {
+        double tot = 0.0;
+        for (size_t i = 0; i < c->prof.used[k]; ++i) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, c->prof.ev[k][i].first, c->prof.ev[k][i].second));
+            tot += t;
+        }
+        if (ms) ms[k] = tot;
+        if (launches) launches[k] = (int64_t)c->prof.used[k];
+    }
+    return nk;
+}
+
+int dgfv_sync_status(dgfv_ctx* c, void* stream) {
+    if (!c) return DGFV_ERR_ARG;
+    return read_status(c, (cudaStream_t)stream);
+}
+
+int64_t dgfv_bank_entry(dgfv_ctx* c, int which, int N, int M, double* out, int64_t cap) {
+    if (!c || !out) return DGFV_ERR_ARG;
+    if (N < c->N_min || N > c->N_max) return DGFV_ERR_ARG;
+    const int n = N + 1, m = M + 1;
+    std::vector<double> v;
+    try {
+        Bank1D b = make_bank(n);
+        switch (which) {
+            case 0: v = b.x; break;
+            case 1: v = b.w; break;
+            case 2: v = b.Dhat; break;
+            case 3: v = b.lm; break;
+            case 4: v = b.lp; break;
+            case 5:
+                if (M < c->N_min || M > c->N_max) return DGFV_ERR_ARG;
+                v = make_vmap(n, m);
+                break;
+            case 6: v = make_dg2fv(n, c->nfv); break;
+            case 7: v = make_fv2dg(n, c->nfv); break;
+            case 8: v = b.vinv; break;
+            default: return DGFV_ERR_ARG;
+        }
+    } catch (...) {
+        return DGFV_ERR_ARG;
+    }
+    if ((int64_t)v.size() > cap) return DGFV_ERR_ARG;
+    std::copy(v.begin(), v.end(), out);
+    return (int64_t)v.size();
+}
+
+double dgfv_probe_dfma(int iters, void* stream) { return probe_dfma(iters, (cudaStream_t)stream); }
+
+}  // extern "C"

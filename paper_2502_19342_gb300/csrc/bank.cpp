@@ -1,0 +1,217 @@
+// Reference-element operators on the host (FP64 results of long-double work),
+// uploaded once per context.  Written independently of any other
+// implementation in this repository:
+//   Legendre-Gauss nodes      Newton on P_n from Chebyshev-Gauss starting points
+//   Lagrange basis / D        barycentric formulas (weights lambda_j = 1/prod(x_j - x_k))
+//   Dhat_ij                   -(w_j/w_i) D_ji  (weighted derivative matrix of the weak
+//                             form; the weight ratio of Eq. 24 read so that the DGSEM
+//                             preserves a free stream and is exact on polynomials)
+//   V^{N->M}, N < M           barycentric interpolation at the finer nodes
+//   V^{N->M}, N > M           L2 projection by exact Gauss quadrature:
+//                             P_ij = w^N_j l^M_i(x^N_j) / w^M_i
+//   V^{DG->FV}                sub-cell means by a Gauss rule on every sub-cell
+//   V^{FV->DG}                Moore-Penrose inverse through a Householder QR factorisation
+//   Legendre Vandermonde^-1   V^-1 = V^T diag(w) (discrete orthonormality, Sec. 3.4)
+#include "bank.h"
+
+#include <cmath>
+#include <stdexcept>
+
+namespace dgfv {
+
+namespace {
+
+using ld = long double;
+
+void legendre_pd(int n, ld x, ld& P, ld& dP) {
+    ld p0 = 1, p1 = x;
+    if (n == 0) { P = 1; dP = 0; return; }
+    for (int k = 2; k <= n; ++k) {
+        ld p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+    }
+    P = p1;
+    // (1 - x^2) P_n' = n (P_{n-1} - x P_n)
+    dP = n * (p0 - x * p1) / (1 - x * x);
+}
+
+ld legendre_orthonormal(int m, ld x) {
+    ld p0 = 1, p1 = x;
+    if (m == 0) return std::sqrt((ld)0.5);
+    for (int k = 2; k <= m; ++k) {
+        ld p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+    }
+    return std::sqrt((2 * m + 1) / (ld)2) * p1;
+}
+
+struct Nodes {
+    std::vector<ld> x, w, lam;
+};
+
+Nodes gauss(int n) {
+    Nodes g;
+    g.x.resize(n);
+    g.w.resize(n);
+    const ld pi = 3.141592653589793238462643383279502884L;
+    for (int i = 0; i < n; ++i) {
+        ld x = -std::cos(pi * (2 * i + 1) / (2 * n));
+        for (int it = 0; it < 100; ++it) {
+            ld P, dP;
+            legendre_pd(n, x, P, dP);
+            const ld dx = P / dP;
+            x -= dx;
+            if (std::fabs((double)dx) < 1e-20) break;
+        }
+        ld P, dP;
+        legendre_pd(n, x, P, dP);
+        g.x[i] = x;
+        g.w[i] = 2 / ((1 - x * x) * dP * dP);
+    }
+    g.lam.resize(n);
+    for (int j = 0; j < n; ++j) {
+        ld p = 1;
+        for (int k = 0; k < n; ++k)
+            if (k != j) p *= (g.x[j] - g.x[k]);
+        g.lam[j] = 1 / p;
+    }
+    return g;
+}
+
+// All Lagrange polynomials of the node set at xi (barycentric formula of the second kind).
+std::vector<ld> lagrange_all(const Nodes& g, ld xi) {
+    const int n = (int)g.x.size();
+    std::vector<ld> l(n, 0);
+    for (int j = 0; j < n; ++j)
+        if (xi == g.x[j]) { l[j] = 1; return l; }
+    ld den = 0;
+    for (int j = 0; j < n; ++j) den += g.lam[j] / (xi - g.x[j]);
+    for (int j = 0; j < n; ++j) l[j] = g.lam[j] / (xi - g.x[j]) / den;
+    return l;
+}
+
+std::vector<double> to_d(const std::vector<ld>& a) { return std::vector<double>(a.begin(), a.end()); }
+
+}  // namespace
+
+Bank1D make_bank(int n) {
+    if (n < 1 || n > 16) throw std::runtime_error("bad node count");
+    Nodes g = gauss(n);
+    Bank1D b;
+    b.n = n;
+    b.x = to_d(g.x);
+    b.w = to_d(g.w);
+    std::vector<ld> D(n * n, 0);
+    for (int i = 0; i < n; ++i) {
+        ld diag = 0;
+        for (int j = 0; j < n; ++j) {
+            if (i == j) continue;
+            D[i * n + j] = (g.lam[j] / g.lam[i]) / (g.x[i] - g.x[j]);
+            diag -= D[i * n + j];
+        }
+        D[i * n + i] = diag;
+    }
+    b.D = to_d(D);
+    b.Dhat.resize(n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) b.Dhat[i * n + j] = (double)(-(g.w[j] / g.w[i]) * D[j * n + i]);
+    std::vector<ld> lm = lagrange_all(g, -1), lp = lagrange_all(g, 1);
+    b.lm = to_d(lm);
+    b.lp = to_d(lp);
+    b.lhm.resize(n);
+    b.lhp.resize(n);
+    for (int j = 0; j < n; ++j) {
+        b.lhm[j] = (double)(lm[j] / g.w[j]);
+        b.lhp[j] = (double)(lp[j] / g.w[j]);
+    }
+    b.vinv.resize(n * n);
+    for (int m = 0; m < n; ++m)
+        for (int i = 0; i < n; ++i) b.vinv[m * n + i] = (double)(g.w[i] * legendre_orthonormal(m, g.x[i]));
+    return b;
+}
+
+std::vector<double> make_vmap(int n_from, int n_to) {
+    Nodes a = gauss(n_from), b = gauss(n_to);
+    std::vector<ld> M(n_to * n_from, 0);
+    if (n_from <= n_to) {
+        for (int i = 0; i < n_to; ++i) {
+            std::vector<ld> l = lagrange_all(a, b.x[i]);
+            for (int j = 0; j < n_from; ++j) M[i * n_from + j] = l[j];
+        }
+    } else {
+        for (int j = 0; j < n_from; ++j) {
+            std::vector<ld> l = lagrange_all(b, a.x[j]);  // coarse basis at the fine nodes
+            for (int i = 0; i < n_to; ++i) M[i * n_from + j] = a.w[j] * l[i] / b.w[i];
+        }
+    }
+    return to_d(M);
+}
+
+namespace {
+
+std::vector<ld> dg2fv_ld(int n, int nfv) {
+    Nodes g = gauss(n);
+    Nodes q = gauss(n + 2);  // exact for the degree n-1 integrand
+    std::vector<ld> A(nfv * n, 0);
+    const ld l = (ld)2 / nfv;
+    for (int s = 0; s < nfv; ++s) {
+        const ld a = -1 + s * l;
+        for (size_t k = 0; k < q.x.size(); ++k) {
+            const ld xi = a + (q.x[k] + 1) * l / 2;
+            std::vector<ld> lv = lagrange_all(g, xi);
+            for (int j = 0; j < n; ++j) A[s * n + j] += q.w[k] * lv[j] / 2;
+        }
+    }
+    return A;
+}
+
+}  // namespace
+
+std::vector<double> make_dg2fv(int n, int nfv) { return to_d(dg2fv_ld(n, nfv)); }
+
+std::vector<double> make_fv2dg(int n, int nfv) {
+    if (nfv < n) throw std::runtime_error("N_FV < N+1");
+    // Householder QR of A (nfv x n): A = Q R, pinv(A) = R^{-1} Q^T.
+    std::vector<ld> A = dg2fv_ld(n, nfv);
+    const int m = nfv;
+    std::vector<ld> Q(m * m, 0);
+    for (int i = 0; i < m; ++i) Q[i * m + i] = 1;  // accumulates Q^T
+    std::vector<ld> Rm = A;
+    for (int k = 0; k < n; ++k) {
+        ld norm = 0;
+        for (int i = k; i < m; ++i) norm += Rm[i * n + k] * Rm[i * n + k];
+        norm = std::sqrt(norm);
+        const ld alpha = Rm[k * n + k] > 0 ? -norm : norm;
+        std::vector<ld> v(m, 0);
+        for (int i = k; i < m; ++i) v[i] = Rm[i * n + k];
+        v[k] -= alpha;
+        ld vv = 0;
+        for (int i = k; i < m; ++i) vv += v[i] * v[i];
+        if (vv == 0) continue;
+        for (int j = 0; j < n; ++j) {
+            ld s = 0;
+            for (int i = k; i < m; ++i) s += v[i] * Rm[i * n + j];
+            s = 2 * s / vv;
+            for (int i = k; i < m; ++i) Rm[i * n + j] -= s * v[i];
+        }
+        for (int j = 0; j < m; ++j) {  // Q^T <- H Q^T
+            ld s = 0;
+            for (int i = k; i < m; ++i) s += v[i] * Q[i * m + j];
+            s = 2 * s / vv;
+            for (int i = k; i < m; ++i) Q[i * m + j] -= s * v[i];
+        }
+    }
+    // X = R^{-1} (Q^T)[0:n, :]  by back substitution, column by column
+    std::vector<ld> X(n * m, 0);
+    for (int c = 0; c < m; ++c)
+        for (int i = n - 1; i >= 0; --i) {
+            ld s = Q[i * m + c];
+            for (int j = i + 1; j < n; ++j) s -= Rm[i * n + j] * X[j * m + c];
+            X[i * m + c] = s / Rm[i * n + i];
+        }
+    return to_d(X);
+}
+
+}  // namespace dgfv

@@ -1,0 +1,23 @@
+// Host computation of the reference-element operators (see bank.cpp).
+#pragma once
+
+#include <vector>
+
+namespace dgfv {
+
+struct Bank1D {
+    int n = 0;                    // Legendre-Gauss nodes per direction (N+1)
+    std::vector<double> x, w;     // nodes (ascending) and weights
+    std::vector<double> D;        // D[i*n+j] = l_j'(x_i)
+    std::vector<double> Dhat;     // Dhat[i*n+j] = -(w_j/w_i) D[j*n+i]
+    std::vector<double> lm, lp;   // l_j(-1), l_j(+1)
+    std::vector<double> lhm, lhp; // l_j(-1)/w_j, l_j(+1)/w_j
+    std::vector<double> vinv;     // inverse orthonormal-Legendre Vandermonde, [m*n + i]
+};
+
+Bank1D make_bank(int n);
+std::vector<double> make_vmap(int n_from, int n_to);  // n_to x n_from
+std::vector<double> make_dg2fv(int n, int nfv);        // nfv x n
+std::vector<double> make_fv2dg(int n, int nfv);        // n x nfv
+
+}  // namespace dgfv

@@ -1,0 +1,85 @@
+// Device-side data layout shared by the kernels and the host driver.
+//
+// Element tables are structure-of-arrays indexed by element id.  Face data is
+// stored per element and face: element e owns 6 face slots of n_e^2 points
+// (n_e = N_e+1 nodes for DG, N_FV sub-cells for FV); slot f of e starts at
+// face point fo[e] + f*n_e^2 and holds `width` doubles per point as
+// [(fo[e] + f*n_e^2)*width + var*n_e^2 + p], p = a + n_e*b with (a, b) the two
+// tangential indices in increasing axis order.  Faces: 0:-x 1:+x 2:-y 3:+y 4:-z 5:+z.
+#pragma once
+
+#include <cstdint>
+
+#include "physics.cuh"
+
+namespace dgfv {
+
+constexpr int MAXP = 8;        // points per direction (N <= 7, N_FV <= 8)
+constexpr int NBANK = MAXP + 1;
+
+// Offsets (in doubles) of the reference operators in the device bank, indexed
+// by the number of points n = N+1 of the DG degree.
+struct BankIdx {
+    int32_t dhat[NBANK];       // n x n weighted derivative matrix
+    int32_t lm[NBANK], lp[NBANK];    // l_j(-1), l_j(+1)
+    int32_t lhm[NBANK], lhp[NBANK];  // l_j(-1)/w_j, l_j(+1)/w_j
+    int32_t vinv[NBANK];       // inverse orthonormal-Legendre Vandermonde (n x n)
+    int32_t d2f[NBANK];        // V^{DG->FV}: N_FV x n
+    int32_t f2d[NBANK];        // V^{FV->DG}: n x N_FV
+    int32_t vm[NBANK][NBANK];  // V^{n->m}: m x n (interpolation up, L2 projection down)
+};
+
+struct Tables {
+    const uint8_t* n;    // points per direction
+    const uint8_t* N;    // DG degree
+    const uint8_t* fv;   // FV flag
+    const int64_t* off;  // state offset
+    const int64_t* fo;   // face-point offset of slot 0
+    const int32_t* nb;   // 6 neighbours per element
+    const double* rh;    // 3 per element: 2/h_d
+};
+
+struct Buffers {
+    double* fu;     // width V : DG trace of u / FV boundary sub-cell means
+    double* fg;     // width 3V: DG trace of the lifted gradient / FV boundary-cell gradient
+    double* flux;   // width V : outward normal flux on the element's own representation
+    double* flift;  // width V : BR1 lifting value U* (DG elements)
+    double* frec;   // width V : FV reconstructed state at the element face
+    double* rtmp;   // state-sized: volume part (DG) / interior sub-cell part (FV) of -R
+};
+
+struct Params {
+    DevPhys ph;
+    Tables t;
+    Buffers b;
+    const double* bank;
+    BankIdx bi;
+    int nfv;
+    int* status;  // device status word (first error wins)
+};
+
+// A tile is a run of `count` items (elements or faces) of one kind and size,
+// stored consecutively in `items` from `first`.
+struct Tiles {
+    const int32_t* first;
+    const int32_t* count;
+    const uint8_t* n;     // points per direction of the items (or common-representation size)
+    const int32_t* items;
+};
+
+// Faces: lower element L (across its +d face) and upper element R (its -d face).
+struct Faces {
+    const int32_t* L;
+    const int32_t* R;
+    const uint8_t* d;
+};
+
+__host__ __device__ __forceinline__ int node_index(int n, int d, int m, int a, int b) {
+    return d == 0 ? m + n * (a + n * b) : (d == 1 ? a + n * (m + n * b) : a + n * (b + n * m));
+}
+
+__device__ __forceinline__ void set_status(int* status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+}  // namespace dgfv

@@ -1,0 +1,33 @@
+// Host-side launchers of the kernels in kernels.cu (no torch types).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace dgfv {
+
+void launch_prolong(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s);
+size_t fv_smem_bytes(int nk, int nfv);
+void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s);
+void launch_face_lift(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s);
+size_t volume_smem_bytes(int nk, int n, int count);
+void launch_dg_volume(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
+                      cudaStream_t s);
+void launch_face_flux(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s);
+void launch_surface(int nk, const Params& P, const Tiles& T, int ntiles, const double* Uin, const double* U0,
+                    double* out, int mode, double a, double b, const double* dt, cudaStream_t s);
+void launch_dt(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, double cfl_c, double cfl_v,
+               double* partial, double* out3, cudaStream_t s);
+void launch_set_scalar(double* p, double v, cudaStream_t s);
+void launch_indicator(int nk, const Params& P, const double* U, int n_elem, double* Ip, double* Ih, uint8_t* dec,
+                      const double thr[4], int N_min, int N_max, cudaStream_t s);
+void launch_remap(const Params& P, const uint8_t* n_old, const uint8_t* N_old, const uint8_t* fv_old,
+                  const int64_t* off_old, const uint8_t* n_new, const uint8_t* N_new, const uint8_t* fv_new,
+                  const int64_t* off_new, int V, int n_elem, const double* Uo, double* Un, cudaStream_t s);
+double probe_dfma(int iters, cudaStream_t s);
+
+}  // namespace dgfv

@@ -1,0 +1,306 @@
+// Pointwise physics of the multi-component Navier-Stokes system (Sec. 2) as
+// device functions, templated on the number of species NK (V = NK + 4).
+//
+// State u = (rho_1..rho_NK, rho v, rho E); flux convention u_t + div(F^c + F^v) = 0:
+//   F^c_d = (rho_k v_d, rho v v_d + p e_d, (rho E + p) v_d)                 (Eq. 1)
+//   F^v_d = (J_k,d, -tau_{d.}, -tau_{d.}.v + q_h,d + q_d,d)                (Eqs. 1, 4, 5)
+// Mixture (Eqs. 8-12): c_v = sum Y c_v,k, c_p = sum Y c_p,k, R_mix = c_p - c_v,
+// kappa = c_p/c_v, T = eps/c_v, p = rho R_mix T, mu = sum Y mu_k,
+// Pr = sum Y Pr_k, lambda = mu c_p/Pr; sound speed c = sqrt(kappa p/rho).
+// Fickian fluxes with the mass-conserving correction
+// J_k = -rho D_k grad Y_k + rho Y_k sum_j D_j grad Y_j (sum_k J_k = 0).
+#pragma once
+
+#include <cstdint>
+
+namespace dgfv {
+
+constexpr int MAXSP = 3;
+constexpr int MAXV = MAXSP + 4;
+
+struct DevPhys {
+    int nk;
+    int viscous;
+    int riemann;  // 0 LLF, 1 Roe + Harten-Hyman
+    double cv[MAXSP], cp[MAXSP], mu[MAXSP], pr[MAXSP], D[MAXSP];
+    double maxD;
+};
+
+template <int NK>
+struct Prim {
+    double rho, irho, Y[NK], v[3], E, cv, icv, cp, kappa, T, p, c, mu, lam;
+};
+
+// Mixture state of a conserved vector.  3 divisions and 1 square root; terms
+// a caller does not use are removed by the compiler after inlining.
+template <int NK>
+__device__ __forceinline__ void prim(const DevPhys& P, const double* u, Prim<NK>& s) {
+    double rho = u[0];
+#pragma unroll
+    for (int k = 1; k < NK; ++k) rho += u[k];
+    s.rho = rho;
+    s.irho = 1.0 / rho;
+    double cv = 0.0, cp = 0.0, mu = 0.0, pr = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        s.Y[k] = u[k] * s.irho;
+        cv = fma(s.Y[k], P.cv[k], cv);
+        cp = fma(s.Y[k], P.cp[k], cp);
+        mu = fma(s.Y[k], P.mu[k], mu);
+        pr = fma(s.Y[k], P.pr[k], pr);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s.v[i] = u[NK + i] * s.irho;
+    s.E = u[NK + 3] * s.irho;
+    double eps = s.E - 0.5 * (s.v[0] * s.v[0] + s.v[1] * s.v[1] + s.v[2] * s.v[2]);
+    s.cv = cv;
+    s.cp = cp;
+    s.icv = 1.0 / cv;
+    s.kappa = cp * s.icv;
+    s.T = eps * s.icv;
+    s.p = rho * (cp - cv) * s.T;
+    s.c = sqrt(s.kappa * s.p * s.irho);
+    s.mu = mu;
+    s.lam = mu * cp / pr;
+}
+
+// Convective flux in direction d.
+template <int NK>
+__device__ __forceinline__ void flux_conv(const double* u, const Prim<NK>& s, int d, double* F) {
+    const double vd = s.v[d];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) F[k] = u[k] * vd;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[NK + i] = u[NK + i] * vd;
+    F[NK + d] += s.p;
+    F[NK + 3] = (u[NK + 3] + s.p) * vd;
+}
+
+// Primitive gradients from the conservative gradient g[dd*V + v] (chain rule
+// of the BR1 lifting variable, Eq. 14b): grad Y_k, grad v, grad T.
+template <int NK>
+struct PrimGrad {
+    double Y[NK][3], v[3][3], T[3];
+};
+
+template <int NK>
+__device__ __forceinline__ void prim_grad(const DevPhys& P, const Prim<NK>& s, const double* g,
+                                          PrimGrad<NK>& G) {
+    constexpr int V = NK + 4;
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+        const double* gd = g + dd * V;
+        double gr = gd[0];
+#pragma unroll
+        for (int k = 1; k < NK; ++k) gr += gd[k];
+        double gcv = 0.0;
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            G.Y[k][dd] = (gd[k] - s.Y[k] * gr) * s.irho;
+            gcv = fma(P.cv[k], G.Y[k][dd], gcv);
+        }
+        double geps = (gd[NK + 3] - s.E * gr) * s.irho;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            G.v[i][dd] = (gd[NK + i] - s.v[i] * gr) * s.irho;
+            geps -= s.v[i] * G.v[i][dd];
+        }
+        G.T[dd] = (geps - s.T * gcv) * s.icv;
+    }
+}
+
+// Viscous flux in direction d from the primitive gradients.
+template <int NK>
+__device__ __forceinline__ void flux_visc(const DevPhys& P, const Prim<NK>& s, const PrimGrad<NK>& G,
+                                          int d, double* F) {
+    const double divv = G.v[0][0] + G.v[1][1] + G.v[2][2];
+    double tau[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) tau[i] = s.mu * (G.v[d][i] + G.v[i][d]);
+    tau[d] -= s.mu * (2.0 / 3.0) * divv;
+    double corr = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) corr = fma(P.D[k], G.Y[k][d], corr);
+    double qd = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const double J = s.rho * (s.Y[k] * corr - P.D[k] * G.Y[k][d]);
+        F[k] = J;
+        qd = fma(P.cp[k], J, qd);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[NK + i] = -tau[i];
+    const double tv = tau[0] * s.v[0] + tau[1] * s.v[1] + tau[2] * s.v[2];
+    F[NK + 3] = -tv - s.lam * G.T[d] + s.T * qd;
+}
+
+// Local Lax-Friedrichs flux in +x_d: (F_L + F_R)/2 - s_max (u_R - u_L)/2.
+template <int NK>
+__device__ __forceinline__ void riemann_llf(const double* uL, const Prim<NK>& sL, const double* uR,
+                                            const Prim<NK>& sR, int d, double* F) {
+    constexpr int V = NK + 4;
+    double FL[V], FR[V];
+    flux_conv<NK>(uL, sL, d, FL);
+    flux_conv<NK>(uR, sR, d, FR);
+    const double aL = fabs(sL.v[d]) + sL.c, aR = fabs(sR.v[d]) + sR.c;
+    const double smax = aL > aR ? aL : aR;
+#pragma unroll
+    for (int v = 0; v < V; ++v) F[v] = 0.5 * ((FL[v] + FR[v]) - smax * (uR[v] - uL[v]));
+}
+
+// Roe flux with the Harten-Hyman entropy fix for the ideal-gas mixture:
+// sqrt(rho)-weighted averages of v, H, Y; kappa~ = c_p(Y~)/c_v(Y~);
+// c~^2 = (kappa~ - 1)(H~ - |v~|^2/2); waves v_n - c, v_n (contact per
+// species, shear), v_n + c; contact energy term eps_k = d(rho eps)/d(rho_k)
+// at fixed p and v; Harten-Hyman fix on the acoustic waves.
+template <int NK>
+__device__ __forceinline__ void riemann_roe(const DevPhys& P, const double* uL, const Prim<NK>& sL,
+                                            const double* uR, const Prim<NK>& sR, int d, double* F) {
+    constexpr int V = NK + 4;
+    double FL[V], FR[V];
+    flux_conv<NK>(uL, sL, d, FL);
+    flux_conv<NK>(uR, sR, d, FR);
+    const double rL = sqrt(sL.rho), rR = sqrt(sR.rho);
+    const double iw = 1.0 / (rL + rR);
+    const double wl = rL * iw, wr = rR * iw;
+    double vt[3], Yt[NK];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) vt[i] = wl * sL.v[i] + wr * sR.v[i];
+    double cvt = 0.0, cpt = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        Yt[k] = wl * sL.Y[k] + wr * sR.Y[k];
+        cvt = fma(Yt[k], P.cv[k], cvt);
+        cpt = fma(Yt[k], P.cp[k], cpt);
+    }
+    const double HL = sL.E + sL.p * sL.irho, HR = sR.E + sR.p * sR.irho;
+    const double Ht = wl * HL + wr * HR;
+    const double kt = cpt / cvt;
+    const double q2 = vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2];
+    const double c2 = (kt - 1.0) * (Ht - 0.5 * q2);
+    const double ct = sqrt(c2);
+    const double ic2 = 1.0 / c2;
+    const double rt = rL * rR;
+    const double vn = vt[d];
+    const double dp = sR.p - sL.p;
+    double dv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dv[i] = sR.v[i] - sL.v[i];
+    const double am = 0.5 * (dp - rt * ct * dv[d]) * ic2;
+    const double ap = 0.5 * (dp + rt * ct * dv[d]) * ic2;
+    auto hh = [](double lt, double lL, double lR) {
+        double delta = 0.0;
+        delta = fmax(delta, lt - lL);
+        delta = fmax(delta, lR - lt);
+        const double a = fabs(lt);
+        return a < delta ? delta : a;
+    };
+    const double lm = hh(vn - ct, sL.v[d] - sL.c, sR.v[d] - sR.c);
+    const double lp = hh(vn + ct, sL.v[d] + sL.c, sR.v[d] + sR.c);
+    const double l0 = fabs(vn);
+    const double sa = lm * am + lp * ap;
+    const double sd = (lp * ap - lm * am) * ct;
+    double Dis[V];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) Dis[k] = sa * Yt[k];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Dis[NK + i] = sa * vt[i];
+    Dis[NK + d] += sd;
+    Dis[NK + 3] = sa * Ht + sd * vn;
+    // contact waves
+    const double pt = rt * c2 / kt;
+    const double ecoef = -pt / ((kt - 1.0) * (kt - 1.0) * rt * cvt);
+    double scon = 0.0, econ = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const double ak = (uR[k] - uL[k]) - Yt[k] * dp * ic2;
+        const double s = l0 * ak;
+        Dis[k] += s;
+        scon += s;
+        econ += s * (0.5 * q2 + ecoef * (P.cp[k] - kt * P.cv[k]));
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Dis[NK + i] += scon * vt[i];
+    Dis[NK + 3] += econ;
+    // shear waves
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (i == d) continue;
+        const double s = l0 * rt * dv[i];
+        Dis[NK + i] += s;
+        Dis[NK + 3] += s * vt[i];
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) F[v] = 0.5 * ((FL[v] + FR[v]) - Dis[v]);
+}
+
+// Interface flux at one point in +x_d: F* = F^c*(uL,uR) + (F^v(uL,gL) + F^v(uR,gR))/2
+// (Eqs. 20, 21).
+template <int NK>
+__device__ __forceinline__ void interface_flux(const DevPhys& P, const double* uL, const double* gL,
+                                               const double* uR, const double* gR, int d, double* F) {
+    constexpr int V = NK + 4;
+    Prim<NK> sL, sR;
+    prim<NK>(P, uL, sL);
+    prim<NK>(P, uR, sR);
+    if (P.riemann == 1)
+        riemann_roe<NK>(P, uL, sL, uR, sR, d, F);
+    else
+        riemann_llf<NK>(uL, sL, uR, sR, d, F);
+    if (P.viscous) {
+        double FvL[V], FvR[V];
+        PrimGrad<NK> G;
+        prim_grad<NK>(P, sL, gL, G);
+        flux_visc<NK>(P, sL, G, d, FvL);
+        prim_grad<NK>(P, sR, gR, G);
+        flux_visc<NK>(P, sR, G, d, FvR);
+#pragma unroll
+        for (int v = 0; v < V; ++v) F[v] += 0.5 * (FvL[v] + FvR[v]);
+    }
+}
+
+// FV reconstruction variables w = (rho_1..rho_NK, v, p) and back.
+template <int NK>
+__device__ __forceinline__ void cons_to_w(const DevPhys& P, const double* u, double* w) {
+    double rho = u[0];
+#pragma unroll
+    for (int k = 1; k < NK; ++k) rho += u[k];
+    const double irho = 1.0 / rho;
+    double cvr = 0.0, cpr = 0.0;  // rho c_v, rho c_p
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        w[k] = u[k];
+        cvr = fma(u[k], P.cv[k], cvr);
+        cpr = fma(u[k], P.cp[k], cpr);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) w[NK + i] = u[NK + i] * irho;
+    const double ke = 0.5 * (u[NK] * w[NK] + u[NK + 1] * w[NK + 1] + u[NK + 2] * w[NK + 2]);
+    w[NK + 3] = ((cpr - cvr) / cvr) * (u[NK + 3] - ke);
+}
+
+template <int NK>
+__device__ __forceinline__ void w_to_cons(const DevPhys& P, const double* w, double* u) {
+    double rho = w[0];
+#pragma unroll
+    for (int k = 1; k < NK; ++k) rho += w[k];
+    double cvr = 0.0, cpr = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        u[k] = w[k];
+        cvr = fma(w[k], P.cv[k], cvr);
+        cpr = fma(w[k], P.cp[k], cpr);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) u[NK + i] = rho * w[NK + i];
+    const double ke = 0.5 * rho * (w[NK] * w[NK] + w[NK + 1] * w[NK + 1] + w[NK + 2] * w[NK + 2]);
+    // rho E = p / (kappa - 1) + rho |v|^2 / 2,  1/(kappa - 1) = c_v / (c_p - c_v)
+    u[NK + 3] = w[NK + 3] * (cvr / (cpr - cvr)) + ke;
+}
+
+__device__ __forceinline__ double minmod(double a, double b) {
+    if (a * b <= 0.0) return 0.0;
+    return fabs(a) <= fabs(b) ? a : b;
+}
+
+}  // namespace dgfv

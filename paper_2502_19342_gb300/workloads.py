@@ -162,7 +162,7 @@ def smooth_random_state(prob, seed, amp=0.05, rho0=1.0, p0=1.0, vel=(0.3, -0.2, 
     rng = np.random.default_rng(seed + 104729)
     nk = len(prob["gamma"])
     modes = [(a, b, c) for a in range(0, 2) for b in range(0, 2) for c in range(0, 2) if (a, b, c) != (0, 0, 0)]
-    ph = rng.uniform(0, 2 * np.pi, size=(nk + 4, len(modes)))
+    ph = rng.uniform(0, 2 * np.pi, size=(6, len(modes)))
     lo0, hi0 = prob["lo"][0], prob["hi"][0]
     L = hi0 - lo0
 
@@ -261,20 +261,52 @@ def _fourier_coeffs(rng, kmax, spectrum, solenoidal):
 
 
 def _eval_fourier(k1, c, X, Y, Z, L=2 * np.pi):
-    """Real part of sum_k c_k exp(i 2pi/L k.x) at points (X, Y, Z) of shape (ne, n^3)."""
+    """Real part of sum_k c_k exp(i 2pi/L k.x) at scattered points (small sets only)."""
     w = 2 * np.pi / L
-    ex = np.exp(1j * w * X[..., None] * k1)  # (ne, P, K)
-    ey = np.exp(1j * w * Y[..., None] * k1)
-    ez = np.exp(1j * w * Z[..., None] * k1)
+    ex = np.exp(1j * w * np.asarray(X)[..., None] * k1)
+    ey = np.exp(1j * w * np.asarray(Y)[..., None] * k1)
+    ez = np.exp(1j * w * np.asarray(Z)[..., None] * k1)
     out = []
     for comp in c:
-        t = np.einsum("epk,ijk->epij", ez, comp, optimize=True)
-        t = np.einsum("epj,epij->epi", ey, t, optimize=True)
-        out.append(np.real(np.einsum("epi,epi->ep", ex, t, optimize=True)))
+        t = np.einsum("pk,ijk->pij", ez.reshape(-1, len(k1)), comp, optimize=True)
+        t = np.einsum("pj,pij->pi", ey.reshape(-1, len(k1)), t, optimize=True)
+        out.append(np.real(np.einsum("pi,pi->p", ex.reshape(-1, len(k1)), t)).reshape(np.shape(X)))
     return out
 
 
-def turbulence(seed=0, nel=(48, 48, 48), riemann=0, mu=5e-4, Mt=0.3, k0=4.0, kmax=8):
+def _fourier_on_mesh(prob, k1, c, L, chunk=4096):
+    """Fourier series evaluated at the nodes of every DG element of a single
+    structured domain, separably: the nodes of an element are a tensor grid,
+    so the series is contracted axis by axis (z, then y, shared by all
+    elements of a layer / row, then x per element).  Returns one flat array
+    per component in the state's point layout (x fastest within an element)."""
+    w = 2 * np.pi / L
+    dims = prob["dims"][0]
+    lo = prob["lo"][0]
+    h = (prob["hi"][0] - lo) / dims
+    _, pos, _, _ = element_index(prob)
+    npd = points_per_dir(prob)
+    off = np.zeros(len(npd) + 1, np.int64)
+    off[1:] = np.cumsum(npd ** 3)
+    out = [np.zeros(off[-1]) for _ in range(len(c))]
+    for n in np.unique(npd):
+        sel = np.nonzero(npd == n)[0]
+        r = (np.polynomial.legendre.leggauss(int(n))[0] + 1) / 2
+        E = [np.exp(1j * w * ((np.arange(dims[a])[:, None] + r[None, :]) * h[a] + lo[a])[..., None] * k1)
+             for a in range(3)]  # (n_a, n, K) per axis
+        for q, comp in enumerate(c):
+            T1 = np.einsum("ijk,zck->zijc", comp, E[2], optimize=True)       # (nz, K, K, n)
+            T2 = np.einsum("ybj,zijc->yzibc", E[1], T1, optimize=True)       # (ny, nz, K, n, n)
+            for s0 in range(0, len(sel), chunk):
+                es = sel[s0:s0 + chunk]
+                ix, iy, iz = pos[es, 0], pos[es, 1], pos[es, 2]
+                v = np.einsum("eai,eibc->ecba", E[0][ix], T2[iy, iz], optimize=True)
+                idx = off[es][:, None] + np.arange(int(n) ** 3)[None, :]
+                out[q][idx.ravel()] = np.real(v).reshape(len(es), -1).ravel()
+    return out
+
+
+def turbulence(seed=0, nel=(48, 48, 48), riemann=0, mu=5e-4, Mt=0.3, k0=4.0, kmax=8, N0=None):
     """Periodic [0,2pi]^3, 48^3 elements, N drawn from {1..7}, 3 species
     (gamma 1.4/1.3/1.67, M 29/44/4), N_FV = 8.  Random-phase solenoidal
     velocity with E(k) ~ k^4 exp(-2 (k/k0)^2), k0 = 4, scaled to turbulent Mach
@@ -282,43 +314,65 @@ def turbulence(seed=0, nel=(48, 48, 48), riemann=0, mu=5e-4, Mt=0.3, k0=4.0, kma
     over about 2 node spacings; p = 1 and uniform temperature."""
     sp = species_set([AIR, CO2, HELIUM], mu=mu)
     n_elem = nel[0] * nel[1] * nel[2]
-    N = random_degrees(n_elem, 1, 7, seed)
+    # N0 = None: degrees drawn from {1..7}; an integer: that degree everywhere
+    N = random_degrees(n_elem, 1, 7, seed) if N0 is None else np.full(n_elem, N0, np.int8)
     L = 2 * np.pi
     prob = make_problem([(nel, (0, 0, 0), (L, L, L))], sp, n_fv=8, N=N, riemann=riemann)
     rng = np.random.default_rng(seed + 1)
     k1, cu = _fourier_coeffs(rng, kmax, lambda k: k ** 4 * np.exp(-2 * (k / k0) ** 2), True)
-    _, cb1 = _fourier_coeffs(rng, 3, lambda k: np.exp(-(k / 2.0) ** 2), False)
+    kb, cb1 = _fourier_coeffs(rng, 3, lambda k: np.exp(-(k / 2.0) ** 2), False)
     _, cb2 = _fourier_coeffs(rng, 3, lambda k: np.exp(-(k / 2.0) ** 2), False)
     T0 = 1.0 / sp["Rgas"][0]
     c0 = math.sqrt(1.4)
-    # normalise the velocity to the turbulent Mach number with a coarse sample
+    # normalise with a coarse sample: turbulent Mach number and blob field scales
     g = np.linspace(0, L, 24, endpoint=False)
-    gx, gy, gz = np.meshgrid(g, g, g, indexing="ij")
-    vs = _eval_fourier(k1, cu, gx.reshape(1, -1), gy.reshape(1, -1), gz.reshape(1, -1))
-    urms = math.sqrt(np.mean(vs[0] ** 2 + vs[1] ** 2 + vs[2] ** 2))
-    vscale = Mt * c0 / urms
-    b1s = _eval_fourier(np.arange(-3, 4), cb1, gx.reshape(1, -1), gy.reshape(1, -1), gz.reshape(1, -1))[0]
-    b2s = _eval_fourier(np.arange(-3, 4), cb2, gx.reshape(1, -1), gy.reshape(1, -1), gz.reshape(1, -1))[0]
-    s1, s2 = b1s.std(), b2s.std()
-    h = L / nel[0]
-    width = 2 * h / 5.0
+    gx, gy, gz = (a.ravel() for a in np.meshgrid(g, g, g, indexing="ij"))
+    vs = _eval_fourier(k1, cu, gx, gy, gz)
+    vscale = Mt * c0 / math.sqrt(np.mean(vs[0] ** 2 + vs[1] ** 2 + vs[2] ** 2))
+    s1 = _eval_fourier(kb, cb1, gx, gy, gz)[0].std()
+    s2 = _eval_fourier(kb, cb2, gx, gy, gz)[0].std()
+    width = 2 * (L / nel[0]) / 2.0  # 2 node spacings of the coarsest degree present (N = 1)
+    vx, vy, vz = _fourier_on_mesh(prob, k1, cu, L)
+    g1 = _fourier_on_mesh(prob, kb, cb1, L)[0] / s1
+    g2 = _fourier_on_mesh(prob, kb, cb2, L)[0] / s2
+    b1 = 0.5 * (1 + np.tanh(g1 / width))
+    b2 = 0.5 * (1 + np.tanh(g2 / width))
+    Y2 = 0.6 * b1 * (1 - b2)
+    Y3 = 0.6 * b2
+    Y1 = 1.0 - Y2 - Y3
+    Rg = sp["Rgas"]
+    rho = 1.0 / ((Y1 * Rg[0] + Y2 * Rg[1] + Y3 * Rg[2]) * T0)
+    pts = dict(rk=[rho * Y1, rho * Y2, rho * Y3], v=[vscale * vx, vscale * vy, vscale * vz], p=np.ones_like(rho))
+    return prob, _assemble(prob, pts)
 
-    def fn(x, y, z):
-        v = _eval_fourier(k1, cu, x, y, z)
-        g1 = _eval_fourier(np.arange(-3, 4), cb1, x, y, z)[0] / s1
-        g2 = _eval_fourier(np.arange(-3, 4), cb2, x, y, z)[0] / s2
-        # unit-slope-normalised level sets, smoothed over ~2 node spacings
-        b1 = 0.5 * (1 + np.tanh(g1 / (width * 1.5)))
-        b2 = 0.5 * (1 + np.tanh(g2 / (width * 1.5)))
-        Y2 = 0.6 * b1 * (1 - b2)
-        Y3 = 0.6 * b2
-        Y1 = 1.0 - Y2 - Y3
-        Rm = Y1 * sp["Rgas"][0] + Y2 * sp["Rgas"][1] + Y3 * sp["Rgas"][2]
-        rho = 1.0 / (Rm * T0)
-        return [rho * Y1, rho * Y2, rho * Y3], tuple(vscale * q for q in v), np.ones_like(x)
 
-    return prob, build_state(prob, fn, chunk=1024)
+def _assemble(prob, pts):
+    """Conserved state from point fields in the state's point layout (rho E
+    from the ideal-gas mixture relation of the initial condition)."""
+    nk = len(prob["gamma"])
+    cv = prob["Rgas"] / (prob["gamma"] - 1.0)
+    cp = prob["gamma"] * cv
+    rk, v, p = pts["rk"], pts["v"], pts["p"]
+    rho = sum(rk)
+    kap = sum(rk[k] * cp[k] for k in range(nk)) / sum(rk[k] * cv[k] for k in range(nk))
+    fields = list(rk) + [rho * v[0], rho * v[1], rho * v[2],
+                         p / (kap - 1.0) + 0.5 * rho * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2)]
+    npd = points_per_dir(prob)
+    n3 = npd ** 3
+    V = nk + 4
+    poff = np.zeros(len(npd), np.int64)
+    poff[1:] = np.cumsum(n3)[:-1]
+    off, size = offsets(prob)
+    U = np.empty(size)
+    for n in np.unique(npd):
+        es = np.nonzero(npd == n)[0]
+        m3 = int(n) ** 3
+        src = poff[es][:, None] + np.arange(m3)[None, :]
+        blk = np.stack([f[src] for f in fields], axis=1)  # (ne, V, m3)
+        dst = off[es][:, None] + np.arange(V * m3)[None, :]
+        U[dst.ravel()] = blk.reshape(len(es), -1).ravel()
+    return U
 
 
 # Indicator thresholds {T_fv_on, T_fv_off, T_ref, T_crs} (configuration values).
-THRESHOLDS = (1.0, 1.6, 3.0, 7.0)
+THRESHOLDS = (1.0, 1.6, 3.0, 5.0)

@@ -1,0 +1,225 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded
+inputs: R(U), the time step, SSP-RK3 steps, the modal indicator's decisions
+and the remap, on small cases that span several tiles and ragged tails, the
+paper-shaped workloads and edge cases."""
+import numpy as np
+import pytest
+
+from paper_2502_19342_gb300 import workloads as W
+from tests.gpu_helpers import RTOL, assert_fields_close, assert_rhs_close, ctx_for, gpu_rhs, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+def _mixed(seed, nk=2, nel=(3, 4, 5), Nlo=1, Nhi=7, fv_frac=0.25, n_fv=8, riemann=0, mu=2e-3, box=(1.0, 1.3, 0.9)):
+    specs = [W.AIR, W.HELIUM, W.CO2][:nk]
+    sp = W.species_set(specs, mu=mu)
+    n = nel[0] * nel[1] * nel[2]
+    prob = W.make_problem([(nel, (0, 0, 0), box)], sp, n_fv=n_fv, N=W.random_degrees(n, Nlo, Nhi, seed),
+                          fv=W.random_fv(n, fv_frac, seed), riemann=riemann)
+    return prob, W.smooth_random_state(prob, seed, amp=0.1)
+
+
+def test_operator_bank_matches_oracle(oracle):
+    prob, _ = _mixed(0)
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    for N in range(1, 8):
+        b = oracle.basis(N)
+        np.testing.assert_allclose(ctx.bank_entry(0, N), b["x"], atol=1e-15)
+        np.testing.assert_allclose(ctx.bank_entry(1, N), b["w"], atol=1e-15)
+        np.testing.assert_allclose(ctx.bank_entry(2, N), b["Dhat"].ravel(), atol=1e-12)
+        np.testing.assert_allclose(ctx.bank_entry(3, N), b["lm"], atol=1e-14)
+        np.testing.assert_allclose(ctx.bank_entry(4, N), b["lp"], atol=1e-14)
+        np.testing.assert_allclose(ctx.bank_entry(6, N), oracle.dg2fv(N, 8).ravel(), atol=1e-14)
+        np.testing.assert_allclose(ctx.bank_entry(7, N), oracle.fv2dg(N, 8).ravel(), atol=1e-12)
+        np.testing.assert_allclose(ctx.bank_entry(8, N), np.linalg.inv(oracle.leg_vandermonde(N)).ravel(), atol=1e-13)
+        for M in range(1, 8):
+            np.testing.assert_allclose(ctx.bank_entry(5, N, M), oracle.vmap(N, M).ravel(), atol=1e-13)
+    ctx.close()
+
+
+def test_rhs_plain_tiny(oracle):
+    """4x4x4 elements, N = 3, two species, viscous: R(U) per field within
+    1e-12 of the extended-precision oracle, or within 3x the FP64 oracle's own
+    rounding error where that is larger."""
+    prob, U = W.plain_tiny(0)
+    assert_rhs_close(oracle, prob, U, gpu_rhs(prob, U))
+
+
+@pytest.mark.parametrize("nk,riemann,mu,seed", [(2, 0, 2e-3, 1), (3, 0, 2e-3, 2), (2, 1, 2e-3, 3), (3, 1, 0.0, 4),
+                                                (1, 0, 1e-3, 5), (3, 1, 5e-3, 6)])
+def test_rhs_mixed_hp_fv(oracle, nk, riemann, mu, seed):
+    """Random degrees 1..7 and FV elements (N_FV = 8) on a 3x4x5 box: every
+    face type (equal and unequal degree, DG/FV, FV/FV) and ragged tiles."""
+    prob, U = _mixed(seed, nk=nk, riemann=riemann, mu=mu)
+    assert_rhs_close(oracle, prob, U, gpu_rhs(prob, U))
+
+
+def test_rhs_batched_domains(oracle):
+    """Several independent periodic domains of uneven size and degree in one context."""
+    sp = W.species_set([W.AIR, W.HELIUM, W.CO2], mu=1e-3)
+    rng = np.random.default_rng(11)
+    doms, N = [], []
+    for d in range(6):
+        dims = tuple(int(x) for x in rng.integers(1, 4, 3))
+        lo = tuple(float(x) for x in rng.uniform(-1, 1, 3))
+        doms.append((dims, lo, tuple(l + float(s) for l, s in zip(lo, rng.uniform(0.5, 2.0, 3)))))
+        N += [int(rng.integers(1, 8))] * int(np.prod(dims))
+    prob = W.make_problem(doms, sp, n_fv=8, N=np.array(N, np.int8), fv=W.random_fv(len(N), 0.2, 3))
+    U = W.smooth_random_state(prob, 3, amp=0.05)
+    assert_rhs_close(oracle, prob, U, gpu_rhs(prob, U))
+
+
+def test_rhs_free_stream(oracle):
+    prob, _ = _mixed(7, nk=3, riemann=1)
+    U = W.constant_state(prob, [0.5, 0.3, 0.2], (1.0, -0.5, 0.25), 1.0)
+    R = gpu_rhs(prob, U)
+    assert np.abs(R).max() < 1e-11
+
+
+def test_rhs_edge_degrees_and_single_element_domains(oracle):
+    """Degree extremes N = 1 and 7, FV with N_FV = N_max + 1, and 1-element-wide
+    periodic directions (an element is its own neighbour)."""
+    sp = W.species_set([W.AIR, W.HELIUM], mu=2e-3)
+    doms = [((1, 1, 1), (0, 0, 0), (1, 1, 1)), ((2, 1, 3), (0, 0, 0), (1, 0.5, 1.5)), ((1, 4, 1), (0, 0, 0), (0.3, 1, 0.3))]
+    n = 1 + 6 + 4
+    N = np.array([7, 1, 7, 1, 7, 1, 7, 1, 2, 7, 3], np.int8)
+    fv = np.array([0, 0, 1, 0, 0, 1, 0, 0, 1, 0, 0], np.uint8)
+    prob = W.make_problem(doms, sp, n_fv=8, N=N, fv=fv, riemann=1)
+    assert n == len(N)
+    U = W.smooth_random_state(prob, 9, amp=0.05)
+    assert_rhs_close(oracle, prob, U, gpu_rhs(prob, U))
+
+
+def test_time_step(oracle):
+    prob, U = _mixed(12, nk=3)
+    ctx = ctx_for(prob, opts=dict(cfl_c=0.5, cfl_v=0.4))
+    dt, dtc, dtv = ctx.compute_dt(to_dev(U))
+    rdt, rdtc, rdtv = oracle.dt(prob, U, 0.5, 0.4)
+    assert abs(dtc - rdtc) <= 1e-14 * rdtc
+    assert abs(dtv - rdtv) <= 1e-14 * rdtv
+    assert abs(dt - rdt) <= 1e-14 * rdt
+
+
+def test_rk3_ten_steps_plain_tiny(oracle):
+    """The plain tiny case advanced 10 SSP-RK3 steps at CFL 0.5: the final state
+    per field within 1e-12 of the oracle's."""
+    prob, U = W.plain_tiny(0)
+    ctx = ctx_for(prob, opts=dict(cfl_c=0.5, cfl_v=0.5))
+    ctx.set_state(to_dev(U))
+    dts = [ctx.rk_step(-1.0) for _ in range(10)]
+    Ug = ctx.get_state().cpu().numpy()
+    Uo, odts = oracle.rk3(prob, U, 10, cfl_c=0.5, cfl_v=0.5)
+    np.testing.assert_allclose(dts, odts, rtol=1e-13)
+    assert_fields_close(prob, Ug - U, Uo - U, what="U(t10) - U(0)", rtol=1e-10)
+    assert_fields_close(prob, Ug, Uo, what="U(t10)")
+
+
+def test_rk_steps_graph_matches_single_steps(oracle):
+    prob, U = _mixed(13, nk=2, Nhi=5)
+    a = ctx_for(prob)
+    b = ctx_for(prob)
+    a.set_state(to_dev(U))
+    b.set_state(to_dev(U))
+    for _ in range(4):
+        a.rk_step(-1.0)
+    b.rk_steps(4, -1.0)
+    np.testing.assert_array_equal(a.get_state().cpu().numpy(), b.get_state().cpu().numpy())
+
+
+def test_rk3_mixed_fixed_dt(oracle):
+    prob, U = _mixed(14, nk=3, riemann=1, Nhi=6)
+    ctx = ctx_for(prob)
+    ctx.set_state(to_dev(U))
+    dt = 2e-4
+    for _ in range(3):
+        ctx.rk_step(dt)
+    Uo, _ = oracle.rk3(prob, U, 3, dt_fixed=dt)
+    assert_fields_close(prob, ctx.get_state().cpu().numpy(), Uo, what="U(3 steps)")
+
+
+def _decisions_match(oracle, prob, U, thr, N_min, N_max):
+    ctx = ctx_for(prob, opts=dict(thresholds=thr), N_min=N_min, N_max=N_max)
+    Ip, Ih, dec = ctx.indicator(to_dev(U))
+    Ip, Ih, dec = Ip.cpu().numpy(), Ih.cpu().numpy(), dec.cpu().numpy()
+    oIp, oIh = oracle.indicator(prob, U)
+    # Indicator values agree to the rounding of the logarithm of small modal
+    # energies (an energy fraction w carries a relative error of about
+    # 1e-16/sqrt(w), so fractions near the 1e-24 floor move I by up to ~1e-6);
+    # the contract is on the decisions: bit-exact outside a 1e-10 band.
+    np.testing.assert_allclose(Ip, oIp, rtol=1e-6, atol=1e-9)
+    np.testing.assert_allclose(Ih, oIh, rtol=1e-6, atol=1e-9)
+    Nn, fn = oracle.adapt_decide(prob, oIp, oIh, thr, N_min, N_max)
+    code = np.zeros(len(Nn), np.uint8)
+    code[(fn == 1) & (prob["fv"] == 0)] = 1
+    code[(fn == 0) & (prob["fv"] == 1)] = 2
+    code[(Nn > prob["N"]) & (code == 0)] = 3
+    code[(Nn < prob["N"]) & (code == 0)] = 4
+    near = np.zeros(len(Nn), bool)
+    for T in thr:
+        near |= (np.abs(oIp - T) < 1e-10) | (np.abs(oIh - T) < 1e-10)
+    mism = (code != dec) & ~near
+    assert not mism.any(), f"{mism.sum()} decisions differ outside the 1e-10 band"
+    return ctx, code, near.sum()
+
+
+def test_indicator_decisions_hp_shock(oracle):
+    """Decisions on the hp-mixed shock workload (reduced to 8x8x8 elements, with
+    random FV elements): bit-exact except for elements whose indicator lies
+    within 1e-10 of a threshold."""
+    prob, U = W.hp_shock(0, nel=(8, 8, 8))
+    prob["fv"] = W.random_fv(W.n_elements(prob), 0.2, 1)
+    U = W.build_state(prob, lambda x, y, z: (
+        [2.3 + 0.2 * np.tanh((x - 0.5) / 0.05), 0.2 + 0.1 * np.sin(6 * y)], (0.1 + 0 * x, 0 * x, 0 * x),
+        1.6 + 0.5 * np.tanh((x - 1.0) / 0.03)))
+    ctx, code, near = _decisions_match(oracle, prob, U, W.THRESHOLDS, 2, 6)
+    assert (code != 0).sum() > 10  # the case exercises the rules
+    ctx.close()
+
+
+def test_adapt_remaps_like_the_oracle(oracle):
+    prob, U = _mixed(21, nk=2, Nlo=2, Nhi=6, fv_frac=0.2, n_fv=8)
+    thr = (1.0, 1.6, 3.0, 7.0)
+    ctx, code, near = _decisions_match(oracle, prob, U, thr, 1, 7)
+    assert near == 0
+    ctx.set_state(to_dev(U))
+    stats = ctx.adapt()
+    N_new, fv_new = ctx.get_degrees()
+    oIp, oIh = oracle.indicator(prob, U)
+    oN, ofv = oracle.adapt_decide(prob, oIp, oIh, thr, 1, 7)
+    np.testing.assert_array_equal(N_new, oN)
+    np.testing.assert_array_equal(fv_new, ofv)
+    assert stats["n_changed"] == int((code != 0).sum())
+    Ug = ctx.get_state().cpu().numpy()
+    Uo = oracle.remap(prob, oN, ofv, U)
+    new = dict(prob, N=oN, fv=ofv)
+    assert_fields_close(new, Ug, Uo, what="remapped state", rtol=1e-13)
+    ctx.close()
+
+
+def test_set_degrees_remap_round_trip(oracle):
+    prob, U = _mixed(22, nk=3, Nlo=1, Nhi=6, fv_frac=0.0)
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    ctx.set_state(to_dev(U))
+    up = (prob["N"] + 1).astype(np.int8)
+    ctx.set_degrees(up, None, remap=True)
+    ctx.set_degrees(prob["N"], None, remap=True)
+    np.testing.assert_allclose(ctx.get_state().cpu().numpy(), U, atol=1e-12)
+    ctx.set_degrees(prob["N"], np.ones(len(up), np.uint8), remap=True)
+    ctx.set_degrees(prob["N"], None, remap=True)
+    np.testing.assert_allclose(ctx.get_state().cpu().numpy(), U, atol=1e-11)
+
+
+def test_rejects_bad_arguments():
+    from paper_2502_19342_gb300 import dgfv
+    prob, U = _mixed(0)
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    with pytest.raises(dgfv.DgfvError):
+        ctx.set_degrees(np.full(ctx.n_elem, 9, np.int8))
+    with pytest.raises(ValueError):
+        ctx.eval_rhs(to_dev(U[:-1]))
+    with pytest.raises(dgfv.DgfvError):
+        ctx.rk_step(-1.0)  # no state yet
+    ctx.close()

@@ -514,7 +514,7 @@ def test_indicator_recovers_exponential_decay_rate(oracle, N, sigma):
     y = np.log(w)
     slope = ((m - m.mean()) * (y - y.mean())).sum() / ((m - m.mean()) ** 2).sum()
     assert abs(Ip[0] - abs(slope)) < 1e-10
-    assert Ih[0] > 5  # uniform p and Y: only round-off in the higher modes
+    assert Ih[0] > 4  # uniform p and Y: all higher modes at the energy floor
 
 
 def test_indicator_pure_exponential_spectrum(oracle):
