@@ -137,6 +137,23 @@ int dgfv_eval_rhs(dgfv_ctx* ctx, const double* d_U, double* d_R, void* stream);
  * min dt_v}.  Synchronises the stream. */
 int dgfv_compute_dt(dgfv_ctx* ctx, const double* d_U, double* out3, void* stream);
 
+/* Allocation-free variant of dgfv_compute_dt, for callers that may not
+ * allocate device memory when they need a time step: code in a
+ * latency-critical loop, where cudaMalloc/cudaFree would synchronise the
+ * device, and hosts that own all device memory and forbid allocations after
+ * start-up.  The paper has no counterpart; it is an interface of this
+ * library.  Same result as dgfv_compute_dt, written to d_out3, a device array
+ * of 3 doubles the caller owns ({dt, min dt_c, min dt_v}); nothing is copied
+ * to the host and the stream is not synchronised.  The reduction's per-block
+ * minima live in one fixed device array of 65536 block pairs (1 MiB) that
+ * every GPU loading the library holds until the process exits; contexts
+ * whose time-step launch needs more blocks get DGFV_ERR_ARG.  The first call
+ * on a device looks the array's device address up; make that first call
+ * before any stream capture.  All calls share the array: calls that may run
+ * at the same time on the GPU (different streams, different contexts) race
+ * and must be ordered by the caller.  Allocates nothing. */
+int dgfv_compute_dt_noalloc(dgfv_ctx* ctx, const double* d_U, double* d_out3, void* stream);
+
 /* One SSP-RK3 step (Shu-Osher) of the context's state.  dt > 0 uses that
  * step; dt <= 0 uses the CFL step of Sec. 3.3 computed on the device from
  * the state at the start of the step.  dt_used (host, may be NULL) receives

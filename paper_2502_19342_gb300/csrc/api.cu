@@ -569,6 +569,18 @@ int dgfv_compute_dt(dgfv_ctx* c, const double* d_U, double* out3, void* stream) 
     return DGFV_OK;
 }
 
+int dgfv_compute_dt_noalloc(dgfv_ctx* c, const double* d_U, double* d_out3, void* stream) {
+    if (!c || !d_U || !d_out3) return DGFV_ERR_ARG;
+    const int r = launch_dt_noalloc(c->nk, params(c), c->all.view(), c->all.ntiles, d_U, c->opts.cfl_c,
+                                    c->opts.cfl_v, d_out3, (cudaStream_t)stream);
+    if (r == 1)
+        return fail(c, DGFV_ERR_ARG, "dgfv_compute_dt_noalloc: " + std::to_string(c->all.ntiles) +
+                                         " work tiles exceed the fixed scratch of " +
+                                         std::to_string(DT_NOALLOC_MAX_BLOCKS) + " blocks");
+    if (r != 0) return fail(c, DGFV_ERR_CUDA, "dgfv_compute_dt_noalloc: CUDA error");
+    return DGFV_OK;
+}
+
 int dgfv_rk_step(dgfv_ctx* c, double dt, double* dt_used, void* stream) {
     if (!c) return DGFV_ERR_ARG;
     if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "rk_step before set_state");

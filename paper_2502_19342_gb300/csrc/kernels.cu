@@ -22,6 +22,7 @@
 
 #include <cfloat>
 #include <cstdint>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -887,6 +888,41 @@ void launch_dt(int nk, const Params& P, const Tiles& T, int ntiles, const double
 }
 
 void launch_set_scalar(double* p, double v, cudaStream_t s) { k_set_scalar<<<1, 1, 0, s>>>(p, v); }
+
+// Scratch of the allocation-free time step (dgfv_compute_dt_noalloc): the
+// per-block minima of k_dt live in this fixed array instead of a buffer the
+// context allocated.  Every device that loads the library holds the array
+// (2 * DT_NOALLOC_MAX_BLOCKS doubles = 1 MiB) until the process exits.
+static __device__ __align__(256) double g_dt_partial[2 * DT_NOALLOC_MAX_BLOCKS];
+
+namespace {
+std::mutex g_dt_partial_mutex;
+double* g_dt_partial_addr[DT_NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+int launch_dt_noalloc(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, double cfl_c,
+                      double cfl_v, double* out3, cudaStream_t s) {
+    if (ntiles < 1 || ntiles > DT_NOALLOC_MAX_BLOCKS) return 1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= DT_NOALLOC_MAX_DEVICES) return 2;
+    double* partial = nullptr;
+    {
+        // Host code cannot use the array's name as a device address: look the
+        // address up once per device, with that device current.
+        std::lock_guard<std::mutex> lock(g_dt_partial_mutex);
+        if (!g_dt_partial_addr[dev]) {
+            void* a = nullptr;
+            if (cudaGetSymbolAddress(&a, g_dt_partial) != cudaSuccess) return 2;
+            g_dt_partial_addr[dev] = static_cast<double*>(a);
+        }
+        partial = g_dt_partial_addr[dev];
+    }
+    // every block writes its pair before k_dt_final reads it, in stream order,
+    // so nothing has to be cleared between calls
+    DGFV_DISPATCH(nk, (k_dt<NK><<<ntiles, 256, 0, s>>>(P, T, U, cfl_c, cfl_v, partial)));
+    k_dt_final<<<1, 1024, 0, s>>>(partial, ntiles, P.ph.viscous, out3);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
 
 void launch_indicator(int nk, const Params& P, const double* U, int n_elem, double* Ip, double* Ih, uint8_t* dec,
                       const double thr[4], int N_min, int N_max, cudaStream_t s) {

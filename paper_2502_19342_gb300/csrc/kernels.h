@@ -23,6 +23,12 @@ void launch_surface(int nk, const Params& P, const Tiles& T, int ntiles, const d
 void launch_dt(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, double cfl_c, double cfl_v,
                double* partial, double* out3, cudaStream_t s);
 void launch_set_scalar(double* p, double v, cudaStream_t s);
+// Time step with the per-block minima in a fixed device array (no allocation).
+// Returns 0, 1 when ntiles exceeds DT_NOALLOC_MAX_BLOCKS, 2 on a CUDA error.
+constexpr int DT_NOALLOC_MAX_BLOCKS = 65536;
+constexpr int DT_NOALLOC_MAX_DEVICES = 64;
+int launch_dt_noalloc(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, double cfl_c,
+                      double cfl_v, double* out3, cudaStream_t s);
 void launch_indicator(int nk, const Params& P, const double* U, int n_elem, double* Ip, double* Ih, uint8_t* dec,
                       const double thr[4], int N_min, int N_max, cudaStream_t s);
 void launch_remap(const Params& P, const uint8_t* n_old, const uint8_t* N_old, const uint8_t* fv_old,

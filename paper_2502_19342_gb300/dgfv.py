@@ -21,7 +21,7 @@ SYMBOLS = ["dgfv_init_mesh", "dgfv_num_elements", "dgfv_set_degrees", "dgfv_get_
            "dgfv_set_state", "dgfv_get_state", "dgfv_set_state_host", "dgfv_get_state_host", "dgfv_eval_rhs",
            "dgfv_compute_dt", "dgfv_rk_step", "dgfv_rk_steps", "dgfv_indicator", "dgfv_adapt", "dgfv_sync_status",
            "dgfv_status_string", "dgfv_last_error", "dgfv_destroy", "dgfv_bank_entry", "dgfv_probe_dfma",
-           "dgfv_profile_enable", "dgfv_profile_read"]
+           "dgfv_profile_enable", "dgfv_profile_read", "dgfv_compute_dt_noalloc"]
 KERNELS = ["prolong", "fv", "face_lift", "dg_volume", "face_flux", "surface", "dt", "indicator", "remap"]
 
 
@@ -66,6 +66,7 @@ def lib():
             getattr(L, f).argtypes = [vp, vp, i64, vp]
         L.dgfv_eval_rhs.argtypes = [vp, vp, vp, vp]
         L.dgfv_compute_dt.argtypes = [vp, vp, dp, vp]
+        L.dgfv_compute_dt_noalloc.argtypes = [vp, vp, vp, vp]
         L.dgfv_rk_step.argtypes = [vp, C.c_double, dp, vp]
         L.dgfv_rk_steps.argtypes = [vp, C.c_int, C.c_double, dp, vp]
         L.dgfv_indicator.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -234,6 +235,14 @@ class Context:
         out = (C.c_double * 3)()
         self._rc(lib().dgfv_compute_dt(self.h, _ptr(U), out, _stream(stream)), "compute_dt")
         return tuple(out)
+
+    def compute_dt_noalloc(self, U, out3, stream=None):
+        """Time step into the caller's device tensor out3 (3 float64), through
+        the allocation-free entry point; does not synchronise."""
+        _check_dev(U, self.state_size)
+        _check_dev(out3, 3)
+        self._rc(lib().dgfv_compute_dt_noalloc(self.h, _ptr(U), _ptr(out3), _stream(stream)), "compute_dt_noalloc")
+        return out3
 
     def rk_step(self, dt=-1.0, want_dt=True, stream=None):
         out = C.c_double(0.0)
