@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--nel", type=int, default=48, help="elements per direction")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--profile-eval", action="store_true",
+                   help="after the warm-up cycles run one R(U) evaluation between cudaProfilerStart/Stop "
+                        "(for ncu --profile-from-start off) and exit")
     return p.parse_args()
 
 
@@ -61,7 +64,7 @@ def workload(nel):
 
 
 WORKLOAD_NAME = ("turbulent multi-component decay, 48^3 elements on [0,2pi]^3, N in 1..7 driven by the modal "
-                 "indicator from N=4, FV sub-cells N_FV=8, 3 species, viscous, LLF")
+                 "indicator from N=4 (thresholds 2.0/3.0/3.5/7.0), FV sub-cells N_FV=8, 3 species, viscous, LLF")
 
 
 def sample_problem(prob, nel_s, seed=5):
@@ -129,10 +132,10 @@ class ClockSampler:
 
 def flops_per_dof(prob):
     """Algorithmic flops per DOF-stage, total and per step of R(U), counted by
-    the oracle on a 10^3 sample with the same degree/FV distribution."""
+    the oracle on a 12^3 sample with the same degree/FV distribution."""
     import oracle
     from paper_2502_19342_gb300 import workloads as W
-    s, Us = sample_problem(prob, 10)
+    s, Us = sample_problem(prob, 12)
     f = oracle.count_flops(s, Us)
     dofs = W.n_dofs(s)
     per_step = {k: sum(v.values()) / dofs for k, v in f["steps"].items()}
@@ -225,6 +228,19 @@ def main():
     for _ in range(args.warmup):
         cycle(ctx)
     torch.cuda.synchronize()
+    if args.profile_eval:
+        Ud = ctx.get_state()
+        R = torch.empty_like(Ud)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        ctx.eval_rhs(Ud, R)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        N, fv = ctx.get_degrees()
+        print(json.dumps({"profile_eval": True, "elements": ctx.n_elem, "dofs": int(W.n_dofs(dict(prob, N=N, fv=fv))),
+                          "fv_elements": int(fv.sum()), "degree_histogram": np.bincount(N[fv == 0], minlength=8).tolist()}))
+        ctx.close()
+        return
 
     def barrier():
         if dist:
@@ -283,8 +299,9 @@ def main():
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)}
 
     if rank == 0:
-        # roofline of the dominant kernel
-        per_dof, per_step = flops_per_dof(prob)
+        # roofline of the dominant kernel, with flops per DOF of the pattern the timed steps ran on
+        N_now, fv_now = ctx.get_degrees()
+        per_dof, per_step = flops_per_dof(dict(prob, N=N_now, fv=fv_now))
         main_k = max((k for k in KERNEL_STEP if prof[k][1] > 0), key=lambda k: prof[k][0])
         kms, kl = prof[main_k]
         dofs_per_launch = units / (args.steps * STEPS_PER_CYCLE * STAGES_PER_STEP)
@@ -296,7 +313,7 @@ def main():
                 "dfma_probe_tflops": probe,
                 "flops_per_dof": {"total": per_dof, main_k: per_step[KERNEL_STEP[main_k]]},
                 "whole_rhs_tflops": per_dof * units / (ms * 1e-3) / 1e12}
-        cpu = None if args.no_cpu else cpu_baseline(prob)
+        cpu = None if args.no_cpu else cpu_baseline(dict(prob, N=N_now, fv=fv_now))
         launches = int(sum(v[1] for v in prof.values()))
         last = pattern[-1]
         line = {"metric": "DOF-stage updates/s (FP64 RHS, hp-mixed)", "value": value, "unit": "DOF-stage/s",

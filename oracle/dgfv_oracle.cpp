@@ -485,9 +485,11 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
             for (int dv = 0; dv < 3 * V; ++dv) gc[dv] = g[(size_t)dv * n3 + c];
             Prim<T> s;
             cons_to_prim(P.ph, uc, s);
+            PrimGrad<T> G;
+            prim_grad(P.ph, gc, s, G);  // one chain rule per node, shared by the three directions
             for (int d = 0; d < 3; ++d) {
                 flux_conv(P.ph, uc, s, d, Fc);
-                flux_visc(P.ph, uc, gc, s, d, Fv);
+                flux_visc(P.ph, G, s, d, Fv);
                 for (int v = 0; v < V; ++v) F[((size_t)d * V + v) * n3 + c] = Fc[v] + Fv[v];
             }
         }

@@ -71,54 +71,71 @@ void flux_conv(const Phys& P, const T* u, const Prim<T>& s, int d, T* F) {
     F[nk + 3] = (u[nk + 3] + s.p) * s.v[d];
 }
 
-// Viscous flux in direction d from the state u and its physical gradient
-// g[dd*V + v] = d u_v / d x_dd (the BR1 lifting variable, Eq. 14b).
-// The primitive gradients follow by the chain rule:
+// Primitive gradients from the state's physical gradient g[dd*V + v] =
+// d u_v / d x_dd (the BR1 lifting variable, Eq. 14b), by the chain rule:
 //   grad Y_k = (grad rho_k - Y_k grad rho)/rho,  grad v = (grad(rho v) - v grad rho)/rho,
 //   grad eps = (grad(rho E) - E grad rho)/rho - sum_i v_i grad v_i,
 //   grad T = (grad eps - T grad c_v,mix)/c_v,mix,  grad c_v,mix = sum_k c_v,k grad Y_k.
+template <class T>
+struct PrimGrad {
+    T Y[MAXSP][3], v[3][3], temp[3];
+};
+
+template <class T>
+void prim_grad(const Phys& P, const T* g, const Prim<T>& s, PrimGrad<T>& G) {
+    const int nk = P.nk, V = P.V();
+    for (int dd = 0; dd < 3; ++dd) {
+        const T* gd = g + dd * V;
+        T gr = gd[0];
+        for (int k = 1; k < nk; ++k) gr = gr + gd[k];
+        for (int k = 0; k < nk; ++k) G.Y[k][dd] = (gd[k] - s.Y[k] * gr) / s.rho;
+        for (int i = 0; i < 3; ++i) G.v[i][dd] = (gd[nk + i] - s.v[i] * gr) / s.rho;
+        T geps = (gd[nk + 3] - s.E * gr) / s.rho;
+        for (int i = 0; i < 3; ++i) geps = geps - s.v[i] * G.v[i][dd];
+        T gcv = T(P.cv[0]) * G.Y[0][dd];
+        for (int k = 1; k < nk; ++k) gcv = gcv + T(P.cv[k]) * G.Y[k][dd];
+        G.temp[dd] = (geps - s.temp * gcv) / s.cv;
+    }
+}
+
+// Viscous flux in direction d from the primitive gradients.
 // Transport (Eqs. 4a-4c, 5):
 //   tau = mu (grad v + grad v^T - 2/3 div v I),  q_h = -lambda grad T,
 //   J_k = -rho D_k grad Y_k + rho Y_k sum_j D_j grad Y_j   (the sign and range of
 //         the correction sum chosen so that sum_k J_k = 0, as Sec. 2 requires),
 //   q_d = sum_k h_k J_k with h_k = c_p,k T.
 template <class T>
-void flux_visc(const Phys& P, const T* u, const T* g, const Prim<T>& s, int d, T* F) {
-    const int nk = P.nk, V = P.V();
-    (void)u;
-    T gY[MAXSP][3], gv[3][3], gT[3];
-    for (int dd = 0; dd < 3; ++dd) {
-        const T* gd = g + dd * V;
-        T gr = gd[0];
-        for (int k = 1; k < nk; ++k) gr = gr + gd[k];
-        for (int k = 0; k < nk; ++k) gY[k][dd] = (gd[k] - s.Y[k] * gr) / s.rho;
-        for (int i = 0; i < 3; ++i) gv[i][dd] = (gd[nk + i] - s.v[i] * gr) / s.rho;
-        T geps = (gd[nk + 3] - s.E * gr) / s.rho;
-        for (int i = 0; i < 3; ++i) geps = geps - s.v[i] * gv[i][dd];
-        T gcv = T(P.cv[0]) * gY[0][dd];
-        for (int k = 1; k < nk; ++k) gcv = gcv + T(P.cv[k]) * gY[k][dd];
-        gT[dd] = (geps - s.temp * gcv) / s.cv;
-    }
-    T divv = gv[0][0] + gv[1][1] + gv[2][2];
+void flux_visc(const Phys& P, const PrimGrad<T>& G, const Prim<T>& s, int d, T* F) {
+    const int nk = P.nk;
+    T divv = G.v[0][0] + G.v[1][1] + G.v[2][2];
     // row d of the stress tensor: tau_{d i}
     T tau[3];
     for (int i = 0; i < 3; ++i) {
-        tau[i] = s.mu * (gv[d][i] + gv[i][d]);
+        tau[i] = s.mu * (G.v[d][i] + G.v[i][d]);
         if (i == d) tau[i] = tau[i] - s.mu * T(2.0 / 3.0) * divv;
     }
     // species diffusion fluxes in direction d
-    T corr = T(P.D[0]) * gY[0][d];
-    for (int k = 1; k < nk; ++k) corr = corr + T(P.D[k]) * gY[k][d];
+    T corr = T(P.D[0]) * G.Y[0][d];
+    for (int k = 1; k < nk; ++k) corr = corr + T(P.D[k]) * G.Y[k][d];
     T J[MAXSP] = {T(0.0), T(0.0), T(0.0)};
     for (int k = 0; k < nk; ++k)
-        J[k] = -(s.rho * T(P.D[k]) * gY[k][d]) + s.rho * s.Y[k] * corr;
-    T qh = -(s.lam * gT[d]);
+        J[k] = -(s.rho * T(P.D[k]) * G.Y[k][d]) + s.rho * s.Y[k] * corr;
+    T qh = -(s.lam * G.temp[d]);
     T qd = T(P.cp[0]) * s.temp * J[0];
     for (int k = 1; k < nk; ++k) qd = qd + T(P.cp[k]) * s.temp * J[k];
     for (int k = 0; k < nk; ++k) F[k] = J[k];
     for (int i = 0; i < 3; ++i) F[nk + i] = -tau[i];
     T tv = tau[0] * s.v[0] + tau[1] * s.v[1] + tau[2] * s.v[2];
     F[nk + 3] = -tv + qh + qd;
+}
+
+// Viscous flux in direction d from the state's physical gradient g.
+template <class T>
+void flux_visc(const Phys& P, const T* u, const T* g, const Prim<T>& s, int d, T* F) {
+    (void)u;
+    PrimGrad<T> G;
+    prim_grad(P, g, s, G);
+    flux_visc(P, G, s, d, F);
 }
 
 // Local Lax-Friedrichs (Rusanov) flux in direction d (used in Sec. 5 at FV

@@ -35,6 +35,15 @@ struct FaceList {
     int count = 0;
 };
 
+struct FaceTileSet {
+    std::vector<int32_t> first, count, items;
+    std::vector<uint8_t> nc, d;
+    int32_t *d_first = nullptr, *d_count = nullptr, *d_items = nullptr;
+    uint8_t *d_nc = nullptr, *d_d = nullptr;
+    int ntiles = 0;
+    FaceTiles view() const { return FaceTiles{d_first, d_count, d_nc, d_d, d_items}; }
+};
+
 enum Kernel { K_PROLONG = 0, K_FV, K_LIFT, K_VOLUME, K_FLUX, K_SURFACE, K_DT, K_INDICATOR, K_REMAP, K_COUNT };
 
 struct Profiler {
@@ -80,7 +89,8 @@ struct dgfv_ctx {
     uint8_t* d_dec = nullptr;
     int* d_status = nullptr;
     TileSet all, dg, fvt;
-    FaceList lift, flux;
+    FaceList lift, flux;    // flux: faces that change representation
+    FaceTileSet conf;       // faces with one representation on both sides
     int n_fv_elems = 0;
     bool state_valid = false;
     std::string err;
@@ -250,12 +260,44 @@ int apply_layout(dgfv_ctx* c) {
     TRY(upload_tiles(c, c->all));
     TRY(upload_tiles(c, c->dg));
     TRY(upload_tiles(c, c->fvt));
-    // face lists: lifting needs a DG side; every face has a flux
+    // face lists: lifting needs a DG side; the flux of a face whose sides share
+    // one representation runs in the conforming kernel, the rest in the mixed one
     c->lift.ids.clear();
     c->flux.ids.clear();
+    std::vector<int32_t> conf_by[3][MAXP + 1];
     for (int f = 0; f < c->n_faces; ++f) {
-        c->flux.ids.push_back(f);
-        if (!(c->fv[c->faceL[f]] && c->fv[c->faceR[f]])) c->lift.ids.push_back(f);
+        const int L = c->faceL[f], R = c->faceR[f];
+        const bool same = (c->fv[L] && c->fv[R]) || (!c->fv[L] && !c->fv[R] && c->npts[L] == c->npts[R]);
+        if (same)
+            conf_by[c->faceD[f]][c->npts[L]].push_back(f);
+        else
+            c->flux.ids.push_back(f);
+        if (!(c->fv[L] && c->fv[R])) c->lift.ids.push_back(f);
+    }
+    {
+        FaceTileSet& t = c->conf;
+        t.first.clear(); t.count.clear(); t.items.clear(); t.nc.clear(); t.d.clear();
+        for (int d = 0; d < 3; ++d)
+            for (int n = 1; n <= MAXP; ++n) {
+                const auto& g = conf_by[d][n];
+                const int per = std::max(1, 256 / (n * n));
+                for (size_t s0 = 0; s0 < g.size(); s0 += per) {
+                    const int cnt = (int)std::min<size_t>(per, g.size() - s0);
+                    t.first.push_back((int32_t)t.items.size());
+                    t.count.push_back(cnt);
+                    t.nc.push_back((uint8_t)n);
+                    t.d.push_back((uint8_t)d);
+                    t.items.insert(t.items.end(), g.begin() + s0, g.begin() + s0 + cnt);
+                }
+            }
+        t.ntiles = (int)t.first.size();
+        if (t.ntiles) {
+            CK(cudaMemcpy(t.d_first, t.first.data(), t.ntiles * sizeof(int32_t), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(t.d_count, t.count.data(), t.ntiles * sizeof(int32_t), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(t.d_nc, t.nc.data(), t.ntiles, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(t.d_d, t.d.data(), t.ntiles, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(t.d_items, t.items.data(), t.items.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        }
     }
     c->lift.count = (int)c->lift.ids.size();
     c->flux.count = (int)c->flux.ids.size();
@@ -285,7 +327,11 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
     if (c->n_fv_elems) { Timed t(c, K_FV, s); launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, Uin, s); }
     if (c->ph.viscous) { Timed t(c, K_LIFT, s); launch_face_lift(c->nk, P, F, c->lift.d, c->lift.count, s); }
     if (c->dg.ntiles) { Timed t(c, K_VOLUME, s); launch_dg_volume(c->nk, P, c->dg.view(), c->dg.ntiles, c->dg.smem, Uin, s); }
-    { Timed t(c, K_FLUX, s); launch_face_flux(c->nk, P, F, c->flux.d, c->flux.count, s); }
+    {
+        Timed t(c, K_FLUX, s);
+        launch_face_flux_conf(c->nk, P, F, c->conf.view(), c->conf.ntiles, s);
+        launch_face_flux(c->nk, P, F, c->flux.d, c->flux.count, s);
+    }
     { Timed t(c, K_SURFACE, s); launch_surface(c->nk, P, c->all.view(), c->all.ntiles, Uin, U0, out, mode, a, b, c->d_dt3, s); }
 }
 
@@ -471,6 +517,8 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     A_(c->d_rtmp, c->cap_state) A_(c->d_U, c->cap_state) A_(c->d_Us, c->cap_state)
     A_(c->d_dt3, 4) A_(c->d_partial, 2 * ne + 2) A_(c->d_Ip, ne) A_(c->d_Ih, ne) A_(c->d_dec, ne)
     A_(c->d_status, 1) A_(c->lift.d, c->n_faces) A_(c->flux.d, c->n_faces)
+    A_(c->conf.d_first, c->n_faces) A_(c->conf.d_count, c->n_faces) A_(c->conf.d_nc, c->n_faces)
+    A_(c->conf.d_d, c->n_faces) A_(c->conf.d_items, c->n_faces)
 #undef A_
     if ((r = alloc_tiles(c, c->all)) != DGFV_OK) return cleanup(r);
     if ((r = alloc_tiles(c, c->dg)) != DGFV_OK) return cleanup(r);

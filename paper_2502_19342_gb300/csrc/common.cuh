@@ -67,6 +67,16 @@ struct Tiles {
     const int32_t* items;
 };
 
+// Tiles of faces that need no change of representation: every face of a tile
+// has the same direction d and the same number of points per direction nc.
+struct FaceTiles {
+    const int32_t* first;
+    const int32_t* count;
+    const uint8_t* nc;
+    const uint8_t* d;
+    const int32_t* items;  // face ids
+};
+
 // Faces: lower element L (across its +d face) and upper element R (its -d face).
 struct Faces {
     const int32_t* L;

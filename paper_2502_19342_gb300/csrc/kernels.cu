@@ -413,19 +413,84 @@ __global__ void __launch_bounds__(256) k_dg_volume(Params P, Tiles T, const doub
 }
 
 // ---------------------------------------------------------------------------------
-// k_face_flux: one CTA per face.  Common representation: N_FV sub-cells if either
-// side is FV, else the higher degree (Sec. 3.2.1, 3.2.2).
+// Face fluxes.  F* = F^c*(uL,uR) + (F^v(uL,gL) + F^v(uR,gR))/2 in +x_d, written as
+// the outward flux of both sides (+F for the lower element, -F for the upper).
+//
+// k_face_flux_conf: faces whose two sides share one representation (equal DG
+// degree, or FV on both sides); one thread per face point, operands straight
+// from the face buffers, the direction a compile-time constant.
+template <int NK, int D>
+__device__ __forceinline__ void conf_face_body(const Params& P, const Faces& Fc, const int32_t* __restrict__ items,
+                                               int first, int count, int nc) {
+    constexpr int V = NK + 4;
+    const int nc2 = nc * nc;
+    const bool visc = P.ph.viscous;
+    for (int t = threadIdx.x; t < count * nc2; t += blockDim.x) {
+        const int fid = items[first + t / nc2], p = t % nc2;
+        const int eL = Fc.L[fid], eR = Fc.R[fid];
+        const int64_t sL = P.t.fo[eL] + (int64_t)(2 * D + 1) * nc2;
+        const int64_t sR = P.t.fo[eR] + (int64_t)(2 * D) * nc2;
+        const double* uLs = (P.t.fv[eL] ? P.b.frec : P.b.fu) + sL * V + p;
+        const double* uRs = (P.t.fv[eR] ? P.b.frec : P.b.fu) + sR * V + p;
+        double uL[V], uR[V], gL[3 * V], gR[3 * V], F[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            uL[v] = uLs[v * nc2];
+            uR[v] = uRs[v * nc2];
+        }
+        if (visc) {
+            const double* gLs = P.b.fg + sL * 3 * V + p;
+            const double* gRs = P.b.fg + sR * 3 * V + p;
+#pragma unroll
+            for (int x = 0; x < 3 * V; ++x) {
+                gL[x] = gLs[x * nc2];
+                gR[x] = gRs[x * nc2];
+            }
+        }
+        interface_flux<NK>(P.ph, uL, gL, uR, gR, D, F);
+        double* dL = P.b.flux + sL * V + p;
+        double* dR = P.b.flux + sR * V + p;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            dL[v * nc2] = F[v];
+            dR[v * nc2] = -F[v];
+        }
+    }
+}
+
 template <int NK>
-__global__ void __launch_bounds__(64) k_face_flux(Params P, Faces Fc, const int32_t* __restrict__ list) {
-    constexpr int V = NK + 4, W = 4 * V, PP = MAXP * MAXP;
-    __shared__ double sU[2][V * PP];
-    __shared__ double sG[2][3 * V * PP];
-    __shared__ double sF[V * PP];
-    __shared__ double sT[W * PP];
-    const int fid = list[blockIdx.x];
-    const int eL = Fc.L[fid], eR = Fc.R[fid], d = Fc.d[fid];
+__global__ void __launch_bounds__(128) k_face_flux_conf(Params P, Faces Fc, FaceTiles T) {
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], nc = T.nc[blockIdx.x];
+    switch (T.d[blockIdx.x]) {
+        case 0: conf_face_body<NK, 0>(P, Fc, T.items, first, count, nc); break;
+        case 1: conf_face_body<NK, 1>(P, Fc, T.items, first, count, nc); break;
+        default: conf_face_body<NK, 2>(P, Fc, T.items, first, count, nc); break;
+    }
+}
+
+// k_face_flux: faces that change representation (unequal DG degrees, or DG/FV),
+// one CTA per face.  Common representation: N_FV sub-cells if either side is
+// FV, else the higher degree (Sec. 3.2.1, 3.2.2); the lower side's u and g are
+// mapped to it in shared memory, the flux is mapped back (L2 projection or
+// V^{FV->DG}).
+template <int NK>
+struct MixedFaceSmem {
+    static constexpr int V = NK + 4, PP = MAXP * MAXP;
+    double U[2][V * PP];
+    double G[2][3 * V * PP];
+    double F[V * PP];
+    double T[4 * V * PP];
+};
+
+template <int NK, int D>
+__device__ __forceinline__ void mixed_face_body(const Params& P, int eL, int eR, MixedFaceSmem<NK>& S) {
+    constexpr int V = NK + 4;
+    auto& sU = S.U;
+    auto& sG = S.G;
+    double* sF = S.F;
+    double* sT = S.T;
     const int es[2] = {eL, eR};
-    const int fs[2] = {2 * d + 1, 2 * d};
+    const int fs[2] = {2 * D + 1, 2 * D};
     const bool common_fv = P.t.fv[eL] || P.t.fv[eR];
     const int nc = common_fv ? P.nfv : max((int)P.t.n[eL], (int)P.t.n[eR]);
     const int nc2 = nc * nc;
@@ -442,13 +507,11 @@ __global__ void __launch_bounds__(64) k_face_flux(Params P, Faces Fc, const int3
                 for (int i = threadIdx.x; i < 3 * V * nc2; i += blockDim.x) sG[side][i] = sg[i];
         } else {
             const double* M = B(P, common_fv ? P.bi.d2f[n] : P.bi.vm[n][nc]);
-            // stage the raw trace in sF/sT-sized scratch: use sG[side] as input staging
-            double* raw = sG[side];
+            double* raw = sG[side];  // staging of the raw trace
             for (int i = threadIdx.x; i < V * n2; i += blockDim.x) raw[i] = su[i];
             __syncthreads();
             face_map(raw, n, sU[side], nc, M, V, sT);
             if (visc) {
-                // gradient: stage in sF-sized chunks of V variables at a time
                 for (int part = 0; part < 3; ++part) {
                     for (int i = threadIdx.x; i < V * n2; i += blockDim.x) sF[i] = sg[part * V * n2 + i];
                     __syncthreads();
@@ -472,7 +535,7 @@ __global__ void __launch_bounds__(64) k_face_flux(Params P, Faces Fc, const int3
                 gR[x] = sG[1][x * nc2 + p];
             }
         }
-        interface_flux<NK>(P.ph, uL, gL, uR, gR, d, F);
+        interface_flux<NK>(P.ph, uL, gL, uR, gR, D, F);
 #pragma unroll
         for (int v = 0; v < V; ++v) sF[v * nc2 + p] = F[v];
     }
@@ -490,6 +553,18 @@ __global__ void __launch_bounds__(64) k_face_flux(Params P, Faces Fc, const int3
             face_map(sF, nc, sU[side], n, M, V, sT);
             for (int i = threadIdx.x; i < V * n2; i += blockDim.x) dst[i] = sgn * sU[side][i];
         }
+    }
+}
+
+template <int NK>
+__global__ void __launch_bounds__(64) k_face_flux(Params P, Faces Fc, const int32_t* __restrict__ list) {
+    __shared__ MixedFaceSmem<NK> S;
+    const int fid = list[blockIdx.x];
+    const int eL = Fc.L[fid], eR = Fc.R[fid];
+    switch (Fc.d[fid]) {
+        case 0: mixed_face_body<NK, 0>(P, eL, eR, S); break;
+        case 1: mixed_face_body<NK, 1>(P, eL, eR, S); break;
+        default: mixed_face_body<NK, 2>(P, eL, eR, S); break;
     }
 }
 
@@ -873,6 +948,11 @@ void launch_dg_volume(int nk, const Params& P, const Tiles& T, int ntiles, size_
 void launch_face_flux(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s) {
     if (nfaces <= 0) return;
     DGFV_DISPATCH(nk, (k_face_flux<NK><<<nfaces, 64, 0, s>>>(P, F, list)));
+}
+
+void launch_face_flux_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    DGFV_DISPATCH(nk, (k_face_flux_conf<NK><<<ntiles, 128, 0, s>>>(P, F, T)));
 }
 
 void launch_surface(int nk, const Params& P, const Tiles& T, int ntiles, const double* Uin, const double* U0,

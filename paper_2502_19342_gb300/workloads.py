@@ -306,12 +306,13 @@ def _fourier_on_mesh(prob, k1, c, L, chunk=4096):
     return out
 
 
-def turbulence(seed=0, nel=(48, 48, 48), riemann=0, mu=5e-4, Mt=0.3, k0=4.0, kmax=8, N0=None):
+def turbulence(seed=0, nel=(48, 48, 48), riemann=0, mu=5e-4, Mt=0.3, k0=4.0, kmax=8, N0=None, y_bg=0.05):
     """Periodic [0,2pi]^3, 48^3 elements, N drawn from {1..7}, 3 species
     (gamma 1.4/1.3/1.67, M 29/44/4), N_FV = 8.  Random-phase solenoidal
     velocity with E(k) ~ k^4 exp(-2 (k/k0)^2), k0 = 4, scaled to turbulent Mach
     0.3; species blobs from thresholded Gaussian random fields smoothed by tanh
-    over about 2 node spacings; p = 1 and uniform temperature."""
+    over about 2 node spacings, on a background mass fraction y_bg of every
+    species; p = 1 and uniform temperature."""
     sp = species_set([AIR, CO2, HELIUM], mu=mu)
     n_elem = nel[0] * nel[1] * nel[2]
     # N0 = None: degrees drawn from {1..7}; an integer: that degree everywhere
@@ -337,8 +338,8 @@ def turbulence(seed=0, nel=(48, 48, 48), riemann=0, mu=5e-4, Mt=0.3, k0=4.0, kma
     g2 = _fourier_on_mesh(prob, kb, cb2, L)[0] / s2
     b1 = 0.5 * (1 + np.tanh(g1 / width))
     b2 = 0.5 * (1 + np.tanh(g2 / width))
-    Y2 = 0.6 * b1 * (1 - b2)
-    Y3 = 0.6 * b2
+    Y2 = y_bg + (0.6 - y_bg) * b1 * (1 - b2)
+    Y3 = y_bg + (0.6 - y_bg) * b2
     Y1 = 1.0 - Y2 - Y3
     Rg = sp["Rgas"]
     rho = 1.0 / ((Y1 * Rg[0] + Y2 * Rg[1] + Y3 * Rg[2]) * T0)
@@ -375,4 +376,4 @@ def _assemble(prob, pts):
 
 
 # Indicator thresholds {T_fv_on, T_fv_off, T_ref, T_crs} (configuration values).
-THRESHOLDS = (1.0, 1.6, 3.0, 5.0)
+THRESHOLDS = (2.0, 3.0, 3.5, 7.0)
