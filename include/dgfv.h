@@ -165,6 +165,23 @@ int dgfv_rk_step(dgfv_ctx* ctx, double dt, double* dt_used, void* stream);
  * replayed; same dt semantics as dgfv_rk_step (dt_used = last step). */
 int dgfv_rk_steps(dgfv_ctx* ctx, int n_steps, double dt, double* dt_used, void* stream);
 
+/* Adjoint (vector-Jacobian product) of the right-hand side:
+ * d_Ubar = (dR/dU)^T d_Rbar at the state d_U, with the degree pattern frozen.
+ * Supported for patterns without FV elements and the local Lax-Friedrichs
+ * flux (DGFV_ERR_ARG otherwise).  Device arrays in the current layout;
+ * d_Ubar must not alias d_U or d_Rbar.  Uses the context's forward face
+ * buffers (a later eval_rhs recomputes them).  The first adjoint call
+ * allocates the adjoint scratch (face adjoints and four state buffers). */
+int dgfv_rhs_vjp(dgfv_ctx* ctx, const double* d_U, const double* d_Rbar, double* d_Ubar, void* stream);
+
+/* Adjoint of one SSP-RK3 step of size dt from the state d_U0:
+ * d_Ubar = (dU1/dU0)^T d_Ubar_next.  The two intermediate stage states are
+ * recomputed from d_U0 (stage checkpointing: a caller stores only the state
+ * at the start of every step).  Same restrictions as dgfv_rhs_vjp; d_Ubar
+ * must not alias the inputs. */
+int dgfv_rk_step_vjp(dgfv_ctx* ctx, const double* d_U0, double dt, const double* d_Ubar_next, double* d_Ubar,
+                     void* stream);
+
 /* Modal indicator of Sec. 3.4 on the state d_U: per element I_p = I(rho),
  * I_h = min(I(p), I(Y_k)) (device arrays of n_elem doubles, may be NULL) and
  * the decision code (device array of n_elem bytes, may be NULL):

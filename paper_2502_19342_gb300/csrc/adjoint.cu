@@ -1,0 +1,471 @@
+// Adjoint (vector-Jacobian product) of R(U) for DG elements with the local
+// Lax-Friedrichs flux: U_bar = (dR/dU)^T R_bar.
+//
+// The forward evaluation is a chain of linear maps (face traces, BR1 lifting,
+// tensor-product maps between degrees, volume and surface integrals) and two
+// pointwise nonlinear functions (nodal fluxes, interface fluxes).  The adjoint
+// runs the chain backwards: every linear map is applied transposed and the
+// pointwise functions through their hand-written reverse mode
+// (physics_adj.cuh).  It needs the forward face values u(+-1), the lifting
+// values U* and the gradient traces g(+-1) of the same U (the caller runs the
+// forward face, lifting and volume kernels first).
+//
+//   k_adj_surface    R_bar -> adjoint of the outward face fluxes        (Eq. 22 surface term)^T
+//   k_adj_face_conf  face-flux adjoint, conforming faces               (Eqs. 20, 21)^T
+//   k_adj_face_mixed face-flux adjoint, unequal degrees, with the
+//                    transposed interpolation / projection maps         (Sec. 3.2.1)^T
+//   k_adj_volume     volume integral^T, nodal-flux adjoint, gradient
+//                    trace^T, lifting^T -> U_bar (part), U*_bar          (Eqs. 22, 23)^T
+//   k_adj_lift       lifting value^T (mean on the lower degree)         (Eq. 19, Sec. 3.2.2)^T
+//   k_adj_prolong    face trace^T -> U_bar (rest)
+#include <cuda_runtime.h>
+
+#include "adjoint.h"
+#include "common.cuh"
+#include "device_util.cuh"
+#include "physics_adj.cuh"
+
+namespace dgfv {
+
+// k_adj_surface: F*_bar on each face slot of a DG element.  The forward adds
+// rh_d * lhat^{+-}_i F*_{+-d}[p] to -R at node (i along d, p).
+template <int NK>
+__global__ void __launch_bounds__(256) k_adj_surface(Params P, AdjBuffers A, Tiles T, const double* __restrict__ Rb) {
+    constexpr int V = NK + 4;
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
+    const int n2 = n * n, n3 = n2 * n, per = 6 * V * n2;
+    for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
+        const int el = idx / per, r = idx % per, f = r / (V * n2), r2 = r % (V * n2), v = r2 / n2, p = r2 % n2;
+        const int e = T.items[first + el];
+        const int d = f >> 1, a = p % n, b = p / n;
+        const double* lh = B(P, (f & 1) ? P.bi.lhp[n] : P.bi.lhm[n]);
+        const double* src = Rb + P.t.off[e] + (int64_t)v * n3;
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s = fma(__ldg(lh + i), src[node_index(n, d, i, a, b)], s);
+        A.fbar[(P.t.fo[e] + (int64_t)f * n2) * V + v * n2 + p] = -P.t.rh[3 * e + d] * s;
+    }
+}
+
+// k_adj_face_conf: faces with equal degree on both sides, one thread per point.
+template <int NK, int D>
+__device__ __forceinline__ void adj_conf_body(const Params& P, const AdjBuffers& A, const Faces& Fc,
+                                              const int32_t* __restrict__ items, int first, int count, int nc) {
+    constexpr int V = NK + 4;
+    const int nc2 = nc * nc;
+    for (int t = threadIdx.x; t < count * nc2; t += blockDim.x) {
+        const int fid = items[first + t / nc2], p = t % nc2;
+        const int eL = Fc.L[fid], eR = Fc.R[fid];
+        const int64_t sL = P.t.fo[eL] + (int64_t)(2 * D + 1) * nc2;
+        const int64_t sR = P.t.fo[eR] + (int64_t)(2 * D) * nc2;
+        double uL[V], uR[V], gL[3 * V], gR[3 * V], Fb[V];
+        double uLb[V] = {}, uRb[V] = {}, gLb[3 * V] = {}, gRb[3 * V] = {};
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            uL[v] = P.b.fu[sL * V + v * nc2 + p];
+            uR[v] = P.b.fu[sR * V + v * nc2 + p];
+            // L's slot holds +F, R's slot -F
+            Fb[v] = A.fbar[sL * V + v * nc2 + p] - A.fbar[sR * V + v * nc2 + p];
+        }
+        if (P.ph.viscous) {
+#pragma unroll
+            for (int x = 0; x < 3 * V; ++x) {
+                gL[x] = P.b.fg[sL * 3 * V + x * nc2 + p];
+                gR[x] = P.b.fg[sR * 3 * V + x * nc2 + p];
+            }
+        }
+        face_point_rev<NK>(P.ph, uL, gL, uR, gR, D, Fb, uLb, gLb, uRb, gRb);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            A.ubar[sL * V + v * nc2 + p] = uLb[v];
+            A.ubar[sR * V + v * nc2 + p] = uRb[v];
+        }
+#pragma unroll
+        for (int x = 0; x < 3 * V; ++x) {
+            A.gbar[sL * 3 * V + x * nc2 + p] = gLb[x];
+            A.gbar[sR * 3 * V + x * nc2 + p] = gRb[x];
+        }
+    }
+}
+
+template <int NK>
+__global__ void __launch_bounds__(128) k_adj_face_conf(Params P, AdjBuffers A, Faces Fc, FaceTiles T) {
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], nc = T.nc[blockIdx.x];
+    switch (T.d[blockIdx.x]) {
+        case 0: adj_conf_body<NK, 0>(P, A, Fc, T.items, first, count, nc); break;
+        case 1: adj_conf_body<NK, 1>(P, A, Fc, T.items, first, count, nc); break;
+        default: adj_conf_body<NK, 2>(P, A, Fc, T.items, first, count, nc); break;
+    }
+}
+
+// k_adj_face_mixed: unequal DG degrees, one CTA per face.  Forward: the lower
+// side's u and g traces are interpolated to the higher degree M, the flux is
+// computed there and L2-projected back to the lower side.  Adjoint: project^T
+// the lower side's flux adjoint, combine, reverse the point flux on M points,
+// interpolate^T the lower side's u/g adjoints.
+template <int NK>
+struct AdjMixedSmem {
+    static constexpr int V = NK + 4, PP = MAXP * MAXP;
+    double U[2][V * PP];
+    double G[2][3 * V * PP];
+    double F[V * PP];
+    double T[V * PP];      // scratch of one 2-pass map of V variables
+    double S[2 * V * PP];  // staging
+};
+
+template <int NK, int D>
+__device__ __forceinline__ void adj_mixed_body(const Params& P, const AdjBuffers& A, int eL, int eR,
+                                               AdjMixedSmem<NK>& S) {
+    constexpr int V = NK + 4;
+    const int es[2] = {eL, eR};
+    const int fs[2] = {2 * D + 1, 2 * D};
+    const int nc = max((int)P.t.n[eL], (int)P.t.n[eR]);
+    const int nc2 = nc * nc;
+    const bool visc = P.ph.viscous;
+    // forward states on the common degree
+    for (int side = 0; side < 2; ++side) {
+        const int e = es[side], n = P.t.n[e], n2 = n * n;
+        const int64_t slot = P.t.fo[e] + (int64_t)fs[side] * n2;
+        const double* su = P.b.fu + slot * V;
+        const double* sg = P.b.fg + slot * 3 * V;
+        if (n == nc) {
+            for (int i = threadIdx.x; i < V * nc2; i += blockDim.x) S.U[side][i] = su[i];
+            if (visc)
+                for (int i = threadIdx.x; i < 3 * V * nc2; i += blockDim.x) S.G[side][i] = sg[i];
+        } else {
+            const double* M = B(P, P.bi.vm[n][nc]);
+            for (int i = threadIdx.x; i < V * n2; i += blockDim.x) S.S[i] = su[i];
+            __syncthreads();
+            face_map(S.S, n, S.U[side], nc, M, V, S.T);
+            if (visc) {
+                for (int part = 0; part < 3; ++part) {
+                    for (int i = threadIdx.x; i < V * n2; i += blockDim.x) S.S[i] = sg[part * V * n2 + i];
+                    __syncthreads();
+                    face_map(S.S, n, S.G[side] + part * V * nc2, nc, M, V, S.T);
+                }
+            }
+        }
+    }
+    // flux adjoint on the common degree: F_bar = B_L^T fbar_L - B_R^T fbar_R
+    for (int i = threadIdx.x; i < V * nc2; i += blockDim.x) S.F[i] = 0.0;
+    __syncthreads();
+    for (int side = 0; side < 2; ++side) {
+        const int e = es[side], n = P.t.n[e], n2 = n * n;
+        const double sgn = side == 0 ? 1.0 : -1.0;
+        const double* fb = A.fbar + (P.t.fo[e] + (int64_t)fs[side] * n2) * V;
+        if (n == nc) {
+            for (int i = threadIdx.x; i < V * nc2; i += blockDim.x) S.F[i] += sgn * fb[i];
+            __syncthreads();
+        } else {
+            for (int i = threadIdx.x; i < V * n2; i += blockDim.x) S.S[i] = fb[i];
+            __syncthreads();
+            face_map_t(S.S, n, S.S + V * MAXP * MAXP, nc, B(P, P.bi.vm[nc][n]), V, S.T);  // projection^T
+            for (int i = threadIdx.x; i < V * nc2; i += blockDim.x) S.F[i] += sgn * S.S[V * MAXP * MAXP + i];
+            __syncthreads();
+        }
+    }
+    // reverse of the point flux; the adjoints overwrite the states in place
+    for (int p = threadIdx.x; p < nc2; p += blockDim.x) {
+        double uL[V], uR[V], gL[3 * V], gR[3 * V], Fb[V];
+        double uLb[V] = {}, uRb[V] = {}, gLb[3 * V] = {}, gRb[3 * V] = {};
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            uL[v] = S.U[0][v * nc2 + p];
+            uR[v] = S.U[1][v * nc2 + p];
+            Fb[v] = S.F[v * nc2 + p];
+        }
+        if (visc) {
+#pragma unroll
+            for (int x = 0; x < 3 * V; ++x) {
+                gL[x] = S.G[0][x * nc2 + p];
+                gR[x] = S.G[1][x * nc2 + p];
+            }
+        }
+        face_point_rev<NK>(P.ph, uL, gL, uR, gR, D, Fb, uLb, gLb, uRb, gRb);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            S.U[0][v * nc2 + p] = uLb[v];
+            S.U[1][v * nc2 + p] = uRb[v];
+        }
+#pragma unroll
+        for (int x = 0; x < 3 * V; ++x) {
+            S.G[0][x * nc2 + p] = visc ? gLb[x] : 0.0;
+            S.G[1][x * nc2 + p] = visc ? gRb[x] : 0.0;
+        }
+    }
+    __syncthreads();
+    // back to each side's degree (interpolation^T for the lower side)
+    for (int side = 0; side < 2; ++side) {
+        const int e = es[side], n = P.t.n[e], n2 = n * n;
+        const int64_t slot = P.t.fo[e] + (int64_t)fs[side] * n2;
+        double* ub = A.ubar + slot * V;
+        double* gb = A.gbar + slot * 3 * V;
+        if (n == nc) {
+            for (int i = threadIdx.x; i < V * nc2; i += blockDim.x) ub[i] = S.U[side][i];
+            for (int i = threadIdx.x; i < 3 * V * nc2; i += blockDim.x) gb[i] = S.G[side][i];
+        } else {
+            const double* M = B(P, P.bi.vm[n][nc]);
+            face_map_t(S.U[side], nc, S.S, n, M, V, S.T);
+            for (int i = threadIdx.x; i < V * n2; i += blockDim.x) ub[i] = S.S[i];
+            __syncthreads();
+            for (int part = 0; part < 3; ++part) {
+                face_map_t(S.G[side] + part * V * nc2, nc, S.S, n, M, V, S.T);
+                for (int i = threadIdx.x; i < V * n2; i += blockDim.x) gb[part * V * n2 + i] = S.S[i];
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int NK>
+__global__ void __launch_bounds__(64) k_adj_face_mixed(Params P, AdjBuffers A, Faces Fc, const int32_t* __restrict__ list) {
+    __shared__ AdjMixedSmem<NK> S;
+    const int fid = list[blockIdx.x];
+    switch (Fc.d[fid]) {
+        case 0: adj_mixed_body<NK, 0>(P, A, Fc.L[fid], Fc.R[fid], S); break;
+        case 1: adj_mixed_body<NK, 1>(P, A, Fc.L[fid], Fc.R[fid], S); break;
+        default: adj_mixed_body<NK, 2>(P, A, Fc.L[fid], Fc.R[fid], S); break;
+    }
+}
+
+// k_adj_volume: per tile of DG elements (shared memory 6V n^3 doubles per element).
+//   g (lifted gradient) is recomputed from U and U*;
+//   F_bar_d = -rh_d Dhat^T R_bar (volume integral^T);
+//   nodal-flux reverse -> U_bar (direct part), g_bar;
+//   g_bar += trace^T of the face gradient adjoints;
+//   lifting^T: U_bar += rh_d Dhat^T g_bar^d, U*_bar = +-rh_d lhat^{+-}^T g_bar^d.
+template <int NK>
+__global__ void __launch_bounds__(256) k_adj_volume(Params P, AdjBuffers A, Tiles T, const double* __restrict__ U,
+                                                    const double* __restrict__ Rb, double* __restrict__ Ub) {
+    constexpr int V = NK + 4;
+    extern __shared__ double sm[];
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
+    const int n2 = n * n, n3 = n2 * n;
+    double* sD = sm;
+    double* sl = sD + n * n;          // lm, lp, lhm, lhp
+    double* sG = sl + 4 * n;          // count * 3V n^3: g, then g_bar
+    double* sF = sG + count * 3 * V * n3;  // count * 3V n^3: F_bar
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) sD[i] = B(P, P.bi.dhat[n])[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        sl[i] = B(P, P.bi.lm[n])[i];
+        sl[n + i] = B(P, P.bi.lp[n])[i];
+        sl[2 * n + i] = B(P, P.bi.lhm[n])[i];
+        sl[3 * n + i] = B(P, P.bi.lhp[n])[i];
+    }
+    __syncthreads();
+    const bool visc = P.ph.viscous;
+    const int per = 3 * V * n3;
+    for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
+        const int el = idx / per, r = idx % per, d = r / (V * n3), r2 = r % (V * n3), v = r2 / n3, c = r2 % n3;
+        const int e = T.items[first + el];
+        const int i = c % n, j = (c / n) % n, k = c / n2;
+        const int m0 = d == 0 ? i : (d == 1 ? j : k);
+        const int a = d == 0 ? j : i, b = d == 2 ? j : k;
+        const int p = a + n * b;
+        const double rh = P.t.rh[3 * e + d];
+        // F_bar_d at node (m0 along d) = -rh sum_i Dhat[i][m0] R_bar[i along d]
+        const double* rsrc = Rb + P.t.off[e] + (int64_t)v * n3;
+        double fb = 0.0;
+        for (int q = 0; q < n; ++q) fb = fma(sD[q * n + m0], rsrc[node_index(n, d, q, a, b)], fb);
+        sF[el * per + r] = -rh * fb;
+        if (visc) {  // lifted gradient (forward recompute)
+            const double* src = U + P.t.off[e] + (int64_t)v * n3;
+            const int64_t fo = P.t.fo[e];
+            double s = 0.0;
+            for (int m = 0; m < n; ++m) s = fma(sD[m0 * n + m], src[node_index(n, d, m, a, b)], s);
+            s = fma(sl[3 * n + m0], P.b.flift[(fo + (int64_t)(2 * d + 1) * n2) * V + v * n2 + p], s);
+            s = fma(-sl[2 * n + m0], P.b.flift[(fo + (int64_t)(2 * d) * n2) * V + v * n2 + p], s);
+            sG[el * per + r] = rh * s;
+        }
+    }
+    __syncthreads();
+    // nodal reverse
+    for (int idx = threadIdx.x; idx < count * n3; idx += blockDim.x) {
+        const int el = idx / n3, c = idx % n3;
+        const int e = T.items[first + el];
+        double u[V], g[3 * V], Fb[3 * V], ub[V] = {}, gb[3 * V] = {};
+#pragma unroll
+        for (int v = 0; v < V; ++v) u[v] = U[P.t.off[e] + (int64_t)v * n3 + c];
+#pragma unroll
+        for (int x = 0; x < 3 * V; ++x) {
+            Fb[x] = sF[el * per + x * n3 + c];
+            g[x] = visc ? sG[el * per + x * n3 + c] : 0.0;
+        }
+        volume_point_rev<NK>(P.ph, u, g, Fb, ub, gb);
+#pragma unroll
+        for (int v = 0; v < V; ++v) Ub[P.t.off[e] + (int64_t)v * n3 + c] = ub[v];
+        if (visc)
+#pragma unroll
+            for (int x = 0; x < 3 * V; ++x) sG[el * per + x * n3 + c] = gb[x];
+    }
+    __syncthreads();
+    if (!visc) return;
+    // g_bar += trace^T of the face gradient adjoints (6 faces, 3V components)
+    for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
+        const int el = idx / per, r = idx % per, x = r / n3, c = r % n3;
+        const int e = T.items[first + el];
+        const int ijk[3] = {c % n, (c / n) % n, c / n2};
+        const int64_t fo = P.t.fo[e];
+        double acc = sG[el * per + r];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int m0 = ijk[d];
+            const int p = (d == 0 ? ijk[1] : ijk[0]) + n * (d == 2 ? ijk[1] : ijk[2]);
+            acc = fma(sl[m0], A.gbar[(fo + (int64_t)(2 * d) * n2) * 3 * V + x * n2 + p], acc);
+            acc = fma(sl[n + m0], A.gbar[(fo + (int64_t)(2 * d + 1) * n2) * 3 * V + x * n2 + p], acc);
+        }
+        sG[el * per + r] = acc;
+    }
+    __syncthreads();
+    // lifting^T into U_bar (a thread per (v, node): sum over d and the line)
+    const int pv = V * n3;
+    for (int idx = threadIdx.x; idx < count * pv; idx += blockDim.x) {
+        const int el = idx / pv, r = idx % pv, v = r / n3, c = r % n3;
+        const int e = T.items[first + el];
+        const int ijk[3] = {c % n, (c / n) % n, c / n2};
+        double acc = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int m0 = ijk[d];
+            const int a = d == 0 ? ijk[1] : ijk[0], b = d == 2 ? ijk[1] : ijk[2];
+            const double* gsrc = sG + el * per + (d * V + v) * n3;
+            double s = 0.0;
+            for (int i = 0; i < n; ++i) s = fma(sD[i * n + m0], gsrc[node_index(n, d, i, a, b)], s);
+            acc = fma(P.t.rh[3 * e + d], s, acc);
+        }
+        Ub[P.t.off[e] + r] += acc;
+    }
+    // U*_bar on the six faces
+    const int pf = 6 * V * n2;
+    for (int idx = threadIdx.x; idx < count * pf; idx += blockDim.x) {
+        const int el = idx / pf, r = idx % pf, f = r / (V * n2), r2 = r % (V * n2), v = r2 / n2, p = r2 % n2;
+        const int e = T.items[first + el];
+        const int d = f >> 1, a = p % n, b = p / n;
+        const double* lh = sl + ((f & 1) ? 3 * n : 2 * n);
+        const double* gsrc = sG + el * per + (d * V + v) * n3;
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s = fma(lh[i], gsrc[node_index(n, d, i, a, b)], s);
+        A.sbar[(P.t.fo[e] + (int64_t)f * n2) * V + v * n2 + p] = ((f & 1) ? 1.0 : -1.0) * P.t.rh[3 * e + d] * s;
+    }
+}
+
+// k_adj_lift: lifting value^T per face (both sides DG).  Forward on the lower
+// degree m: avg = (P_{nL->m} uL + P_{nR->m} uR)/2, U*_side = I_{m->n_side} avg.
+template <int NK>
+__global__ void __launch_bounds__(64) k_adj_lift(Params P, AdjBuffers A, Faces Fc, const int32_t* __restrict__ list) {
+    constexpr int V = NK + 4, PP = MAXP * MAXP;
+    __shared__ double sA[V * PP], sB[V * PP], sT[V * PP];
+    const int fid = list[blockIdx.x];
+    const int eL = Fc.L[fid], eR = Fc.R[fid], d = Fc.d[fid];
+    if (P.t.fv[eL] || P.t.fv[eR]) return;
+    const int nL = P.t.n[eL], nR = P.t.n[eR];
+    const int64_t sL = (P.t.fo[eL] + (int64_t)(2 * d + 1) * nL * nL) * V;
+    const int64_t sR = (P.t.fo[eR] + (int64_t)(2 * d) * nR * nR) * V;
+    if (nL == nR) {
+        for (int i = threadIdx.x; i < V * nL * nL; i += blockDim.x) {
+            const double a = 0.5 * (A.sbar[sL + i] + A.sbar[sR + i]);
+            A.ubar[sL + i] += a;
+            A.ubar[sR + i] += a;
+        }
+        return;
+    }
+    const bool lowL = nL < nR;
+    const int m = lowL ? nL : nR, M = lowL ? nR : nL;
+    const int64_t sLo = lowL ? sL : sR, sHi = lowL ? sR : sL;
+    // avg_bar = U*_bar_lo + I^T U*_bar_hi
+    for (int i = threadIdx.x; i < V * M * M; i += blockDim.x) sA[i] = A.sbar[sHi + i];
+    __syncthreads();
+    face_map_t(sA, M, sB, m, B(P, P.bi.vm[m][M]), V, sT);
+    for (int i = threadIdx.x; i < V * m * m; i += blockDim.x) {
+        const double a = 0.5 * (sB[i] + A.sbar[sLo + i]);
+        A.ubar[sLo + i] += a;
+        sB[i] = a;
+    }
+    __syncthreads();
+    face_map_t(sB, m, sA, M, B(P, P.bi.vm[M][m]), V, sT);  // projection^T
+    for (int i = threadIdx.x; i < V * M * M; i += blockDim.x) A.ubar[sHi + i] += sA[i];
+}
+
+// k_adj_prolong: U_bar += trace^T of the face-value adjoints.
+template <int NK>
+__global__ void __launch_bounds__(256) k_adj_prolong(Params P, AdjBuffers A, Tiles T, double* __restrict__ Ub) {
+    constexpr int V = NK + 4;
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
+    const int n2 = n * n, n3 = n2 * n, per = V * n3;
+    const double* lm = B(P, P.bi.lm[n]);
+    const double* lp = B(P, P.bi.lp[n]);
+    for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
+        const int el = idx / per, r = idx % per, v = r / n3, c = r % n3;
+        const int e = T.items[first + el];
+        const int ijk[3] = {c % n, (c / n) % n, c / n2};
+        const int64_t fo = P.t.fo[e];
+        double acc = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int m0 = ijk[d];
+            const int p = (d == 0 ? ijk[1] : ijk[0]) + n * (d == 2 ? ijk[1] : ijk[2]);
+            acc = fma(__ldg(lm + m0), A.ubar[(fo + (int64_t)(2 * d) * n2) * V + v * n2 + p], acc);
+            acc = fma(__ldg(lp + m0), A.ubar[(fo + (int64_t)(2 * d + 1) * n2) * V + v * n2 + p], acc);
+        }
+        Ub[P.t.off[e] + r] += acc;
+    }
+}
+
+// out = a*x + b*y (element-wise over n doubles)
+__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                        double* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = fma(a, x[i], b * y[i]);
+}
+
+// ================================================================= launchers
+#define DGFV_DISPATCH(nk, call)                          \
+    switch (nk) {                                        \
+        case 1: { constexpr int NK = 1; call; } break;   \
+        case 2: { constexpr int NK = 2; call; } break;   \
+        default: { constexpr int NK = 3; call; } break;  \
+    }
+
+void launch_adj_surface(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, const double* Rb,
+                        cudaStream_t s) {
+    if (ntiles <= 0) return;
+    DGFV_DISPATCH(nk, (k_adj_surface<NK><<<ntiles, 256, 0, s>>>(P, A, T, Rb)));
+}
+
+void launch_adj_faces(int nk, const Params& P, const AdjBuffers& A, const Faces& F, const FaceTiles& conf,
+                      int nconf, const int32_t* mixed, int nmixed, cudaStream_t s) {
+    if (nconf > 0) DGFV_DISPATCH(nk, (k_adj_face_conf<NK><<<nconf, 128, 0, s>>>(P, A, F, conf)));
+    if (nmixed > 0) DGFV_DISPATCH(nk, (k_adj_face_mixed<NK><<<nmixed, 64, 0, s>>>(P, A, F, mixed)));
+}
+
+size_t adj_volume_smem_bytes(int nk, int n, int count) {
+    const int V = nk + 4;
+    return sizeof(double) * (size_t)(n * n + 4 * n + 2 * count * 3 * V * n * n * n);
+}
+
+void launch_adj_volume(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, size_t smem,
+                       const double* U, const double* Rb, double* Ub, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_adj_volume<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       k_adj_volume<NK><<<ntiles, 256, smem, s>>>(P, A, T, U, Rb, Ub)));
+}
+
+void launch_adj_lift(int nk, const Params& P, const AdjBuffers& A, const Faces& F, const int32_t* list, int nfaces,
+                     cudaStream_t s) {
+    if (nfaces <= 0) return;
+    DGFV_DISPATCH(nk, (k_adj_lift<NK><<<nfaces, 64, 0, s>>>(P, A, F, list)));
+}
+
+void launch_adj_prolong(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, double* Ub,
+                        cudaStream_t s) {
+    if (ntiles <= 0) return;
+    DGFV_DISPATCH(nk, (k_adj_prolong<NK><<<ntiles, 256, 0, s>>>(P, A, T, Ub)));
+}
+
+void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s) {
+    if (n <= 0) return;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 32);
+    k_axpby<<<blocks, 256, 0, s>>>(n, a, x, b, y, out);
+}
+
+}  // namespace dgfv

@@ -1,0 +1,26 @@
+// Host-side launchers of the adjoint kernels in adjoint.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace dgfv {
+
+void launch_adj_surface(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, const double* Rb,
+                        cudaStream_t s);
+void launch_adj_faces(int nk, const Params& P, const AdjBuffers& A, const Faces& F, const FaceTiles& conf,
+                      int nconf, const int32_t* mixed, int nmixed, cudaStream_t s);
+size_t adj_volume_smem_bytes(int nk, int n, int count);
+void launch_adj_volume(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, size_t smem,
+                       const double* U, const double* Rb, double* Ub, cudaStream_t s);
+void launch_adj_lift(int nk, const Params& P, const AdjBuffers& A, const Faces& F, const int32_t* list, int nfaces,
+                     cudaStream_t s);
+void launch_adj_prolong(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, double* Ub,
+                        cudaStream_t s);
+void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);
+
+}  // namespace dgfv

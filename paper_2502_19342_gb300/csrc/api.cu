@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/dgfv.h"
+#include "adjoint.h"
 #include "bank.h"
 #include "common.cuh"
 #include "kernels.h"
@@ -100,6 +101,11 @@ struct dgfv_ctx {
     double graph_dt = 0.0;
     cudaStream_t graph_stream = nullptr;
     Profiler prof;
+    // adjoint buffers, allocated by the first adjoint call
+    bool adj_ready = false;
+    double *d_fbar = nullptr, *d_ubar = nullptr, *d_gbar = nullptr, *d_sbar = nullptr;
+    double *d_S1 = nullptr, *d_S2 = nullptr, *d_B1 = nullptr, *d_B2 = nullptr, *d_W = nullptr;
+    size_t adj_smem = 0;
     std::vector<void*> allocs;
 };
 
@@ -257,6 +263,10 @@ int apply_layout(dgfv_ctx* c) {
     for (int t = 0; t < (int)c->dg.first.size(); ++t)
         sm = std::max(sm, volume_smem_bytes(c->nk, c->dg.n[t], c->dg.count[t]));
     c->dg.smem = sm;
+    size_t asm_ = 0;
+    for (int t = 0; t < (int)c->dg.first.size(); ++t)
+        asm_ = std::max(asm_, adj_volume_smem_bytes(c->nk, c->dg.n[t], c->dg.count[t]));
+    c->adj_smem = asm_;
     TRY(upload_tiles(c, c->all));
     TRY(upload_tiles(c, c->dg));
     TRY(upload_tiles(c, c->fvt));
@@ -626,6 +636,75 @@ int dgfv_compute_dt_noalloc(dgfv_ctx* c, const double* d_U, double* d_out3, void
                                          " work tiles exceed the fixed scratch of " +
                                          std::to_string(DT_NOALLOC_MAX_BLOCKS) + " blocks");
     if (r != 0) return fail(c, DGFV_ERR_CUDA, "dgfv_compute_dt_noalloc: CUDA error");
+    return DGFV_OK;
+}
+
+static int adj_prepare(dgfv_ctx* c) {
+    if (c->n_fv_elems) return fail(c, DGFV_ERR_ARG, "the adjoint supports DG elements only (the pattern has FV elements)");
+    if (c->ph.riemann != 0) return fail(c, DGFV_ERR_ARG, "the adjoint supports the local Lax-Friedrichs flux only");
+    if (c->adj_ready) return DGFV_OK;
+    TRY(dalloc(c, &c->d_fbar, c->cap_fpts * c->V));
+    TRY(dalloc(c, &c->d_ubar, c->cap_fpts * c->V));
+    TRY(dalloc(c, &c->d_gbar, c->cap_fpts * 3 * c->V));
+    TRY(dalloc(c, &c->d_sbar, c->cap_fpts * c->V));
+    TRY(dalloc(c, &c->d_S1, c->cap_state));
+    TRY(dalloc(c, &c->d_S2, c->cap_state));
+    TRY(dalloc(c, &c->d_B1, c->cap_state));
+    TRY(dalloc(c, &c->d_B2, c->cap_state));
+    TRY(dalloc(c, &c->d_W, c->cap_state));
+    c->adj_ready = true;
+    return DGFV_OK;
+}
+
+// U_bar = (dR/dU)^T R_bar at U (Ub must not alias U or Rb).
+static void enqueue_vjp(dgfv_ctx* c, const double* U, const double* Rb, double* Ub, cudaStream_t s) {
+    const Params P = params(c);
+    const Faces F{c->d_faceL, c->d_faceR, c->d_faceD};
+    const AdjBuffers A{c->d_fbar, c->d_ubar, c->d_gbar, c->d_sbar};
+    // forward face values, lifting values and gradient traces of U
+    launch_prolong(c->nk, P, c->all.view(), c->all.ntiles, U, s);
+    if (c->ph.viscous) {
+        launch_face_lift(c->nk, P, F, c->lift.d, c->lift.count, s);
+        launch_dg_volume(c->nk, P, c->dg.view(), c->dg.ntiles, c->dg.smem, U, s);
+    }
+    launch_adj_surface(c->nk, P, A, c->dg.view(), c->dg.ntiles, Rb, s);
+    launch_adj_faces(c->nk, P, A, F, c->conf.view(), c->conf.ntiles, c->flux.d, c->flux.count, s);
+    launch_adj_volume(c->nk, P, A, c->dg.view(), c->dg.ntiles, c->adj_smem, U, Rb, Ub, s);
+    if (c->ph.viscous) launch_adj_lift(c->nk, P, A, F, c->lift.d, c->lift.count, s);
+    launch_adj_prolong(c->nk, P, A, c->dg.view(), c->dg.ntiles, Ub, s);
+}
+
+int dgfv_rhs_vjp(dgfv_ctx* c, const double* d_U, const double* d_Rbar, double* d_Ubar, void* stream) {
+    if (!c || !d_U || !d_Rbar || !d_Ubar) return DGFV_ERR_ARG;
+    if (d_Ubar == d_U || d_Ubar == d_Rbar) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
+    TRY(adj_prepare(c));
+    enqueue_vjp(c, d_U, d_Rbar, d_Ubar, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return DGFV_OK;
+}
+
+int dgfv_rk_step_vjp(dgfv_ctx* c, const double* d_U0, double dt, const double* d_Ubar_next, double* d_Ubar,
+                     void* stream) {
+    if (!c || !d_U0 || !d_Ubar_next || !d_Ubar || !(dt > 0.0)) return DGFV_ERR_ARG;
+    if (d_Ubar == d_Ubar_next || d_Ubar == d_U0) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
+    TRY(adj_prepare(c));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = c->n_state;
+    // stage states of the step (recomputed from the step's start state)
+    launch_set_scalar(c->d_dt3, dt, s);
+    enqueue_stage(c, d_U0, d_U0, c->d_S1, 1, 0.0, 1.0, s);       // U1 = U0 + dt R(U0)
+    enqueue_stage(c, c->d_S1, d_U0, c->d_S2, 1, 0.75, 0.25, s);  // U2 = 3/4 U0 + 1/4 (U1 + dt R(U1))
+    // U3 = 1/3 U0 + 2/3 (U2 + dt R(U2)), backwards:
+    enqueue_vjp(c, c->d_S2, d_Ubar_next, c->d_W, s);
+    launch_axpby(n, 2.0 / 3.0, d_Ubar_next, 2.0 / 3.0 * dt, c->d_W, c->d_B2, s);   // U2_bar
+    launch_axpby(n, 1.0 / 3.0, d_Ubar_next, 0.0, d_Ubar_next, d_Ubar, s);          // U0_bar  = 1/3 U3_bar
+    enqueue_vjp(c, c->d_S1, c->d_B2, c->d_W, s);
+    launch_axpby(n, 0.25, c->d_B2, 0.25 * dt, c->d_W, c->d_B1, s);                  // U1_bar
+    launch_axpby(n, 1.0, d_Ubar, 0.75, c->d_B2, d_Ubar, s);                         // U0_bar += 3/4 U2_bar
+    enqueue_vjp(c, d_U0, c->d_B1, c->d_W, s);
+    launch_axpby(n, 1.0, d_Ubar, 1.0, c->d_B1, d_Ubar, s);                          // += U1_bar
+    launch_axpby(n, 1.0, d_Ubar, dt, c->d_W, d_Ubar, s);                            // += dt J^T U1_bar
+    CK(cudaGetLastError());
     return DGFV_OK;
 }
 

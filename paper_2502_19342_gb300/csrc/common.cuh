@@ -48,6 +48,14 @@ struct Buffers {
     double* rtmp;   // state-sized: volume part (DG) / interior sub-cell part (FV) of -R
 };
 
+// Adjoint face buffers (same slot layout as the forward face buffers).
+struct AdjBuffers {
+    double* fbar;  // width V : adjoint of the outward face fluxes
+    double* ubar;  // width V : adjoint of the face values u(+-1)
+    double* gbar;  // width 3V: adjoint of the gradient traces
+    double* sbar;  // width V : adjoint of the lifting values U*
+};
+
 struct Params {
     DevPhys ph;
     Tables t;

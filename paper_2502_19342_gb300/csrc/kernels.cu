@@ -25,40 +25,11 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "device_util.cuh"
 #include "kernels.h"
 
 namespace dgfv {
 
-namespace {
-
-__device__ __forceinline__ const double* B(const Params& P, int32_t off) { return P.bank + off; }
-
-// 2D tensor-product map of a face field on shared memory: out[x][ao + no*bo] =
-// sum M[ao][ai] M[bo][bi] in[x][ai + ni*bi] for x < nvar; M is no x ni.
-// tmp holds nvar*no*ni doubles.  All threads of the block take part.
-__device__ void face_map(const double* in, int ni, double* out, int no, const double* M, int nvar,
-                         double* tmp) {
-    const int n1 = no * ni;
-    for (int i = threadIdx.x; i < nvar * n1; i += blockDim.x) {
-        const int x = i / n1, r = i % n1, ao = r % no, bi = r / no;
-        const double* src = in + x * ni * ni + ni * bi;
-        double s = 0.0;
-        for (int ai = 0; ai < ni; ++ai) s = fma(__ldg(M + ao * ni + ai), src[ai], s);
-        tmp[x * n1 + ao + no * bi] = s;
-    }
-    __syncthreads();
-    const int n2 = no * no;
-    for (int i = threadIdx.x; i < nvar * n2; i += blockDim.x) {
-        const int x = i / n2, r = i % n2, ao = r % no, bo = r / no;
-        const double* src = tmp + x * n1 + ao;
-        double s = 0.0;
-        for (int bi = 0; bi < ni; ++bi) s = fma(__ldg(M + bo * ni + bi), src[no * bi], s);
-        out[x * n2 + r] = s;
-    }
-    __syncthreads();
-}
-
-}  // namespace
 
 // ---------------------------------------------------------------------------------
 // k_prolong: face values of every element.
@@ -479,7 +450,7 @@ struct MixedFaceSmem {
     double U[2][V * PP];
     double G[2][3 * V * PP];
     double F[V * PP];
-    double T[4 * V * PP];
+    double T[V * PP];  // scratch of one 2-pass map of V variables
 };
 
 template <int NK, int D>

@@ -11,7 +11,20 @@
 // J_k = -rho D_k grad Y_k + rho Y_k sum_j D_j grad Y_j (sum_k J_k = 0).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+
+// Pointwise functions compile for the device and, for host-side checks of the
+// hand-written adjoints, for the host.
+#if defined(__CUDACC__)
+#define DGFV_HD __host__ __device__ __forceinline__
+#else
+#define DGFV_HD inline
+using std::fabs;
+using std::fma;
+using std::fmax;
+using std::sqrt;
+#endif
 
 namespace dgfv {
 
@@ -28,13 +41,13 @@ struct DevPhys {
 
 template <int NK>
 struct Prim {
-    double rho, irho, Y[NK], v[3], E, cv, icv, cp, kappa, T, p, c, mu, lam;
+    double rho, irho, Y[NK], v[3], E, eps, cv, icv, cp, kappa, T, p, c, mu, pr, lam;
 };
 
 // Mixture state of a conserved vector.  3 divisions and 1 square root; terms
 // a caller does not use are removed by the compiler after inlining.
 template <int NK>
-__device__ __forceinline__ void prim(const DevPhys& P, const double* u, Prim<NK>& s) {
+DGFV_HD void prim(const DevPhys& P, const double* u, Prim<NK>& s) {
     double rho = u[0];
 #pragma unroll
     for (int k = 1; k < NK; ++k) rho += u[k];
@@ -53,8 +66,10 @@ __device__ __forceinline__ void prim(const DevPhys& P, const double* u, Prim<NK>
     for (int i = 0; i < 3; ++i) s.v[i] = u[NK + i] * s.irho;
     s.E = u[NK + 3] * s.irho;
     double eps = s.E - 0.5 * (s.v[0] * s.v[0] + s.v[1] * s.v[1] + s.v[2] * s.v[2]);
+    s.eps = eps;
     s.cv = cv;
     s.cp = cp;
+    s.pr = pr;
     s.icv = 1.0 / cv;
     s.kappa = cp * s.icv;
     s.T = eps * s.icv;
@@ -66,7 +81,7 @@ __device__ __forceinline__ void prim(const DevPhys& P, const double* u, Prim<NK>
 
 // Convective flux in direction d.
 template <int NK>
-__device__ __forceinline__ void flux_conv(const double* u, const Prim<NK>& s, int d, double* F) {
+DGFV_HD void flux_conv(const double* u, const Prim<NK>& s, int d, double* F) {
     const double vd = s.v[d];
 #pragma unroll
     for (int k = 0; k < NK; ++k) F[k] = u[k] * vd;
@@ -84,7 +99,7 @@ struct PrimGrad {
 };
 
 template <int NK>
-__device__ __forceinline__ void prim_grad(const DevPhys& P, const Prim<NK>& s, const double* g,
+DGFV_HD void prim_grad(const DevPhys& P, const Prim<NK>& s, const double* g,
                                           PrimGrad<NK>& G) {
     constexpr int V = NK + 4;
 #pragma unroll
@@ -111,7 +126,7 @@ __device__ __forceinline__ void prim_grad(const DevPhys& P, const Prim<NK>& s, c
 
 // Viscous flux in direction d from the primitive gradients.
 template <int NK>
-__device__ __forceinline__ void flux_visc(const DevPhys& P, const Prim<NK>& s, const PrimGrad<NK>& G,
+DGFV_HD void flux_visc(const DevPhys& P, const Prim<NK>& s, const PrimGrad<NK>& G,
                                           int d, double* F) {
     const double divv = G.v[0][0] + G.v[1][1] + G.v[2][2];
     double tau[3];
@@ -136,7 +151,7 @@ __device__ __forceinline__ void flux_visc(const DevPhys& P, const Prim<NK>& s, c
 
 // Local Lax-Friedrichs flux in +x_d: (F_L + F_R)/2 - s_max (u_R - u_L)/2.
 template <int NK>
-__device__ __forceinline__ void riemann_llf(const double* uL, const Prim<NK>& sL, const double* uR,
+DGFV_HD void riemann_llf(const double* uL, const Prim<NK>& sL, const double* uR,
                                             const Prim<NK>& sR, int d, double* F) {
     constexpr int V = NK + 4;
     double FL[V], FR[V];
@@ -154,7 +169,7 @@ __device__ __forceinline__ void riemann_llf(const double* uL, const Prim<NK>& sL
 // species, shear), v_n + c; contact energy term eps_k = d(rho eps)/d(rho_k)
 // at fixed p and v; Harten-Hyman fix on the acoustic waves.
 template <int NK>
-__device__ __forceinline__ void riemann_roe(const DevPhys& P, const double* uL, const Prim<NK>& sL,
+DGFV_HD void riemann_roe(const DevPhys& P, const double* uL, const Prim<NK>& sL,
                                             const double* uR, const Prim<NK>& sR, int d, double* F) {
     constexpr int V = NK + 4;
     double FL[V], FR[V];
@@ -237,7 +252,7 @@ __device__ __forceinline__ void riemann_roe(const DevPhys& P, const double* uL, 
 // Interface flux at one point in +x_d: F* = F^c*(uL,uR) + (F^v(uL,gL) + F^v(uR,gR))/2
 // (Eqs. 20, 21).
 template <int NK>
-__device__ __forceinline__ void interface_flux(const DevPhys& P, const double* uL, const double* gL,
+DGFV_HD void interface_flux(const DevPhys& P, const double* uL, const double* gL,
                                                const double* uR, const double* gR, int d, double* F) {
     constexpr int V = NK + 4;
     Prim<NK> sL, sR;
@@ -261,7 +276,7 @@ __device__ __forceinline__ void interface_flux(const DevPhys& P, const double* u
 
 // FV reconstruction variables w = (rho_1..rho_NK, v, p) and back.
 template <int NK>
-__device__ __forceinline__ void cons_to_w(const DevPhys& P, const double* u, double* w) {
+DGFV_HD void cons_to_w(const DevPhys& P, const double* u, double* w) {
     double rho = u[0];
 #pragma unroll
     for (int k = 1; k < NK; ++k) rho += u[k];
@@ -280,7 +295,7 @@ __device__ __forceinline__ void cons_to_w(const DevPhys& P, const double* u, dou
 }
 
 template <int NK>
-__device__ __forceinline__ void w_to_cons(const DevPhys& P, const double* w, double* u) {
+DGFV_HD void w_to_cons(const DevPhys& P, const double* w, double* u) {
     double rho = w[0];
 #pragma unroll
     for (int k = 1; k < NK; ++k) rho += w[k];
@@ -298,7 +313,7 @@ __device__ __forceinline__ void w_to_cons(const DevPhys& P, const double* w, dou
     u[NK + 3] = w[NK + 3] * (cvr / (cpr - cvr)) + ke;
 }
 
-__device__ __forceinline__ double minmod(double a, double b) {
+DGFV_HD double minmod(double a, double b) {
     if (a * b <= 0.0) return 0.0;
     return fabs(a) <= fabs(b) ? a : b;
 }

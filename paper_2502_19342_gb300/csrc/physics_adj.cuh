@@ -1,0 +1,296 @@
+// Reverse-mode (vector-Jacobian) versions of the pointwise physics in
+// physics.cuh, written statement by statement from the forward functions:
+// every forward assignment y = f(x) becomes x_bar += (df/dx)^T y_bar, in
+// reverse order.  Branches (the larger wave speed of the local Lax-Friedrichs
+// flux, the sign of |v_d|) follow the forward evaluation.  These serve the
+// adjoint of R(U) on DG elements with the local Lax-Friedrichs flux.
+#pragma once
+
+#include "physics.cuh"
+
+namespace dgfv {
+
+template <int NK>
+struct PrimBar {
+    double rho, irho, Y[NK], v[3], E, eps, cv, icv, cp, kappa, T, p, c, mu, pr, lam;
+};
+
+template <int NK>
+DGFV_HD void zero(PrimBar<NK>& b) {
+    b.rho = b.irho = b.E = b.eps = b.cv = b.icv = b.cp = b.kappa = b.T = b.p = b.c = b.mu = b.pr = b.lam = 0.0;
+    for (int k = 0; k < NK; ++k) b.Y[k] = 0.0;
+    for (int i = 0; i < 3; ++i) b.v[i] = 0.0;
+}
+
+// u_bar += (d prim / d u)^T s_bar
+template <int NK>
+DGFV_HD void prim_rev(const DevPhys& P, const double* u, const Prim<NK>& s, PrimBar<NK> b, double* ub) {
+    // lam = mu cp / pr
+    b.mu += b.lam * s.cp / s.pr;
+    b.cp += b.lam * s.mu / s.pr;
+    b.pr -= b.lam * s.lam / s.pr;
+    // c = sqrt(kappa p irho)
+    if (s.c > 0.0) {
+        const double qb = 0.5 * b.c / s.c;
+        b.kappa += qb * s.p * s.irho;
+        b.p += qb * s.kappa * s.irho;
+        b.irho += qb * s.kappa * s.p;
+    }
+    // p = rho (cp - cv) T
+    const double Rm = s.cp - s.cv;
+    b.rho += b.p * Rm * s.T;
+    b.cp += b.p * s.rho * s.T;
+    b.cv -= b.p * s.rho * s.T;
+    b.T += b.p * s.rho * Rm;
+    // T = eps icv
+    b.eps += b.T * s.icv;
+    b.icv += b.T * s.eps;
+    // kappa = cp icv
+    b.cp += b.kappa * s.icv;
+    b.icv += b.kappa * s.cp;
+    // icv = 1/cv
+    b.cv -= b.icv * s.icv * s.icv;
+    // eps = E - |v|^2/2
+    b.E += b.eps;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) b.v[i] -= b.eps * s.v[i];
+    // E = u_E irho;  v_i = u_{m_i} irho
+    ub[NK + 3] += b.E * s.irho;
+    b.irho += b.E * u[NK + 3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        ub[NK + i] += b.v[i] * s.irho;
+        b.irho += b.v[i] * u[NK + i];
+    }
+    // mixture sums and Y_k = u_k irho
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const double Yb = b.Y[k] + b.cv * P.cv[k] + b.cp * P.cp[k] + b.mu * P.mu[k] + b.pr * P.pr[k];
+        ub[k] += Yb * s.irho;
+        b.irho += Yb * u[k];
+    }
+    // irho = 1/rho;  rho = sum u_k
+    b.rho -= b.irho * s.irho * s.irho;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) ub[k] += b.rho;
+}
+
+// reverse of flux_conv: u_bar, s_bar += (dF/d(u, s))^T F_bar
+template <int NK>
+DGFV_HD void flux_conv_rev(const double* u, const Prim<NK>& s, int d, const double* Fb, double* ub,
+                           PrimBar<NK>& b) {
+    const double vd = s.v[d];
+    double vdb = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        ub[k] += Fb[k] * vd;
+        vdb += Fb[k] * u[k];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        ub[NK + i] += Fb[NK + i] * vd;
+        vdb += Fb[NK + i] * u[NK + i];
+    }
+    b.p += Fb[NK + d];
+    ub[NK + 3] += Fb[NK + 3] * vd;
+    b.p += Fb[NK + 3] * vd;
+    vdb += Fb[NK + 3] * (u[NK + 3] + s.p);
+    b.v[d] += vdb;
+}
+
+template <int NK>
+struct PrimGradBar {
+    double Y[NK][3], v[3][3], T[3];
+};
+
+template <int NK>
+DGFV_HD void zero(PrimGradBar<NK>& b) {
+    for (int d = 0; d < 3; ++d) {
+        for (int k = 0; k < NK; ++k) b.Y[k][d] = 0.0;
+        for (int i = 0; i < 3; ++i) b.v[i][d] = 0.0;
+        b.T[d] = 0.0;
+    }
+}
+
+// reverse of flux_visc: (G, s)_bar += (dF^v_d/d(G, s))^T F_bar
+template <int NK>
+DGFV_HD void flux_visc_rev(const DevPhys& P, const Prim<NK>& s, const PrimGrad<NK>& G, int d, const double* Fb,
+                           PrimGradBar<NK>& Gb, PrimBar<NK>& b) {
+    const double divv = G.v[0][0] + G.v[1][1] + G.v[2][2];
+    double tau[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) tau[i] = s.mu * (G.v[d][i] + G.v[i][d]);
+    tau[d] -= s.mu * (2.0 / 3.0) * divv;
+    double corr = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) corr = fma(P.D[k], G.Y[k][d], corr);
+    double qd = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) qd = fma(P.cp[k], s.rho * (s.Y[k] * corr - P.D[k] * G.Y[k][d]), qd);
+    // F_E = -tau.v - lam GT_d + T qd
+    const double FE = Fb[NK + 3];
+    b.lam -= FE * G.T[d];
+    Gb.T[d] -= FE * s.lam;
+    b.T += FE * qd;
+    const double qdb = FE * s.T;
+    double taub[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        taub[i] = -FE * s.v[i] - Fb[NK + i];  // from -tau.v and F_{m_i} = -tau_i
+        b.v[i] -= FE * tau[i];
+    }
+    // J_k (= F_k) with qd = sum cp_k J_k
+    double corrb = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const double Jb = Fb[k] + qdb * P.cp[k];
+        b.rho += Jb * (s.Y[k] * corr - P.D[k] * G.Y[k][d]);
+        b.Y[k] += Jb * s.rho * corr;
+        corrb += Jb * s.rho * s.Y[k];
+        Gb.Y[k][d] -= Jb * s.rho * P.D[k];
+    }
+#pragma unroll
+    for (int k = 0; k < NK; ++k) Gb.Y[k][d] += corrb * P.D[k];
+    // tau_i = mu (Gv[d][i] + Gv[i][d]) - delta_id mu 2/3 divv
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        b.mu += taub[i] * (G.v[d][i] + G.v[i][d]);
+        Gb.v[d][i] += taub[i] * s.mu;
+        Gb.v[i][d] += taub[i] * s.mu;
+    }
+    b.mu -= taub[d] * (2.0 / 3.0) * divv;
+    const double divvb = -taub[d] * s.mu * (2.0 / 3.0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Gb.v[i][i] += divvb;
+}
+
+// reverse of prim_grad: g_bar, s_bar += (dG/d(g, s))^T G_bar
+template <int NK>
+DGFV_HD void prim_grad_rev(const DevPhys& P, const Prim<NK>& s, const double* g, const PrimGrad<NK>& G,
+                           const PrimGradBar<NK>& Gb, double* gb, PrimBar<NK>& b) {
+    constexpr int V = NK + 4;
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+        const double* gd = g + dd * V;
+        double* gbd = gb + dd * V;
+        double gr = gd[0];
+#pragma unroll
+        for (int k = 1; k < NK; ++k) gr += gd[k];
+        double gcv = 0.0;
+#pragma unroll
+        for (int k = 0; k < NK; ++k) gcv = fma(P.cv[k], G.Y[k][dd], gcv);
+        double geps = (gd[NK + 3] - s.E * gr) * s.irho;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) geps -= s.v[i] * G.v[i][dd];
+        // GT = (geps - T gcv) icv
+        const double GTb = Gb.T[dd];
+        const double gepsb = GTb * s.icv;
+        b.T -= GTb * gcv * s.icv;
+        const double gcvb = -GTb * s.T * s.icv;
+        b.icv += GTb * (geps - s.T * gcv);
+        // geps = (g_E - E gr) irho - sum_i v_i Gv_i
+        double grb = 0.0;
+        gbd[NK + 3] += gepsb * s.irho;
+        b.E -= gepsb * gr * s.irho;
+        grb -= gepsb * s.E * s.irho;
+        b.irho += gepsb * (gd[NK + 3] - s.E * gr);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            b.v[i] -= gepsb * G.v[i][dd];
+            const double Gvb = Gb.v[i][dd] - gepsb * s.v[i];
+            // Gv_i = (g_{m_i} - v_i gr) irho
+            gbd[NK + i] += Gvb * s.irho;
+            b.v[i] -= Gvb * gr * s.irho;
+            grb -= Gvb * s.v[i] * s.irho;
+            b.irho += Gvb * (gd[NK + i] - s.v[i] * gr);
+        }
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            // gcv = sum cv_k GY_k;  GY_k = (g_k - Y_k gr) irho
+            const double GYb = Gb.Y[k][dd] + gcvb * P.cv[k];
+            gbd[k] += GYb * s.irho;
+            b.Y[k] -= GYb * gr * s.irho;
+            grb -= GYb * s.Y[k] * s.irho;
+            b.irho += GYb * (gd[k] - s.Y[k] * gr);
+        }
+        // gr = sum_k g_k
+#pragma unroll
+        for (int k = 0; k < NK; ++k) gbd[k] += grb;
+    }
+}
+
+// Adjoint of the nodal volume fluxes F_d = F^c_d(u) + F^v_d(u, g), d = 0..2:
+// given F_bar[d*V + v], accumulate u_bar (V) and g_bar (3V).
+template <int NK>
+DGFV_HD void volume_point_rev(const DevPhys& P, const double* u, const double* g, const double* Fb, double* ub,
+                              double* gb) {
+    Prim<NK> s;
+    prim<NK>(P, u, s);
+    PrimBar<NK> b;
+    zero(b);
+    PrimGrad<NK> G;
+    PrimGradBar<NK> Gb;
+    if (P.viscous) {
+        prim_grad<NK>(P, s, g, G);
+        zero(Gb);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        flux_conv_rev<NK>(u, s, d, Fb + d * (NK + 4), ub, b);
+        if (P.viscous) flux_visc_rev<NK>(P, s, G, d, Fb + d * (NK + 4), Gb, b);
+    }
+    if (P.viscous) prim_grad_rev<NK>(P, s, g, G, Gb, gb, b);
+    prim_rev<NK>(P, u, s, b, ub);
+}
+
+// Adjoint of the interface flux F* = LLF(uL, uR) + (F^v(uL,gL) + F^v(uR,gR))/2 in +x_d:
+// given F_bar (V), accumulate uL_bar, gL_bar, uR_bar, gR_bar.
+template <int NK>
+DGFV_HD void face_point_rev(const DevPhys& P, const double* uL, const double* gL, const double* uR,
+                            const double* gR, int d, const double* Fb, double* uLb, double* gLb, double* uRb,
+                            double* gRb) {
+    constexpr int V = NK + 4;
+    Prim<NK> sL, sR;
+    prim<NK>(P, uL, sL);
+    prim<NK>(P, uR, sR);
+    PrimBar<NK> bL, bR;
+    zero(bL);
+    zero(bR);
+    // local Lax-Friedrichs: F = (F_L + F_R)/2 - smax (uR - uL)/2
+    const double aL = fabs(sL.v[d]) + sL.c, aR = fabs(sR.v[d]) + sR.c;
+    const double smax = aL > aR ? aL : aR;
+    double half[V];
+    double smaxb = 0.0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        half[v] = 0.5 * Fb[v];
+        uRb[v] -= half[v] * smax;
+        uLb[v] += half[v] * smax;
+        smaxb -= half[v] * (uR[v] - uL[v]);
+    }
+    flux_conv_rev<NK>(uL, sL, d, half, uLb, bL);
+    flux_conv_rev<NK>(uR, sR, d, half, uRb, bR);
+    if (aL > aR) {
+        bL.v[d] += smaxb * (sL.v[d] > 0.0 ? 1.0 : (sL.v[d] < 0.0 ? -1.0 : 0.0));
+        bL.c += smaxb;
+    } else {
+        bR.v[d] += smaxb * (sR.v[d] > 0.0 ? 1.0 : (sR.v[d] < 0.0 ? -1.0 : 0.0));
+        bR.c += smaxb;
+    }
+    if (P.viscous) {
+        PrimGrad<NK> G;
+        PrimGradBar<NK> Gb;
+        prim_grad<NK>(P, sL, gL, G);
+        zero(Gb);
+        flux_visc_rev<NK>(P, sL, G, d, half, Gb, bL);
+        prim_grad_rev<NK>(P, sL, gL, G, Gb, gLb, bL);
+        prim_grad<NK>(P, sR, gR, G);
+        zero(Gb);
+        flux_visc_rev<NK>(P, sR, G, d, half, Gb, bR);
+        prim_grad_rev<NK>(P, sR, gR, G, Gb, gRb, bR);
+    }
+    prim_rev<NK>(P, uL, sL, bL, uLb);
+    prim_rev<NK>(P, uR, sR, bR, uRb);
+}
+
+}  // namespace dgfv

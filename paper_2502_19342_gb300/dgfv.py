@@ -21,7 +21,8 @@ SYMBOLS = ["dgfv_init_mesh", "dgfv_num_elements", "dgfv_set_degrees", "dgfv_get_
            "dgfv_set_state", "dgfv_get_state", "dgfv_set_state_host", "dgfv_get_state_host", "dgfv_eval_rhs",
            "dgfv_compute_dt", "dgfv_rk_step", "dgfv_rk_steps", "dgfv_indicator", "dgfv_adapt", "dgfv_sync_status",
            "dgfv_status_string", "dgfv_last_error", "dgfv_destroy", "dgfv_bank_entry", "dgfv_probe_dfma",
-           "dgfv_profile_enable", "dgfv_profile_read", "dgfv_compute_dt_noalloc"]
+           "dgfv_profile_enable", "dgfv_profile_read", "dgfv_compute_dt_noalloc", "dgfv_rhs_vjp",
+           "dgfv_rk_step_vjp"]
 KERNELS = ["prolong", "fv", "face_lift", "dg_volume", "face_flux", "surface", "dt", "indicator", "remap"]
 
 
@@ -67,6 +68,8 @@ def lib():
         L.dgfv_eval_rhs.argtypes = [vp, vp, vp, vp]
         L.dgfv_compute_dt.argtypes = [vp, vp, dp, vp]
         L.dgfv_compute_dt_noalloc.argtypes = [vp, vp, vp, vp]
+        L.dgfv_rhs_vjp.argtypes = [vp, vp, vp, vp, vp]
+        L.dgfv_rk_step_vjp.argtypes = [vp, vp, C.c_double, vp, vp, vp]
         L.dgfv_rk_step.argtypes = [vp, C.c_double, dp, vp]
         L.dgfv_rk_steps.argtypes = [vp, C.c_int, C.c_double, dp, vp]
         L.dgfv_indicator.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -230,6 +233,31 @@ class Context:
         self._rc(lib().dgfv_eval_rhs(self.h, _ptr(U), _ptr(R), _stream(stream)), "eval_rhs")
         return R
 
+    def rhs_vjp(self, U, Rbar, Ubar=None, stream=None):
+        """(dR/dU)^T Rbar at U (DG patterns, local Lax-Friedrichs flux)."""
+        import torch
+        n = self.state_size
+        _check_dev(U, n)
+        _check_dev(Rbar, n)
+        if Ubar is None:
+            Ubar = torch.empty(n, dtype=torch.float64, device="cuda")
+        _check_dev(Ubar, n)
+        self._rc(lib().dgfv_rhs_vjp(self.h, _ptr(U), _ptr(Rbar), _ptr(Ubar), _stream(stream)), "rhs_vjp")
+        return Ubar
+
+    def rk_step_vjp(self, U0, dt, Ubar_next, Ubar=None, stream=None):
+        """Adjoint of one SSP-RK3 step of size dt from U0 (stages recomputed)."""
+        import torch
+        n = self.state_size
+        _check_dev(U0, n)
+        _check_dev(Ubar_next, n)
+        if Ubar is None:
+            Ubar = torch.empty(n, dtype=torch.float64, device="cuda")
+        _check_dev(Ubar, n)
+        self._rc(lib().dgfv_rk_step_vjp(self.h, _ptr(U0), float(dt), _ptr(Ubar_next), _ptr(Ubar), _stream(stream)),
+                 "rk_step_vjp")
+        return Ubar
+
     def compute_dt(self, U, stream=None):
         _check_dev(U, self.state_size)
         out = (C.c_double * 3)()
@@ -301,3 +329,41 @@ def init_mesh(problem, N_min=None, N_max=None, opts=None):
 def probe_dfma(iters=1 << 16, stream=None):
     """Measured FP64 FMA throughput (flop/s, 2 per DFMA) of this GPU."""
     return float(lib().dgfv_probe_dfma(int(iters), _stream(stream)))
+
+
+def rhs_function():
+    """torch.autograd.Function computing R(U) on the CUDA path, with the
+    hand-written adjoint as its backward (degree pattern frozen).
+    Usage: R = rhs_function().apply(U, ctx)."""
+    import torch
+
+    class RHS(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, U, ctx):
+            fctx.ctx = ctx
+            fctx.save_for_backward(U)
+            return ctx.eval_rhs(U.contiguous())
+
+        @staticmethod
+        def backward(fctx, Rbar):
+            (U,) = fctx.saved_tensors
+            return fctx.ctx.rhs_vjp(U, Rbar.contiguous()), None
+
+    return RHS
+
+
+def rollout_gradient(ctx, U0, n_steps, dt, loss_grad):
+    """Gradient of a loss of the state after n_steps SSP-RK3 steps of size dt
+    with respect to the initial state, by the adjoint of every step; the state
+    at the start of every step is the only checkpoint (the stage states are
+    recomputed).  loss_grad(U_final) returns dLoss/dU_final."""
+    import torch
+    states = [U0.clone()]
+    ctx.set_state(U0)
+    for _ in range(n_steps):
+        ctx.rk_step(dt, want_dt=False)
+        states.append(ctx.get_state())
+    lam = loss_grad(states[-1])
+    for k in range(n_steps - 1, -1, -1):
+        lam = ctx.rk_step_vjp(states[k], dt, lam)
+    return lam, states[-1]

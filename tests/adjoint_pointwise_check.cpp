@@ -1,0 +1,135 @@
+// Host check of the hand-written pointwise adjoints of the CUDA path
+// (physics_adj.cuh) against central finite differences of the forward
+// functions (physics.cuh), compiled for the host by the test suite.
+#include <cstdio>
+#include <cstdlib>
+#include <random>
+
+#include "../paper_2502_19342_gb300/csrc/physics_adj.cuh"
+
+using namespace dgfv;
+
+template <int NK>
+DevPhys phys(bool visc) {
+    DevPhys P{};
+    P.nk = NK;
+    P.viscous = visc;
+    const double gam[3] = {1.4, 1.3, 1.67}, R[3] = {1.0 / 29, 1.0 / 44, 1.0 / 4};
+    for (int k = 0; k < NK; ++k) {
+        P.cv[k] = R[k] / (gam[k] - 1);
+        P.cp[k] = gam[k] * P.cv[k];
+        P.mu[k] = 1e-2 * (1 + 0.3 * k);
+        P.pr[k] = 0.72 - 0.02 * k;
+        P.D[k] = 3e-3 * (1 + 0.5 * k);
+    }
+    return P;
+}
+
+template <int NK>
+void state(std::mt19937& rng, const DevPhys& P, double* u) {
+    std::uniform_real_distribution<double> U(0.0, 1.0);
+    double rho = 0.0, cv = 0.0;
+    for (int k = 0; k < NK; ++k) {
+        u[k] = 0.2 + 0.5 * U(rng);
+        rho += u[k];
+        cv += u[k] * P.cv[k];
+    }
+    double v[3], ke = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        v[i] = U(rng) - 0.5;
+        u[NK + i] = rho * v[i];
+        ke += 0.5 * rho * v[i] * v[i];
+    }
+    u[NK + 3] = cv * (20.0 + 10 * U(rng)) + ke;  // rho c_v T + kinetic energy
+}
+
+template <int NK>
+double vol_dot(const DevPhys& P, const double* u, const double* g, const double* Fb) {
+    constexpr int V = NK + 4;
+    Prim<NK> s;
+    prim<NK>(P, u, s);
+    PrimGrad<NK> G;
+    if (P.viscous) prim_grad<NK>(P, s, g, G);
+    double acc = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double F[V], Fv[V];
+        flux_conv<NK>(u, s, d, F);
+        if (P.viscous) {
+            flux_visc<NK>(P, s, G, d, Fv);
+            for (int v = 0; v < V; ++v) F[v] += Fv[v];
+        }
+        for (int v = 0; v < V; ++v) acc += Fb[d * V + v] * F[v];
+    }
+    return acc;
+}
+
+template <int NK>
+double face_dot(const DevPhys& P, const double* uL, const double* gL, const double* uR, const double* gR, int d,
+                const double* Fb) {
+    constexpr int V = NK + 4;
+    double F[V];
+    interface_flux<NK>(P, uL, gL, uR, gR, d, F);
+    double acc = 0.0;
+    for (int v = 0; v < V; ++v) acc += Fb[v] * F[v];
+    return acc;
+}
+
+template <int NK>
+int check(bool visc, int seed) {
+    constexpr int V = NK + 4;
+    std::mt19937 rng(seed);
+    std::normal_distribution<double> N01(0.0, 1.0);
+    DevPhys P = phys<NK>(visc);
+    int bad = 0;
+    for (int trial = 0; trial < 20; ++trial) {
+        double u[V], g[3 * V], Fb[3 * V], du[V], dg[3 * V];
+        state<NK>(rng, P, u);
+        for (int x = 0; x < 3 * V; ++x) { g[x] = 0.3 * N01(rng); Fb[x] = N01(rng); dg[x] = N01(rng); }
+        for (int v = 0; v < V; ++v) du[v] = 0.05 * N01(rng) * std::fabs(u[v]);
+        double ub[V] = {}, gb[3 * V] = {};
+        volume_point_rev<NK>(P, u, g, Fb, ub, gb);
+        const double eps = 1e-6;
+        double up[V], um[V], gp[3 * V], gm[3 * V];
+        for (int v = 0; v < V; ++v) { up[v] = u[v] + eps * du[v]; um[v] = u[v] - eps * du[v]; }
+        for (int x = 0; x < 3 * V; ++x) { gp[x] = g[x] + eps * dg[x]; gm[x] = g[x] - eps * dg[x]; }
+        const double fd = (vol_dot<NK>(P, up, gp, Fb) - vol_dot<NK>(P, um, gm, Fb)) / (2 * eps);
+        double ad = 0.0;
+        for (int v = 0; v < V; ++v) ad += ub[v] * du[v];
+        for (int x = 0; x < 3 * V; ++x) ad += gb[x] * dg[x];
+        if (std::fabs(fd - ad) > 1e-7 + 1e-6 * std::fabs(fd)) {
+            std::printf("volume NK=%d visc=%d trial %d: fd %.12e adjoint %.12e\n", NK, visc, trial, fd, ad);
+            ++bad;
+        }
+        // face
+        double uR[V], gR[3 * V], FbF[V], duR[V], dgR[3 * V];
+        state<NK>(rng, P, uR);
+        for (int x = 0; x < 3 * V; ++x) { gR[x] = 0.3 * N01(rng); dgR[x] = N01(rng); }
+        for (int v = 0; v < V; ++v) { FbF[v] = N01(rng); duR[v] = 0.05 * N01(rng) * std::fabs(uR[v]); }
+        const int d = trial % 3;
+        double uLb[V] = {}, gLb[3 * V] = {}, uRb[V] = {}, gRb[3 * V] = {};
+        face_point_rev<NK>(P, u, g, uR, gR, d, FbF, uLb, gLb, uRb, gRb);
+        double uRp[V], uRm[V], gRp[3 * V], gRm[3 * V];
+        for (int v = 0; v < V; ++v) { uRp[v] = uR[v] + eps * duR[v]; uRm[v] = uR[v] - eps * duR[v]; }
+        for (int x = 0; x < 3 * V; ++x) { gRp[x] = gR[x] + eps * dgR[x]; gRm[x] = gR[x] - eps * dgR[x]; }
+        const double fdf = (face_dot<NK>(P, up, gp, uRp, gRp, d, FbF) - face_dot<NK>(P, um, gm, uRm, gRm, d, FbF)) / (2 * eps);
+        double adf = 0.0;
+        for (int v = 0; v < V; ++v) adf += uLb[v] * du[v] + uRb[v] * duR[v];
+        for (int x = 0; x < 3 * V; ++x) adf += gLb[x] * dg[x] + gRb[x] * dgR[x];
+        if (std::fabs(fdf - adf) > 1e-7 + 1e-6 * std::fabs(fdf)) {
+            std::printf("face NK=%d visc=%d trial %d: fd %.12e adjoint %.12e\n", NK, visc, trial, fdf, adf);
+            ++bad;
+        }
+    }
+    return bad;
+}
+
+int main() {
+    int bad = 0;
+    for (int visc = 0; visc < 2; ++visc) {
+        bad += check<1>(visc, 1 + visc);
+        bad += check<2>(visc, 3 + visc);
+        bad += check<3>(visc, 5 + visc);
+    }
+    std::printf("%s (%d mismatches)\n", bad ? "FAIL" : "OK", bad);
+    return bad ? 1 : 0;
+}

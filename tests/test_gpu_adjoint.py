@@ -1,0 +1,167 @@
+"""The hand-written adjoint of the CUDA path (dgfv_rhs_vjp, dgfv_rk_step_vjp)
+against the oracle: the dot-product test <R_bar, J v> (oracle, exact dual
+numbers) = <J^T R_bar (CUDA), v>, central finite differences (eps = 1e-6) of
+the oracle's SSP-RK3 step along seeded directions, and the gradient of a
+kinetic-energy-plus-species-variance functional after a short rollout."""
+import numpy as np
+import pytest
+
+from paper_2502_19342_gb300 import workloads as W
+from tests.gpu_helpers import ctx_for, per_field, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+def _dg_problem(seed, nk=3, nel=(3, 2, 3), Nlo=1, Nhi=5, mu=3e-3, uniform=None):
+    specs = [W.AIR, W.HELIUM, W.CO2][:nk]
+    sp = W.species_set(specs, mu=mu)
+    n = nel[0] * nel[1] * nel[2]
+    N = np.full(n, uniform, np.int8) if uniform else W.random_degrees(n, Nlo, Nhi, seed)
+    prob = W.make_problem([(nel, (0, 0, 0), (1.0, 0.8, 1.1))], sp, n_fv=8, N=N, riemann=0)
+    return prob, W.smooth_random_state(prob, seed, amp=0.1)
+
+
+@pytest.mark.parametrize("nk,mu,seed,uniform", [(3, 3e-3, 1, None), (2, 0.0, 2, None), (1, 1e-3, 3, None),
+                                                (3, 2e-3, 4, 4)])
+def test_rhs_vjp_dot_product_with_oracle_jvp(oracle, nk, mu, seed, uniform):
+    prob, U = _dg_problem(seed, nk=nk, mu=mu, uniform=uniform)
+    rng = np.random.default_rng(seed)
+    Rbar = rng.standard_normal(U.size)
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    Ubar = ctx.rhs_vjp(to_dev(U), to_dev(Rbar)).cpu().numpy()
+    for _ in range(3):
+        v = rng.standard_normal(U.size) * 1e-2 * np.abs(U).mean()
+        _, Jv = oracle.eval_rhs_jvp(prob, U, v)
+        lhs = float(np.dot(Rbar, Jv))
+        rhs = float(np.dot(Ubar, v))
+        scale = float(np.abs(Rbar * Jv).sum())
+        assert abs(lhs - rhs) <= 1e-11 * scale, (lhs, rhs, scale)
+    ctx.close()
+
+
+def test_rhs_vjp_full_adjoint_against_oracle_columns(oracle):
+    """On a tiny mesh the whole matrix J^T R_bar is checked entry by entry: the
+    oracle's JVP along every unit vector gives the columns of J."""
+    prob, U = _dg_problem(5, nk=2, nel=(2, 1, 2), Nlo=1, Nhi=2)
+    rng = np.random.default_rng(5)
+    Rbar = rng.standard_normal(U.size)
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    Ubar = ctx.rhs_vjp(to_dev(U), to_dev(Rbar)).cpu().numpy()
+    ref = np.zeros(U.size)
+    for j in range(U.size):
+        e = np.zeros(U.size)
+        e[j] = 1.0
+        ref[j] = np.dot(Rbar, oracle.eval_rhs_jvp(prob, U, e)[1])
+    np.testing.assert_allclose(Ubar, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+    ctx.close()
+
+
+def test_rk_step_vjp_against_central_differences(oracle):
+    prob, U = _dg_problem(6, nk=3, uniform=3)
+    dt = 2e-4
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    rng = np.random.default_rng(6)
+    lam = rng.standard_normal(U.size)
+    Ubar = ctx.rk_step_vjp(to_dev(U), dt, to_dev(lam)).cpu().numpy()
+    eps = 1e-6
+    for _ in range(6):
+        v = rng.standard_normal(U.size) * np.abs(U).mean()
+        up, _ = oracle.rk3(prob, U + eps * v, 1, dt_fixed=dt)
+        um, _ = oracle.rk3(prob, U - eps * v, 1, dt_fixed=dt)
+        fd = float(np.dot(lam, (up - um) / (2 * eps)))
+        ad = float(np.dot(Ubar, v))
+        assert abs(fd - ad) <= 1e-6 * abs(fd) + 1e-9 * float(np.abs(lam).sum() * np.abs(v).mean()), (fd, ad)
+    ctx.close()
+
+
+def _functional(prob, U, Ybar):
+    """sum over nodes of w J [rho |v|^2 / 2 + sum_{k<Nk} (Y_k - Ybar_k)^2] (DG elements)."""
+    f = per_field(prob, U)
+    nk = len(prob["gamma"])
+    rho = sum(f[:nk])
+    ke = 0.5 * (f[nk] ** 2 + f[nk + 1] ** 2 + f[nk + 2] ** 2) / rho
+    var = sum((f[k] / rho - Ybar[k]) ** 2 for k in range(nk - 1))
+    wts = np.concatenate([np.einsum("k,j,i->kji", *(np.polynomial.legendre.leggauss(int(N) + 1)[1],) * 3).ravel()
+                          for N in prob["N"]])
+    return float(np.sum(wts * (ke + var)))
+
+
+def test_rollout_gradient_against_central_differences(oracle):
+    """Gradient of the functional after 4 SSP-RK3 steps with respect to the
+    initial state (stage checkpointing), against central differences of the
+    oracle's rollout along seeded directions."""
+    from paper_2502_19342_gb300 import dgfv
+    prob, U = _dg_problem(7, nk=3, nel=(2, 2, 2), uniform=3, mu=2e-3)
+    Ybar = [0.3, 0.3]
+    dt, steps = 3e-4, 4
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    nk = 3
+
+    def loss_grad(Uf):
+        X = Uf.detach().clone().requires_grad_(True)
+        f = per_field_torch(prob, X)
+        rho = f[0] + f[1] + f[2]
+        ke = 0.5 * (f[nk] ** 2 + f[nk + 1] ** 2 + f[nk + 2] ** 2) / rho
+        var = sum((f[k] / rho - Ybar[k]) ** 2 for k in range(nk - 1))
+        w = torch.from_numpy(_weights(prob)).cuda()
+        (w * (ke + var)).sum().backward()
+        return X.grad.contiguous()
+
+    grad, _ = dgfv.rollout_gradient(ctx, to_dev(U), steps, dt, loss_grad)
+    grad = grad.cpu().numpy()
+    rng = np.random.default_rng(7)
+    eps = 1e-6
+    for _ in range(5):
+        v = rng.standard_normal(U.size) * np.abs(U).mean()
+        Jp = _functional(prob, oracle.rk3(prob, U + eps * v, steps, dt_fixed=dt)[0], Ybar)
+        Jm = _functional(prob, oracle.rk3(prob, U - eps * v, steps, dt_fixed=dt)[0], Ybar)
+        fd = (Jp - Jm) / (2 * eps)
+        ad = float(np.dot(grad, v))
+        assert abs(fd - ad) <= 1e-6 * abs(fd) + 1e-10, (fd, ad)
+    ctx.close()
+
+
+def _weights(prob):
+    """Per-point LG weights (x fastest) of every element, repeated for no variable."""
+    return np.concatenate([np.einsum("k,j,i->kji", *(np.polynomial.legendre.leggauss(int(N) + 1)[1],) * 3).ravel()
+                           for N in prob["N"]])
+
+
+def per_field_torch(prob, X):
+    off, _ = W.offsets(prob)
+    V = W.n_vars(prob)
+    n = W.points_per_dir(prob)
+    out = [[] for _ in range(V)]
+    for e in range(len(off)):
+        m3 = int(n[e]) ** 3
+        blk = X[int(off[e]):int(off[e]) + V * m3].reshape(V, m3)
+        for v in range(V):
+            out[v].append(blk[v])
+    return [torch.cat(o) for o in out]
+
+
+def test_autograd_function_backward_is_the_adjoint():
+    from paper_2502_19342_gb300 import dgfv
+    prob, U = _dg_problem(8, nk=2, uniform=2)
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    X = to_dev(U).requires_grad_(True)
+    R = dgfv.rhs_function().apply(X, ctx)
+    Rbar = torch.randn_like(R)
+    (R * Rbar).sum().backward()
+    ref = ctx.rhs_vjp(to_dev(U), Rbar.detach().contiguous())
+    torch.testing.assert_close(X.grad, ref, rtol=0, atol=0)
+    ctx.close()
+
+
+def test_adjoint_rejects_fv_patterns():
+    from paper_2502_19342_gb300 import dgfv
+    prob, U = _dg_problem(9, nk=2)
+    prob["fv"] = np.zeros(len(prob["N"]), np.uint8)
+    prob["fv"][0] = 1
+    U = W.smooth_random_state(prob, 9)
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    with pytest.raises(dgfv.DgfvError):
+        ctx.rhs_vjp(to_dev(U), to_dev(np.ones_like(U)))
+    ctx.close()
