@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--nel", type=int, default=48, help="elements per direction")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
     p.add_argument("--profile-eval", action="store_true",
                    help="after the warm-up cycles run one R(U) evaluation between cudaProfilerStart/Stop "
                         "(for ncu --profile-from-start off) and exit")
@@ -161,6 +162,102 @@ def cpu_baseline(prob, budget_s=12.0):
     return {"value": dofs * reps / dt, "unit": "DOF-stage/s", "cores": cores, "kind": "oracle",
             "sample": f"{reps} evaluations of R(U) on a 12^3-element sample ({dofs} DOFs) with the workload's "
                       f"degree/FV distribution, {dt:.1f} s"}
+
+
+def adjoint_cost(steps=10):
+    """Adjoint of the SSP-RK3 rollout on the mixing-layer workload (16^3
+    elements, N = 4, 3 species, viscous, pattern frozen): time of the forward
+    steps vs the adjoint steps (stage states recomputed from one checkpoint per
+    step), CUDA events."""
+    import torch
+    from paper_2502_19342_gb300 import dgfv, workloads as W
+    prob, U = W.mixing_layer()
+    ctx = dgfv.Context(prob, N_min=4, N_max=4)
+    Ud = torch.from_numpy(U).cuda()
+    dt = ctx.compute_dt(Ud)[0]
+    states = [Ud.clone()]
+    ctx.set_state(Ud)
+    for _ in range(2):  # warm-up of both directions
+        ctx.rk_step(dt, want_dt=False)
+        ctx.rk_step_vjp(Ud, dt, Ud.clone())
+    ctx.set_state(Ud)
+    s = torch.cuda.current_stream()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(steps):
+        ctx.rk_step(dt, want_dt=False)
+        states.append(ctx.get_state())
+    e1.record(s)
+    lam = torch.ones_like(Ud)
+    for k in range(steps - 1, -1, -1):
+        lam = ctx.rk_step_vjp(states[k], dt, lam)
+    e2.record(s)
+    torch.cuda.synchronize()
+    fwd, bwd = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    dofs = W.n_dofs(prob)
+    ctx.close()
+    return {"workload": "temporal mixing layer, 16^3 elements, N=4, 3 species, viscous, LLF, pattern frozen",
+            "steps": steps, "dofs": dofs, "forward_ms_per_step": fwd / steps, "adjoint_ms_per_step": bwd / steps,
+            "adjoint_over_forward": bwd / fwd,
+            "note": "adjoint step = 2 forward stages (recomputed stage states) + 3 vector-Jacobian products"}
+
+
+def batched_comparison(steps=5):
+    """256 independent periodic domains of 2^3..8^3 elements, one degree
+    N in 1..7 per domain, 3 species: DOF-stage/s of SSP-RK3 steps (fixed dt)
+    in one context with one launch per kernel (as run), the same with the
+    volume tiles autotuned, one launch per degree bin, and one context per
+    domain stepped in a loop."""
+    import torch
+    from paper_2502_19342_gb300 import dgfv, workloads as W
+    prob, U = W.batched_domains()
+    dofs = W.n_dofs(prob)
+    s = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()  # warm-up (graph capture, autotuned tiles)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    ctx = dgfv.Context(prob, N_min=1, N_max=7)
+    Ud = torch.from_numpy(U).cuda()
+    dt = 0.5 * ctx.compute_dt(Ud)[0]
+    res = {}
+    for name, mode in (("batched", 0), ("per_degree_loop", 1)):
+        ctx.set_launch_mode(mode)
+        ctx.set_state(Ud)
+        ms = timed(lambda: ctx.rk_steps(steps, dt, want_dt=False))
+        res[name] = dofs * 3 * steps / (ms * 1e-3)
+    ctx.set_launch_mode(0)
+    ctx.set_state(Ud)
+    tuned = ctx.autotune()
+    ctx.set_state(Ud)
+    res["batched_autotuned"] = dofs * 3 * steps / (timed(lambda: ctx.rk_steps(steps, dt, want_dt=False)) * 1e-3)
+    ctx.close()
+    subs = []
+    for sub, sl in W.domain_slices(prob):
+        c = dgfv.Context(sub, N_min=1, N_max=7)
+        c.set_state(Ud[sl].contiguous())
+        subs.append(c)
+
+    def loop():
+        for _ in range(steps):
+            for c in subs:
+                c.rk_step(dt, want_dt=False)
+
+    res["per_domain_loop"] = dofs * 3 * steps / (timed(loop) * 1e-3)
+    for c in subs:
+        c.close()
+    return {"workload": "256 periodic domains, 2^3..8^3 elements, N in 1..7 per domain, 3 species, viscous",
+            "dofs": dofs, "steps": steps, "unit": "DOF-stage/s",
+            **{k: round(v, 1) for k, v in res.items()},
+            "autotuned_elements_per_tile": tuned}
 
 
 def run_reference(args, rank, world):
@@ -314,6 +411,8 @@ def main():
                 "flops_per_dof": {"total": per_dof, main_k: per_step[KERNEL_STEP[main_k]]},
                 "whole_rhs_tflops": per_dof * units / (ms * 1e-3) / 1e12}
         cpu = None if args.no_cpu else cpu_baseline(dict(prob, N=N_now, fv=fv_now))
+        adjoint = adjoint_cost()
+        batched = None if args.no_batched else batched_comparison()
         launches = int(sum(v[1] for v in prof.values()))
         last = pattern[-1]
         line = {"metric": "DOF-stage updates/s (FP64 RHS, hp-mixed)", "value": value, "unit": "DOF-stage/s",
@@ -325,7 +424,8 @@ def main():
                            "dofs_last_step": int(last["mean_dofs"] * ctx.n_elem), "fv_elements": last["n_fv"],
                            "degree_histogram": last["hist"], "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (state ~1.2 GB)"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "adjoint": adjoint,
+                "batched_domains": batched,
                 "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
                 "clocks": clk.summary()}
         print(json.dumps(line))

@@ -204,6 +204,19 @@ int dgfv_adapt(dgfv_ctx* ctx, dgfv_adapt_stats* stats, void* stream);
 int dgfv_profile_enable(dgfv_ctx* ctx, int on);
 int dgfv_profile_read(dgfv_ctx* ctx, double* ms, int64_t* launches, int cap);
 
+/* Launch organisation of the element and conforming-face kernels: mode 0 (the
+ * default) issues one launch per kernel covering every degree (tiles of
+ * elements of one degree, the degree read per tile); mode 1 issues one launch
+ * per degree bin, the loop a per-degree implementation would run.  Results
+ * are identical. */
+int dgfv_set_launch_mode(dgfv_ctx* ctx, int mode);
+
+/* Chooses, for every degree present, the number of elements per tile of the
+ * volume kernel by timing candidates (64 to 2048 nodes per tile) on the
+ * context's state, and keeps the fastest.  per_tile_out (host, 9 entries,
+ * may be NULL) receives the choice per point count n = N+1.  Synchronises. */
+int dgfv_autotune(dgfv_ctx* ctx, int* per_tile_out, void* stream);
+
 /* Device status word: DGFV_OK or the first error a kernel recorded; clears it. */
 int dgfv_sync_status(dgfv_ctx* ctx, void* stream);
 

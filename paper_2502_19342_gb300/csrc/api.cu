@@ -23,11 +23,14 @@ namespace {
 struct TileSet {
     std::vector<int32_t> first, count, items;
     std::vector<uint8_t> n;
+    std::vector<int> bin_first, bin_count;  // consecutive tiles of one point count
+    std::vector<size_t> bin_smem;
     int32_t *d_first = nullptr, *d_count = nullptr, *d_items = nullptr;
     uint8_t* d_n = nullptr;
     int ntiles = 0;
     size_t smem = 0;
     Tiles view() const { return Tiles{d_first, d_count, d_n, d_items}; }
+    Tiles view(int tile0) const { return Tiles{d_first + tile0, d_count + tile0, d_n + tile0, d_items}; }
 };
 
 struct FaceList {
@@ -39,10 +42,12 @@ struct FaceList {
 struct FaceTileSet {
     std::vector<int32_t> first, count, items;
     std::vector<uint8_t> nc, d;
+    std::vector<int> bin_first, bin_count;  // consecutive tiles of one (direction, point count)
     int32_t *d_first = nullptr, *d_count = nullptr, *d_items = nullptr;
     uint8_t *d_nc = nullptr, *d_d = nullptr;
     int ntiles = 0;
     FaceTiles view() const { return FaceTiles{d_first, d_count, d_nc, d_d, d_items}; }
+    FaceTiles view(int t0) const { return FaceTiles{d_first + t0, d_count + t0, d_nc + t0, d_d + t0, d_items}; }
 };
 
 enum Kernel { K_PROLONG = 0, K_FV, K_LIFT, K_VOLUME, K_FLUX, K_SURFACE, K_DT, K_INDICATOR, K_REMAP, K_COUNT };
@@ -93,6 +98,8 @@ struct dgfv_ctx {
     FaceList lift, flux;    // flux: faces that change representation
     FaceTileSet conf;       // faces with one representation on both sides
     int n_fv_elems = 0;
+    int launch_mode = 0;           // 0: one launch per kernel; 1: one launch per degree bin
+    int vol_per_tile[MAXP + 1] = {};  // elements per volume tile (0: default), set by the autotuner
     bool state_valid = false;
     std::string err;
     // graph of one RK step
@@ -213,12 +220,15 @@ int upload_tiles(dgfv_ctx* c, TileSet& t) {
 template <class Sel, class Per>
 void make_tiles(const dgfv_ctx* c, TileSet& t, Sel sel, Per per_tile) {
     t.first.clear(); t.count.clear(); t.items.clear(); t.n.clear();
+    t.bin_first.clear(); t.bin_count.clear();
     for (int n = 1; n <= MAXP; ++n) {
         std::vector<int32_t> group;
         for (int e = 0; e < c->n_elem; ++e)
             if (c->npts[e] == n && sel(e)) group.push_back(e);
         if (group.empty()) continue;
         const int per = std::max(1, per_tile(n));
+        t.bin_first.push_back((int)t.first.size());
+        t.bin_count.push_back((int)((group.size() + per - 1) / per));
         for (size_t s = 0; s < group.size(); s += per) {
             const int cnt = (int)std::min<size_t>(per, group.size() - s);
             t.first.push_back((int32_t)t.items.size());
@@ -229,8 +239,10 @@ void make_tiles(const dgfv_ctx* c, TileSet& t, Sel sel, Per per_tile) {
     }
 }
 
-// Elements per volume tile: about 256 nodes per CTA.
-int volume_per_tile(int n) { return std::max(1, 256 / (n * n * n)); }
+// Elements per volume tile: about 256 nodes per CTA unless autotuned.
+int volume_per_tile(const dgfv_ctx* c, int n) {
+    return c->vol_per_tile[n] > 0 ? c->vol_per_tile[n] : std::max(1, 256 / (n * n * n));
+}
 
 int apply_layout(dgfv_ctx* c) {
     const int ne = c->n_elem;
@@ -257,11 +269,16 @@ int apply_layout(dgfv_ctx* c) {
     CK(cudaMemcpy(c->d_fo, c->fo.data(), ne * sizeof(int64_t), cudaMemcpyHostToDevice));
     // tiles
     make_tiles(c, c->all, [](int) { return true; }, [](int n) { return std::max(1, 512 / (n * n * n)); });
-    make_tiles(c, c->dg, [&](int e) { return !c->fv[e]; }, volume_per_tile);
+    make_tiles(c, c->dg, [&](int e) { return !c->fv[e]; }, [&](int n) { return volume_per_tile(c, n); });
     make_tiles(c, c->fvt, [&](int e) { return c->fv[e] != 0; }, [](int) { return 1; });
     size_t sm = 0;
-    for (int t = 0; t < (int)c->dg.first.size(); ++t)
-        sm = std::max(sm, volume_smem_bytes(c->nk, c->dg.n[t], c->dg.count[t]));
+    c->dg.bin_smem.assign(c->dg.bin_first.size(), 0);
+    for (size_t b = 0; b < c->dg.bin_first.size(); ++b)
+        for (int t = c->dg.bin_first[b]; t < c->dg.bin_first[b] + c->dg.bin_count[b]; ++t) {
+            const size_t x = volume_smem_bytes(c->nk, c->dg.n[t], c->dg.count[t]);
+            c->dg.bin_smem[b] = std::max(c->dg.bin_smem[b], x);
+            sm = std::max(sm, x);
+        }
     c->dg.smem = sm;
     size_t asm_ = 0;
     for (int t = 0; t < (int)c->dg.first.size(); ++t)
@@ -287,10 +304,15 @@ int apply_layout(dgfv_ctx* c) {
     {
         FaceTileSet& t = c->conf;
         t.first.clear(); t.count.clear(); t.items.clear(); t.nc.clear(); t.d.clear();
+        t.bin_first.clear(); t.bin_count.clear();
         for (int d = 0; d < 3; ++d)
             for (int n = 1; n <= MAXP; ++n) {
                 const auto& g = conf_by[d][n];
                 const int per = std::max(1, 256 / (n * n));
+                if (!g.empty()) {
+                    t.bin_first.push_back((int)t.first.size());
+                    t.bin_count.push_back((int)((g.size() + per - 1) / per));
+                }
                 for (size_t s0 = 0; s0 < g.size(); s0 += per) {
                     const int cnt = (int)std::min<size_t>(per, g.size() - s0);
                     t.first.push_back((int32_t)t.items.size());
@@ -333,16 +355,44 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
                    cudaStream_t s) {
     const Params P = params(c);
     const Faces F{c->d_faceL, c->d_faceR, c->d_faceD};
-    { Timed t(c, K_PROLONG, s); launch_prolong(c->nk, P, c->all.view(), c->all.ntiles, Uin, s); }
+    const bool per_bin = c->launch_mode == 1;
+    {
+        Timed t(c, K_PROLONG, s);
+        if (per_bin)
+            for (size_t bi = 0; bi < c->all.bin_first.size(); ++bi)
+                launch_prolong(c->nk, P, c->all.view(c->all.bin_first[bi]), c->all.bin_count[bi], Uin, s);
+        else
+            launch_prolong(c->nk, P, c->all.view(), c->all.ntiles, Uin, s);
+    }
     if (c->n_fv_elems) { Timed t(c, K_FV, s); launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, Uin, s); }
     if (c->ph.viscous) { Timed t(c, K_LIFT, s); launch_face_lift(c->nk, P, F, c->lift.d, c->lift.count, s); }
-    if (c->dg.ntiles) { Timed t(c, K_VOLUME, s); launch_dg_volume(c->nk, P, c->dg.view(), c->dg.ntiles, c->dg.smem, Uin, s); }
+    if (c->dg.ntiles) {
+        Timed t(c, K_VOLUME, s);
+        if (per_bin)
+            for (size_t bi = 0; bi < c->dg.bin_first.size(); ++bi)
+                launch_dg_volume(c->nk, P, c->dg.view(c->dg.bin_first[bi]), c->dg.bin_count[bi], c->dg.bin_smem[bi],
+                                 Uin, s);
+        else
+            launch_dg_volume(c->nk, P, c->dg.view(), c->dg.ntiles, c->dg.smem, Uin, s);
+    }
     {
         Timed t(c, K_FLUX, s);
-        launch_face_flux_conf(c->nk, P, F, c->conf.view(), c->conf.ntiles, s);
+        if (per_bin)
+            for (size_t bi = 0; bi < c->conf.bin_first.size(); ++bi)
+                launch_face_flux_conf(c->nk, P, F, c->conf.view(c->conf.bin_first[bi]), c->conf.bin_count[bi], s);
+        else
+            launch_face_flux_conf(c->nk, P, F, c->conf.view(), c->conf.ntiles, s);
         launch_face_flux(c->nk, P, F, c->flux.d, c->flux.count, s);
     }
-    { Timed t(c, K_SURFACE, s); launch_surface(c->nk, P, c->all.view(), c->all.ntiles, Uin, U0, out, mode, a, b, c->d_dt3, s); }
+    {
+        Timed t(c, K_SURFACE, s);
+        if (per_bin)
+            for (size_t bi = 0; bi < c->all.bin_first.size(); ++bi)
+                launch_surface(c->nk, P, c->all.view(c->all.bin_first[bi]), c->all.bin_count[bi], Uin, U0, out, mode,
+                               a, b, c->d_dt3, s);
+        else
+            launch_surface(c->nk, P, c->all.view(), c->all.ntiles, Uin, U0, out, mode, a, b, c->d_dt3, s);
+    }
 }
 
 void enqueue_rk_step(dgfv_ctx* c, double dt, cudaStream_t s) {
@@ -840,6 +890,71 @@ int dgfv_profile_read(dgfv_ctx* c, double* ms, int64_t* launches, int cap) {
         if (launches) launches[k] = (int64_t)c->prof.used[k];
     }
     return nk;
+}
+
+int dgfv_set_launch_mode(dgfv_ctx* c, int mode) {
+    if (!c || (mode != 0 && mode != 1)) return DGFV_ERR_ARG;
+    c->launch_mode = mode;
+    c->graph_valid = false;
+    return DGFV_OK;
+}
+
+int dgfv_autotune(dgfv_ctx* c, int* per_tile_out, void* stream) {
+    if (!c) return DGFV_ERR_ARG;
+    if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "autotune before set_state");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Params P0 = params(c);
+    const Faces F{c->d_faceL, c->d_faceR, c->d_faceD};
+    // face values and lifting values of the current state, read by the volume kernel
+    launch_prolong(c->nk, P0, c->all.view(), c->all.ntiles, c->d_U, s);
+    if (c->n_fv_elems) launch_fv(c->nk, P0, c->fvt.view(), c->fvt.ntiles, c->d_U, s);
+    if (c->ph.viscous) launch_face_lift(c->nk, P0, F, c->lift.d, c->lift.count, s);
+    CK(cudaStreamSynchronize(s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best_all[MAXP + 1] = {};
+    for (int n = 1; n <= MAXP; ++n) {
+        int cnt = 0;
+        for (int e = 0; e < c->n_elem; ++e) cnt += (!c->fv[e] && c->npts[e] == n);
+        if (cnt == 0) continue;
+        double best_ms = 1e300;
+        int best = 0, last = -1;
+        for (int nodes : {64, 128, 256, 512, 1024, 2048}) {
+            const int per = std::max(1, nodes / (n * n * n));
+            if (per == last) continue;
+            last = per;
+            if (per > 1 && per * n * n * n > 2048) continue;
+            if (volume_smem_bytes(c->nk, n, per) > 200 * 1024) continue;
+            c->vol_per_tile[n] = per;
+            TileSet& t = c->dg;
+            make_tiles(c, t, [&](int e) { return !c->fv[e] && c->npts[e] == n; }, [&](int) { return per; });
+            TRY(upload_tiles(c, t));
+            const size_t sm = volume_smem_bytes(c->nk, n, per);
+            const Params P = params(c);
+            launch_dg_volume(c->nk, P, t.view(), t.ntiles, sm, c->d_U, s);  // warm
+            CK(cudaEventRecord(e0, s));
+            for (int r = 0; r < 3; ++r) launch_dg_volume(c->nk, P, t.view(), t.ntiles, sm, c->d_U, s);
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = per;
+            }
+        }
+        best_all[n] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int n = 1; n <= MAXP; ++n) {
+        c->vol_per_tile[n] = best_all[n];
+        if (per_tile_out) per_tile_out[n] = best_all[n];
+    }
+    if (per_tile_out) per_tile_out[0] = 0;
+    TRY(apply_layout(c));
+    return DGFV_OK;
 }
 
 int dgfv_sync_status(dgfv_ctx* c, void* stream) {

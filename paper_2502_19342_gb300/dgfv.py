@@ -22,7 +22,7 @@ SYMBOLS = ["dgfv_init_mesh", "dgfv_num_elements", "dgfv_set_degrees", "dgfv_get_
            "dgfv_compute_dt", "dgfv_rk_step", "dgfv_rk_steps", "dgfv_indicator", "dgfv_adapt", "dgfv_sync_status",
            "dgfv_status_string", "dgfv_last_error", "dgfv_destroy", "dgfv_bank_entry", "dgfv_probe_dfma",
            "dgfv_profile_enable", "dgfv_profile_read", "dgfv_compute_dt_noalloc", "dgfv_rhs_vjp",
-           "dgfv_rk_step_vjp"]
+           "dgfv_rk_step_vjp", "dgfv_set_launch_mode", "dgfv_autotune"]
 KERNELS = ["prolong", "fv", "face_lift", "dg_volume", "face_flux", "surface", "dt", "indicator", "remap"]
 
 
@@ -69,6 +69,8 @@ def lib():
         L.dgfv_compute_dt.argtypes = [vp, vp, dp, vp]
         L.dgfv_compute_dt_noalloc.argtypes = [vp, vp, vp, vp]
         L.dgfv_rhs_vjp.argtypes = [vp, vp, vp, vp, vp]
+        L.dgfv_set_launch_mode.argtypes = [vp, C.c_int]
+        L.dgfv_autotune.argtypes = [vp, C.POINTER(C.c_int), vp]
         L.dgfv_rk_step_vjp.argtypes = [vp, vp, C.c_double, vp, vp, vp]
         L.dgfv_rk_step.argtypes = [vp, C.c_double, dp, vp]
         L.dgfv_rk_steps.argtypes = [vp, C.c_int, C.c_double, dp, vp]
@@ -301,6 +303,16 @@ class Context:
 
     def sync_status(self, stream=None):
         self._rc(lib().dgfv_sync_status(self.h, _stream(stream)), "device status")
+
+    def set_launch_mode(self, per_degree):
+        """False: one launch per kernel over all degrees; True: one launch per degree bin."""
+        self._rc(lib().dgfv_set_launch_mode(self.h, int(bool(per_degree))), "set_launch_mode")
+
+    def autotune(self, stream=None):
+        """Time candidate tile sizes of the volume kernel per degree; returns {N: elements per tile}."""
+        out = (C.c_int * 9)()
+        self._rc(lib().dgfv_autotune(self.h, out, _stream(stream)), "autotune")
+        return {n - 1: out[n] for n in range(1, 9) if out[n] > 0}
 
     def profile_enable(self, on=True):
         self._rc(lib().dgfv_profile_enable(self.h, int(on)), "profile_enable")

@@ -375,5 +375,62 @@ def _assemble(prob, pts):
     return U
 
 
+def mixing_layer(seed=0, nel=(16, 16, 16), N=4, delta=0.05, U0=0.5, amp=1e-2, mu=1e-3):
+    """Temporal mixing layer for the adjoint: [0,1]^3 periodic, 16^3 elements,
+    uniform N = 4, 3 species (air/CO2/helium).  A periodic pair of shear
+    layers at y = 1/4 and 3/4 (tanh of thickness delta) carries v_x = +-U0 and
+    the species: CO2 between the layers, air outside, 10 % helium everywhere;
+    seeded random-phase velocity perturbations of amplitude amp; p = 1, uniform T."""
+    sp = species_set([AIR, CO2, HELIUM], mu=mu)
+    prob = make_problem([(nel, (0, 0, 0), (1, 1, 1))], sp, n_fv=N + 1, N=N)
+    rng = np.random.default_rng(seed)
+    ks = [(a, b, c) for a in range(1, 3) for b in range(1, 3) for c in range(0, 3)]
+    ph = rng.uniform(0, 2 * np.pi, (3, len(ks)))
+    T0 = 1.0 / sp["Rgas"][0]
+
+    def fn(x, y, z):
+        s = 0.5 * (np.tanh((y - 0.25) / delta) - np.tanh((y - 0.75) / delta))  # 1 between the layers
+        pert = [amp * sum(np.sin(2 * np.pi * (a * x + b * y + c * z) + ph[q, m]) for m, (a, b, c) in enumerate(ks))
+                / len(ks) for q in range(3)]
+        Y2 = 0.8 * s + 0.05
+        Y3 = 0.1 + 0 * x
+        Y1 = 1.0 - Y2 - Y3
+        Rm = Y1 * sp["Rgas"][0] + Y2 * sp["Rgas"][1] + Y3 * sp["Rgas"][2]
+        rho = 1.0 / (Rm * T0)
+        vx = U0 * (2 * s - 1) + pert[0]
+        return [rho * Y1, rho * Y2, rho * Y3], (vx, pert[1], pert[2]), np.ones_like(x)
+
+    return prob, build_state(prob, fn)
+
+
+def batched_domains(seed=0, n_domains=256, mu=5e-4):
+    """Many independent periodic domains in one context: n_d^3 elements with
+    n_d drawn from {2..8} and one degree N_d from {1..7} per domain, 3 species,
+    smooth random-phase states (unit boxes)."""
+    rng = np.random.default_rng(seed)
+    sp = species_set([AIR, CO2, HELIUM], mu=mu)
+    doms, N = [], []
+    for _ in range(n_domains):
+        nd = int(rng.integers(2, 9))
+        doms.append(((nd, nd, nd), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)))
+        N += [int(rng.integers(1, 8))] * nd ** 3
+    prob = make_problem(doms, sp, n_fv=8, N=np.array(N, np.int8))
+    return prob, smooth_random_state(prob, seed, amp=0.05)
+
+
+def domain_slices(prob):
+    """Per domain: (problem of that domain alone, slice of the batched state)."""
+    off, size = offsets(prob)
+    out, e0 = [], 0
+    for d, dm in enumerate(prob["dims"]):
+        ne = int(np.prod(dm))
+        sub = dict(prob, dims=prob["dims"][d:d + 1], lo=prob["lo"][d:d + 1], hi=prob["hi"][d:d + 1],
+                   N=prob["N"][e0:e0 + ne].copy(), fv=prob["fv"][e0:e0 + ne].copy())
+        end = off[e0 + ne] if e0 + ne < len(off) else size
+        out.append((sub, slice(int(off[e0]), int(end))))
+        e0 += ne
+    return out
+
+
 # Indicator thresholds {T_fv_on, T_fv_off, T_ref, T_crs} (configuration values).
 THRESHOLDS = (2.0, 3.0, 3.5, 7.0)

@@ -223,3 +223,31 @@ def test_rejects_bad_arguments():
     with pytest.raises(dgfv.DgfvError):
         ctx.rk_step(-1.0)  # no state yet
     ctx.close()
+
+
+def test_launch_modes_and_autotuned_tiles_give_identical_results(oracle):
+    """One launch per kernel, one launch per degree bin, and autotuned volume
+    tiles run the same per-element arithmetic: bitwise equal results."""
+    sp = W.species_set([W.AIR, W.HELIUM, W.CO2], mu=1e-3)
+    rng = np.random.default_rng(31)
+    doms, N = [], []
+    for _ in range(12):
+        nd = int(rng.integers(1, 4))
+        doms.append(((nd, nd, nd), (0, 0, 0), (1, 1, 1)))
+        N += [int(rng.integers(1, 8))] * nd ** 3
+    prob = W.make_problem(doms, sp, n_fv=8, N=np.array(N, np.int8))
+    U = W.smooth_random_state(prob, 31, amp=0.05)
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    Ud = to_dev(U)
+    R0 = ctx.eval_rhs(Ud).cpu().numpy()
+    ctx.set_launch_mode(True)
+    R1 = ctx.eval_rhs(Ud).cpu().numpy()
+    ctx.set_launch_mode(False)
+    ctx.set_state(Ud)
+    tuned = ctx.autotune()
+    assert set(tuned) == set(int(x) for x in np.unique(prob["N"]))
+    R2 = ctx.eval_rhs(Ud).cpu().numpy()
+    np.testing.assert_array_equal(R1, R0)
+    np.testing.assert_array_equal(R2, R0)
+    assert_rhs_close(oracle, prob, U, R0)
+    ctx.close()
