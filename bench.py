@@ -182,25 +182,39 @@ def adjoint_cost(steps=10):
         ctx.rk_step_vjp(Ud, dt, Ud.clone())
     ctx.set_state(Ud)
     s = torch.cuda.current_stream()
-    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     torch.cuda.synchronize()
-    e0.record(s)
-    for _ in range(steps):
+    ev[0].record(s)
+    for _ in range(steps):  # forward, one checkpoint per step
         ctx.rk_step(dt, want_dt=False)
         states.append(ctx.get_state())
-    e1.record(s)
+    ev[1].record(s)
     lam = torch.ones_like(Ud)
-    for k in range(steps - 1, -1, -1):
+    for k in range(steps - 1, -1, -1):  # adjoint, stage states recomputed
         lam = ctx.rk_step_vjp(states[k], dt, lam)
-    e2.record(s)
+    ev[2].record(s)
+    stages = []
+    ctx.set_state(Ud)
+    for k in range(steps):  # forward keeping the stage states
+        s1, s2 = torch.empty_like(Ud), torch.empty_like(Ud)
+        ctx.rk_step_save(dt, s1, s2)
+        stages.append((states[k], s1, s2))
+    ev[3].record(s)
+    lam2 = torch.ones_like(Ud)
+    for k in range(steps - 1, -1, -1):  # adjoint from the stored stage states
+        lam2 = ctx.rk_step_vjp_stages(stages[k], dt, lam2)
+    ev[4].record(s)
     torch.cuda.synchronize()
-    fwd, bwd = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    fwd, bwd, bwd2 = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[3].elapsed_time(ev[4])
+    same = bool(torch.equal(lam, lam2))
     dofs = W.n_dofs(prob)
     ctx.close()
     return {"workload": "temporal mixing layer, 16^3 elements, N=4, 3 species, viscous, LLF, pattern frozen",
-            "steps": steps, "dofs": dofs, "forward_ms_per_step": fwd / steps, "adjoint_ms_per_step": bwd / steps,
-            "adjoint_over_forward": bwd / fwd,
-            "note": "adjoint step = 2 forward stages (recomputed stage states) + 3 vector-Jacobian products"}
+            "steps": steps, "dofs": dofs, "forward_ms_per_step": fwd / steps,
+            "adjoint_ms_per_step_stored_stages": bwd2 / steps, "adjoint_over_forward": bwd2 / fwd,
+            "adjoint_ms_per_step_recomputed_stages": bwd / steps, "adjoint_over_forward_recomputed": bwd / fwd,
+            "gradients_identical": same,
+            "note": "adjoint step = 3 vector-Jacobian products (+2 forward stages when the stages are recomputed)"}
 
 
 def batched_comparison(steps=5):

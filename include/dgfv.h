@@ -182,6 +182,17 @@ int dgfv_rhs_vjp(dgfv_ctx* ctx, const double* d_U, const double* d_Rbar, double*
 int dgfv_rk_step_vjp(dgfv_ctx* ctx, const double* d_U0, double dt, const double* d_Ubar_next, double* d_Ubar,
                      void* stream);
 
+/* One SSP-RK3 step of size dt > 0 of the context's state that also copies the
+ * two intermediate stage states U1, U2 into caller-owned device arrays (for
+ * dgfv_rk_step_vjp_stages). */
+int dgfv_rk_step_save(dgfv_ctx* ctx, double dt, double* d_stage1, double* d_stage2, void* stream);
+
+/* Adjoint of one SSP-RK3 step from stored stage states: d_stages = {U0, U1,
+ * U2} (device arrays), otherwise as dgfv_rk_step_vjp without recomputing the
+ * stages. */
+int dgfv_rk_step_vjp_stages(dgfv_ctx* ctx, const double* const* d_stages, double dt, const double* d_Ubar_next,
+                            double* d_Ubar, void* stream);
+
 /* Modal indicator of Sec. 3.4 on the state d_U: per element I_p = I(rho),
  * I_h = min(I(p), I(Y_k)) (device arrays of n_elem doubles, may be NULL) and
  * the decision code (device array of n_elem bytes, may be NULL):

@@ -228,22 +228,22 @@ __global__ void __launch_bounds__(64) k_adj_face_mixed(Params P, AdjBuffers A, F
     }
 }
 
-// k_adj_volume: per tile of DG elements (shared memory 6V n^3 doubles per element).
-//   g (lifted gradient) is recomputed from U and U*;
-//   F_bar_d = -rh_d Dhat^T R_bar (volume integral^T);
-//   nodal-flux reverse -> U_bar (direct part), g_bar;
-//   g_bar += trace^T of the face gradient adjoints;
-//   lifting^T: U_bar += rh_d Dhat^T g_bar^d, U*_bar = +-rh_d lhat^{+-}^T g_bar^d.
+// Volume adjoint in two kernels around the face adjoint.
+// k_adj_vol_a: per tile of DG elements (shared memory 6V n^3 doubles per element):
+//   g (lifted gradient) recomputed from U and U*, its face traces written for
+//   the face adjoint; F_bar_d = -rh_d Dhat^T R_bar (volume integral^T);
+//   nodal-flux reverse -> U_bar (direct part) and g_bar (to global scratch).
 template <int NK>
-__global__ void __launch_bounds__(256) k_adj_volume(Params P, AdjBuffers A, Tiles T, const double* __restrict__ U,
-                                                    const double* __restrict__ Rb, double* __restrict__ Ub) {
+__global__ void __launch_bounds__(256) k_adj_vol_a(Params P, Tiles T, const double* __restrict__ U,
+                                                   const double* __restrict__ Rb, double* __restrict__ Ub,
+                                                   double* __restrict__ gvol) {
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
     const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
     const int n2 = n * n, n3 = n2 * n;
     double* sD = sm;
-    double* sl = sD + n * n;          // lm, lp, lhm, lhp
-    double* sG = sl + 4 * n;          // count * 3V n^3: g, then g_bar
+    double* sl = sD + n * n;               // lm, lp, lhm, lhp
+    double* sG = sl + 4 * n;               // count * 3V n^3: g
     double* sF = sG + count * 3 * V * n3;  // count * 3V n^3: F_bar
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) sD[i] = B(P, P.bi.dhat[n])[i];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -263,12 +263,11 @@ __global__ void __launch_bounds__(256) k_adj_volume(Params P, AdjBuffers A, Tile
         const int a = d == 0 ? j : i, b = d == 2 ? j : k;
         const int p = a + n * b;
         const double rh = P.t.rh[3 * e + d];
-        // F_bar_d at node (m0 along d) = -rh sum_i Dhat[i][m0] R_bar[i along d]
         const double* rsrc = Rb + P.t.off[e] + (int64_t)v * n3;
         double fb = 0.0;
         for (int q = 0; q < n; ++q) fb = fma(sD[q * n + m0], rsrc[node_index(n, d, q, a, b)], fb);
         sF[el * per + r] = -rh * fb;
-        if (visc) {  // lifted gradient (forward recompute)
+        if (visc) {
             const double* src = U + P.t.off[e] + (int64_t)v * n3;
             const int64_t fo = P.t.fo[e];
             double s = 0.0;
@@ -279,7 +278,19 @@ __global__ void __launch_bounds__(256) k_adj_volume(Params P, AdjBuffers A, Tile
         }
     }
     __syncthreads();
-    // nodal reverse
+    if (visc) {  // gradient traces for the face adjoint
+        const int pt = 6 * 3 * V * n2;
+        for (int idx = threadIdx.x; idx < count * pt; idx += blockDim.x) {
+            const int el = idx / pt, r = idx % pt, f = r / (3 * V * n2), r2 = r % (3 * V * n2), x = r2 / n2, p = r2 % n2;
+            const int e = T.items[first + el];
+            const int d = f >> 1, a = p % n, b = p / n;
+            const double* lb = sl + ((f & 1) ? n : 0);
+            const double* src = sG + el * per + x * n3;
+            double s = 0.0;
+            for (int m = 0; m < n; ++m) s = fma(lb[m], src[node_index(n, d, m, a, b)], s);
+            P.b.fg[(P.t.fo[e] + (int64_t)f * n2) * 3 * V + x * n2 + p] = s;
+        }
+    }
     for (int idx = threadIdx.x; idx < count * n3; idx += blockDim.x) {
         const int el = idx / n3, c = idx % n3;
         const int e = T.items[first + el];
@@ -296,17 +307,37 @@ __global__ void __launch_bounds__(256) k_adj_volume(Params P, AdjBuffers A, Tile
         for (int v = 0; v < V; ++v) Ub[P.t.off[e] + (int64_t)v * n3 + c] = ub[v];
         if (visc)
 #pragma unroll
-            for (int x = 0; x < 3 * V; ++x) sG[el * per + x * n3 + c] = gb[x];
+            for (int x = 0; x < 3 * V; ++x) gvol[3 * P.t.off[e] + (int64_t)x * n3 + c] = gb[x];
+    }
+}
+
+// k_adj_vol_b (viscous only): g_bar += trace^T of the face gradient adjoints;
+// lifting^T: U_bar += rh_d Dhat^T g_bar^d and U*_bar = +-rh_d lhat^{+-}^T g_bar^d.
+template <int NK>
+__global__ void __launch_bounds__(256) k_adj_vol_b(Params P, AdjBuffers A, Tiles T, const double* __restrict__ gvol,
+                                                   double* __restrict__ Ub) {
+    constexpr int V = NK + 4;
+    extern __shared__ double sm[];
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
+    const int n2 = n * n, n3 = n2 * n;
+    double* sD = sm;
+    double* sl = sD + n * n;
+    double* sG = sl + 4 * n;  // count * 3V n^3: g_bar
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) sD[i] = B(P, P.bi.dhat[n])[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        sl[i] = B(P, P.bi.lm[n])[i];
+        sl[n + i] = B(P, P.bi.lp[n])[i];
+        sl[2 * n + i] = B(P, P.bi.lhm[n])[i];
+        sl[3 * n + i] = B(P, P.bi.lhp[n])[i];
     }
     __syncthreads();
-    if (!visc) return;
-    // g_bar += trace^T of the face gradient adjoints (6 faces, 3V components)
+    const int per = 3 * V * n3;
     for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
         const int el = idx / per, r = idx % per, x = r / n3, c = r % n3;
         const int e = T.items[first + el];
         const int ijk[3] = {c % n, (c / n) % n, c / n2};
         const int64_t fo = P.t.fo[e];
-        double acc = sG[el * per + r];
+        double acc = gvol[3 * P.t.off[e] + r];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const int m0 = ijk[d];
@@ -317,7 +348,6 @@ __global__ void __launch_bounds__(256) k_adj_volume(Params P, AdjBuffers A, Tile
         sG[el * per + r] = acc;
     }
     __syncthreads();
-    // lifting^T into U_bar (a thread per (v, node): sum over d and the line)
     const int pv = V * n3;
     for (int idx = threadIdx.x; idx < count * pv; idx += blockDim.x) {
         const int el = idx / pv, r = idx % pv, v = r / n3, c = r % n3;
@@ -335,7 +365,6 @@ __global__ void __launch_bounds__(256) k_adj_volume(Params P, AdjBuffers A, Tile
         }
         Ub[P.t.off[e] + r] += acc;
     }
-    // U*_bar on the six faces
     const int pf = 6 * V * n2;
     for (int idx = threadIdx.x; idx < count * pf; idx += blockDim.x) {
         const int el = idx / pf, r = idx % pf, f = r / (V * n2), r2 = r % (V * n2), v = r2 / n2, p = r2 % n2;
@@ -443,11 +472,18 @@ size_t adj_volume_smem_bytes(int nk, int n, int count) {
     return sizeof(double) * (size_t)(n * n + 4 * n + 2 * count * 3 * V * n * n * n);
 }
 
-void launch_adj_volume(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, size_t smem,
-                       const double* U, const double* Rb, double* Ub, cudaStream_t s) {
+void launch_adj_vol_a(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
+                      const double* Rb, double* Ub, double* gvol, cudaStream_t s) {
     if (ntiles <= 0) return;
-    DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_adj_volume<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                       k_adj_volume<NK><<<ntiles, 256, smem, s>>>(P, A, T, U, Rb, Ub)));
+    DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_adj_vol_a<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       k_adj_vol_a<NK><<<ntiles, 256, smem, s>>>(P, T, U, Rb, Ub, gvol)));
+}
+
+void launch_adj_vol_b(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, size_t smem,
+                      const double* gvol, double* Ub, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_adj_vol_b<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       k_adj_vol_b<NK><<<ntiles, 256, smem, s>>>(P, A, T, gvol, Ub)));
 }
 
 void launch_adj_lift(int nk, const Params& P, const AdjBuffers& A, const Faces& F, const int32_t* list, int nfaces,

@@ -112,6 +112,7 @@ struct dgfv_ctx {
     bool adj_ready = false;
     double *d_fbar = nullptr, *d_ubar = nullptr, *d_gbar = nullptr, *d_sbar = nullptr;
     double *d_S1 = nullptr, *d_S2 = nullptr, *d_B1 = nullptr, *d_B2 = nullptr, *d_W = nullptr;
+    double* d_gvol = nullptr;  // nodal gradient adjoint, 3 x state
     size_t adj_smem = 0;
     std::vector<void*> allocs;
 };
@@ -702,6 +703,7 @@ static int adj_prepare(dgfv_ctx* c) {
     TRY(dalloc(c, &c->d_B1, c->cap_state));
     TRY(dalloc(c, &c->d_B2, c->cap_state));
     TRY(dalloc(c, &c->d_W, c->cap_state));
+    TRY(dalloc(c, &c->d_gvol, 3 * c->cap_state));
     c->adj_ready = true;
     return DGFV_OK;
 }
@@ -711,16 +713,17 @@ static void enqueue_vjp(dgfv_ctx* c, const double* U, const double* Rb, double* 
     const Params P = params(c);
     const Faces F{c->d_faceL, c->d_faceR, c->d_faceD};
     const AdjBuffers A{c->d_fbar, c->d_ubar, c->d_gbar, c->d_sbar};
-    // forward face values, lifting values and gradient traces of U
+    // forward face values and lifting values of U
     launch_prolong(c->nk, P, c->all.view(), c->all.ntiles, U, s);
-    if (c->ph.viscous) {
-        launch_face_lift(c->nk, P, F, c->lift.d, c->lift.count, s);
-        launch_dg_volume(c->nk, P, c->dg.view(), c->dg.ntiles, c->dg.smem, U, s);
-    }
+    if (c->ph.viscous) launch_face_lift(c->nk, P, F, c->lift.d, c->lift.count, s);
     launch_adj_surface(c->nk, P, A, c->dg.view(), c->dg.ntiles, Rb, s);
+    // recomputed gradient (and its traces), volume integral^T, nodal reverse
+    launch_adj_vol_a(c->nk, P, c->dg.view(), c->dg.ntiles, c->adj_smem, U, Rb, Ub, c->d_gvol, s);
     launch_adj_faces(c->nk, P, A, F, c->conf.view(), c->conf.ntiles, c->flux.d, c->flux.count, s);
-    launch_adj_volume(c->nk, P, A, c->dg.view(), c->dg.ntiles, c->adj_smem, U, Rb, Ub, s);
-    if (c->ph.viscous) launch_adj_lift(c->nk, P, A, F, c->lift.d, c->lift.count, s);
+    if (c->ph.viscous) {
+        launch_adj_vol_b(c->nk, P, A, c->dg.view(), c->dg.ntiles, c->dg.smem, c->d_gvol, Ub, s);
+        launch_adj_lift(c->nk, P, A, F, c->lift.d, c->lift.count, s);
+    }
     launch_adj_prolong(c->nk, P, A, c->dg.view(), c->dg.ntiles, Ub, s);
 }
 
@@ -733,27 +736,55 @@ int dgfv_rhs_vjp(dgfv_ctx* c, const double* d_U, const double* d_Rbar, double* d
     return DGFV_OK;
 }
 
+static int rk_step_vjp_impl(dgfv_ctx* c, const double* d_U0, const double* d_U1, const double* d_U2, double dt,
+                            const double* d_Ubar_next, double* d_Ubar, cudaStream_t s) {
+    const int64_t n = c->n_state;
+    // U3 = 1/3 U0 + 2/3 (U2 + dt R(U2)), backwards:
+    enqueue_vjp(c, d_U2, d_Ubar_next, c->d_W, s);
+    launch_axpby(n, 2.0 / 3.0, d_Ubar_next, 2.0 / 3.0 * dt, c->d_W, c->d_B2, s);   // U2_bar
+    launch_axpby(n, 1.0 / 3.0, d_Ubar_next, 0.0, d_Ubar_next, d_Ubar, s);          // U0_bar  = 1/3 U3_bar
+    enqueue_vjp(c, d_U1, c->d_B2, c->d_W, s);
+    launch_axpby(n, 0.25, c->d_B2, 0.25 * dt, c->d_W, c->d_B1, s);                  // U1_bar
+    launch_axpby(n, 1.0, d_Ubar, 0.75, c->d_B2, d_Ubar, s);                         // U0_bar += 3/4 U2_bar
+    enqueue_vjp(c, d_U0, c->d_B1, c->d_W, s);
+    launch_axpby(n, 1.0, d_Ubar, 1.0, c->d_B1, d_Ubar, s);                          // += U1_bar
+    launch_axpby(n, 1.0, d_Ubar, dt, c->d_W, d_Ubar, s);                            // += dt J^T U1_bar
+    CK(cudaGetLastError());
+    return DGFV_OK;
+}
+
 int dgfv_rk_step_vjp(dgfv_ctx* c, const double* d_U0, double dt, const double* d_Ubar_next, double* d_Ubar,
                      void* stream) {
     if (!c || !d_U0 || !d_Ubar_next || !d_Ubar || !(dt > 0.0)) return DGFV_ERR_ARG;
     if (d_Ubar == d_Ubar_next || d_Ubar == d_U0) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
     TRY(adj_prepare(c));
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t n = c->n_state;
     // stage states of the step (recomputed from the step's start state)
     launch_set_scalar(c->d_dt3, dt, s);
     enqueue_stage(c, d_U0, d_U0, c->d_S1, 1, 0.0, 1.0, s);       // U1 = U0 + dt R(U0)
     enqueue_stage(c, c->d_S1, d_U0, c->d_S2, 1, 0.75, 0.25, s);  // U2 = 3/4 U0 + 1/4 (U1 + dt R(U1))
-    // U3 = 1/3 U0 + 2/3 (U2 + dt R(U2)), backwards:
-    enqueue_vjp(c, c->d_S2, d_Ubar_next, c->d_W, s);
-    launch_axpby(n, 2.0 / 3.0, d_Ubar_next, 2.0 / 3.0 * dt, c->d_W, c->d_B2, s);   // U2_bar
-    launch_axpby(n, 1.0 / 3.0, d_Ubar_next, 0.0, d_Ubar_next, d_Ubar, s);          // U0_bar  = 1/3 U3_bar
-    enqueue_vjp(c, c->d_S1, c->d_B2, c->d_W, s);
-    launch_axpby(n, 0.25, c->d_B2, 0.25 * dt, c->d_W, c->d_B1, s);                  // U1_bar
-    launch_axpby(n, 1.0, d_Ubar, 0.75, c->d_B2, d_Ubar, s);                         // U0_bar += 3/4 U2_bar
-    enqueue_vjp(c, d_U0, c->d_B1, c->d_W, s);
-    launch_axpby(n, 1.0, d_Ubar, 1.0, c->d_B1, d_Ubar, s);                          // += U1_bar
-    launch_axpby(n, 1.0, d_Ubar, dt, c->d_W, d_Ubar, s);                            // += dt J^T U1_bar
+    return rk_step_vjp_impl(c, d_U0, c->d_S1, c->d_S2, dt, d_Ubar_next, d_Ubar, s);
+}
+
+int dgfv_rk_step_vjp_stages(dgfv_ctx* c, const double* const* d_stages, double dt, const double* d_Ubar_next,
+                            double* d_Ubar, void* stream) {
+    if (!c || !d_stages || !d_stages[0] || !d_stages[1] || !d_stages[2] || !d_Ubar_next || !d_Ubar || !(dt > 0.0))
+        return DGFV_ERR_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (d_Ubar == d_stages[i]) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
+    if (d_Ubar == d_Ubar_next) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
+    TRY(adj_prepare(c));
+    return rk_step_vjp_impl(c, d_stages[0], d_stages[1], d_stages[2], dt, d_Ubar_next, d_Ubar, (cudaStream_t)stream);
+}
+
+int dgfv_rk_step_save(dgfv_ctx* c, double dt, double* d_stage1, double* d_stage2, void* stream) {
+    if (!c || !d_stage1 || !d_stage2 || !(dt > 0.0)) return DGFV_ERR_ARG;
+    if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "rk_step_save before set_state");
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_set_scalar(c->d_dt3, dt, s);
+    enqueue_stage(c, c->d_U, c->d_U, d_stage1, 1, 0.0, 1.0, s);
+    enqueue_stage(c, d_stage1, c->d_U, d_stage2, 1, 0.75, 0.25, s);
+    enqueue_stage(c, d_stage2, c->d_U, c->d_U, 1, 1.0 / 3.0, 2.0 / 3.0, s);
     CK(cudaGetLastError());
     return DGFV_OK;
 }

@@ -22,7 +22,8 @@ SYMBOLS = ["dgfv_init_mesh", "dgfv_num_elements", "dgfv_set_degrees", "dgfv_get_
            "dgfv_compute_dt", "dgfv_rk_step", "dgfv_rk_steps", "dgfv_indicator", "dgfv_adapt", "dgfv_sync_status",
            "dgfv_status_string", "dgfv_last_error", "dgfv_destroy", "dgfv_bank_entry", "dgfv_probe_dfma",
            "dgfv_profile_enable", "dgfv_profile_read", "dgfv_compute_dt_noalloc", "dgfv_rhs_vjp",
-           "dgfv_rk_step_vjp", "dgfv_set_launch_mode", "dgfv_autotune"]
+           "dgfv_rk_step_vjp", "dgfv_set_launch_mode", "dgfv_autotune", "dgfv_rk_step_save",
+           "dgfv_rk_step_vjp_stages"]
 KERNELS = ["prolong", "fv", "face_lift", "dg_volume", "face_flux", "surface", "dt", "indicator", "remap"]
 
 
@@ -72,6 +73,8 @@ def lib():
         L.dgfv_set_launch_mode.argtypes = [vp, C.c_int]
         L.dgfv_autotune.argtypes = [vp, C.POINTER(C.c_int), vp]
         L.dgfv_rk_step_vjp.argtypes = [vp, vp, C.c_double, vp, vp, vp]
+        L.dgfv_rk_step_save.argtypes = [vp, C.c_double, vp, vp, vp]
+        L.dgfv_rk_step_vjp_stages.argtypes = [vp, C.POINTER(vp), C.c_double, vp, vp, vp]
         L.dgfv_rk_step.argtypes = [vp, C.c_double, dp, vp]
         L.dgfv_rk_steps.argtypes = [vp, C.c_int, C.c_double, dp, vp]
         L.dgfv_indicator.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -260,6 +263,28 @@ class Context:
                  "rk_step_vjp")
         return Ubar
 
+    def rk_step_save(self, dt, stage1, stage2, stream=None):
+        """One RK step of size dt; the two intermediate stage states go to stage1, stage2."""
+        n = self.state_size
+        _check_dev(stage1, n)
+        _check_dev(stage2, n)
+        self._rc(lib().dgfv_rk_step_save(self.h, float(dt), _ptr(stage1), _ptr(stage2), _stream(stream)),
+                 "rk_step_save")
+
+    def rk_step_vjp_stages(self, stages, dt, Ubar_next, Ubar=None, stream=None):
+        """Adjoint of one RK step from the stored stage states (U0, U1, U2)."""
+        import torch
+        n = self.state_size
+        for t in stages:
+            _check_dev(t, n)
+        _check_dev(Ubar_next, n)
+        if Ubar is None:
+            Ubar = torch.empty(n, dtype=torch.float64, device="cuda")
+        arr = (C.c_void_p * 3)(*[t.data_ptr() for t in stages])
+        self._rc(lib().dgfv_rk_step_vjp_stages(self.h, arr, float(dt), _ptr(Ubar_next), _ptr(Ubar), _stream(stream)),
+                 "rk_step_vjp_stages")
+        return Ubar
+
     def compute_dt(self, U, stream=None):
         _check_dev(U, self.state_size)
         out = (C.c_double * 3)()
@@ -364,18 +389,27 @@ def rhs_function():
     return RHS
 
 
-def rollout_gradient(ctx, U0, n_steps, dt, loss_grad):
+def rollout_gradient(ctx, U0, n_steps, dt, loss_grad, keep_stages=False):
     """Gradient of a loss of the state after n_steps SSP-RK3 steps of size dt
-    with respect to the initial state, by the adjoint of every step; the state
-    at the start of every step is the only checkpoint (the stage states are
-    recomputed).  loss_grad(U_final) returns dLoss/dU_final."""
+    with respect to the initial state, by the adjoint of every step.
+    keep_stages=False keeps one checkpoint per step (the stage states are
+    recomputed in the backward pass); True keeps all three stage states per
+    step (three times the memory, no recomputation).
+    loss_grad(U_final) returns dLoss/dU_final."""
     import torch
-    states = [U0.clone()]
     ctx.set_state(U0)
+    ckpt = []
     for _ in range(n_steps):
-        ctx.rk_step(dt, want_dt=False)
-        states.append(ctx.get_state())
-    lam = loss_grad(states[-1])
+        U = ctx.get_state()
+        if keep_stages:
+            s1, s2 = torch.empty_like(U), torch.empty_like(U)
+            ctx.rk_step_save(dt, s1, s2)
+            ckpt.append((U, s1, s2))
+        else:
+            ctx.rk_step(dt, want_dt=False)
+            ckpt.append(U)
+    Uf = ctx.get_state()
+    lam = loss_grad(Uf)
     for k in range(n_steps - 1, -1, -1):
-        lam = ctx.rk_step_vjp(states[k], dt, lam)
-    return lam, states[-1]
+        lam = ctx.rk_step_vjp_stages(ckpt[k], dt, lam) if keep_stages else ctx.rk_step_vjp(ckpt[k], dt, lam)
+    return lam, Uf

@@ -165,3 +165,31 @@ def test_adjoint_rejects_fv_patterns():
     with pytest.raises(dgfv.DgfvError):
         ctx.rhs_vjp(to_dev(U), to_dev(np.ones_like(U)))
     ctx.close()
+
+
+def test_stored_stage_adjoint_matches_recomputed_stages():
+    """dgfv_rk_step_save advances the state exactly as dgfv_rk_step and keeps
+    U1, U2; the adjoint from those stored stages equals, bit for bit, the
+    adjoint that recomputes them (same kernels on the same inputs)."""
+    from paper_2502_19342_gb300 import dgfv
+    prob, U = _dg_problem(10, nk=3, nel=(3, 2, 2), uniform=None, mu=2e-3)
+    dt = 2e-4
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    U0 = to_dev(U)
+    ctx.set_state(U0)
+    ctx.rk_step(dt, want_dt=False)
+    ref = ctx.get_state()
+    ctx.set_state(U0)
+    s1, s2 = torch.empty_like(U0), torch.empty_like(U0)
+    ctx.rk_step_save(dt, s1, s2)
+    assert torch.equal(ctx.get_state(), ref)
+    lam = to_dev(np.random.default_rng(10).standard_normal(U.size))
+    a = ctx.rk_step_vjp(U0, dt, lam)
+    b = ctx.rk_step_vjp_stages((U0, s1, s2), dt, lam)
+    assert torch.equal(a, b)
+    with pytest.raises(dgfv.DgfvError):
+        ctx.rk_step_vjp_stages((U0, s1, s2), dt, lam, Ubar=s1)
+    g1, _ = dgfv.rollout_gradient(ctx, U0, 3, dt, lambda Uf: torch.ones_like(Uf))
+    g2, _ = dgfv.rollout_gradient(ctx, U0, 3, dt, lambda Uf: torch.ones_like(Uf), keep_stages=True)
+    assert torch.equal(g1, g2)
+    ctx.close()
