@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-autotune", dest="autotune", action="store_false",
+                   help="keep the default volume-kernel launch instead of timing variants first")
     p.add_argument("--profile-eval", action="store_true",
                    help="after the warm-up cycles run one R(U) evaluation between cudaProfilerStart/Stop "
                         "(for ncu --profile-from-start off) and exit")
@@ -339,6 +341,10 @@ def main():
     for _ in range(args.warmup):
         cycle(ctx)
     torch.cuda.synchronize()
+    tuned = ctx.autotune() if args.autotune else None
+    if tuned is not None:
+        cycle(ctx)  # one more untimed cycle with the tuned volume launches
+        torch.cuda.synchronize()
     if args.profile_eval:
         Ud = ctx.get_state()
         R = torch.empty_like(Ud)
@@ -437,6 +443,7 @@ def main():
                            "step": "adapt + 10 SSP-RK3 steps (30 stages), CFL 0.5",
                            "dofs_last_step": int(last["mean_dofs"] * ctx.n_elem), "fv_elements": last["n_fv"],
                            "degree_histogram": last["hist"], "parallelism": f"replicas x{world}",
+                           "volume_launch": ({str(k): v for k, v in tuned.items()} if tuned else "default"),
                            "l2": "inputs larger than L2 (state ~1.2 GB)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "adjoint": adjoint,
                 "batched_domains": batched,

@@ -222,10 +222,13 @@ int dgfv_profile_read(dgfv_ctx* ctx, double* ms, int64_t* launches, int cap);
  * are identical. */
 int dgfv_set_launch_mode(dgfv_ctx* ctx, int mode);
 
-/* Chooses, for every degree present, the number of elements per tile of the
- * volume kernel by timing candidates (64 to 2048 nodes per tile) on the
- * context's state, and keeps the fastest.  per_tile_out (host, 9 entries,
- * may be NULL) receives the choice per point count n = N+1.  Synchronises. */
+/* Chooses the launch variant of the volume kernel (bit 0: 128 instead of 256
+ * threads per CTA; bit 1: a register budget for three instead of two 256-thread
+ * CTAs per SM) and then, for every degree present, the number of elements per
+ * tile (64 to 2048 nodes per tile), by timing candidates on the context's state;
+ * keeps the fastest.  per_tile_out (host, 9 entries, may be NULL) receives the
+ * variant in entry 0 and the tile size per point count n = N+1 in entry n.
+ * Synchronises. */
 int dgfv_autotune(dgfv_ctx* ctx, int* per_tile_out, void* stream);
 
 /* Device status word: DGFV_OK or the first error a kernel recorded; clears it. */

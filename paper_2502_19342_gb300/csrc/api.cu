@@ -100,6 +100,7 @@ struct dgfv_ctx {
     int n_fv_elems = 0;
     int launch_mode = 0;           // 0: one launch per kernel; 1: one launch per degree bin
     int vol_per_tile[MAXP + 1] = {};  // elements per volume tile (0: default), set by the autotuner
+    int vol_variant = 0;              // volume-kernel launch variant (threads, register budget), autotuned
     bool state_valid = false;
     std::string err;
     // graph of one RK step
@@ -352,12 +353,16 @@ int alloc_tiles(dgfv_ctx* c, TileSet& t) {
 
 // One evaluation of R on Uin; the surface kernel writes mode 0: out = R, or
 // mode 1: out = a*U0 + b*(Uin + dt*R).
+// One evaluation of R(Uin) and, in mode 1, the stage combination.  have_faces:
+// the face values of Uin are already in the face buffer (written by the
+// previous stage's fused surface pass).  fuse_faces (mode 1): write the face
+// values of out for the next stage.
 void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out, int mode, double a, double b,
-                   cudaStream_t s) {
+                   cudaStream_t s, bool have_faces = false, bool fuse_faces = false) {
     const Params P = params(c);
     const Faces F{c->d_faceL, c->d_faceR, c->d_faceD};
     const bool per_bin = c->launch_mode == 1;
-    {
+    if (!have_faces) {
         Timed t(c, K_PROLONG, s);
         if (per_bin)
             for (size_t bi = 0; bi < c->all.bin_first.size(); ++bi)
@@ -366,15 +371,21 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
             launch_prolong(c->nk, P, c->all.view(), c->all.ntiles, Uin, s);
     }
     if (c->n_fv_elems) { Timed t(c, K_FV, s); launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, Uin, s); }
-    if (c->ph.viscous) { Timed t(c, K_LIFT, s); launch_face_lift(c->nk, P, F, c->lift.d, c->lift.count, s); }
+    if (c->ph.viscous) {
+        // conforming DG faces one thread per point; faces that change degree or
+        // type (all with a DG side) one CTA each
+        Timed t(c, K_LIFT, s);
+        launch_face_lift_conf(c->nk, P, F, c->conf.view(), c->conf.ntiles, s);
+        launch_face_lift(c->nk, P, F, c->flux.d, c->flux.count, s);
+    }
     if (c->dg.ntiles) {
         Timed t(c, K_VOLUME, s);
         if (per_bin)
             for (size_t bi = 0; bi < c->dg.bin_first.size(); ++bi)
                 launch_dg_volume(c->nk, P, c->dg.view(c->dg.bin_first[bi]), c->dg.bin_count[bi], c->dg.bin_smem[bi],
-                                 Uin, s);
+                                 Uin, s, c->vol_variant);
         else
-            launch_dg_volume(c->nk, P, c->dg.view(), c->dg.ntiles, c->dg.smem, Uin, s);
+            launch_dg_volume(c->nk, P, c->dg.view(), c->dg.ntiles, c->dg.smem, Uin, s, c->vol_variant);
     }
     {
         Timed t(c, K_FLUX, s);
@@ -390,9 +401,9 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
         if (per_bin)
             for (size_t bi = 0; bi < c->all.bin_first.size(); ++bi)
                 launch_surface(c->nk, P, c->all.view(c->all.bin_first[bi]), c->all.bin_count[bi], Uin, U0, out, mode,
-                               a, b, c->d_dt3, s);
+                               a, b, c->d_dt3, fuse_faces, s);
         else
-            launch_surface(c->nk, P, c->all.view(), c->all.ntiles, Uin, U0, out, mode, a, b, c->d_dt3, s);
+            launch_surface(c->nk, P, c->all.view(), c->all.ntiles, Uin, U0, out, mode, a, b, c->d_dt3, fuse_faces, s);
     }
 }
 
@@ -407,9 +418,9 @@ void enqueue_rk_step(dgfv_ctx* c, double dt, cudaStream_t s) {
     }
     // SSP-RK3 (Shu-Osher): U1 = U + dt R(U); U2 = 3/4 U + 1/4 (U1 + dt R(U1));
     // U <- 1/3 U + 2/3 (U2 + dt R(U2)).
-    enqueue_stage(c, c->d_U, c->d_U, c->d_Us, 1, 0.0, 1.0, s);
-    enqueue_stage(c, c->d_Us, c->d_U, c->d_Us, 1, 0.75, 0.25, s);
-    enqueue_stage(c, c->d_Us, c->d_U, c->d_U, 1, 1.0 / 3.0, 2.0 / 3.0, s);
+    enqueue_stage(c, c->d_U, c->d_U, c->d_Us, 1, 0.0, 1.0, s, false, true);
+    enqueue_stage(c, c->d_Us, c->d_U, c->d_Us, 1, 0.75, 0.25, s, true, true);
+    enqueue_stage(c, c->d_Us, c->d_U, c->d_U, 1, 1.0 / 3.0, 2.0 / 3.0, s, true, false);
 }
 
 int set_pattern(dgfv_ctx* c, const int8_t* N, const uint8_t* fv, bool remap, cudaStream_t s) {
@@ -761,8 +772,8 @@ int dgfv_rk_step_vjp(dgfv_ctx* c, const double* d_U0, double dt, const double* d
     cudaStream_t s = (cudaStream_t)stream;
     // stage states of the step (recomputed from the step's start state)
     launch_set_scalar(c->d_dt3, dt, s);
-    enqueue_stage(c, d_U0, d_U0, c->d_S1, 1, 0.0, 1.0, s);       // U1 = U0 + dt R(U0)
-    enqueue_stage(c, c->d_S1, d_U0, c->d_S2, 1, 0.75, 0.25, s);  // U2 = 3/4 U0 + 1/4 (U1 + dt R(U1))
+    enqueue_stage(c, d_U0, d_U0, c->d_S1, 1, 0.0, 1.0, s, false, true);      // U1 = U0 + dt R(U0)
+    enqueue_stage(c, c->d_S1, d_U0, c->d_S2, 1, 0.75, 0.25, s, true, false);  // U2 = 3/4 U0 + 1/4 (U1 + dt R(U1))
     return rk_step_vjp_impl(c, d_U0, c->d_S1, c->d_S2, dt, d_Ubar_next, d_Ubar, s);
 }
 
@@ -782,9 +793,9 @@ int dgfv_rk_step_save(dgfv_ctx* c, double dt, double* d_stage1, double* d_stage2
     if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "rk_step_save before set_state");
     cudaStream_t s = (cudaStream_t)stream;
     launch_set_scalar(c->d_dt3, dt, s);
-    enqueue_stage(c, c->d_U, c->d_U, d_stage1, 1, 0.0, 1.0, s);
-    enqueue_stage(c, d_stage1, c->d_U, d_stage2, 1, 0.75, 0.25, s);
-    enqueue_stage(c, d_stage2, c->d_U, c->d_U, 1, 1.0 / 3.0, 2.0 / 3.0, s);
+    enqueue_stage(c, c->d_U, c->d_U, d_stage1, 1, 0.0, 1.0, s, false, true);
+    enqueue_stage(c, d_stage1, c->d_U, d_stage2, 1, 0.75, 0.25, s, true, true);
+    enqueue_stage(c, d_stage2, c->d_U, c->d_U, 1, 1.0 / 3.0, 2.0 / 3.0, s, true, false);
     CK(cudaGetLastError());
     return DGFV_OK;
 }
@@ -944,6 +955,28 @@ int dgfv_autotune(dgfv_ctx* c, int* per_tile_out, void* stream) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    // launch variant first, on the whole volume launch with the default tiles
+    {
+        for (int n = 0; n <= MAXP; ++n) c->vol_per_tile[n] = 0;
+        TRY(apply_layout(c));
+        const Params P = params(c);
+        double best_ms = 1e300;
+        int best = 0;
+        for (int var = 0; var < 4; ++var) {
+            launch_dg_volume(c->nk, P, c->dg.view(), c->dg.ntiles, c->dg.smem, c->d_U, s, var);  // warm
+            CK(cudaEventRecord(e0, s));
+            for (int r = 0; r < 3; ++r) launch_dg_volume(c->nk, P, c->dg.view(), c->dg.ntiles, c->dg.smem, c->d_U, s, var);
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = var;
+            }
+        }
+        c->vol_variant = best;
+    }
     int best_all[MAXP + 1] = {};
     for (int n = 1; n <= MAXP; ++n) {
         int cnt = 0;
@@ -963,9 +996,9 @@ int dgfv_autotune(dgfv_ctx* c, int* per_tile_out, void* stream) {
             TRY(upload_tiles(c, t));
             const size_t sm = volume_smem_bytes(c->nk, n, per);
             const Params P = params(c);
-            launch_dg_volume(c->nk, P, t.view(), t.ntiles, sm, c->d_U, s);  // warm
+            launch_dg_volume(c->nk, P, t.view(), t.ntiles, sm, c->d_U, s, c->vol_variant);  // warm
             CK(cudaEventRecord(e0, s));
-            for (int r = 0; r < 3; ++r) launch_dg_volume(c->nk, P, t.view(), t.ntiles, sm, c->d_U, s);
+            for (int r = 0; r < 3; ++r) launch_dg_volume(c->nk, P, t.view(), t.ntiles, sm, c->d_U, s, c->vol_variant);
             CK(cudaEventRecord(e1, s));
             CK(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -983,7 +1016,7 @@ int dgfv_autotune(dgfv_ctx* c, int* per_tile_out, void* stream) {
         c->vol_per_tile[n] = best_all[n];
         if (per_tile_out) per_tile_out[n] = best_all[n];
     }
-    if (per_tile_out) per_tile_out[0] = 0;
+    if (per_tile_out) per_tile_out[0] = c->vol_variant;
     TRY(apply_layout(c));
     return DGFV_OK;
 }

@@ -96,6 +96,12 @@ __host__ __device__ __forceinline__ int node_index(int n, int d, int m, int a, i
     return d == 0 ? m + n * (a + n * b) : (d == 1 ? a + n * (m + n * b) : a + n * (b + n * m));
 }
 
+// Non-finite test on the exponent bits (integer pipe; the FP64 pipe is the
+// bottleneck of every kernel here).
+__device__ __forceinline__ bool nonfinite_bits(double x) {
+    return ((__double2hiint(x) >> 20) & 0x7ff) == 0x7ff;
+}
+
 __device__ __forceinline__ void set_status(int* status, int code) {
     if (status) atomicCAS(status, 0, code);
 }

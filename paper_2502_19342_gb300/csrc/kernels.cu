@@ -32,27 +32,57 @@ namespace dgfv {
 
 
 // ---------------------------------------------------------------------------------
-// k_prolong: face values of every element.
+// Face values of a tile of elements whose states sit in shared memory
+// (sU: count x V x n^3): u(+-1) = sum_m l_m(+-1) u_m along the face normal for DG
+// elements, the boundary sub-cell mean for FV elements.  One thread per face
+// point, all variables.
+template <int NK>
+__device__ __forceinline__ void tile_face_values(const Params& P, const Tiles& T, int first, int count, int n,
+                                                 const double* sU, const double* sl) {
+    constexpr int V = NK + 4;
+    const int n2 = n * n, n3 = n2 * n, per = 6 * n2;
+    for (int i = threadIdx.x; i < count * per; i += blockDim.x) {
+        const int el = i / per, r = i - el * per, f = r / n2, p = r - f * n2;
+        const int a = p % n, b = p / n, d = f >> 1, side = f & 1;
+        const int e = T.items[first + el];
+        const double* src = sU + el * V * n3;
+        double* dst = P.b.fu + (P.t.fo[e] + (int64_t)f * n2) * V + p;
+        if (P.t.fv[e]) {
+            const int c = node_index(n, d, side ? n - 1 : 0, a, b);
+#pragma unroll
+            for (int v = 0; v < V; ++v) dst[v * n2] = src[v * n3 + c];
+        } else {
+            const double* l = sl + (side ? MAXP : 0);
+            const int c0 = node_index(n, d, 0, a, b), st = d == 0 ? 1 : (d == 1 ? n : n2);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                double val = 0.0;
+                for (int m = 0; m < n; ++m) val = fma(l[m], src[v * n3 + c0 + m * st], val);
+                dst[v * n2] = val;
+            }
+        }
+    }
+}
+
+// k_prolong: face values of every element (tile staged in shared memory).
 template <int NK>
 __global__ void __launch_bounds__(256) k_prolong(Params P, Tiles T, const double* __restrict__ U) {
     constexpr int V = NK + 4;
+    extern __shared__ double sm[];
+    double* sl = sm;              // lm, lp
+    double* sU = sm + 2 * MAXP;   // count * V n^3
     const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
-    const int n2 = n * n, n3 = n2 * n, per = 6 * V * n2;
-    for (int i = threadIdx.x; i < count * per; i += blockDim.x) {
-        const int el = i / per, r = i % per, f = r / (V * n2), r2 = r % (V * n2), v = r2 / n2, p = r2 % n2;
-        const int a = p % n, b = p / n, d = f >> 1, s = f & 1;
-        const int e = T.items[first + el];
-        const double* src = U + P.t.off[e] + (int64_t)v * n3;
-        double val;
-        if (P.t.fv[e]) {
-            val = src[node_index(n, d, s ? n - 1 : 0, a, b)];
-        } else {
-            const double* l = B(P, s ? P.bi.lp[n] : P.bi.lm[n]);
-            val = 0.0;
-            for (int m = 0; m < n; ++m) val = fma(__ldg(l + m), src[node_index(n, d, m, a, b)], val);
-        }
-        P.b.fu[(P.t.fo[e] + (int64_t)f * n2) * V + v * n2 + p] = val;
+    const int n3 = n * n * n, per = V * n3;
+    if (threadIdx.x < n) {
+        sl[threadIdx.x] = B(P, P.bi.lm[n])[threadIdx.x];
+        sl[MAXP + threadIdx.x] = B(P, P.bi.lp[n])[threadIdx.x];
     }
+    for (int i = threadIdx.x; i < count * per; i += blockDim.x) {
+        const int el = i / per, r = i - el * per;
+        sU[i] = U[P.t.off[T.items[first + el]] + r];
+    }
+    __syncthreads();
+    tile_face_values<NK>(P, T, first, count, n, sU, sl);
 }
 
 // ---------------------------------------------------------------------------------
@@ -225,6 +255,27 @@ __global__ void __launch_bounds__(256) k_fv(Params P, Tiles T, const double* __r
 }
 
 // ---------------------------------------------------------------------------------
+// k_face_lift_conf: lifting value U* = (u- + u+)/2 on faces whose two sides are
+// DG of one degree; one thread per face point (FV/FV faces of the conforming
+// tiles carry no lifting value and are skipped).
+__global__ void __launch_bounds__(128) k_face_lift_conf(Params P, Faces Fc, FaceTiles T, int V) {
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], nc = T.nc[blockIdx.x], d = T.d[blockIdx.x];
+    const int nc2 = nc * nc;
+    for (int t = threadIdx.x; t < count * nc2; t += blockDim.x) {
+        const int fid = T.items[first + t / nc2], p = t % nc2;
+        const int eL = Fc.L[fid], eR = Fc.R[fid];
+        if (P.t.fv[eL]) continue;
+        const int64_t sL = (P.t.fo[eL] + (int64_t)(2 * d + 1) * nc2) * V + p;
+        const int64_t sR = (P.t.fo[eR] + (int64_t)(2 * d) * nc2) * V + p;
+        for (int v = 0; v < V; ++v) {
+            const double u = 0.5 * (P.b.fu[sL + v * nc2] + P.b.fu[sR + v * nc2]);
+            P.b.flift[sL + v * nc2] = u;
+            P.b.flift[sR + v * nc2] = u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // k_face_lift: one CTA per face that has a DG side.
 template <int NK>
 __global__ void __launch_bounds__(64) k_face_lift(Params P, Faces Fc, const int32_t* __restrict__ list) {
@@ -278,8 +329,8 @@ __global__ void __launch_bounds__(64) k_face_lift(Params P, Faces Fc, const int3
 // k_dg_volume: tiles of DG elements of one degree; the lifted gradient lives in
 // shared memory (3V n^3 doubles per element) and is overwritten in place by
 // the nodal fluxes before the volume integral.
-template <int NK>
-__global__ void __launch_bounds__(256) k_dg_volume(Params P, Tiles T, const double* __restrict__ U) {
+template <int NK, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_dg_volume(Params P, Tiles T, const double* __restrict__ U) {
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
     const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
@@ -542,133 +593,196 @@ __global__ void __launch_bounds__(64) k_face_flux(Params P, Faces Fc, const int3
 // ---------------------------------------------------------------------------------
 // k_surface: surface integral and -1/J, fused with the SSP-RK3 stage combination.
 //   mode 0: out = R
-//   mode 1: out = a*U0 + b*(Uin + dt*R)   (out may alias Uin)
+//   mode 1: out = a*U0 + b*(Uin + dt*R)   (out may alias Uin or U0)
+// One thread per node, all variables.  With fuse != 0 (mode 1) the new state
+// is also kept in shared memory and its face values are written for the next
+// evaluation (the face-value pass of that evaluation is then skipped).
 template <int NK>
-__global__ void __launch_bounds__(256) k_surface(Params P, Tiles T, const double* Uin, const double* __restrict__ U0,
+__global__ void __launch_bounds__(256) k_surface(Params P, Tiles T, const double* Uin, const double* U0,
                                                  double* out, int mode, double a, double b,
-                                                 const double* __restrict__ dtp) {
+                                                 const double* __restrict__ dtp, int fuse) {
     constexpr int V = NK + 4;
+    extern __shared__ double sm[];
+    double* sl = sm;             // lm, lp, lhm, lhp
+    double* sU = sm + 4 * MAXP;  // count * V n^3 (fuse)
     const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
-    const int n2 = n * n, n3 = n2 * n, per = V * n3;
+    const int n2 = n * n, n3 = n2 * n;
+    if (threadIdx.x < n) {
+        sl[threadIdx.x] = B(P, P.bi.lm[n])[threadIdx.x];
+        sl[MAXP + threadIdx.x] = B(P, P.bi.lp[n])[threadIdx.x];
+        sl[2 * MAXP + threadIdx.x] = B(P, P.bi.lhm[n])[threadIdx.x];
+        sl[3 * MAXP + threadIdx.x] = B(P, P.bi.lhp[n])[threadIdx.x];
+    }
+    __syncthreads();
     const double dt = mode ? *dtp : 0.0;
-    for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
-        const int el = idx / per, r = idx % per, v = r / n3, c = r % n3;
+    for (int idx = threadIdx.x; idx < count * n3; idx += blockDim.x) {
+        const int el = idx / n3, c = idx - el * n3;
         const int e = T.items[first + el];
-        const int64_t off = P.t.off[e], fo = P.t.fo[e];
-        const int ijk[3] = {c % n, (c / n) % n, c / n2};
-        double acc = P.b.rtmp[off + r];
-        if (!P.t.fv[e]) {
-            const double* lhm = B(P, P.bi.lhm[n]);
-            const double* lhp = B(P, P.bi.lhp[n]);
+        const int i = c % n, jk = c / n, j = jk % n, k = jk / n;
+        const int m[3] = {i, j, k};
+        const int pt[3] = {j + n * k, i + n * k, i + n * j};
+        const int64_t off = P.t.off[e] + c, fo = P.t.fo[e];
+        const bool fv = P.t.fv[e];
+        // weights of the six face fluxes at this node (FV: boundary sub-cells only)
+        double wm[3], wp[3];
+        const double* Fm[3];
+        const double* Fp[3];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const int m0 = ijk[d];
-                const int p = (d == 0 ? ijk[1] : ijk[0]) + n * (d == 2 ? ijk[1] : ijk[2]);
-                const double Fp = P.b.flux[(fo + (int64_t)(2 * d + 1) * n2) * V + v * n2 + p];
-                const double Fm = P.b.flux[(fo + (int64_t)(2 * d) * n2) * V + v * n2 + p];
-                acc = fma(P.t.rh[3 * e + d], fma(__ldg(lhp + m0), Fp, __ldg(lhm + m0) * Fm), acc);
+        for (int d = 0; d < 3; ++d) {
+            const double rh = P.t.rh[3 * e + d];
+            if (fv) {
+                const double sc = 0.5 * n * rh;  // n/h_d
+                wm[d] = m[d] == 0 ? sc : 0.0;
+                wp[d] = m[d] == n - 1 ? sc : 0.0;
+            } else {
+                wm[d] = rh * sl[2 * MAXP + m[d]];
+                wp[d] = rh * sl[3 * MAXP + m[d]];
             }
-        } else {
+            Fm[d] = P.b.flux + (fo + (int64_t)(2 * d) * n2) * V + pt[d];
+            Fp[d] = P.b.flux + (fo + (int64_t)(2 * d + 1) * n2) * V + pt[d];
+        }
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const int m0 = ijk[d];
-                const int p = (d == 0 ? ijk[1] : ijk[0]) + n * (d == 2 ? ijk[1] : ijk[2]);
-                const double sc = 0.5 * n * P.t.rh[3 * e + d];  // n/h_d
-                if (m0 == n - 1) acc = fma(sc, P.b.flux[(fo + (int64_t)(2 * d + 1) * n2) * V + v * n2 + p], acc);
-                if (m0 == 0) acc = fma(sc, P.b.flux[(fo + (int64_t)(2 * d) * n2) * V + v * n2 + p], acc);
+        for (int v = 0; v < V; ++v) {
+            double acc = P.b.rtmp[off + (int64_t)v * n3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) acc = fma(wp[d], Fp[d][v * n2], fma(wm[d], Fm[d][v * n2], acc));
+            const double R = -acc;
+            if (mode == 0) {
+                out[off + (int64_t)v * n3] = R;
+            } else {
+                // a = 0 (first stage): U0 is not read
+                const double y = fma(dt, R, Uin[off + (int64_t)v * n3]);
+                const double x = a == 0.0 ? b * y : fma(b, y, a * U0[off + (int64_t)v * n3]);
+                if (nonfinite_bits(x)) set_status(P.status, -5);
+                out[off + (int64_t)v * n3] = x;
+                if (fuse) sU[el * V * n3 + v * n3 + c] = x;
             }
         }
-        const double R = -acc;
-        if (mode == 0) {
-            out[off + r] = R;
-        } else {
-            const double x = fma(b, fma(dt, R, Uin[off + r]), a * U0[off + r]);
-            if (!isfinite(x)) set_status(P.status, -5);
-            out[off + r] = x;
-        }
+    }
+    if (fuse) {
+        __syncthreads();
+        tile_face_values<NK>(P, T, first, count, n, sU, sl);
     }
 }
 
 // ---------------------------------------------------------------------------------
-// Time step of Sec. 3.3: per-block minima of dt_c and dt_v, then a final reduction.
+// Time step of Sec. 3.3: per-block maxima of the inverse time scales
+//   lc = (2N+1) sum_d (|v_d| + c)/dx_d,  lv = (2N+1) dv sum_d 1/dx_d^2
+// (FV: factor 1, dx = h/N_FV), then dt_c = cfl_c / max lc and dt_v = cfl_v / max lv
+// in a final reduction (identical to the minimum of the per-node quotients,
+// since correctly rounded division is monotone).  One reciprocal per node:
+// with r = 1/(rho (rho c_v)(rho Pr)), 1/rho, 1/(rho c_v) and 1/(rho Pr) are products.
 template <int NK>
-__global__ void __launch_bounds__(256) k_dt(Params P, Tiles T, const double* __restrict__ U, double cfl_c,
-                                            double cfl_v, double* __restrict__ partial) {
+__global__ void __launch_bounds__(256) k_dt(Params P, Tiles T, const double* __restrict__ U,
+                                            double* __restrict__ partial) {
     constexpr int V = NK + 4;
     __shared__ double red[2][256 / 32];
     const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
     const int n3 = n * n * n;
-    double mc = DBL_MAX, mv = DBL_MAX;
+    const bool visc = P.ph.viscous;
+    double mc = 0.0, mv = 0.0, kc[3] = {0.0, 0.0, 0.0}, kv = 0.0;
+    int ce = -1;
     for (int idx = threadIdx.x; idx < count * n3; idx += blockDim.x) {
-        const int el = idx / n3, c = idx % n3;
+        const int el = idx / n3, c = idx - el * n3;
         const int e = T.items[first + el];
         const double* src = U + P.t.off[e] + c;
         double u[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) u[v] = src[(int64_t)v * n3];
-        Prim<NK> s;
-        prim<NK>(P.ph, u, s);
-        const bool fv = P.t.fv[e];
-        const double fac = fv ? 1.0 : 2.0 * P.t.N[e] + 1.0;
-        const double sub = fv ? (double)P.nfv : 1.0;
-        double lam = 0.0, sdx = 0.0;
+        double rho = u[0], rcv = 0.0, rcp = 0.0, rmu = 0.0, rpr = 0.0;
+#pragma unroll
+        for (int k = 1; k < NK; ++k) rho += u[k];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            rcv = fma(u[k], P.ph.cv[k], rcv);
+            rcp = fma(u[k], P.ph.cp[k], rcp);
+            rmu = fma(u[k], P.ph.mu[k], rmu);
+            rpr = fma(u[k], P.ph.pr[k], rpr);
+        }
+        const double t = rcv * rpr, r = 1.0 / (rho * t);
+        const double irho = t * r, ircv = (rho * rpr) * r;
+        double vv[3], ke = 0.0;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const double idx_d = 0.5 * P.t.rh[3 * e + d] * sub;  // 1/dx_d
-            lam = fma(fabs(s.v[d]) + s.c, idx_d, lam);
-            sdx = fma(idx_d, idx_d, sdx);
+            vv[d] = u[NK + d] * irho;
+            ke = fma(vv[d], vv[d], ke);
         }
-        mc = fmin(mc, cfl_c / (lam * fac));
-        if (P.ph.viscous) {
-            const double prm = s.mu * s.cp / s.lam;  // Pr_mix
-            double dv = fmax(4.0 / 3.0 * s.mu * s.irho, s.kappa * s.mu / (prm * s.rho));
+        const double eps = fma(-0.5, ke, u[NK + 3] * irho);
+        const double cs = sqrt(rcp * (rcp - rcv) * eps) * ircv;  // c^2 = c_p (c_p - c_v) eps / c_v^2
+        if (e != ce) {  // per-element constants: (2N+1)/dx_d and (2N+1) sum_d 1/dx_d^2
+            ce = e;
+            const bool fv = P.t.fv[e];
+            const double fac = fv ? 1.0 : 2.0 * P.t.N[e] + 1.0;
+            const double sub = fv ? (double)P.nfv : 1.0;
+            double sdx = 0.0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const double idx_d = 0.5 * P.t.rh[3 * e + d] * sub;  // 1/dx_d
+                kc[d] = idx_d * fac;
+                sdx = fma(idx_d, idx_d, sdx);
+            }
+            kv = sdx * fac;
+        }
+        const double lam = fma(fabs(vv[0]) + cs, kc[0], fma(fabs(vv[1]) + cs, kc[1], (fabs(vv[2]) + cs) * kc[2]));
+        mc = fmax(mc, lam);
+        if (visc) {
+            const double irpr = (rho * rcv) * r;
+            // max(4/3 mu/rho, kappa mu/(Pr rho), max_k D_k)
+            double dv = fmax(4.0 / 3.0 * rmu * irho * irho, rcp * rmu * ircv * irpr * irho);
             dv = fmax(dv, P.ph.maxD);
-            mv = fmin(mv, cfl_v / (dv * sdx * fac));
+            mv = fmax(mv, dv * kv);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
-        mc = fmin(mc, __shfl_down_sync(0xffffffffu, mc, o));
-        mv = fmin(mv, __shfl_down_sync(0xffffffffu, mv, o));
+        mc = fmax(mc, __shfl_down_sync(0xffffffffu, mc, o));
+        mv = fmax(mv, __shfl_down_sync(0xffffffffu, mv, o));
     }
     const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
     if (ln == 0) { red[0][w] = mc; red[1][w] = mv; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) { mc = fmin(mc, red[0][i]); mv = fmin(mv, red[1][i]); }
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) { mc = fmax(mc, red[0][i]); mv = fmax(mv, red[1][i]); }
         partial[2 * blockIdx.x] = mc;
         partial[2 * blockIdx.x + 1] = mv;
     }
 }
 
-__global__ void k_dt_final(const double* __restrict__ partial, int nb, int viscous, double* __restrict__ out3) {
+__global__ void k_dt_final(const double* __restrict__ partial, int nb, int viscous, double cfl_c, double cfl_v,
+                           double* __restrict__ out3) {
     __shared__ double red[2][32];
-    double mc = DBL_MAX, mv = DBL_MAX;
+    double mc = 0.0, mv = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        mc = fmin(mc, partial[2 * i]);
-        mv = fmin(mv, partial[2 * i + 1]);
+        mc = fmax(mc, partial[2 * i]);
+        mv = fmax(mv, partial[2 * i + 1]);
     }
     for (int o = 16; o > 0; o >>= 1) {
-        mc = fmin(mc, __shfl_down_sync(0xffffffffu, mc, o));
-        mv = fmin(mv, __shfl_down_sync(0xffffffffu, mv, o));
+        mc = fmax(mc, __shfl_down_sync(0xffffffffu, mc, o));
+        mv = fmax(mv, __shfl_down_sync(0xffffffffu, mv, o));
     }
     const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
     if (ln == 0) { red[0][w] = mc; red[1][w] = mv; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) { mc = fmin(mc, red[0][i]); mv = fmin(mv, red[1][i]); }
-        out3[1] = mc;
-        out3[2] = viscous ? mv : INFINITY;
-        out3[0] = viscous ? 1.0 / (1.0 / mc + 1.0 / mv) : mc;
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) { mc = fmax(mc, red[0][i]); mv = fmax(mv, red[1][i]); }
+        const double dtc = cfl_c / mc, dtv = viscous ? cfl_v / mv : INFINITY;
+        out3[1] = dtc;
+        out3[2] = dtv;
+        out3[0] = viscous ? 1.0 / (1.0 / dtc + 1.0 / dtv) : dtc;
     }
 }
 
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
+// Decision thresholds of Sec. 3.4: FV on / FV off (on I_h), refine / coarsen (on I_rho).
+struct Thresholds {
+    double fv_on, fv_off, ref, crs;
+};
+
 // ---------------------------------------------------------------------------------
 // Modal indicator (Sec. 3.4): one CTA per element.
 template <int NK>
 __global__ void __launch_bounds__(128) k_indicator(Params P, const double* __restrict__ U, int n_elem,
-                                                   double* Ip, double* Ih, uint8_t* dec, double4 thr,
+                                                   double* Ip, double* Ih, uint8_t* dec, Thresholds thr,
                                                    int N_min, int N_max) {
     constexpr int V = NK + 4, NQ = 2 + (NK - 1);  // rho, p, Y_1..Y_{NK-1}
     constexpr int P3 = MAXP * MAXP * MAXP;
@@ -798,12 +912,12 @@ __global__ void __launch_bounds__(128) k_indicator(Params P, const double* __res
         if (Ih) Ih[e] = ih;
         uint8_t code = 0;
         if (fv) {
-            if (ih > thr.y) code = 2;
-        } else if (ih < thr.x) {
+            if (ih > thr.fv_off) code = 2;
+        } else if (ih < thr.fv_on) {
             code = 1;
-        } else if (ip < thr.z && N < N_max) {
+        } else if (ip < thr.ref && N < N_max) {
             code = 3;
-        } else if (ip > thr.w && N > N_min) {
+        } else if (ip > thr.crs && N > N_min) {
             code = 4;
         }
         if (dec) dec[e] = code;
@@ -882,9 +996,13 @@ __global__ void k_probe_dfma(int iters, double* sink) {
         default: { constexpr int NK = 3; call; } break; \
     }
 
+// Shared memory of the tile kernels that stage a tile of states: count * n^3 <= 512
+// nodes per tile (the "all" tiling) and 4 * MAXP bank values.
+static size_t tile_state_smem(int nk) { return sizeof(double) * (size_t)(4 * MAXP + (nk + 4) * 512); }
+
 void launch_prolong(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s) {
     if (ntiles <= 0) return;
-    DGFV_DISPATCH(nk, (k_prolong<NK><<<ntiles, 256, 0, s>>>(P, T, U)));
+    DGFV_DISPATCH(nk, (k_prolong<NK><<<ntiles, 256, tile_state_smem(nk), s>>>(P, T, U)));
 }
 
 size_t fv_smem_bytes(int nk, int nfv) {
@@ -899,6 +1017,11 @@ void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double
                        k_fv<NK><<<ntiles, 256, sm, s>>>(P, T, U)));
 }
 
+void launch_face_lift_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    k_face_lift_conf<<<ntiles, 128, 0, s>>>(P, F, T, nk + 4);
+}
+
 void launch_face_lift(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s) {
     if (nfaces <= 0) return;
     DGFV_DISPATCH(nk, (k_face_lift<NK><<<nfaces, 64, 0, s>>>(P, F, list)));
@@ -909,11 +1032,21 @@ size_t volume_smem_bytes(int nk, int n, int count) {
     return sizeof(double) * (size_t)(n * n + 4 * n + count * 3 * V * n * n * n);
 }
 
+// variant bit 0: 128 threads per CTA (else 256); bit 1: register budget for
+// three 256-thread CTAs per SM (else two).
 void launch_dg_volume(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
-                      cudaStream_t s) {
+                      cudaStream_t s, int variant) {
     if (ntiles <= 0) return;
-    DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_dg_volume<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                       k_dg_volume<NK><<<ntiles, 256, smem, s>>>(P, T, U)));
+    const int threads = (variant & 1) ? 128 : 256;
+    if (variant & 2) {
+        DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_dg_volume<NK, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem),
+                           k_dg_volume<NK, 3><<<ntiles, threads, smem, s>>>(P, T, U)));
+    } else {
+        DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_dg_volume<NK, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem),
+                           k_dg_volume<NK, 2><<<ntiles, threads, smem, s>>>(P, T, U)));
+    }
 }
 
 void launch_face_flux(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s) {
@@ -927,21 +1060,23 @@ void launch_face_flux_conf(int nk, const Params& P, const Faces& F, const FaceTi
 }
 
 void launch_surface(int nk, const Params& P, const Tiles& T, int ntiles, const double* Uin, const double* U0,
-                    double* out, int mode, double a, double b, const double* dt, cudaStream_t s) {
+                    double* out, int mode, double a, double b, const double* dt, bool fuse, cudaStream_t s) {
     if (ntiles <= 0) return;
-    DGFV_DISPATCH(nk, (k_surface<NK><<<ntiles, 256, 0, s>>>(P, T, Uin, U0, out, mode, a, b, dt)));
+    const int f = (fuse && mode == 1) ? 1 : 0;
+    const size_t sm = f ? tile_state_smem(nk) : sizeof(double) * 4 * MAXP;
+    DGFV_DISPATCH(nk, (k_surface<NK><<<ntiles, 256, sm, s>>>(P, T, Uin, U0, out, mode, a, b, dt, f)));
 }
 
 void launch_dt(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, double cfl_c, double cfl_v,
                double* partial, double* out3, cudaStream_t s) {
-    DGFV_DISPATCH(nk, (k_dt<NK><<<ntiles, 256, 0, s>>>(P, T, U, cfl_c, cfl_v, partial)));
-    k_dt_final<<<1, 1024, 0, s>>>(partial, ntiles, P.ph.viscous, out3);
+    DGFV_DISPATCH(nk, (k_dt<NK><<<ntiles, 256, 0, s>>>(P, T, U, partial)));
+    k_dt_final<<<1, 1024, 0, s>>>(partial, ntiles, P.ph.viscous, cfl_c, cfl_v, out3);
 }
 
 void launch_set_scalar(double* p, double v, cudaStream_t s) { k_set_scalar<<<1, 1, 0, s>>>(p, v); }
 
 // Scratch of the allocation-free time step (dgfv_compute_dt_noalloc): the
-// per-block minima of k_dt live in this fixed array instead of a buffer the
+// per-block maxima of k_dt live in this fixed array instead of a buffer the
 // context allocated.  Every device that loads the library holds the array
 // (2 * DT_NOALLOC_MAX_BLOCKS doubles = 1 MiB) until the process exits.
 static __device__ __align__(256) double g_dt_partial[2 * DT_NOALLOC_MAX_BLOCKS];
@@ -970,14 +1105,14 @@ int launch_dt_noalloc(int nk, const Params& P, const Tiles& T, int ntiles, const
     }
     // every block writes its pair before k_dt_final reads it, in stream order,
     // so nothing has to be cleared between calls
-    DGFV_DISPATCH(nk, (k_dt<NK><<<ntiles, 256, 0, s>>>(P, T, U, cfl_c, cfl_v, partial)));
-    k_dt_final<<<1, 1024, 0, s>>>(partial, ntiles, P.ph.viscous, out3);
+    DGFV_DISPATCH(nk, (k_dt<NK><<<ntiles, 256, 0, s>>>(P, T, U, partial)));
+    k_dt_final<<<1, 1024, 0, s>>>(partial, ntiles, P.ph.viscous, cfl_c, cfl_v, out3);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
 void launch_indicator(int nk, const Params& P, const double* U, int n_elem, double* Ip, double* Ih, uint8_t* dec,
                       const double thr[4], int N_min, int N_max, cudaStream_t s) {
-    const double4 t = make_double4(thr[0], thr[1], thr[2], thr[3]);
+    const Thresholds t{thr[0], thr[1], thr[2], thr[3]};
     const size_t sm = sizeof(double) * (size_t)MAXP * MAXP * MAXP * (nk + 4 + 2 + 2 * (nk + 1));
     DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_indicator<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                        k_indicator<NK><<<n_elem, 128, sm, s>>>(P, U, n_elem, Ip, Ih, dec, t, N_min, N_max)));

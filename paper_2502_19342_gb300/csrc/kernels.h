@@ -13,14 +13,15 @@ namespace dgfv {
 void launch_prolong(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s);
 size_t fv_smem_bytes(int nk, int nfv);
 void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s);
+void launch_face_lift_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s);
 void launch_face_lift(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s);
 size_t volume_smem_bytes(int nk, int n, int count);
 void launch_dg_volume(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
-                      cudaStream_t s);
+                      cudaStream_t s, int variant = 0);
 void launch_face_flux(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s);
 void launch_face_flux_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s);
 void launch_surface(int nk, const Params& P, const Tiles& T, int ntiles, const double* Uin, const double* U0,
-                    double* out, int mode, double a, double b, const double* dt, cudaStream_t s);
+                    double* out, int mode, double a, double b, const double* dt, bool fuse, cudaStream_t s);
 void launch_dt(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, double cfl_c, double cfl_v,
                double* partial, double* out3, cudaStream_t s);
 void launch_set_scalar(double* p, double v, cudaStream_t s);

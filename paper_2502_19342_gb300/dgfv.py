@@ -334,10 +334,13 @@ class Context:
         self._rc(lib().dgfv_set_launch_mode(self.h, int(bool(per_degree))), "set_launch_mode")
 
     def autotune(self, stream=None):
-        """Time candidate tile sizes of the volume kernel per degree; returns {N: elements per tile}."""
+        """Time launch variants and tile sizes of the volume kernel on the current
+        state; returns {"variant": v, N: elements per tile, ...}."""
         out = (C.c_int * 9)()
         self._rc(lib().dgfv_autotune(self.h, out, _stream(stream)), "autotune")
-        return {n - 1: out[n] for n in range(1, 9) if out[n] > 0}
+        res = {"variant": int(out[0])}
+        res.update({n - 1: out[n] for n in range(1, 9) if out[n] > 0})
+        return res
 
     def profile_enable(self, on=True):
         self._rc(lib().dgfv_profile_enable(self.h, int(on)), "profile_enable")
