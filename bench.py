@@ -36,6 +36,10 @@ STEPS_PER_CYCLE = 10
 STAGES_PER_STEP = 3
 # FP64 peak from the unit count and clock of a GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 SMS, DFMA_PER_CLK, SM_MHZ_MAX = 152, 2, 2070.0
+# DRAM bytes per DG DOF of one k_dg_volume launch, from an ncu capture of the
+# turbulence workload at 28^3 elements (dram__bytes_read.sum + write.sum =
+# 0.398 + 0.815 GB for 3.45e6 DG DOFs).
+VOLUME_DRAM_BYTES_PER_DG_DOF = 351.5
 FP64_PEAK_TFLOPS = SMS * DFMA_PER_CLK * 2 * SM_MHZ_MAX * 1e6 / 1e12
 KERNEL_STEP = {"prolong": 1, "fv": 2, "face_lift": 3, "dg_volume": 4, "face_flux": 5, "surface": 6}
 
@@ -52,6 +56,8 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the default volume-kernel launch instead of timing variants first")
+    p.add_argument("--profile-timed", action="store_true",
+                   help="bracket the timed region with cudaProfilerStart/Stop (for a profiler's launch list)")
     p.add_argument("--profile-eval", action="store_true",
                    help="after the warm-up cycles run one R(U) evaluation between cudaProfilerStart/Stop "
                         "(for ncu --profile-from-start off) and exit")
@@ -166,53 +172,98 @@ def cpu_baseline(prob, budget_s=12.0):
                       f"degree/FV distribution, {dt:.1f} s"}
 
 
-def adjoint_cost(steps=10):
+def mixing_functional_grad(prob, Ybar, Uf):
+    """Gradient of J = sum over nodes of w J_geo [rho |v|^2 / 2 + sum_{k<N_k} (Y_k - Ybar_k)^2]
+    (uniform N, DG) with respect to the final state, by torch autograd."""
+    import torch
+    nk = len(prob["gamma"])
+    V = nk + 4
+    n = int(prob["N"][0]) + 1
+    w1 = torch.from_numpy(np.polynomial.legendre.leggauss(n)[1]).cuda()
+    w = (w1[:, None, None] * w1[None, :, None] * w1[None, None, :]).reshape(-1)  # (k, j, i) order
+    X = Uf.detach().clone().requires_grad_(True)
+    blk = X.view(-1, V, n ** 3)
+    rho = blk[:, :nk].sum(1)
+    ke = 0.5 * (blk[:, nk] ** 2 + blk[:, nk + 1] ** 2 + blk[:, nk + 2] ** 2) / rho
+    var = sum((blk[:, k] / rho - Ybar[k]) ** 2 for k in range(nk - 1))
+    (w[None, :] * (ke + var)).sum().backward()  # J_geo is one constant for the uniform mesh: left out
+    return X.grad.contiguous()
+
+
+def adjoint_cost(steps=50):
     """Adjoint of the SSP-RK3 rollout on the mixing-layer workload (16^3
-    elements, N = 4, 3 species, viscous, pattern frozen): time of the forward
-    steps vs the adjoint steps (stage states recomputed from one checkpoint per
-    step), CUDA events."""
+    elements, N = 4, 3 species, viscous, pattern frozen, dt frozen at its
+    initial CFL value): the gradient of the kinetic-energy-plus-species-variance
+    functional of the final state with respect to the initial state.  CUDA
+    events around the forward steps and around the adjoint steps; checkpoint
+    buffers allocated before timing."""
     import torch
     from paper_2502_19342_gb300 import dgfv, workloads as W
     prob, U = W.mixing_layer()
+    nk = len(prob["gamma"])
     ctx = dgfv.Context(prob, N_min=4, N_max=4)
     Ud = torch.from_numpy(U).cuda()
     dt = ctx.compute_dt(Ud)[0]
-    states = [Ud.clone()]
+    blk = Ud.view(-1, nk + 4, 125)
+    rho0 = blk[:, :nk].sum(1)
+    Ybar = [float((blk[:, k] / rho0).mean()) for k in range(nk - 1)]
+    ck = [torch.empty_like(Ud) for _ in range(steps + 1)]       # U_k, one checkpoint per step
+    st = [(torch.empty_like(Ud), torch.empty_like(Ud)) for _ in range(steps)]  # stage states
+    lam = [torch.empty_like(Ud) for _ in range(2)]
     ctx.set_state(Ud)
-    for _ in range(2):  # warm-up of both directions
-        ctx.rk_step(dt, want_dt=False)
-        ctx.rk_step_vjp(Ud, dt, Ud.clone())
-    ctx.set_state(Ud)
+    ctx.rk_step_save(dt, *st[0])  # warm-up of every path
+    ctx.rk_step(dt, want_dt=False)
+    ctx.rk_step_vjp_stages((Ud, *st[0]), dt, Ud, lam[0])
+    ctx.rk_step_vjp(Ud, dt, Ud, lam[1])
     s = torch.cuda.current_stream()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+
+    def forward_plain():
+        ctx.set_state(Ud)
+        for k in range(steps):
+            ctx.get_state(ck[k])
+            ctx.rk_step(dt, want_dt=False)
+        ctx.get_state(ck[steps])
+
+    def forward_save():
+        ctx.set_state(Ud)
+        for k in range(steps):
+            ctx.get_state(ck[k])
+            ctx.rk_step_save(dt, *st[k])
+        ctx.get_state(ck[steps])
+
     torch.cuda.synchronize()
     ev[0].record(s)
-    for _ in range(steps):  # forward, one checkpoint per step
-        ctx.rk_step(dt, want_dt=False)
-        states.append(ctx.get_state())
+    forward_plain()
     ev[1].record(s)
-    lam = torch.ones_like(Ud)
-    for k in range(steps - 1, -1, -1):  # adjoint, stage states recomputed
-        lam = ctx.rk_step_vjp(states[k], dt, lam)
+    g = mixing_functional_grad(prob, Ybar, ck[steps])
     ev[2].record(s)
-    stages = []
-    ctx.set_state(Ud)
-    for k in range(steps):  # forward keeping the stage states
-        s1, s2 = torch.empty_like(Ud), torch.empty_like(Ud)
-        ctx.rk_step_save(dt, s1, s2)
-        stages.append((states[k], s1, s2))
+    a = g
+    for k in range(steps - 1, -1, -1):  # stage states recomputed from the checkpoints
+        b = lam[k % 2]
+        ctx.rk_step_vjp(ck[k], dt, a, b)
+        a = b
     ev[3].record(s)
-    lam2 = torch.ones_like(Ud)
-    for k in range(steps - 1, -1, -1):  # adjoint from the stored stage states
-        lam2 = ctx.rk_step_vjp_stages(stages[k], dt, lam2)
+    grad_recomputed = a.clone()
     ev[4].record(s)
+    forward_save()
+    ev[5].record(s)
+    a = g
+    for k in range(steps - 1, -1, -1):  # stored stage states
+        b = lam[k % 2]
+        ctx.rk_step_vjp_stages((ck[k], *st[k]), dt, a, b)
+        a = b
+    ev[6].record(s)
     torch.cuda.synchronize()
-    fwd, bwd, bwd2 = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[3].elapsed_time(ev[4])
-    same = bool(torch.equal(lam, lam2))
+    fwd, bwd, fsave, bwd2 = (ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3]), ev[4].elapsed_time(ev[5]),
+                             ev[5].elapsed_time(ev[6]))
+    same = bool(torch.equal(grad_recomputed, a))
     dofs = W.n_dofs(prob)
     ctx.close()
-    return {"workload": "temporal mixing layer, 16^3 elements, N=4, 3 species, viscous, LLF, pattern frozen",
-            "steps": steps, "dofs": dofs, "forward_ms_per_step": fwd / steps,
+    return {"workload": "temporal mixing layer, 16^3 elements, N=4, 3 species, viscous, LLF, pattern and dt frozen; "
+                        "gradient of kinetic energy + species variance of the final state",
+            "steps": steps, "dofs": dofs, "stage_state_gb": round(3 * steps * Ud.numel() * 8 / 1e9, 2),
+            "forward_ms_per_step": fwd / steps, "forward_keeping_stages_ms_per_step": fsave / steps,
             "adjoint_ms_per_step_stored_stages": bwd2 / steps, "adjoint_over_forward": bwd2 / fwd,
             "adjoint_ms_per_step_recomputed_stages": bwd / steps, "adjoint_over_forward_recomputed": bwd / fwd,
             "gradients_identical": same,
@@ -371,6 +422,8 @@ def main():
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        if args.profile_timed:
+            torch.cuda.profiler.start()
         ev0.record(stream)
         for _ in range(args.steps):
             u, st = cycle(ctx)
@@ -378,6 +431,8 @@ def main():
             pattern.append(st)
         ev1.record(stream)
         barrier()
+        if args.profile_timed:
+            torch.cuda.profiler.stop()
     ms = ev0.elapsed_time(ev1)
     prof = ctx.profile_read()
     ctx.profile_enable(False)
@@ -424,10 +479,15 @@ def main():
         dofs_per_launch = units / (args.steps * STEPS_PER_CYCLE * STAGES_PER_STEP)
         achieved = per_step[KERNEL_STEP[main_k]] * dofs_per_launch / (kms / kl * 1e-3) / 1e12
         probe = dgfv.probe_dfma(1 << 14) / 1e12
+        probe_mma = dgfv.probe_dmma(1 << 11) / 1e12
+        dg_dofs = float(np.sum((N_now[fv_now == 0].astype(np.int64) + 1) ** 3))
+        traffic = VOLUME_DRAM_BYTES_PER_DG_DOF * dg_dofs if main_k == "dg_volume" else None
         roof = {"bound": "alu", "kernel": main_k, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_dg_volume on the 28^3 "
+                                  "case, 351.5 B per DG DOF, times the DG DOFs of one launch here",
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 1.26 TFLOP/s)",
-                "dfma_probe_tflops": probe,
+                "dfma_probe_tflops": probe, "dmma_probe_tflops": probe_mma,
                 "flops_per_dof": {"total": per_dof, main_k: per_step[KERNEL_STEP[main_k]]},
                 "whole_rhs_tflops": per_dof * units / (ms * 1e-3) / 1e12}
         cpu = None if args.no_cpu else cpu_baseline(dict(prob, N=N_now, fv=fv_now))

@@ -55,7 +55,11 @@ typedef enum {
     DGFV_ERR_STATE = -7         /* call order (e.g. rk_step before set_state)             */
 } dgfv_status;
 
-typedef enum { DGFV_RIEMANN_LLF = 0, DGFV_RIEMANN_ROE_HH = 1 } dgfv_riemann;
+/* Convective flux: local Lax-Friedrichs, Roe with the Harten-Hyman entropy fix
+ * (Sec. 3.1.1), or Roe-HH between DG elements and LLF on every face that
+ * touches FV data (FV sub-cell faces, FV/FV and DG/FV faces), the choice of the
+ * jet computation (Sec. 5.1). */
+typedef enum { DGFV_RIEMANN_LLF = 0, DGFV_RIEMANN_ROE_HH = 1, DGFV_RIEMANN_HYBRID = 2 } dgfv_riemann;
 
 /* Mesh: n_domains periodic boxes; arrays have 3 entries per domain. */
 typedef struct {
@@ -250,6 +254,12 @@ int64_t dgfv_bank_entry(dgfv_ctx* ctx, int which, int N, int M, double* out, int
  * achieved FMA-flops per second (2 per DFMA) over `iters` iterations.
  * Synchronises. */
 double dgfv_probe_dfma(int iters, void* stream);
+
+/* FP64 tensor-core probe: independent mma.sync m8n8k4 f64 chains; returns
+ * achieved flops per second (2 per multiply-add) over `iters` iterations.
+ * Decides whether the small tensor-product contractions of the volume kernel
+ * would gain from FP64 MMA on this GPU.  Synchronises. */
+double dgfv_probe_dmma(int iters, void* stream);
 
 #ifdef __cplusplus
 }

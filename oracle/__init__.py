@@ -9,7 +9,8 @@ A *problem* is a plain dict:
     lo,hi float64 (n_domains, 3)   box corners
     n_fv  int                      FV sub-cells per direction
     gamma, Rgas, mu, Pr, Dk        float64 (n_species,) species properties
-    riemann int                    0 = local Lax-Friedrichs, 1 = Roe + Harten-Hyman
+    riemann int                    0 = local Lax-Friedrichs, 1 = Roe + Harten-Hyman, 2 = Roe-HH between
+                                   DG elements, LLF on faces touching FV data (Sec. 5.1)
     N     int8 (n_elem,)           DG degree per element
     fv    uint8 (n_elem,)          1 for FV sub-cell elements
 """

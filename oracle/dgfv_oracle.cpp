@@ -224,15 +224,24 @@ struct ElemWork {
     vector<T> div;          // volume (DG) or interior sub-cell face (FV) part of -R  (V x n^3)
 };
 
+// Convective flux choice per face (Sec. 5.1, the jet): riemann = 2 takes Roe-HH
+// on faces between two DG elements and local Lax-Friedrichs on every face that
+// touches FV data (FV sub-cell faces, FV/FV and DG/FV element faces).
+int riemann_kind(const Problem& P, bool fv_involved) {
+    if (P.riemann == 2) return fv_involved ? 0 : 1;
+    return P.riemann;
+}
+
 // Face flux at one point: F* = F^c*(uL,uR) + (F^v(uL,gL) + F^v(uR,gR))/2 in +x_d direction.
 template <class T>
-void point_flux(const Problem& P, const T* uL, const T* gL, const T* uR, const T* gR, int d, T* F) {
+void point_flux(const Problem& P, const T* uL, const T* gL, const T* uR, const T* gR, int d, T* F,
+                bool fv_involved) {
     const int V = P.V;
     T Fc[MAXV], FvL[MAXV], FvR[MAXV];
     Prim<T> sL, sR;
     cons_to_prim(P.ph, uL, sL);
     cons_to_prim(P.ph, uR, sR);
-    riemann(P.ph, P.riemann, uL, sL, uR, sR, d, Fc);
+    riemann(P.ph, riemann_kind(P, fv_involved), uL, sL, uR, sR, d, Fc);
     flux_visc(P.ph, uL, gL, sL, d, FvL);
     flux_visc(P.ph, uR, gR, sR, d, FvR);
     for (int v = 0; v < V; ++v) F[v] = Fc[v] + T(0.5) * (FvL[v] + FvR[v]);
@@ -395,7 +404,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
                                 gL[dd * V + v] = grad[((size_t)dd * V + v) * n3 + cL];
                                 gR[dd * V + v] = grad[((size_t)dd * V + v) * n3 + cR];
                             }
-                        point_flux(P, uL, gL, uR, gR, d, F);
+                        point_flux(P, uL, gL, uR, gR, d, F, true);
                         for (int v = 0; v < V; ++v) {
                             div[(size_t)v * n3 + cL] = div[(size_t)v * n3 + cL] + scale * F[v];
                             div[(size_t)v * n3 + cR] = div[(size_t)v * n3 + cR] - scale * F[v];
@@ -569,7 +578,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
                 T a[MAXV], b[MAXV], ga[3 * MAXV], gb[3 * MAXV], F[MAXV];
                 for (int v = 0; v < V; ++v) { a[v] = uL[(size_t)v * np + p]; b[v] = uR[(size_t)v * np + p]; }
                 for (int dv = 0; dv < 3 * V; ++dv) { ga[dv] = gL[(size_t)dv * np + p]; gb[dv] = gR[(size_t)dv * np + p]; }
-                point_flux(P, a, ga, b, gb, d, F);
+                point_flux(P, a, ga, b, gb, d, F, common_fv);
                 for (int v = 0; v < V; ++v) Fc[(size_t)v * np + p] = F[v];
             }
             // back to each side's native representation (projection / V^{FV->DG})
@@ -963,7 +972,7 @@ int oracle_riemann(const oracle_problem* p, const double* uL, const double* uR, 
     Prim<double> sL, sR;
     cons_to_prim(ph, uL, sL);
     cons_to_prim(ph, uR, sR);
-    riemann(ph, p->riemann, uL, sL, uR, sR, dir, F);
+    riemann(ph, p->riemann == 2 ? 1 : p->riemann, uL, sL, uR, sR, dir, F);
     return 0;
 }
 

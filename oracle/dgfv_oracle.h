@@ -38,7 +38,8 @@ typedef struct {
     const double* mu;      /* per species dynamic viscosity              */
     const double* Pr;      /* per species Prandtl number                 */
     const double* Dk;      /* per species diffusion coefficient          */
-    int riemann;           /* 0 = local Lax-Friedrichs, 1 = Roe + Harten-Hyman */
+    int riemann;           /* 0 = local Lax-Friedrichs, 1 = Roe + Harten-Hyman, 2 = Roe + Harten-Hyman
+                              between DG elements and local Lax-Friedrichs on every face touching FV data */
     const int8_t* N;       /* per element DG degree (kept while FV)      */
     const uint8_t* fv;     /* per element: 1 = FV sub-cell element       */
 } oracle_problem;

@@ -529,7 +529,8 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     c->N_max = mesh->N_max;
     c->nfv = mesh->N_fv;
     c->ph.nk = c->nk;
-    c->ph.riemann = opts->riemann == DGFV_RIEMANN_ROE_HH ? 1 : 0;
+    if (opts->riemann < DGFV_RIEMANN_LLF || opts->riemann > DGFV_RIEMANN_HYBRID) return cleanup(DGFV_ERR_ARG);
+    c->ph.riemann = opts->riemann;
     c->ph.viscous = 0;
     c->ph.maxD = 0.0;
     for (int k = 0; k < c->nk; ++k) {
@@ -1057,5 +1058,7 @@ int64_t dgfv_bank_entry(dgfv_ctx* c, int which, int N, int M, double* out, int64
 }
 
 double dgfv_probe_dfma(int iters, void* stream) { return probe_dfma(iters, (cudaStream_t)stream); }
+
+double dgfv_probe_dmma(int iters, void* stream) { return probe_dmma(iters, (cudaStream_t)stream); }
 
 }  // extern "C"

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(256) k_fv(Params P, Tiles T, const double* __r
             if (P.ph.viscous) grad(i, j, k, gL);
             coords(d, m + 1, a, b, i, j, k);
             if (P.ph.viscous) grad(i, j, k, gR);
-            interface_flux<NK>(P.ph, uL, gL, uR, gR, d, F);
+            interface_flux<NK>(P.ph, uL, gL, uR, gR, d, F, true);
 #pragma unroll
             for (int v = 0; v < V; ++v) sF[v * nif + fidx] = F[v];
         }
@@ -469,7 +469,7 @@ __device__ __forceinline__ void conf_face_body(const Params& P, const Faces& Fc,
                 gR[x] = gRs[x * nc2];
             }
         }
-        interface_flux<NK>(P.ph, uL, gL, uR, gR, D, F);
+        interface_flux<NK>(P.ph, uL, gL, uR, gR, D, F, P.t.fv[eL] != 0);  // conforming: both FV or both DG
         double* dL = P.b.flux + sL * V + p;
         double* dR = P.b.flux + sR * V + p;
 #pragma unroll
@@ -557,7 +557,7 @@ __device__ __forceinline__ void mixed_face_body(const Params& P, int eL, int eR,
                 gR[x] = sG[1][x * nc2 + p];
             }
         }
-        interface_flux<NK>(P.ph, uL, gL, uR, gR, D, F);
+        interface_flux<NK>(P.ph, uL, gL, uR, gR, D, F, common_fv);
 #pragma unroll
         for (int v = 0; v < V; ++v) sF[v * nc2 + p] = F[v];
     }
@@ -988,6 +988,27 @@ __global__ void k_probe_dfma(int iters, double* sink) {
     if (s == 12345.0) sink[threadIdx.x] = s;
 }
 
+// FP64 tensor-core probe: eight independent mma.sync m8n8k4 (f64) accumulators
+// per warp; each instruction is 8 x 8 x 4 FMAs.  Every lane of a warp runs it
+// (all lanes converged), operands in registers only.
+__global__ void k_probe_dmma(int iters, double* sink) {
+    double c[8][2];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c[j][0] = c[j][1] = threadIdx.x * 1e-9 + j;
+    const double a = 0.999999999, b = 1e-3;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                         : "+d"(c[j][0]), "+d"(c[j][1])
+                         : "d"(a), "d"(b));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += c[j][0] + c[j][1];
+    if (s == 12345.0) sink[threadIdx.x] = s;
+}
+
 // ================================================================= launchers
 #define DGFV_DISPATCH(nk, call)           \
     switch (nk) {                         \
@@ -1125,6 +1146,30 @@ void launch_remap(const Params& P, const uint8_t* n_old, const uint8_t* N_old, c
     const size_t sm = sizeof(double) * (size_t)(2 * V * MAXP * MAXP * MAXP);
     cudaFuncSetAttribute(k_remap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_remap<<<n_elem, 128, sm, s>>>(P, A, Bn, V, Uo, Un);
+}
+
+double probe_dmma(int iters, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    double* sink = nullptr;
+    if (cudaMalloc(&sink, 1024 * sizeof(double)) != cudaSuccess) return -1.0;
+    const int blocks = sms * 4, threads = 256;
+    k_probe_dmma<<<blocks, threads, 0, s>>>(16, sink);  // warm-up
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+    k_probe_dmma<<<blocks, threads, 0, s>>>(iters, sink);
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    const double flops = 2.0 * 8 * 8 * 4 * 8.0 * (double)iters * blocks * (threads / 32);
+    return ms > 0 ? flops / (ms * 1e-3) : -1.0;
 }
 
 double probe_dfma(int iters, cudaStream_t s) {

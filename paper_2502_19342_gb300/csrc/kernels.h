@@ -37,5 +37,6 @@ void launch_remap(const Params& P, const uint8_t* n_old, const uint8_t* N_old, c
                   const int64_t* off_old, const uint8_t* n_new, const uint8_t* N_new, const uint8_t* fv_new,
                   const int64_t* off_new, int V, int n_elem, const double* Uo, double* Un, cudaStream_t s);
 double probe_dfma(int iters, cudaStream_t s);
+double probe_dmma(int iters, cudaStream_t s);
 
 }  // namespace dgfv

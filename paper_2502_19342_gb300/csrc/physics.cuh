@@ -34,7 +34,7 @@ constexpr int MAXV = MAXSP + 4;
 struct DevPhys {
     int nk;
     int viscous;
-    int riemann;  // 0 LLF, 1 Roe + Harten-Hyman
+    int riemann;  // 0 LLF, 1 Roe + Harten-Hyman, 2 Roe-HH between DG elements, LLF where FV data meet
     double cv[MAXSP], cp[MAXSP], mu[MAXSP], pr[MAXSP], D[MAXSP];
     double maxD;
 };
@@ -249,16 +249,24 @@ DGFV_HD void riemann_roe(const DevPhys& P, const double* uL, const Prim<NK>& sL,
     for (int v = 0; v < V; ++v) F[v] = 0.5 * ((FL[v] + FR[v]) - Dis[v]);
 }
 
+// Convective flux of a face: riemann 0 LLF, 1 Roe-HH, 2 Roe-HH between DG
+// elements and LLF on every face that touches FV data (the jet set-up of
+// Sec. 5.1).  fv_involved: an FV sub-cell face, or an element face with an FV side.
+DGFV_HD bool use_roe(const DevPhys& P, bool fv_involved) {
+    return P.riemann == 1 || (P.riemann == 2 && !fv_involved);
+}
+
 // Interface flux at one point in +x_d: F* = F^c*(uL,uR) + (F^v(uL,gL) + F^v(uR,gR))/2
 // (Eqs. 20, 21).
 template <int NK>
 DGFV_HD void interface_flux(const DevPhys& P, const double* uL, const double* gL,
-                                               const double* uR, const double* gR, int d, double* F) {
+                                               const double* uR, const double* gR, int d, double* F,
+                                               bool fv_involved) {
     constexpr int V = NK + 4;
     Prim<NK> sL, sR;
     prim<NK>(P, uL, sL);
     prim<NK>(P, uR, sR);
-    if (P.riemann == 1)
+    if (use_roe(P, fv_involved))
         riemann_roe<NK>(P, uL, sL, uR, sR, d, F);
     else
         riemann_llf<NK>(uL, sL, uR, sR, d, F);

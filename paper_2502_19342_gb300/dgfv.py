@@ -23,7 +23,7 @@ SYMBOLS = ["dgfv_init_mesh", "dgfv_num_elements", "dgfv_set_degrees", "dgfv_get_
            "dgfv_status_string", "dgfv_last_error", "dgfv_destroy", "dgfv_bank_entry", "dgfv_probe_dfma",
            "dgfv_profile_enable", "dgfv_profile_read", "dgfv_compute_dt_noalloc", "dgfv_rhs_vjp",
            "dgfv_rk_step_vjp", "dgfv_set_launch_mode", "dgfv_autotune", "dgfv_rk_step_save",
-           "dgfv_rk_step_vjp_stages"]
+           "dgfv_rk_step_vjp_stages", "dgfv_probe_dmma"]
 KERNELS = ["prolong", "fv", "face_lift", "dg_volume", "face_flux", "surface", "dt", "indicator", "remap"]
 
 
@@ -90,6 +90,8 @@ def lib():
         L.dgfv_bank_entry.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp, i64]
         L.dgfv_probe_dfma.restype = C.c_double
         L.dgfv_probe_dfma.argtypes = [C.c_int, vp]
+        L.dgfv_probe_dmma.restype = C.c_double
+        L.dgfv_probe_dmma.argtypes = [C.c_int, vp]
         L.dgfv_profile_enable.argtypes = [vp, C.c_int]
         L.dgfv_profile_read.argtypes = [vp, dp, C.POINTER(i64), C.c_int]
         _lib = L
@@ -369,6 +371,11 @@ def init_mesh(problem, N_min=None, N_max=None, opts=None):
 def probe_dfma(iters=1 << 16, stream=None):
     """Measured FP64 FMA throughput (flop/s, 2 per DFMA) of this GPU."""
     return float(lib().dgfv_probe_dfma(int(iters), _stream(stream)))
+
+
+def probe_dmma(iters=1 << 12, stream=None):
+    """Measured FP64 tensor-core (mma.sync m8n8k4) throughput (flop/s) of this GPU."""
+    return float(lib().dgfv_probe_dmma(int(iters), _stream(stream)))
 
 
 def rhs_function():

@@ -68,7 +68,7 @@ double face_dot(const DevPhys& P, const double* uL, const double* gL, const doub
                 const double* Fb) {
     constexpr int V = NK + 4;
     double F[V];
-    interface_flux<NK>(P, uL, gL, uR, gR, d, F);
+    interface_flux<NK>(P, uL, gL, uR, gR, d, F, false);
     double acc = 0.0;
     for (int v = 0; v < V; ++v) acc += Fb[v] * F[v];
     return acc;

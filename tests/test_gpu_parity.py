@@ -49,7 +49,7 @@ def test_rhs_plain_tiny(oracle):
 
 
 @pytest.mark.parametrize("nk,riemann,mu,seed", [(2, 0, 2e-3, 1), (3, 0, 2e-3, 2), (2, 1, 2e-3, 3), (3, 1, 0.0, 4),
-                                                (1, 0, 1e-3, 5), (3, 1, 5e-3, 6)])
+                                                (1, 0, 1e-3, 5), (3, 1, 5e-3, 6), (3, 2, 2e-3, 7), (2, 2, 0.0, 8)])
 def test_rhs_mixed_hp_fv(oracle, nk, riemann, mu, seed):
     """Random degrees 1..7 and FV elements (N_FV = 8) on a 3x4x5 box: every
     face type (equal and unequal degree, DG/FV, FV/FV) and ragged tiles."""
@@ -223,6 +223,8 @@ def test_rejects_bad_arguments():
     with pytest.raises(dgfv.DgfvError):
         ctx.rk_step(-1.0)  # no state yet
     ctx.close()
+    with pytest.raises(dgfv.DgfvError):
+        ctx_for(dict(prob, riemann=3))  # no such flux
 
 
 def test_launch_modes_and_autotuned_tiles_give_identical_results(oracle):

@@ -62,7 +62,7 @@ def test_golden_freestream_table_parses():
     assert max(rows["Linf"]) < 1e-13
 
 
-@pytest.mark.parametrize("riemann", [0, 1])
+@pytest.mark.parametrize("riemann", [0, 1, 2])
 def test_freestream_preserved_on_random_hp_fv_pattern(oracle, riemann):
     """Sec. 4.1: a uniform state stays uniform to round-off after 180 steps on a
     random distribution of degrees N in [2,5] and FV elements (N_FV = 8).  The
@@ -85,7 +85,7 @@ def test_freestream_preserved_on_random_hp_fv_pattern(oracle, riemann):
 
 
 # ---------------------------------------------------------------- conservation
-@pytest.mark.parametrize("nk,riemann,seed", [(2, 0, 1), (3, 1, 2), (2, 1, 4), (3, 0, 5)])
+@pytest.mark.parametrize("nk,riemann,seed", [(2, 0, 1), (3, 1, 2), (2, 1, 4), (3, 0, 5), (3, 2, 6)])
 def test_discrete_conservation_periodic(oracle, nk, riemann, seed):
     """Sum of J w R over DG nodes plus sub-cell volume x R over FV cells vanishes
     for every conserved variable on a periodic mesh, through p- and DG/FV
@@ -98,6 +98,45 @@ def test_discrete_conservation_periodic(oracle, nk, riemann, seed):
     tot = [np.sum(r * w) for r, w in zip(_per_var(prob, R), _per_var(prob, wts))]
     scale = np.abs(R).max() * wts.sum() / W.n_vars(prob)
     assert max(abs(t) for t in tot) < 1e-14 * scale
+
+
+def test_flux_choice_per_face_type(oracle):
+    """Sec. 5.1: Roe-HH between DG elements, local Lax-Friedrichs wherever FV
+    data meet (FV sub-cell faces, FV/FV and DG/FV faces).  An element's R uses
+    only its own faces, so on a mixed pattern the result equals the all-Roe
+    result on every DG element with six DG neighbours and the all-LLF result
+    on every FV element with six FV neighbours; elements on the DG/FV border
+    differ from both."""
+    nel = (4, 4, 3)
+    prob = _mixed_problem(7, nk=3, nel=nel, Nlo=1, Nhi=5, fv_frac=0.35, n_fv=6)
+    U = W.smooth_random_state(prob, 7, amp=0.15)
+    R = {k: oracle.eval_rhs(dict(prob, riemann=k), U) for k in (0, 1, 2)}
+    _, pos, _, _ = W.element_index(prob)
+    lin = {tuple(p): e for e, p in enumerate(pos)}
+    off, _ = W.offsets(prob)
+    size = np.diff(np.append(off, R[2].size))
+    fv = prob["fv"]
+    n_in = {0: 0, 1: 0, "border": 0}
+    for e, p in enumerate(pos):
+        nb = [lin[tuple((p + s * np.eye(3, dtype=int)[d]) % nel)] for d in range(3) for s in (-1, 1)]
+        sl = slice(off[e], off[e] + size[e])
+        if not fv[e] and not any(fv[q] for q in nb):
+            np.testing.assert_array_equal(R[2][sl], R[1][sl])
+            n_in[1] += 1
+        elif fv[e] and all(fv[q] for q in nb):
+            np.testing.assert_array_equal(R[2][sl], R[0][sl])
+            n_in[0] += 1
+        elif not fv[e]:
+            assert np.abs(R[2][sl] - R[1][sl]).max() > 0 and np.abs(R[2][sl] - R[0][sl]).max() > 0
+            n_in["border"] += 1
+    assert n_in[1] > 0 and n_in["border"] > 0
+    # all-DG and all-FV patterns reduce to the single solvers
+    dg = dict(prob, fv=np.zeros_like(fv), riemann=2)
+    Udg = W.smooth_random_state(dg, 8, amp=0.15)
+    np.testing.assert_array_equal(oracle.eval_rhs(dg, Udg), oracle.eval_rhs(dict(dg, riemann=1), Udg))
+    allfv = dict(prob, fv=np.ones_like(fv), riemann=2)
+    Ufv = W.smooth_random_state(allfv, 9, amp=0.15)
+    np.testing.assert_array_equal(oracle.eval_rhs(allfv, Ufv), oracle.eval_rhs(dict(allfv, riemann=0), Ufv))
 
 
 # ---------------------------------------------------------------- 1D brute force
