@@ -34,7 +34,7 @@ class _Problem(C.Structure):
     _fields_ = [
         ("n_domains", C.c_int), ("dims", _i32p), ("lo", _dp), ("hi", _dp), ("n_fv", C.c_int),
         ("n_species", C.c_int), ("gamma", _dp), ("Rgas", _dp), ("mu", _dp), ("Pr", _dp),
-        ("Dk", _dp), ("riemann", C.c_int), ("N", _i8p), ("fv", _u8p),
+        ("Dk", _dp), ("riemann", C.c_int), ("N", _i8p), ("fv", _u8p), ("nodes", C.c_int), ("split", C.c_int),
     ]
 
 
@@ -58,11 +58,11 @@ def lib():
         L.oracle_indicator.argtypes = [P, _dp, _dp, _dp]
         L.oracle_adapt_decide.argtypes = [P, _dp, _dp, _dp, C.c_int, C.c_int, _i8p, _u8p]
         L.oracle_remap.argtypes = [P, _i8p, _u8p, _dp, _dp]
-        L.oracle_basis.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
-        L.oracle_vmap.argtypes = [C.c_int, C.c_int, _dp]
-        L.oracle_dg2fv.argtypes = [C.c_int, C.c_int, _dp]
-        L.oracle_fv2dg.argtypes = [C.c_int, C.c_int, _dp]
-        L.oracle_leg_vandermonde.argtypes = [C.c_int, _dp]
+        L.oracle_basis.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, C.c_int]
+        L.oracle_vmap.argtypes = [C.c_int, C.c_int, _dp, C.c_int]
+        L.oracle_dg2fv.argtypes = [C.c_int, C.c_int, _dp, C.c_int]
+        L.oracle_fv2dg.argtypes = [C.c_int, C.c_int, _dp, C.c_int]
+        L.oracle_leg_vandermonde.argtypes = [C.c_int, _dp, C.c_int]
         L.oracle_flux.argtypes = [P, _dp, _dp, C.c_int, _dp, _dp]
         L.oracle_riemann.argtypes = [P, _dp, _dp, C.c_int, _dp]
         L.oracle_primitives.argtypes = [P, _dp, _dp]
@@ -98,7 +98,7 @@ class _Bound:
             self.dims.shape[0], _ptr(self.dims, _i32p), _ptr(self.lo, _dp), _ptr(self.hi, _dp),
             int(prob["n_fv"]), len(sp[0]), _ptr(sp[0], _dp), _ptr(sp[1], _dp), _ptr(sp[2], _dp),
             _ptr(sp[3], _dp), _ptr(sp[4], _dp), int(prob.get("riemann", 0)),
-            _ptr(self.N, _i8p), _ptr(self.fv, _u8p))
+            _ptr(self.N, _i8p), _ptr(self.fv, _u8p), int(prob.get("nodes", 0)), int(prob.get("split", 0)))
 
     @property
     def ref(self):
@@ -222,36 +222,37 @@ def remap(prob, N_new, fv_new, U_old):
     return Unew
 
 
-def basis(N):
+def basis(N, nodes=0):
+    """Reference operators of degree N; nodes 0 = Legendre-Gauss, 1 = Legendre-Gauss-Lobatto."""
     n = N + 1
     x, w, lm, lp = (np.zeros(n) for _ in range(4))
     D, Dh = np.zeros((n, n)), np.zeros((n, n))
     _check(lib().oracle_basis(N, _ptr(x, _dp), _ptr(w, _dp), _ptr(D, _dp), _ptr(Dh, _dp), _ptr(lm, _dp),
-                              _ptr(lp, _dp)), "basis")
+                              _ptr(lp, _dp), int(nodes)), "basis")
     return {"x": x, "w": w, "D": D, "Dhat": Dh, "lm": lm, "lp": lp}
 
 
-def vmap(N_from, N_to):
+def vmap(N_from, N_to, nodes=0):
     M = np.zeros((N_to + 1, N_from + 1))
-    _check(lib().oracle_vmap(N_from, N_to, _ptr(M, _dp)), "vmap")
+    _check(lib().oracle_vmap(N_from, N_to, _ptr(M, _dp), int(nodes)), "vmap")
     return M
 
 
-def dg2fv(N, n_fv):
+def dg2fv(N, n_fv, nodes=0):
     M = np.zeros((n_fv, N + 1))
-    _check(lib().oracle_dg2fv(N, n_fv, _ptr(M, _dp)), "dg2fv")
+    _check(lib().oracle_dg2fv(N, n_fv, _ptr(M, _dp), int(nodes)), "dg2fv")
     return M
 
 
-def fv2dg(N, n_fv):
+def fv2dg(N, n_fv, nodes=0):
     M = np.zeros((N + 1, n_fv))
-    _check(lib().oracle_fv2dg(N, n_fv, _ptr(M, _dp)), "fv2dg")
+    _check(lib().oracle_fv2dg(N, n_fv, _ptr(M, _dp), int(nodes)), "fv2dg")
     return M
 
 
-def leg_vandermonde(N):
+def leg_vandermonde(N, nodes=0):
     M = np.zeros((N + 1, N + 1))
-    _check(lib().oracle_leg_vandermonde(N, _ptr(M, _dp)), "leg_vandermonde")
+    _check(lib().oracle_leg_vandermonde(N, _ptr(M, _dp), int(nodes)), "leg_vandermonde")
     return M
 
 

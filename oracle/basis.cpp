@@ -44,6 +44,44 @@ void gauss_legendre(int n, std::vector<ld>& x, std::vector<ld>& w) {
     }
 }
 
+// Legendre-Gauss-Lobatto nodes of degree N (N+1 points): -1, the roots of
+// P_N' (Newton on P_N' with P_N'' from Legendre's equation
+// (1 - x^2) P'' = 2 x P' - N (N+1) P), +1; weights w = 2 / (N (N+1) P_N(x)^2).
+void gauss_lobatto(int N, std::vector<ld>& x, std::vector<ld>& w) {
+    const ld pi = 3.14159265358979323846264338327950288L;
+    const int n = N + 1;
+    x.assign(n, 0); w.assign(n, 0);
+    x[0] = -1;
+    x[N] = 1;
+    for (int i = 1; i < N; ++i) {
+        ld xi = -std::cos(pi * i / N);
+        for (int it = 0; it < 200; ++it) {
+            ld P, dP;
+            legendre(N, xi, P, dP);
+            const ld d2P = (2 * xi * dP - N * (N + 1) * P) / (1 - xi * xi);
+            const ld dx = dP / d2P;
+            xi -= dx;
+            if (std::fabs((double)dx) < 1e-19) break;
+        }
+        x[i] = xi;
+    }
+    for (int i = 0; i < n; ++i) {
+        ld P, dP;
+        legendre(N, x[i], P, dP);
+        w[i] = 2 / ((ld)N * (N + 1) * P * P);
+    }
+}
+
+// Nodes and weights of the node family (0: Legendre-Gauss, 1: Legendre-Gauss-Lobatto).
+void node_set(int N, int kind, std::vector<ld>& x, std::vector<ld>& w) {
+    if (kind == 1) {
+        if (N < 1) throw std::runtime_error("LGL needs N >= 1");
+        gauss_lobatto(N, x, w);
+    } else {
+        gauss_legendre(N + 1, x, w);
+    }
+}
+
 // Lagrange polynomial l_j of the nodes x, evaluated at xi.
 ld lagrange(const std::vector<ld>& x, int j, ld xi) {
     ld r = 1;
@@ -104,15 +142,15 @@ std::vector<double> to_double(const std::vector<ld>& a) {
     return std::vector<double>(a.begin(), a.end());
 }
 
-std::vector<ld> nodes_ld(int N) {
+std::vector<ld> nodes_ld(int N, int kind) {
     std::vector<ld> x, w;
-    gauss_legendre(N + 1, x, w);
+    node_set(N, kind, x, w);
     return x;
 }
 
 // (N_to+1) x (N_from+1) interpolation matrix l^{from}_j(x^{to}_i).
-std::vector<ld> interp_ld(int N_from, int N_to) {
-    std::vector<ld> xf = nodes_ld(N_from), xt = nodes_ld(N_to);
+std::vector<ld> interp_ld(int N_from, int N_to, int kind) {
+    std::vector<ld> xf = nodes_ld(N_from, kind), xt = nodes_ld(N_to, kind);
     int nf = N_from + 1, nt = N_to + 1;
     std::vector<ld> M(nt * nf);
     for (int i = 0; i < nt; ++i)
@@ -120,18 +158,18 @@ std::vector<ld> interp_ld(int N_from, int N_to) {
     return M;
 }
 
-std::vector<ld> leg_vandermonde_ld(int N) {
+std::vector<ld> leg_vandermonde_ld(int N, int kind) {
     int n = N + 1;
-    std::vector<ld> x = nodes_ld(N), V(n * n);
+    std::vector<ld> x = nodes_ld(N, kind), V(n * n);
     for (int i = 0; i < n; ++i)
         for (int m = 0; m < n; ++m) V[i * n + m] = legendre_orthonormal(m, x[i]);
     return V;
 }
 
-std::vector<ld> dg2fv_ld(int N, int n_fv) {
+std::vector<ld> dg2fv_ld(int N, int n_fv, int kind) {
     int n = N + 1;
-    std::vector<ld> x, w;
-    gauss_legendre(n, x, w);  // exact for the degree-N integrand
+    std::vector<ld> x = nodes_ld(N, kind), q, w;
+    gauss_legendre(n, q, w);  // exact for the degree-N integrand
     ld l = (ld)2 / n_fv;
     std::vector<ld> A(n_fv * n);
     for (int s = 0; s < n_fv; ++s) {
@@ -139,7 +177,7 @@ std::vector<ld> dg2fv_ld(int N, int n_fv) {
         for (int j = 0; j < n; ++j) {
             // (1/l) * integral over [a, a+l] of l_j  =  (1/2) sum_q w_q l_j(a + (l/2)(x_q+1))
             ld sum = 0;
-            for (int q = 0; q < n; ++q) sum += w[q] * lagrange(x, j, a + l / 2 * (x[q] + 1));
+            for (int k = 0; k < n; ++k) sum += w[k] * lagrange(x, j, a + l / 2 * (q[k] + 1));
             A[s * n + j] = sum / 2;
         }
     }
@@ -148,14 +186,14 @@ std::vector<ld> dg2fv_ld(int N, int n_fv) {
 
 }  // namespace
 
-Basis1D make_basis(int N) {
+Basis1D make_basis(int N, int kind) {
     if (N < 0 || N > 15) throw std::runtime_error("degree out of range");
     Basis1D b;
     b.N = N;
     b.n = N + 1;
     const int n = b.n;
     std::vector<ld> x, w;
-    gauss_legendre(n, x, w);
+    node_set(N, kind, x, w);
     b.x = to_double(x);
     b.w = to_double(w);
     std::vector<ld> D(n * n);
@@ -176,14 +214,14 @@ Basis1D make_basis(int N) {
     return b;
 }
 
-std::vector<double> vmap(int N_from, int N_to) {
-    if (N_from <= N_to) return to_double(interp_ld(N_from, N_to));
+std::vector<double> vmap(int N_from, int N_to, int kind) {
+    if (N_from <= N_to) return to_double(interp_ld(N_from, N_to, kind));
     // L2 projection onto degree N_to: expand in orthonormal Legendre modes
     // (inverse Vandermonde of the finer degree), keep modes 0..N_to, evaluate
     // the truncated series on the coarser nodes.
     int nf = N_from + 1, nt = N_to + 1;
-    std::vector<ld> Vinv = invert(leg_vandermonde_ld(N_from), nf);
-    std::vector<ld> xt = nodes_ld(N_to);
+    std::vector<ld> Vinv = invert(leg_vandermonde_ld(N_from, kind), nf);
+    std::vector<ld> xt = nodes_ld(N_to, kind);
     std::vector<ld> M(nt * nf, 0);
     for (int i = 0; i < nt; ++i)
         for (int j = 0; j < nf; ++j) {
@@ -194,14 +232,14 @@ std::vector<double> vmap(int N_from, int N_to) {
     return to_double(M);
 }
 
-std::vector<double> dg2fv(int N, int n_fv) { return to_double(dg2fv_ld(N, n_fv)); }
+std::vector<double> dg2fv(int N, int n_fv, int kind) { return to_double(dg2fv_ld(N, n_fv, kind)); }
 
-std::vector<double> fv2dg(int N, int n_fv) {
+std::vector<double> fv2dg(int N, int n_fv, int kind) {
     // Pseudo-inverse through the normal equations, (A^T A)^{-1} A^T; A has full
     // column rank whenever n_fv >= N+1.
     int n = N + 1;
     if (n_fv < n) throw std::runtime_error("n_fv < N+1: DG->FV map not injective");
-    std::vector<ld> A = dg2fv_ld(N, n_fv);
+    std::vector<ld> A = dg2fv_ld(N, n_fv, kind);
     std::vector<ld> AtA(n * n, 0);
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {
@@ -220,10 +258,10 @@ std::vector<double> fv2dg(int N, int n_fv) {
     return to_double(P);
 }
 
-std::vector<double> leg_vandermonde(int N) { return to_double(leg_vandermonde_ld(N)); }
+std::vector<double> leg_vandermonde(int N, int kind) { return to_double(leg_vandermonde_ld(N, kind)); }
 
-std::vector<double> leg_vandermonde_inv(int N) {
-    return to_double(invert(leg_vandermonde_ld(N), N + 1));
+std::vector<double> leg_vandermonde_inv(int N, int kind) {
+    return to_double(invert(leg_vandermonde_ld(N, kind), N + 1));
 }
 
 }  // namespace ora

@@ -6,6 +6,8 @@
 //   Sec. 3.1.1: Legendre-Gauss nodes/weights, Lagrange basis (Eq. 18
 //               langrange_basis), derivative matrix D, weighted derivative
 //               matrix Dhat and l_hat = l/omega (Eq. 24 dgsem_abbrev).
+//   Sec. 3.5:   the same on Legendre-Gauss-Lobatto nodes (split-form DGSEM).
+//   Every function takes the node family: kind 0 Legendre-Gauss, 1 LGL.
 //   Sec. 3.2:   V^{N->M} (interpolation for N<M, L2 projection for N>M),
 //               V^{DG->FV} (sub-cell integration), V^{FV->DG} (pseudo-inverse).
 //   Sec. 3.4:   Legendre Vandermonde V_Leg (orthonormal Legendre modes).
@@ -19,25 +21,25 @@ namespace ora {
 struct Basis1D {
     int N = 0;                 // polynomial degree
     int n = 0;                 // number of nodes, N+1
-    std::vector<double> x, w;  // Legendre-Gauss nodes (ascending) and weights
+    std::vector<double> x, w;  // nodes (ascending) and quadrature weights of the node family
     std::vector<double> D;     // D[i*n+j] = l_j'(x_i)
     std::vector<double> Dhat;  // Dhat[i*n+j] = -(w_j / w_i) * D[j*n+i]   (reading of Eq. 24)
     std::vector<double> lm, lp;    // l_j(-1), l_j(+1)
     std::vector<double> lhm, lhp;  // l_j(-1)/w_j, l_j(+1)/w_j
 };
 
-Basis1D make_basis(int N);
+Basis1D make_basis(int N, int kind = 0);
 
 // (N_to+1) x (N_from+1): interpolation if N_from <= N_to, L2 projection otherwise.
-std::vector<double> vmap(int N_from, int N_to);
+std::vector<double> vmap(int N_from, int N_to, int kind = 0);
 // n_fv x (N+1): mean value of the degree-N interpolant over each of n_fv equal sub-cells.
-std::vector<double> dg2fv(int N, int n_fv);
+std::vector<double> dg2fv(int N, int n_fv, int kind = 0);
 // (N+1) x n_fv: Moore-Penrose pseudo-inverse of dg2fv(N, n_fv).
-std::vector<double> fv2dg(int N, int n_fv);
-// (N+1) x (N+1): V[i*n+m] = sqrt((2m+1)/2) P_m(x_i) on the LG nodes of degree N.
-std::vector<double> leg_vandermonde(int N);
+std::vector<double> fv2dg(int N, int n_fv, int kind = 0);
+// (N+1) x (N+1): V[i*n+m] = sqrt((2m+1)/2) P_m(x_i) on the nodes of degree N.
+std::vector<double> leg_vandermonde(int N, int kind = 0);
 // Inverse of leg_vandermonde(N) (Gauss-Jordan elimination).
-std::vector<double> leg_vandermonde_inv(int N);
+std::vector<double> leg_vandermonde_inv(int N, int kind = 0);
 
 }  // namespace ora
 

@@ -59,6 +59,8 @@ struct Problem {
     int V = 6;
     int nfv = 2;
     int riemann = 0;
+    int nodes = 0;  // 0 Legendre-Gauss, 1 Legendre-Gauss-Lobatto
+    int split = 0;  // 1: split-form volume integral with the kinetic-energy-preserving two-point flux
     vector<Elem> el;
     int64_t size = 0;
     Ops ops;
@@ -81,6 +83,10 @@ Problem make_problem(const oracle_problem* p, bool need_ops = true) {
     P.V = P.ph.V();
     P.nfv = p->n_fv;
     P.riemann = p->riemann;
+    P.nodes = p->nodes;
+    P.split = p->split;
+    if (P.nodes < 0 || P.nodes > 1 || P.split < 0 || P.split > 1 || (P.split && P.nodes != 1))
+        throw std::runtime_error("bad node family / split form (split form needs LGL nodes)");
     int64_t e0 = 0;
     for (int d = 0; d < p->n_domains; ++d) {
         const int nx = p->dims[3 * d], ny = p->dims[3 * d + 1], nz = p->dims[3 * d + 2];
@@ -121,13 +127,13 @@ Problem make_problem(const oracle_problem* p, bool need_ops = true) {
         std::sort(degs.begin(), degs.end());
         degs.erase(std::unique(degs.begin(), degs.end()), degs.end());
         for (int N : degs) {
-            P.ops.basis[N] = make_basis(N);
-            P.ops.vleg_inv[N] = leg_vandermonde_inv(N);
+            P.ops.basis[N] = make_basis(N, P.nodes);
+            P.ops.vleg_inv[N] = leg_vandermonde_inv(N, P.nodes);
             if (P.nfv >= N + 1) {
-                P.ops.d2f[N] = dg2fv(N, P.nfv);
-                P.ops.f2d[N] = fv2dg(N, P.nfv);
+                P.ops.d2f[N] = dg2fv(N, P.nfv, P.nodes);
+                P.ops.f2d[N] = fv2dg(N, P.nfv, P.nodes);
             }
-            for (int M : degs) P.ops.vm[{N, M}] = vmap(N, M);
+            for (int M : degs) P.ops.vm[{N, M}] = vmap(N, M, P.nodes);
         }
         for (auto& E : P.el)
             if (E.fv && P.nfv < E.N + 1) throw std::runtime_error("n_fv < N+1 for an FV element");
@@ -245,6 +251,65 @@ void point_flux(const Problem& P, const T* uL, const T* gL, const T* uR, const T
     flux_visc(P.ph, uL, gL, sL, d, FvL);
     flux_visc(P.ph, uR, gR, sR, d, FvR);
     for (int v = 0; v < V; ++v) F[v] = Fc[v] + T(0.5) * (FvL[v] + FvR[v]);
+}
+
+// Kinetic-energy-preserving two-point flux of Pirozzoli in +x_d (Sec. 3.5):
+// with arithmetic means {.} of the two states,
+//   rho_k: {rho}{v_d}{Y_k},  rho v_j: {rho}{v_d}{v_j} + {p} delta_jd,  rho E: {rho}{v_d}{H},
+// H = (rho E + p)/rho the total enthalpy (species: the transported mass
+// fraction times the mean mass flux, so that the species fluxes add up to
+// the mass flux {rho}{v_d}).
+template <class T>
+void kep_flux(const Phys& ph, const Prim<T>& a, const T* ua, const Prim<T>& b, const T* ub, int d, T* F) {
+    const int nk = ph.nk;
+    const T rho = T(0.5) * (a.rho + b.rho);
+    const T vd = T(0.5) * (a.v[d] + b.v[d]);
+    const T mass = rho * vd;
+    for (int k = 0; k < nk; ++k) F[k] = mass * (T(0.5) * (a.Y[k] + b.Y[k]));
+    for (int j = 0; j < 3; ++j) F[nk + j] = mass * (T(0.5) * (a.v[j] + b.v[j]));
+    F[nk + d] = F[nk + d] + T(0.5) * (a.p + b.p);
+    const T Ha = (ua[nk + 3] + a.p) / a.rho, Hb = (ub[nk + 3] + b.p) / b.rho;
+    F[nk + 3] = mass * (T(0.5) * (Ha + Hb));
+}
+
+// Split form on LGL nodes (Sec. 3.5): the convective part of the volume term,
+// sum_m Dhat_im F^c(u_m) = sum_m D_im F^c(u_m) - (B_ii/w_i) F^c(u_i) (summation
+// by parts, B = diag(-1, 0, .., 0, 1)), is replaced by
+//   sum_m 2 D_im F#(u_i, u_m) - (B_ii/w_i) F^c(u_i)
+// along every direction; the viscous part keeps the standard form.  Applied as
+// a correction to the standard volume term already in div.
+template <class T>
+void split_form_correction(const Problem& P, const Elem& E, const Basis1D& B, const T* u, vector<T>& div) {
+    const int V = P.V, n = E.n, n3 = n * n * n;
+    vector<Prim<T>> s(n3);
+    for (int c = 0; c < n3; ++c) {
+        T uc[MAXV];
+        for (int v = 0; v < V; ++v) uc[v] = u[(size_t)v * n3 + c];
+        cons_to_prim(P.ph, uc, s[c]);
+    }
+    for (int d = 0; d < 3; ++d) {
+        const T metric = T(2.0 / E.h[d]);
+        for (int b = 0; b < n; ++b)
+            for (int a = 0; a < n; ++a)
+                for (int i = 0; i < n; ++i) {
+                    const int ci = node_index(n, d, i, a, b);
+                    T ui[MAXV], um[MAXV], Fs[MAXV], Fc[MAXV], acc[MAXV];
+                    for (int v = 0; v < V; ++v) {
+                        ui[v] = u[(size_t)v * n3 + ci];
+                        acc[v] = T(0.0);
+                    }
+                    for (int m = 0; m < n; ++m) {
+                        const int cm = node_index(n, d, m, a, b);
+                        for (int v = 0; v < V; ++v) um[v] = u[(size_t)v * n3 + cm];
+                        kep_flux(P.ph, s[ci], ui, s[cm], um, d, Fs);  // two-point flux
+                        flux_conv(P.ph, um, s[cm], d, Fc);             // standard nodal flux
+                        const T Dim = T(B.D[i * n + m]);
+                        for (int v = 0; v < V; ++v) acc[v] = acc[v] + T(2.0) * Dim * Fs[v] - Dim * Fc[v];
+                    }
+                    for (int v = 0; v < V; ++v)
+                        div[(size_t)v * n3 + ci] = div[(size_t)v * n3 + ci] + metric * acc[v];
+                }
+    }
 }
 
 template <class T>
@@ -517,6 +582,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
                             div[(size_t)v * n3 + c] = div[(size_t)v * n3 + c] + metric * s;
                         }
         }
+        if (P.split) split_form_correction(P, E, B, u, div);
         W[e].div = div;
         // traces of the lifted gradient on the six faces
         for (int f = 0; f < 6; ++f) {
@@ -905,11 +971,11 @@ int oracle_remap(const oracle_problem* p_old, const int8_t* N_new, const uint8_t
             if (A.fv == B.fv && A.n == B.n) {
                 out.assign(src, src + (int64_t)V * A.n * A.n * A.n);
             } else if (!A.fv && !B.fv) {
-                out = map_volume(src, V, A.n, B.n, vmap(A.N, B.N));      // V^{N->N~}
+                out = map_volume(src, V, A.n, B.n, vmap(A.N, B.N, Po.nodes));      // V^{N->N~}
             } else if (!A.fv && B.fv) {
-                out = map_volume(src, V, A.n, B.n, dg2fv(A.N, Po.nfv));  // V^{DG->FV}
+                out = map_volume(src, V, A.n, B.n, dg2fv(A.N, Po.nfv, Po.nodes));  // V^{DG->FV}
             } else {
-                out = map_volume(src, V, A.n, B.n, fv2dg(B.N, Po.nfv));  // V^{FV->DG}
+                out = map_volume(src, V, A.n, B.n, fv2dg(B.N, Po.nfv, Po.nodes));  // V^{FV->DG}
             }
             std::copy(out.begin(), out.end(), dst);
         }
@@ -917,9 +983,10 @@ int oracle_remap(const oracle_problem* p_old, const int8_t* N_new, const uint8_t
     } catch (...) { return -1; }
 }
 
-int oracle_basis(int N, double* x, double* w, double* D, double* Dhat, double* l_minus, double* l_plus) {
+int oracle_basis(int N, double* x, double* w, double* D, double* Dhat, double* l_minus, double* l_plus,
+                 int nodes) {
     try {
-        Basis1D b = make_basis(N);
+        Basis1D b = make_basis(N, nodes);
         std::copy(b.x.begin(), b.x.end(), x);
         std::copy(b.w.begin(), b.w.end(), w);
         std::copy(b.D.begin(), b.D.end(), D);
@@ -930,17 +997,17 @@ int oracle_basis(int N, double* x, double* w, double* D, double* Dhat, double* l
     } catch (...) { return -1; }
 }
 
-int oracle_vmap(int N_from, int N_to, double* M) {
-    try { auto m = vmap(N_from, N_to); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }
+int oracle_vmap(int N_from, int N_to, double* M, int nodes) {
+    try { auto m = vmap(N_from, N_to, nodes); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }
 }
-int oracle_dg2fv(int N, int n_fv, double* M) {
-    try { auto m = dg2fv(N, n_fv); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }
+int oracle_dg2fv(int N, int n_fv, double* M, int nodes) {
+    try { auto m = dg2fv(N, n_fv, nodes); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }
 }
-int oracle_fv2dg(int N, int n_fv, double* M) {
-    try { auto m = fv2dg(N, n_fv); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }
+int oracle_fv2dg(int N, int n_fv, double* M, int nodes) {
+    try { auto m = fv2dg(N, n_fv, nodes); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }
 }
-int oracle_leg_vandermonde(int N, double* V) {
-    try { auto m = leg_vandermonde(N); std::copy(m.begin(), m.end(), V); return 0; } catch (...) { return -1; }
+int oracle_leg_vandermonde(int N, double* V, int nodes) {
+    try { auto m = leg_vandermonde(N, nodes); std::copy(m.begin(), m.end(), V); return 0; } catch (...) { return -1; }
 }
 
 static Phys phys_only(const oracle_problem* p) {

@@ -42,6 +42,9 @@ typedef struct {
                               between DG elements and local Lax-Friedrichs on every face touching FV data */
     const int8_t* N;       /* per element DG degree (kept while FV)      */
     const uint8_t* fv;     /* per element: 1 = FV sub-cell element       */
+    int nodes;             /* 0 = Legendre-Gauss, 1 = Legendre-Gauss-Lobatto */
+    int split;             /* 1 = split-form volume integral, kinetic-energy-preserving
+                              two-point flux (needs nodes = 1), Sec. 3.5     */
 } oracle_problem;
 
 /* 0 on success, negative on a malformed problem. */
@@ -94,13 +97,14 @@ int oracle_adapt_decide(const oracle_problem* p, const double* Ip, const double*
 int oracle_remap(const oracle_problem* p_old, const int8_t* N_new, const uint8_t* fv_new,
                  const double* U_old, double* U_new);
 
-/* Reference-element operators (for pins). Matrices are row-major. */
+/* Reference-element operators (for pins). Matrices are row-major; nodes:
+ * 0 = Legendre-Gauss, 1 = Legendre-Gauss-Lobatto. */
 int oracle_basis(int N, double* x, double* w, double* D, double* Dhat,
-                 double* l_minus, double* l_plus);
-int oracle_vmap(int N_from, int N_to, double* M);          /* (N_to+1) x (N_from+1) */
-int oracle_dg2fv(int N, int n_fv, double* M);              /* n_fv x (N+1)          */
-int oracle_fv2dg(int N, int n_fv, double* M);              /* (N+1) x n_fv          */
-int oracle_leg_vandermonde(int N, double* V);              /* V[i][m] = Lhat_m(x_i) */
+                 double* l_minus, double* l_plus, int nodes);
+int oracle_vmap(int N_from, int N_to, double* M, int nodes);   /* (N_to+1) x (N_from+1) */
+int oracle_dg2fv(int N, int n_fv, double* M, int nodes);       /* n_fv x (N+1)          */
+int oracle_fv2dg(int N, int n_fv, double* M, int nodes);       /* (N+1) x n_fv          */
+int oracle_leg_vandermonde(int N, double* V, int nodes);       /* V[i][m] = Lhat_m(x_i) */
 
 /* Pointwise physics (for pins): convective and viscous flux in direction
  * dir of state u (V) and conservative gradient g (3*V, g[d*V+v] = du_v/dx_d). */

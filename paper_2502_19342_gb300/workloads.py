@@ -40,15 +40,18 @@ def species_set(specs, mu=0.0, Pr=0.72, Sc=1.0, rho_ref=1.0):
     )
 
 
-def make_problem(domains, species, n_fv, N, fv=None, riemann=0):
-    """domains: list of (dims(3), lo(3), hi(3)); species: dict from species_set."""
+def make_problem(domains, species, n_fv, N, fv=None, riemann=0, nodes=0, split=0):
+    """domains: list of (dims(3), lo(3), hi(3)); species: dict from species_set;
+    nodes 0 = Legendre-Gauss, 1 = Legendre-Gauss-Lobatto; split 1 = split-form
+    volume integral (LGL only)."""
     dims = np.array([d[0] for d in domains], np.int32).reshape(-1, 3)
     lo = np.array([d[1] for d in domains], float).reshape(-1, 3)
     hi = np.array([d[2] for d in domains], float).reshape(-1, 3)
     n_elem = int(np.prod(dims, axis=1).sum())
     N = np.broadcast_to(np.asarray(N, np.int8), (n_elem,)).copy()
     fv = np.zeros(n_elem, np.uint8) if fv is None else np.broadcast_to(np.asarray(fv, np.uint8), (n_elem,)).copy()
-    p = dict(dims=dims, lo=lo, hi=hi, n_fv=int(n_fv), riemann=int(riemann), N=N, fv=fv)
+    p = dict(dims=dims, lo=lo, hi=hi, n_fv=int(n_fv), riemann=int(riemann), N=N, fv=fv, nodes=int(nodes),
+             split=int(split))
     p.update({k: np.array(v, float) for k, v in species.items()})
     return p
 
@@ -93,12 +96,25 @@ def element_index(prob):
     return np.concatenate(dom), np.concatenate(pos), np.concatenate(corner), np.concatenate(h)
 
 
-def _ref_points(n, is_fv):
-    """Reference coordinates of the points of one direction: LG nodes (numpy's
-    Gauss-Legendre rule) for DG, sub-cell centres for FV."""
+def lgl_nodes(n):
+    """Legendre-Gauss-Lobatto points of n = N+1 nodes: -1, the roots of P_N'
+    (numpy's Legendre series), +1."""
+    N = n - 1
+    inner = np.polynomial.legendre.Legendre.basis(N).deriv().roots() if N > 1 else np.zeros(0)
+    return np.concatenate([[-1.0], np.sort(np.real(inner)), [1.0]])
+
+
+def dg_points(n, nodes=0):
+    """DG nodes of one direction: LG (numpy's Gauss-Legendre rule) or LGL."""
+    return lgl_nodes(n) if nodes == 1 else np.polynomial.legendre.leggauss(n)[0]
+
+
+def _ref_points(n, is_fv, nodes=0):
+    """Reference coordinates of the points of one direction: DG nodes for DG,
+    sub-cell centres for FV."""
     if is_fv:
         return -1.0 + (np.arange(n) + 0.5) * (2.0 / n)
-    return np.polynomial.legendre.leggauss(n)[0]
+    return dg_points(n, nodes)
 
 
 def build_state(prob, prim_fn, chunk=4096):
@@ -119,7 +135,7 @@ def build_state(prob, prim_fn, chunk=4096):
             sel = np.nonzero((npd == n) & (fv == isfv))[0]
             if len(sel) == 0:
                 continue
-            r = _ref_points(int(n), isfv)
+            r = _ref_points(int(n), isfv, int(prob.get("nodes", 0)))
             kk, jj, ii = np.meshgrid(r, r, r, indexing="ij")
             ref = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1)  # (n^3, 3), x fastest
             for s in range(0, len(sel), chunk):
@@ -291,7 +307,7 @@ def _fourier_on_mesh(prob, k1, c, L, chunk=4096):
     out = [np.zeros(off[-1]) for _ in range(len(c))]
     for n in np.unique(npd):
         sel = np.nonzero(npd == n)[0]
-        r = (np.polynomial.legendre.leggauss(int(n))[0] + 1) / 2
+        r = (dg_points(int(n), int(prob.get("nodes", 0))) + 1) / 2
         E = [np.exp(1j * w * ((np.arange(dims[a])[:, None] + r[None, :]) * h[a] + lo[a])[..., None] * k1)
              for a in range(3)]  # (n_a, n, K) per axis
         for q, comp in enumerate(c):

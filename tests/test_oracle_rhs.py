@@ -13,8 +13,19 @@ from paper_2502_19342_gb300 import workloads as W
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "freestream_table.txt")
 
 
+def _dg_weights(n, nodes):
+    """Quadrature weights of n DG nodes: numpy's Gauss rule (LG), or for LGL the
+    weights that make the rule exact up to degree n-1 on the LGL points
+    (a Vandermonde solve)."""
+    if nodes == 0:
+        return np.polynomial.legendre.leggauss(n)[1]
+    x = W.lgl_nodes(n)
+    mom = np.array([(1 - (-1) ** (k + 1)) / (k + 1) for k in range(n)])
+    return np.linalg.solve(np.vander(x, n, increasing=True).T, mom)
+
+
 def _weights(prob):
-    """Quadrature weight x Jacobian of every DOF (DG: LG weights; FV: sub-cell volume)."""
+    """Quadrature weight x Jacobian of every DOF (DG: weights of the node family; FV: sub-cell volume)."""
     off, size = W.offsets(prob)
     _, _, _, h = W.element_index(prob)
     V = W.n_vars(prob)
@@ -25,7 +36,7 @@ def _weights(prob):
             w3 = np.full(m ** 3, (2.0 / m) ** 3)
         else:
             m = int(prob["N"][e]) + 1
-            w = np.polynomial.legendre.leggauss(m)[1]
+            w = _dg_weights(m, int(prob.get("nodes", 0)))
             w3 = np.einsum("k,j,i->kji", w, w, w).ravel()
         J = np.prod(h[e]) / 8.0
         wts[off[e]:off[e] + V * m ** 3] = np.tile(w3 * J, V)
@@ -46,13 +57,14 @@ def _per_var(prob, x):
 
 
 def _mixed_problem(seed, nk=2, nel=(3, 3, 3), Nlo=1, Nhi=5, fv_frac=0.3, n_fv=6, riemann=0, mu=2e-3,
-                   box=(1.0, 1.0, 1.0)):
+                   box=(1.0, 1.0, 1.0), nodes=0, split=0):
     specs = [W.AIR, W.HELIUM, W.CO2][:nk]
     sp = W.species_set(specs, mu=mu)
     n = nel[0] * nel[1] * nel[2]
     N = W.random_degrees(n, Nlo, Nhi, seed)
     fv = W.random_fv(n, fv_frac, seed)
-    return W.make_problem([(nel, (0, 0, 0), box)], sp, n_fv=n_fv, N=N, fv=fv, riemann=riemann)
+    return W.make_problem([(nel, (0, 0, 0), box)], sp, n_fv=n_fv, N=N, fv=fv, riemann=riemann, nodes=nodes,
+                          split=split)
 
 
 # ---------------------------------------------------------------- free stream
@@ -62,14 +74,15 @@ def test_golden_freestream_table_parses():
     assert max(rows["Linf"]) < 1e-13
 
 
-@pytest.mark.parametrize("riemann", [0, 1, 2])
-def test_freestream_preserved_on_random_hp_fv_pattern(oracle, riemann):
+@pytest.mark.parametrize("riemann,nodes,split", [(0, 0, 0), (1, 0, 0), (2, 0, 0), (0, 1, 0), (1, 1, 1)])
+def test_freestream_preserved_on_random_hp_fv_pattern(oracle, riemann, nodes, split):
     """Sec. 4.1: a uniform state stays uniform to round-off after 180 steps on a
     random distribution of degrees N in [2,5] and FV elements (N_FV = 8).  The
     errors must stay at the level the paper reports in Table 1 (scaled by the
     state's magnitude, which is O(1) in both)."""
     rows = {l.split()[0]: [float(x) for x in l.split()[1:]] for l in open(GOLDEN) if l[0] != "#" and l.strip()}
-    prob = _mixed_problem(3, nel=(3, 3, 3), Nlo=2, Nhi=5, fv_frac=0.3, n_fv=8, riemann=riemann)
+    prob = _mixed_problem(3, nel=(3, 3, 3), Nlo=2, Nhi=5, fv_frac=0.3, n_fv=8, riemann=riemann, nodes=nodes,
+                          split=split)
     U0 = W.constant_state(prob, [0.7, 0.3], (1.0, 1.0, 1.0), 1.0)
     R = oracle.eval_rhs(prob, U0)
     assert np.abs(R).max() < 5e-12
@@ -85,13 +98,15 @@ def test_freestream_preserved_on_random_hp_fv_pattern(oracle, riemann):
 
 
 # ---------------------------------------------------------------- conservation
-@pytest.mark.parametrize("nk,riemann,seed", [(2, 0, 1), (3, 1, 2), (2, 1, 4), (3, 0, 5), (3, 2, 6)])
-def test_discrete_conservation_periodic(oracle, nk, riemann, seed):
+@pytest.mark.parametrize("nk,riemann,seed,nodes,split", [(2, 0, 1, 0, 0), (3, 1, 2, 0, 0), (2, 1, 4, 0, 0),
+                                                          (3, 0, 5, 0, 0), (3, 2, 6, 0, 0), (3, 1, 7, 1, 0),
+                                                          (3, 0, 8, 1, 1), (2, 2, 9, 1, 1)])
+def test_discrete_conservation_periodic(oracle, nk, riemann, seed, nodes, split):
     """Sum of J w R over DG nodes plus sub-cell volume x R over FV cells vanishes
     for every conserved variable on a periodic mesh, through p- and DG/FV
     interfaces (the L2 projection and the pseudo-inverse preserve face integrals)."""
     prob = _mixed_problem(seed, nk=nk, nel=(3, 4, 3), Nlo=1, Nhi=6, fv_frac=0.3, n_fv=7, riemann=riemann,
-                          box=(1.0, 1.3, 0.8))
+                          box=(1.0, 1.3, 0.8), nodes=nodes, split=split)
     U = W.smooth_random_state(prob, seed, amp=0.1)
     R = oracle.eval_rhs(prob, U)
     wts = _weights(prob)
@@ -431,7 +446,7 @@ def test_viscous_terms_converge_to_analytic_derivatives(oracle):
 
 
 # ---------------------------------------------------------------- convergence order
-def _advected_l2(oracle, nel, N_of, fv_of=None, wave=(1, 0, 0), T=0.05, n_fv=7):
+def _advected_l2(oracle, nel, N_of, fv_of=None, wave=(1, 0, 0), T=0.05, n_fv=7, nodes=0, split=0):
     """L2 error in rho_1 of an advected density/species wave (Euler limit)
     after time T; nel = elements per direction, N_of/fv_of map element
     positions (i, j, k) to the degree / FV flag (checkerboards)."""
@@ -441,7 +456,7 @@ def _advected_l2(oracle, nel, N_of, fv_of=None, wave=(1, 0, 0), T=0.05, n_fv=7):
     N = np.array([N_of(*p) for p in pos], np.int8)
     fv = np.array([fv_of(*p) if fv_of else 0 for p in pos], np.uint8)
     hi = tuple(1.0 if wave[a] else 1.0 / nel[a] for a in range(3))
-    prob = W.make_problem([(dims, (0, 0, 0), hi)], sp, n_fv=n_fv, N=N, fv=fv)
+    prob = W.make_problem([(dims, (0, 0, 0), hi)], sp, n_fv=n_fv, N=N, fv=fv, nodes=nodes, split=split)
     vel = tuple(0.5 * wv for wv in wave)
     c = 0.5 * sum(wv * wv for wv in wave)
 
@@ -628,3 +643,92 @@ def test_jvp_matches_central_differences(oracle):
     eps = 1e-6
     fd = (oracle.eval_rhs(prob, U + eps * dU) - oracle.eval_rhs(prob, U - eps * dU)) / (2 * eps)
     assert np.abs(fd - dR).max() < 1e-6 * np.abs(dR).max()
+
+
+# ---------------------------------------------------------------- split form on LGL nodes (Sec. 3.5)
+def _lgl_derivative_matrix(n):
+    """D_ij = l_j'(x_i) on the LGL points from the monomial coefficients of the
+    Lagrange polynomials (inverse Vandermonde)."""
+    x = W.lgl_nodes(n)
+    C = np.linalg.inv(np.vander(x, n, increasing=True))  # column j: coefficients of l_j
+    k = np.arange(n)
+    return np.array([[np.sum(k[1:] * C[1:, j] * xi ** (k[1:] - 1)) for j in range(n)] for xi in x])
+
+
+def _prims(prob, blk):
+    """rho, v (3), p, H, Y_k per node of one element block (V, n^3)."""
+    nk = len(prob["gamma"])
+    cv = prob["Rgas"] / (prob["gamma"] - 1.0)
+    rho = blk[:nk].sum(0)
+    Y = blk[:nk] / rho
+    v = blk[nk:nk + 3] / rho
+    eps = blk[nk + 3] / rho - 0.5 * (v ** 2).sum(0)
+    cvm, cpm = Y.T @ cv, Y.T @ (prob["gamma"] * cv)
+    p = rho * (cpm - cvm) / cvm * eps
+    H = (blk[nk + 3] + p) / rho
+    return rho, v, p, H, Y
+
+
+def test_split_form_volume_term_equals_the_quadratic_and_cubic_split_forms(oracle):
+    """With arithmetic means, sum_m 2 D_im {a}{b} = (D(ab) + a Db + b Da)_i / 2 and
+    sum_m 2 D_im {a}{b}{c} = (D(abc) + a D(bc) + b D(ac) + c D(ab) + ab Dc + ac Db
+    + bc Da)_i / 4 (D 1 = 0).  The split-form R minus the standard LGL R on a
+    DG element is therefore, per direction d with metric 2/h_d, minus the
+    metric times [split(rho Y_k v_d) - D(rho_k v_d)], [split(rho v_d v_j) +
+    D p delta_jd - D(rho v_d v_j + p delta_jd)], [split(rho v_d H) - D(rho H v_d)]
+    along every line; zero on FV elements.  D comes from numpy (monomials)."""
+    prob = _mixed_problem(11, nk=3, nel=(2, 3, 2), Nlo=1, Nhi=6, fv_frac=0.25, n_fv=7, nodes=1, mu=1e-3)
+    U = W.smooth_random_state(prob, 11, amp=0.2)
+    Rstd = oracle.eval_rhs(prob, U)
+    Rspl = oracle.eval_rhs(dict(prob, split=1), U)
+    nk = 3
+    V = nk + 4
+    off, _ = W.offsets(prob)
+    npd = W.points_per_dir(prob)
+    _, _, _, h = W.element_index(prob)
+    checked = 0
+    for e in range(len(off)):
+        n = int(npd[e])
+        blk = U[off[e]:off[e] + V * n ** 3].reshape(V, n, n, n)  # (v, k, j, i)
+        diff = (Rspl - Rstd)[off[e]:off[e] + V * n ** 3].reshape(V, n, n, n)
+        if prob["fv"][e]:
+            assert np.abs(diff).max() == 0.0
+            continue
+        D = _lgl_derivative_matrix(n)
+        rho, v, p, H, Y = _prims(prob, blk.reshape(V, -1).T.T.reshape(V, -1))
+        sh = (n, n, n)
+        rho, p, H = rho.reshape(sh), p.reshape(sh), H.reshape(sh)
+        v, Y = v.reshape(3, *sh), Y.reshape(nk, *sh)
+        expect = np.zeros((V, n, n, n))
+        for d in range(3):
+            ax = 2 - d  # array axis of direction d in (k, j, i) order
+
+            def Dd(f):
+                return np.moveaxis(np.tensordot(D, np.moveaxis(f, ax, 0), axes=(1, 0)), 0, ax)
+
+            def s2(a, b):
+                return 0.5 * (Dd(a * b) + a * Dd(b) + b * Dd(a))
+
+            def s3(a, b, c):
+                return 0.25 * (Dd(a * b * c) + a * Dd(b * c) + b * Dd(a * c) + c * Dd(a * b)
+                               + a * b * Dd(c) + a * c * Dd(b) + b * c * Dd(a))
+            vd = v[d]
+            terms = [s3(rho, vd, Y[k]) - Dd(rho * Y[k] * vd) for k in range(nk)]
+            terms += [s3(rho, vd, v[j]) - Dd(rho * vd * v[j]) for j in range(3)]
+            terms += [s3(rho, vd, H) - Dd(rho * H * vd)]
+            expect -= (2.0 / h[e][d]) * np.array(terms)
+        scale = np.abs(Rstd).max()
+        np.testing.assert_allclose(diff, expect, atol=1e-11 * scale)
+        checked += 1
+    assert checked > 4
+
+
+@pytest.mark.parametrize("split", [0, 1])
+def test_convergence_lgl_uniform_degree_3(split):
+    """Order N+1 on LGL nodes, standard and split form (advected wave, Euler);
+    the LGL scheme reaches its asymptotic order on finer meshes than LG (at
+    K = 4 -> 8 the observed order is 3.3-3.5)."""
+    import oracle
+    e1 = _advected_l2(oracle, (16, 1, 1), lambda i, j, k: 3, nodes=1, split=split)
+    e2 = _advected_l2(oracle, (32, 1, 1), lambda i, j, k: 3, nodes=1, split=split)
+    assert _order(e1, e2, 16, 32) > 3.7, (e1, e2)
