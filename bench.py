@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-split", action="store_true", help="skip the split-form (LGL) measurement")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the default volume-kernel launch instead of timing variants first")
     p.add_argument("--profile-timed", action="store_true",
@@ -268,6 +269,50 @@ def adjoint_cost(steps=50):
             "adjoint_ms_per_step_recomputed_stages": bwd / steps, "adjoint_over_forward_recomputed": bwd / fwd,
             "gradients_identical": same,
             "note": "adjoint step = 3 vector-Jacobian products (+2 forward stages when the stages are recomputed)"}
+
+
+def split_form_run(nel, warmup=2, steps=1):
+    """The turbulence workload with the jet's scheme (Sec. 5.1): split-form DGSEM
+    on LGL nodes with the kinetic-energy-preserving flux, Roe-HH between DG
+    elements and LLF where FV data meet; adaptation cycles as in the main
+    measurement.  DOF-stage/s and the roofline of the split volume kernel."""
+    import torch
+    from paper_2502_19342_gb300 import dgfv, workloads as W
+    prob, U = W.turbulence(seed=0, nel=(nel, nel, nel), N0=4, nodes=1, split=1, riemann=2)
+    ctx = dgfv.Context(prob, N_min=1, N_max=7, opts=dict(cfl_c=0.5, cfl_v=0.5, thresholds=W.THRESHOLDS))
+    ctx.set_state(torch.from_numpy(U).cuda())
+    for _ in range(warmup):
+        cycle(ctx)
+    s = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile_enable(True)
+    torch.cuda.synchronize()
+    units = 0.0
+    ev0.record(s)
+    for _ in range(steps):
+        units += cycle(ctx)[0]
+    ev1.record(s)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    N_now, fv_now = ctx.get_degrees()
+    per_dof, per_step = flops_per_dof(dict(prob, N=N_now, fv=fv_now))
+    kms, kl = prof["dg_volume"]
+    dofs_per_launch = units / (steps * STEPS_PER_CYCLE * STAGES_PER_STEP)
+    achieved = per_step[4] * dofs_per_launch / (kms / kl * 1e-3) / 1e12
+    ctx.close()
+    return {"workload": f"turbulent multi-component decay, {nel}^3 elements, split-form DGSEM on LGL nodes "
+                        "(kinetic-energy-preserving two-point flux), Roe-HH between DG elements, LLF where FV "
+                        "data meet, N in 1..7 by the indicator, N_FV=8, 3 species, viscous",
+            "value": units / (ms * 1e-3), "unit": "DOF-stage/s", "ms_per_step": ms / steps,
+            "fv_elements": int(fv_now.sum()),
+            "degree_histogram": np.bincount(N_now[fv_now == 0], minlength=8).tolist(),
+            "volume_kernel": {"kernel": "k_dg_volume_split", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                              "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                              "flops_per_dof": per_step[4], "share_of_step": kms / sum(v[0] for v in prof.values())},
+            "flops_per_dof_total": per_dof,
+            "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()}}
 
 
 def batched_comparison(steps=5):
@@ -493,6 +538,7 @@ def main():
         cpu = None if args.no_cpu else cpu_baseline(dict(prob, N=N_now, fv=fv_now))
         adjoint = adjoint_cost()
         batched = None if args.no_batched else batched_comparison()
+        split = None if args.no_split else split_form_run(args.nel)
         launches = int(sum(v[1] for v in prof.values()))
         last = pattern[-1]
         line = {"metric": "DOF-stage updates/s (FP64 RHS, hp-mixed)", "value": value, "unit": "DOF-stage/s",
@@ -506,7 +552,7 @@ def main():
                            "volume_launch": ({str(k): v for k, v in tuned.items()} if tuned else "default"),
                            "l2": "inputs larger than L2 (state ~1.2 GB)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "adjoint": adjoint,
-                "batched_domains": batched,
+                "batched_domains": batched, "split_form": split,
                 "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
                 "clocks": clk.summary()}
         print(json.dumps(line))

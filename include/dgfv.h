@@ -89,6 +89,10 @@ typedef struct {
     double T_fv_off;    /* FV -> DG when I_h > T_fv_off                        */
     double T_ref;       /* N -> N+1 when I_p < T_ref                           */
     double T_crs;       /* N -> N-1 when I_p > T_crs                           */
+    int nodes;          /* DG nodes: 0 Legendre-Gauss, 1 Legendre-Gauss-Lobatto  */
+    int split_form;     /* 1: split-form volume integral with the kinetic-energy-
+                           preserving two-point flux of Pirozzoli (Sec. 3.5);
+                           needs nodes = 1                                    */
 } dgfv_opts;
 
 typedef struct {
@@ -245,7 +249,8 @@ void dgfv_destroy(dgfv_ctx* ctx);
 /* Operator bank entries, for checks against an independent computation:
  * which = 0 nodes, 1 weights, 2 Dhat (n x n), 3 l(-1), 4 l(+1),
  * 5 V^{N->M} ((M+1) x (N+1)), 6 V^{DG->FV} (N_fv x (N+1)),
- * 7 V^{FV->DG} ((N+1) x N_fv), 8 inverse Legendre Vandermonde.
+ * 7 V^{FV->DG} ((N+1) x N_fv), 8 inverse Legendre Vandermonde, 9 D (n x n),
+ * all on the context's node family.
  * Copies the row-major matrix to host memory `out` of `cap` doubles and
  * returns the number of entries, or a negative status. */
 int64_t dgfv_bank_entry(dgfv_ctx* ctx, int which, int N, int M, double* out, int64_t cap);

@@ -260,7 +260,7 @@ void point_flux(const Problem& P, const T* uL, const T* gL, const T* uR, const T
 // fraction times the mean mass flux, so that the species fluxes add up to
 // the mass flux {rho}{v_d}).
 template <class T>
-void kep_flux(const Phys& ph, const Prim<T>& a, const T* ua, const Prim<T>& b, const T* ub, int d, T* F) {
+void kep_flux(const Phys& ph, const Prim<T>& a, const T& Ha, const Prim<T>& b, const T& Hb, int d, T* F) {
     const int nk = ph.nk;
     const T rho = T(0.5) * (a.rho + b.rho);
     const T vd = T(0.5) * (a.v[d] + b.v[d]);
@@ -268,24 +268,25 @@ void kep_flux(const Phys& ph, const Prim<T>& a, const T* ua, const Prim<T>& b, c
     for (int k = 0; k < nk; ++k) F[k] = mass * (T(0.5) * (a.Y[k] + b.Y[k]));
     for (int j = 0; j < 3; ++j) F[nk + j] = mass * (T(0.5) * (a.v[j] + b.v[j]));
     F[nk + d] = F[nk + d] + T(0.5) * (a.p + b.p);
-    const T Ha = (ua[nk + 3] + a.p) / a.rho, Hb = (ub[nk + 3] + b.p) / b.rho;
     F[nk + 3] = mass * (T(0.5) * (Ha + Hb));
 }
 
-// Split form on LGL nodes (Sec. 3.5): the convective part of the volume term,
-// sum_m Dhat_im F^c(u_m) = sum_m D_im F^c(u_m) - (B_ii/w_i) F^c(u_i) (summation
-// by parts, B = diag(-1, 0, .., 0, 1)), is replaced by
-//   sum_m 2 D_im F#(u_i, u_m) - (B_ii/w_i) F^c(u_i)
-// along every direction; the viscous part keeps the standard form.  Applied as
-// a correction to the standard volume term already in div.
+// Split form on LGL nodes (Sec. 3.5): the convective part of the volume term
+// of node i along direction d is
+//   sum_m 2 D_im F#(u_i, u_m) - (B_ii/w_i) F^c(u_i),   B = diag(-1, 0, .., 0, 1)
+// (the strong form with the two-point flux; by summation by parts the weak
+// form's sum_m Dhat_im F^c(u_m) is the same expression with F^c(u_m) in place
+// of 2 F#(u_i, u_m)).  Added to div, which holds the viscous part.
 template <class T>
-void split_form_correction(const Problem& P, const Elem& E, const Basis1D& B, const T* u, vector<T>& div) {
+void split_form_convective(const Problem& P, const Elem& E, const Basis1D& B, const T* u, vector<T>& div) {
     const int V = P.V, n = E.n, n3 = n * n * n;
     vector<Prim<T>> s(n3);
+    vector<T> H(n3);  // total enthalpy (rho E + p) / rho
     for (int c = 0; c < n3; ++c) {
         T uc[MAXV];
         for (int v = 0; v < V; ++v) uc[v] = u[(size_t)v * n3 + c];
         cons_to_prim(P.ph, uc, s[c]);
+        H[c] = (uc[P.ph.nk + 3] + s[c].p) / s[c].rho;
     }
     for (int d = 0; d < 3; ++d) {
         const T metric = T(2.0 / E.h[d]);
@@ -293,18 +294,22 @@ void split_form_correction(const Problem& P, const Elem& E, const Basis1D& B, co
             for (int a = 0; a < n; ++a)
                 for (int i = 0; i < n; ++i) {
                     const int ci = node_index(n, d, i, a, b);
-                    T ui[MAXV], um[MAXV], Fs[MAXV], Fc[MAXV], acc[MAXV];
+                    T ui[MAXV], Fs[MAXV], acc[MAXV];
                     for (int v = 0; v < V; ++v) {
                         ui[v] = u[(size_t)v * n3 + ci];
                         acc[v] = T(0.0);
                     }
                     for (int m = 0; m < n; ++m) {
                         const int cm = node_index(n, d, m, a, b);
-                        for (int v = 0; v < V; ++v) um[v] = u[(size_t)v * n3 + cm];
-                        kep_flux(P.ph, s[ci], ui, s[cm], um, d, Fs);  // two-point flux
-                        flux_conv(P.ph, um, s[cm], d, Fc);             // standard nodal flux
-                        const T Dim = T(B.D[i * n + m]);
-                        for (int v = 0; v < V; ++v) acc[v] = acc[v] + T(2.0) * Dim * Fs[v] - Dim * Fc[v];
+                        kep_flux(P.ph, s[ci], H[ci], s[cm], H[cm], d, Fs);
+                        const T two_D = T(2.0 * B.D[i * n + m]);
+                        for (int v = 0; v < V; ++v) acc[v] = acc[v] + two_D * Fs[v];
+                    }
+                    if (i == 0 || i == n - 1) {  // boundary nodes: -(B_ii/w_i) F^c(u_i)
+                        T Fc[MAXV];
+                        flux_conv(P.ph, ui, s[ci], d, Fc);
+                        const T c = T((i == 0 ? 1.0 : -1.0) / B.w[i]);
+                        for (int v = 0; v < V; ++v) acc[v] = acc[v] + c * Fc[v];
                     }
                     for (int v = 0; v < V; ++v)
                         div[(size_t)v * n3 + ci] = div[(size_t)v * n3 + ci] + metric * acc[v];
@@ -562,9 +567,13 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
             PrimGrad<T> G;
             prim_grad(P.ph, gc, s, G);  // one chain rule per node, shared by the three directions
             for (int d = 0; d < 3; ++d) {
-                flux_conv(P.ph, uc, s, d, Fc);
                 flux_visc(P.ph, G, s, d, Fv);
-                for (int v = 0; v < V; ++v) F[((size_t)d * V + v) * n3 + c] = Fc[v] + Fv[v];
+                if (P.split) {  // the convective part follows in split_form_convective
+                    for (int v = 0; v < V; ++v) F[((size_t)d * V + v) * n3 + c] = Fv[v];
+                } else {
+                    flux_conv(P.ph, uc, s, d, Fc);
+                    for (int v = 0; v < V; ++v) F[((size_t)d * V + v) * n3 + c] = Fc[v] + Fv[v];
+                }
             }
         }
         // volume integral sum_m Ftilde_m Dhat_im / J
@@ -582,7 +591,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
                             div[(size_t)v * n3 + c] = div[(size_t)v * n3 + c] + metric * s;
                         }
         }
-        if (P.split) split_form_correction(P, E, B, u, div);
+        if (P.split) split_form_convective(P, E, B, u, div);
         W[e].div = div;
         // traces of the lifted gradient on the six faces
         for (int f = 0; f < 6; ++f) {

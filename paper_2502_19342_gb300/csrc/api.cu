@@ -190,17 +190,26 @@ int build_bank(dgfv_ctx* c) {
         return o;
     };
     std::memset(&c->bi, 0, sizeof(c->bi));
+    const int kind = c->opts.nodes;
     for (int n = c->N_min + 1; n <= c->N_max + 1; ++n) {
-        Bank1D b = make_bank(n);
+        Bank1D b = make_bank(n, kind);
         c->bi.dhat[n] = put(b.Dhat);
+        if (c->opts.split_form) {
+            // 2D - W^{-1}B: the boundary correction -(B_ii/w_i) F(u_i) folded into the diagonal
+            std::vector<double> S(n * n);
+            for (int i = 0; i < n * n; ++i) S[i] = 2.0 * b.D[i];
+            S[0] += 1.0 / b.w[0];
+            S[n * n - 1] -= 1.0 / b.w[n - 1];
+            c->bi.dsplit[n] = put(S);
+        }
         c->bi.lm[n] = put(b.lm);
         c->bi.lp[n] = put(b.lp);
         c->bi.lhm[n] = put(b.lhm);
         c->bi.lhp[n] = put(b.lhp);
         c->bi.vinv[n] = put(b.vinv);
-        c->bi.d2f[n] = put(make_dg2fv(n, c->nfv));
-        c->bi.f2d[n] = put(make_fv2dg(n, c->nfv));
-        for (int m = c->N_min + 1; m <= c->N_max + 1; ++m) c->bi.vm[n][m] = put(make_vmap(n, m));
+        c->bi.d2f[n] = put(make_dg2fv(n, c->nfv, kind));
+        c->bi.f2d[n] = put(make_fv2dg(n, c->nfv, kind));
+        for (int m = c->N_min + 1; m <= c->N_max + 1; ++m) c->bi.vm[n][m] = put(make_vmap(n, m, kind));
     }
     TRY(dalloc(c, &c->d_bank, bank.size()));
     CK(cudaMemcpy(c->d_bank, bank.data(), bank.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -241,6 +250,21 @@ void make_tiles(const dgfv_ctx* c, TileSet& t, Sel sel, Per per_tile) {
     }
 }
 
+// Shared memory of one volume tile (standard or split form).
+size_t vol_smem(const dgfv_ctx* c, int n, int count) {
+    return c->opts.split_form ? volume_split_smem_bytes(c->nk, n, count, c->ph.viscous != 0)
+                              : volume_smem_bytes(c->nk, n, count);
+}
+
+// The volume kernel of the context's scheme.
+void launch_volume(const dgfv_ctx* c, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
+                   cudaStream_t s, int variant) {
+    if (c->opts.split_form)
+        launch_dg_volume_split(c->nk, P, T, ntiles, smem, U, s);
+    else
+        launch_dg_volume(c->nk, P, T, ntiles, smem, U, s, variant);
+}
+
 // Elements per volume tile: about 256 nodes per CTA unless autotuned.
 int volume_per_tile(const dgfv_ctx* c, int n) {
     return c->vol_per_tile[n] > 0 ? c->vol_per_tile[n] : std::max(1, 256 / (n * n * n));
@@ -277,7 +301,7 @@ int apply_layout(dgfv_ctx* c) {
     c->dg.bin_smem.assign(c->dg.bin_first.size(), 0);
     for (size_t b = 0; b < c->dg.bin_first.size(); ++b)
         for (int t = c->dg.bin_first[b]; t < c->dg.bin_first[b] + c->dg.bin_count[b]; ++t) {
-            const size_t x = volume_smem_bytes(c->nk, c->dg.n[t], c->dg.count[t]);
+            const size_t x = vol_smem(c, c->dg.n[t], c->dg.count[t]);
             c->dg.bin_smem[b] = std::max(c->dg.bin_smem[b], x);
             sm = std::max(sm, x);
         }
@@ -382,10 +406,10 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
         Timed t(c, K_VOLUME, s);
         if (per_bin)
             for (size_t bi = 0; bi < c->dg.bin_first.size(); ++bi)
-                launch_dg_volume(c->nk, P, c->dg.view(c->dg.bin_first[bi]), c->dg.bin_count[bi], c->dg.bin_smem[bi],
-                                 Uin, s, c->vol_variant);
+                launch_volume(c, P, c->dg.view(c->dg.bin_first[bi]), c->dg.bin_count[bi], c->dg.bin_smem[bi], Uin, s,
+                              c->vol_variant);
         else
-            launch_dg_volume(c->nk, P, c->dg.view(), c->dg.ntiles, c->dg.smem, Uin, s, c->vol_variant);
+            launch_volume(c, P, c->dg.view(), c->dg.ntiles, c->dg.smem, Uin, s, c->vol_variant);
     }
     {
         Timed t(c, K_FLUX, s);
@@ -530,6 +554,9 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     c->nfv = mesh->N_fv;
     c->ph.nk = c->nk;
     if (opts->riemann < DGFV_RIEMANN_LLF || opts->riemann > DGFV_RIEMANN_HYBRID) return cleanup(DGFV_ERR_ARG);
+    if (opts->nodes < 0 || opts->nodes > 1 || opts->split_form < 0 || opts->split_form > 1 ||
+        (opts->split_form && opts->nodes != 1))
+        return cleanup(DGFV_ERR_ARG);
     c->ph.riemann = opts->riemann;
     c->ph.viscous = 0;
     c->ph.maxD = 0.0;
@@ -705,6 +732,7 @@ int dgfv_compute_dt_noalloc(dgfv_ctx* c, const double* d_U, double* d_out3, void
 static int adj_prepare(dgfv_ctx* c) {
     if (c->n_fv_elems) return fail(c, DGFV_ERR_ARG, "the adjoint supports DG elements only (the pattern has FV elements)");
     if (c->ph.riemann != 0) return fail(c, DGFV_ERR_ARG, "the adjoint supports the local Lax-Friedrichs flux only");
+    if (c->opts.split_form) return fail(c, DGFV_ERR_ARG, "the adjoint supports the standard volume integral only");
     if (c->adj_ready) return DGFV_OK;
     TRY(dalloc(c, &c->d_fbar, c->cap_fpts * c->V));
     TRY(dalloc(c, &c->d_ubar, c->cap_fpts * c->V));
@@ -963,7 +991,7 @@ int dgfv_autotune(dgfv_ctx* c, int* per_tile_out, void* stream) {
         const Params P = params(c);
         double best_ms = 1e300;
         int best = 0;
-        for (int var = 0; var < 4; ++var) {
+        for (int var = 0; var < (c->opts.split_form ? 0 : 4); ++var) {  // the split kernel has one variant
             launch_dg_volume(c->nk, P, c->dg.view(), c->dg.ntiles, c->dg.smem, c->d_U, s, var);  // warm
             CK(cudaEventRecord(e0, s));
             for (int r = 0; r < 3; ++r) launch_dg_volume(c->nk, P, c->dg.view(), c->dg.ntiles, c->dg.smem, c->d_U, s, var);
@@ -990,16 +1018,16 @@ int dgfv_autotune(dgfv_ctx* c, int* per_tile_out, void* stream) {
             if (per == last) continue;
             last = per;
             if (per > 1 && per * n * n * n > 2048) continue;
-            if (volume_smem_bytes(c->nk, n, per) > 200 * 1024) continue;
+            if (vol_smem(c, n, per) > 200 * 1024) continue;
             c->vol_per_tile[n] = per;
             TileSet& t = c->dg;
             make_tiles(c, t, [&](int e) { return !c->fv[e] && c->npts[e] == n; }, [&](int) { return per; });
             TRY(upload_tiles(c, t));
-            const size_t sm = volume_smem_bytes(c->nk, n, per);
+            const size_t sm = vol_smem(c, n, per);
             const Params P = params(c);
-            launch_dg_volume(c->nk, P, t.view(), t.ntiles, sm, c->d_U, s, c->vol_variant);  // warm
+            launch_volume(c, P, t.view(), t.ntiles, sm, c->d_U, s, c->vol_variant);  // warm
             CK(cudaEventRecord(e0, s));
-            for (int r = 0; r < 3; ++r) launch_dg_volume(c->nk, P, t.view(), t.ntiles, sm, c->d_U, s, c->vol_variant);
+            for (int r = 0; r < 3; ++r) launch_volume(c, P, t.view(), t.ntiles, sm, c->d_U, s, c->vol_variant);
             CK(cudaEventRecord(e1, s));
             CK(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -1033,7 +1061,8 @@ int64_t dgfv_bank_entry(dgfv_ctx* c, int which, int N, int M, double* out, int64
     const int n = N + 1, m = M + 1;
     std::vector<double> v;
     try {
-        Bank1D b = make_bank(n);
+        const int kind = c->opts.nodes;
+        Bank1D b = make_bank(n, kind);
         switch (which) {
             case 0: v = b.x; break;
             case 1: v = b.w; break;
@@ -1042,11 +1071,12 @@ int64_t dgfv_bank_entry(dgfv_ctx* c, int which, int N, int M, double* out, int64
             case 4: v = b.lp; break;
             case 5:
                 if (M < c->N_min || M > c->N_max) return DGFV_ERR_ARG;
-                v = make_vmap(n, m);
+                v = make_vmap(n, m, kind);
                 break;
-            case 6: v = make_dg2fv(n, c->nfv); break;
-            case 7: v = make_fv2dg(n, c->nfv); break;
+            case 6: v = make_dg2fv(n, c->nfv, kind); break;
+            case 7: v = make_fv2dg(n, c->nfv, kind); break;
             case 8: v = b.vinv; break;
+            case 9: v = b.D; break;
             default: return DGFV_ERR_ARG;
         }
     } catch (...) {

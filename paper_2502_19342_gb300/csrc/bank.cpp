@@ -12,6 +12,14 @@
 //   V^{DG->FV}                sub-cell means by a Gauss rule on every sub-cell
 //   V^{FV->DG}                Moore-Penrose inverse through a Householder QR factorisation
 //   Legendre Vandermonde^-1   V^-1 = V^T diag(w) (discrete orthonormality, Sec. 3.4)
+// Legendre-Gauss-Lobatto nodes (split form, Sec. 3.5):
+//   nodes                     Newton on f = x P_N - P_{N-1} (f' = (N+1) P_N; its roots
+//                             are +-1 and the zeros of P_N') from Chebyshev-Lobatto points
+//   weights                   2 / (N (N+1) P_N(x)^2)
+//   V^{N->M}, N > M           L2 projection with the exact mass matrix of the coarse
+//                             basis (LGL quadrature under-integrates it), Cholesky solve
+//   Legendre Vandermonde^-1   V^T diag(w) with the top mode rescaled by its discrete
+//                             norm (the LGL rule is exact for every other mode product)
 #include "bank.h"
 
 #include <cmath>
@@ -32,8 +40,11 @@ void legendre_pd(int n, ld x, ld& P, ld& dP) {
         p1 = p2;
     }
     P = p1;
-    // (1 - x^2) P_n' = n (P_{n-1} - x P_n)
-    dP = n * (p0 - x * p1) / (1 - x * x);
+    // (1 - x^2) P_n' = n (P_{n-1} - x P_n); at x = +-1, P_n'(+-1) = (+-1)^{n-1} n (n+1)/2
+    if (1 - x * x == 0)
+        dP = (x > 0 ? 1 : (n % 2 ? 1 : -1)) * (ld)n * (n + 1) / 2;
+    else
+        dP = n * (p0 - x * p1) / (1 - x * x);
 }
 
 ld legendre_orthonormal(int m, ld x) {
@@ -80,6 +91,48 @@ Nodes gauss(int n) {
     return g;
 }
 
+void barycentric_weights(Nodes& g) {
+    const int n = (int)g.x.size();
+    g.lam.resize(n);
+    for (int j = 0; j < n; ++j) {
+        ld p = 1;
+        for (int k = 0; k < n; ++k)
+            if (k != j) p *= (g.x[j] - g.x[k]);
+        g.lam[j] = 1 / p;
+    }
+}
+
+Nodes lobatto(int n) {
+    if (n < 2) throw std::runtime_error("LGL needs at least two nodes");
+    const int N = n - 1;
+    Nodes g;
+    g.x.resize(n);
+    g.w.resize(n);
+    const ld pi = 3.141592653589793238462643383279502884L;
+    for (int i = 0; i < n; ++i) {
+        ld x = -std::cos(pi * i / N);
+        for (int it = 0; it < 100; ++it) {
+            ld PN, dPN, PM, dPM;
+            legendre_pd(N, x, PN, dPN);
+            legendre_pd(N - 1, x, PM, dPM);
+            const ld f = x * PN - PM, df = (N + 1) * PN;
+            const ld dx = f / df;
+            x -= dx;
+            if (std::fabs((double)dx) < 1e-20) break;
+        }
+        if (i == 0) x = -1;
+        if (i == N) x = 1;
+        ld PN, dPN;
+        legendre_pd(N, x, PN, dPN);
+        g.x[i] = x;
+        g.w[i] = 2 / ((ld)N * (N + 1) * PN * PN);
+    }
+    barycentric_weights(g);
+    return g;
+}
+
+Nodes node_family(int n, int kind) { return kind == 1 ? lobatto(n) : gauss(n); }
+
 // All Lagrange polynomials of the node set at xi (barycentric formula of the second kind).
 std::vector<ld> lagrange_all(const Nodes& g, ld xi) {
     const int n = (int)g.x.size();
@@ -96,9 +149,9 @@ std::vector<double> to_d(const std::vector<ld>& a) { return std::vector<double>(
 
 }  // namespace
 
-Bank1D make_bank(int n) {
+Bank1D make_bank(int n, int kind) {
     if (n < 1 || n > 16) throw std::runtime_error("bad node count");
-    Nodes g = gauss(n);
+    Nodes g = node_family(n, kind);
     Bank1D b;
     b.n = n;
     b.x = to_d(g.x);
@@ -127,18 +180,57 @@ Bank1D make_bank(int n) {
         b.lhp[j] = (double)(lp[j] / g.w[j]);
     }
     b.vinv.resize(n * n);
-    for (int m = 0; m < n; ++m)
-        for (int i = 0; i < n; ++i) b.vinv[m * n + i] = (double)(g.w[i] * legendre_orthonormal(m, g.x[i]));
+    for (int m = 0; m < n; ++m) {
+        ld gam = 1;  // discrete norm of mode m (1 except the top LGL mode)
+        if (kind == 1 && m == n - 1) {
+            gam = 0;
+            for (int i = 0; i < n; ++i) gam += g.w[i] * legendre_orthonormal(m, g.x[i]) * legendre_orthonormal(m, g.x[i]);
+        }
+        for (int i = 0; i < n; ++i) b.vinv[m * n + i] = (double)(g.w[i] * legendre_orthonormal(m, g.x[i]) / gam);
+    }
     return b;
 }
 
-std::vector<double> make_vmap(int n_from, int n_to) {
-    Nodes a = gauss(n_from), b = gauss(n_to);
+std::vector<double> make_vmap(int n_from, int n_to, int kind) {
+    Nodes a = node_family(n_from, kind), b = node_family(n_to, kind);
     std::vector<ld> M(n_to * n_from, 0);
     if (n_from <= n_to) {
         for (int i = 0; i < n_to; ++i) {
             std::vector<ld> l = lagrange_all(a, b.x[i]);
             for (int j = 0; j < n_from; ++j) M[i * n_from + j] = l[j];
+        }
+    } else if (kind == 1) {
+        // exact L2 projection: (integral l^to_i l^to_k) P = integral l^to_i l^from_j,
+        // integrals by a Gauss rule exact for the products
+        Nodes q = gauss(n_from + n_to);
+        std::vector<ld> Mc(n_to * n_to, 0), Bm(n_to * n_from, 0);
+        for (size_t k = 0; k < q.x.size(); ++k) {
+            std::vector<ld> lt = lagrange_all(b, q.x[k]), lf = lagrange_all(a, q.x[k]);
+            for (int i = 0; i < n_to; ++i) {
+                for (int j = 0; j < n_to; ++j) Mc[i * n_to + j] += q.w[k] * lt[i] * lt[j];
+                for (int j = 0; j < n_from; ++j) Bm[i * n_from + j] += q.w[k] * lt[i] * lf[j];
+            }
+        }
+        // Cholesky Mc = L L^T, then two triangular solves per column of Bm
+        std::vector<ld> L(n_to * n_to, 0);
+        for (int i = 0; i < n_to; ++i)
+            for (int j = 0; j <= i; ++j) {
+                ld s = Mc[i * n_to + j];
+                for (int k = 0; k < j; ++k) s -= L[i * n_to + k] * L[j * n_to + k];
+                L[i * n_to + j] = i == j ? std::sqrt(s) : s / L[j * n_to + j];
+            }
+        for (int c = 0; c < n_from; ++c) {
+            std::vector<ld> y(n_to);
+            for (int i = 0; i < n_to; ++i) {
+                ld s = Bm[i * n_from + c];
+                for (int k = 0; k < i; ++k) s -= L[i * n_to + k] * y[k];
+                y[i] = s / L[i * n_to + i];
+            }
+            for (int i = n_to - 1; i >= 0; --i) {
+                ld s = y[i];
+                for (int k = i + 1; k < n_to; ++k) s -= L[k * n_to + i] * M[k * n_from + c];
+                M[i * n_from + c] = s / L[i * n_to + i];
+            }
         }
     } else {
         for (int j = 0; j < n_from; ++j) {
@@ -151,8 +243,8 @@ std::vector<double> make_vmap(int n_from, int n_to) {
 
 namespace {
 
-std::vector<ld> dg2fv_ld(int n, int nfv) {
-    Nodes g = gauss(n);
+std::vector<ld> dg2fv_ld(int n, int nfv, int kind) {
+    Nodes g = node_family(n, kind);
     Nodes q = gauss(n + 2);  // exact for the degree n-1 integrand
     std::vector<ld> A(nfv * n, 0);
     const ld l = (ld)2 / nfv;
@@ -169,12 +261,12 @@ std::vector<ld> dg2fv_ld(int n, int nfv) {
 
 }  // namespace
 
-std::vector<double> make_dg2fv(int n, int nfv) { return to_d(dg2fv_ld(n, nfv)); }
+std::vector<double> make_dg2fv(int n, int nfv, int kind) { return to_d(dg2fv_ld(n, nfv, kind)); }
 
-std::vector<double> make_fv2dg(int n, int nfv) {
+std::vector<double> make_fv2dg(int n, int nfv, int kind) {
     if (nfv < n) throw std::runtime_error("N_FV < N+1");
     // Householder QR of A (nfv x n): A = Q R, pinv(A) = R^{-1} Q^T.
-    std::vector<ld> A = dg2fv_ld(n, nfv);
+    std::vector<ld> A = dg2fv_ld(n, nfv, kind);
     const int m = nfv;
     std::vector<ld> Q(m * m, 0);
     for (int i = 0; i < m; ++i) Q[i * m + i] = 1;  // accumulates Q^T

@@ -6,7 +6,7 @@
 namespace dgfv {
 
 struct Bank1D {
-    int n = 0;                    // Legendre-Gauss nodes per direction (N+1)
+    int n = 0;                    // nodes per direction (N+1)
     std::vector<double> x, w;     // nodes (ascending) and weights
     std::vector<double> D;        // D[i*n+j] = l_j'(x_i)
     std::vector<double> Dhat;     // Dhat[i*n+j] = -(w_j/w_i) D[j*n+i]
@@ -15,9 +15,10 @@ struct Bank1D {
     std::vector<double> vinv;     // inverse orthonormal-Legendre Vandermonde, [m*n + i]
 };
 
-Bank1D make_bank(int n);
-std::vector<double> make_vmap(int n_from, int n_to);  // n_to x n_from
-std::vector<double> make_dg2fv(int n, int nfv);        // nfv x n
-std::vector<double> make_fv2dg(int n, int nfv);        // n x nfv
+// kind: node family, 0 Legendre-Gauss, 1 Legendre-Gauss-Lobatto
+Bank1D make_bank(int n, int kind = 0);
+std::vector<double> make_vmap(int n_from, int n_to, int kind = 0);  // n_to x n_from
+std::vector<double> make_dg2fv(int n, int nfv, int kind = 0);        // nfv x n
+std::vector<double> make_fv2dg(int n, int nfv, int kind = 0);        // n x nfv
 
 }  // namespace dgfv

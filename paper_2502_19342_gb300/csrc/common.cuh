@@ -21,6 +21,7 @@ constexpr int NBANK = MAXP + 1;
 // by the number of points n = N+1 of the DG degree.
 struct BankIdx {
     int32_t dhat[NBANK];       // n x n weighted derivative matrix
+    int32_t dsplit[NBANK];     // n x n split-form matrix 2D - W^{-1}B (LGL nodes only)
     int32_t lm[NBANK], lp[NBANK];    // l_j(-1), l_j(+1)
     int32_t lhm[NBANK], lhp[NBANK];  // l_j(-1)/w_j, l_j(+1)/w_j
     int32_t vinv[NBANK];       // inverse orthonormal-Legendre Vandermonde (n x n)

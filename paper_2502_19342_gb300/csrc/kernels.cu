@@ -435,6 +435,143 @@ __global__ void __launch_bounds__(256, MINB) k_dg_volume(Params P, Tiles T, cons
 }
 
 // ---------------------------------------------------------------------------------
+// k_dg_volume_split: split-form DGSEM on LGL nodes (Sec. 3.5).  Lifting and
+// gradient traces as in k_dg_volume; the nodal viscous fluxes overwrite the
+// gradient; the volume term of node i along direction d is
+//   sum_m Dhat_im F^v_d(m) + sum_m S_im F#_d(u_i, u_m),   S = 2D - W^{-1}B,
+// F# the kinetic-energy-preserving two-point flux (its diagonal F#(u_i,u_i) =
+// F^c(u_i) carries the boundary correction).  One thread per node, all variables.
+template <int NK>
+__global__ void __launch_bounds__(256) k_dg_volume_split(Params P, Tiles T, const double* __restrict__ U) {
+    constexpr int V = NK + 4, NT = 6 + NK;
+    extern __shared__ double sm[];
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
+    const int n2 = n * n, n3 = n2 * n;
+    const bool visc = P.ph.viscous;
+    double* sD = sm;            // n*n Dhat
+    double* sS = sD + n * n;    // n*n split matrix
+    double* sl = sS + n * n;    // lm, lp, lhm, lhp (4n)
+    double* sK = sl + 4 * n;    // count * NT * n3 two-point flux tuples
+    double* sG = sK + count * NT * n3;  // count * 3V * n3 (viscous only)
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+        sD[i] = B(P, P.bi.dhat[n])[i];
+        sS[i] = B(P, P.bi.dsplit[n])[i];
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        sl[i] = B(P, P.bi.lm[n])[i];
+        sl[n + i] = B(P, P.bi.lp[n])[i];
+        sl[2 * n + i] = B(P, P.bi.lhm[n])[i];
+        sl[3 * n + i] = B(P, P.bi.lhp[n])[i];
+    }
+    __syncthreads();
+    if (visc) {
+        // lifting, Eq. 23 (gradient sign), as in k_dg_volume
+        const int per = 3 * V * n3;
+        for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
+            const int el = idx / per, r = idx % per, d = r / (V * n3), r2 = r % (V * n3), v = r2 / n3, c = r2 % n3;
+            const int e = T.items[first + el];
+            const int i = c % n, j = (c / n) % n, k = c / n2;
+            const int m0 = d == 0 ? i : (d == 1 ? j : k);
+            const int a = d == 0 ? j : i, b = d == 2 ? j : k;
+            const double* src = U + P.t.off[e] + (int64_t)v * n3;
+            double s = 0.0;
+            for (int m = 0; m < n; ++m) s = fma(sD[m0 * n + m], src[node_index(n, d, m, a, b)], s);
+            const int64_t fo = P.t.fo[e];
+            const int p = a + n * b;
+            s = fma(sl[3 * n + m0], P.b.flift[(fo + (int64_t)(2 * d + 1) * n2) * V + v * n2 + p], s);
+            s = fma(-sl[2 * n + m0], P.b.flift[(fo + (int64_t)(2 * d) * n2) * V + v * n2 + p], s);
+            sG[el * per + r] = P.t.rh[3 * e + d] * s;
+        }
+        __syncthreads();
+        const int pt = 6 * 3 * V * n2;
+        for (int idx = threadIdx.x; idx < count * pt; idx += blockDim.x) {
+            const int el = idx / pt, r = idx % pt, f = r / (3 * V * n2), r2 = r % (3 * V * n2), x = r2 / n2, p = r2 % n2;
+            const int e = T.items[first + el];
+            const int d = f >> 1, a = p % n, b = p / n;
+            const double* lb = sl + ((f & 1) ? n : 0);
+            const double* src = sG + el * 3 * V * n3 + x * n3;
+            double s = 0.0;
+            for (int m = 0; m < n; ++m) s = fma(lb[m], src[node_index(n, d, m, a, b)], s);
+            P.b.fg[(P.t.fo[e] + (int64_t)f * n2) * 3 * V + x * n2 + p] = s;
+        }
+        __syncthreads();
+    }
+    // per node: two-point flux tuple; viscous fluxes written over the gradient
+    for (int idx = threadIdx.x; idx < count * n3; idx += blockDim.x) {
+        const int el = idx / n3, c = idx % n3;
+        const int e = T.items[first + el];
+        const double* src = U + P.t.off[e] + c;
+        double u[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) u[v] = src[(int64_t)v * n3];
+        Prim<NK> s;
+        prim<NK>(P.ph, u, s);
+        double t[NT];
+        kep_tuple<NK>(s, t);
+#pragma unroll
+        for (int q = 0; q < NT; ++q) sK[(el * NT + q) * n3 + c] = t[q];
+        if (visc) {
+            double* G = sG + el * 3 * V * n3 + c;
+            double g[3 * V];
+#pragma unroll
+            for (int x = 0; x < 3 * V; ++x) g[x] = G[x * n3];
+            PrimGrad<NK> pg;
+            prim_grad<NK>(P.ph, s, g, pg);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                double Fv[V];
+                flux_visc<NK>(P.ph, s, pg, d, Fv);
+#pragma unroll
+                for (int v = 0; v < V; ++v) G[(d * V + v) * n3] = Fv[v];
+            }
+        }
+    }
+    __syncthreads();
+    // volume term per node, all variables
+    for (int idx = threadIdx.x; idx < count * n3; idx += blockDim.x) {
+        const int el = idx / n3, c = idx % n3;
+        const int e = T.items[first + el];
+        const int ijk[3] = {c % n, (c / n) % n, c / n2};
+        const double* K = sK + el * NT * n3;
+        double ti[NT];
+#pragma unroll
+        for (int q = 0; q < NT; ++q) ti[q] = K[q * n3 + c];
+        double acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int m0 = ijk[d];
+            const int a = d == 0 ? ijk[1] : ijk[0], b = d == 2 ? ijk[1] : ijk[2];
+            double sd[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) sd[v] = 0.0;
+            for (int m = 0; m < n; ++m) {
+                const int cm = node_index(n, d, m, a, b);
+                double tm[NT], F[V];
+#pragma unroll
+                for (int q = 0; q < NT; ++q) tm[q] = K[q * n3 + cm];
+                kep_flux<NK>(ti, tm, d, F);
+                const double Sim = sS[m0 * n + m];
+#pragma unroll
+                for (int v = 0; v < V; ++v) sd[v] = fma(Sim, F[v], sd[v]);
+                if (visc) {
+                    const double* Fv = sG + el * 3 * V * n3 + d * V * n3 + cm;
+                    const double Dim = sD[m0 * n + m];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) sd[v] = fma(Dim, Fv[v * n3], sd[v]);
+                }
+            }
+            const double rh = P.t.rh[3 * e + d];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = fma(rh, sd[v], acc[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) P.b.rtmp[P.t.off[e] + (int64_t)v * n3 + c] = acc[v];
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // Face fluxes.  F* = F^c*(uL,uR) + (F^v(uL,gL) + F^v(uR,gR))/2 in +x_d, written as
 // the outward flux of both sides (+F for the lower element, -F for the upper).
 //
@@ -1068,6 +1205,19 @@ void launch_dg_volume(int nk, const Params& P, const Tiles& T, int ntiles, size_
                                                 (int)smem),
                            k_dg_volume<NK, 2><<<ntiles, threads, smem, s>>>(P, T, U)));
     }
+}
+
+size_t volume_split_smem_bytes(int nk, int n, int count, bool viscous) {
+    const int V = nk + 4, NT = 6 + nk;
+    return sizeof(double) * (size_t)(2 * n * n + 4 * n + count * (NT + (viscous ? 3 * V : 0)) * n * n * n);
+}
+
+void launch_dg_volume_split(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
+                            cudaStream_t s) {
+    if (ntiles <= 0) return;
+    DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_dg_volume_split<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem),
+                       k_dg_volume_split<NK><<<ntiles, 256, smem, s>>>(P, T, U)));
 }
 
 void launch_face_flux(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s) {

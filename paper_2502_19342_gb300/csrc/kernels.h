@@ -16,6 +16,9 @@ void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double
 void launch_face_lift_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s);
 void launch_face_lift(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s);
 size_t volume_smem_bytes(int nk, int n, int count);
+size_t volume_split_smem_bytes(int nk, int n, int count, bool viscous);
+void launch_dg_volume_split(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
+                            cudaStream_t s);
 void launch_dg_volume(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
                       cudaStream_t s, int variant = 0);
 void launch_face_flux(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s);

@@ -282,6 +282,33 @@ DGFV_HD void interface_flux(const DevPhys& P, const double* uL, const double* gL
     }
 }
 
+// Split form (Sec. 3.5): per-node tuple of the two-point flux,
+// t = (rho, v_1, v_2, v_3, p, H, Y_1..Y_NK), H = (rho E + p)/rho.
+template <int NK>
+DGFV_HD void kep_tuple(const Prim<NK>& s, double* t) {
+    t[0] = s.rho;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t[1 + i] = s.v[i];
+    t[4] = s.p;
+    t[5] = s.E + s.p * s.irho;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) t[6 + k] = s.Y[k];
+}
+
+// Kinetic-energy-preserving two-point flux of Pirozzoli in +x_d from two tuples:
+// arithmetic means {.};  rho_k: {rho}{v_d}{Y_k},  rho v_j: {rho}{v_d}{v_j} + {p} delta_jd,
+// rho E: {rho}{v_d}{H}.  Symmetric in its arguments, equal to F^c on equal states.
+template <int NK>
+DGFV_HD void kep_flux(const double* a, const double* b, int d, double* F) {
+    const double mass = (0.5 * (a[0] + b[0])) * (0.5 * (a[1 + d] + b[1 + d]));
+#pragma unroll
+    for (int k = 0; k < NK; ++k) F[k] = mass * (0.5 * (a[6 + k] + b[6 + k]));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F[NK + j] = mass * (0.5 * (a[1 + j] + b[1 + j]));
+    F[NK + d] += 0.5 * (a[4] + b[4]);
+    F[NK + 3] = mass * (0.5 * (a[5] + b[5]));
+}
+
 // FV reconstruction variables w = (rho_1..rho_NK, v, p) and back.
 template <int NK>
 DGFV_HD void cons_to_w(const DevPhys& P, const double* u, double* w) {

@@ -39,7 +39,8 @@ class Phys(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("riemann", C.c_int), ("cfl_c", C.c_double), ("cfl_v", C.c_double), ("T_fv_on", C.c_double),
-                ("T_fv_off", C.c_double), ("T_ref", C.c_double), ("T_crs", C.c_double)]
+                ("T_fv_off", C.c_double), ("T_ref", C.c_double), ("T_crs", C.c_double), ("nodes", C.c_int),
+                ("split_form", C.c_int)]
 
 
 class AdaptStats(C.Structure):
@@ -149,7 +150,8 @@ class Context:
         o = dict(cfl_c=0.5, cfl_v=0.5, thresholds=(1.0, 1.6, 3.0, 7.0))
         o.update(opts or {})
         thr = o["thresholds"]
-        op = Opts(int(problem.get("riemann", 0)), float(o["cfl_c"]), float(o["cfl_v"]), *[float(x) for x in thr])
+        op = Opts(int(problem.get("riemann", 0)), float(o["cfl_c"]), float(o["cfl_v"]), *[float(x) for x in thr],
+                  int(problem.get("nodes", 0)), int(problem.get("split", 0)))
         h = C.c_void_p()
         rc = L.dgfv_init_mesh(C.byref(h), C.byref(mesh), C.byref(ph), C.byref(op))
         if rc != 0:

@@ -322,7 +322,8 @@ def _fourier_on_mesh(prob, k1, c, L, chunk=4096):
     return out
 
 
-def turbulence(seed=0, nel=(48, 48, 48), riemann=0, mu=5e-4, Mt=0.3, k0=4.0, kmax=8, N0=None, y_bg=0.05):
+def turbulence(seed=0, nel=(48, 48, 48), riemann=0, mu=5e-4, Mt=0.3, k0=4.0, kmax=8, N0=None, y_bg=0.05, nodes=0,
+               split=0):
     """Periodic [0,2pi]^3, 48^3 elements, N drawn from {1..7}, 3 species
     (gamma 1.4/1.3/1.67, M 29/44/4), N_FV = 8.  Random-phase solenoidal
     velocity with E(k) ~ k^4 exp(-2 (k/k0)^2), k0 = 4, scaled to turbulent Mach
@@ -334,7 +335,7 @@ def turbulence(seed=0, nel=(48, 48, 48), riemann=0, mu=5e-4, Mt=0.3, k0=4.0, kma
     # N0 = None: degrees drawn from {1..7}; an integer: that degree everywhere
     N = random_degrees(n_elem, 1, 7, seed) if N0 is None else np.full(n_elem, N0, np.int8)
     L = 2 * np.pi
-    prob = make_problem([(nel, (0, 0, 0), (L, L, L))], sp, n_fv=8, N=N, riemann=riemann)
+    prob = make_problem([(nel, (0, 0, 0), (L, L, L))], sp, n_fv=8, N=N, riemann=riemann, nodes=nodes, split=split)
     rng = np.random.default_rng(seed + 1)
     k1, cu = _fourier_coeffs(rng, kmax, lambda k: k ** 4 * np.exp(-2 * (k / k0) ** 2), True)
     kb, cb1 = _fourier_coeffs(rng, 3, lambda k: np.exp(-(k / 2.0) ** 2), False)

@@ -14,19 +14,20 @@ pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
 
 
-def _dg_problem(seed, nk=3, nel=(3, 2, 3), Nlo=1, Nhi=5, mu=3e-3, uniform=None):
+def _dg_problem(seed, nk=3, nel=(3, 2, 3), Nlo=1, Nhi=5, mu=3e-3, uniform=None, nodes=0):
     specs = [W.AIR, W.HELIUM, W.CO2][:nk]
     sp = W.species_set(specs, mu=mu)
     n = nel[0] * nel[1] * nel[2]
     N = np.full(n, uniform, np.int8) if uniform else W.random_degrees(n, Nlo, Nhi, seed)
-    prob = W.make_problem([(nel, (0, 0, 0), (1.0, 0.8, 1.1))], sp, n_fv=8, N=N, riemann=0)
+    prob = W.make_problem([(nel, (0, 0, 0), (1.0, 0.8, 1.1))], sp, n_fv=8, N=N, riemann=0, nodes=nodes)
     return prob, W.smooth_random_state(prob, seed, amp=0.1)
 
 
-@pytest.mark.parametrize("nk,mu,seed,uniform", [(3, 3e-3, 1, None), (2, 0.0, 2, None), (1, 1e-3, 3, None),
-                                                (3, 2e-3, 4, 4)])
-def test_rhs_vjp_dot_product_with_oracle_jvp(oracle, nk, mu, seed, uniform):
-    prob, U = _dg_problem(seed, nk=nk, mu=mu, uniform=uniform)
+@pytest.mark.parametrize("nk,mu,seed,uniform,nodes", [(3, 3e-3, 1, None, 0), (2, 0.0, 2, None, 0),
+                                                      (1, 1e-3, 3, None, 0), (3, 2e-3, 4, 4, 0),
+                                                      (3, 2e-3, 5, None, 1)])
+def test_rhs_vjp_dot_product_with_oracle_jvp(oracle, nk, mu, seed, uniform, nodes):
+    prob, U = _dg_problem(seed, nk=nk, mu=mu, uniform=uniform, nodes=nodes)
     rng = np.random.default_rng(seed)
     Rbar = rng.standard_normal(U.size)
     ctx = ctx_for(prob, N_min=1, N_max=7)
@@ -152,6 +153,16 @@ def test_autograd_function_backward_is_the_adjoint():
     (R * Rbar).sum().backward()
     ref = ctx.rhs_vjp(to_dev(U), Rbar.detach().contiguous())
     torch.testing.assert_close(X.grad, ref, rtol=0, atol=0)
+    ctx.close()
+
+
+def test_adjoint_rejects_split_form():
+    from paper_2502_19342_gb300 import dgfv
+    prob, U = _dg_problem(12, nk=2, nodes=1)
+    prob["split"] = 1
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    with pytest.raises(dgfv.DgfvError):
+        ctx.rhs_vjp(to_dev(U), to_dev(np.ones_like(U)))
     ctx.close()
 
 

@@ -13,30 +13,34 @@ pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
 
 
-def _mixed(seed, nk=2, nel=(3, 4, 5), Nlo=1, Nhi=7, fv_frac=0.25, n_fv=8, riemann=0, mu=2e-3, box=(1.0, 1.3, 0.9)):
+def _mixed(seed, nk=2, nel=(3, 4, 5), Nlo=1, Nhi=7, fv_frac=0.25, n_fv=8, riemann=0, mu=2e-3, box=(1.0, 1.3, 0.9),
+           nodes=0, split=0):
     specs = [W.AIR, W.HELIUM, W.CO2][:nk]
     sp = W.species_set(specs, mu=mu)
     n = nel[0] * nel[1] * nel[2]
     prob = W.make_problem([(nel, (0, 0, 0), box)], sp, n_fv=n_fv, N=W.random_degrees(n, Nlo, Nhi, seed),
-                          fv=W.random_fv(n, fv_frac, seed), riemann=riemann)
+                          fv=W.random_fv(n, fv_frac, seed), riemann=riemann, nodes=nodes, split=split)
     return prob, W.smooth_random_state(prob, seed, amp=0.1)
 
 
-def test_operator_bank_matches_oracle(oracle):
-    prob, _ = _mixed(0)
+@pytest.mark.parametrize("nodes", [0, 1])
+def test_operator_bank_matches_oracle(oracle, nodes):
+    prob, _ = _mixed(0, nodes=nodes)
     ctx = ctx_for(prob, N_min=1, N_max=7)
     for N in range(1, 8):
-        b = oracle.basis(N)
+        b = oracle.basis(N, nodes)
         np.testing.assert_allclose(ctx.bank_entry(0, N), b["x"], atol=1e-15)
         np.testing.assert_allclose(ctx.bank_entry(1, N), b["w"], atol=1e-15)
         np.testing.assert_allclose(ctx.bank_entry(2, N), b["Dhat"].ravel(), atol=1e-12)
+        np.testing.assert_allclose(ctx.bank_entry(9, N), b["D"].ravel(), atol=1e-12)
         np.testing.assert_allclose(ctx.bank_entry(3, N), b["lm"], atol=1e-14)
         np.testing.assert_allclose(ctx.bank_entry(4, N), b["lp"], atol=1e-14)
-        np.testing.assert_allclose(ctx.bank_entry(6, N), oracle.dg2fv(N, 8).ravel(), atol=1e-14)
-        np.testing.assert_allclose(ctx.bank_entry(7, N), oracle.fv2dg(N, 8).ravel(), atol=1e-12)
-        np.testing.assert_allclose(ctx.bank_entry(8, N), np.linalg.inv(oracle.leg_vandermonde(N)).ravel(), atol=1e-13)
+        np.testing.assert_allclose(ctx.bank_entry(6, N), oracle.dg2fv(N, 8, nodes).ravel(), atol=1e-14)
+        np.testing.assert_allclose(ctx.bank_entry(7, N), oracle.fv2dg(N, 8, nodes).ravel(), atol=1e-12)
+        np.testing.assert_allclose(ctx.bank_entry(8, N), np.linalg.inv(oracle.leg_vandermonde(N, nodes)).ravel(),
+                                   atol=1e-13)
         for M in range(1, 8):
-            np.testing.assert_allclose(ctx.bank_entry(5, N, M), oracle.vmap(N, M).ravel(), atol=1e-13)
+            np.testing.assert_allclose(ctx.bank_entry(5, N, M), oracle.vmap(N, M, nodes).ravel(), atol=1e-13)
     ctx.close()
 
 
@@ -48,12 +52,15 @@ def test_rhs_plain_tiny(oracle):
     assert_rhs_close(oracle, prob, U, gpu_rhs(prob, U))
 
 
-@pytest.mark.parametrize("nk,riemann,mu,seed", [(2, 0, 2e-3, 1), (3, 0, 2e-3, 2), (2, 1, 2e-3, 3), (3, 1, 0.0, 4),
-                                                (1, 0, 1e-3, 5), (3, 1, 5e-3, 6), (3, 2, 2e-3, 7), (2, 2, 0.0, 8)])
-def test_rhs_mixed_hp_fv(oracle, nk, riemann, mu, seed):
+@pytest.mark.parametrize("nk,riemann,mu,seed,nodes,split", [
+    (2, 0, 2e-3, 1, 0, 0), (3, 0, 2e-3, 2, 0, 0), (2, 1, 2e-3, 3, 0, 0), (3, 1, 0.0, 4, 0, 0),
+    (1, 0, 1e-3, 5, 0, 0), (3, 1, 5e-3, 6, 0, 0), (3, 2, 2e-3, 7, 0, 0), (2, 2, 0.0, 8, 0, 0),
+    (3, 0, 2e-3, 9, 1, 0), (3, 1, 2e-3, 10, 1, 1), (2, 0, 0.0, 11, 1, 1), (3, 2, 1e-3, 12, 1, 1)])
+def test_rhs_mixed_hp_fv(oracle, nk, riemann, mu, seed, nodes, split):
     """Random degrees 1..7 and FV elements (N_FV = 8) on a 3x4x5 box: every
-    face type (equal and unequal degree, DG/FV, FV/FV) and ragged tiles."""
-    prob, U = _mixed(seed, nk=nk, riemann=riemann, mu=mu)
+    face type (equal and unequal degree, DG/FV, FV/FV) and ragged tiles; LG
+    nodes, LGL nodes, and the split form on LGL nodes."""
+    prob, U = _mixed(seed, nk=nk, riemann=riemann, mu=mu, nodes=nodes, split=split)
     assert_rhs_close(oracle, prob, U, gpu_rhs(prob, U))
 
 
@@ -253,4 +260,36 @@ def test_launch_modes_and_autotuned_tiles_give_identical_results(oracle):
     np.testing.assert_array_equal(R1, R0)
     np.testing.assert_array_equal(R2, R0)
     assert_rhs_close(oracle, prob, U, R0)
+    ctx.close()
+
+
+def test_split_form_rk3_steps(oracle):
+    """Split form on LGL nodes, mixed degrees and FV elements, 3 species,
+    viscous, Roe-HH between DG elements: 5 SSP-RK3 steps at a fixed step."""
+    prob, U = _mixed(21, nk=3, riemann=2, Nhi=6, nodes=1, split=1)
+    ctx = ctx_for(prob)
+    ctx.set_state(to_dev(U))
+    dt = 2e-4
+    for _ in range(5):
+        ctx.rk_step(dt)
+    Uo, _ = oracle.rk3(prob, U, 5, dt_fixed=dt)
+    assert_fields_close(prob, ctx.get_state().cpu().numpy(), Uo, what="U(5 steps, split form)")
+
+
+def test_split_form_indicator_and_remap_on_lgl(oracle):
+    """Indicator decisions and the remap on LGL nodes (their Vandermonde and
+    projection matrices differ from the LG ones)."""
+    prob, U = _mixed(22, nk=3, nodes=1, split=1, fv_frac=0.2)
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    Ip, Ih, _ = ctx.indicator(to_dev(U))
+    oIp, oIh = oracle.indicator(prob, U)
+    np.testing.assert_allclose(Ip.cpu().numpy(), oIp, rtol=1e-6, atol=1e-9)
+    np.testing.assert_allclose(Ih.cpu().numpy(), oIh, rtol=1e-6, atol=1e-9)
+    ctx.set_state(to_dev(U))
+    N2 = np.clip(prob["N"] + np.where(np.arange(len(prob["N"])) % 2 == 0, 1, -1), 1, 7).astype(np.int8)
+    fv2 = prob["fv"].copy()
+    fv2[::5] ^= 1
+    ctx.set_degrees(N2, fv2, remap=True)
+    ref = oracle.remap(prob, N2, fv2, U)
+    np.testing.assert_allclose(ctx.get_state().cpu().numpy(), ref, atol=1e-13)
     ctx.close()
