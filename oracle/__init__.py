@@ -53,6 +53,9 @@ def lib():
         L.oracle_count_flops.argtypes = [P, _dp, _dp]
         L.oracle_dt.argtypes = [P, _dp, C.c_double, C.c_double, _dp]
         L.oracle_rk3.argtypes = [P, _dp, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
+        L.oracle_lsrk4.argtypes = [P, _dp, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
+        L.oracle_lsrk4_scalar.restype = C.c_double
+        L.oracle_lsrk4_scalar.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
         L.oracle_rk3_scalar_linear.restype = C.c_double
         L.oracle_rk3_scalar_linear.argtypes = [C.c_double, C.c_double, C.c_double]
         L.oracle_indicator.argtypes = [P, _dp, _dp, _dp]
@@ -188,6 +191,20 @@ def rk3(prob, U, n_steps, dt_fixed=-1.0, cfl_c=0.5, cfl_v=0.5):
 
 def rk3_scalar_linear(lam, dt_, u0):
     return lib().oracle_rk3_scalar_linear(lam, dt_, u0)
+
+
+def lsrk4(prob, U, n_steps, dt_fixed=-1.0, cfl_c=0.5, cfl_v=0.5):
+    """n_steps steps of the five-stage low-storage RK4; returns (U_final, dts)."""
+    b = _Bound(prob)
+    X = np.array(U, dtype=np.float64, copy=True)
+    dts = np.zeros(max(n_steps, 1))
+    _check(lib().oracle_lsrk4(b.ref, _ptr(X, _dp), n_steps, dt_fixed, cfl_c, cfl_v, _ptr(dts, _dp)), "lsrk4")
+    return X, dts[:n_steps]
+
+
+def lsrk4_scalar(kind, lam, dt_, u0):
+    """One low-storage RK4 step of u' = lam u (kind 0) or u' = -u^2 (kind 1)."""
+    return lib().oracle_lsrk4_scalar(int(kind), lam, dt_, u0)
 
 
 def indicator(prob, U):

@@ -760,6 +760,28 @@ void ssp_rk3_step(int64_t n, double* U, double dt, Rhs rhs) {
     std::copy(Us.begin(), Us.end(), U);
 }
 
+// ------------------------------------------------------------------ low-storage RK4 (Sec. 3.3)
+// The explicit fourth-order low-storage scheme the paper cites (Kennedy and
+// Carpenter), read as the five-stage 2N-storage method of Carpenter and Kennedy
+// (1994), coefficients as published:
+//   dU <- A_s dU + dt R(U);   U <- U + B_s dU,   s = 1..5,  A_1 = 0.
+template <class Rhs>
+void lsrk4_step(int64_t n, double* U, double dt, Rhs rhs) {
+    static const double A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                                -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+    static const double B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                                1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                                2277821191437.0 / 14882151754819.0};
+    vector<double> dU(n, 0.0), Rv(n);
+    for (int s = 0; s < 5; ++s) {
+        rhs(U, Rv.data());
+        for (int64_t i = 0; i < n; ++i) {
+            dU[i] = A[s] * dU[i] + dt * Rv[i];
+            U[i] = U[i] + B[s] * dU[i];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ indicator, Sec. 3.4
 // Reading: orthonormal Legendre modes; fit over m = 0..N; I = min over the three
 // directions of |sigma|; FV elements are mapped to their DG degree by V^{FV->DG}
@@ -919,6 +941,33 @@ int oracle_rk3(const oracle_problem* p, double* U, int n_steps, double dt_fixed,
         }
         return 0;
     } catch (...) { return -1; }
+}
+
+int oracle_lsrk4(const oracle_problem* p, double* U, int n_steps, double dt_fixed, double cfl_c, double cfl_v,
+                 double* dts) {
+    try {
+        Problem P = make_problem(p);
+        for (int it = 0; it < n_steps; ++it) {
+            double dt = dt_fixed;
+            if (!(dt > 0.0)) {
+                double o[3];
+                time_step(P, U, cfl_c, cfl_v, o);
+                dt = o[0];
+            }
+            if (dts) dts[it] = dt;
+            lsrk4_step(P.size, U, dt, [&](const double* x, double* r) { eval_rhs_t<double>(P, x, r); });
+        }
+        return 0;
+    } catch (...) { return -1; }
+}
+
+double oracle_lsrk4_scalar(int kind, double lambda, double dt, double u0) {
+    double u = u0;
+    if (kind == 0)
+        lsrk4_step(1, &u, dt, [&](const double* x, double* r) { r[0] = lambda * x[0]; });
+    else
+        lsrk4_step(1, &u, dt, [&](const double* x, double* r) { r[0] = -x[0] * x[0]; });
+    return u;
 }
 
 double oracle_rk3_scalar_linear(double lambda, double dt, double u0) {

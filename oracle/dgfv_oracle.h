@@ -84,6 +84,15 @@ int oracle_rk3(const oracle_problem* p, double* U, int n_steps, double dt_fixed,
  * combination routine as oracle_rk3 (test hook for the stage coefficients). */
 double oracle_rk3_scalar_linear(double lambda, double dt, double u0);
 
+/* n_steps steps of the five-stage fourth-order low-storage Runge-Kutta scheme
+ * (Sec. 3.3), otherwise as oracle_rk3. */
+int oracle_lsrk4(const oracle_problem* p, double* U, int n_steps, double dt_fixed,
+                 double cfl_c, double cfl_v, double* dts);
+
+/* One low-storage RK4 step of u' = lambda u (kind 0) or u' = -u^2 (kind 1),
+ * through the same stage routine as oracle_lsrk4 (test hook). */
+double oracle_lsrk4_scalar(int kind, double lambda, double dt, double u0);
+
 /* Modal indicator of Sec. 3.4 per element: Ip = I(rho), Ih = min(I(p), I(Y_k)). */
 int oracle_indicator(const oracle_problem* p, const double* U, double* Ip, double* Ih);
 

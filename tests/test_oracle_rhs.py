@@ -732,3 +732,36 @@ def test_convergence_lgl_uniform_degree_3(split):
     e1 = _advected_l2(oracle, (16, 1, 1), lambda i, j, k: 3, nodes=1, split=split)
     e2 = _advected_l2(oracle, (32, 1, 1), lambda i, j, k: 3, nodes=1, split=split)
     assert _order(e1, e2, 16, 32) > 3.7, (e1, e2)
+
+
+# ---------------------------------------------------------------- low-storage RK4 (Sec. 3.3)
+def test_lsrk4_linear_stability_polynomial(oracle):
+    """Five stages: the amplification factor of u' = z u is a degree-5
+    polynomial in z whose first five coefficients are 1/k! (fourth order)."""
+    zs = np.linspace(-2.0, 0.5, 9)
+    amp = np.array([oracle.lsrk4_scalar(0, z, 1.0, 1.0) for z in zs])
+    coef = np.polynomial.polynomial.polyfit(zs, amp, 5)
+    np.testing.assert_allclose(coef[:5], [1.0, 1.0, 0.5, 1 / 6, 1 / 24], atol=1e-12)
+    assert abs(coef[5]) < 0.01 and abs(coef[5]) > 1e-4
+
+
+def test_lsrk4_fourth_order_on_a_nonlinear_ode(oracle):
+    """u' = -u^2, u(0) = 1 has u(1) = 1/2; the global error falls 16x per halving
+    of the step (the nonlinear order conditions, not only the linear ones)."""
+    def solve(m):
+        u = 1.0
+        for _ in range(m):
+            u = oracle.lsrk4_scalar(1, 0.0, 1.0 / m, u)
+        return abs(u - 0.5)
+    e = [solve(m) for m in (4, 8, 16)]
+    assert np.log2(e[0] / e[1]) > 3.8 and np.log2(e[1] / e[2]) > 3.8, e
+
+
+def test_lsrk4_on_the_dg_operator_is_fourth_order_in_time(oracle):
+    """The plain tiny case (viscous, two species) advanced to t = 4e-3 with
+    1, 2 and 4 steps against 32 steps: errors fall at order 4."""
+    prob, U = W.plain_tiny(0)
+    T = 4e-3
+    ref, _ = oracle.lsrk4(prob, U, 32, dt_fixed=T / 32)
+    e = [np.abs(oracle.lsrk4(prob, U, m, dt_fixed=T / m)[0] - ref).max() for m in (1, 2, 4)]
+    assert np.log2(e[0] / e[1]) > 3.6 and np.log2(e[1] / e[2]) > 3.6, e
