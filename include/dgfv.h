@@ -61,6 +61,12 @@ typedef enum {
  * jet computation (Sec. 5.1). */
 typedef enum { DGFV_RIEMANN_LLF = 0, DGFV_RIEMANN_ROE_HH = 1, DGFV_RIEMANN_HYBRID = 2 } dgfv_riemann;
 
+/* Time integrator of dgfv_rk_step / dgfv_rk_steps: the three-stage SSP-RK3 of
+ * Shu and Osher, or the explicit fourth-order low-storage scheme of Sec. 3.3
+ * (five stages, 2N storage, Carpenter and Kennedy's coefficients).  The
+ * adjoint calls and dgfv_rk_step_save support SSP-RK3 only. */
+typedef enum { DGFV_INTEGRATOR_SSPRK3 = 0, DGFV_INTEGRATOR_LSRK4 = 1 } dgfv_integrator;
+
 /* Mesh: n_domains periodic boxes; arrays have 3 entries per domain. */
 typedef struct {
     int n_domains;
@@ -93,6 +99,7 @@ typedef struct {
     int split_form;     /* 1: split-form volume integral with the kinetic-energy-
                            preserving two-point flux of Pirozzoli (Sec. 3.5);
                            needs nodes = 1                                    */
+    int integrator;     /* dgfv_integrator                                      */
 } dgfv_opts;
 
 typedef struct {

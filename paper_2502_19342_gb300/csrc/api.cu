@@ -377,7 +377,8 @@ int alloc_tiles(dgfv_ctx* c, TileSet& t) {
 
 // One evaluation of R on Uin; the surface kernel writes mode 0: out = R, or
 // mode 1: out = a*U0 + b*(Uin + dt*R).
-// One evaluation of R(Uin) and, in mode 1, the stage combination.  have_faces:
+// One evaluation of R(Uin) and, in mode 1 (SSP-RK3) or 2 (low-storage RK4,
+// dU in d_Us, out = Uin), the stage update.  have_faces:
 // the face values of Uin are already in the face buffer (written by the
 // previous stage's fused surface pass).  fuse_faces (mode 1): write the face
 // values of out for the next stage.
@@ -386,6 +387,7 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
     const Params P = params(c);
     const Faces F{c->d_faceL, c->d_faceR, c->d_faceD};
     const bool per_bin = c->launch_mode == 1;
+    double* dU = mode == 2 ? c->d_Us : nullptr;  // low-storage RK4 register
     if (!have_faces) {
         Timed t(c, K_PROLONG, s);
         if (per_bin)
@@ -425,9 +427,10 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
         if (per_bin)
             for (size_t bi = 0; bi < c->all.bin_first.size(); ++bi)
                 launch_surface(c->nk, P, c->all.view(c->all.bin_first[bi]), c->all.bin_count[bi], Uin, U0, out, mode,
-                               a, b, c->d_dt3, fuse_faces, s);
+                               a, b, c->d_dt3, fuse_faces, dU, s);
         else
-            launch_surface(c->nk, P, c->all.view(), c->all.ntiles, Uin, U0, out, mode, a, b, c->d_dt3, fuse_faces, s);
+            launch_surface(c->nk, P, c->all.view(), c->all.ntiles, Uin, U0, out, mode, a, b, c->d_dt3, fuse_faces, dU,
+                           s);
     }
 }
 
@@ -442,6 +445,18 @@ void enqueue_rk_step(dgfv_ctx* c, double dt, cudaStream_t s) {
     }
     // SSP-RK3 (Shu-Osher): U1 = U + dt R(U); U2 = 3/4 U + 1/4 (U1 + dt R(U1));
     // U <- 1/3 U + 2/3 (U2 + dt R(U2)).
+    if (c->opts.integrator == DGFV_INTEGRATOR_LSRK4) {
+        // five-stage fourth-order 2N-storage scheme (Carpenter and Kennedy):
+        // dU <- A_s dU + dt R(U); U <- U + B_s dU
+        static const double A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                                    -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+        static const double Bc[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                                     1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                                     2277821191437.0 / 14882151754819.0};
+        for (int st = 0; st < 5; ++st)
+            enqueue_stage(c, c->d_U, c->d_U, c->d_U, 2, A[st], Bc[st], s, st > 0, st < 4);
+        return;
+    }
     enqueue_stage(c, c->d_U, c->d_U, c->d_Us, 1, 0.0, 1.0, s, false, true);
     enqueue_stage(c, c->d_Us, c->d_U, c->d_Us, 1, 0.75, 0.25, s, true, true);
     enqueue_stage(c, c->d_Us, c->d_U, c->d_U, 1, 1.0 / 3.0, 2.0 / 3.0, s, true, false);
@@ -556,6 +571,8 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     if (opts->riemann < DGFV_RIEMANN_LLF || opts->riemann > DGFV_RIEMANN_HYBRID) return cleanup(DGFV_ERR_ARG);
     if (opts->nodes < 0 || opts->nodes > 1 || opts->split_form < 0 || opts->split_form > 1 ||
         (opts->split_form && opts->nodes != 1))
+        return cleanup(DGFV_ERR_ARG);
+    if (opts->integrator != DGFV_INTEGRATOR_SSPRK3 && opts->integrator != DGFV_INTEGRATOR_LSRK4)
         return cleanup(DGFV_ERR_ARG);
     c->ph.riemann = opts->riemann;
     c->ph.viscous = 0;
@@ -797,6 +814,8 @@ int dgfv_rk_step_vjp(dgfv_ctx* c, const double* d_U0, double dt, const double* d
                      void* stream) {
     if (!c || !d_U0 || !d_Ubar_next || !d_Ubar || !(dt > 0.0)) return DGFV_ERR_ARG;
     if (d_Ubar == d_Ubar_next || d_Ubar == d_U0) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
+    if (c->opts.integrator != DGFV_INTEGRATOR_SSPRK3)
+        return fail(c, DGFV_ERR_ARG, "stage adjoints and stage saving support SSP-RK3 only");
     TRY(adj_prepare(c));
     cudaStream_t s = (cudaStream_t)stream;
     // stage states of the step (recomputed from the step's start state)
@@ -813,6 +832,8 @@ int dgfv_rk_step_vjp_stages(dgfv_ctx* c, const double* const* d_stages, double d
     for (int i = 0; i < 3; ++i)
         if (d_Ubar == d_stages[i]) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
     if (d_Ubar == d_Ubar_next) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
+    if (c->opts.integrator != DGFV_INTEGRATOR_SSPRK3)
+        return fail(c, DGFV_ERR_ARG, "stage adjoints and stage saving support SSP-RK3 only");
     TRY(adj_prepare(c));
     return rk_step_vjp_impl(c, d_stages[0], d_stages[1], d_stages[2], dt, d_Ubar_next, d_Ubar, (cudaStream_t)stream);
 }
@@ -820,6 +841,8 @@ int dgfv_rk_step_vjp_stages(dgfv_ctx* c, const double* const* d_stages, double d
 int dgfv_rk_step_save(dgfv_ctx* c, double dt, double* d_stage1, double* d_stage2, void* stream) {
     if (!c || !d_stage1 || !d_stage2 || !(dt > 0.0)) return DGFV_ERR_ARG;
     if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "rk_step_save before set_state");
+    if (c->opts.integrator != DGFV_INTEGRATOR_SSPRK3)
+        return fail(c, DGFV_ERR_ARG, "stage adjoints and stage saving support SSP-RK3 only");
     cudaStream_t s = (cudaStream_t)stream;
     launch_set_scalar(c->d_dt3, dt, s);
     enqueue_stage(c, c->d_U, c->d_U, d_stage1, 1, 0.0, 1.0, s, false, true);

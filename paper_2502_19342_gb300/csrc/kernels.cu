@@ -728,16 +728,17 @@ __global__ void __launch_bounds__(64) k_face_flux(Params P, Faces Fc, const int3
 }
 
 // ---------------------------------------------------------------------------------
-// k_surface: surface integral and -1/J, fused with the SSP-RK3 stage combination.
+// k_surface: surface integral and -1/J, fused with the Runge-Kutta stage update.
 //   mode 0: out = R
-//   mode 1: out = a*U0 + b*(Uin + dt*R)   (out may alias Uin or U0)
+//   mode 1: out = a*U0 + b*(Uin + dt*R)   (SSP-RK3; out may alias Uin or U0)
+//   mode 2: dU = a*dU + dt*R; out = Uin + b*dU   (low-storage RK4; out may alias Uin)
 // One thread per node, all variables.  With fuse != 0 (mode 1) the new state
 // is also kept in shared memory and its face values are written for the next
 // evaluation (the face-value pass of that evaluation is then skipped).
 template <int NK>
 __global__ void __launch_bounds__(256) k_surface(Params P, Tiles T, const double* Uin, const double* U0,
                                                  double* out, int mode, double a, double b,
-                                                 const double* __restrict__ dtp, int fuse) {
+                                                 const double* __restrict__ dtp, int fuse, double* dU) {
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
     double* sl = sm;             // lm, lp, lhm, lhp
@@ -787,9 +788,17 @@ __global__ void __launch_bounds__(256) k_surface(Params P, Tiles T, const double
             if (mode == 0) {
                 out[off + (int64_t)v * n3] = R;
             } else {
-                // a = 0 (first stage): U0 is not read
-                const double y = fma(dt, R, Uin[off + (int64_t)v * n3]);
-                const double x = a == 0.0 ? b * y : fma(b, y, a * U0[off + (int64_t)v * n3]);
+                double x;
+                if (mode == 1) {
+                    // a = 0 (first stage): U0 is not read
+                    const double y = fma(dt, R, Uin[off + (int64_t)v * n3]);
+                    x = a == 0.0 ? b * y : fma(b, y, a * U0[off + (int64_t)v * n3]);
+                } else {
+                    // a = 0 (first stage): the previous dU is not read
+                    const double y = a == 0.0 ? dt * R : fma(a, dU[off + (int64_t)v * n3], dt * R);
+                    dU[off + (int64_t)v * n3] = y;
+                    x = fma(b, y, Uin[off + (int64_t)v * n3]);
+                }
                 if (nonfinite_bits(x)) set_status(P.status, -5);
                 out[off + (int64_t)v * n3] = x;
                 if (fuse) sU[el * V * n3 + v * n3 + c] = x;
@@ -1231,11 +1240,12 @@ void launch_face_flux_conf(int nk, const Params& P, const Faces& F, const FaceTi
 }
 
 void launch_surface(int nk, const Params& P, const Tiles& T, int ntiles, const double* Uin, const double* U0,
-                    double* out, int mode, double a, double b, const double* dt, bool fuse, cudaStream_t s) {
+                    double* out, int mode, double a, double b, const double* dt, bool fuse, double* dU,
+                    cudaStream_t s) {
     if (ntiles <= 0) return;
-    const int f = (fuse && mode == 1) ? 1 : 0;
+    const int f = (fuse && mode != 0) ? 1 : 0;
     const size_t sm = f ? tile_state_smem(nk) : sizeof(double) * 4 * MAXP;
-    DGFV_DISPATCH(nk, (k_surface<NK><<<ntiles, 256, sm, s>>>(P, T, Uin, U0, out, mode, a, b, dt, f)));
+    DGFV_DISPATCH(nk, (k_surface<NK><<<ntiles, 256, sm, s>>>(P, T, Uin, U0, out, mode, a, b, dt, f, dU)));
 }
 
 void launch_dt(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, double cfl_c, double cfl_v,

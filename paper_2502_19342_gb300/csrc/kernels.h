@@ -24,7 +24,8 @@ void launch_dg_volume(int nk, const Params& P, const Tiles& T, int ntiles, size_
 void launch_face_flux(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s);
 void launch_face_flux_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s);
 void launch_surface(int nk, const Params& P, const Tiles& T, int ntiles, const double* Uin, const double* U0,
-                    double* out, int mode, double a, double b, const double* dt, bool fuse, cudaStream_t s);
+                    double* out, int mode, double a, double b, const double* dt, bool fuse, double* dU,
+                    cudaStream_t s);
 void launch_dt(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, double cfl_c, double cfl_v,
                double* partial, double* out3, cudaStream_t s);
 void launch_set_scalar(double* p, double v, cudaStream_t s);

@@ -40,7 +40,7 @@ class Phys(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("riemann", C.c_int), ("cfl_c", C.c_double), ("cfl_v", C.c_double), ("T_fv_on", C.c_double),
                 ("T_fv_off", C.c_double), ("T_ref", C.c_double), ("T_crs", C.c_double), ("nodes", C.c_int),
-                ("split_form", C.c_int)]
+                ("split_form", C.c_int), ("integrator", C.c_int)]
 
 
 class AdaptStats(C.Structure):
@@ -151,7 +151,7 @@ class Context:
         o.update(opts or {})
         thr = o["thresholds"]
         op = Opts(int(problem.get("riemann", 0)), float(o["cfl_c"]), float(o["cfl_v"]), *[float(x) for x in thr],
-                  int(problem.get("nodes", 0)), int(problem.get("split", 0)))
+                  int(problem.get("nodes", 0)), int(problem.get("split", 0)), int(o.get("integrator", 0)))
         h = C.c_void_p()
         rc = L.dgfv_init_mesh(C.byref(h), C.byref(mesh), C.byref(ph), C.byref(op))
         if rc != 0:

@@ -293,3 +293,41 @@ def test_split_form_indicator_and_remap_on_lgl(oracle):
     ref = oracle.remap(prob, N2, fv2, U)
     np.testing.assert_allclose(ctx.get_state().cpu().numpy(), ref, atol=1e-13)
     ctx.close()
+
+
+def test_lsrk4_steps_match_oracle(oracle):
+    """Five-stage low-storage RK4 (Sec. 3.3): 4 steps at a fixed step on a mixed
+    hp/FV pattern (Roe-HH), and 3 CFL steps on the plain tiny case."""
+    prob, U = _mixed(23, nk=3, riemann=1, Nhi=6)
+    ctx = ctx_for(prob, opts=dict(integrator=1))
+    ctx.set_state(to_dev(U))
+    for _ in range(4):
+        ctx.rk_step(2e-4)
+    Uo, _ = oracle.lsrk4(prob, U, 4, dt_fixed=2e-4)
+    assert_fields_close(prob, ctx.get_state().cpu().numpy(), Uo, what="U(4 LSRK4 steps)")
+    ctx.close()
+    prob, U = W.plain_tiny(0)
+    ctx = ctx_for(prob, opts=dict(cfl_c=0.5, cfl_v=0.5, integrator=1))
+    ctx.set_state(to_dev(U))
+    dts = [ctx.rk_step(-1.0) for _ in range(3)]
+    Uo, odts = oracle.lsrk4(prob, U, 3, cfl_c=0.5, cfl_v=0.5)
+    np.testing.assert_allclose(dts, odts, rtol=1e-13)
+    assert_fields_close(prob, ctx.get_state().cpu().numpy(), Uo, what="U(3 LSRK4 CFL steps)")
+    ctx.close()
+
+
+def test_lsrk4_graph_equals_steps_and_stage_adjoint_is_rejected():
+    from paper_2502_19342_gb300 import dgfv
+    prob, U = _mixed(24, nk=2)
+    ctx = ctx_for(prob, opts=dict(integrator=1))
+    ctx.set_state(to_dev(U))
+    for _ in range(3):
+        ctx.rk_step(1e-4, want_dt=False)
+    a = ctx.get_state()
+    ctx.set_state(to_dev(U))
+    ctx.rk_steps(3, 1e-4, want_dt=False)
+    assert torch.equal(ctx.get_state(), a)
+    s1, s2 = torch.empty_like(a), torch.empty_like(a)
+    with pytest.raises(dgfv.DgfvError):
+        ctx.rk_step_save(1e-4, s1, s2)
+    ctx.close()
