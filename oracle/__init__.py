@@ -35,6 +35,7 @@ class _Problem(C.Structure):
         ("n_domains", C.c_int), ("dims", _i32p), ("lo", _dp), ("hi", _dp), ("n_fv", C.c_int),
         ("n_species", C.c_int), ("gamma", _dp), ("Rgas", _dp), ("mu", _dp), ("Pr", _dp),
         ("Dk", _dp), ("riemann", C.c_int), ("N", _i8p), ("fv", _u8p), ("nodes", C.c_int), ("split", C.c_int),
+        ("sutherland", C.c_int), ("T_ref", C.c_double), ("S_sutherland", C.c_double), ("indicator_vars", C.c_int),
     ]
 
 
@@ -101,7 +102,9 @@ class _Bound:
             self.dims.shape[0], _ptr(self.dims, _i32p), _ptr(self.lo, _dp), _ptr(self.hi, _dp),
             int(prob["n_fv"]), len(sp[0]), _ptr(sp[0], _dp), _ptr(sp[1], _dp), _ptr(sp[2], _dp),
             _ptr(sp[3], _dp), _ptr(sp[4], _dp), int(prob.get("riemann", 0)),
-            _ptr(self.N, _i8p), _ptr(self.fv, _u8p), int(prob.get("nodes", 0)), int(prob.get("split", 0)))
+            _ptr(self.N, _i8p), _ptr(self.fv, _u8p), int(prob.get("nodes", 0)), int(prob.get("split", 0)),
+            int(prob.get("sutherland", 0)), float(prob.get("T_ref", 1.0)), float(prob.get("S_sutherland", 0.0)),
+            int(prob.get("indicator_vars", 0)))
 
     @property
     def ref(self):

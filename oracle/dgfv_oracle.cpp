@@ -60,6 +60,7 @@ struct Problem {
     int nfv = 2;
     int riemann = 0;
     int nodes = 0;  // 0 Legendre-Gauss, 1 Legendre-Gauss-Lobatto
+    int indicator_vars = 0;  // 0: p-adaptation on rho, FV on min(p, Y_k); 1: p-adaptation on p, FV on rho
     int split = 0;  // 1: split-form volume integral with the kinetic-energy-preserving two-point flux
     vector<Elem> el;
     int64_t size = 0;
@@ -85,6 +86,12 @@ Problem make_problem(const oracle_problem* p, bool need_ops = true) {
     P.riemann = p->riemann;
     P.nodes = p->nodes;
     P.split = p->split;
+    P.indicator_vars = p->indicator_vars;
+    P.ph.sutherland = p->sutherland != 0;
+    P.ph.T_ref = p->T_ref;
+    P.ph.S = p->S_sutherland;
+    if (P.ph.sutherland && !(P.ph.T_ref > 0.0 && P.ph.S >= 0.0)) throw std::runtime_error("bad Sutherland law");
+    if (P.indicator_vars < 0 || P.indicator_vars > 1) throw std::runtime_error("bad indicator variables");
     if (P.nodes < 0 || P.nodes > 1 || P.split < 0 || P.split > 1 || (P.split && P.nodes != 1))
         throw std::runtime_error("bad node family / split form (split form needs LGL nodes)");
     int64_t e0 = 0;
@@ -845,6 +852,11 @@ void indicator(const Problem& P, const double* U, double* Ip, double* Ih) {
             for (int k = 0; k < nk; ++k) Y[k][c] = s.Y[k];
         }
         const vector<double>& Vinv = P.ops.vleg_inv.at(E.N);
+        if (P.indicator_vars == 1) {  // the TGV of Sec. 4.3: p-refinement on p, FV on rho
+            Ip[e] = modal_indicator(pr, E.N, Vinv);
+            Ih[e] = modal_indicator(rho, E.N, Vinv);
+            continue;
+        }
         Ip[e] = modal_indicator(rho, E.N, Vinv);
         double ih = modal_indicator(pr, E.N, Vinv);
         for (int k = 0; k + 1 < nk; ++k) ih = std::min(ih, modal_indicator(Y[k], E.N, Vinv));
@@ -1080,6 +1092,9 @@ static Phys phys_only(const oracle_problem* p) {
         ph.pr[k] = p->Pr[k];
         ph.D[k] = p->Dk[k];
     }
+    ph.sutherland = p->sutherland != 0;
+    ph.T_ref = p->T_ref;
+    ph.S = p->S_sutherland;
     return ph;
 }
 

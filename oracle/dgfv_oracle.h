@@ -45,6 +45,11 @@ typedef struct {
     int nodes;             /* 0 = Legendre-Gauss, 1 = Legendre-Gauss-Lobatto */
     int split;             /* 1 = split-form volume integral, kinetic-energy-preserving
                               two-point flux (needs nodes = 1), Sec. 3.5     */
+    int sutherland;        /* 1 = viscosity mu_mix (T/T_ref)^{3/2} (T_ref+S)/(T+S) (Sec. 4.3) */
+    double T_ref;          /* Sutherland reference temperature (> 0)         */
+    double S_sutherland;   /* Sutherland constant S (>= 0)                   */
+    int indicator_vars;    /* 0: p-adaptation on rho, FV on min(p, Y_k);
+                              1: p-adaptation on p, FV on rho (Sec. 4.3)     */
 } oracle_problem;
 
 /* 0 on success, negative on a malformed problem. */
@@ -93,7 +98,8 @@ int oracle_lsrk4(const oracle_problem* p, double* U, int n_steps, double dt_fixe
  * through the same stage routine as oracle_lsrk4 (test hook). */
 double oracle_lsrk4_scalar(int kind, double lambda, double dt, double u0);
 
-/* Modal indicator of Sec. 3.4 per element: Ip = I(rho), Ih = min(I(p), I(Y_k)). */
+/* Modal indicator of Sec. 3.4 per element: Ip = I(rho), Ih = min(I(p), I(Y_k))
+ * (indicator_vars 1: Ip = I(p), Ih = I(rho)). */
 int oracle_indicator(const oracle_problem* p, const double* U, double* Ip, double* Ih);
 
 /* Adaptation decision per element from Ip, Ih and thresholds

@@ -20,6 +20,8 @@ constexpr int MAXV = MAXSP + 4;
 struct Phys {
     int nk = 2;
     double gamma[MAXSP], R[MAXSP], cv[MAXSP], cp[MAXSP], mu[MAXSP], pr[MAXSP], D[MAXSP];
+    bool sutherland = false;    // temperature-dependent viscosity (Sec. 4.3)
+    double T_ref = 1.0, S = 0.0;  // Sutherland reference temperature and constant
     int V() const { return nk + 4; }
 };
 
@@ -34,6 +36,8 @@ struct Prim {
 //   T = eps / c_v,mix,  p = rho R_mix T                              (Eq. 8)
 //   mu = sum Y mu_k,  Pr = sum Y Pr_k (Eq. 11),  lambda = mu c_p / Pr (Eq. 12)
 //   c = sqrt(kappa p / rho)   (frozen-composition sound speed of the ideal-gas mixture)
+// With Sutherland's law (the TGV of Sec. 4.3) the mixture viscosity is scaled by
+//   (T/T_ref)^{3/2} (T_ref + S) / (T + S).
 template <class T>
 void cons_to_prim(const Phys& P, const T* u, Prim<T>& s) {
     const int nk = P.nk;
@@ -58,6 +62,10 @@ void cons_to_prim(const Phys& P, const T* u, Prim<T>& s) {
     s.temp = s.eps / s.cv;
     s.p = s.rho * s.Rm * s.temp;
     s.c = sqrt_(s.kappa * s.p / s.rho);
+    if (P.sutherland) {
+        const T r = s.temp / T(P.T_ref);
+        s.mu = s.mu * (r * sqrt_(r)) * (T(P.T_ref + P.S) / (s.temp + T(P.S)));
+    }
     s.lam = s.mu * s.cp / s.pr;
 }
 

@@ -268,3 +268,43 @@ def test_llf_textbook_form(oracle):
         smax = max(abs(uL[2 + d] / sL["rho"]) + sL["c"], abs(uR[2 + d] / sR["rho"]) + sR["c"])
         np.testing.assert_allclose(oracle.riemann(prob, uL, uR, d), 0.5 * (FL + FR) - 0.5 * smax * (uR - uL),
                                    rtol=1e-14, atol=1e-15)
+
+
+def _at_temperature(prob, T, rho=1.0):
+    """Single-species state at rest with temperature T."""
+    cv = prob["Rgas"][0] / (prob["gamma"][0] - 1)
+    return np.array([rho, 0.0, 0.0, 0.0, rho * cv * T])
+
+
+def test_sutherland_viscosity_limits_and_log_slope(oracle):
+    """Sutherland's law (the TGV of Sec. 4.3): mu(T_ref) = mu_0; the logarithmic
+    slope d ln mu / d ln T = 3/2 - T/(T + S) (3/2 far below S, 1/2 far above);
+    lambda = mu c_p / Pr follows mu.  Slopes by central differences."""
+    prob = _prob(1, mu=2e-3)
+    prob.update(sutherland=1, T_ref=0.8, S_sutherland=0.3)
+    s0 = oracle.primitives(prob, _at_temperature(prob, 0.8))
+    assert abs(s0["mu"] - 2e-3) < 1e-18
+    for T in (0.01, 0.3, 0.8, 2.5, 300.0):
+        h = 1e-5
+        mp = oracle.primitives(prob, _at_temperature(prob, T * (1 + h)))["mu"]
+        mm = oracle.primitives(prob, _at_temperature(prob, T * (1 - h)))["mu"]
+        slope = (np.log(mp) - np.log(mm)) / (np.log(1 + h) - np.log(1 - h))
+        assert abs(slope - (1.5 - T / (T + 0.3))) < 1e-6, (T, slope)
+        s = oracle.primitives(prob, _at_temperature(prob, T))
+        assert abs(s["lam"] / s["mu"] - s["cp"] / prob["Pr"][0]) < 1e-12 * s["cp"] / prob["Pr"][0]
+    plain = _prob(1, mu=2e-3)
+    assert oracle.primitives(plain, _at_temperature(plain, 2.5))["mu"] == 2e-3
+
+
+def test_indicator_variable_choice_swaps_the_roles(oracle):
+    """indicator_vars = 1 (Sec. 4.3): p-refinement on the pressure indicator and
+    FV on the density indicator.  With one species the default takes I(rho) and
+    I(p) the other way round, so the two outputs swap exactly."""
+    sp = W.species_set([W.AIR], mu=1e-3)
+    prob = W.make_problem([((3, 2, 2), (0, 0, 0), (1, 1, 1))], sp, n_fv=6, N=W.random_degrees(12, 1, 5, 3),
+                          fv=W.random_fv(12, 0.25, 3))
+    U = W.smooth_random_state(prob, 3, amp=0.2)
+    Ip0, Ih0 = oracle.indicator(prob, U)
+    Ip1, Ih1 = oracle.indicator(dict(prob, indicator_vars=1), U)
+    np.testing.assert_array_equal(Ip1, Ih0)
+    np.testing.assert_array_equal(Ih1, Ip0)
