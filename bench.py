@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-split", action="store_true", help="skip the split-form (LGL) measurement")
+    p.add_argument("--no-tgv", action="store_true", help="skip the Taylor-Green vortex measurement")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the default volume-kernel launch instead of timing variants first")
     p.add_argument("--profile-timed", action="store_true",
@@ -315,6 +316,47 @@ def split_form_run(nel, warmup=2, steps=1):
             "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()}}
 
 
+def tgv_run(nel=32, warmup=2, steps=2):
+    """Supersonic Taylor-Green vortex (Sec. 4.3) as a throughput workload: 32^3
+    elements, N in 2..4 by the pressure indicator, FV by the density indicator,
+    Sutherland viscosity, five-stage low-storage RK4; one step = adaptation +
+    10 RK4 steps (50 stages).  DOF-stage/s (CUDA events)."""
+    import torch
+    from paper_2502_19342_gb300 import dgfv, workloads as W
+    prob, U = W.tgv(nel=nel, N0=3)
+    ctx = dgfv.Context(prob, N_min=2, N_max=4,
+                       opts=dict(cfl_c=0.5, cfl_v=0.5, thresholds=W.TGV_THRESHOLDS, integrator=1))
+    ctx.set_state(torch.from_numpy(U).cuda())
+
+    def tgv_cycle():
+        st = ctx.adapt()
+        ctx.rk_steps(STEPS_PER_CYCLE, -1.0, want_dt=False)
+        return st["mean_dofs"] * ctx.n_elem * STEPS_PER_CYCLE * 5, st
+
+    for _ in range(warmup):
+        tgv_cycle()
+    s = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    units, st = 0.0, None
+    ev0.record(s)
+    for _ in range(steps):
+        u, st = tgv_cycle()
+        units += u
+    ev1.record(s)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    N_now, fv_now = ctx.get_degrees()
+    ctx.close()
+    return {"workload": f"supersonic Taylor-Green vortex, Ma 1.25, Re 1600, {nel}^3 elements on [-pi,pi]^3, "
+                        "N in 2..4 (pressure indicator), FV sub-cells N_FV=8 (density indicator), Sutherland "
+                        "viscosity, low-storage RK4, LLF, early time",
+            "value": units / (ms * 1e-3), "unit": "DOF-stage/s", "ms_per_step": ms / steps,
+            "step": "adapt + 10 low-storage RK4 steps (50 stages), CFL 0.5",
+            "fv_elements": int(fv_now.sum()), "mean_dofs_per_element": st["mean_dofs"],
+            "degree_histogram": np.bincount(N_now[fv_now == 0], minlength=5).tolist()}
+
+
 def batched_comparison(steps=5):
     """256 independent periodic domains of 2^3..8^3 elements, one degree
     N in 1..7 per domain, 3 species: DOF-stage/s of SSP-RK3 steps (fixed dt)
@@ -539,6 +581,7 @@ def main():
         adjoint = adjoint_cost()
         batched = None if args.no_batched else batched_comparison()
         split = None if args.no_split else split_form_run(args.nel)
+        tgv = None if args.no_tgv else tgv_run()
         launches = int(sum(v[1] for v in prof.values()))
         last = pattern[-1]
         line = {"metric": "DOF-stage updates/s (FP64 RHS, hp-mixed)", "value": value, "unit": "DOF-stage/s",
@@ -552,7 +595,7 @@ def main():
                            "volume_launch": ({str(k): v for k, v in tuned.items()} if tuned else "default"),
                            "l2": "inputs larger than L2 (state ~1.2 GB)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "adjoint": adjoint,
-                "batched_domains": batched, "split_form": split,
+                "batched_domains": batched, "split_form": split, "tgv": tgv,
                 "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
                 "clocks": clk.summary()}
         print(json.dumps(line))

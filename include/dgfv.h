@@ -85,6 +85,10 @@ typedef struct {
     double mu[3];     /* dynamic viscosity                          */
     double Pr[3];     /* Prandtl number                             */
     double D[3];      /* Fickian diffusion coefficient              */
+    int sutherland;   /* 1: mixture viscosity scaled by Sutherland's law
+                         (T/T_ref)^{3/2} (T_ref + S)/(T + S) (Sec. 4.3)  */
+    double T_ref;     /* Sutherland reference temperature (> 0)     */
+    double S;         /* Sutherland constant (>= 0)                 */
 } dgfv_phys;
 
 typedef struct {
@@ -100,6 +104,9 @@ typedef struct {
                            preserving two-point flux of Pirozzoli (Sec. 3.5);
                            needs nodes = 1                                    */
     int integrator;     /* dgfv_integrator                                      */
+    int indicator_vars; /* 0: p-adaptation on I(rho), FV on min(I(p), I(Y_k));
+                           1: p-adaptation on I(p), FV on I(rho) (the TGV of
+                           Sec. 4.3)                                          */
 } dgfv_opts;
 
 typedef struct {

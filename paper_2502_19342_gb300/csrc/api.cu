@@ -589,6 +589,11 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
         c->ph.maxD = std::max(c->ph.maxD, phys->D[k]);
         if (phys->mu[k] != 0.0 || phys->D[k] != 0.0) c->ph.viscous = 1;
     }
+    c->ph.sutherland = phys->sutherland ? 1 : 0;
+    c->ph.T_ref = phys->T_ref;
+    c->ph.S = phys->S;
+    if (c->ph.sutherland && !(phys->T_ref > 0.0 && phys->S >= 0.0)) return cleanup(DGFV_ERR_ARG);
+    if (opts->indicator_vars < 0 || opts->indicator_vars > 1) return cleanup(DGFV_ERR_ARG);
     c->n_elem = (int)ne;
     c->nb.resize(6 * ne);
     c->rh.resize(3 * ne);
@@ -750,6 +755,7 @@ static int adj_prepare(dgfv_ctx* c) {
     if (c->n_fv_elems) return fail(c, DGFV_ERR_ARG, "the adjoint supports DG elements only (the pattern has FV elements)");
     if (c->ph.riemann != 0) return fail(c, DGFV_ERR_ARG, "the adjoint supports the local Lax-Friedrichs flux only");
     if (c->opts.split_form) return fail(c, DGFV_ERR_ARG, "the adjoint supports the standard volume integral only");
+    if (c->ph.sutherland) return fail(c, DGFV_ERR_ARG, "the adjoint supports constant viscosity only");
     if (c->adj_ready) return DGFV_OK;
     TRY(dalloc(c, &c->d_fbar, c->cap_fpts * c->V));
     TRY(dalloc(c, &c->d_ubar, c->cap_fpts * c->V));
@@ -908,6 +914,7 @@ int dgfv_indicator(dgfv_ctx* c, const double* d_U, double* d_Ip, double* d_Ih, u
     const double thr[4] = {c->opts.T_fv_on, c->opts.T_fv_off, c->opts.T_ref, c->opts.T_crs};
     Timed t(c, K_INDICATOR, (cudaStream_t)stream);
     launch_indicator(c->nk, params(c), d_U, c->n_elem, d_Ip, d_Ih, d_decision, thr, c->N_min, c->N_max,
+                     c->opts.indicator_vars,
                      (cudaStream_t)stream);
     CK(cudaGetLastError());
     return DGFV_OK;

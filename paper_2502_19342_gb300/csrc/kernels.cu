@@ -873,6 +873,7 @@ __global__ void __launch_bounds__(256) k_dt(Params P, Tiles T, const double* __r
         mc = fmax(mc, lam);
         if (visc) {
             const double irpr = (rho * rcv) * r;
+            if (P.ph.sutherland) rmu *= sutherland_factor(P.ph, eps * rho * ircv);  // T = eps / c_v
             // max(4/3 mu/rho, kappa mu/(Pr rho), max_k D_k)
             double dv = fmax(4.0 / 3.0 * rmu * irho * irho, rcp * rmu * ircv * irpr * irho);
             dv = fmax(dv, P.ph.maxD);
@@ -929,7 +930,7 @@ struct Thresholds {
 template <int NK>
 __global__ void __launch_bounds__(128) k_indicator(Params P, const double* __restrict__ U, int n_elem,
                                                    double* Ip, double* Ih, uint8_t* dec, Thresholds thr,
-                                                   int N_min, int N_max) {
+                                                   int N_min, int N_max, int vars) {
     constexpr int V = NK + 4, NQ = 2 + (NK - 1);  // rho, p, Y_1..Y_{NK-1}
     constexpr int P3 = MAXP * MAXP * MAXP;
     extern __shared__ double sm[];
@@ -1051,9 +1052,12 @@ __global__ void __launch_bounds__(128) k_indicator(Params P, const double* __res
     if (threadIdx.x == 0) {
         double I[NQ];
         for (int q = 0; q < NQ; ++q) I[q] = fmin(sI[q][0], fmin(sI[q][1], sI[q][2]));
-        const double ip = I[0];
-        double ih = I[1];
+        double ip = I[0], ih = I[1];
         for (int q = 2; q < NQ; ++q) ih = fmin(ih, I[q]);
+        if (vars == 1) {  // p-refinement on I(p), FV on I(rho) (Sec. 4.3)
+            ip = I[1];
+            ih = I[0];
+        }
         if (Ip) Ip[e] = ip;
         if (Ih) Ih[e] = ih;
         uint8_t code = 0;
@@ -1292,11 +1296,11 @@ int launch_dt_noalloc(int nk, const Params& P, const Tiles& T, int ntiles, const
 }
 
 void launch_indicator(int nk, const Params& P, const double* U, int n_elem, double* Ip, double* Ih, uint8_t* dec,
-                      const double thr[4], int N_min, int N_max, cudaStream_t s) {
+                      const double thr[4], int N_min, int N_max, int vars, cudaStream_t s) {
     const Thresholds t{thr[0], thr[1], thr[2], thr[3]};
     const size_t sm = sizeof(double) * (size_t)MAXP * MAXP * MAXP * (nk + 4 + 2 + 2 * (nk + 1));
     DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_indicator<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
-                       k_indicator<NK><<<n_elem, 128, sm, s>>>(P, U, n_elem, Ip, Ih, dec, t, N_min, N_max)));
+                       k_indicator<NK><<<n_elem, 128, sm, s>>>(P, U, n_elem, Ip, Ih, dec, t, N_min, N_max, vars)));
 }
 
 void launch_remap(const Params& P, const uint8_t* n_old, const uint8_t* N_old, const uint8_t* fv_old,

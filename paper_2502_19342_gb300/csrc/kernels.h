@@ -36,7 +36,7 @@ constexpr int DT_NOALLOC_MAX_DEVICES = 64;
 int launch_dt_noalloc(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, double cfl_c,
                       double cfl_v, double* out3, cudaStream_t s);
 void launch_indicator(int nk, const Params& P, const double* U, int n_elem, double* Ip, double* Ih, uint8_t* dec,
-                      const double thr[4], int N_min, int N_max, cudaStream_t s);
+                      const double thr[4], int N_min, int N_max, int vars, cudaStream_t s);
 void launch_remap(const Params& P, const uint8_t* n_old, const uint8_t* N_old, const uint8_t* fv_old,
                   const int64_t* off_old, const uint8_t* n_new, const uint8_t* N_new, const uint8_t* fv_new,
                   const int64_t* off_new, int V, int n_elem, const double* Uo, double* Un, cudaStream_t s);

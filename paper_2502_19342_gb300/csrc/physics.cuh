@@ -37,7 +37,15 @@ struct DevPhys {
     int riemann;  // 0 LLF, 1 Roe + Harten-Hyman, 2 Roe-HH between DG elements, LLF where FV data meet
     double cv[MAXSP], cp[MAXSP], mu[MAXSP], pr[MAXSP], D[MAXSP];
     double maxD;
+    int sutherland;     // viscosity by Sutherland's law (Sec. 4.3)
+    double T_ref, S;    // its reference temperature and constant
 };
+
+// Sutherland factor (T/T_ref)^{3/2} (T_ref + S)/(T + S) of the viscosity.
+DGFV_HD double sutherland_factor(const DevPhys& P, double T) {
+    const double r = T / P.T_ref;
+    return r * sqrt(r) * ((P.T_ref + P.S) / (T + P.S));
+}
 
 template <int NK>
 struct Prim {
@@ -75,6 +83,7 @@ DGFV_HD void prim(const DevPhys& P, const double* u, Prim<NK>& s) {
     s.T = eps * s.icv;
     s.p = rho * (cp - cv) * s.T;
     s.c = sqrt(s.kappa * s.p * s.irho);
+    if (P.sutherland) mu *= sutherland_factor(P, s.T);
     s.mu = mu;
     s.lam = mu * cp / pr;
 }

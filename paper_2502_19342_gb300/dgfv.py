@@ -34,13 +34,14 @@ class MeshDesc(C.Structure):
 
 class Phys(C.Structure):
     _fields_ = [("n_species", C.c_int), ("gamma", C.c_double * 3), ("Rgas", C.c_double * 3),
-                ("mu", C.c_double * 3), ("Pr", C.c_double * 3), ("D", C.c_double * 3)]
+                ("mu", C.c_double * 3), ("Pr", C.c_double * 3), ("D", C.c_double * 3), ("sutherland", C.c_int),
+                ("T_ref", C.c_double), ("S", C.c_double)]
 
 
 class Opts(C.Structure):
     _fields_ = [("riemann", C.c_int), ("cfl_c", C.c_double), ("cfl_v", C.c_double), ("T_fv_on", C.c_double),
                 ("T_fv_off", C.c_double), ("T_ref", C.c_double), ("T_crs", C.c_double), ("nodes", C.c_int),
-                ("split_form", C.c_int), ("integrator", C.c_int)]
+                ("split_form", C.c_int), ("integrator", C.c_int), ("indicator_vars", C.c_int)]
 
 
 class AdaptStats(C.Structure):
@@ -147,11 +148,15 @@ class Context:
             ph.mu[k] = float(problem["mu"][k])
             ph.Pr[k] = float(problem["Pr"][k])
             ph.D[k] = float(problem["Dk"][k])
+        ph.sutherland = int(problem.get("sutherland", 0))
+        ph.T_ref = float(problem.get("T_ref", 1.0))
+        ph.S = float(problem.get("S_sutherland", 0.0))
         o = dict(cfl_c=0.5, cfl_v=0.5, thresholds=(1.0, 1.6, 3.0, 7.0))
         o.update(opts or {})
         thr = o["thresholds"]
         op = Opts(int(problem.get("riemann", 0)), float(o["cfl_c"]), float(o["cfl_v"]), *[float(x) for x in thr],
-                  int(problem.get("nodes", 0)), int(problem.get("split", 0)), int(o.get("integrator", 0)))
+                  int(problem.get("nodes", 0)), int(problem.get("split", 0)), int(o.get("integrator", 0)),
+                  int(problem.get("indicator_vars", 0)))
         h = C.c_void_p()
         rc = L.dgfv_init_mesh(C.byref(h), C.byref(mesh), C.byref(ph), C.byref(op))
         if rc != 0:

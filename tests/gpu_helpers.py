@@ -39,7 +39,8 @@ def field_errors(prob, got, ref):
 
 def assert_fields_close(prob, got, ref, rtol=RTOL, what="R"):
     errs = field_errors(prob, got, ref)
-    assert max(errs) <= rtol, f"{what}: per-field relative errors {errs}"
+    assert np.isfinite(ref).all(), f"{what}: the reference is not finite"
+    assert all(e <= rtol for e in errs), f"{what}: per-field relative errors {errs}"  # NaN fails too
     return errs
 
 
@@ -53,6 +54,7 @@ def assert_rhs_close(oracle, prob, U, got, factor=3.0):
     FP64 oracle itself) can sit above it.  The CUDA path must be as accurate
     as the FP64 oracle within `factor`."""
     ref = oracle.eval_rhs_extended(prob, U)
+    assert np.isfinite(ref).all(), "the oracle's R is not finite on this input"
     own = field_errors(prob, oracle.eval_rhs(prob, U), ref)
     errs = field_errors(prob, got, ref)
     bound = [max(RTOL, factor * max(own))] * len(own)

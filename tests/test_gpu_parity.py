@@ -331,3 +331,25 @@ def test_lsrk4_graph_equals_steps_and_stage_adjoint_is_rejected():
     with pytest.raises(dgfv.DgfvError):
         ctx.rk_step_save(1e-4, s1, s2)
     ctx.close()
+
+
+def test_tgv_sutherland_indicator_choice_and_lsrk4(oracle):
+    """The supersonic TGV set-up (Sec. 4.3) on 6^3 elements with degrees 2..4 and
+    FV elements: R(U) with Sutherland's viscosity, the indicator with
+    p-refinement on the pressure and FV on the density, and 3 low-storage RK4
+    CFL steps.  (On 4^3 elements the p-coupling of N = 2 faces to N = 4 gives
+    negative pressures at face points, in the oracle and the CUDA path alike.)"""
+    n = 216
+    prob, U = W.tgv(nel=6, N0=W.random_degrees(n, 2, 4, 31), fv=W.random_fv(n, 0.2, 31))
+    assert_rhs_close(oracle, prob, U, gpu_rhs(prob, U))
+    ctx = ctx_for(prob, opts=dict(integrator=1, cfl_c=0.5, cfl_v=0.5), N_min=2, N_max=4)
+    Ip, Ih, _ = ctx.indicator(to_dev(U))
+    oIp, oIh = oracle.indicator(prob, U)
+    np.testing.assert_allclose(Ip.cpu().numpy(), oIp, rtol=1e-6, atol=1e-9)
+    np.testing.assert_allclose(Ih.cpu().numpy(), oIh, rtol=1e-6, atol=1e-9)
+    ctx.set_state(to_dev(U))
+    dts = [ctx.rk_step(-1.0) for _ in range(3)]
+    Uo, odts = oracle.lsrk4(prob, U, 3, cfl_c=0.5, cfl_v=0.5)
+    np.testing.assert_allclose(dts, odts, rtol=1e-13)
+    assert_fields_close(prob, ctx.get_state().cpu().numpy(), Uo, what="TGV U(3 LSRK4 steps)")
+    ctx.close()
