@@ -36,6 +36,7 @@ class _Problem(C.Structure):
         ("n_species", C.c_int), ("gamma", _dp), ("Rgas", _dp), ("mu", _dp), ("Pr", _dp),
         ("Dk", _dp), ("riemann", C.c_int), ("N", _i8p), ("fv", _u8p), ("nodes", C.c_int), ("split", C.c_int),
         ("sutherland", C.c_int), ("T_ref", C.c_double), ("S_sutherland", C.c_double), ("indicator_vars", C.c_int),
+        ("pp_limiter", C.c_int), ("pp_eps", C.c_double),
     ]
 
 
@@ -57,6 +58,8 @@ def lib():
         L.oracle_lsrk4.argtypes = [P, _dp, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
         L.oracle_lsrk4_scalar.restype = C.c_double
         L.oracle_lsrk4_scalar.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
+        L.oracle_pp_limit.restype = C.c_int64
+        L.oracle_pp_limit.argtypes = [P, _dp, C.c_double]
         L.oracle_rk3_scalar_linear.restype = C.c_double
         L.oracle_rk3_scalar_linear.argtypes = [C.c_double, C.c_double, C.c_double]
         L.oracle_indicator.argtypes = [P, _dp, _dp, _dp]
@@ -104,7 +107,7 @@ class _Bound:
             _ptr(sp[3], _dp), _ptr(sp[4], _dp), int(prob.get("riemann", 0)),
             _ptr(self.N, _i8p), _ptr(self.fv, _u8p), int(prob.get("nodes", 0)), int(prob.get("split", 0)),
             int(prob.get("sutherland", 0)), float(prob.get("T_ref", 1.0)), float(prob.get("S_sutherland", 0.0)),
-            int(prob.get("indicator_vars", 0)))
+            int(prob.get("indicator_vars", 0)), int(prob.get("pp_limiter", 0)), float(prob.get("pp_eps", 1e-10)))
 
     @property
     def ref(self):
@@ -203,6 +206,16 @@ def lsrk4(prob, U, n_steps, dt_fixed=-1.0, cfl_c=0.5, cfl_v=0.5):
     dts = np.zeros(max(n_steps, 1))
     _check(lib().oracle_lsrk4(b.ref, _ptr(X, _dp), n_steps, dt_fixed, cfl_c, cfl_v, _ptr(dts, _dp)), "lsrk4")
     return X, dts[:n_steps]
+
+
+def pp_limit(prob, U, eps=1e-10):
+    """Positivity limiter (Sec. 3.5) applied once; returns (U_limited, elements changed)."""
+    b = _Bound(prob)
+    X = np.array(U, dtype=np.float64, copy=True)
+    n = lib().oracle_pp_limit(b.ref, _ptr(X, _dp), float(eps))
+    if n < 0:
+        raise RuntimeError("oracle pp_limit failed")
+    return X, int(n)
 
 
 def lsrk4_scalar(kind, lam, dt_, u0):

@@ -19,6 +19,7 @@
 #include "dgfv_oracle.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -61,6 +62,8 @@ struct Problem {
     int riemann = 0;
     int nodes = 0;  // 0 Legendre-Gauss, 1 Legendre-Gauss-Lobatto
     int indicator_vars = 0;  // 0: p-adaptation on rho, FV on min(p, Y_k); 1: p-adaptation on p, FV on rho
+    int pp = 0;              // positivity limiter after every stage
+    double pp_eps = 1e-10;
     int split = 0;  // 1: split-form volume integral with the kinetic-energy-preserving two-point flux
     vector<Elem> el;
     int64_t size = 0;
@@ -87,6 +90,9 @@ Problem make_problem(const oracle_problem* p, bool need_ops = true) {
     P.nodes = p->nodes;
     P.split = p->split;
     P.indicator_vars = p->indicator_vars;
+    P.pp = p->pp_limiter;
+    P.pp_eps = p->pp_eps;
+    if (P.pp && !(P.pp_eps > 0.0)) throw std::runtime_error("bad positivity floor");
     P.ph.sutherland = p->sutherland != 0;
     P.ph.T_ref = p->T_ref;
     P.ph.S = p->S_sutherland;
@@ -755,16 +761,23 @@ void time_step(const Problem& P, const double* U, double cfl_c, double cfl_v, do
 
 // ------------------------------------------------------------------ SSP-RK3 (Shu-Osher)
 //   U1 = U0 + dt R(U0);  U2 = 3/4 U0 + 1/4 (U1 + dt R(U1));  U3 = 1/3 U0 + 2/3 (U2 + dt R(U2))
-template <class Rhs>
-void ssp_rk3_step(int64_t n, double* U, double dt, Rhs rhs) {
+// post(U) is applied to every stage state (the positivity limiter, Sec. 3.5).
+template <class Rhs, class Post>
+void ssp_rk3_step(int64_t n, double* U, double dt, Rhs rhs, Post post) {
     static const double a[3] = {0.0, 0.75, 1.0 / 3.0};
     static const double b[3] = {1.0, 0.25, 2.0 / 3.0};
     vector<double> U0(U, U + n), Us(U, U + n), Rv(n);
     for (int s = 0; s < 3; ++s) {
         rhs(Us.data(), Rv.data());
         for (int64_t i = 0; i < n; ++i) Us[i] = a[s] * U0[i] + b[s] * (Us[i] + dt * Rv[i]);
+        post(Us.data());
     }
     std::copy(Us.begin(), Us.end(), U);
+}
+
+template <class Rhs>
+void ssp_rk3_step(int64_t n, double* U, double dt, Rhs rhs) {
+    ssp_rk3_step(n, U, dt, rhs, [](double*) {});
 }
 
 // ------------------------------------------------------------------ low-storage RK4 (Sec. 3.3)
@@ -772,8 +785,8 @@ void ssp_rk3_step(int64_t n, double* U, double dt, Rhs rhs) {
 // Carpenter), read as the five-stage 2N-storage method of Carpenter and Kennedy
 // (1994), coefficients as published:
 //   dU <- A_s dU + dt R(U);   U <- U + B_s dU,   s = 1..5,  A_1 = 0.
-template <class Rhs>
-void lsrk4_step(int64_t n, double* U, double dt, Rhs rhs) {
+template <class Rhs, class Post>
+void lsrk4_step(int64_t n, double* U, double dt, Rhs rhs, Post post) {
     static const double A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
                                 -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
     static const double B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
@@ -786,7 +799,109 @@ void lsrk4_step(int64_t n, double* U, double dt, Rhs rhs) {
             dU[i] = A[s] * dU[i] + dt * Rv[i];
             U[i] = U[i] + B[s] * dU[i];
         }
+        post(U);
     }
+}
+
+template <class Rhs>
+void lsrk4_step(int64_t n, double* U, double dt, Rhs rhs) {
+    lsrk4_step(n, U, dt, rhs, [](double*) {});
+}
+
+// ------------------------------------------------------------------ positivity limiter (Sec. 3.5)
+// Zhang and Shu's limiter on every DG element (FV elements are left alone):
+// with the element mean ubar (quadrature of the element's own nodes, exact for
+// its polynomial) and the check points = the nodes and the points of the six
+// faces (the face values that the face fluxes use),
+//  (1) every partial density: theta_k = (ubar_k - eps_k)/(ubar_k - min rho_k) if the
+//      minimum is below eps_k = min(eps, ubar_k); rho_k <- ubar_k + theta_k (rho_k - ubar_k);
+//  (2) the internal energy rho e = rho E - |rho v|^2/(2 rho) (positive exactly
+//      when the pressure is, kappa > 1): at every check point with rho e < eps_e =
+//      min(eps, rho e(ubar)), t = the root in (0, 1) of rho e(ubar + t (u - ubar))
+//      = eps_e (found by bisection; rho e is concave along the segment);
+//      theta = min t;  u <- ubar + theta (u - ubar), every variable.
+// Reading (the paper names the limiter only): partial densities limited one by
+// one; check points include the face points; applied to every stage state.
+double internal_energy(int nk, const double* u) {
+    double rho = 0.0;
+    for (int k = 0; k < nk; ++k) rho += u[k];
+    return u[nk + 3] - 0.5 * (u[nk] * u[nk] + u[nk + 1] * u[nk + 1] + u[nk + 2] * u[nk + 2]) / rho;
+}
+
+int64_t pp_limit(const Problem& P, double* U, double eps) {
+    const int V = P.V, nk = P.ph.nk;
+    int64_t limited = 0;
+    for (const Elem& E : P.el) {
+        if (E.fv) continue;
+        const Basis1D& B = P.ops.B(E.N);
+        const int n = E.n, n3 = n * n * n;
+        double* u = U + E.off;
+        auto node = [&](int v, int c) -> double& { return u[(size_t)v * n3 + c]; };
+        double mean[MAXV];
+        for (int v = 0; v < V; ++v) {
+            double m = 0.0;
+            for (int c = 0; c < n3; ++c) m += B.w[c % n] * B.w[(c / n) % n] * B.w[c / (n * n)] * node(v, c);
+            mean[v] = m / 8.0;
+        }
+        // the check points: nodes, then the face points (linear in the nodes)
+        auto points = [&](std::vector<std::array<double, MAXV>>& pts) {
+            pts.clear();
+            for (int c = 0; c < n3; ++c) {
+                std::array<double, MAXV> q{};
+                for (int v = 0; v < V; ++v) q[v] = node(v, c);
+                pts.push_back(q);
+            }
+            for (int f = 0; f < 6; ++f) {
+                const int d = f / 2;
+                const vector<double>& l = (f % 2) ? B.lp : B.lm;
+                for (int b = 0; b < n; ++b)
+                    for (int a = 0; a < n; ++a) {
+                        std::array<double, MAXV> q{};
+                        for (int v = 0; v < V; ++v) {
+                            double s = 0.0;
+                            for (int m = 0; m < n; ++m) s += l[m] * node(v, node_index(n, d, m, a, b));
+                            q[v] = s;
+                        }
+                        pts.push_back(q);
+                    }
+            }
+        };
+        std::vector<std::array<double, MAXV>> pts;
+        bool active = false;
+        points(pts);
+        for (int k = 0; k < nk; ++k) {
+            double mn = mean[k];
+            for (auto& q : pts) mn = std::min(mn, q[k]);
+            const double ek = std::min(eps, mean[k]);
+            if (mn < ek) {
+                const double th = (mean[k] - ek) / (mean[k] - mn);
+                for (int c = 0; c < n3; ++c) node(k, c) = mean[k] + th * (node(k, c) - mean[k]);
+                active = true;
+            }
+        }
+        points(pts);
+        const double ee = std::min(eps, internal_energy(nk, mean));
+        double theta = 1.0;
+        for (auto& q : pts) {
+            if (internal_energy(nk, q.data()) >= ee) continue;
+            double lo = 0.0, hi = 1.0;  // rho e(lo) >= ee > rho e(hi)
+            for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+                const double t = 0.5 * (lo + hi);
+                if (t <= lo || t >= hi) break;
+                double x[MAXV];
+                for (int v = 0; v < V; ++v) x[v] = mean[v] + t * (q[v] - mean[v]);
+                (internal_energy(nk, x) >= ee ? lo : hi) = t;
+            }
+            theta = std::min(theta, lo);
+        }
+        if (theta < 1.0) {
+            for (int v = 0; v < V; ++v)
+                for (int c = 0; c < n3; ++c) node(v, c) = mean[v] + theta * (node(v, c) - mean[v]);
+            active = true;
+        }
+        limited += active ? 1 : 0;
+    }
+    return limited;
 }
 
 // ------------------------------------------------------------------ indicator, Sec. 3.4
@@ -949,7 +1064,8 @@ int oracle_rk3(const oracle_problem* p, double* U, int n_steps, double dt_fixed,
                 dt = o[0];
             }
             if (dts) dts[it] = dt;
-            ssp_rk3_step(P.size, U, dt, [&](const double* x, double* r) { eval_rhs_t<double>(P, x, r); });
+            ssp_rk3_step(P.size, U, dt, [&](const double* x, double* r) { eval_rhs_t<double>(P, x, r); },
+                         [&](double* x) { if (P.pp) pp_limit(P, x, P.pp_eps); });
         }
         return 0;
     } catch (...) { return -1; }
@@ -967,7 +1083,8 @@ int oracle_lsrk4(const oracle_problem* p, double* U, int n_steps, double dt_fixe
                 dt = o[0];
             }
             if (dts) dts[it] = dt;
-            lsrk4_step(P.size, U, dt, [&](const double* x, double* r) { eval_rhs_t<double>(P, x, r); });
+            lsrk4_step(P.size, U, dt, [&](const double* x, double* r) { eval_rhs_t<double>(P, x, r); },
+                       [&](double* x) { if (P.pp) pp_limit(P, x, P.pp_eps); });
         }
         return 0;
     } catch (...) { return -1; }
@@ -980,6 +1097,13 @@ double oracle_lsrk4_scalar(int kind, double lambda, double dt, double u0) {
     else
         lsrk4_step(1, &u, dt, [&](const double* x, double* r) { r[0] = -x[0] * x[0]; });
     return u;
+}
+
+int64_t oracle_pp_limit(const oracle_problem* p, double* U, double eps) {
+    try {
+        Problem P = make_problem(p);
+        return pp_limit(P, U, eps);
+    } catch (...) { return -1; }
 }
 
 double oracle_rk3_scalar_linear(double lambda, double dt, double u0) {

@@ -50,6 +50,8 @@ typedef struct {
     double S_sutherland;   /* Sutherland constant S (>= 0)                   */
     int indicator_vars;    /* 0: p-adaptation on rho, FV on min(p, Y_k);
                               1: p-adaptation on p, FV on rho (Sec. 4.3)     */
+    int pp_limiter;        /* 1 = Zhang-Shu positivity limiter after every RK stage (Sec. 3.5) */
+    double pp_eps;         /* its floor for partial densities and internal energy (> 0) */
 } oracle_problem;
 
 /* 0 on success, negative on a malformed problem. */
@@ -93,6 +95,10 @@ double oracle_rk3_scalar_linear(double lambda, double dt, double u0);
  * (Sec. 3.3), otherwise as oracle_rk3. */
 int oracle_lsrk4(const oracle_problem* p, double* U, int n_steps, double dt_fixed,
                  double cfl_c, double cfl_v, double* dts);
+
+/* Positivity limiter of Sec. 3.5 applied once to U in place (floor eps);
+ * returns the number of DG elements it changed, or -1. */
+int64_t oracle_pp_limit(const oracle_problem* p, double* U, double eps);
 
 /* One low-storage RK4 step of u' = lambda u (kind 0) or u' = -u^2 (kind 1),
  * through the same stage routine as oracle_lsrk4 (test hook). */

@@ -765,3 +765,96 @@ def test_lsrk4_on_the_dg_operator_is_fourth_order_in_time(oracle):
     ref, _ = oracle.lsrk4(prob, U, 32, dt_fixed=T / 32)
     e = [np.abs(oracle.lsrk4(prob, U, m, dt_fixed=T / m)[0] - ref).max() for m in (1, 2, 4)]
     assert np.log2(e[0] / e[1]) > 3.6 and np.log2(e[1] / e[2]) > 3.6, e
+
+
+# ---------------------------------------------------------------- positivity limiter (Sec. 3.5)
+def _rarefaction():
+    """Two streams pulled apart (v_x up to 12, p = 0.4) on 16 x 1 x 1 elements,
+    N = 3, air/helium, inviscid: the unlimited scheme loses positivity."""
+    sp = W.species_set([W.AIR, W.HELIUM], mu=0.0)
+    prob = W.make_problem([((16, 1, 1), (0, 0, 0), (1, 1.0 / 16, 1.0 / 16))], sp, n_fv=6, N=3)
+
+    def fn(x, y, z):
+        v = 12.0 * np.tanh((x - 0.5) / 0.05) * np.sin(2 * np.pi * x) ** 2
+        return [0.5 + 0 * x, 0.5 + 0 * x], (v, 0 * x, 0 * x), 0.4 + 0 * x
+    return prob, W.build_state(prob, fn)
+
+
+def _check_points(prob, U, e):
+    """Nodes and the six faces' points of DG element e (numpy's LG basis)."""
+    off, _ = W.offsets(prob)
+    V = W.n_vars(prob)
+    n = int(prob["N"][e]) + 1
+    blk = U[off[e]:off[e] + V * n ** 3].reshape(V, n, n, n)  # (v, k, j, i)
+    x = np.polynomial.legendre.leggauss(n)[0]
+    C = np.linalg.inv(np.vander(x, n, increasing=True))
+    lm, lp = np.vander([-1.0], n, increasing=True) @ C, np.vander([1.0], n, increasing=True) @ C
+    pts = [blk.reshape(V, -1)]
+    for ax in (1, 2, 3):
+        for l in (lm[0], lp[0]):
+            pts.append(np.tensordot(blk, l, axes=([ax], [0])).reshape(V, -1))
+    return np.concatenate(pts, axis=1)
+
+
+def _mean(prob, U, e):
+    off, _ = W.offsets(prob)
+    V = W.n_vars(prob)
+    n = int(prob["N"][e]) + 1
+    w = np.polynomial.legendre.leggauss(n)[1]
+    blk = U[off[e]:off[e] + V * n ** 3].reshape(V, n, n, n)
+    return np.einsum("vkji,k,j,i->v", blk, w, w, w) / 8.0
+
+
+def _rho_e(q, nk):
+    return q[nk + 3] - 0.5 * (q[nk] ** 2 + q[nk + 1] ** 2 + q[nk + 2] ** 2) / q[:nk].sum(0)
+
+
+def test_pp_limiter_keeps_positivity_means_and_is_a_no_op_on_positive_states(oracle):
+    prob, U = _rarefaction()
+    nk, eps = 2, 1e-10
+    same, n0 = oracle.pp_limit(prob, U, eps)
+    assert n0 == 0 and np.array_equal(same, U)
+    # a state that lost positivity: 46 unlimited steps (still positive), then the
+    # deviations from every element mean amplified sixfold (means unchanged)
+    X, _ = oracle.rk3(prob, U, 46, cfl_c=0.3, cfl_v=0.3)
+    off, _ = W.offsets(prob)
+    for e in range(16):
+        blk = X[off[e]:off[e] + 6 * 64].reshape(6, 64)
+        m = _mean(prob, X, e)
+        blk[:] = m[:, None] + 6.0 * (blk - m[:, None])
+    bad = [e for e in range(16) if (_check_points(prob, X, e)[:nk] < 0).any()
+           or (_rho_e(_check_points(prob, X, e), nk) < 0).any()]
+    assert bad, "the unlimited run should have lost positivity by now"
+    L, nl = oracle.pp_limit(prob, X, eps)
+    assert nl >= len(bad)
+    for e in range(16):
+        m0, m1 = _mean(prob, X, e), _mean(prob, L, e)
+        np.testing.assert_allclose(m1, m0, rtol=1e-13, atol=1e-14 * np.abs(m0).max())
+        q = _check_points(prob, L, e)
+        for k in range(nk):
+            assert q[k].min() >= min(eps, m0[k]) * (1 - 1e-9) - 1e-15
+        re = _rho_e(q, nk)
+        assert re.min() >= min(eps, _rho_e(m0, nk)) - 1e-12
+        if e in bad and (_rho_e(_check_points(prob, X, e), nk) < 0).any():
+            # the internal-energy step is tight: the smallest value sits on the floor
+            assert re.min() < min(eps, _rho_e(m0, nk)) + 1e-9
+        # momentum and energy move on one line towards the mean (one theta per element)
+        d0 = (_check_points(prob, X, e) - m0[:, None])[nk:]
+        d1 = (q - m0[:, None])[nk:]
+        big = np.abs(d0) > 1e-8 * np.abs(d0).max()
+        ratios = d1[big] / d0[big]
+        assert ratios.max() - ratios.min() < 1e-9
+
+
+def test_pp_limiter_keeps_a_rarefaction_alive(oracle):
+    """Without the limiter the rarefaction breaks down (non-finite values
+    within 60 SSP-RK3 steps); with it the run stays finite and every partial
+    density and internal energy at the check points stays non-negative."""
+    prob, U = _rarefaction()
+    X, _ = oracle.rk3(prob, U, 60, cfl_c=0.3, cfl_v=0.3)
+    assert not np.isfinite(X).all()
+    Y, _ = oracle.rk3(dict(prob, pp_limiter=1, pp_eps=1e-10), U, 60, cfl_c=0.3, cfl_v=0.3)
+    assert np.isfinite(Y).all()
+    for e in range(16):
+        q = _check_points(prob, Y, e)
+        assert q[:2].min() >= -1e-14 and _rho_e(q, 2).min() >= -1e-12
