@@ -107,6 +107,10 @@ typedef struct {
     int indicator_vars; /* 0: p-adaptation on I(rho), FV on min(I(p), I(Y_k));
                            1: p-adaptation on I(p), FV on I(rho) (the TGV of
                            Sec. 4.3)                                          */
+    int pp_limiter;     /* 1: Zhang-Shu positivity limiter on every DG element
+                           after every Runge-Kutta stage (Sec. 3.5)           */
+    double pp_eps;      /* its floor for partial densities and internal energy
+                           (> 0 when pp_limiter = 1)                          */
 } dgfv_opts;
 
 typedef struct {
@@ -214,6 +218,19 @@ int dgfv_rk_step_save(dgfv_ctx* ctx, double dt, double* d_stage1, double* d_stag
  * stages. */
 int dgfv_rk_step_vjp_stages(dgfv_ctx* ctx, const double* const* d_stages, double dt, const double* d_Ubar_next,
                             double* d_Ubar, void* stream);
+
+/* Positivity limiter of Sec. 3.5 (Zhang and Shu) applied once, in place, to
+ * the caller's device state d_U (the context's layout): every DG element's
+ * partial densities and internal energy are pulled towards the element mean
+ * until they are >= min(pp_eps, mean value) at the nodes and face points; the
+ * means are unchanged.  *changed (host, may be NULL) receives the number of
+ * elements changed (synchronises when non-NULL).  With pp_limiter = 1 the same
+ * kernel runs after every stage of dgfv_rk_step / dgfv_rk_steps. */
+int dgfv_pp_limit(dgfv_ctx* ctx, double* d_U, int64_t* changed, void* stream);
+
+/* Number of element limitings by the stage limiter since the last reset
+ * (reset != 0 clears the counter after reading).  Synchronises. */
+int dgfv_pp_count(dgfv_ctx* ctx, int64_t* count, int reset, void* stream);
 
 /* Modal indicator of Sec. 3.4 on the state d_U: per element I_p = I(rho),
  * I_h = min(I(p), I(Y_k)) (device arrays of n_elem doubles, may be NULL) and

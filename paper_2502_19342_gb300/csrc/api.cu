@@ -94,6 +94,7 @@ struct dgfv_ctx {
     double *d_Ip = nullptr, *d_Ih = nullptr;
     uint8_t* d_dec = nullptr;
     int* d_status = nullptr;
+    unsigned long long* d_pp_count = nullptr;  // elements changed by the stage limiter
     TileSet all, dg, fvt;
     FaceList lift, flux;    // flux: faces that change representation
     FaceTileSet conf;       // faces with one representation on both sides
@@ -194,6 +195,7 @@ int build_bank(dgfv_ctx* c) {
     for (int n = c->N_min + 1; n <= c->N_max + 1; ++n) {
         Bank1D b = make_bank(n, kind);
         c->bi.dhat[n] = put(b.Dhat);
+        c->bi.w[n] = put(b.w);
         if (c->opts.split_form) {
             // 2D - W^{-1}B: the boundary correction -(B_ii/w_i) F(u_i) folded into the diagonal
             std::vector<double> S(n * n);
@@ -388,6 +390,7 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
     const Faces F{c->d_faceL, c->d_faceR, c->d_faceD};
     const bool per_bin = c->launch_mode == 1;
     double* dU = mode == 2 ? c->d_Us : nullptr;  // low-storage RK4 register
+    const int n_dg = (int)c->dg.items.size();
     if (!have_faces) {
         Timed t(c, K_PROLONG, s);
         if (per_bin)
@@ -431,6 +434,12 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
         else
             launch_surface(c->nk, P, c->all.view(), c->all.ntiles, Uin, U0, out, mode, a, b, c->d_dt3, fuse_faces, dU,
                            s);
+    }
+    if (mode != 0 && c->opts.pp_limiter && n_dg > 0) {
+        // positivity limiter on the new stage state; changed elements also
+        // rewrite the face values fused above
+        Timed t(c, K_SURFACE, s);
+        launch_pp_limit(c->nk, P, c->dg.d_items, n_dg, out, c->opts.pp_eps, c->d_pp_count, fuse_faces, s);
     }
 }
 
@@ -594,6 +603,8 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     c->ph.S = phys->S;
     if (c->ph.sutherland && !(phys->T_ref > 0.0 && phys->S >= 0.0)) return cleanup(DGFV_ERR_ARG);
     if (opts->indicator_vars < 0 || opts->indicator_vars > 1) return cleanup(DGFV_ERR_ARG);
+    if (opts->pp_limiter < 0 || opts->pp_limiter > 1 || (opts->pp_limiter && !(opts->pp_eps > 0.0)))
+        return cleanup(DGFV_ERR_ARG);
     c->n_elem = (int)ne;
     c->nb.resize(6 * ne);
     c->rh.resize(3 * ne);
@@ -638,7 +649,7 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     A_(c->d_flift, c->cap_fpts * c->V) A_(c->d_frec, c->cap_fpts * c->V)
     A_(c->d_rtmp, c->cap_state) A_(c->d_U, c->cap_state) A_(c->d_Us, c->cap_state)
     A_(c->d_dt3, 4) A_(c->d_partial, 2 * ne + 2) A_(c->d_Ip, ne) A_(c->d_Ih, ne) A_(c->d_dec, ne)
-    A_(c->d_status, 1) A_(c->lift.d, c->n_faces) A_(c->flux.d, c->n_faces)
+    A_(c->d_status, 1) A_(c->d_pp_count, 2) A_(c->lift.d, c->n_faces) A_(c->flux.d, c->n_faces)
     A_(c->conf.d_first, c->n_faces) A_(c->conf.d_count, c->n_faces) A_(c->conf.d_nc, c->n_faces)
     A_(c->conf.d_d, c->n_faces) A_(c->conf.d_items, c->n_faces)
 #undef A_
@@ -646,6 +657,7 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     if ((r = alloc_tiles(c, c->dg)) != DGFV_OK) return cleanup(r);
     if ((r = alloc_tiles(c, c->fvt)) != DGFV_OK) return cleanup(r);
     if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) return cleanup(DGFV_ERR_CUDA);
+    if (cudaMemset(c->d_pp_count, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) return cleanup(DGFV_ERR_CUDA);
     if (cudaMemcpy(c->d_nb, c->nb.data(), c->nb.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->d_rh, c->rh.data(), c->rh.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->d_faceL, c->faceL.data(), c->n_faces * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -820,8 +832,8 @@ int dgfv_rk_step_vjp(dgfv_ctx* c, const double* d_U0, double dt, const double* d
                      void* stream) {
     if (!c || !d_U0 || !d_Ubar_next || !d_Ubar || !(dt > 0.0)) return DGFV_ERR_ARG;
     if (d_Ubar == d_Ubar_next || d_Ubar == d_U0) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
-    if (c->opts.integrator != DGFV_INTEGRATOR_SSPRK3)
-        return fail(c, DGFV_ERR_ARG, "stage adjoints and stage saving support SSP-RK3 only");
+    if (c->opts.integrator != DGFV_INTEGRATOR_SSPRK3 || c->opts.pp_limiter)
+        return fail(c, DGFV_ERR_ARG, "stage adjoints and stage saving support SSP-RK3 without the limiter only");
     TRY(adj_prepare(c));
     cudaStream_t s = (cudaStream_t)stream;
     // stage states of the step (recomputed from the step's start state)
@@ -838,8 +850,8 @@ int dgfv_rk_step_vjp_stages(dgfv_ctx* c, const double* const* d_stages, double d
     for (int i = 0; i < 3; ++i)
         if (d_Ubar == d_stages[i]) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
     if (d_Ubar == d_Ubar_next) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
-    if (c->opts.integrator != DGFV_INTEGRATOR_SSPRK3)
-        return fail(c, DGFV_ERR_ARG, "stage adjoints and stage saving support SSP-RK3 only");
+    if (c->opts.integrator != DGFV_INTEGRATOR_SSPRK3 || c->opts.pp_limiter)
+        return fail(c, DGFV_ERR_ARG, "stage adjoints and stage saving support SSP-RK3 without the limiter only");
     TRY(adj_prepare(c));
     return rk_step_vjp_impl(c, d_stages[0], d_stages[1], d_stages[2], dt, d_Ubar_next, d_Ubar, (cudaStream_t)stream);
 }
@@ -847,8 +859,8 @@ int dgfv_rk_step_vjp_stages(dgfv_ctx* c, const double* const* d_stages, double d
 int dgfv_rk_step_save(dgfv_ctx* c, double dt, double* d_stage1, double* d_stage2, void* stream) {
     if (!c || !d_stage1 || !d_stage2 || !(dt > 0.0)) return DGFV_ERR_ARG;
     if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "rk_step_save before set_state");
-    if (c->opts.integrator != DGFV_INTEGRATOR_SSPRK3)
-        return fail(c, DGFV_ERR_ARG, "stage adjoints and stage saving support SSP-RK3 only");
+    if (c->opts.integrator != DGFV_INTEGRATOR_SSPRK3 || c->opts.pp_limiter)
+        return fail(c, DGFV_ERR_ARG, "stage adjoints and stage saving support SSP-RK3 without the limiter only");
     cudaStream_t s = (cudaStream_t)stream;
     launch_set_scalar(c->d_dt3, dt, s);
     enqueue_stage(c, c->d_U, c->d_U, d_stage1, 1, 0.0, 1.0, s, false, true);
@@ -1115,6 +1127,34 @@ int64_t dgfv_bank_entry(dgfv_ctx* c, int which, int N, int M, double* out, int64
     if ((int64_t)v.size() > cap) return DGFV_ERR_ARG;
     std::copy(v.begin(), v.end(), out);
     return (int64_t)v.size();
+}
+
+int dgfv_pp_limit(dgfv_ctx* c, double* d_U, int64_t* changed, void* stream) {
+    if (!c || !d_U) return DGFV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double eps = c->opts.pp_eps > 0.0 ? c->opts.pp_eps : 1e-10;
+    unsigned long long* cnt = c->d_pp_count + 1;  // scratch counter of this call
+    CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+    launch_pp_limit(c->nk, params(c), c->dg.d_items, (int)c->dg.items.size(), d_U, eps, cnt, false, s);
+    CK(cudaGetLastError());
+    if (changed) {
+        unsigned long long h = 0;
+        CK(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *changed = (int64_t)h;
+    }
+    return DGFV_OK;
+}
+
+int dgfv_pp_count(dgfv_ctx* c, int64_t* count, int reset, void* stream) {
+    if (!c || !count) return DGFV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long h = 0;
+    CK(cudaMemcpyAsync(&h, c->d_pp_count, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *count = (int64_t)h;
+    if (reset) CK(cudaMemsetAsync(c->d_pp_count, 0, sizeof(unsigned long long), s));
+    return DGFV_OK;
 }
 
 double dgfv_probe_dfma(int iters, void* stream) { return probe_dfma(iters, (cudaStream_t)stream); }

@@ -22,6 +22,7 @@ constexpr int NBANK = MAXP + 1;
 struct BankIdx {
     int32_t dhat[NBANK];       // n x n weighted derivative matrix
     int32_t dsplit[NBANK];     // n x n split-form matrix 2D - W^{-1}B (LGL nodes only)
+    int32_t w[NBANK];          // quadrature weights of the nodes
     int32_t lm[NBANK], lp[NBANK];    // l_j(-1), l_j(+1)
     int32_t lhm[NBANK], lhp[NBANK];  // l_j(-1)/w_j, l_j(+1)/w_j
     int32_t vinv[NBANK];       // inverse orthonormal-Legendre Vandermonde (n x n)

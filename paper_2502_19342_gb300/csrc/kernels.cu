@@ -812,6 +812,180 @@ __global__ void __launch_bounds__(256) k_surface(Params P, Tiles T, const double
 }
 
 // ---------------------------------------------------------------------------------
+// k_pp_limit: Zhang-Shu positivity limiter (Sec. 3.5), one CTA per DG element.
+// Element mean by the element's quadrature; check points = nodes + face points;
+// (1) every partial density towards its mean (floor min(eps, mean));
+// (2) one factor theta for all variables from the internal energy rho e =
+//     rho E - |rho v|^2/(2 rho): at a check point below the floor, t solves the
+//     quadratic rho(t) (rho E(t) - floor) - |m(t)|^2/2 = 0 on the segment from the
+//     mean (closed form; rho e is concave along it, one root in (0, 1)).
+// Changed elements are written back (state and their face values for the next
+// stage) and counted.
+template <int NK>
+__global__ void __launch_bounds__(128) k_pp_limit(Params P, const int32_t* __restrict__ items, double* U,
+                                                  double eps, unsigned long long* count, int write_faces) {
+    constexpr int V = NK + 4;
+    extern __shared__ double sm[];
+    __shared__ double red[V][4];
+    __shared__ double s_theta[NK + 1];
+    __shared__ int s_active;
+    const int e = items[blockIdx.x];
+    const int n = P.t.n[e], n2 = n * n, n3 = n2 * n, nf = 6 * n2;
+    double* su = sm;            // V * n3 nodes
+    double* sf = su + V * n3;   // V * 6 n^2 face points
+    double* sw = sf + V * nf;   // weights (n), lm, lp (n each)
+    double* src = U + P.t.off[e];
+    if (threadIdx.x < n) {
+        sw[threadIdx.x] = B(P, P.bi.w[n])[threadIdx.x];
+        sw[n + threadIdx.x] = B(P, P.bi.lm[n])[threadIdx.x];
+        sw[2 * n + threadIdx.x] = B(P, P.bi.lp[n])[threadIdx.x];
+    }
+    if (threadIdx.x == 0) s_active = 0;
+    for (int i = threadIdx.x; i < V * n3; i += blockDim.x) su[i] = src[i];
+    __syncthreads();
+    // element mean (fixed per-thread order, then a fixed reduction order)
+    double part[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) part[v] = 0.0;
+    for (int c = threadIdx.x; c < n3; c += blockDim.x) {
+        const double w = sw[c % n] * sw[(c / n) % n] * sw[c / n2];
+#pragma unroll
+        for (int v = 0; v < V; ++v) part[v] = fma(w, su[v * n3 + c], part[v]);
+    }
+    __shared__ double sred[V][128 / 32];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        double x = part[v];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) sred[v][threadIdx.x >> 5] = x;
+    }
+    // face points
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        const int f = i / n2, p = i % n2, d = f >> 1, a = p % n, b = p / n;
+        const double* l = sw + ((f & 1) ? 2 * n : n);
+        const int c0 = node_index(n, d, 0, a, b), st = d == 0 ? 1 : (d == 1 ? n : n2);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            double s = 0.0;
+            for (int m = 0; m < n; ++m) s = fma(l[m], su[v * n3 + c0 + m * st], s);
+            sf[v * nf + i] = s;
+        }
+    }
+    __syncthreads();
+    double mean[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        double x = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += sred[v][w];
+        mean[v] = 0.125 * x;
+    }
+    // (1) partial densities: minima over nodes and face points
+    double mn[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) mn[k] = mean[k];
+    for (int i = threadIdx.x; i < n3 + nf; i += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k) mn[k] = fmin(mn[k], i < n3 ? su[k * n3 + i] : sf[k * nf + i - n3]);
+    }
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        double x = mn[k];
+        for (int o = 16; o > 0; o >>= 1) x = fmin(x, __shfl_down_sync(0xffffffffu, x, o));
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            double x = red[k][0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) x = fmin(x, red[k][w]);
+            const double ek = fmin(eps, mean[k]);
+            s_theta[k] = x < ek ? (mean[k] - ek) / (mean[k] - x) : 1.0;
+            if (x < ek) s_active = 1;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n3 + nf; i += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const double th = s_theta[k];
+            if (th < 1.0) {
+                double* q = i < n3 ? &su[k * n3 + i] : &sf[k * nf + i - n3];
+                *q = fma(th, *q - mean[k], mean[k]);
+            }
+        }
+    }
+    __syncthreads();
+    // (2) internal energy
+    double rb = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) rb += mean[k];
+    const double mb2 = mean[NK] * mean[NK] + mean[NK + 1] * mean[NK + 1] + mean[NK + 2] * mean[NK + 2];
+    const double ee = fmin(eps, mean[NK + 3] - 0.5 * mb2 / rb);
+    double tmin = 1.0;
+    for (int i = threadIdx.x; i < n3 + nf; i += blockDim.x) {
+        double q[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) q[v] = i < n3 ? su[v * n3 + i] : sf[v * nf + i - n3];
+        double r = 0.0;
+#pragma unroll
+        for (int k = 0; k < NK; ++k) r += q[k];
+        const double m2 = q[NK] * q[NK] + q[NK + 1] * q[NK + 1] + q[NK + 2] * q[NK + 2];
+        if (q[NK + 3] - 0.5 * m2 / r >= ee) continue;
+        double ar = 0.0;
+#pragma unroll
+        for (int k = 0; k < NK; ++k) ar += q[k] - mean[k];
+        const double aE = q[NK + 3] - mean[NK + 3];
+        double am2 = 0.0, mam = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double a = q[NK + j] - mean[NK + j];
+            am2 = fma(a, a, am2);
+            mam = fma(mean[NK + j], a, mam);
+        }
+        const double c0 = rb * (mean[NK + 3] - ee) - 0.5 * mb2;
+        const double c1 = rb * aE + ar * (mean[NK + 3] - ee) - mam;
+        const double c2 = ar * aE - 0.5 * am2;
+        double t;
+        if (fabs(c2) <= 1e-14 * (fabs(c1) + fabs(c0))) {
+            t = -c0 / c1;
+        } else {
+            const double disc = fmax(c1 * c1 - 4.0 * c0 * c2, 0.0);
+            const double qq = -0.5 * (c1 + copysign(sqrt(disc), c1));
+            const double r1 = qq / c2, r2 = c0 / qq;
+            t = 1.0;
+            if (r1 >= 0.0 && r1 <= 1.0) t = fmin(t, r1);
+            if (r2 >= 0.0 && r2 <= 1.0) t = fmin(t, r2);
+        }
+        tmin = fmin(tmin, fmax(t, 0.0));
+    }
+    for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_down_sync(0xffffffffu, tmin, o));
+    if ((threadIdx.x & 31) == 0) red[0][threadIdx.x >> 5] = tmin;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = red[0][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) x = fmin(x, red[0][w]);
+        s_theta[NK] = x;
+        if (x < 1.0) s_active = 1;
+        if (s_active) atomicAdd(count, 1ULL);
+    }
+    __syncthreads();
+    if (!s_active) return;
+    const double th = s_theta[NK];
+    for (int i = threadIdx.x; i < V * n3; i += blockDim.x) {
+        const int v = i / n3;
+        src[i] = th < 1.0 ? fma(th, su[i] - mean[v], mean[v]) : su[i];
+    }
+    if (write_faces) {
+        for (int i = threadIdx.x; i < V * nf; i += blockDim.x) {
+            const int v = i / nf, r = i % nf, f = r / n2, p = r % n2;
+            const double x = th < 1.0 ? fma(th, sf[i] - mean[v], mean[v]) : sf[i];
+            P.b.fu[(P.t.fo[e] + (int64_t)f * n2) * V + v * n2 + p] = x;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // Time step of Sec. 3.3: per-block maxima of the inverse time scales
 //   lc = (2N+1) sum_d (|v_d| + c)/dx_d,  lv = (2N+1) dv sum_d 1/dx_d^2
 // (FV: factor 1, dx = h/N_FV), then dt_c = cfl_c / max lc and dt_v = cfl_v / max lv
@@ -1259,6 +1433,15 @@ void launch_dt(int nk, const Params& P, const Tiles& T, int ntiles, const double
 }
 
 void launch_set_scalar(double* p, double v, cudaStream_t s) { k_set_scalar<<<1, 1, 0, s>>>(p, v); }
+
+void launch_pp_limit(int nk, const Params& P, const int32_t* items, int n_dg, double* U, double eps,
+                     unsigned long long* count, bool write_faces, cudaStream_t s) {
+    if (n_dg <= 0) return;
+    const int V = nk + 4;
+    const size_t sm = sizeof(double) * (size_t)(V * MAXP * MAXP * MAXP + 6 * V * MAXP * MAXP + 3 * MAXP);
+    DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_pp_limit<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                       k_pp_limit<NK><<<n_dg, 128, sm, s>>>(P, items, U, eps, count, write_faces ? 1 : 0)));
+}
 
 // Scratch of the allocation-free time step (dgfv_compute_dt_noalloc): the
 // per-block maxima of k_dt live in this fixed array instead of a buffer the

@@ -28,6 +28,8 @@ void launch_surface(int nk, const Params& P, const Tiles& T, int ntiles, const d
                     cudaStream_t s);
 void launch_dt(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, double cfl_c, double cfl_v,
                double* partial, double* out3, cudaStream_t s);
+void launch_pp_limit(int nk, const Params& P, const int32_t* items, int n_dg, double* U, double eps,
+                     unsigned long long* count, bool write_faces, cudaStream_t s);
 void launch_set_scalar(double* p, double v, cudaStream_t s);
 // Time step with the per-block minima in a fixed device array (no allocation).
 // Returns 0, 1 when ntiles exceeds DT_NOALLOC_MAX_BLOCKS, 2 on a CUDA error.

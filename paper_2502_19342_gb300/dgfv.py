@@ -23,7 +23,7 @@ SYMBOLS = ["dgfv_init_mesh", "dgfv_num_elements", "dgfv_set_degrees", "dgfv_get_
            "dgfv_status_string", "dgfv_last_error", "dgfv_destroy", "dgfv_bank_entry", "dgfv_probe_dfma",
            "dgfv_profile_enable", "dgfv_profile_read", "dgfv_compute_dt_noalloc", "dgfv_rhs_vjp",
            "dgfv_rk_step_vjp", "dgfv_set_launch_mode", "dgfv_autotune", "dgfv_rk_step_save",
-           "dgfv_rk_step_vjp_stages", "dgfv_probe_dmma"]
+           "dgfv_rk_step_vjp_stages", "dgfv_probe_dmma", "dgfv_pp_limit", "dgfv_pp_count"]
 KERNELS = ["prolong", "fv", "face_lift", "dg_volume", "face_flux", "surface", "dt", "indicator", "remap"]
 
 
@@ -41,7 +41,8 @@ class Phys(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("riemann", C.c_int), ("cfl_c", C.c_double), ("cfl_v", C.c_double), ("T_fv_on", C.c_double),
                 ("T_fv_off", C.c_double), ("T_ref", C.c_double), ("T_crs", C.c_double), ("nodes", C.c_int),
-                ("split_form", C.c_int), ("integrator", C.c_int), ("indicator_vars", C.c_int)]
+                ("split_form", C.c_int), ("integrator", C.c_int), ("indicator_vars", C.c_int),
+                ("pp_limiter", C.c_int), ("pp_eps", C.c_double)]
 
 
 class AdaptStats(C.Structure):
@@ -92,6 +93,8 @@ def lib():
         L.dgfv_bank_entry.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp, i64]
         L.dgfv_probe_dfma.restype = C.c_double
         L.dgfv_probe_dfma.argtypes = [C.c_int, vp]
+        L.dgfv_pp_limit.argtypes = [vp, vp, C.POINTER(i64), vp]
+        L.dgfv_pp_count.argtypes = [vp, C.POINTER(i64), C.c_int, vp]
         L.dgfv_probe_dmma.restype = C.c_double
         L.dgfv_probe_dmma.argtypes = [C.c_int, vp]
         L.dgfv_profile_enable.argtypes = [vp, C.c_int]
@@ -156,7 +159,8 @@ class Context:
         thr = o["thresholds"]
         op = Opts(int(problem.get("riemann", 0)), float(o["cfl_c"]), float(o["cfl_v"]), *[float(x) for x in thr],
                   int(problem.get("nodes", 0)), int(problem.get("split", 0)), int(o.get("integrator", 0)),
-                  int(problem.get("indicator_vars", 0)))
+                  int(problem.get("indicator_vars", 0)), int(problem.get("pp_limiter", 0)),
+                  float(problem.get("pp_eps", 1e-10)))
         h = C.c_void_p()
         rc = L.dgfv_init_mesh(C.byref(h), C.byref(mesh), C.byref(ph), C.byref(op))
         if rc != 0:
@@ -293,6 +297,19 @@ class Context:
         self._rc(lib().dgfv_rk_step_vjp_stages(self.h, arr, float(dt), _ptr(Ubar_next), _ptr(Ubar), _stream(stream)),
                  "rk_step_vjp_stages")
         return Ubar
+
+    def pp_limit(self, U, stream=None):
+        """Positivity limiter (Sec. 3.5) applied once to U in place; returns the elements changed."""
+        _check_dev(U, self.state_size)
+        n = C.c_int64(0)
+        self._rc(lib().dgfv_pp_limit(self.h, _ptr(U), C.byref(n), _stream(stream)), "pp_limit")
+        return int(n.value)
+
+    def pp_count(self, reset=False, stream=None):
+        """Element limitings by the stage limiter since the last reset."""
+        n = C.c_int64(0)
+        self._rc(lib().dgfv_pp_count(self.h, C.byref(n), int(bool(reset)), _stream(stream)), "pp_count")
+        return int(n.value)
 
     def compute_dt(self, U, stream=None):
         _check_dev(U, self.state_size)

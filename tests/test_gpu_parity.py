@@ -353,3 +353,61 @@ def test_tgv_sutherland_indicator_choice_and_lsrk4(oracle):
     np.testing.assert_allclose(dts, odts, rtol=1e-13)
     assert_fields_close(prob, ctx.get_state().cpu().numpy(), Uo, what="TGV U(3 LSRK4 steps)")
     ctx.close()
+
+
+def _amplified_rarefaction(oracle, nodes=0):
+    """The limiter pins' rarefaction after 46 (LGL: 30) SSP-RK3 steps with every
+    element's deviation from its mean amplified sixfold (negative partial
+    densities and internal energies at some points, positive means)."""
+    sp = W.species_set([W.AIR, W.HELIUM], mu=0.0)
+    prob = W.make_problem([((16, 1, 1), (0, 0, 0), (1, 1.0 / 16, 1.0 / 16))], sp, n_fv=6, N=3, nodes=nodes)
+
+    def fn(x, y, z):
+        v = 12.0 * np.tanh((x - 0.5) / 0.05) * np.sin(2 * np.pi * x) ** 2
+        return [0.5 + 0 * x, 0.5 + 0 * x], (v, 0 * x, 0 * x), 0.4 + 0 * x
+    U = W.build_state(prob, fn)
+    X, _ = oracle.rk3(prob, U, 46 if nodes == 0 else 30, cfl_c=0.3, cfl_v=0.3)  # LGL breaks down earlier
+    assert np.isfinite(X).all()
+    w = np.polynomial.legendre.leggauss(4)[1] if nodes == 0 else np.array([1 / 6, 5 / 6, 5 / 6, 1 / 6])
+    w3 = np.einsum("k,j,i->kji", w, w, w).ravel() / 8.0
+    for e in range(16):
+        blk = X[e * 384:(e + 1) * 384].reshape(6, 64)
+        m = blk @ w3
+        blk[:] = m[:, None] + 6.0 * (blk - m[:, None])
+    return prob, U, X
+
+
+@pytest.mark.parametrize("nodes", [0, 1])
+def test_pp_limiter_once_matches_oracle(oracle, nodes):
+    prob, _, X = _amplified_rarefaction(oracle, nodes)
+    ref, n_ref = oracle.pp_limit(prob, X, 1e-10)
+    assert n_ref > 0
+    ctx = ctx_for(prob, opts=dict(pp_eps=1e-10))
+    Xd = to_dev(X)
+    n = ctx.pp_limit(Xd)
+    assert n == n_ref
+    assert_fields_close(prob, Xd.cpu().numpy(), ref, rtol=1e-12, what="limited state")
+    ctx.close()
+
+
+def test_pp_limiter_in_the_stages_matches_oracle(oracle):
+    """SSP-RK3 with the limiter after every stage through the breakdown point of
+    the unlimited rarefaction (step 47).  Near vacuum the limited dynamics
+    amplify rounding: the oracle started from U (1 + 1e-15 noise) drifts from
+    itself by ~1e-10 after 48 steps and ~1e-5 after 52.  The bound is 10x that
+    drift of the oracle against itself (at least 1e-10)."""
+    from tests.gpu_helpers import field_errors
+    prob, U, _ = _amplified_rarefaction(oracle)
+    p = dict(prob, pp_limiter=1, pp_eps=1e-10)
+    steps = 48
+    Uo, dto = oracle.rk3(p, U, steps, cfl_c=0.3, cfl_v=0.3)
+    noise = 1e-15 * np.random.default_rng(0).standard_normal(U.size)
+    Up, _ = oracle.rk3(p, U * (1 + noise), steps, cfl_c=0.3, cfl_v=0.3)
+    bound = max(1e-10, 10 * max(field_errors(prob, Up, Uo)))
+    ctx = ctx_for(p, opts=dict(cfl_c=0.3, cfl_v=0.3))
+    ctx.set_state(to_dev(U))
+    dts = [ctx.rk_step(-1.0) for _ in range(steps)]
+    assert ctx.pp_count() > 0
+    np.testing.assert_allclose(dts, dto, rtol=1e-10)
+    assert_fields_close(prob, ctx.get_state().cpu().numpy(), Uo, rtol=bound, what=f"U({steps} limited steps)")
+    ctx.close()
