@@ -58,6 +58,8 @@ def lib():
         L.oracle_lsrk4.argtypes = [P, _dp, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
         L.oracle_lsrk4_scalar.restype = C.c_double
         L.oracle_lsrk4_scalar.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
+        L.oracle_set_threads.restype = C.c_int
+        L.oracle_set_threads.argtypes = [C.c_int]
         L.oracle_pp_limit.restype = C.c_int64
         L.oracle_pp_limit.argtypes = [P, _dp, C.c_double]
         L.oracle_rk3_scalar_linear.restype = C.c_double
@@ -206,6 +208,11 @@ def lsrk4(prob, U, n_steps, dt_fixed=-1.0, cfl_c=0.5, cfl_v=0.5):
     dts = np.zeros(max(n_steps, 1))
     _check(lib().oracle_lsrk4(b.ref, _ptr(X, _dp), n_steps, dt_fixed, cfl_c, cfl_v, _ptr(dts, _dp)), "lsrk4")
     return X, dts[:n_steps]
+
+
+def set_threads(n=0):
+    """Host threads of the oracle's loops (n > 0 sets them); returns the number in use."""
+    return int(lib().oracle_set_threads(int(n)))
 
 
 def pp_limit(prob, U, eps=1e-10):

@@ -27,6 +27,10 @@
 #include <utility>
 #include <vector>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #include "basis.hpp"
 #include "physics.hpp"
 
@@ -1097,6 +1101,16 @@ double oracle_lsrk4_scalar(int kind, double lambda, double dt, double u0) {
     else
         lsrk4_step(1, &u, dt, [&](const double* x, double* r) { r[0] = -x[0] * x[0]; });
     return u;
+}
+
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 int64_t oracle_pp_limit(const oracle_problem* p, double* U, double eps) {

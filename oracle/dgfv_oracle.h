@@ -96,6 +96,10 @@ double oracle_rk3_scalar_linear(double lambda, double dt, double u0);
 int oracle_lsrk4(const oracle_problem* p, double* U, int n_steps, double dt_fixed,
                  double cfl_c, double cfl_v, double* dts);
 
+/* Host threads of the oracle's parallel loops (n > 0 sets them); returns the
+ * number in use. */
+int oracle_set_threads(int n);
+
 /* Positivity limiter of Sec. 3.5 applied once to U in place (floor eps);
  * returns the number of DG elements it changed, or -1. */
 int64_t oracle_pp_limit(const oracle_problem* p, double* U, double eps);

@@ -485,3 +485,27 @@ def tgv(nel=32, N0=3, Ma=1.25, Re=1600.0, n_fv=8, nodes=0, riemann=0, fv=None):
         return [p / (R * T0)], v, p
 
     return prob, build_state(prob, fn)
+
+
+def shard_domains(prob, U, rank, world):
+    """This rank's share of a batch of independent domains: domains taken in
+    order of decreasing DOFs, each given to the rank with the fewest DOFs so far
+    (ties to the lower rank).  Returns (problem of the share, its state, the
+    domain ids, in increasing order)."""
+    slices = domain_slices(prob)
+    sizes = [sl.stop - sl.start for _, sl in slices]
+    load = [0] * world
+    owner = [0] * len(slices)
+    for d in sorted(range(len(slices)), key=lambda i: (-sizes[i], i)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[d] = r
+        load[r] += sizes[d]
+    ids = [d for d in range(len(slices)) if owner[d] == rank]
+    if not ids:
+        return None, None, []
+    subs = [slices[d][0] for d in ids]
+    share = dict(prob, dims=np.concatenate([s["dims"] for s in subs]), lo=np.concatenate([s["lo"] for s in subs]),
+                 hi=np.concatenate([s["hi"] for s in subs]), N=np.concatenate([s["N"] for s in subs]),
+                 fv=np.concatenate([s["fv"] for s in subs]))
+    Us = np.concatenate([U[slices[d][1]] for d in ids])
+    return share, Us, ids
