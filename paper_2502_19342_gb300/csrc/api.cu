@@ -50,6 +50,20 @@ struct FaceTileSet {
     FaceTiles view(int t0) const { return FaceTiles{d_first + t0, d_count + t0, d_nc + t0, d_d + t0, d_items}; }
 };
 
+// Faces that change representation, grouped like the conforming tiles by
+// (direction, common point count); face[k], pt[k] (scratch point offset) per
+// mixed face k in tile order.
+struct MixedSet {
+    FaceTileSet tiles;
+    std::vector<int32_t> face;
+    std::vector<int64_t> pt;
+    int32_t* d_face = nullptr;
+    int64_t* d_pt = nullptr;
+    int n = 0;
+    int64_t cap_pts = 0;              // capacity of the scratch in face points
+    double *d_in = nullptr, *d_out = nullptr;  // 4V and V values per point
+};
+
 enum Kernel { K_PROLONG = 0, K_FV, K_LIFT, K_VOLUME, K_FLUX, K_SURFACE, K_DT, K_INDICATOR, K_REMAP, K_COUNT };
 
 struct Profiler {
@@ -98,6 +112,7 @@ struct dgfv_ctx {
     TileSet all, dg, fvt;
     FaceList lift, flux;    // flux: faces that change representation
     FaceTileSet conf;       // faces with one representation on both sides
+    MixedSet mixed;         // the flux faces in three passes
     int n_fv_elems = 0;
     int launch_mode = 0;           // 0: one launch per kernel; 1: one launch per degree bin
     int vol_per_tile[MAXP + 1] = {};  // elements per volume tile (0: default), set by the autotuner
@@ -359,6 +374,62 @@ int apply_layout(dgfv_ctx* c) {
             CK(cudaMemcpy(t.d_items, t.items.data(), t.items.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
         }
     }
+    {
+        // mixed faces: common representation N_FV sub-cells or the higher degree
+        MixedSet& m = c->mixed;
+        FaceTileSet& t = m.tiles;
+        t.first.clear(); t.count.clear(); t.items.clear(); t.nc.clear(); t.d.clear();
+        m.face.clear();
+        m.pt.clear();
+        std::vector<int32_t> by[3][MAXP + 1];
+        for (int32_t f : c->flux.ids) {
+            const int L = c->faceL[f], R = c->faceR[f];
+            const int nc = (c->fv[L] || c->fv[R]) ? c->nfv : std::max<int>(c->npts[L], c->npts[R]);
+            by[c->faceD[f]][nc].push_back(f);
+        }
+        int64_t pts = 0;
+        for (int d = 0; d < 3; ++d)
+            for (int nc = 1; nc <= MAXP; ++nc) {
+                const auto& g = by[d][nc];
+                const int per = std::max(1, 128 / (nc * nc));
+                for (size_t s0 = 0; s0 < g.size(); s0 += per) {
+                    const int cnt = (int)std::min<size_t>(per, g.size() - s0);
+                    t.first.push_back((int32_t)t.items.size());
+                    t.count.push_back(cnt);
+                    t.nc.push_back((uint8_t)nc);
+                    t.d.push_back((uint8_t)d);
+                    for (int q = 0; q < cnt; ++q) {
+                        t.items.push_back((int32_t)m.face.size());
+                        m.face.push_back(g[s0 + q]);
+                        m.pt.push_back(pts);
+                        pts += nc * nc;
+                    }
+                }
+            }
+        t.ntiles = (int)t.first.size();
+        m.n = (int)m.face.size();
+        if (pts > m.cap_pts) {  // grow the scratch (graphs are recaptured after a layout change)
+            for (double** q : {&m.d_in, &m.d_out}) {
+                if (*q) {
+                    cudaFree(*q);
+                    c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), (void*)*q));
+                    *q = nullptr;
+                }
+            }
+            m.cap_pts = pts + pts / 4;
+            TRY(dalloc(c, &m.d_in, (size_t)m.cap_pts * 4 * c->V));
+            TRY(dalloc(c, &m.d_out, (size_t)m.cap_pts * c->V));
+        }
+        if (t.ntiles) {
+            CK(cudaMemcpy(t.d_first, t.first.data(), t.ntiles * sizeof(int32_t), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(t.d_count, t.count.data(), t.ntiles * sizeof(int32_t), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(t.d_nc, t.nc.data(), t.ntiles, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(t.d_d, t.d.data(), t.ntiles, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(t.d_items, t.items.data(), t.items.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(m.d_face, m.face.data(), m.n * sizeof(int32_t), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(m.d_pt, m.pt.data(), m.n * sizeof(int64_t), cudaMemcpyHostToDevice));
+        }
+    }
     c->lift.count = (int)c->lift.ids.size();
     c->flux.count = (int)c->flux.ids.size();
     if (c->lift.count)
@@ -423,7 +494,8 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
                 launch_face_flux_conf(c->nk, P, F, c->conf.view(c->conf.bin_first[bi]), c->conf.bin_count[bi], s);
         else
             launch_face_flux_conf(c->nk, P, F, c->conf.view(), c->conf.ntiles, s);
-        launch_face_flux(c->nk, P, F, c->flux.d, c->flux.count, s);
+        launch_mixed_faces(c->nk, P, F, c->mixed.tiles.view(), c->mixed.tiles.ntiles, c->mixed.d_face, c->mixed.d_pt,
+                           c->mixed.n, c->mixed.d_in, c->mixed.d_out, s);
     }
     {
         Timed t(c, K_SURFACE, s);
@@ -652,6 +724,9 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     A_(c->d_status, 1) A_(c->d_pp_count, 2) A_(c->lift.d, c->n_faces) A_(c->flux.d, c->n_faces)
     A_(c->conf.d_first, c->n_faces) A_(c->conf.d_count, c->n_faces) A_(c->conf.d_nc, c->n_faces)
     A_(c->conf.d_d, c->n_faces) A_(c->conf.d_items, c->n_faces)
+    A_(c->mixed.tiles.d_first, c->n_faces) A_(c->mixed.tiles.d_count, c->n_faces)
+    A_(c->mixed.tiles.d_nc, c->n_faces) A_(c->mixed.tiles.d_d, c->n_faces) A_(c->mixed.tiles.d_items, c->n_faces)
+    A_(c->mixed.d_face, c->n_faces) A_(c->mixed.d_pt, c->n_faces)
 #undef A_
     if ((r = alloc_tiles(c, c->all)) != DGFV_OK) return cleanup(r);
     if ((r = alloc_tiles(c, c->dg)) != DGFV_OK) return cleanup(r);

@@ -1,17 +1,20 @@
 // FP64 CUDA kernels of the hybrid DG/FV right-hand side (sm_103a).
 //
-// One stage R(U) is six launches, in the paper's order of dependencies:
+// One stage R(U), in the paper's order of dependencies:
 //   k_prolong    face values: DG traces u(+-1) (Sec. 3.1.1), FV boundary sub-cell means
+//                (fused into the previous stage's k_surface within a step)
 //   k_fv         FV sub-cell elements (Sec. 3.1.2): minmod reconstruction, central
 //                gradients, interior sub-cell fluxes, element-face states
-//   k_face_lift  BR1 lifting value U* = (u- + u+)/2 (Eq. 19) on the lower degree /
+//   k_face_lift* BR1 lifting value U* = (u- + u+)/2 (Eq. 19) on the lower degree /
 //                on DG data at DG/FV faces (Sec. 3.2.2)
 //   k_dg_volume  lifting (Eq. 23) -> gradient in shared memory -> fluxes at the nodes
 //                -> volume integral (Eq. 22); traces of the gradient
-//   k_face_flux  F* = F^c* + (F^v- + F^v+)/2 (Eqs. 20, 21) on the higher degree / on
+//                (k_dg_volume_split: the split form on LGL nodes, Sec. 3.5)
+//   k_face_flux_conf, k_mixed_*
+//                F* = F^c* + (F^v- + F^v+)/2 (Eqs. 20, 21) on the higher degree / on
 //                FV data (Sec. 3.2.1), mapped back to both sides
-//   k_surface    surface integral and -1/J (Eqs. 22, 26), fused with the SSP-RK3
-//                stage combination
+//   k_surface    surface integral and -1/J (Eqs. 22, 26), fused with the Runge-Kutta
+//                stage update (k_pp_limit after it when the limiter is on)
 // plus the time step (Sec. 3.3), the modal indicator (Sec. 3.4) and the remap
 // of adapted elements (Sec. 3.2 mappings).
 //
@@ -334,16 +337,20 @@ __global__ void __launch_bounds__(256, MINB) k_dg_volume(Params P, Tiles T, cons
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
     const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
-    const int n2 = n * n, n3 = n2 * n;
-    double* sD = sm;             // n*n Dhat
-    double* sl = sD + n * n;     // lm, lp, lhm, lhp (4n)
-    double* sG = sl + 4 * n;     // count * 3V * n3
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) sD[i] = B(P, P.bi.dhat[n])[i];
+    const int n2 = n * n, n3 = n2 * n, q = n2 + 2 * n;
+    double* sl = sm;                 // lm, lp (2n)
+    double* sS = sl + 2 * n;         // per element and direction: (2/h_d) Dhat, (2/h_d) lhat(-1), (2/h_d) lhat(+1)
+    double* sG = sS + count * 3 * q; // count * 3V * n3
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         sl[i] = B(P, P.bi.lm[n])[i];
         sl[n + i] = B(P, P.bi.lp[n])[i];
-        sl[2 * n + i] = B(P, P.bi.lhm[n])[i];
-        sl[3 * n + i] = B(P, P.bi.lhp[n])[i];
+    }
+    for (int i = threadIdx.x; i < count * 3 * q; i += blockDim.x) {
+        const int el = i / (3 * q), r = i % (3 * q), d = r / q, k = r % q;
+        const double rh = P.t.rh[3 * T.items[first + el] + d];
+        const double b = k < n2 ? B(P, P.bi.dhat[n])[k]
+                                : (k < n2 + n ? B(P, P.bi.lhm[n])[k - n2] : B(P, P.bi.lhp[n])[k - n2 - n]);
+        sS[i] = rh * b;
     }
     __syncthreads();
     const bool visc = P.ph.viscous;
@@ -357,13 +364,14 @@ __global__ void __launch_bounds__(256, MINB) k_dg_volume(Params P, Tiles T, cons
             const int m0 = d == 0 ? i : (d == 1 ? j : k);
             const int a = d == 0 ? j : i, b = d == 2 ? j : k;
             const double* src = U + P.t.off[e] + (int64_t)v * n3;
+            const double* Sd = sS + (el * 3 + d) * q;
             double s = 0.0;
-            for (int m = 0; m < n; ++m) s = fma(sD[m0 * n + m], src[node_index(n, d, m, a, b)], s);
+            for (int m = 0; m < n; ++m) s = fma(Sd[m0 * n + m], src[node_index(n, d, m, a, b)], s);
             const int64_t fo = P.t.fo[e];
             const int p = a + n * b;
-            s = fma(sl[3 * n + m0], P.b.flift[(fo + (int64_t)(2 * d + 1) * n2) * V + v * n2 + p], s);
-            s = fma(-sl[2 * n + m0], P.b.flift[(fo + (int64_t)(2 * d) * n2) * V + v * n2 + p], s);
-            sG[el * per + r] = P.t.rh[3 * e + d] * s;
+            s = fma(Sd[n2 + n + m0], P.b.flift[(fo + (int64_t)(2 * d + 1) * n2) * V + v * n2 + p], s);
+            s = fma(-Sd[n2 + m0], P.b.flift[(fo + (int64_t)(2 * d) * n2) * V + v * n2 + p], s);
+            sG[el * per + r] = s;
         }
         __syncthreads();
         // traces of the gradient on the six faces
@@ -402,18 +410,13 @@ __global__ void __launch_bounds__(256, MINB) k_dg_volume(Params P, Tiles T, cons
         for (int d = 0; d < 3; ++d) {
             double F[V];
             flux_conv<NK>(u, s, d, F);
-            if (visc) {
-                double Fv[V];
-                flux_visc<NK>(P.ph, s, pg, d, Fv);
-#pragma unroll
-                for (int v = 0; v < V; ++v) F[v] += Fv[v];
-            }
+            if (visc) flux_visc_add<NK>(P.ph, s, pg, d, F);
 #pragma unroll
             for (int v = 0; v < V; ++v) G[(d * V + v) * n3] = F[v];
         }
     }
     __syncthreads();
-    // volume integral sum_d (2/h_d) sum_m Dhat_{i_d m} F_d(m)
+    // volume integral sum_d sum_m (2/h_d) Dhat_{i_d m} F_d(m), one accumulation chain
     const int per = V * n3;
     for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
         const int el = idx / per, r = idx % per, v = r / n3, c = r % n3;
@@ -426,9 +429,8 @@ __global__ void __launch_bounds__(256, MINB) k_dg_volume(Params P, Tiles T, cons
             const int m0 = ijk[d];
             const int a = d == 0 ? ijk[1] : ijk[0], b = d == 2 ? ijk[1] : ijk[2];
             const double* src = Fe + (d * V + v) * n3;
-            double s = 0.0;
-            for (int m = 0; m < n; ++m) s = fma(sD[m0 * n + m], src[node_index(n, d, m, a, b)], s);
-            acc = fma(P.t.rh[3 * e + d], s, acc);
+            const double* Sd = sS + (el * 3 + d) * q + m0 * n;
+            for (int m = 0; m < n; ++m) acc = fma(Sd[m], src[node_index(n, d, m, a, b)], acc);
         }
         P.b.rtmp[P.t.off[e] + r] = acc;
     }
@@ -627,104 +629,115 @@ __global__ void __launch_bounds__(128) k_face_flux_conf(Params P, Faces Fc, Face
     }
 }
 
-// k_face_flux: faces that change representation (unequal DG degrees, or DG/FV),
-// one CTA per face.  Common representation: N_FV sub-cells if either side is
-// FV, else the higher degree (Sec. 3.2.1, 3.2.2); the lower side's u and g are
-// mapped to it in shared memory, the flux is mapped back (L2 projection or
-// V^{FV->DG}).
-template <int NK>
-struct MixedFaceSmem {
-    static constexpr int V = NK + 4, PP = MAXP * MAXP;
-    double U[2][V * PP];
-    double G[2][3 * V * PP];
-    double F[V * PP];
-    double T[V * PP];  // scratch of one 2-pass map of V variables
+// ---------------------------------------------------------------------------------
+// Faces that change representation, in three passes (Sec. 3.2.1, 3.2.2): the
+// side not in the common representation (always a DG side: the lower degree,
+// or the DG side of a DG/FV face) is mapped to it (k_mixed_in: u and g by
+// V^{N->Nc} or V^{DG->FV}, into scratch); the flux runs one thread per common
+// face point like the conforming faces (k_mixed_flux; the other side read in
+// place, its flux written directly); the mapped side's flux is mapped back
+// (k_mixed_out: L2 projection or V^{FV->DG}).  Mixed face k: face mface[k],
+// scratch at point offset mpt[k] (4V values per point in, V out).
+struct MixedFace {
+    int eL, eR, nc;
+    bool cfv, mapL;
 };
 
-template <int NK, int D>
-__device__ __forceinline__ void mixed_face_body(const Params& P, int eL, int eR, MixedFaceSmem<NK>& S) {
+__device__ __forceinline__ MixedFace mixed_face(const Params& P, const Faces& Fc, int fid) {
+    MixedFace m;
+    m.eL = Fc.L[fid];
+    m.eR = Fc.R[fid];
+    m.cfv = P.t.fv[m.eL] || P.t.fv[m.eR];
+    const int nL = P.t.n[m.eL], nR = P.t.n[m.eR];
+    m.nc = m.cfv ? P.nfv : max(nL, nR);
+    m.mapL = m.cfv ? !P.t.fv[m.eL] : nL != m.nc;
+    return m;
+}
+
+template <int NK>
+__global__ void __launch_bounds__(128) k_mixed_in(Params P, Faces Fc, const int32_t* __restrict__ mface,
+                                                  const int64_t* __restrict__ mpt, double* __restrict__ Sin) {
     constexpr int V = NK + 4;
-    auto& sU = S.U;
-    auto& sG = S.G;
-    double* sF = S.F;
-    double* sT = S.T;
-    const int es[2] = {eL, eR};
-    const int fs[2] = {2 * D + 1, 2 * D};
-    const bool common_fv = P.t.fv[eL] || P.t.fv[eR];
-    const int nc = common_fv ? P.nfv : max((int)P.t.n[eL], (int)P.t.n[eR]);
+    __shared__ double tmp[3 * V * MAXP * MAXP];
+    const int k = blockIdx.x, fid = mface[k], d = Fc.d[fid];
+    const MixedFace m = mixed_face(P, Fc, fid);
+    const int e = m.mapL ? m.eL : m.eR, f = m.mapL ? 2 * d + 1 : 2 * d, n = P.t.n[e];
+    const int64_t slot = P.t.fo[e] + (int64_t)f * n * n;
+    const double* M = B(P, m.cfv ? P.bi.d2f[n] : P.bi.vm[n][m.nc]);
+    double* out = Sin + mpt[k] * 4 * V;
+    face_map(P.b.fu + slot * V, n, out, m.nc, M, V, tmp);
+    if (P.ph.viscous) face_map(P.b.fg + slot * 3 * V, n, out + V * m.nc * m.nc, m.nc, M, 3 * V, tmp);
+}
+
+template <int NK, int D>
+__device__ __forceinline__ void mixed_flux_body(const Params& P, const Faces& Fc, const int32_t* __restrict__ mface,
+                                                const int64_t* __restrict__ mpt, const double* __restrict__ Sin,
+                                                double* __restrict__ Sout, const int32_t* __restrict__ items,
+                                                int first, int count, int nc) {
+    constexpr int V = NK + 4;
     const int nc2 = nc * nc;
     const bool visc = P.ph.viscous;
-    for (int side = 0; side < 2; ++side) {
-        const int e = es[side], f = fs[side], n = P.t.n[e], n2 = n * n;
-        const bool fv = P.t.fv[e];
-        const int64_t slot = P.t.fo[e] + (int64_t)f * n2;
-        const double* su = (fv ? P.b.frec : P.b.fu) + slot * V;
-        const double* sg = P.b.fg + slot * 3 * V;
-        if (common_fv ? fv : n == nc) {  // already in the common representation
-            for (int i = threadIdx.x; i < V * nc2; i += blockDim.x) sU[side][i] = su[i];
-            if (visc)
-                for (int i = threadIdx.x; i < 3 * V * nc2; i += blockDim.x) sG[side][i] = sg[i];
-        } else {
-            const double* M = B(P, common_fv ? P.bi.d2f[n] : P.bi.vm[n][nc]);
-            double* raw = sG[side];  // staging of the raw trace
-            for (int i = threadIdx.x; i < V * n2; i += blockDim.x) raw[i] = su[i];
-            __syncthreads();
-            face_map(raw, n, sU[side], nc, M, V, sT);
-            if (visc) {
-                for (int part = 0; part < 3; ++part) {
-                    for (int i = threadIdx.x; i < V * n2; i += blockDim.x) sF[i] = sg[part * V * n2 + i];
-                    __syncthreads();
-                    face_map(sF, n, sG[side] + part * V * nc2, nc, M, V, sT);
-                }
-            }
-        }
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < nc2; p += blockDim.x) {
+    for (int t = threadIdx.x; t < count * nc2; t += blockDim.x) {
+        const int k = items[first + t / nc2], p = t % nc2;
+        const MixedFace m = mixed_face(P, Fc, mface[k]);
+        const int ed = m.mapL ? m.eR : m.eL, fd = m.mapL ? 2 * D : 2 * D + 1;
+        const int64_t sd = P.t.fo[ed] + (int64_t)fd * nc2;
+        const double* ud = (P.t.fv[ed] ? P.b.frec : P.b.fu) + sd * V + p;
+        const double* gd = P.b.fg + sd * 3 * V + p;
+        const double* um = Sin + mpt[k] * 4 * V + p;
+        const double* gm = um + V * nc2;
         double uL[V], uR[V], gL[3 * V], gR[3 * V], F[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            uL[v] = sU[0][v * nc2 + p];
-            uR[v] = sU[1][v * nc2 + p];
+            const double a = um[v * nc2], b = ud[v * nc2];
+            uL[v] = m.mapL ? a : b;
+            uR[v] = m.mapL ? b : a;
         }
         if (visc) {
 #pragma unroll
             for (int x = 0; x < 3 * V; ++x) {
-                gL[x] = sG[0][x * nc2 + p];
-                gR[x] = sG[1][x * nc2 + p];
+                const double a = gm[x * nc2], b = gd[x * nc2];
+                gL[x] = m.mapL ? a : b;
+                gR[x] = m.mapL ? b : a;
             }
         }
-        interface_flux<NK>(P.ph, uL, gL, uR, gR, D, F, common_fv);
+        interface_flux<NK>(P.ph, uL, gL, uR, gR, D, F, m.cfv);
+        double* dd = P.b.flux + sd * V + p;
+        double* so = Sout + mpt[k] * V + p;
+        const double sgn = m.mapL ? -1.0 : 1.0;  // the direct side is the upper element when L is mapped
 #pragma unroll
-        for (int v = 0; v < V; ++v) sF[v * nc2 + p] = F[v];
-    }
-    __syncthreads();
-    for (int side = 0; side < 2; ++side) {
-        const int e = es[side], f = fs[side], n = P.t.n[e], n2 = n * n;
-        const bool fv = P.t.fv[e];
-        const double sgn = side == 0 ? 1.0 : -1.0;  // outward normal of the upper element is -x_d
-        double* dst = P.b.flux + (P.t.fo[e] + (int64_t)f * n2) * V;
-        if (common_fv ? fv : n == nc) {
-            for (int i = threadIdx.x; i < V * nc2; i += blockDim.x) dst[i] = sgn * sF[i];
-        } else {
-            // back to the side's degree: L2 projection, or V^{FV->DG} from sub-cell data
-            const double* M = B(P, common_fv ? P.bi.f2d[n] : P.bi.vm[nc][n]);
-            face_map(sF, nc, sU[side], n, M, V, sT);
-            for (int i = threadIdx.x; i < V * n2; i += blockDim.x) dst[i] = sgn * sU[side][i];
+        for (int v = 0; v < V; ++v) {
+            dd[v * nc2] = sgn * F[v];
+            so[v * nc2] = F[v];
         }
     }
 }
 
 template <int NK>
-__global__ void __launch_bounds__(64) k_face_flux(Params P, Faces Fc, const int32_t* __restrict__ list) {
-    __shared__ MixedFaceSmem<NK> S;
-    const int fid = list[blockIdx.x];
-    const int eL = Fc.L[fid], eR = Fc.R[fid];
-    switch (Fc.d[fid]) {
-        case 0: mixed_face_body<NK, 0>(P, eL, eR, S); break;
-        case 1: mixed_face_body<NK, 1>(P, eL, eR, S); break;
-        default: mixed_face_body<NK, 2>(P, eL, eR, S); break;
+__global__ void __launch_bounds__(128) k_mixed_flux(Params P, Faces Fc, FaceTiles T, const int32_t* __restrict__ mface,
+                                                    const int64_t* __restrict__ mpt, const double* __restrict__ Sin,
+                                                    double* __restrict__ Sout) {
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], nc = T.nc[blockIdx.x];
+    switch (T.d[blockIdx.x]) {
+        case 0: mixed_flux_body<NK, 0>(P, Fc, mface, mpt, Sin, Sout, T.items, first, count, nc); break;
+        case 1: mixed_flux_body<NK, 1>(P, Fc, mface, mpt, Sin, Sout, T.items, first, count, nc); break;
+        default: mixed_flux_body<NK, 2>(P, Fc, mface, mpt, Sin, Sout, T.items, first, count, nc); break;
     }
+}
+
+template <int NK>
+__global__ void __launch_bounds__(128) k_mixed_out(Params P, Faces Fc, const int32_t* __restrict__ mface,
+                                                   const int64_t* __restrict__ mpt, const double* __restrict__ Sout) {
+    constexpr int V = NK + 4;
+    __shared__ double tmp[V * MAXP * MAXP], res[V * MAXP * MAXP];
+    const int k = blockIdx.x, fid = mface[k], d = Fc.d[fid];
+    const MixedFace m = mixed_face(P, Fc, fid);
+    const int e = m.mapL ? m.eL : m.eR, f = m.mapL ? 2 * d + 1 : 2 * d, n = P.t.n[e], n2 = n * n;
+    const double* M = B(P, m.cfv ? P.bi.f2d[n] : P.bi.vm[m.nc][n]);
+    face_map(Sout + mpt[k] * V, m.nc, res, n, M, V, tmp);
+    const double sgn = m.mapL ? 1.0 : -1.0;  // outward normal of the upper element is -x_d
+    double* dst = P.b.flux + (P.t.fo[e] + (int64_t)f * n2) * V;
+    for (int i = threadIdx.x; i < V * n2; i += blockDim.x) dst[i] = sgn * res[i];
 }
 
 // ---------------------------------------------------------------------------------
@@ -735,10 +748,11 @@ __global__ void __launch_bounds__(64) k_face_flux(Params P, Faces Fc, const int3
 // One thread per node, all variables.  With fuse != 0 (mode 1) the new state
 // is also kept in shared memory and its face values are written for the next
 // evaluation (the face-value pass of that evaluation is then skipped).
-template <int NK>
+template <int NK, int MODE>
 __global__ void __launch_bounds__(256) k_surface(Params P, Tiles T, const double* Uin, const double* U0,
-                                                 double* out, int mode, double a, double b,
+                                                 double* out, double a, double b,
                                                  const double* __restrict__ dtp, int fuse, double* dU) {
+    constexpr int mode = MODE;
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
     double* sl = sm;             // lm, lp, lhm, lhp
@@ -1374,7 +1388,7 @@ void launch_face_lift(int nk, const Params& P, const Faces& F, const int32_t* li
 
 size_t volume_smem_bytes(int nk, int n, int count) {
     const int V = nk + 4;
-    return sizeof(double) * (size_t)(n * n + 4 * n + count * 3 * V * n * n * n);
+    return sizeof(double) * (size_t)(2 * n + count * 3 * (n * n + 2 * n) + count * 3 * V * n * n * n);
 }
 
 // variant bit 0: 128 threads per CTA (else 256); bit 1: register budget for
@@ -1407,9 +1421,12 @@ void launch_dg_volume_split(int nk, const Params& P, const Tiles& T, int ntiles,
                        k_dg_volume_split<NK><<<ntiles, 256, smem, s>>>(P, T, U)));
 }
 
-void launch_face_flux(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s) {
-    if (nfaces <= 0) return;
-    DGFV_DISPATCH(nk, (k_face_flux<NK><<<nfaces, 64, 0, s>>>(P, F, list)));
+void launch_mixed_faces(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, const int32_t* mface,
+                        const int64_t* mpt, int nmixed, double* Sin, double* Sout, cudaStream_t s) {
+    if (nmixed <= 0) return;
+    DGFV_DISPATCH(nk, (k_mixed_in<NK><<<nmixed, 128, 0, s>>>(P, F, mface, mpt, Sin),
+                       k_mixed_flux<NK><<<ntiles, 128, 0, s>>>(P, F, T, mface, mpt, Sin, Sout),
+                       k_mixed_out<NK><<<nmixed, 128, 0, s>>>(P, F, mface, mpt, Sout)));
 }
 
 void launch_face_flux_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s) {
@@ -1423,7 +1440,13 @@ void launch_surface(int nk, const Params& P, const Tiles& T, int ntiles, const d
     if (ntiles <= 0) return;
     const int f = (fuse && mode != 0) ? 1 : 0;
     const size_t sm = f ? tile_state_smem(nk) : sizeof(double) * 4 * MAXP;
-    DGFV_DISPATCH(nk, (k_surface<NK><<<ntiles, 256, sm, s>>>(P, T, Uin, U0, out, mode, a, b, dt, f, dU)));
+    if (mode == 0) {
+        DGFV_DISPATCH(nk, (k_surface<NK, 0><<<ntiles, 256, sm, s>>>(P, T, Uin, U0, out, a, b, dt, f, dU)));
+    } else if (mode == 1) {
+        DGFV_DISPATCH(nk, (k_surface<NK, 1><<<ntiles, 256, sm, s>>>(P, T, Uin, U0, out, a, b, dt, f, dU)));
+    } else {
+        DGFV_DISPATCH(nk, (k_surface<NK, 2><<<ntiles, 256, sm, s>>>(P, T, Uin, U0, out, a, b, dt, f, dU)));
+    }
 }
 
 void launch_dt(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, double cfl_c, double cfl_v,

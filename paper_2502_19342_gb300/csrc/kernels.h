@@ -21,7 +21,8 @@ void launch_dg_volume_split(int nk, const Params& P, const Tiles& T, int ntiles,
                             cudaStream_t s);
 void launch_dg_volume(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
                       cudaStream_t s, int variant = 0);
-void launch_face_flux(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s);
+void launch_mixed_faces(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, const int32_t* mface,
+                        const int64_t* mpt, int nmixed, double* Sin, double* Sout, cudaStream_t s);
 void launch_face_flux_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s);
 void launch_surface(int nk, const Params& P, const Tiles& T, int ntiles, const double* Uin, const double* U0,
                     double* out, int mode, double a, double b, const double* dt, bool fuse, double* dU,

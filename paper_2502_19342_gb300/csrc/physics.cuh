@@ -158,6 +158,34 @@ DGFV_HD void flux_visc(const DevPhys& P, const Prim<NK>& s, const PrimGrad<NK>& 
     F[NK + 3] = -tv - s.lam * G.T[d] + s.T * qd;
 }
 
+// F += F^v_d: the viscous flux of flux_visc added into F with fused
+// multiply-adds (the volume kernel's nodal flux F^c + F^v).
+template <int NK>
+DGFV_HD void flux_visc_add(const DevPhys& P, const Prim<NK>& s, const PrimGrad<NK>& G, int d, double* F) {
+    const double divv = G.v[0][0] + G.v[1][1] + G.v[2][2];
+    double tau[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) tau[i] = s.mu * (G.v[d][i] + G.v[i][d]);
+    tau[d] -= s.mu * (2.0 / 3.0) * divv;
+    double corr = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) corr = fma(P.D[k], G.Y[k][d], corr);
+    double qd = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const double J = s.rho * fma(s.Y[k], corr, -P.D[k] * G.Y[k][d]);
+        F[k] += J;
+        qd = fma(P.cp[k], J, qd);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[NK + i] -= tau[i];
+    double e = fma(s.T, qd, F[NK + 3]);
+    e = fma(-s.lam, G.T[d], e);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) e = fma(-tau[i], s.v[i], e);
+    F[NK + 3] = e;
+}
+
 // Local Lax-Friedrichs flux in +x_d: (F_L + F_R)/2 - s_max (u_R - u_L)/2.
 template <int NK>
 DGFV_HD void riemann_llf(const double* uL, const Prim<NK>& sL, const double* uR,
