@@ -38,8 +38,8 @@ STAGES_PER_STEP = 3
 SMS, DFMA_PER_CLK, SM_MHZ_MAX = 152, 2, 2070.0
 # DRAM bytes per DG DOF of one k_dg_volume launch, from an ncu capture of the
 # turbulence workload at 28^3 elements (dram__bytes_read.sum + write.sum =
-# 0.398 + 0.815 GB for 3.45e6 DG DOFs).
-VOLUME_DRAM_BYTES_PER_DG_DOF = 351.5
+# 0.373 + 0.703 GB for 3.13e6 DG DOFs).
+VOLUME_DRAM_BYTES_PER_DG_DOF = 344.0
 FP64_PEAK_TFLOPS = SMS * DFMA_PER_CLK * 2 * SM_MHZ_MAX * 1e6 / 1e12
 KERNEL_STEP = {"prolong": 1, "fv": 2, "face_lift": 3, "dg_volume": 4, "face_flux": 5, "surface": 6}
 
@@ -579,7 +579,7 @@ def main():
         roof = {"bound": "alu", "kernel": main_k, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_dg_volume on the 28^3 "
-                                  "case, 351.5 B per DG DOF, times the DG DOFs of one launch here",
+                                  "case, 344 B per DG DOF, times the DG DOFs of one launch here",
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 1.26 TFLOP/s)",
                 "dfma_probe_tflops": probe, "dmma_probe_tflops": probe_mma,
                 "flops_per_dof": {"total": per_dof, main_k: per_step[KERNEL_STEP[main_k]]},
