@@ -228,15 +228,14 @@ __global__ void __launch_bounds__(64) k_adj_face_mixed(Params P, AdjBuffers A, F
     }
 }
 
-// Volume adjoint in two kernels around the face adjoint.
-// k_adj_vol_a: per tile of DG elements (shared memory 6V n^3 doubles per element):
+// Volume adjoint in three kernels around the face adjoint.
+// k_adj_vol_a: per tile of DG elements (shared memory 3V n^3 doubles per element):
 //   g (lifted gradient) recomputed from U and U*, its face traces written for
-//   the face adjoint; F_bar_d = -rh_d Dhat^T R_bar (volume integral^T);
-//   nodal-flux reverse -> U_bar (direct part) and g_bar (to global scratch).
+//   the face adjoint; g and F_bar_d = -rh_d Dhat^T R_bar (volume integral^T)
+//   written per node (6V values) for k_adj_point.
 template <int NK>
 __global__ void __launch_bounds__(256) k_adj_vol_a(Params P, Tiles T, const double* __restrict__ U,
-                                                   const double* __restrict__ Rb, double* __restrict__ Ub,
-                                                   double* __restrict__ gvol) {
+                                                   const double* __restrict__ Rb, double* __restrict__ gf) {
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
     const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
@@ -244,7 +243,6 @@ __global__ void __launch_bounds__(256) k_adj_vol_a(Params P, Tiles T, const doub
     double* sD = sm;
     double* sl = sD + n * n;               // lm, lp, lhm, lhp
     double* sG = sl + 4 * n;               // count * 3V n^3: g
-    double* sF = sG + count * 3 * V * n3;  // count * 3V n^3: F_bar
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) sD[i] = B(P, P.bi.dhat[n])[i];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         sl[i] = B(P, P.bi.lm[n])[i];
@@ -263,10 +261,11 @@ __global__ void __launch_bounds__(256) k_adj_vol_a(Params P, Tiles T, const doub
         const int a = d == 0 ? j : i, b = d == 2 ? j : k;
         const int p = a + n * b;
         const double rh = P.t.rh[3 * e + d];
+        double* out = gf + 6 * P.t.off[e];  // [g (3V x n3) | F_bar (3V x n3)] per element
         const double* rsrc = Rb + P.t.off[e] + (int64_t)v * n3;
         double fb = 0.0;
         for (int q = 0; q < n; ++q) fb = fma(sD[q * n + m0], rsrc[node_index(n, d, q, a, b)], fb);
-        sF[el * per + r] = -rh * fb;
+        out[per + r] = -rh * fb;
         if (visc) {
             const double* src = U + P.t.off[e] + (int64_t)v * n3;
             const int64_t fo = P.t.fo[e];
@@ -275,39 +274,54 @@ __global__ void __launch_bounds__(256) k_adj_vol_a(Params P, Tiles T, const doub
             s = fma(sl[3 * n + m0], P.b.flift[(fo + (int64_t)(2 * d + 1) * n2) * V + v * n2 + p], s);
             s = fma(-sl[2 * n + m0], P.b.flift[(fo + (int64_t)(2 * d) * n2) * V + v * n2 + p], s);
             sG[el * per + r] = rh * s;
+            out[r] = rh * s;
         }
     }
+    if (!visc) return;
     __syncthreads();
-    if (visc) {  // gradient traces for the face adjoint
-        const int pt = 6 * 3 * V * n2;
-        for (int idx = threadIdx.x; idx < count * pt; idx += blockDim.x) {
-            const int el = idx / pt, r = idx % pt, f = r / (3 * V * n2), r2 = r % (3 * V * n2), x = r2 / n2, p = r2 % n2;
-            const int e = T.items[first + el];
-            const int d = f >> 1, a = p % n, b = p / n;
-            const double* lb = sl + ((f & 1) ? n : 0);
-            const double* src = sG + el * per + x * n3;
-            double s = 0.0;
-            for (int m = 0; m < n; ++m) s = fma(lb[m], src[node_index(n, d, m, a, b)], s);
-            P.b.fg[(P.t.fo[e] + (int64_t)f * n2) * 3 * V + x * n2 + p] = s;
-        }
+    // gradient traces for the face adjoint
+    const int pt = 6 * 3 * V * n2;
+    for (int idx = threadIdx.x; idx < count * pt; idx += blockDim.x) {
+        const int el = idx / pt, r = idx % pt, f = r / (3 * V * n2), r2 = r % (3 * V * n2), x = r2 / n2, p = r2 % n2;
+        const int e = T.items[first + el];
+        const int d = f >> 1, a = p % n, b = p / n;
+        const double* lb = sl + ((f & 1) ? n : 0);
+        const double* src = sG + el * per + x * n3;
+        double s = 0.0;
+        for (int m = 0; m < n; ++m) s = fma(lb[m], src[node_index(n, d, m, a, b)], s);
+        P.b.fg[(P.t.fo[e] + (int64_t)f * n2) * 3 * V + x * n2 + p] = s;
     }
+}
+
+// k_adj_point: nodal-flux reverse, one thread per DG node (no shared memory, no
+// barriers): U_bar (direct part) and g_bar (to gvol) from u, g and F_bar.
+template <int NK>
+__global__ void __launch_bounds__(128) k_adj_point(Params P, Tiles T, const double* __restrict__ U,
+                                                   const double* __restrict__ gf, double* __restrict__ Ub,
+                                                   double* __restrict__ gvol) {
+    constexpr int V = NK + 4;
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
+    const int n3 = n * n * n, per = 3 * V * n3;
+    const bool visc = P.ph.viscous;
     for (int idx = threadIdx.x; idx < count * n3; idx += blockDim.x) {
         const int el = idx / n3, c = idx % n3;
         const int e = T.items[first + el];
+        const int64_t off = P.t.off[e];
+        const double* in = gf + 6 * off + c;
         double u[V], g[3 * V], Fb[3 * V], ub[V] = {}, gb[3 * V] = {};
 #pragma unroll
-        for (int v = 0; v < V; ++v) u[v] = U[P.t.off[e] + (int64_t)v * n3 + c];
+        for (int v = 0; v < V; ++v) u[v] = U[off + (int64_t)v * n3 + c];
 #pragma unroll
         for (int x = 0; x < 3 * V; ++x) {
-            Fb[x] = sF[el * per + x * n3 + c];
-            g[x] = visc ? sG[el * per + x * n3 + c] : 0.0;
+            Fb[x] = in[(per + x * n3)];
+            g[x] = visc ? in[x * n3] : 0.0;
         }
         volume_point_rev<NK>(P.ph, u, g, Fb, ub, gb);
 #pragma unroll
-        for (int v = 0; v < V; ++v) Ub[P.t.off[e] + (int64_t)v * n3 + c] = ub[v];
+        for (int v = 0; v < V; ++v) Ub[off + (int64_t)v * n3 + c] = ub[v];
         if (visc)
 #pragma unroll
-            for (int x = 0; x < 3 * V; ++x) gvol[3 * P.t.off[e] + (int64_t)x * n3 + c] = gb[x];
+            for (int x = 0; x < 3 * V; ++x) gvol[3 * off + (int64_t)x * n3 + c] = gb[x];
     }
 }
 
@@ -469,14 +483,15 @@ void launch_adj_faces(int nk, const Params& P, const AdjBuffers& A, const Faces&
 
 size_t adj_volume_smem_bytes(int nk, int n, int count) {
     const int V = nk + 4;
-    return sizeof(double) * (size_t)(n * n + 4 * n + 2 * count * 3 * V * n * n * n);
+    return sizeof(double) * (size_t)(n * n + 4 * n + count * 3 * V * n * n * n);
 }
 
 void launch_adj_vol_a(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
-                      const double* Rb, double* Ub, double* gvol, cudaStream_t s) {
+                      const double* Rb, double* Ub, double* gvol, double* gf, cudaStream_t s) {
     if (ntiles <= 0) return;
     DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_adj_vol_a<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                       k_adj_vol_a<NK><<<ntiles, 256, smem, s>>>(P, T, U, Rb, Ub, gvol)));
+                       k_adj_vol_a<NK><<<ntiles, 256, smem, s>>>(P, T, U, Rb, gf),
+                       k_adj_point<NK><<<ntiles, 128, 0, s>>>(P, T, U, gf, Ub, gvol)));
 }
 
 void launch_adj_vol_b(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, size_t smem,

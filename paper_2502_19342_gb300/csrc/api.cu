@@ -130,6 +130,7 @@ struct dgfv_ctx {
     double *d_fbar = nullptr, *d_ubar = nullptr, *d_gbar = nullptr, *d_sbar = nullptr;
     double *d_S1 = nullptr, *d_S2 = nullptr, *d_B1 = nullptr, *d_B2 = nullptr, *d_W = nullptr;
     double* d_gvol = nullptr;  // nodal gradient adjoint, 3 x state
+    double* d_gf = nullptr;    // lifted gradient and volume-flux adjoint per node, 6 x state
     size_t adj_smem = 0;
     std::vector<void*> allocs;
 };
@@ -854,6 +855,7 @@ static int adj_prepare(dgfv_ctx* c) {
     TRY(dalloc(c, &c->d_B2, c->cap_state));
     TRY(dalloc(c, &c->d_W, c->cap_state));
     TRY(dalloc(c, &c->d_gvol, 3 * c->cap_state));
+    TRY(dalloc(c, &c->d_gf, 6 * c->cap_state));
     c->adj_ready = true;
     return DGFV_OK;
 }
@@ -868,7 +870,7 @@ static void enqueue_vjp(dgfv_ctx* c, const double* U, const double* Rb, double* 
     if (c->ph.viscous) launch_face_lift(c->nk, P, F, c->lift.d, c->lift.count, s);
     launch_adj_surface(c->nk, P, A, c->dg.view(), c->dg.ntiles, Rb, s);
     // recomputed gradient (and its traces), volume integral^T, nodal reverse
-    launch_adj_vol_a(c->nk, P, c->dg.view(), c->dg.ntiles, c->adj_smem, U, Rb, Ub, c->d_gvol, s);
+    launch_adj_vol_a(c->nk, P, c->dg.view(), c->dg.ntiles, c->adj_smem, U, Rb, Ub, c->d_gvol, c->d_gf, s);
     launch_adj_faces(c->nk, P, A, F, c->conf.view(), c->conf.ntiles, c->flux.d, c->flux.count, s);
     if (c->ph.viscous) {
         launch_adj_vol_b(c->nk, P, A, c->dg.view(), c->dg.ntiles, c->dg.smem, c->d_gvol, Ub, s);

@@ -411,3 +411,22 @@ def test_pp_limiter_in_the_stages_matches_oracle(oracle):
     np.testing.assert_allclose(dts, dto, rtol=1e-10)
     assert_fields_close(prob, ctx.get_state().cpu().numpy(), Uo, rtol=bound, what=f"U({steps} limited steps)")
     ctx.close()
+
+
+@pytest.mark.parametrize("riemann", [0, 1, 2])
+def test_all_fv_mesh_and_uniform_max_degree(oracle, riemann):
+    """Degenerate patterns: every element FV (no DG work at all: empty volume,
+    lifting and mixed-face launches) and every element at the maximum degree
+    N = 7 (no FV, no mixed faces); R and two RK steps."""
+    sp = W.species_set([W.AIR, W.HELIUM, W.CO2], mu=1e-3)
+    for N, fv in ((3, 1), (7, 0)):
+        prob = W.make_problem([((3, 3, 2), (0, 0, 0), (1, 1, 0.7))], sp, n_fv=8, N=N, fv=fv, riemann=riemann)
+        U = W.smooth_random_state(prob, 40 + N, amp=0.1)
+        assert_rhs_close(oracle, prob, U, gpu_rhs(prob, U))
+        ctx = ctx_for(prob, N_min=1, N_max=7)
+        ctx.set_state(to_dev(U))
+        for _ in range(2):
+            ctx.rk_step(1e-4)
+        Uo, _ = oracle.rk3(prob, U, 2, dt_fixed=1e-4)
+        assert_fields_close(prob, ctx.get_state().cpu().numpy(), Uo, what=f"U(N={N}, fv={fv})")
+        ctx.close()
