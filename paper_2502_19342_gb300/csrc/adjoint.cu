@@ -233,12 +233,13 @@ __global__ void __launch_bounds__(64) k_adj_face_mixed(Params P, AdjBuffers A, F
 //   g (lifted gradient) recomputed from U and U*, its face traces written for
 //   the face adjoint; g and F_bar_d = -rh_d Dhat^T R_bar (volume integral^T)
 //   written per node (6V values) for k_adj_point.
-template <int NK>
-__global__ void __launch_bounds__(256) k_adj_vol_a(Params P, Tiles T, const double* __restrict__ U,
-                                                   const double* __restrict__ Rb, double* __restrict__ gf) {
+template <int NK, int NP>
+__device__ __forceinline__ void adj_vol_a_body(const Params& P, const Tiles& T, const double* __restrict__ U,
+                                               const double* __restrict__ Rb, double* __restrict__ gf) {
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
-    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x];
+    const int n = NP > 0 ? NP : T.n[blockIdx.x];
     const int n2 = n * n, n3 = n2 * n;
     double* sD = sm;
     double* sl = sD + n * n;               // lm, lp, lhm, lhp
@@ -293,6 +294,20 @@ __global__ void __launch_bounds__(256) k_adj_vol_a(Params P, Tiles T, const doub
     }
 }
 
+template <int NK>
+__global__ void __launch_bounds__(256) k_adj_vol_a(Params P, Tiles T, const double* __restrict__ U,
+                                                   const double* __restrict__ Rb, double* __restrict__ gf) {
+    switch (T.n[blockIdx.x]) {  // the tile's point count as a compile-time constant
+        case 2: adj_vol_a_body<NK, 2>(P, T, U, Rb, gf); break;
+        case 3: adj_vol_a_body<NK, 3>(P, T, U, Rb, gf); break;
+        case 4: adj_vol_a_body<NK, 4>(P, T, U, Rb, gf); break;
+        case 5: adj_vol_a_body<NK, 5>(P, T, U, Rb, gf); break;
+        case 6: adj_vol_a_body<NK, 6>(P, T, U, Rb, gf); break;
+        case 7: adj_vol_a_body<NK, 7>(P, T, U, Rb, gf); break;
+        default: adj_vol_a_body<NK, 8>(P, T, U, Rb, gf); break;
+    }
+}
+
 // k_adj_point: nodal-flux reverse, one thread per DG node (no shared memory, no
 // barriers): U_bar (direct part) and g_bar (to gvol) from u, g and F_bar.
 template <int NK>
@@ -327,12 +342,13 @@ __global__ void __launch_bounds__(128) k_adj_point(Params P, Tiles T, const doub
 
 // k_adj_vol_b (viscous only): g_bar += trace^T of the face gradient adjoints;
 // lifting^T: U_bar += rh_d Dhat^T g_bar^d and U*_bar = +-rh_d lhat^{+-}^T g_bar^d.
-template <int NK>
-__global__ void __launch_bounds__(256) k_adj_vol_b(Params P, AdjBuffers A, Tiles T, const double* __restrict__ gvol,
-                                                   double* __restrict__ Ub) {
+template <int NK, int NP>
+__device__ __forceinline__ void adj_vol_b_body(const Params& P, const AdjBuffers& A, const Tiles& T,
+                                               const double* __restrict__ gvol, double* __restrict__ Ub) {
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
-    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x];
+    const int n = NP > 0 ? NP : T.n[blockIdx.x];
     const int n2 = n * n, n3 = n2 * n;
     double* sD = sm;
     double* sl = sD + n * n;
@@ -389,6 +405,20 @@ __global__ void __launch_bounds__(256) k_adj_vol_b(Params P, AdjBuffers A, Tiles
         double s = 0.0;
         for (int i = 0; i < n; ++i) s = fma(lh[i], gsrc[node_index(n, d, i, a, b)], s);
         A.sbar[(P.t.fo[e] + (int64_t)f * n2) * V + v * n2 + p] = ((f & 1) ? 1.0 : -1.0) * P.t.rh[3 * e + d] * s;
+    }
+}
+
+template <int NK>
+__global__ void __launch_bounds__(256) k_adj_vol_b(Params P, AdjBuffers A, Tiles T, const double* __restrict__ gvol,
+                                                   double* __restrict__ Ub) {
+    switch (T.n[blockIdx.x]) {  // the tile's point count as a compile-time constant
+        case 2: adj_vol_b_body<NK, 2>(P, A, T, gvol, Ub); break;
+        case 3: adj_vol_b_body<NK, 3>(P, A, T, gvol, Ub); break;
+        case 4: adj_vol_b_body<NK, 4>(P, A, T, gvol, Ub); break;
+        case 5: adj_vol_b_body<NK, 5>(P, A, T, gvol, Ub); break;
+        case 6: adj_vol_b_body<NK, 6>(P, A, T, gvol, Ub); break;
+        case 7: adj_vol_b_body<NK, 7>(P, A, T, gvol, Ub); break;
+        default: adj_vol_b_body<NK, 8>(P, A, T, gvol, Ub); break;
     }
 }
 

@@ -39,10 +39,11 @@ namespace dgfv {
 // (sU: count x V x n^3): u(+-1) = sum_m l_m(+-1) u_m along the face normal for DG
 // elements, the boundary sub-cell mean for FV elements.  One thread per face
 // point, all variables.
-template <int NK>
-__device__ __forceinline__ void tile_face_values(const Params& P, const Tiles& T, int first, int count, int n,
+template <int NK, int NP = 0>
+__device__ __forceinline__ void tile_face_values(const Params& P, const Tiles& T, int first, int count, int n_rt,
                                                  const double* sU, const double* sl) {
     constexpr int V = NK + 4;
+    const int n = NP > 0 ? NP : n_rt;
     const int n2 = n * n, n3 = n2 * n, per = 6 * n2;
     for (int i = threadIdx.x; i < count * per; i += blockDim.x) {
         const int el = i / per, r = i - el * per, f = r / n2, p = r - f * n2;
@@ -94,11 +95,11 @@ __global__ void __launch_bounds__(256) k_prolong(Params P, Tiles T, const double
 //   DG neighbour -> its solution mapped to sub-cell means by V^{DG->FV}, boundary layer.
 //   minmod reconstruction of (rho_k, v, p), conservative central-difference
 //   gradients, interior sub-cell fluxes -> rtmp; element-face states -> frec, fg.
-template <int NK>
-__global__ void __launch_bounds__(256) k_fv(Params P, Tiles T, const double* __restrict__ U) {
+template <int NK, int NF>
+__device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const double* __restrict__ U) {
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
-    const int n = P.nfv, n2 = n * n, n3 = n2 * n;
+    const int n = NF > 0 ? NF : P.nfv, n2 = n * n, n3 = n2 * n;
     const int e = T.items[T.first[blockIdx.x]];
     double* sU = sm;                 // V*n3 conservative means
     double* sW = sU + V * n3;        // V*n3 reconstruction variables
@@ -257,6 +258,16 @@ __global__ void __launch_bounds__(256) k_fv(Params P, Tiles T, const double* __r
     }
 }
 
+
+// NF: the sub-cell count as a compile-time constant for the common N_FV = 8.
+template <int NK>
+__global__ void __launch_bounds__(256) k_fv(Params P, Tiles T, const double* __restrict__ U) {
+    if (P.nfv == 8)
+        fv_body<NK, 8>(P, T, U);
+    else
+        fv_body<NK, 0>(P, T, U);
+}
+
 // ---------------------------------------------------------------------------------
 // k_face_lift_conf: lifting value U* = (u- + u+)/2 on faces whose two sides are
 // DG of one degree; one thread per face point (FV/FV faces of the conforming
@@ -332,11 +343,14 @@ __global__ void __launch_bounds__(64) k_face_lift(Params P, Faces Fc, const int3
 // k_dg_volume: tiles of DG elements of one degree; the lifted gradient lives in
 // shared memory (3V n^3 doubles per element) and is overwritten in place by
 // the nodal fluxes before the volume integral.
-template <int NK, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_dg_volume(Params P, Tiles T, const double* __restrict__ U) {
+// NP > 0: the tile's point count as a compile-time constant (unrolled
+// contractions); NP = 0: read from the tile.
+template <int NK, int NP>
+__device__ __forceinline__ void dg_volume_body(const Params& P, const Tiles& T, const double* __restrict__ U) {
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
-    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x];
+    const int n = NP > 0 ? NP : T.n[blockIdx.x];
     const int n2 = n * n, n3 = n2 * n, q = n2 + 2 * n;
     double* sl = sm;                 // lm, lp (2n)
     double* sS = sl + 2 * n;         // per element and direction: (2/h_d) Dhat, (2/h_d) lhat(-1), (2/h_d) lhat(+1)
@@ -433,6 +447,19 @@ __global__ void __launch_bounds__(256, MINB) k_dg_volume(Params P, Tiles T, cons
             for (int m = 0; m < n; ++m) acc = fma(Sd[m], src[node_index(n, d, m, a, b)], acc);
         }
         P.b.rtmp[P.t.off[e] + r] = acc;
+    }
+}
+
+template <int NK, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_dg_volume(Params P, Tiles T, const double* __restrict__ U) {
+    switch (T.n[blockIdx.x]) {
+        case 2: dg_volume_body<NK, 2>(P, T, U); break;
+        case 3: dg_volume_body<NK, 3>(P, T, U); break;
+        case 4: dg_volume_body<NK, 4>(P, T, U); break;
+        case 5: dg_volume_body<NK, 5>(P, T, U); break;
+        case 6: dg_volume_body<NK, 6>(P, T, U); break;
+        case 7: dg_volume_body<NK, 7>(P, T, U); break;
+        default: dg_volume_body<NK, 8>(P, T, U); break;
     }
 }
 
@@ -748,16 +775,17 @@ __global__ void __launch_bounds__(128) k_mixed_out(Params P, Faces Fc, const int
 // One thread per node, all variables.  With fuse != 0 (mode 1) the new state
 // is also kept in shared memory and its face values are written for the next
 // evaluation (the face-value pass of that evaluation is then skipped).
-template <int NK, int MODE>
-__global__ void __launch_bounds__(256) k_surface(Params P, Tiles T, const double* Uin, const double* U0,
-                                                 double* out, double a, double b,
-                                                 const double* __restrict__ dtp, int fuse, double* dU) {
+template <int NK, int MODE, int NP>
+__device__ __forceinline__ void surface_body(const Params& P, const Tiles& T, const double* Uin, const double* U0,
+                                             double* out, double a, double b, const double* __restrict__ dtp,
+                                             int fuse, double* dU) {
     constexpr int mode = MODE;
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
     double* sl = sm;             // lm, lp, lhm, lhp
     double* sU = sm + 4 * MAXP;  // count * V n^3 (fuse)
-    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x];
+    const int n = NP > 0 ? NP : T.n[blockIdx.x];
     const int n2 = n * n, n3 = n2 * n;
     if (threadIdx.x < n) {
         sl[threadIdx.x] = B(P, P.bi.lm[n])[threadIdx.x];
@@ -821,7 +849,23 @@ __global__ void __launch_bounds__(256) k_surface(Params P, Tiles T, const double
     }
     if (fuse) {
         __syncthreads();
-        tile_face_values<NK>(P, T, first, count, n, sU, sl);
+        tile_face_values<NK, NP>(P, T, first, count, n, sU, sl);
+    }
+}
+
+// NP: the tile's point count as a compile-time constant.
+template <int NK, int MODE>
+__global__ void __launch_bounds__(256) k_surface(Params P, Tiles T, const double* Uin, const double* U0,
+                                                 double* out, double a, double b,
+                                                 const double* __restrict__ dtp, int fuse, double* dU) {
+    switch (T.n[blockIdx.x]) {
+        case 2: surface_body<NK, MODE, 2>(P, T, Uin, U0, out, a, b, dtp, fuse, dU); break;
+        case 3: surface_body<NK, MODE, 3>(P, T, Uin, U0, out, a, b, dtp, fuse, dU); break;
+        case 4: surface_body<NK, MODE, 4>(P, T, Uin, U0, out, a, b, dtp, fuse, dU); break;
+        case 5: surface_body<NK, MODE, 5>(P, T, Uin, U0, out, a, b, dtp, fuse, dU); break;
+        case 6: surface_body<NK, MODE, 6>(P, T, Uin, U0, out, a, b, dtp, fuse, dU); break;
+        case 7: surface_body<NK, MODE, 7>(P, T, Uin, U0, out, a, b, dtp, fuse, dU); break;
+        default: surface_body<NK, MODE, 8>(P, T, Uin, U0, out, a, b, dtp, fuse, dU); break;
     }
 }
 
