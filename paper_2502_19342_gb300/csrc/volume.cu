@@ -154,7 +154,7 @@ __device__ __forceinline__ void dg_volume_split_body(const Params& P, const Tile
     double* sS = sD + n * n;    // n*n split matrix
     double* sl = sS + n * n;    // lm, lp, lhm, lhp (4n)
     double* sK = sl + 4 * n;    // count * NT * n3 two-point flux tuples
-    double* sG = sK + count * NT * n3;  // count * 3V * n3 (viscous only)
+    double* sG = sK + count * NT * n3;  // count * 3V * n3: g, then F^v, then the per-direction partial sums
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
         sD[i] = B(P, P.bi.dhat[n])[i];
         sS[i] = B(P, P.bi.dsplit[n])[i];
@@ -229,47 +229,75 @@ __device__ __forceinline__ void dg_volume_split_body(const Params& P, const Tile
         }
     }
     __syncthreads();
-    // volume term per node, all variables
-    for (int idx = threadIdx.x; idx < count * n3; idx += blockDim.x) {
-        const int el = idx / n3, c = idx % n3;
+    // volume term, one thread per line (element, direction d, line (a, b)):
+    // every two-point flux of a pair of the line's nodes once, F#(u_i, u_m) =
+    // F#(u_m, u_i), added to both nodes with S_im and S_mi; the viscous part
+    // sum_m Dhat_im F^v_d(m) first.  The line's partial sums (times 2/h_d) are
+    // written over its F^v_d values (only this thread reads them).
+    constexpr int NL = NP > 0 ? NP : MAXP;
+    const int lines = 3 * n2;
+    for (int idx = threadIdx.x; idx < count * lines; idx += blockDim.x) {
+        const int el = idx / lines, r = idx % lines, d = r / n2, p = r % n2, a = p % n, b = p / n;
         const int e = T.items[first + el];
-        const int ijk[3] = {c % n, (c / n) % n, c / n2};
         const double* K = sK + el * NT * n3;
-        double ti[NT];
+        double* Fv = sG + el * 3 * V * n3 + d * V * n3;
+        double acc[NL][V];
 #pragma unroll
-        for (int q = 0; q < NT; ++q) ti[q] = K[q * n3 + c];
-        double acc[V];
+        for (int i = 0; i < NL; ++i)
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = 0.0;
+            for (int v = 0; v < V; ++v) acc[i][v] = 0.0;
+        if (visc) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const int m0 = ijk[d];
-            const int a = d == 0 ? ijk[1] : ijk[0], b = d == 2 ? ijk[1] : ijk[2];
-            double sd[V];
+            for (int i = 0; i < NL; ++i)
 #pragma unroll
-            for (int v = 0; v < V; ++v) sd[v] = 0.0;
-            for (int m = 0; m < n; ++m) {
+                for (int m = 0; m < NL; ++m) {
+                    const double Dim = sD[i * n + m];
+                    const int cm = node_index(n, d, m, a, b);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[i][v] = fma(Dim, Fv[v * n3 + cm], acc[i][v]);
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < NL; ++i) {
+            const int ci = node_index(n, d, i, a, b);
+            double ti[NT], F[V];
+#pragma unroll
+            for (int q = 0; q < NT; ++q) ti[q] = K[q * n3 + ci];
+            kep_flux<NK>(ti, ti, d, F);  // = F^c(u_i)
+            const double Sii = sS[i * n + i];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[i][v] = fma(Sii, F[v], acc[i][v]);
+#pragma unroll
+            for (int m = i + 1; m < NL; ++m) {
                 const int cm = node_index(n, d, m, a, b);
-                double tm[NT], F[V];
+                double tm[NT];
 #pragma unroll
                 for (int q = 0; q < NT; ++q) tm[q] = K[q * n3 + cm];
                 kep_flux<NK>(ti, tm, d, F);
-                const double Sim = sS[m0 * n + m];
+                const double Sim = sS[i * n + m], Smi = sS[m * n + i];
 #pragma unroll
-                for (int v = 0; v < V; ++v) sd[v] = fma(Sim, F[v], sd[v]);
-                if (visc) {
-                    const double* Fv = sG + el * 3 * V * n3 + d * V * n3 + cm;
-                    const double Dim = sD[m0 * n + m];
-#pragma unroll
-                    for (int v = 0; v < V; ++v) sd[v] = fma(Dim, Fv[v * n3], sd[v]);
+                for (int v = 0; v < V; ++v) {
+                    acc[i][v] = fma(Sim, F[v], acc[i][v]);
+                    acc[m][v] = fma(Smi, F[v], acc[m][v]);
                 }
             }
-            const double rh = P.t.rh[3 * e + d];
-#pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] = fma(rh, sd[v], acc[v]);
         }
+        const double rh = P.t.rh[3 * e + d];
 #pragma unroll
-        for (int v = 0; v < V; ++v) P.b.rtmp[P.t.off[e] + (int64_t)v * n3 + c] = acc[v];
+        for (int i = 0; i < NL; ++i) {
+            const int ci = node_index(n, d, i, a, b);
+#pragma unroll
+            for (int v = 0; v < V; ++v) Fv[v * n3 + ci] = rh * acc[i][v];
+        }
+    }
+    __syncthreads();
+    // sum of the three directions
+    const int per = V * n3;
+    for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
+        const int el = idx / per, r = idx % per;
+        const int e = T.items[first + el];
+        const double* G = sG + el * 3 * V * n3 + r;
+        P.b.rtmp[P.t.off[e] + r] = G[0] + G[V * n3] + G[2 * V * n3];
     }
 }
 
@@ -317,8 +345,9 @@ void launch_dg_volume(int nk, const Params& P, const Tiles& T, int ntiles, size_
 }
 
 size_t volume_split_smem_bytes(int nk, int n, int count, bool viscous) {
+    (void)viscous;  // the per-direction partial sums need the 3V n^3 block either way
     const int V = nk + 4, NT = 6 + nk;
-    return sizeof(double) * (size_t)(2 * n * n + 4 * n + count * (NT + (viscous ? 3 * V : 0)) * n * n * n);
+    return sizeof(double) * (size_t)(2 * n * n + 4 * n + count * (NT + 3 * V) * n * n * n);
 }
 
 void launch_dg_volume_split(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
