@@ -467,7 +467,7 @@ def tgv(nel=32, N0=3, Ma=1.25, Re=1600.0, n_fv=8, nodes=0, riemann=0, fv=None):
     p = p_0 + rho_0/16 (cos 2x + cos 2y)(2 + cos 2z), rho = p / (R T_0).
     Elements start at degree N0 (a scalar or one per element) and FV flags fv;
     p-refinement on the pressure indicator, FV on the density indicator.  The
-    paper's N_FV = 9 is above this build's sub-cell limit of 8 per direction:
+    paper's N_FV = 9 is above the library's limit of 8 sub-cells per direction:
     N_FV = 8."""
     rho0 = 1.0
     p0 = rho0 / (1.4 * Ma * Ma)
