@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-split", action="store_true", help="skip the split-form (LGL) measurement")
     p.add_argument("--no-tgv", action="store_true", help="skip the Taylor-Green vortex measurement")
+    p.add_argument("--no-shock", action="store_true", help="skip the hp-mixed shock measurement")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the default volume-kernel launch instead of timing variants first")
     p.add_argument("--profile-timed", action="store_true",
@@ -371,6 +372,47 @@ def tgv_run(nel=32, warmup=2, steps=2):
             "degree_histogram": np.bincount(N_now[fv_now == 0], minlength=5).tolist()}
 
 
+def hp_shock_run(warmup=2, cycles=4):
+    """The hp-mixed shock case: 16^3 elements on [0,2]x[0,1]^2, N in 2..6 with FV
+    sub-cells (N_FV = 7) chosen by the indicator every 5 SSP-RK3 steps, a Mach
+    1.5 shock into a heavy-gas bubble, 2 species.  DOF-stage/s over `cycles`
+    cycles of (adaptation + 5 steps), CUDA events."""
+    import torch
+    from paper_2502_19342_gb300 import dgfv, workloads as W
+    prob, U = W.hp_shock(0, y_bg=0.01)
+    ctx = dgfv.Context(prob, N_min=2, N_max=6, opts=dict(cfl_c=0.5, cfl_v=0.5, thresholds=W.THRESHOLDS))
+    ctx.set_state(torch.from_numpy(U).cuda())
+
+    def shock_cycle():
+        st = ctx.adapt()
+        ctx.rk_steps(5, -1.0, want_dt=False)
+        return st["mean_dofs"] * ctx.n_elem * 5 * STAGES_PER_STEP, st
+
+    for _ in range(warmup):
+        shock_cycle()
+    s = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    units, st = 0.0, None
+    ev0.record(s)
+    for _ in range(cycles):
+        u, st = shock_cycle()
+        units += u
+    ev1.record(s)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    N_now, fv_now = ctx.get_degrees()
+    ctx.close()
+    return {"workload": "hp-mixed shock case: 16^3 elements on [0,2]x[0,1]^2, Mach 1.5 shock into a heavy-gas "
+                        "bubble (density ratio 3.5), 1 % heavy-gas background, 2 species, N in 2..6 and FV sub-cells "
+                        "(N_FV = 7) by the "
+                        "indicator every 5 SSP-RK3 steps",
+            "value": units / (ms * 1e-3), "unit": "DOF-stage/s", "ms_per_cycle": ms / cycles,
+            "cycle": "adapt + 5 SSP-RK3 steps (15 stages), CFL 0.5",
+            "fv_elements": int(fv_now.sum()), "mean_dofs_per_element": st["mean_dofs"],
+            "degree_histogram": np.bincount(N_now[fv_now == 0], minlength=7).tolist()}
+
+
 def batched_comparison(steps=5):
     """256 independent periodic domains of 2^3..8^3 elements, one degree
     N in 1..7 per domain, 3 species: DOF-stage/s of SSP-RK3 steps (fixed dt)
@@ -592,6 +634,7 @@ def main():
         batched = None if args.no_batched else batched_comparison()
         split = None if args.no_split else split_form_run(args.nel)
         tgv = None if args.no_tgv else tgv_run()
+        shock = None if args.no_shock else hp_shock_run()
         launches = int(sum(v[1] for v in prof.values()))
         last = pattern[-1]
         line = {"metric": "DOF-stage updates/s (FP64 RHS, hp-mixed)", "value": value, "unit": "DOF-stage/s",
@@ -605,7 +648,7 @@ def main():
                            "volume_launch": ({str(k): v for k, v in tuned.items()} if tuned else "default"),
                            "l2": "inputs larger than L2 (state ~1.2 GB)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "adjoint": adjoint,
-                "batched_domains": batched, "split_form": split, "tgv": tgv,
+                "batched_domains": batched, "split_form": split, "tgv": tgv, "hp_shock": shock,
                 "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
                 "clocks": clk.summary()}
         print(json.dumps(line))

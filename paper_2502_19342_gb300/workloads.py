@@ -232,11 +232,13 @@ def _post_shock(gamma, Ms, rho1=1.0, p1=1.0):
     return rho1 * r, p1 * pr, u2
 
 
-def hp_shock(seed=0, nel=(16, 16, 16), riemann=0, mu=1e-4):
+def hp_shock(seed=0, nel=(16, 16, 16), riemann=0, mu=1e-4, y_bg=0.0):
     """[0,2]x[0,1]x[0,1], periodic, 16^3 elements, N drawn from {2..6},
     N_FV = 7; a Mach 1.5 planar shock in air at x = 0.4 moving +x towards a
     bubble (r = 0.2, centre (0.8, 0.5, 0.5)) of the heavy species (density
-    ratio 3.5), interface smoothed over 2 node spacings of degree 4."""
+    ratio 3.5), interface smoothed over 2 node spacings of degree 4.  y_bg: a
+    background mass fraction of the heavy species (with none, the species'
+    round-off far from the bubble reads as noise to the modal indicator)."""
     sp = species_set([AIR, HEAVY], mu=mu)
     n_elem = nel[0] * nel[1] * nel[2]
     N = random_degrees(n_elem, 2, 6, seed)
@@ -248,7 +250,7 @@ def hp_shock(seed=0, nel=(16, 16, 16), riemann=0, mu=1e-4):
 
     def fn(x, y, z):
         r = np.sqrt((x - 0.8) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2)
-        Yb = 0.5 * (1 - np.tanh((r - 0.2) / width))
+        Yb = y_bg + (1 - y_bg) * 0.5 * (1 - np.tanh((r - 0.2) / width))
         s = 0.5 * (1 - np.tanh((x - xs) / width))  # 1 behind the shock
         Rm = (1 - Yb) * sp["Rgas"][0] + Yb * sp["Rgas"][1]
         p = 1.0 + s * (p2 - 1.0)
