@@ -260,8 +260,11 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
 
 
 // NF: the sub-cell count as a compile-time constant for the common N_FV = 8.
+// Register budget for two CTAs per SM: where the shared memory allows two (up
+// to N_FV = 7 with 3 species) that doubles the resident warps; the spills it
+// costs go to L1.
 template <int NK>
-__global__ void __launch_bounds__(256) k_fv(Params P, Tiles T, const double* __restrict__ U) {
+__global__ void __launch_bounds__(256, 2) k_fv(Params P, Tiles T, const double* __restrict__ U) {
     if (P.nfv == 8)
         fv_body<NK, 8>(P, T, U);
     else
