@@ -105,8 +105,8 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
     double* sW = sU + V * n3;        // V*n3 reconstruction variables
     double* sNb = sW + V * n3;       // 6*V*n2 neighbour values (conservative)
     double* sNw = sNb + 6 * V * n2;  // 6*V*n2 neighbour reconstruction variables
-    double* sF = sNw + 6 * V * n2;   // V*(n-1)*n2 interior face fluxes of one direction
-    double* sT1 = sF + V * (n - 1) * n2;   // scratch V*MAXP*MAXP
+    double* sF = sNw + 6 * V * n2;   // 3V*(n-1)*n2 interior face fluxes of the three directions
+    double* sT1 = sF + 3 * V * (n - 1) * n2;   // scratch V*MAXP*MAXP
     double* sT2 = sT1 + V * MAXP * MAXP;   // scratch V*MAXP*MAXP
     const int64_t off = P.t.off[e];
     const double* rh = P.t.rh + 3 * e;
@@ -196,48 +196,47 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
         else if (d == 1) { i = a; j = m; k = b; }
         else { i = a; j = b; k = m; }
     };
-    constexpr int MAXC = (MAXP * MAXP * MAXP + 255) / 256;
-    double acc[MAXC][V];
-#pragma unroll
-    for (int q = 0; q < MAXC; ++q)
-#pragma unroll
-        for (int v = 0; v < V; ++v) acc[q][v] = 0.0;
+    // interior sub-cell faces of all three directions in one pass (better
+    // balanced over the CTA than one direction at a time), then the flux
+    // differences of every cell
     const int nif = (n - 1) * n2;
-    for (int d = 0; d < 3; ++d) {
-        for (int fidx = threadIdx.x; fidx < nif; fidx += blockDim.x) {
-            const int m = fidx % (n - 1), p = fidx / (n - 1), a = p % n, b = p / n;
-            double uL[V], uR[V], gL[3 * V], gR[3 * V], F[V];
-            recon(d, m, a, b, +1, uL);
-            recon(d, m + 1, a, b, -1, uR);
-            int i, j, k;
-            coords(d, m, a, b, i, j, k);
-            if (P.ph.viscous) grad(i, j, k, gL);
-            coords(d, m + 1, a, b, i, j, k);
-            if (P.ph.viscous) grad(i, j, k, gR);
-            interface_flux<NK>(P.ph, uL, gL, uR, gR, d, F, true);
+    for (int t = threadIdx.x; t < 3 * nif; t += blockDim.x) {
+        const int d = t / nif, fidx = t - d * nif;
+        const int m = fidx % (n - 1), p = fidx / (n - 1), a = p % n, b = p / n;
+        double uL[V], uR[V], gL[3 * V], gR[3 * V], F[V];
+        recon(d, m, a, b, +1, uL);
+        recon(d, m + 1, a, b, -1, uR);
+        int i, j, k;
+        coords(d, m, a, b, i, j, k);
+        if (P.ph.viscous) grad(i, j, k, gL);
+        coords(d, m + 1, a, b, i, j, k);
+        if (P.ph.viscous) grad(i, j, k, gR);
+        interface_flux<NK>(P.ph, uL, gL, uR, gR, d, F, true);
 #pragma unroll
-            for (int v = 0; v < V; ++v) sF[v * nif + fidx] = F[v];
-        }
-        __syncthreads();
-        const double sc = 0.5 * n * rh[d];  // n/h_d
-        for (int c = threadIdx.x, q = 0; c < n3; c += blockDim.x, ++q) {
-            const int i = c % n, j = (c / n) % n, k = c / n2;
-            const int m = d == 0 ? i : (d == 1 ? j : k);
-            const int a = d == 0 ? j : i, b = d == 2 ? j : k;
-            const int p = a + n * b;
+        for (int v = 0; v < V; ++v) sF[(d * V + v) * nif + fidx] = F[v];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n3; c += blockDim.x) {
+        const int ijk[3] = {c % n, (c / n) % n, c / n2};
+        double acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int m = ijk[d];
+            const int p = (d == 0 ? ijk[1] : ijk[0]) + n * (d == 2 ? ijk[1] : ijk[2]);
+            const double sc = 0.5 * n * rh[d];  // n/h_d
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 double t = 0.0;
-                if (m < n - 1) t += sF[v * nif + m + (n - 1) * p];
-                if (m > 0) t -= sF[v * nif + (m - 1) + (n - 1) * p];
-                acc[q][v] = fma(sc, t, acc[q][v]);
+                if (m < n - 1) t += sF[(d * V + v) * nif + m + (n - 1) * p];
+                if (m > 0) t -= sF[(d * V + v) * nif + (m - 1) + (n - 1) * p];
+                acc[v] = fma(sc, t, acc[v]);
             }
         }
-        __syncthreads();
-    }
-    for (int c = threadIdx.x, q = 0; c < n3; c += blockDim.x, ++q)
 #pragma unroll
-        for (int v = 0; v < V; ++v) P.b.rtmp[off + (int64_t)v * n3 + c] = acc[q][v];
+        for (int v = 0; v < V; ++v) P.b.rtmp[off + (int64_t)v * n3 + c] = acc[v];
+    }
     // element-face states and boundary-cell gradients
     for (int i = threadIdx.x; i < 6 * n2; i += blockDim.x) {
         const int f = i / n2, p = i % n2, a = p % n, b = p / n, d = f >> 1, s = f & 1;
@@ -1152,7 +1151,7 @@ void launch_prolong(int nk, const Params& P, const Tiles& T, int ntiles, const d
 
 size_t fv_smem_bytes(int nk, int nfv) {
     const int V = nk + 4, n2 = nfv * nfv, n3 = n2 * nfv;
-    return sizeof(double) * (size_t)(2 * V * n3 + 12 * V * n2 + V * (nfv - 1) * n2 + 2 * V * MAXP * MAXP);
+    return sizeof(double) * (size_t)(2 * V * n3 + 12 * V * n2 + 3 * V * (nfv - 1) * n2 + 2 * V * MAXP * MAXP);
 }
 
 void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s) {
