@@ -13,6 +13,8 @@ A *problem* is a plain dict:
                                    DG elements, LLF on faces touching FV data (Sec. 5.1)
     N     int8 (n_elem,)           DG degree per element
     fv    uint8 (n_elem,)          1 for FV sub-cell elements
+    chain int (optional)           1: domains glued in order along x, conforming or mortar
+                                   interfaces between them (Sec. 3.2.3)
 """
 import ctypes as C
 import os
@@ -36,7 +38,7 @@ class _Problem(C.Structure):
         ("n_species", C.c_int), ("gamma", _dp), ("Rgas", _dp), ("mu", _dp), ("Pr", _dp),
         ("Dk", _dp), ("riemann", C.c_int), ("N", _i8p), ("fv", _u8p), ("nodes", C.c_int), ("split", C.c_int),
         ("sutherland", C.c_int), ("T_ref", C.c_double), ("S_sutherland", C.c_double), ("indicator_vars", C.c_int),
-        ("pp_limiter", C.c_int), ("pp_eps", C.c_double),
+        ("pp_limiter", C.c_int), ("pp_eps", C.c_double), ("chain_x", C.c_int),
     ]
 
 
@@ -72,6 +74,7 @@ def lib():
         L.oracle_dg2fv.argtypes = [C.c_int, C.c_int, _dp, C.c_int]
         L.oracle_fv2dg.argtypes = [C.c_int, C.c_int, _dp, C.c_int]
         L.oracle_leg_vandermonde.argtypes = [C.c_int, _dp, C.c_int]
+        L.oracle_mortar.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, C.c_int]
         L.oracle_flux.argtypes = [P, _dp, _dp, C.c_int, _dp, _dp]
         L.oracle_riemann.argtypes = [P, _dp, _dp, C.c_int, _dp]
         L.oracle_primitives.argtypes = [P, _dp, _dp]
@@ -109,7 +112,8 @@ class _Bound:
             _ptr(sp[3], _dp), _ptr(sp[4], _dp), int(prob.get("riemann", 0)),
             _ptr(self.N, _i8p), _ptr(self.fv, _u8p), int(prob.get("nodes", 0)), int(prob.get("split", 0)),
             int(prob.get("sutherland", 0)), float(prob.get("T_ref", 1.0)), float(prob.get("S_sutherland", 0.0)),
-            int(prob.get("indicator_vars", 0)), int(prob.get("pp_limiter", 0)), float(prob.get("pp_eps", 1e-10)))
+            int(prob.get("indicator_vars", 0)), int(prob.get("pp_limiter", 0)), float(prob.get("pp_eps", 1e-10)),
+            int(prob.get("chain", 0)))
 
     @property
     def ref(self):
@@ -287,6 +291,16 @@ def dg2fv(N, n_fv, nodes=0):
 def fv2dg(N, n_fv, nodes=0):
     M = np.zeros((N + 1, n_fv))
     _check(lib().oracle_fv2dg(N, n_fv, _ptr(M, _dp), int(nodes)), "fv2dg")
+    return M
+
+
+def mortar(N, half, proj=False, fv=False, nodes=0):
+    """Sec. 3.2.3 mortar matrix of one direction: interpolation to the virtual small
+    side of half `half` (proj=False) or L2 projection back (proj=True); on degree-N
+    nodes, or (fv=True) on N sub-cells."""
+    n = N if fv else N + 1
+    M = np.zeros((n, n))
+    _check(lib().oracle_mortar(int(N), int(half), int(bool(proj)), int(bool(fv)), _ptr(M, _dp), int(nodes)), "mortar")
     return M
 
 

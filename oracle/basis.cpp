@@ -260,6 +260,60 @@ std::vector<double> fv2dg(int N, int n_fv, int kind) {
 
 std::vector<double> leg_vandermonde(int N, int kind) { return to_double(leg_vandermonde_ld(N, kind)); }
 
+// Sec. 3.2.3: half s of a mortar face (s = 0: xi in [-1, 0], s = 1: [0, 1] of the
+// big side's reference coordinate); the virtual small side's coordinate eta
+// maps to xi = (eta + 2s - 1)/2.
+std::vector<double> mortar_interp(int N, int s, int kind) {
+    if (s < 0 || s > 1) throw std::runtime_error("mortar half out of range");
+    const int n = N + 1;
+    std::vector<ld> x = nodes_ld(N, kind);
+    std::vector<ld> M(n * n);
+    for (int i = 0; i < n; ++i) {
+        const ld xi = (x[i] + 2 * s - 1) / 2;
+        for (int j = 0; j < n; ++j) M[i * n + j] = lagrange(x, j, xi);
+    }
+    return to_double(M);
+}
+
+std::vector<double> mortar_proj(int N, int s, int kind) {
+    // L2 projection onto degree N over [-1, 1] of f = (the small side's interpolant
+    // on half s, zero on the other half), through orthonormal Legendre modes:
+    //   c_m = int_{half s} f phi_m dxi = 1/2 int_{-1}^{1} f_s(eta) phi_m(xi(eta)) deta
+    // (Gauss quadrature with N+1 points, exact for the degree-2N integrand),
+    //   P[i][j] = sum_m phi_m(x_i) * 1/2 sum_k w_k l_j(eta_k) phi_m(xi(eta_k)).
+    if (s < 0 || s > 1) throw std::runtime_error("mortar half out of range");
+    const int n = N + 1;
+    std::vector<ld> x = nodes_ld(N, kind), q, w;
+    gauss_legendre(n, q, w);
+    std::vector<ld> P(n * n, 0);
+    for (int j = 0; j < n; ++j)
+        for (int m = 0; m < n; ++m) {
+            ld c = 0;
+            for (int k = 0; k < n; ++k) c += w[k] * lagrange(x, j, q[k]) * legendre_orthonormal(m, (q[k] + 2 * s - 1) / 2);
+            c /= 2;
+            for (int i = 0; i < n; ++i) P[i * n + j] += legendre_orthonormal(m, x[i]) * c;
+        }
+    return to_double(P);
+}
+
+std::vector<double> mortar_interp_fv(int n_fv, int s) {
+    // small sub-cell i of half s spans [(s n + i)/(2n), (s n + i + 1)/(2n)] of the big
+    // face (unit length); it lies inside big sub-cell floor((s n + i)/2)
+    if (s < 0 || s > 1 || n_fv < 1) throw std::runtime_error("bad FV mortar");
+    std::vector<double> M((size_t)n_fv * n_fv, 0.0);
+    for (int i = 0; i < n_fv; ++i) M[(size_t)i * n_fv + (s * n_fv + i) / 2] = 1.0;
+    return M;
+}
+
+std::vector<double> mortar_proj_fv(int n_fv, int s) {
+    // mean over big sub-cell j of the piecewise constant given on half s: each small
+    // sub-cell inside it covers half of it
+    if (s < 0 || s > 1 || n_fv < 1) throw std::runtime_error("bad FV mortar");
+    std::vector<double> P((size_t)n_fv * n_fv, 0.0);
+    for (int i = 0; i < n_fv; ++i) P[(size_t)((s * n_fv + i) / 2) * n_fv + i] = 0.5;
+    return P;
+}
+
 std::vector<double> leg_vandermonde_inv(int N, int kind) {
     return to_double(invert(leg_vandermonde_ld(N, kind), N + 1));
 }

@@ -11,6 +11,8 @@
 //   Sec. 3.2:   V^{N->M} (interpolation for N<M, L2 projection for N>M),
 //               V^{DG->FV} (sub-cell integration), V^{FV->DG} (pseudo-inverse).
 //   Sec. 3.4:   Legendre Vandermonde V_Leg (orthonormal Legendre modes).
+//   Sec. 3.2.3: mortar interpolation to the virtual small sides and L2
+//               projection back, DG and FV.
 #ifndef DGFV_ORACLE_BASIS_HPP
 #define DGFV_ORACLE_BASIS_HPP
 
@@ -40,6 +42,21 @@ std::vector<double> fv2dg(int N, int n_fv, int kind = 0);
 std::vector<double> leg_vandermonde(int N, int kind = 0);
 // Inverse of leg_vandermonde(N) (Gauss-Jordan elimination).
 std::vector<double> leg_vandermonde_inv(int N, int kind = 0);
+
+// Sec. 3.2.3 (non-conforming interfaces), one direction of a face halved at
+// xi = 0; s = 0 the half [-1, 0], s = 1 the half [0, 1].
+// (N+1) x (N+1): the big side's degree-N polynomial evaluated at the nodes of
+// the virtual small side (M_01, M_02: exact, a polynomial stays one on a half).
+std::vector<double> mortar_interp(int N, int s, int kind = 0);
+// (N+1) x (N+1): L2 projection onto degree N of a degree-N polynomial given on
+// half s (zero on the other half); M_10 and M_20 add up the two halves.
+std::vector<double> mortar_proj(int N, int s, int kind = 0);
+// FV sub-cells (n_fv per direction on the big side and on each virtual small
+// side): n_fv x n_fv sub-cell means of the virtual small side of the big side's
+// piecewise constant, and the big sub-cell means of a piecewise constant given on
+// half s.
+std::vector<double> mortar_interp_fv(int n_fv, int s);
+std::vector<double> mortar_proj_fv(int n_fv, int s);
 
 }  // namespace ora
 

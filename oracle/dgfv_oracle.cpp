@@ -47,8 +47,21 @@ struct Elem {
     bool fv = false;  // FV sub-cell element
     int n = 2;        // points per direction: N+1 (DG) or n_fv (FV)
     int64_t off = 0;  // offset of the element's block in the state
-    int nb[6];        // neighbour across face f (0:-x 1:+x 2:-y 3:+y 4:-z 5:+z)
+    int nb[6];        // neighbour across face f (0:-x 1:+x 2:-y 3:+y 4:-z 5:+z); -1 at a mortar
+    int mort[6];      // mortar of face f (index into Problem::mortars) or -1
+    int quad[6];      // quadrant of this element on that mortar's small side, -1 on the big side
     double h[3];      // element size
+};
+
+// Non-conforming interface (Sec. 3.2.3): one big element face against two
+// (types 1, 2: halved along one tangential direction) or four (type 3: halved
+// along both) small element faces.  Tangential directions a, b of an x-face:
+// y and z.  Quadrant q = qa + 2 qb, qa/qb = 0 the lower half, 1 the upper.
+struct Mortar {
+    int big = -1;
+    int fB = 0;                      // face of the big element (0: -x, 1: +x)
+    int split[2] = {0, 0};           // halved along a / along b
+    int small[4] = {-1, -1, -1, -1}; // small element of quadrant q
 };
 
 struct Ops {  // reference operators, built once per problem before any parallel loop
@@ -56,6 +69,10 @@ struct Ops {  // reference operators, built once per problem before any parallel
     std::map<std::pair<int, int>, vector<double>> vm;  // (from,to) -> V^{from->to}
     std::map<int, vector<double>> d2f, f2d;            // per DG degree
     std::map<int, vector<double>> vleg_inv;
+    // mortar maps per (DG degree, half): interpolation to the virtual small side, projection back
+    std::map<std::pair<int, int>, vector<double>> mi, mp;
+    vector<double> mi_fv[2], mp_fv[2];  // the same on FV sub-cells
+    std::map<int, vector<double>> eye;  // identity of each size (a direction that is not halved)
     const Basis1D& B(int N) const { return basis.at(N); }
 };
 
@@ -70,6 +87,7 @@ struct Problem {
     double pp_eps = 1e-10;
     int split = 0;  // 1: split-form volume integral with the kinetic-energy-preserving two-point flux
     vector<Elem> el;
+    vector<Mortar> mortars;
     int64_t size = 0;
     Ops ops;
 };
@@ -104,7 +122,9 @@ Problem make_problem(const oracle_problem* p, bool need_ops = true) {
     if (P.indicator_vars < 0 || P.indicator_vars > 1) throw std::runtime_error("bad indicator variables");
     if (P.nodes < 0 || P.nodes > 1 || P.split < 0 || P.split > 1 || (P.split && P.nodes != 1))
         throw std::runtime_error("bad node family / split form (split form needs LGL nodes)");
+    if (p->chain_x < 0 || p->chain_x > 1) throw std::runtime_error("bad chain flag");
     int64_t e0 = 0;
+    vector<int64_t> first(p->n_domains + 1, 0);
     for (int d = 0; d < p->n_domains; ++d) {
         const int nx = p->dims[3 * d], ny = p->dims[3 * d + 1], nz = p->dims[3 * d + 2];
         if (nx < 1 || ny < 1 || nz < 1) throw std::runtime_error("bad domain");
@@ -124,10 +144,70 @@ Problem make_problem(const oracle_problem* p, bool need_ops = true) {
                         int a = f / 2;
                         q[a] = (q[a] + (f % 2 ? 1 : -1) + dims[a]) % dims[a];
                         E.nb[f] = (int)(e0 + q[0] + nx * (q[1] + ny * q[2]));
+                        E.mort[f] = -1;
+                        E.quad[f] = -1;
                     }
                     P.el.push_back(E);
                 }
         e0 += (int64_t)nx * ny * nz;
+        first[d + 1] = e0;
+    }
+    if (p->chain_x) {
+        // glue the +x side of domain A to the -x side of domain A+1 (cyclically)
+        const int D = p->n_domains;
+        for (int A = 0; A < D; ++A)
+            for (int a = 1; a < 3; ++a)
+                if (p->lo[3 * A + a] != p->lo[a] || p->hi[3 * A + a] != p->hi[a])
+                    throw std::runtime_error("chained domains must share the y and z extents");
+        auto elem = [&](int dm, int i, int j, int k) {
+            const int* dd = p->dims + 3 * dm;
+            return (int)(first[dm] + i + dd[0] * (j + dd[1] * k));
+        };
+        for (int A = 0; A < D; ++A) {
+            const int Bd = (A + 1) % D;
+            const int* da = p->dims + 3 * A;
+            const int* db = p->dims + 3 * Bd;
+            const int ra = da[1] == db[1] ? 0 : (db[1] == 2 * da[1] ? 1 : (da[1] == 2 * db[1] ? -1 : 9));
+            const int rb = da[2] == db[2] ? 0 : (db[2] == 2 * da[2] ? 1 : (da[2] == 2 * db[2] ? -1 : 9));
+            if (ra == 9 || rb == 9 || ra * rb < 0) throw std::runtime_error("chained domains must be 1:1 or 2:1");
+            if (ra == 0 && rb == 0) {  // conforming
+                for (int k = 0; k < da[2]; ++k)
+                    for (int j = 0; j < da[1]; ++j) {
+                        const int eA = elem(A, da[0] - 1, j, k), eB = elem(Bd, 0, j, k);
+                        P.el[eA].nb[1] = eB;
+                        P.el[eB].nb[0] = eA;
+                    }
+                continue;
+            }
+            // the coarser domain holds the big sides
+            const bool bigA = ra > 0 || rb > 0;
+            const int Dbig = bigA ? A : Bd, Dsm = bigA ? Bd : A;
+            const int* dg = p->dims + 3 * Dbig;
+            const int* ds = p->dims + 3 * Dsm;
+            const int fB = bigA ? 1 : 0;
+            const int sa = ra != 0, sb = rb != 0;
+            for (int k = 0; k < dg[2]; ++k)
+                for (int j = 0; j < dg[1]; ++j) {
+                    Mortar M;
+                    M.big = elem(Dbig, bigA ? dg[0] - 1 : 0, j, k);
+                    M.fB = fB;
+                    M.split[0] = sa;
+                    M.split[1] = sb;
+                    const int m = (int)P.mortars.size();
+                    for (int qb = 0; qb <= sb; ++qb)
+                        for (int qa = 0; qa <= sa; ++qa) {
+                            const int q = qa + 2 * qb;
+                            const int es = elem(Dsm, bigA ? 0 : ds[0] - 1, sa ? 2 * j + qa : j, sb ? 2 * k + qb : k);
+                            M.small[q] = es;
+                            P.el[es].nb[fB ^ 1] = -1;
+                            P.el[es].mort[fB ^ 1] = m;
+                            P.el[es].quad[fB ^ 1] = q;
+                        }
+                    P.el[M.big].nb[fB] = -1;
+                    P.el[M.big].mort[fB] = m;
+                    P.mortars.push_back(M);
+                }
+        }
     }
     for (size_t e = 0; e < P.el.size(); ++e) {
         Elem& E = P.el[e];
@@ -151,6 +231,19 @@ Problem make_problem(const oracle_problem* p, bool need_ops = true) {
                 P.ops.f2d[N] = fv2dg(N, P.nfv, P.nodes);
             }
             for (int M : degs) P.ops.vm[{N, M}] = vmap(N, M, P.nodes);
+            for (int h = 0; h < 2; ++h) {
+                P.ops.mi[{N, h}] = mortar_interp(N, h, P.nodes);
+                P.ops.mp[{N, h}] = mortar_proj(N, h, P.nodes);
+            }
+        }
+        for (int h = 0; h < 2; ++h) {
+            P.ops.mi_fv[h] = mortar_interp_fv(P.nfv, h);
+            P.ops.mp_fv[h] = mortar_proj_fv(P.nfv, h);
+        }
+        for (int n = 1; n <= 16; ++n) {
+            vector<double> I((size_t)n * n, 0.0);
+            for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+            P.ops.eye[n] = I;
         }
         for (auto& E : P.el)
             if (E.fv && P.nfv < E.N + 1) throw std::runtime_error("n_fv < N+1 for an FV element");
@@ -190,6 +283,55 @@ vector<T> map_face(const vector<T>& in, int nvar, int nin, int nout, const vecto
                 out[(size_t)v * nout * nout + ao + nout * bo] = s;
             }
     return out;
+}
+
+// Tensor-product map with its own matrix along each face direction:
+// out[var][ao + nout*bo] = sum Ma[ao][ai] Mb[bo][bi] in[var][ai + nin*bi].
+template <class T>
+vector<T> map_face2(const vector<T>& in, int nvar, int nin, int nout, const vector<double>& Ma,
+                    const vector<double>& Mb) {
+    vector<T> out((size_t)nvar * nout * nout, T(0.0));
+    for (int v = 0; v < nvar; ++v)
+        for (int bo = 0; bo < nout; ++bo)
+            for (int ao = 0; ao < nout; ++ao) {
+                T s = T(0.0);
+                for (int bi = 0; bi < nin; ++bi)
+                    for (int ai = 0; ai < nin; ++ai)
+                        s = s + T(Ma[ao * nin + ai] * Mb[bo * nin + bi]) * in[(size_t)v * nin * nin + ai + nin * bi];
+                out[(size_t)v * nout * nout + ao + nout * bo] = s;
+            }
+    return out;
+}
+
+// Sec. 3.2.3: the maps of quadrant q of mortar M along the face directions a
+// (dir 0) and b (dir 1): interpolation from the big side to the virtual small
+// side (proj = false) or L2 projection back (proj = true), on the big side's
+// representation (degree N_big; FV sub-cells when the big element is FV or
+// fvgrid is set); the identity along a direction that is not halved.
+const vector<double>& mortar_map(const Problem& P, const Mortar& M, int q, int dir, bool proj, bool fvgrid) {
+    const Elem& B = P.el[M.big];
+    const bool fvg = fvgrid || B.fv;
+    if (!M.split[dir]) return P.ops.eye.at(fvg ? P.nfv : B.n);
+    const int h = dir == 0 ? q % 2 : q / 2;
+    if (fvg) return proj ? P.ops.mp_fv[h] : P.ops.mi_fv[h];
+    return proj ? P.ops.mp.at({B.N, h}) : P.ops.mi.at({B.N, h});
+}
+
+// A face field of the big side restricted to quadrant q (its virtual small side).
+template <class T>
+vector<T> to_virtual(const Problem& P, const Mortar& M, int q, const vector<T>& big, int nvar, bool fvgrid = false) {
+    const int n = (fvgrid || P.el[M.big].fv) ? P.nfv : P.el[M.big].n;
+    return map_face2(big, nvar, n, n, mortar_map(P, M, q, 0, false, fvgrid), mortar_map(P, M, q, 1, false, fvgrid));
+}
+
+// acc += the projection of a virtual small side's field of quadrant q onto the big side.
+template <class T>
+void add_from_virtual(const Problem& P, const Mortar& M, int q, const vector<T>& virt, int nvar, vector<T>& acc,
+                      bool fvgrid = false) {
+    const int n = (fvgrid || P.el[M.big].fv) ? P.nfv : P.el[M.big].n;
+    vector<T> t = map_face2(virt, nvar, n, n, mortar_map(P, M, q, 0, true, fvgrid), mortar_map(P, M, q, 1, true, fvgrid));
+    if (acc.empty()) acc.assign(t.size(), T(0.0));
+    for (size_t i = 0; i < t.size(); ++i) acc[i] = acc[i] + t[i];
 }
 
 // V^{N_from -> N_to} on a face field; the identity when the degrees agree.
@@ -334,6 +476,17 @@ void split_form_convective(const Problem& P, const Elem& E, const Basis1D& B, co
     }
 }
 
+// Whether FV data lies across face f of E (at a mortar: the big element, or
+// any small element).
+bool fv_across(const Problem& P, const Elem& E, int f) {
+    if (E.mort[f] < 0) return P.el[E.nb[f]].fv;
+    const Mortar& M = P.mortars[E.mort[f]];
+    if (E.quad[f] >= 0) return P.el[M.big].fv;
+    for (int q = 0; q < 4; ++q)
+        if (M.small[q] >= 0 && P.el[M.small[q]].fv) return true;
+    return false;
+}
+
 template <class T>
 T minmod(T a, T b) {
     // minmod(a,b) = 0 if a b <= 0, else the argument of smaller magnitude (a on ties)
@@ -374,7 +527,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
             // the boundary layer of sub-cell means that an FV neighbour sees:
             // V^{DG->FV} in all three directions, keeping the sub-cells next to face f
             // (counted with the FV step, which is where it is needed)
-            const bool fv_neighbour = P.el[E.nb[f]].fv;
+            const bool fv_neighbour = fv_across(P, E, f);
             if (!E.fv && fv_neighbour && !parallel) flop_counter().phase = 2;
             if (!E.fv && fv_neighbour) {
                 const vector<double>& A = P.ops.d2f.at(E.N);
@@ -407,12 +560,34 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
         // face-adjacent sub-cell mean: an FV neighbour's own, or, for a DG
         // neighbour, its solution mapped to sub-cell means by V^{DG->FV}
         // (Sec. 3.2.1: the DG side is transformed to the FV representation).
+        // The distance to the neighbour's sub-cell centre, in this element's
+        // reference coordinates, is l/2 (1 + h_nb/h), l when the sizes agree.
+        // Reading at a mortar (Sec. 3.2.3 maps the face data, the paper says
+        // nothing of the reconstruction stencil): a small side sees the big
+        // side's layer on its quadrant (M^FV_01, M^FV_02), the big side the
+        // small sides' layers projected onto its sub-cells (M^FV_10, M^FV_20).
         vector<T> nbval[6];
         double nbdist[6];
+        auto layer = [&](int q, int fq) -> const vector<T>& {
+            return P.el[q].fv ? W[q].face_u[fq] : W[q].face_layer[fq];
+        };
         for (int f = 0; f < 6; ++f) {
-            const Elem& Q = P.el[E.nb[f]];
-            nbval[f] = Q.fv ? W[E.nb[f]].face_u[f ^ 1] : W[E.nb[f]].face_layer[f ^ 1];
-            nbdist[f] = l;
+            const int d = f / 2;
+            if (E.mort[f] < 0) {
+                nbval[f] = layer(E.nb[f], f ^ 1);
+                nbdist[f] = l / 2 * (1.0 + P.el[E.nb[f]].h[d] / E.h[d]);
+                continue;
+            }
+            const Mortar& M = P.mortars[E.mort[f]];
+            if (E.quad[f] >= 0) {
+                nbval[f] = to_virtual(P, M, E.quad[f], layer(M.big, M.fB), V, true);
+                nbdist[f] = l / 2 * (1.0 + P.el[M.big].h[d] / E.h[d]);
+            } else {
+                nbval[f].clear();
+                for (int q = 0; q < 4; ++q)
+                    if (M.small[q] >= 0) add_from_virtual(P, M, q, layer(M.small[q], f ^ 1), V, nbval[f], true);
+                nbdist[f] = l / 2 * (1.0 + P.el[M.small[0]].h[d] / E.h[d]);
+            }
         }
         // primitive reconstruction variables of every sub-cell and of the neighbour values
         vector<T> w((size_t)V * n3);
@@ -522,25 +697,51 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
     for (int e = 0; e < nel; ++e) {
         const Elem& E = P.el[e];
         if (E.fv) continue;
-        for (int f = 0; f < 6; ++f) {
-            const Elem& Q = P.el[E.nb[f]];
-            const vector<T>& mine = W[e].face_u[f];
+        // U* on this side's degree N from this side's trace and the other side's
+        // data (its degree-No trace, or its FV reconstructed face state)
+        auto lift_with = [&](const vector<T>& mine, int N, bool ofv, int No, const vector<T>& other) {
             vector<T> us;
-            if (Q.fv) {
+            if (ofv) {
                 // Sec. 3.2.2: FV side mapped to the DG element's polynomial data by V^{FV->DG}
-                vector<T> other = map_face(W[E.nb[f]].face_rec[f ^ 1], V, nfv, E.n, P.ops.f2d.at(E.N));
+                vector<T> o = map_face(other, V, nfv, N + 1, P.ops.f2d.at(N));
                 us.resize(mine.size());
-                for (size_t i = 0; i < mine.size(); ++i) us[i] = T(0.5) * (mine[i] + other[i]);
+                for (size_t i = 0; i < mine.size(); ++i) us[i] = T(0.5) * (mine[i] + o[i]);
             } else {
                 // Sec. 3.2.2: lifting flux on the lower degree, interpolated back up
-                const int Nm = std::min(E.N, Q.N);
-                vector<T> a = map_face_deg(P, mine, V, E.N, Nm);
-                vector<T> b = map_face_deg(P, W[E.nb[f]].face_u[f ^ 1], V, Q.N, Nm);
+                const int Nm = std::min(N, No);
+                vector<T> a = map_face_deg(P, mine, V, N, Nm);
+                vector<T> b = map_face_deg(P, other, V, No, Nm);
                 vector<T> avg(a.size());
                 for (size_t i = 0; i < a.size(); ++i) avg[i] = T(0.5) * (a[i] + b[i]);
-                us = map_face_deg(P, avg, V, Nm, E.N);
+                us = map_face_deg(P, avg, V, Nm, N);
             }
-            W[e].ustar[f] = us;
+            return us;
+        };
+        auto data = [&](int q, int fq) -> const vector<T>& { return P.el[q].fv ? W[q].face_rec[fq] : W[q].face_u[fq]; };
+        for (int f = 0; f < 6; ++f) {
+            const vector<T>& mine = W[e].face_u[f];
+            if (E.mort[f] < 0) {
+                const Elem& Q = P.el[E.nb[f]];
+                W[e].ustar[f] = lift_with(mine, E.N, Q.fv, Q.N, data(E.nb[f], f ^ 1));
+                continue;
+            }
+            // Sec. 3.2.3: the lifting value on each virtual small side, by the
+            // conforming rules above; the big side takes the L2 projection of the
+            // virtual sides' values
+            const Mortar& M = P.mortars[E.mort[f]];
+            const Elem& Bg = P.el[M.big];
+            if (E.quad[f] >= 0) {
+                W[e].ustar[f] = lift_with(mine, E.N, Bg.fv, Bg.N, to_virtual(P, M, E.quad[f], data(M.big, M.fB), V));
+            } else {
+                vector<T> acc;
+                for (int q = 0; q < 4; ++q) {
+                    if (M.small[q] < 0) continue;
+                    const Elem& S = P.el[M.small[q]];
+                    vector<T> Uq = lift_with(to_virtual(P, M, q, mine, V), E.N, S.fv, S.N, data(M.small[q], f ^ 1));
+                    add_from_virtual(P, M, q, Uq, V, acc);
+                }
+                W[e].ustar[f] = acc;
+            }
         }
     }
 
@@ -626,64 +827,118 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
         }
     }
 
-    // ---- step 5: face fluxes; every face is visited once, from its lower element L
+    // ---- step 5: face fluxes; every conforming face is visited once, from its
+    // lower element L, every mortar once, from its big side
     flop_counter().phase = 5;
     for (int e = 0; e < nel; ++e)
         for (int f = 0; f < 6; ++f) W[e].flux[f].clear();
+    // One side of a face: FV flag, degree, and its face data (DG trace of u or FV
+    // reconstructed state; gradient trace).
+    struct Side {
+        bool fv;
+        int N;
+        const vector<T>* u;
+        const vector<T>* g;
+    };
+    // F* in +x_d between a lower side L and an upper side R, returned on each
+    // side's own representation (FL, FR).
+    auto pair_flux = [&](int d, const Side& L, const Side& Rr, vector<T>& FL, vector<T>& FR) {
+        // common representation (Sec. 3.2.1): max degree, or FV data if either side is FV
+        vector<T> uL, gL, uR, gR;
+        int nc;
+        const bool common_fv = L.fv || Rr.fv;
+        if (!common_fv) {
+            const int Nc = std::max(L.N, Rr.N);
+            nc = Nc + 1;
+            uL = map_face_deg(P, *L.u, V, L.N, Nc);
+            gL = map_face_deg(P, *L.g, 3 * V, L.N, Nc);
+            uR = map_face_deg(P, *Rr.u, V, Rr.N, Nc);
+            gR = map_face_deg(P, *Rr.g, 3 * V, Rr.N, Nc);
+        } else {
+            nc = nfv;
+            if (L.fv) {
+                uL = *L.u;
+                gL = *L.g;
+            } else {
+                uL = map_face(*L.u, V, L.N + 1, nc, P.ops.d2f.at(L.N));
+                gL = map_face(*L.g, 3 * V, L.N + 1, nc, P.ops.d2f.at(L.N));
+            }
+            if (Rr.fv) {
+                uR = *Rr.u;
+                gR = *Rr.g;
+            } else {
+                uR = map_face(*Rr.u, V, Rr.N + 1, nc, P.ops.d2f.at(Rr.N));
+                gR = map_face(*Rr.g, 3 * V, Rr.N + 1, nc, P.ops.d2f.at(Rr.N));
+            }
+        }
+        const int np = nc * nc;
+        vector<T> Fc((size_t)V * np);
+        for (int p = 0; p < np; ++p) {
+            T a[MAXV], b[MAXV], ga[3 * MAXV], gb[3 * MAXV], F[MAXV];
+            for (int v = 0; v < V; ++v) { a[v] = uL[(size_t)v * np + p]; b[v] = uR[(size_t)v * np + p]; }
+            for (int dv = 0; dv < 3 * V; ++dv) { ga[dv] = gL[(size_t)dv * np + p]; gb[dv] = gR[(size_t)dv * np + p]; }
+            point_flux(P, a, ga, b, gb, d, F, common_fv);
+            for (int v = 0; v < V; ++v) Fc[(size_t)v * np + p] = F[v];
+        }
+        // back to each side's native representation (projection / V^{FV->DG})
+        auto back = [&](const Side& S) -> vector<T> {
+            if (!common_fv) return map_face_deg(P, Fc, V, nc - 1, S.N);
+            if (S.fv) return Fc;
+            return map_face(Fc, V, nc, S.N + 1, P.ops.f2d.at(S.N));
+        };
+        FL = back(L);
+        FR = back(Rr);
+    };
+    auto side = [&](int e, int f) -> Side {
+        const Elem& E = P.el[e];
+        return Side{E.fv, E.N, E.fv ? &W[e].face_rec[f] : &W[e].face_u[f], &W[e].face_g[f]};
+    };
 #pragma omp parallel for schedule(dynamic, 16) if (parallel)
     for (int e = 0; e < nel; ++e) {
         for (int d = 0; d < 3; ++d) {
+            if (P.el[e].mort[2 * d + 1] >= 0) continue;
             const int eL = e, eR = P.el[e].nb[2 * d + 1];
             const int fL = 2 * d + 1, fR = 2 * d;
-            const Elem &L = P.el[eL], &Rr = P.el[eR];
-            // common representation (Sec. 3.2.1): max degree, or FV data if either side is FV
-            vector<T> uL, gL, uR, gR;
-            int nc;
-            const bool common_fv = L.fv || Rr.fv;
-            if (!common_fv) {
-                const int Nc = std::max(L.N, Rr.N);
-                nc = Nc + 1;
-                uL = map_face_deg(P, W[eL].face_u[fL], V, L.N, Nc);
-                gL = map_face_deg(P, W[eL].face_g[fL], 3 * V, L.N, Nc);
-                uR = map_face_deg(P, W[eR].face_u[fR], V, Rr.N, Nc);
-                gR = map_face_deg(P, W[eR].face_g[fR], 3 * V, Rr.N, Nc);
-            } else {
-                nc = nfv;
-                if (L.fv) {
-                    uL = W[eL].face_rec[fL];
-                    gL = W[eL].face_g[fL];
-                } else {
-                    uL = map_face(W[eL].face_u[fL], V, L.n, nc, P.ops.d2f.at(L.N));
-                    gL = map_face(W[eL].face_g[fL], 3 * V, L.n, nc, P.ops.d2f.at(L.N));
-                }
-                if (Rr.fv) {
-                    uR = W[eR].face_rec[fR];
-                    gR = W[eR].face_g[fR];
-                } else {
-                    uR = map_face(W[eR].face_u[fR], V, Rr.n, nc, P.ops.d2f.at(Rr.N));
-                    gR = map_face(W[eR].face_g[fR], 3 * V, Rr.n, nc, P.ops.d2f.at(Rr.N));
-                }
-            }
-            const int np = nc * nc;
-            vector<T> Fc((size_t)V * np);
-            for (int p = 0; p < np; ++p) {
-                T a[MAXV], b[MAXV], ga[3 * MAXV], gb[3 * MAXV], F[MAXV];
-                for (int v = 0; v < V; ++v) { a[v] = uL[(size_t)v * np + p]; b[v] = uR[(size_t)v * np + p]; }
-                for (int dv = 0; dv < 3 * V; ++dv) { ga[dv] = gL[(size_t)dv * np + p]; gb[dv] = gR[(size_t)dv * np + p]; }
-                point_flux(P, a, ga, b, gb, d, F, common_fv);
-                for (int v = 0; v < V; ++v) Fc[(size_t)v * np + p] = F[v];
-            }
-            // back to each side's native representation (projection / V^{FV->DG})
-            auto back = [&](const Elem& S) -> vector<T> {
-                if (!common_fv) return map_face_deg(P, Fc, V, nc - 1, S.N);
-                if (S.fv) return Fc;
-                return map_face(Fc, V, nc, S.n, P.ops.f2d.at(S.N));
-            };
-            vector<T> FLs = back(L), FRs = back(Rr);
+            vector<T> FLs, FRs;
+            pair_flux(d, side(eL, fL), side(eR, fR), FLs, FRs);
             for (auto& x : FRs) x = -x;  // outward normal of the upper element is -x_d
             W[eL].flux[fL] = FLs;
             W[eR].flux[fR] = FRs;
         }
+    }
+    // Sec. 3.2.3: at a mortar the big side's face data is interpolated to each
+    // virtual small side (M_01, M_02, or M^FV), the flux computed there against
+    // the small side by the conforming rules, and the virtual sides' fluxes
+    // projected back onto the big side (M_10, M_20, or M^FV).
+    const int nmort = (int)P.mortars.size();
+#pragma omp parallel for schedule(dynamic, 4) if (parallel)
+    for (int m = 0; m < nmort; ++m) {
+        const Mortar& M = P.mortars[m];
+        const Elem& Bg = P.el[M.big];
+        const int fB = M.fB, fS = fB ^ 1;
+        const bool big_lower = fB == 1;
+        const vector<T>& bu = Bg.fv ? W[M.big].face_rec[fB] : W[M.big].face_u[fB];
+        vector<T> acc;
+        for (int q = 0; q < 4; ++q) {
+            const int es = M.small[q];
+            if (es < 0) continue;
+            const vector<T> vu = to_virtual(P, M, q, bu, V);
+            const vector<T> vg = to_virtual(P, M, q, W[M.big].face_g[fB], 3 * V);
+            const Side vs{Bg.fv, Bg.N, &vu, &vg};
+            vector<T> FL, FR;
+            if (big_lower) {
+                pair_flux(0, vs, side(es, fS), FL, FR);
+                for (auto& x : FR) x = -x;
+                W[es].flux[fS] = FR;
+                add_from_virtual(P, M, q, FL, V, acc);
+            } else {
+                pair_flux(0, side(es, fS), vs, FL, FR);
+                for (auto& x : FR) x = -x;
+                W[es].flux[fS] = FL;
+                add_from_virtual(P, M, q, FR, V, acc);
+            }
+        }
+        W[M.big].flux[fB] = acc;
     }
 
     // ---- step 6: surface integral and -1/J (Eqs. 22, 26)
@@ -1213,6 +1468,14 @@ int oracle_dg2fv(int N, int n_fv, double* M, int nodes) {
 }
 int oracle_fv2dg(int N, int n_fv, double* M, int nodes) {
     try { auto m = fv2dg(N, n_fv, nodes); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }
+}
+int oracle_mortar(int N, int s, int proj, int fv, double* M, int nodes) {
+    try {
+        auto m = fv ? (proj ? mortar_proj_fv(N, s) : mortar_interp_fv(N, s))
+                    : (proj ? mortar_proj(N, s, nodes) : mortar_interp(N, s, nodes));
+        std::copy(m.begin(), m.end(), M);
+        return 0;
+    } catch (...) { return -1; }
 }
 int oracle_leg_vandermonde(int N, double* V, int nodes) {
     try { auto m = leg_vandermonde(N, nodes); std::copy(m.begin(), m.end(), V); return 0; } catch (...) { return -1; }

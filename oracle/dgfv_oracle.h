@@ -15,7 +15,8 @@
  *   - Element-contiguous state: U[off_e + v*n^3 + i + n*(j + n*k)] with
  *     n = N_e + 1 for DG elements and n = N_FV for FV elements; off_e is the
  *     exclusive prefix sum of V*n_e^3.
- *   - All domains are periodic Cartesian boxes.
+ *   - Domains are Cartesian boxes, periodic each on its own or glued along x
+ *     into one periodic chain with conforming and mortar interfaces (chain_x).
  */
 #ifndef DGFV_ORACLE_H
 #define DGFV_ORACLE_H
@@ -52,6 +53,12 @@ typedef struct {
                               1: p-adaptation on p, FV on rho (Sec. 4.3)     */
     int pp_limiter;        /* 1 = Zhang-Shu positivity limiter after every RK stage (Sec. 3.5) */
     double pp_eps;         /* its floor for partial densities and internal energy (> 0) */
+    int chain_x;           /* 0: every domain a periodic box of its own.  1: the domains are
+                              glued in order along x (the +x side of domain i meets the -x side
+                              of domain i+1, the last wraps to the first), each periodic in y and
+                              z; all share the y and z extents, and neighbouring domains have
+                              equal ny, nz (conforming) or twice as many in one or both of them
+                              (non-conforming mortar interfaces of types 1-3, Sec. 3.2.3) */
 } oracle_problem;
 
 /* 0 on success, negative on a malformed problem. */
@@ -130,6 +137,10 @@ int oracle_vmap(int N_from, int N_to, double* M, int nodes);   /* (N_to+1) x (N_
 int oracle_dg2fv(int N, int n_fv, double* M, int nodes);       /* n_fv x (N+1)          */
 int oracle_fv2dg(int N, int n_fv, double* M, int nodes);       /* (N+1) x n_fv          */
 int oracle_leg_vandermonde(int N, double* V, int nodes);       /* V[i][m] = Lhat_m(x_i) */
+/* Mortar operators of Sec. 3.2.3 for half s (0: [-1,0], 1: [0,1]): proj = 0 the
+ * interpolation to the virtual small side, 1 the L2 projection back; fv = 0 on
+ * the nodes of degree N ((N+1) x (N+1)), fv = 1 on N sub-cells (N x N). */
+int oracle_mortar(int N, int s, int proj, int fv, double* M, int nodes);
 
 /* Pointwise physics (for pins): convective and viscous flux in direction
  * dir of state u (V) and conservative gradient g (3*V, g[d*V+v] = du_v/dx_d). */

@@ -40,10 +40,11 @@ def species_set(specs, mu=0.0, Pr=0.72, Sc=1.0, rho_ref=1.0):
     )
 
 
-def make_problem(domains, species, n_fv, N, fv=None, riemann=0, nodes=0, split=0):
+def make_problem(domains, species, n_fv, N, fv=None, riemann=0, nodes=0, split=0, chain=0):
     """domains: list of (dims(3), lo(3), hi(3)); species: dict from species_set;
     nodes 0 = Legendre-Gauss, 1 = Legendre-Gauss-Lobatto; split 1 = split-form
-    volume integral (LGL only)."""
+    volume integral (LGL only); chain 1 = the domains glued in order along x
+    (conforming or mortar interfaces between neighbours, Sec. 3.2.3)."""
     dims = np.array([d[0] for d in domains], np.int32).reshape(-1, 3)
     lo = np.array([d[1] for d in domains], float).reshape(-1, 3)
     hi = np.array([d[2] for d in domains], float).reshape(-1, 3)
@@ -51,9 +52,21 @@ def make_problem(domains, species, n_fv, N, fv=None, riemann=0, nodes=0, split=0
     N = np.broadcast_to(np.asarray(N, np.int8), (n_elem,)).copy()
     fv = np.zeros(n_elem, np.uint8) if fv is None else np.broadcast_to(np.asarray(fv, np.uint8), (n_elem,)).copy()
     p = dict(dims=dims, lo=lo, hi=hi, n_fv=int(n_fv), riemann=int(riemann), N=N, fv=fv, nodes=int(nodes),
-             split=int(split))
+             split=int(split), chain=int(chain))
     p.update({k: np.array(v, float) for k, v in species.items()})
     return p
+
+
+def chain_domains(segments, L=(1.0, 1.0)):
+    """Domains of a chain along x: segments = [(nx, ny, nz, x_length), ...] placed
+    one after the other from x = 0, all on [0, L_y] x [0, L_z].  Neighbouring
+    segments need equal ny, nz, or twice as many in one or both (mortar types 1-3,
+    Sec. 3.2.3)."""
+    out, x0 = [], 0.0
+    for nx, ny, nz, lx in segments:
+        out.append(((nx, ny, nz), (x0, 0.0, 0.0), (x0 + lx, L[0], L[1])))
+        x0 += lx
+    return out
 
 
 def n_elements(prob):
@@ -174,12 +187,16 @@ def random_fv(n_elem, frac, seed):
 
 
 def smooth_random_state(prob, seed, amp=0.05, rho0=1.0, p0=1.0, vel=(0.3, -0.2, 0.1)):
-    """Smooth periodic random-phase state (low Fourier modes of each domain box)."""
+    """Smooth periodic random-phase state (low Fourier modes of the first domain's
+    box, or of the whole chain when the domains are glued along x)."""
     rng = np.random.default_rng(seed + 104729)
     nk = len(prob["gamma"])
     modes = [(a, b, c) for a in range(0, 2) for b in range(0, 2) for c in range(0, 2) if (a, b, c) != (0, 0, 0)]
     ph = rng.uniform(0, 2 * np.pi, size=(6, len(modes)))
-    lo0, hi0 = prob["lo"][0], prob["hi"][0]
+    if prob.get("chain", 0):
+        lo0, hi0 = np.min(prob["lo"], axis=0), np.max(prob["hi"], axis=0)
+    else:
+        lo0, hi0 = prob["lo"][0], prob["hi"][0]
     L = hi0 - lo0
 
     def wave(x, y, z, q):
