@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--no-split", action="store_true", help="skip the split-form (LGL) measurement")
     p.add_argument("--no-tgv", action="store_true", help="skip the Taylor-Green vortex measurement")
     p.add_argument("--no-shock", action="store_true", help="skip the hp-mixed shock measurement")
+    p.add_argument("--no-mortar", action="store_true", help="skip the non-conforming (mortar) mesh measurement")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the default volume-kernel launch instead of timing variants first")
     p.add_argument("--profile-timed", action="store_true",
@@ -413,6 +414,41 @@ def hp_shock_run(warmup=2, cycles=4):
             "degree_histogram": np.bincount(N_now[fv_now == 0], minlength=7).tolist()}
 
 
+def mortar_run(k=24, warmup=1, steps=3):
+    """Non-conforming mesh (Sec. 3.2.3) at scale: the half-refined unit cube of
+    Sec. 4.1 / 4.2 with (k, 2k, 2k) + (k/2, k, k) elements and type-3 mortars on
+    both x interfaces, random degrees N in 2..5 and 5 % FV elements (N_FV = 8),
+    2 species, viscous, the Sec. 4.2 density wave.  DOF-stage/s over `steps` x
+    10 SSP-RK3 steps at CFL 0.5 (pattern fixed), CUDA events."""
+    import torch
+    from paper_2502_19342_gb300 import dgfv, workloads as W
+    prob, U = W.half_refined_wave(k)
+    ctx = dgfv.Context(prob, N_min=1, N_max=7, opts=dict(cfl_c=0.5, cfl_v=0.5))
+    ctx.set_state(torch.from_numpy(U).cuda())
+    n = W.points_per_dir(prob).astype(np.int64)
+    dofs = int((n ** 3).sum())
+    for _ in range(warmup):
+        ctx.rk_steps(STEPS_PER_CYCLE, -1.0, want_dt=False)
+    s = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(s)
+    for _ in range(steps):
+        ctx.rk_steps(STEPS_PER_CYCLE, -1.0, want_dt=False)
+    ev1.record(s)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    ctx.sync_status()
+    ctx.close()
+    ne = W.n_elements(prob)
+    return {"workload": f"half-refined unit cube (Sec. 4.1/4.2 layout), {k}x{2 * k}x{2 * k} + {k // 2}x{k}x{k} "
+                        "elements, type-3 mortars on both x interfaces, N in 2..5 and 5 % FV (N_FV = 8) at random, "
+                        "2 species, viscous, density wave along [1,1,1]",
+            "value": dofs * steps * STEPS_PER_CYCLE * STAGES_PER_STEP / (ms * 1e-3), "unit": "DOF-stage/s",
+            "ms_per_step": ms / (steps * STEPS_PER_CYCLE), "elements": ne, "dofs": dofs,
+            "mortars": 2 * k * k, "fv_elements": int(prob["fv"].sum())}
+
+
 def batched_comparison(steps=5):
     """256 independent periodic domains of 2^3..8^3 elements, one degree
     N in 1..7 per domain, 3 species: DOF-stage/s of SSP-RK3 steps (fixed dt)
@@ -635,6 +671,7 @@ def main():
         split = None if args.no_split else split_form_run(args.nel)
         tgv = None if args.no_tgv else tgv_run()
         shock = None if args.no_shock else hp_shock_run()
+        mortar = None if args.no_mortar else mortar_run()
         launches = int(sum(v[1] for v in prof.values()))
         last = pattern[-1]
         line = {"metric": "DOF-stage updates/s (FP64 RHS, hp-mixed)", "value": value, "unit": "DOF-stage/s",
@@ -648,7 +685,7 @@ def main():
                            "volume_launch": ({str(k): v for k, v in tuned.items()} if tuned else "default"),
                            "l2": "inputs larger than L2 (state ~1.2 GB)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "adjoint": adjoint,
-                "batched_domains": batched, "split_form": split, "tgv": tgv, "hp_shock": shock,
+                "batched_domains": batched, "split_form": split, "tgv": tgv, "hp_shock": shock, "mortar": mortar,
                 "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
                 "clocks": clk.summary()}
         print(json.dumps(line))

@@ -67,7 +67,16 @@ typedef enum { DGFV_RIEMANN_LLF = 0, DGFV_RIEMANN_ROE_HH = 1, DGFV_RIEMANN_HYBRI
  * adjoint calls and dgfv_rk_step_save support SSP-RK3 only. */
 typedef enum { DGFV_INTEGRATOR_SSPRK3 = 0, DGFV_INTEGRATOR_LSRK4 = 1 } dgfv_integrator;
 
-/* Mesh: n_domains periodic boxes; arrays have 3 entries per domain. */
+/* Mesh: n_domains Cartesian boxes; arrays have 3 entries per domain.
+ * chain_x = 0: every domain is a periodic box of its own (batched domains).
+ * chain_x = 1: the domains are glued in order along x into one periodic
+ *   chain: the +x side of domain i meets the -x side of domain i+1, the last
+ *   wraps to the first; each domain stays periodic in y and z.  All domains
+ *   share the y and z extents; neighbouring domains have equal ny and nz
+ *   (conforming interface) or one has twice as many in one of them (mortar
+ *   types 1 and 2) or in both (type 3), Sec. 3.2.3.  The coarser side holds
+ *   the big mortar sides.  Other ratios: DGFV_ERR_ARG.
+ * Element order: domain by domain, x fastest within a domain. */
 typedef struct {
     int n_domains;
     const int32_t* dims;  /* nx, ny, nz per domain (>= 1)               */
@@ -75,6 +84,7 @@ typedef struct {
     const double* hi;     /* upper corner per domain (hi > lo)          */
     int N_min, N_max;     /* degree bounds, 1 <= N_min <= N_max <= 7    */
     int N_fv;             /* FV sub-cells per direction, N_max+1 <= N_fv <= 8 */
+    int chain_x;          /* 0 or 1, see above                          */
 } dgfv_mesh_desc;
 
 /* Species (Sec. 2): constant properties, ideal-gas mixture, 1 <= n_species <= 3. */
@@ -281,7 +291,9 @@ void dgfv_destroy(dgfv_ctx* ctx);
  * which = 0 nodes, 1 weights, 2 Dhat (n x n), 3 l(-1), 4 l(+1),
  * 5 V^{N->M} ((M+1) x (N+1)), 6 V^{DG->FV} (N_fv x (N+1)),
  * 7 V^{FV->DG} ((N+1) x N_fv), 8 inverse Legendre Vandermonde, 9 D (n x n),
- * all on the context's node family.
+ * 10 / 11 mortar interpolation to / L2 projection from the virtual small side
+ * of half M (0 or 1) ((N+1) x (N+1), Sec. 3.2.3), 12 / 13 the same on the
+ * N_fv sub-cells (N_fv x N_fv), all on the context's node family.
  * Copies the row-major matrix to host memory `out` of `cap` doubles and
  * returns the number of entries, or a negative status. */
 int64_t dgfv_bank_entry(dgfv_ctx* ctx, int which, int N, int M, double* out, int64_t cap);

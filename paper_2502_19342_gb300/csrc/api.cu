@@ -125,6 +125,16 @@ struct dgfv_ctx {
     double graph_dt = 0.0;
     cudaStream_t graph_stream = nullptr;
     Profiler prof;
+    // non-conforming interfaces (Sec. 3.2.3); virtual element v is entry n_elem + v
+    int n_mort = 0, n_virt = 0, n_slot = 0, n_slot_active = 0;
+    std::vector<int32_t> m_big, m_vfirst, v_mort, v_small, s_elem, s_mort, s_nbe;
+    std::vector<uint8_t> m_fB, m_split, v_quad, s_face;
+    std::vector<int8_t> s_quad;
+    int32_t *d_m_big = nullptr, *d_m_vfirst = nullptr, *d_v_mort = nullptr, *d_v_small = nullptr;
+    int32_t *d_s_elem = nullptr, *d_s_mort = nullptr, *d_s_nbe = nullptr, *d_s_active = nullptr;
+    uint8_t *d_m_fB = nullptr, *d_m_split = nullptr, *d_v_quad = nullptr, *d_s_face = nullptr;
+    int8_t* d_s_quad = nullptr;
+    double* d_mnb = nullptr;  // FV neighbour values per slot, V x N_FV^2
     // adjoint buffers, allocated by the first adjoint call
     bool adj_ready = false;
     double *d_fbar = nullptr, *d_ubar = nullptr, *d_gbar = nullptr, *d_sbar = nullptr;
@@ -167,13 +177,18 @@ int dalloc(dgfv_ctx* c, T** p, size_t count) {
 Params params(const dgfv_ctx* c) {
     Params P{};
     P.ph = c->ph;
-    P.t = Tables{c->d_n, c->d_N, c->d_fv, c->d_off, c->d_fo, c->d_nb, c->d_rh};
+    P.t = Tables{c->d_n, c->d_N, c->d_fv, c->d_off, c->d_fo, c->d_nb, c->d_rh, c->d_mnb, c->d_s_nbe};
     P.b = Buffers{c->d_fu, c->d_fg, c->d_flux, c->d_flift, c->d_frec, c->d_rtmp};
     P.bank = c->d_bank;
     P.bi = c->bi;
     P.nfv = c->nfv;
     P.status = c->d_status;
     return P;
+}
+
+MortarTables mortar_tables(const dgfv_ctx* c) {
+    return MortarTables{c->n_elem,    c->d_m_big,  c->d_m_fB,   c->d_m_split, c->d_m_vfirst, c->d_v_mort,
+                        c->d_v_quad,  c->d_v_small, c->d_s_elem, c->d_s_face,  c->d_s_mort,   c->d_s_quad};
 }
 
 // Brackets one kernel launch with events when profiling is on.
@@ -228,6 +243,19 @@ int build_bank(dgfv_ctx* c) {
         c->bi.d2f[n] = put(make_dg2fv(n, c->nfv, kind));
         c->bi.f2d[n] = put(make_fv2dg(n, c->nfv, kind));
         for (int m = c->N_min + 1; m <= c->N_max + 1; ++m) c->bi.vm[n][m] = put(make_vmap(n, m, kind));
+        for (int h = 0; h < 2; ++h) {
+            c->bi.mi[n][h] = put(make_mortar(n, h, false, kind));
+            c->bi.mp[n][h] = put(make_mortar(n, h, true, kind));
+        }
+    }
+    for (int h = 0; h < 2; ++h) {
+        c->bi.mfi[h] = put(make_mortar_fv(c->nfv, h, false));
+        c->bi.mfp[h] = put(make_mortar_fv(c->nfv, h, true));
+    }
+    for (int n = 1; n <= MAXP; ++n) {
+        std::vector<double> I((size_t)n * n, 0.0);
+        for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+        c->bi.eye[n] = put(I);
     }
     TRY(dalloc(c, &c->d_bank, bank.size()));
     CK(cudaMemcpy(c->d_bank, bank.data(), bank.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -289,10 +317,12 @@ int volume_per_tile(const dgfv_ctx* c, int n) {
 }
 
 int apply_layout(dgfv_ctx* c) {
-    const int ne = c->n_elem;
-    c->npts.resize(ne);
+    const int ne = c->n_elem, nt = ne + c->n_virt;
+    c->npts.resize(nt);
     c->off.resize(ne);
-    c->fo.resize(ne);
+    c->fo.resize(nt);
+    c->N.resize(nt);
+    c->fv.resize(nt);
     int64_t so = 0, fpo = 0;
     c->n_fv_elems = 0;
     for (int e = 0; e < ne; ++e) {
@@ -304,13 +334,32 @@ int apply_layout(dgfv_ctx* c) {
         fpo += 6LL * n * n;
         c->n_fv_elems += c->fv[e] ? 1 : 0;
     }
+    // virtual small sides take the representation of their big element; they
+    // use face slots 0 and 1 only
+    for (int v = 0; v < c->n_virt; ++v) {
+        const int eb = c->m_big[c->v_mort[v]], e = ne + v;
+        c->N[e] = c->N[eb];
+        c->fv[e] = c->fv[eb];
+        c->npts[e] = c->npts[eb];
+        c->fo[e] = fpo;
+        fpo += 2LL * c->npts[e] * c->npts[e];
+    }
     c->n_state = so;
     c->n_fpts = fpo;
-    CK(cudaMemcpy(c->d_n, c->npts.data(), ne, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->d_N, c->N.data(), ne, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->d_fv, c->fv.data(), ne, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_n, c->npts.data(), nt, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_N, c->N.data(), nt, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_fv, c->fv.data(), nt, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d_off, c->off.data(), ne * sizeof(int64_t), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->d_fo, c->fo.data(), ne * sizeof(int64_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_fo, c->fo.data(), nt * sizeof(int64_t), cudaMemcpyHostToDevice));
+    // mortar faces of FV elements need their neighbour values gathered
+    {
+        std::vector<int32_t> act;
+        for (int sl = 0; sl < c->n_slot; ++sl)
+            if (c->fv[c->s_elem[sl]]) act.push_back(sl);
+        c->n_slot_active = (int)act.size();
+        if (!act.empty())
+            CK(cudaMemcpy(c->d_s_active, act.data(), act.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     // tiles
     make_tiles(c, c->all, [](int) { return true; }, [](int n) { return std::max(1, 512 / (n * n * n)); });
     make_tiles(c, c->dg, [&](int e) { return !c->fv[e]; }, [&](int n) { return volume_per_tile(c, n); });
@@ -471,13 +520,20 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
         else
             launch_prolong(c->nk, P, c->all.view(), c->all.ntiles, Uin, s);
     }
-    if (c->n_fv_elems) { Timed t(c, K_FV, s); launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, Uin, s); }
+    const MortarTables MT = mortar_tables(c);
+    if (c->n_fv_elems) {
+        Timed t(c, K_FV, s);
+        launch_mortar_nb(c->nk, P, MT, c->d_s_active, c->n_slot_active, Uin, c->d_mnb, s);
+        launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, Uin, s);
+    }
+    if (c->n_mort) { Timed t(c, K_LIFT, s); launch_mortar_in(c->nk, P, MT, c->n_virt, 0, s); }
     if (c->ph.viscous) {
         // conforming DG faces one thread per point; faces that change degree or
         // type (all with a DG side) one CTA each
         Timed t(c, K_LIFT, s);
         launch_face_lift_conf(c->nk, P, F, c->conf.view(), c->conf.ntiles, s);
         launch_face_lift(c->nk, P, F, c->flux.d, c->flux.count, s);
+        launch_mortar_out(c->nk, P, MT, c->n_mort, 0, s);
     }
     if (c->dg.ntiles) {
         Timed t(c, K_VOLUME, s);
@@ -490,6 +546,7 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
     }
     {
         Timed t(c, K_FLUX, s);
+        if (c->n_mort && c->ph.viscous) launch_mortar_in(c->nk, P, MT, c->n_virt, 1, s);
         if (per_bin)
             for (size_t bi = 0; bi < c->conf.bin_first.size(); ++bi)
                 launch_face_flux_conf(c->nk, P, F, c->conf.view(c->conf.bin_first[bi]), c->conf.bin_count[bi], s);
@@ -497,6 +554,7 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
             launch_face_flux_conf(c->nk, P, F, c->conf.view(), c->conf.ntiles, s);
         launch_mixed_faces(c->nk, P, F, c->mixed.tiles.view(), c->mixed.tiles.ntiles, c->mixed.d_face, c->mixed.d_pt,
                            c->mixed.n, c->mixed.d_in, c->mixed.d_out, s);
+        launch_mortar_out(c->nk, P, MT, c->n_mort, 1, s);
     }
     {
         Timed t(c, K_SURFACE, s);
@@ -681,9 +739,10 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     c->n_elem = (int)ne;
     c->nb.resize(6 * ne);
     c->rh.resize(3 * ne);
-    int64_t e0 = 0;
+    std::vector<int64_t> first(mesh->n_domains + 1, 0);
     for (int dm = 0; dm < mesh->n_domains; ++dm) {
         const int dims[3] = {mesh->dims[3 * dm], mesh->dims[3 * dm + 1], mesh->dims[3 * dm + 2]};
+        const int64_t e0 = first[dm];
         double rh[3];
         for (int a = 0; a < 3; ++a) rh[a] = 2.0 * dims[a] / (mesh->hi[3 * dm + a] - mesh->lo[3 * dm + a]);
         for (int k = 0; k < dims[2]; ++k)
@@ -698,23 +757,106 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
                         c->nb[6 * e + f] = (int32_t)(e0 + q[0] + (int64_t)dims[0] * (q[1] + (int64_t)dims[1] * q[2]));
                     }
                     for (int a = 0; a < 3; ++a) c->rh[3 * e + a] = rh[a];
-                    for (int a = 0; a < 3; ++a) {  // face towards +a, owned by the lower element
-                        c->faceL.push_back((int32_t)e);
-                        c->faceR.push_back(c->nb[6 * e + 2 * a + 1]);
-                        c->faceD.push_back((uint8_t)a);
-                    }
                 }
-        e0 += (int64_t)dims[0] * dims[1] * dims[2];
+        first[dm + 1] = e0 + (int64_t)dims[0] * dims[1] * dims[2];
+    }
+    if (mesh->chain_x != 0 && mesh->chain_x != 1) return cleanup(DGFV_ERR_ARG);
+    if (mesh->chain_x) {
+        // Sec. 3.2.3: domain A's +x side against domain A+1's -x side (cyclic);
+        // equal (ny, nz): conforming; 2:1 in one or both: mortars, big sides on
+        // the coarser domain.  Each mortar face of an element gets a slot.
+        const int D = mesh->n_domains;
+        for (int A = 0; A < D; ++A)
+            for (int a = 1; a < 3; ++a)
+                if (mesh->lo[3 * A + a] != mesh->lo[a] || mesh->hi[3 * A + a] != mesh->hi[a]) return cleanup(DGFV_ERR_ARG);
+        auto elem = [&](int dm, int i, int j, int k) {
+            const int32_t* dd = mesh->dims + 3 * dm;
+            return (int32_t)(first[dm] + i + (int64_t)dd[0] * (j + (int64_t)dd[1] * k));
+        };
+        auto ratio = [](int x, int y) { return x == y ? 0 : (y == 2 * x ? 1 : (x == 2 * y ? -1 : 9)); };
+        for (int A = 0; A < D; ++A) {
+            const int Bd = (A + 1) % D;
+            const int32_t *da = mesh->dims + 3 * A, *db = mesh->dims + 3 * Bd;
+            const int ra = ratio(da[1], db[1]), rb = ratio(da[2], db[2]);
+            if (ra == 9 || rb == 9 || ra * rb < 0) return cleanup(DGFV_ERR_ARG);
+            if (ra == 0 && rb == 0) {
+                for (int k = 0; k < da[2]; ++k)
+                    for (int j = 0; j < da[1]; ++j) {
+                        const int32_t eA = elem(A, da[0] - 1, j, k), eB = elem(Bd, 0, j, k);
+                        c->nb[6 * (int64_t)eA + 1] = eB;
+                        c->nb[6 * (int64_t)eB + 0] = eA;
+                    }
+                continue;
+            }
+            const bool bigA = ra > 0 || rb > 0;
+            const int Dg = bigA ? A : Bd, Ds = bigA ? Bd : A;
+            const int32_t *dg = mesh->dims + 3 * Dg, *ds = mesh->dims + 3 * Ds;
+            const int fB = bigA ? 1 : 0, sa = ra != 0, sb = rb != 0;
+            for (int k = 0; k < dg[2]; ++k)
+                for (int j = 0; j < dg[1]; ++j) {
+                    const int m = c->n_mort++;
+                    const int32_t eb = elem(Dg, bigA ? dg[0] - 1 : 0, j, k);
+                    c->m_big.push_back(eb);
+                    c->m_fB.push_back((uint8_t)fB);
+                    c->m_split.push_back((uint8_t)(sa | (sb << 1)));
+                    c->m_vfirst.push_back(c->n_virt);
+                    int32_t first_small = -1;
+                    for (int qb = 0; qb <= sb; ++qb)
+                        for (int qa = 0; qa <= sa; ++qa) {
+                            const int32_t es = elem(Ds, bigA ? 0 : ds[0] - 1, sa ? 2 * j + qa : j, sb ? 2 * k + qb : k);
+                            if (first_small < 0) first_small = es;
+                            c->v_mort.push_back(m);
+                            c->v_quad.push_back((uint8_t)(qa + 2 * qb));
+                            c->v_small.push_back(es);
+                            c->n_virt++;
+                            c->nb[6 * (int64_t)es + (fB ^ 1)] = -1 - c->n_slot++;
+                            c->s_elem.push_back(es);
+                            c->s_face.push_back((uint8_t)(fB ^ 1));
+                            c->s_mort.push_back(m);
+                            c->s_quad.push_back((int8_t)(qa + 2 * qb));
+                            c->s_nbe.push_back(eb);
+                        }
+                    c->nb[6 * (int64_t)eb + fB] = -1 - c->n_slot++;
+                    c->s_elem.push_back(eb);
+                    c->s_face.push_back((uint8_t)fB);
+                    c->s_mort.push_back(m);
+                    c->s_quad.push_back(-1);
+                    c->s_nbe.push_back(first_small);
+                }
+        }
+        c->m_vfirst.push_back(c->n_virt);
+    }
+    // faces: every +a face of an element with an element across (conforming),
+    // then every virtual small side against its small element (x faces)
+    for (int64_t e = 0; e < ne; ++e)
+        for (int a = 0; a < 3; ++a) {
+            const int32_t q = c->nb[6 * e + 2 * a + 1];
+            if (q < 0) continue;
+            c->faceL.push_back((int32_t)e);
+            c->faceR.push_back(q);
+            c->faceD.push_back((uint8_t)a);
+        }
+    for (int v = 0; v < c->n_virt; ++v) {
+        const int32_t ev = (int32_t)(ne + v), es = c->v_small[v];
+        const bool big_lower = c->m_fB[c->v_mort[v]] == 1;
+        c->faceL.push_back(big_lower ? ev : es);
+        c->faceR.push_back(big_lower ? es : ev);
+        c->faceD.push_back(0);
     }
     c->n_faces = (int)c->faceL.size();
     // capacity: every element at the largest point count
     const int nmax = std::max(c->N_max + 1, c->nfv);
     c->cap_state = ne * (int64_t)c->V * nmax * nmax * nmax;
-    c->cap_fpts = ne * 6LL * nmax * nmax;
+    c->cap_fpts = (ne + c->n_virt) * 6LL * nmax * nmax;
+    const int64_t nt = ne + c->n_virt;
     int r = DGFV_OK;
 #define A_(p, n)                                 \
     if ((r = dalloc(c, &(p), (size_t)(n))) != DGFV_OK) return cleanup(r);
-    A_(c->d_n, ne) A_(c->d_N, ne) A_(c->d_fv, ne) A_(c->d_off, ne) A_(c->d_fo, ne)
+    A_(c->d_n, nt) A_(c->d_N, nt) A_(c->d_fv, nt) A_(c->d_off, ne) A_(c->d_fo, nt)
+    A_(c->d_m_big, c->n_mort) A_(c->d_m_fB, c->n_mort) A_(c->d_m_split, c->n_mort) A_(c->d_m_vfirst, c->n_mort + 1)
+    A_(c->d_v_mort, c->n_virt) A_(c->d_v_quad, c->n_virt) A_(c->d_v_small, c->n_virt)
+    A_(c->d_s_elem, c->n_slot) A_(c->d_s_face, c->n_slot) A_(c->d_s_mort, c->n_slot) A_(c->d_s_quad, c->n_slot)
+    A_(c->d_s_nbe, c->n_slot) A_(c->d_s_active, c->n_slot) A_(c->d_mnb, (int64_t)c->n_slot * c->V * c->nfv * c->nfv)
     A_(c->d_n_old, ne) A_(c->d_N_old, ne) A_(c->d_fv_old, ne) A_(c->d_off_old, ne)
     A_(c->d_nb, 6 * ne) A_(c->d_rh, 3 * ne)
     A_(c->d_faceL, c->n_faces) A_(c->d_faceR, c->n_faces) A_(c->d_faceD, c->n_faces)
@@ -740,13 +882,29 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
         cudaMemcpy(c->d_faceR, c->faceR.data(), c->n_faces * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->d_faceD, c->faceD.data(), c->n_faces, cudaMemcpyHostToDevice) != cudaSuccess)
         return cleanup(DGFV_ERR_CUDA);
+    if (c->n_mort) {
+        auto up = [](void* d, const void* h, size_t bytes) { return cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice); };
+        if (up(c->d_m_big, c->m_big.data(), c->n_mort * 4) != cudaSuccess ||
+            up(c->d_m_fB, c->m_fB.data(), c->n_mort) != cudaSuccess ||
+            up(c->d_m_split, c->m_split.data(), c->n_mort) != cudaSuccess ||
+            up(c->d_m_vfirst, c->m_vfirst.data(), (c->n_mort + 1) * 4) != cudaSuccess ||
+            up(c->d_v_mort, c->v_mort.data(), c->n_virt * 4) != cudaSuccess ||
+            up(c->d_v_quad, c->v_quad.data(), c->n_virt) != cudaSuccess ||
+            up(c->d_v_small, c->v_small.data(), c->n_virt * 4) != cudaSuccess ||
+            up(c->d_s_elem, c->s_elem.data(), c->n_slot * 4) != cudaSuccess ||
+            up(c->d_s_face, c->s_face.data(), c->n_slot) != cudaSuccess ||
+            up(c->d_s_mort, c->s_mort.data(), c->n_slot * 4) != cudaSuccess ||
+            up(c->d_s_quad, c->s_quad.data(), c->n_slot) != cudaSuccess ||
+            up(c->d_s_nbe, c->s_nbe.data(), c->n_slot * 4) != cudaSuccess)
+            return cleanup(DGFV_ERR_CUDA);
+    }
     try {
         if ((r = build_bank(c)) != DGFV_OK) return cleanup(r);
     } catch (...) {
         return cleanup(DGFV_ERR_ARG);
     }
-    c->N.assign(ne, (uint8_t)c->N_min);
-    c->fv.assign(ne, 0);
+    c->N.assign(nt, (uint8_t)c->N_min);
+    c->fv.assign(nt, 0);
     if ((r = apply_layout(c)) != DGFV_OK) return cleanup(r);
     *out = c;
     return DGFV_OK;
@@ -841,6 +999,7 @@ int dgfv_compute_dt_noalloc(dgfv_ctx* c, const double* d_U, double* d_out3, void
 
 static int adj_prepare(dgfv_ctx* c) {
     if (c->n_fv_elems) return fail(c, DGFV_ERR_ARG, "the adjoint supports DG elements only (the pattern has FV elements)");
+    if (c->n_mort) return fail(c, DGFV_ERR_ARG, "the adjoint supports conforming meshes only (the mesh has mortars)");
     if (c->ph.riemann != 0) return fail(c, DGFV_ERR_ARG, "the adjoint supports the local Lax-Friedrichs flux only");
     if (c->opts.split_form) return fail(c, DGFV_ERR_ARG, "the adjoint supports the standard volume integral only");
     if (c->ph.sutherland) return fail(c, DGFV_ERR_ARG, "the adjoint supports constant viscosity only");
@@ -1196,6 +1355,16 @@ int64_t dgfv_bank_entry(dgfv_ctx* c, int which, int N, int M, double* out, int64
             case 7: v = make_fv2dg(n, c->nfv, kind); break;
             case 8: v = b.vinv; break;
             case 9: v = b.D; break;
+            case 10:  // mortar maps of half M (0 or 1), Sec. 3.2.3
+            case 11:
+                if (M < 0 || M > 1) return DGFV_ERR_ARG;
+                v = make_mortar(n, M, which == 11, kind);
+                break;
+            case 12:
+            case 13:
+                if (M < 0 || M > 1) return DGFV_ERR_ARG;
+                v = make_mortar_fv(c->nfv, M, which == 13);
+                break;
             default: return DGFV_ERR_ARG;
         }
     } catch (...) {

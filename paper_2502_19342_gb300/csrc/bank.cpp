@@ -20,6 +20,13 @@
 //                             basis (LGL quadrature under-integrates it), Cholesky solve
 //   Legendre Vandermonde^-1   V^T diag(w) with the top mode rescaled by its discrete
 //                             norm (the LGL rule is exact for every other mode product)
+// Mortars (Sec. 3.2.3), half s of a face halved at xi = 0:
+//   interpolation             barycentric, big-side basis at (x_i + 2s - 1)/2
+//   projection back           exact L2 projection: mass matrix of the big-side basis
+//                             times P = 1/2 int l_i(xi(eta)) l_j(eta) deta (Gauss rule
+//                             exact for the products), Cholesky solve
+//   FV                        sub-cell j of the big side holds the small sub-cells
+//                             2j - s n and 2j + 1 - s n of half s (injection / mean)
 #include "bank.h"
 
 #include <cmath>
@@ -147,6 +154,32 @@ std::vector<ld> lagrange_all(const Nodes& g, ld xi) {
 
 std::vector<double> to_d(const std::vector<ld>& a) { return std::vector<double>(a.begin(), a.end()); }
 
+// X = A^{-1} B for a symmetric positive definite A (n x n) and B (n x m):
+// Cholesky A = L L^T, then two triangular solves per column.
+std::vector<ld> chol_solve(const std::vector<ld>& A, const std::vector<ld>& Bm, int n, int m) {
+    std::vector<ld> L(n * n, 0), X(n * m, 0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) {
+            ld s = A[i * n + j];
+            for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+            L[i * n + j] = i == j ? std::sqrt(s) : s / L[j * n + j];
+        }
+    for (int c = 0; c < m; ++c) {
+        std::vector<ld> y(n);
+        for (int i = 0; i < n; ++i) {
+            ld s = Bm[i * m + c];
+            for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+            y[i] = s / L[i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            ld s = y[i];
+            for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * X[k * m + c];
+            X[i * m + c] = s / L[i * n + i];
+        }
+    }
+    return X;
+}
+
 }  // namespace
 
 Bank1D make_bank(int n, int kind) {
@@ -211,27 +244,7 @@ std::vector<double> make_vmap(int n_from, int n_to, int kind) {
                 for (int j = 0; j < n_from; ++j) Bm[i * n_from + j] += q.w[k] * lt[i] * lf[j];
             }
         }
-        // Cholesky Mc = L L^T, then two triangular solves per column of Bm
-        std::vector<ld> L(n_to * n_to, 0);
-        for (int i = 0; i < n_to; ++i)
-            for (int j = 0; j <= i; ++j) {
-                ld s = Mc[i * n_to + j];
-                for (int k = 0; k < j; ++k) s -= L[i * n_to + k] * L[j * n_to + k];
-                L[i * n_to + j] = i == j ? std::sqrt(s) : s / L[j * n_to + j];
-            }
-        for (int c = 0; c < n_from; ++c) {
-            std::vector<ld> y(n_to);
-            for (int i = 0; i < n_to; ++i) {
-                ld s = Bm[i * n_from + c];
-                for (int k = 0; k < i; ++k) s -= L[i * n_to + k] * y[k];
-                y[i] = s / L[i * n_to + i];
-            }
-            for (int i = n_to - 1; i >= 0; --i) {
-                ld s = y[i];
-                for (int k = i + 1; k < n_to; ++k) s -= L[k * n_to + i] * M[k * n_from + c];
-                M[i * n_from + c] = s / L[i * n_to + i];
-            }
-        }
+        M = chol_solve(Mc, Bm, n_to, n_from);
     } else {
         for (int j = 0; j < n_from; ++j) {
             std::vector<ld> l = lagrange_all(b, a.x[j]);  // coarse basis at the fine nodes
@@ -304,6 +317,50 @@ std::vector<double> make_fv2dg(int n, int nfv, int kind) {
             X[i * m + c] = s / Rm[i * n + i];
         }
     return to_d(X);
+}
+
+}  // namespace dgfv
+
+namespace dgfv {
+
+std::vector<double> make_mortar(int n, int s, bool proj, int kind) {
+    if (s < 0 || s > 1) throw std::runtime_error("bad mortar half");
+    Nodes g = node_family(n, kind);
+    std::vector<ld> M(n * n, 0);
+    if (!proj) {
+        for (int i = 0; i < n; ++i) {
+            std::vector<ld> l = lagrange_all(g, (g.x[i] + 2 * s - 1) / 2);
+            for (int j = 0; j < n; ++j) M[i * n + j] = l[j];
+        }
+        return to_d(M);
+    }
+    Nodes q = gauss(n + 1);
+    std::vector<ld> Mc(n * n, 0), Bm(n * n, 0);
+    for (size_t k = 0; k < q.x.size(); ++k) {
+        std::vector<ld> lb = lagrange_all(g, q.x[k]);                      // big basis on [-1, 1]
+        std::vector<ld> lh = lagrange_all(g, (q.x[k] + 2 * s - 1) / 2);    // big basis on half s
+        std::vector<ld> ls = lagrange_all(g, q.x[k]);                      // small basis at eta
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) Mc[i * n + j] += q.w[k] * lb[i] * lb[j];
+            for (int j = 0; j < n; ++j) Bm[i * n + j] += q.w[k] * lh[i] * ls[j] / 2;
+        }
+    }
+    return to_d(chol_solve(Mc, Bm, n, n));
+}
+
+std::vector<double> make_mortar_fv(int nfv, int s, bool proj) {
+    if (s < 0 || s > 1 || nfv < 1) throw std::runtime_error("bad FV mortar");
+    std::vector<double> M((size_t)nfv * nfv, 0.0);
+    for (int j = 0; j < nfv; ++j)
+        for (int t = 0; t < 2; ++t) {
+            const int i = 2 * j + t - s * nfv;  // small sub-cell of half s inside big sub-cell j
+            if (i < 0 || i >= nfv) continue;
+            if (proj)
+                M[(size_t)j * nfv + i] = 0.5;
+            else
+                M[(size_t)i * nfv + j] = 1.0;
+        }
+    return M;
 }
 
 }  // namespace dgfv

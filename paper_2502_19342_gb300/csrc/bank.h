@@ -20,5 +20,9 @@ Bank1D make_bank(int n, int kind = 0);
 std::vector<double> make_vmap(int n_from, int n_to, int kind = 0);  // n_to x n_from
 std::vector<double> make_dg2fv(int n, int nfv, int kind = 0);        // nfv x n
 std::vector<double> make_fv2dg(int n, int nfv, int kind = 0);        // n x nfv
+// Mortar maps of half s (Sec. 3.2.3), n x n: interpolation to the virtual small
+// side (proj = false) or L2 projection back (proj = true); FV: on nfv sub-cells.
+std::vector<double> make_mortar(int n, int s, bool proj, int kind = 0);
+std::vector<double> make_mortar_fv(int nfv, int s, bool proj);
 
 }  // namespace dgfv

@@ -29,6 +29,10 @@ struct BankIdx {
     int32_t d2f[NBANK];        // V^{DG->FV}: N_FV x n
     int32_t f2d[NBANK];        // V^{FV->DG}: n x N_FV
     int32_t vm[NBANK][NBANK];  // V^{n->m}: m x n (interpolation up, L2 projection down)
+    int32_t mi[NBANK][2];      // mortar half s: interpolation to the virtual small side, n x n
+    int32_t mp[NBANK][2];      // mortar half s: L2 projection back to the big side, n x n
+    int32_t mfi[2], mfp[2];    // the same on N_FV sub-cells
+    int32_t eye[NBANK];        // identity, n x n (a face direction that is not halved)
 };
 
 struct Tables {
@@ -37,8 +41,32 @@ struct Tables {
     const uint8_t* fv;   // FV flag
     const int64_t* off;  // state offset
     const int64_t* fo;   // face-point offset of slot 0
-    const int32_t* nb;   // 6 neighbours per element
+    const int32_t* nb;   // 6 neighbours per element; -1 - slot at a mortar face (Sec. 3.2.3)
     const double* rh;    // 3 per element: 2/h_d
+    const double* mnb;   // per mortar slot: V x N_FV^2 FV neighbour values (for FV owners)
+    const int32_t* mnbe; // per mortar slot: an element across (its size sets the distance)
+};
+
+// Non-conforming interfaces (Sec. 3.2.3).  The virtual small sides of a big
+// element face are extra entries n_elem + v of the element tables (no state;
+// face slots 0 and 1 only), so that the face kernels couple them with the small
+// elements like any other face.  Mortar m: big element, its face fB (0: -x,
+// 1: +x), split bits (1: halved along a = y, 2: along b = z), virtual elements
+// vfirst[m] .. vfirst[m+1]-1.  Slot s: the mortar face of an element, whose FV
+// neighbour values are gathered into Tables::mnb when the element is FV.
+struct MortarTables {
+    int n_elem;
+    const int32_t* big;
+    const uint8_t* fB;
+    const uint8_t* split;
+    const int32_t* vfirst;
+    const int32_t* vmort;   // per virtual element
+    const uint8_t* vquad;   // quadrant qa + 2 qb
+    const int32_t* vsmall;  // the small element across
+    const int32_t* selem;   // per slot: owner element
+    const uint8_t* sface;   // owner's face
+    const int32_t* smort;   // mortar
+    const int8_t* squad;    // owner's quadrant, -1 for the big side
 };
 
 struct Buffers {

@@ -90,6 +90,38 @@ __global__ void __launch_bounds__(256) k_prolong(Params P, Tiles T, const double
 }
 
 // ---------------------------------------------------------------------------------
+// The layer of sub-cell means that an FV neighbour sees across face fq of element
+// q, on N_FV x N_FV points: an FV element's boundary sub-cell means (its face
+// values), or a DG element's solution mapped by V^{DG->FV} (boundary row along
+// the face normal, then both face directions).  All threads of the block take
+// part; ends with a barrier.
+template <int NK>
+__device__ __forceinline__ void fv_layer(const Params& P, const double* __restrict__ U, int q, int fq, int n,
+                                         double* dst, double* sT1, double* sT2) {
+    constexpr int V = NK + 4;
+    const int n2 = n * n, d = fq >> 1;
+    if (P.t.fv[q]) {
+        const double* src = P.b.fu + (P.t.fo[q] + (int64_t)fq * n2) * V;
+        for (int i = threadIdx.x; i < V * n2; i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+        return;
+    }
+    const int nq = P.t.n[q], nq2 = nq * nq, nq3 = nq2 * nq;
+    const double* A = B(P, P.bi.d2f[nq]);  // n x nq
+    const int row = (fq & 1) ? n - 1 : 0;   // sub-cell layer next to the shared face
+    const double* src = U + P.t.off[q];
+    for (int i = threadIdx.x; i < V * nq2; i += blockDim.x) {
+        const int v = i / nq2, p = i % nq2, a = p % nq, b = p / nq;
+        double s = 0.0;
+        for (int m = 0; m < nq; ++m)
+            s = fma(__ldg(A + row * nq + m), src[(int64_t)v * nq3 + node_index(nq, d, m, a, b)], s);
+        sT1[i] = s;
+    }
+    __syncthreads();
+    face_map(sT1, nq, dst, n, A, V, sT2);
+}
+
+// ---------------------------------------------------------------------------------
 // k_fv: one CTA per FV element (n = N_FV sub-cells per direction).
 //   neighbour value across each face: FV neighbour -> its boundary sub-cell mean;
 //   DG neighbour -> its solution mapped to sub-cell means by V^{DG->FV}, boundary layer.
@@ -110,29 +142,29 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
     double* sT2 = sT1 + V * MAXP * MAXP;   // scratch V*MAXP*MAXP
     const int64_t off = P.t.off[e];
     const double* rh = P.t.rh + 3 * e;
+    __shared__ double sID[6], sGS[6];  // per face: 1/distance to the neighbour's centre, rh/(l + distance)
+    const double l = 2.0 / n;
     for (int i = threadIdx.x; i < V * n3; i += blockDim.x) sU[i] = U[off + i];
-    // neighbour values
+    // neighbour values (across a mortar: gathered beforehand into the slot's values)
     for (int f = 0; f < 6; ++f) {
-        const int q = P.t.nb[6 * e + f], fq = f ^ 1, d = f >> 1;
+        const int q = P.t.nb[6 * e + f];
         double* dst = sNb + f * V * n2;
-        if (P.t.fv[q]) {
-            const double* src = P.b.fu + (P.t.fo[q] + (int64_t)fq * n2) * V;
+        int qe = q;
+        if (q < 0) {
+            const int sl = -1 - q;
+            const double* src = P.t.mnb + (int64_t)sl * V * n2;
             for (int i = threadIdx.x; i < V * n2; i += blockDim.x) dst[i] = src[i];
+            qe = P.t.mnbe[sl];
         } else {
-            const int nq = P.t.n[q], nq2 = nq * nq, nq3 = nq2 * nq;
-            const double* A = B(P, P.bi.d2f[nq]);  // n x nq
-            const int row = (fq & 1) ? n - 1 : 0;   // sub-cell layer next to the shared face
-            const double* src = U + P.t.off[q];
-            // contraction along d with the boundary row of V^{DG->FV}
-            for (int i = threadIdx.x; i < V * nq2; i += blockDim.x) {
-                const int v = i / nq2, p = i % nq2, a = p % nq, b = p / nq;
-                double s = 0.0;
-                for (int m = 0; m < nq; ++m)
-                    s = fma(__ldg(A + row * nq + m), src[(int64_t)v * nq3 + node_index(nq, d, m, a, b)], s);
-                sT1[i] = s;
-            }
-            __syncthreads();
-            face_map(sT1, nq, dst, n, A, V, sT2);
+            fv_layer<NK>(P, U, q, f ^ 1, n, dst, sT1, sT2);
+        }
+        if (threadIdx.x == 0) {
+            // distance between the sub-cell centres in this element's reference
+            // coordinates: l/2 (1 + h_neighbour/h), l when the sizes agree
+            const int d = f >> 1;
+            const double dist = 0.5 * l * (1.0 + rh[d] / P.t.rh[3 * qe + d]);
+            sID[f] = 1.0 / dist;
+            sGS[f] = rh[d] / (l + dist);
         }
     }
     __syncthreads();
@@ -154,7 +186,6 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
         for (int v = 0; v < V; ++v) sNw[(f * V + v) * n2 + p] = w[v];
     }
     __syncthreads();
-    const double l = 2.0 / n;
     // value of variable v of cell (m along d, a, b) or of the neighbour beyond
     auto cellU = [&](int d, int m, int a, int b, int v) -> double {
         if (m < 0) return sNb[((2 * d) * V + v) * n2 + a + n * b];
@@ -170,10 +201,11 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
     auto recon = [&](int d, int m, int a, int b, int side, double* uo) {
         double w[V];
         const double il = 1.0 / l;
+        const double ilm = m > 0 ? il : sID[2 * d], ilp = m < n - 1 ? il : sID[2 * d + 1];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const double wc = cellW(d, m, a, b, v);
-            const double s = minmod((wc - cellW(d, m - 1, a, b, v)) * il, (cellW(d, m + 1, a, b, v) - wc) * il);
+            const double s = minmod((wc - cellW(d, m - 1, a, b, v)) * ilm, (cellW(d, m + 1, a, b, v) - wc) * ilp);
             w[v] = side > 0 ? wc + s * (0.5 * l) : wc - s * (0.5 * l);
         }
         w_to_cons<NK>(P.ph, w, uo);
@@ -185,7 +217,8 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
         for (int dd = 0; dd < 3; ++dd) {
             const int m = c3[dd];
             const int a = dd == 0 ? j : i, b = dd == 2 ? j : k;
-            const double sc = 0.5 * n * 0.5 * rh[dd];  // 1/(2l) * 2/h = n/(2h)
+            // 1/(2l) * 2/h = n/(2h) inside; 1/(l + distance) * 2/h at the element boundary
+            const double sc = m == 0 ? sGS[2 * dd] : (m == n - 1 ? sGS[2 * dd + 1] : 0.5 * n * 0.5 * rh[dd]);
 #pragma unroll
             for (int v = 0; v < V; ++v)
                 g[dd * V + v] = (cellU(dd, m + 1, a, b, v) - cellU(dd, m - 1, a, b, v)) * sc;
@@ -1133,6 +1166,98 @@ __global__ void k_probe_dmma(int iters, double* sink) {
 }
 
 // ================================================================= launchers
+// ---------------------------------------------------------------------------------
+// Non-conforming interfaces (Sec. 3.2.3).  Per direction of the big face: the
+// map of half h, or the identity when the face is not halved that way.  On the
+// big side's representation: DG nodes (n points) or FV sub-cells (fv).
+__device__ __forceinline__ const double* mortar_dir(const Params& P, int split, int quad, int dir, bool fv, int n,
+                                                    bool proj) {
+    if (!((split >> dir) & 1)) return B(P, P.bi.eye[n]);
+    const int h = (quad >> dir) & 1;
+    if (fv) return B(P, proj ? P.bi.mfp[h] : P.bi.mfi[h]);
+    return B(P, proj ? P.bi.mp[n][h] : P.bi.mi[n][h]);
+}
+
+// k_mortar_in: one CTA per virtual small side.  pass 0: the big side's face
+// values interpolated to the quadrant (DG: the trace of u; FV: the
+// reconstructed face state and, viscous, the boundary-cell gradient), after the
+// FV kernel.  pass 1: the DG big side's gradient trace, after the volume kernel.
+template <int NK>
+__global__ void __launch_bounds__(128) k_mortar_in(Params P, MortarTables M, int pass) {
+    constexpr int V = NK + 4;
+    __shared__ double tmp[3 * V * MAXP * MAXP];
+    const int v = M.n_elem + blockIdx.x, m = M.vmort[blockIdx.x], q = M.vquad[blockIdx.x];
+    const int eb = M.big[m], fB = M.fB[m], sp = M.split[m];
+    const bool fv = P.t.fv[eb];
+    const int n = P.t.n[eb], n2 = n * n;
+    if (pass == 1 && fv) return;
+    const double* Ma = mortar_dir(P, sp, q, 0, fv, n, false);
+    const double* Mb = mortar_dir(P, sp, q, 1, fv, n, false);
+    const int64_t src = P.t.fo[eb] + (int64_t)fB * n2, dst = P.t.fo[v] + (int64_t)fB * n2;
+    if (pass == 0) {
+        const double* u = fv ? P.b.frec : P.b.fu;
+        double* o = fv ? P.b.frec : P.b.fu;
+        face_map2(u + src * V, n, o + dst * V, n, Ma, Mb, V, tmp);
+        if (!fv || !P.ph.viscous) return;
+    }
+    face_map2(P.b.fg + src * 3 * V, n, P.b.fg + dst * 3 * V, n, Ma, Mb, 3 * V, tmp);
+}
+
+// k_mortar_out: one CTA per mortar; the L2 projection of the virtual sides'
+// lifting values (which = 0, DG big sides) or outward fluxes (which = 1) onto
+// the big side: F_0 = M_10 F_1 + M_20 F_2 (+ the other direction's halves).
+template <int NK>
+__global__ void __launch_bounds__(128) k_mortar_out(Params P, MortarTables M, int which) {
+    constexpr int V = NK + 4;
+    __shared__ double tmp[V * MAXP * MAXP], res[V * MAXP * MAXP], acc[V * MAXP * MAXP];
+    const int m = blockIdx.x, eb = M.big[m], fB = M.fB[m], sp = M.split[m];
+    const bool fv = P.t.fv[eb];
+    if (which == 0 && fv) return;
+    const int n = P.t.n[eb], n2 = n * n;
+    double* buf = which == 0 ? P.b.flift : P.b.flux;
+    for (int i = threadIdx.x; i < V * n2; i += blockDim.x) acc[i] = 0.0;
+    for (int vi = M.vfirst[m]; vi < M.vfirst[m + 1]; ++vi) {
+        const int v = M.n_elem + vi, q = M.vquad[vi];
+        const double* Pa = mortar_dir(P, sp, q, 0, fv, n, true);
+        const double* Pb = mortar_dir(P, sp, q, 1, fv, n, true);
+        face_map2(buf + (P.t.fo[v] + (int64_t)fB * n2) * V, n, res, n, Pa, Pb, V, tmp);
+        for (int i = threadIdx.x; i < V * n2; i += blockDim.x) acc[i] += res[i];
+        __syncthreads();
+    }
+    double* dst = buf + (P.t.fo[eb] + (int64_t)fB * n2) * V;
+    for (int i = threadIdx.x; i < V * n2; i += blockDim.x) dst[i] = acc[i];
+}
+
+// k_mortar_nb: one CTA per mortar face of an FV element: its neighbour values
+// for the reconstruction and the central differences.  A small side takes the
+// big element's layer on its quadrant (M^FV_01, M^FV_02); a big side the small
+// elements' layers projected onto its sub-cells (M^FV_10, M^FV_20).
+template <int NK>
+__global__ void __launch_bounds__(128) k_mortar_nb(Params P, MortarTables M, const int32_t* __restrict__ active,
+                                                   const double* __restrict__ U, double* __restrict__ out) {
+    constexpr int V = NK + 4;
+    __shared__ double sL[V * MAXP * MAXP], sR[V * MAXP * MAXP], sT1[V * MAXP * MAXP], sT2[V * MAXP * MAXP];
+    const int sl = active[blockIdx.x], m = M.smort[sl], q = M.squad[sl], f = M.sface[sl];
+    const int sp = M.split[m], n = P.nfv, n2 = n * n;
+    double* dst = out + (int64_t)sl * V * n2;
+    if (q >= 0) {
+        const int eb = M.big[m];
+        fv_layer<NK>(P, U, eb, M.fB[m], n, sL, sT1, sT2);
+        face_map2(sL, n, dst, n, mortar_dir(P, sp, q, 0, true, n, false), mortar_dir(P, sp, q, 1, true, n, false), V,
+                  sT1);
+        return;
+    }
+    for (int i = threadIdx.x; i < V * n2; i += blockDim.x) dst[i] = 0.0;
+    for (int vi = M.vfirst[m]; vi < M.vfirst[m + 1]; ++vi) {
+        const int qq = M.vquad[vi];
+        fv_layer<NK>(P, U, M.vsmall[vi], f ^ 1, n, sL, sT1, sT2);
+        face_map2(sL, n, sR, n, mortar_dir(P, sp, qq, 0, true, n, true), mortar_dir(P, sp, qq, 1, true, n, true), V,
+                  sT1);
+        for (int i = threadIdx.x; i < V * n2; i += blockDim.x) dst[i] += sR[i];
+        __syncthreads();
+    }
+}
+
 #define DGFV_DISPATCH(nk, call)           \
     switch (nk) {                         \
         case 1: { constexpr int NK = 1; call; } break; \
@@ -1177,6 +1302,22 @@ void launch_mixed_faces(int nk, const Params& P, const Faces& F, const FaceTiles
     DGFV_DISPATCH(nk, (k_mixed_in<NK><<<nmixed, 128, 0, s>>>(P, F, mface, mpt, Sin),
                        k_mixed_flux<NK><<<ntiles, 128, 0, s>>>(P, F, T, mface, mpt, Sin, Sout),
                        k_mixed_out<NK><<<nmixed, 128, 0, s>>>(P, F, mface, mpt, Sout)));
+}
+
+void launch_mortar_in(int nk, const Params& P, const MortarTables& M, int n_virt, int pass, cudaStream_t s) {
+    if (n_virt <= 0) return;
+    DGFV_DISPATCH(nk, (k_mortar_in<NK><<<n_virt, 128, 0, s>>>(P, M, pass)));
+}
+
+void launch_mortar_out(int nk, const Params& P, const MortarTables& M, int n_mort, int which, cudaStream_t s) {
+    if (n_mort <= 0) return;
+    DGFV_DISPATCH(nk, (k_mortar_out<NK><<<n_mort, 128, 0, s>>>(P, M, which)));
+}
+
+void launch_mortar_nb(int nk, const Params& P, const MortarTables& M, const int32_t* active, int n_active,
+                      const double* U, double* out, cudaStream_t s) {
+    if (n_active <= 0) return;
+    DGFV_DISPATCH(nk, (k_mortar_nb<NK><<<n_active, 128, 0, s>>>(P, M, active, U, out)));
 }
 
 void launch_face_flux_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s) {

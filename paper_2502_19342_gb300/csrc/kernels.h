@@ -24,6 +24,13 @@ void launch_dg_volume(int nk, const Params& P, const Tiles& T, int ntiles, size_
 void launch_mixed_faces(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, const int32_t* mface,
                         const int64_t* mpt, int nmixed, double* Sin, double* Sout, cudaStream_t s);
 void launch_face_flux_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s);
+// Mortars (Sec. 3.2.3): virtual small sides from the big side (pass 0: u /
+// FV state and gradient, pass 1: DG gradient), projection back (which 0:
+// lifting values, 1: fluxes), FV neighbour values of mortar faces.
+void launch_mortar_in(int nk, const Params& P, const MortarTables& M, int n_virt, int pass, cudaStream_t s);
+void launch_mortar_out(int nk, const Params& P, const MortarTables& M, int n_mort, int which, cudaStream_t s);
+void launch_mortar_nb(int nk, const Params& P, const MortarTables& M, const int32_t* active, int n_active,
+                      const double* U, double* out, cudaStream_t s);
 void launch_surface(int nk, const Params& P, const Tiles& T, int ntiles, const double* Uin, const double* U0,
                     double* out, int mode, double a, double b, const double* dt, bool fuse, double* dU,
                     cudaStream_t s);

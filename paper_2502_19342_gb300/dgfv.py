@@ -29,7 +29,8 @@ KERNELS = ["prolong", "fv", "face_lift", "dg_volume", "face_flux", "surface", "d
 
 class MeshDesc(C.Structure):
     _fields_ = [("n_domains", C.c_int), ("dims", C.POINTER(C.c_int32)), ("lo", C.POINTER(C.c_double)),
-                ("hi", C.POINTER(C.c_double)), ("N_min", C.c_int), ("N_max", C.c_int), ("N_fv", C.c_int)]
+                ("hi", C.POINTER(C.c_double)), ("N_min", C.c_int), ("N_max", C.c_int), ("N_fv", C.c_int),
+                ("chain_x", C.c_int)]
 
 
 class Phys(C.Structure):
@@ -141,7 +142,7 @@ class Context:
         self._keep = (dims, lo, hi)
         mesh = MeshDesc(dims.shape[0], dims.ctypes.data_as(C.POINTER(C.c_int32)),
                         lo.ctypes.data_as(C.POINTER(C.c_double)), hi.ctypes.data_as(C.POINTER(C.c_double)),
-                        N_min, N_max, int(problem["n_fv"]))
+                        N_min, N_max, int(problem["n_fv"]), int(problem.get("chain", 0)))
         nk = len(problem["gamma"])
         ph = Phys()
         ph.n_species = nk

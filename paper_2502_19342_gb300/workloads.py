@@ -506,6 +506,27 @@ def tgv(nel=32, N0=3, Ma=1.25, Re=1600.0, n_fv=8, nodes=0, riemann=0, fv=None):
     return prob, build_state(prob, fn)
 
 
+def half_refined_wave(k=24, N_lo=2, N_hi=5, fv_frac=0.05, n_fv=8, seed=0, mu=1e-4, riemann=0):
+    """Non-conforming mesh of Sec. 4.1 / 4.2 on the unit cube (Cartesian): the
+    lower half in x at twice the resolution, (k, 2k, 2k) elements, the upper
+    half (k/2, k, k), so both x interfaces carry type-3 mortars (Sec. 3.2.3);
+    random degrees in [N_lo, N_hi] and FV elements (Sec. 4.1 draws both at
+    random); 2 species; the density wave of Sec. 4.2 travelling along [1,1,1]."""
+    sp = species_set([AIR, HELIUM], mu=mu)
+    doms = chain_domains([(k, 2 * k, 2 * k, 0.5), (k // 2, k, k, 0.5)])
+    ne = sum(int(np.prod(d[0])) for d in doms)
+    prob = make_problem(doms, sp, n_fv=n_fv, N=random_degrees(ne, N_lo, N_hi, seed), fv=random_fv(ne, fv_frac, seed),
+                        chain=1, riemann=riemann)
+
+    def fn(x, y, z):
+        s = 2 * np.pi * (x + y + z)
+        rho = 1 + 0.2 * np.sin(s)
+        Y = 0.5 + 0.2 * np.cos(s)
+        return [rho * Y, rho * (1 - Y)], (0.5 + 0 * x, 0.5 + 0 * x, 0.5 + 0 * x), np.ones_like(x)
+
+    return prob, build_state(prob, fn)
+
+
 def shard_domains(prob, U, rank, world):
     """This rank's share of a batch of independent domains: domains taken in
     order of decreasing DOFs, each given to the rank with the fewest DOFs so far
