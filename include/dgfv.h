@@ -63,8 +63,9 @@ typedef enum { DGFV_RIEMANN_LLF = 0, DGFV_RIEMANN_ROE_HH = 1, DGFV_RIEMANN_HYBRI
 
 /* Time integrator of dgfv_rk_step / dgfv_rk_steps: the three-stage SSP-RK3 of
  * Shu and Osher, or the explicit fourth-order low-storage scheme of Sec. 3.3
- * (five stages, 2N storage, Carpenter and Kennedy's coefficients).  The
- * adjoint calls and dgfv_rk_step_save support SSP-RK3 only. */
+ * (five stages, 2N storage, Carpenter and Kennedy's coefficients).
+ * dgfv_rk_step_vjp supports both; dgfv_rk_step_save and
+ * dgfv_rk_step_vjp_stages support SSP-RK3 only. */
 typedef enum { DGFV_INTEGRATOR_SSPRK3 = 0, DGFV_INTEGRATOR_LSRK4 = 1 } dgfv_integrator;
 
 /* Mesh: n_domains Cartesian boxes; arrays have 3 entries per domain.
@@ -203,18 +204,23 @@ int dgfv_rk_steps(dgfv_ctx* ctx, int n_steps, double dt, double* dt_used, void* 
 
 /* Adjoint (vector-Jacobian product) of the right-hand side:
  * d_Ubar = (dR/dU)^T d_Rbar at the state d_U, with the degree pattern frozen.
- * Supported for patterns without FV elements and the local Lax-Friedrichs
- * flux (DGFV_ERR_ARG otherwise).  Device arrays in the current layout;
+ * Supported for patterns without FV elements and the standard volume
+ * integral (DGFV_ERR_ARG otherwise), every flux choice (without FV elements
+ * the hybrid choice is Roe-HH everywhere), constant or Sutherland viscosity,
+ * conforming and mortar meshes (the mortar maps enter transposed).  Device
+ * arrays in the current layout;
  * d_Ubar must not alias d_U or d_Rbar.  Uses the context's forward face
  * buffers (a later eval_rhs recomputes them).  The first adjoint call
  * allocates the adjoint scratch (face adjoints and four state buffers). */
 int dgfv_rhs_vjp(dgfv_ctx* ctx, const double* d_U, const double* d_Rbar, double* d_Ubar, void* stream);
 
-/* Adjoint of one SSP-RK3 step of size dt from the state d_U0:
- * d_Ubar = (dU1/dU0)^T d_Ubar_next.  The two intermediate stage states are
+/* Adjoint of one step of size dt of the context's integrator from the state
+ * d_U0: d_Ubar = (dU1/dU0)^T d_Ubar_next.  The intermediate stage states are
  * recomputed from d_U0 (stage checkpointing: a caller stores only the state
- * at the start of every step).  Same restrictions as dgfv_rhs_vjp; d_Ubar
- * must not alias the inputs. */
+ * at the start of every step): two for SSP-RK3, four for the low-storage RK4
+ * (whose reverse runs the 2N-storage recursion backwards).  Same
+ * restrictions as dgfv_rhs_vjp, and no positivity limiter; d_Ubar must not
+ * alias the inputs. */
 int dgfv_rk_step_vjp(dgfv_ctx* ctx, const double* d_U0, double dt, const double* d_Ubar_next, double* d_Ubar,
                      void* stream);
 

@@ -492,12 +492,71 @@ __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, doubl
 }
 
 // ================================================================= launchers
+// ---------------------------------------------------------------------------------
+// Mortars (Sec. 3.2.3), transposed.  The forward projects the virtual small
+// sides' fluxes and lifting values onto the big side, F_0 = sum_q P_q F_q, and
+// interpolates the big side's traces to them, u_q = M_q u_0, g_q = M_q g_0
+// (P_q, M_q tensor products of the per-direction maps; DG big sides only, the
+// adjoint has no FV elements).
+//   k_adj_mortar_virt: which 0: fbar_q = P_q^T fbar_0, which 1: sbar_q = P_q^T sbar_0
+//                      (one CTA per virtual side)
+//   k_adj_mortar_big:  which 0: gbar_0 = sum_q M_q^T gbar_q, which 1: ubar_0 = sum_q M_q^T ubar_q
+//                      (one CTA per mortar; no face writes the big side's slot)
+__device__ __forceinline__ const double* adj_mortar_dir(const Params& P, int split, int quad, int dir, int n,
+                                                        bool proj) {
+    if (!((split >> dir) & 1)) return B(P, P.bi.eye[n]);
+    const int h = (quad >> dir) & 1;
+    return B(P, proj ? P.bi.mp[n][h] : P.bi.mi[n][h]);
+}
+
+template <int NK>
+__global__ void __launch_bounds__(128) k_adj_mortar_virt(Params P, AdjBuffers A, MortarTables M, int which) {
+    constexpr int V = NK + 4;
+    __shared__ double tmp[V * MAXP * MAXP];
+    const int v = M.n_elem + blockIdx.x, m = M.vmort[blockIdx.x], q = M.vquad[blockIdx.x];
+    const int eb = M.big[m], fB = M.fB[m], sp = M.split[m], n = P.t.n[eb], n2 = n * n;
+    double* buf = which == 0 ? A.fbar : A.sbar;
+    face_map2_t(buf + (P.t.fo[eb] + (int64_t)fB * n2) * V, n, buf + (P.t.fo[v] + (int64_t)fB * n2) * V, n,
+                adj_mortar_dir(P, sp, q, 0, n, true), adj_mortar_dir(P, sp, q, 1, n, true), V, tmp);
+}
+
+template <int NK>
+__global__ void __launch_bounds__(128) k_adj_mortar_big(Params P, AdjBuffers A, MortarTables M, int which) {
+    constexpr int V = NK + 4;
+    __shared__ double tmp[3 * V * MAXP * MAXP], res[3 * V * MAXP * MAXP], acc[3 * V * MAXP * MAXP];
+    const int m = blockIdx.x, eb = M.big[m], fB = M.fB[m], sp = M.split[m], n = P.t.n[eb], n2 = n * n;
+    const int w = which == 0 ? 3 * V : V;
+    double* buf = which == 0 ? A.gbar : A.ubar;
+    for (int i = threadIdx.x; i < w * n2; i += blockDim.x) acc[i] = 0.0;
+    for (int vi = M.vfirst[m]; vi < M.vfirst[m + 1]; ++vi) {
+        const int v = M.n_elem + vi, q = M.vquad[vi];
+        face_map2_t(buf + (P.t.fo[v] + (int64_t)fB * n2) * w, n, res, n, adj_mortar_dir(P, sp, q, 0, n, false),
+                    adj_mortar_dir(P, sp, q, 1, n, false), w, tmp);
+        for (int i = threadIdx.x; i < w * n2; i += blockDim.x) acc[i] += res[i];
+        __syncthreads();
+    }
+    double* dst = buf + (P.t.fo[eb] + (int64_t)fB * n2) * w;
+    for (int i = threadIdx.x; i < w * n2; i += blockDim.x) dst[i] = acc[i];
+}
+
 #define DGFV_DISPATCH(nk, call)                          \
     switch (nk) {                                        \
         case 1: { constexpr int NK = 1; call; } break;   \
         case 2: { constexpr int NK = 2; call; } break;   \
         default: { constexpr int NK = 3; call; } break;  \
     }
+
+void launch_adj_mortar_virt(int nk, const Params& P, const AdjBuffers& A, const MortarTables& M, int n_virt,
+                            int which, cudaStream_t s) {
+    if (n_virt <= 0) return;
+    DGFV_DISPATCH(nk, (k_adj_mortar_virt<NK><<<n_virt, 128, 0, s>>>(P, A, M, which)));
+}
+
+void launch_adj_mortar_big(int nk, const Params& P, const AdjBuffers& A, const MortarTables& M, int n_mort,
+                           int which, cudaStream_t s) {
+    if (n_mort <= 0) return;
+    DGFV_DISPATCH(nk, (k_adj_mortar_big<NK><<<n_mort, 128, 0, s>>>(P, A, M, which)));
+}
 
 void launch_adj_surface(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, const double* Rb,
                         cudaStream_t s) {

@@ -12,6 +12,13 @@ namespace dgfv {
 
 void launch_adj_surface(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, const double* Rb,
                         cudaStream_t s);
+// Mortars, transposed: which 0/1 = fluxes / lifting values onto the virtual
+// sides (launch_adj_mortar_virt), gradient / value traces back onto the big
+// side (launch_adj_mortar_big).
+void launch_adj_mortar_virt(int nk, const Params& P, const AdjBuffers& A, const MortarTables& M, int n_virt,
+                            int which, cudaStream_t s);
+void launch_adj_mortar_big(int nk, const Params& P, const AdjBuffers& A, const MortarTables& M, int n_mort,
+                           int which, cudaStream_t s);
 void launch_adj_faces(int nk, const Params& P, const AdjBuffers& A, const Faces& F, const FaceTiles& conf,
                       int nconf, const int32_t* mixed, int nmixed, cudaStream_t s);
 size_t adj_volume_smem_bytes(int nk, int n, int count);

@@ -574,6 +574,14 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
     }
 }
 
+// Five-stage fourth-order 2N-storage scheme (Carpenter and Kennedy), Sec. 3.3:
+// dU <- A_s dU + dt R(U); U <- U + B_s dU, s = 1..5, A_1 = 0.
+const double LSRK4_A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                           -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double LSRK4_B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                           1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                           2277821191437.0 / 14882151754819.0};
+
 void enqueue_rk_step(dgfv_ctx* c, double dt, cudaStream_t s) {
     const Params P = params(c);
     if (dt > 0.0) {
@@ -586,15 +594,8 @@ void enqueue_rk_step(dgfv_ctx* c, double dt, cudaStream_t s) {
     // SSP-RK3 (Shu-Osher): U1 = U + dt R(U); U2 = 3/4 U + 1/4 (U1 + dt R(U1));
     // U <- 1/3 U + 2/3 (U2 + dt R(U2)).
     if (c->opts.integrator == DGFV_INTEGRATOR_LSRK4) {
-        // five-stage fourth-order 2N-storage scheme (Carpenter and Kennedy):
-        // dU <- A_s dU + dt R(U); U <- U + B_s dU
-        static const double A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
-                                    -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
-        static const double Bc[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
-                                     1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
-                                     2277821191437.0 / 14882151754819.0};
         for (int st = 0; st < 5; ++st)
-            enqueue_stage(c, c->d_U, c->d_U, c->d_U, 2, A[st], Bc[st], s, st > 0, st < 4);
+            enqueue_stage(c, c->d_U, c->d_U, c->d_U, 2, LSRK4_A[st], LSRK4_B[st], s, st > 0, st < 4);
         return;
     }
     enqueue_stage(c, c->d_U, c->d_U, c->d_Us, 1, 0.0, 1.0, s, false, true);
@@ -999,10 +1000,7 @@ int dgfv_compute_dt_noalloc(dgfv_ctx* c, const double* d_U, double* d_out3, void
 
 static int adj_prepare(dgfv_ctx* c) {
     if (c->n_fv_elems) return fail(c, DGFV_ERR_ARG, "the adjoint supports DG elements only (the pattern has FV elements)");
-    if (c->n_mort) return fail(c, DGFV_ERR_ARG, "the adjoint supports conforming meshes only (the mesh has mortars)");
-    if (c->ph.riemann != 0) return fail(c, DGFV_ERR_ARG, "the adjoint supports the local Lax-Friedrichs flux only");
     if (c->opts.split_form) return fail(c, DGFV_ERR_ARG, "the adjoint supports the standard volume integral only");
-    if (c->ph.sutherland) return fail(c, DGFV_ERR_ARG, "the adjoint supports constant viscosity only");
     if (c->adj_ready) return DGFV_OK;
     TRY(dalloc(c, &c->d_fbar, c->cap_fpts * c->V));
     TRY(dalloc(c, &c->d_ubar, c->cap_fpts * c->V));
@@ -1024,17 +1022,28 @@ static void enqueue_vjp(dgfv_ctx* c, const double* U, const double* Rb, double* 
     const Params P = params(c);
     const Faces F{c->d_faceL, c->d_faceR, c->d_faceD};
     const AdjBuffers A{c->d_fbar, c->d_ubar, c->d_gbar, c->d_sbar};
-    // forward face values and lifting values of U
+    const MortarTables MT = mortar_tables(c);
+    // forward face values and lifting values of U (mortars: the virtual small
+    // sides' values, the big sides' projected lifting values)
     launch_prolong(c->nk, P, c->all.view(), c->all.ntiles, U, s);
-    if (c->ph.viscous) launch_face_lift(c->nk, P, F, c->lift.d, c->lift.count, s);
+    launch_mortar_in(c->nk, P, MT, c->n_virt, 0, s);
+    if (c->ph.viscous) {
+        launch_face_lift(c->nk, P, F, c->lift.d, c->lift.count, s);
+        launch_mortar_out(c->nk, P, MT, c->n_mort, 0, s);
+    }
     launch_adj_surface(c->nk, P, A, c->dg.view(), c->dg.ntiles, Rb, s);
+    launch_adj_mortar_virt(c->nk, P, A, MT, c->n_virt, 0, s);
     // recomputed gradient (and its traces), volume integral^T, nodal reverse
     launch_adj_vol_a(c->nk, P, c->dg.view(), c->dg.ntiles, c->adj_smem, U, Rb, Ub, c->d_gvol, c->d_gf, s);
+    if (c->ph.viscous) launch_mortar_in(c->nk, P, MT, c->n_virt, 1, s);
     launch_adj_faces(c->nk, P, A, F, c->conf.view(), c->conf.ntiles, c->flux.d, c->flux.count, s);
     if (c->ph.viscous) {
+        launch_adj_mortar_big(c->nk, P, A, MT, c->n_mort, 0, s);
         launch_adj_vol_b(c->nk, P, A, c->dg.view(), c->dg.ntiles, c->dg.smem, c->d_gvol, Ub, s);
+        launch_adj_mortar_virt(c->nk, P, A, MT, c->n_virt, 1, s);
         launch_adj_lift(c->nk, P, A, F, c->lift.d, c->lift.count, s);
     }
+    launch_adj_mortar_big(c->nk, P, A, MT, c->n_mort, 1, s);
     launch_adj_prolong(c->nk, P, A, c->dg.view(), c->dg.ntiles, Ub, s);
 }
 
@@ -1064,14 +1073,44 @@ static int rk_step_vjp_impl(dgfv_ctx* c, const double* d_U0, const double* d_U1,
     return DGFV_OK;
 }
 
+// Adjoint of one low-storage RK4 step from U0, the stage states recomputed:
+// forward U_s = U_{s-1} + B_s dU_s, dU_s = A_s dU_{s-1} + dt R(U_{s-1});
+// backwards, with dU_bar = 0 after the step:
+//   dU_bar_s += B_s U_bar_s;  U_bar_{s-1} = U_bar_s + dt J(U_{s-1})^T dU_bar_s;
+//   dU_bar_{s-1} = A_s dU_bar_s.
+// U_1..U_4 live in the four adjoint stage buffers, dU_bar in the context's
+// low-storage register (free between steps).
+static int lsrk4_step_vjp(dgfv_ctx* c, const double* d_U0, double dt, const double* d_Ubar_next, double* d_Ubar,
+                          cudaStream_t s) {
+    const int64_t n = c->n_state;
+    const double* Us[5] = {d_U0, c->d_S1, c->d_S2, c->d_B1, c->d_B2};
+    launch_set_scalar(c->d_dt3, dt, s);
+    for (int st = 0; st < 4; ++st)
+        enqueue_stage(c, Us[st], Us[st], const_cast<double*>(Us[st + 1]), 2, LSRK4_A[st], LSRK4_B[st], s, st > 0,
+                      st < 3);
+    double* dUb = c->d_Us;
+    launch_axpby(n, 1.0, d_Ubar_next, 0.0, d_Ubar_next, d_Ubar, s);                  // U_bar_5
+    for (int st = 4; st >= 0; --st) {
+        if (st == 4)
+            launch_axpby(n, LSRK4_B[4], d_Ubar, 0.0, d_Ubar, dUb, s);                // dU_bar_5 = B_5 U_bar_5
+        else
+            launch_axpby(n, 1.0, dUb, LSRK4_B[st], d_Ubar, dUb, s);
+        enqueue_vjp(c, Us[st], dUb, c->d_W, s);
+        launch_axpby(n, 1.0, d_Ubar, dt, c->d_W, d_Ubar, s);
+        if (st > 0) launch_axpby(n, LSRK4_A[st], dUb, 0.0, dUb, dUb, s);
+    }
+    CK(cudaGetLastError());
+    return DGFV_OK;
+}
+
 int dgfv_rk_step_vjp(dgfv_ctx* c, const double* d_U0, double dt, const double* d_Ubar_next, double* d_Ubar,
                      void* stream) {
     if (!c || !d_U0 || !d_Ubar_next || !d_Ubar || !(dt > 0.0)) return DGFV_ERR_ARG;
     if (d_Ubar == d_Ubar_next || d_Ubar == d_U0) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
-    if (c->opts.integrator != DGFV_INTEGRATOR_SSPRK3 || c->opts.pp_limiter)
-        return fail(c, DGFV_ERR_ARG, "stage adjoints and stage saving support SSP-RK3 without the limiter only");
+    if (c->opts.pp_limiter) return fail(c, DGFV_ERR_ARG, "step adjoints do not support the positivity limiter");
     TRY(adj_prepare(c));
     cudaStream_t s = (cudaStream_t)stream;
+    if (c->opts.integrator == DGFV_INTEGRATOR_LSRK4) return lsrk4_step_vjp(c, d_U0, dt, d_Ubar_next, d_Ubar, s);
     // stage states of the step (recomputed from the step's start state)
     launch_set_scalar(c->d_dt3, dt, s);
     enqueue_stage(c, d_U0, d_U0, c->d_S1, 1, 0.0, 1.0, s, false, true);      // U1 = U0 + dt R(U0)

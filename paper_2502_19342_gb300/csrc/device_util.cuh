@@ -81,4 +81,27 @@ __device__ __forceinline__ void face_map_t(const double* in, int no, double* out
     __syncthreads();
 }
 
+// Transpose of face_map2 with the same Ma, Mb (no x ni): out = (Ma^T x Mb^T) in.
+__device__ __forceinline__ void face_map2_t(const double* in, int no, double* out, int ni, const double* Ma,
+                                            const double* Mb, int nvar, double* tmp) {
+    const int n1 = ni * no;
+    for (int i = threadIdx.x; i < nvar * n1; i += blockDim.x) {
+        const int x = i / n1, r = i % n1, ai = r % ni, bo = r / ni;
+        const double* src = in + x * no * no + no * bo;
+        double s = 0.0;
+        for (int ao = 0; ao < no; ++ao) s = fma(__ldg(Ma + ao * ni + ai), src[ao], s);
+        tmp[x * n1 + ai + ni * bo] = s;
+    }
+    __syncthreads();
+    const int n2 = ni * ni;
+    for (int i = threadIdx.x; i < nvar * n2; i += blockDim.x) {
+        const int x = i / n2, r = i % n2, ai = r % ni, bi = r / ni;
+        const double* src = tmp + x * n1 + ai;
+        double s = 0.0;
+        for (int bo = 0; bo < no; ++bo) s = fma(__ldg(Mb + bo * ni + bi), src[ni * bo], s);
+        out[x * n2 + r] = s;
+    }
+    __syncthreads();
+}
+
 }  // namespace dgfv

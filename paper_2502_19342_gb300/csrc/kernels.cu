@@ -292,11 +292,12 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
 
 
 // NF: the sub-cell count as a compile-time constant for the common N_FV = 8.
-// Register budget for two CTAs per SM: where the shared memory allows two (up
-// to N_FV = 7 with 3 species) that doubles the resident warps; the spills it
-// costs go to L1.
-template <int NK>
-__global__ void __launch_bounds__(256, 2) k_fv(Params P, Tiles T, const double* __restrict__ U) {
+// 16 warps per SM at 128 registers a thread (the spills of that budget go to
+// L1): two CTAs of 256 threads where the shared memory of two elements fits
+// on an SM (N_FV <= 7), otherwise one CTA of 512 threads (N_FV = 8, up to
+// 180 KB for one element).
+template <int NK, int TPB>
+__global__ void __launch_bounds__(TPB, 512 / TPB) k_fv(Params P, Tiles T, const double* __restrict__ U) {
     if (P.nfv == 8)
         fv_body<NK, 8>(P, T, U);
     else
@@ -1282,8 +1283,14 @@ size_t fv_smem_bytes(int nk, int nfv) {
 void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s) {
     if (ntiles <= 0) return;
     const size_t sm = fv_smem_bytes(nk, P.nfv);
-    DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_fv<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
-                       k_fv<NK><<<ntiles, 256, sm, s>>>(P, T, U)));
+    // 228 KB of shared memory per SM, 1 KB of it reserved per resident CTA
+    if (2 * (sm + 1024 + 256) <= 228 * 1024) {
+        DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_fv<NK, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                           k_fv<NK, 256><<<ntiles, 256, sm, s>>>(P, T, U)));
+    } else {
+        DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_fv<NK, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                           k_fv<NK, 512><<<ntiles, 512, sm, s>>>(P, T, U)));
+    }
 }
 
 void launch_face_lift_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s) {

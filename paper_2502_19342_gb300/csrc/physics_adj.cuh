@@ -3,7 +3,8 @@
 // every forward assignment y = f(x) becomes x_bar += (df/dx)^T y_bar, in
 // reverse order.  Branches (the larger wave speed of the local Lax-Friedrichs
 // flux, the sign of |v_d|) follow the forward evaluation.  These serve the
-// adjoint of R(U) on DG elements with the local Lax-Friedrichs flux.
+// adjoint of R(U) on DG elements with the local Lax-Friedrichs or the Roe-HH
+// flux, constant or Sutherland viscosity.
 #pragma once
 
 #include "physics.cuh"
@@ -29,6 +30,12 @@ DGFV_HD void prim_rev(const DevPhys& P, const double* u, const Prim<NK>& s, Prim
     b.mu += b.lam * s.cp / s.pr;
     b.cp += b.lam * s.mu / s.pr;
     b.pr -= b.lam * s.lam / s.pr;
+    // Sutherland (Sec. 4.3): mu = mu_mix f(T), f = (T/T_ref)^{3/2} (T_ref + S)/(T + S),
+    // f'/f = 3/(2T) - 1/(T + S); b.mu becomes the adjoint of mu_mix
+    if (P.sutherland) {
+        b.T += b.mu * s.mu * (1.5 / s.T - 1.0 / (s.T + P.S));
+        b.mu *= sutherland_factor(P, s.T);
+    }
     // c = sqrt(kappa p irho)
     if (s.c > 0.0) {
         const double qb = 0.5 * b.c / s.c;
@@ -245,6 +252,223 @@ DGFV_HD void volume_point_rev(const DevPhys& P, const double* u, const double* g
 
 // Adjoint of the interface flux F* = LLF(uL, uR) + (F^v(uL,gL) + F^v(uR,gR))/2 in +x_d:
 // given F_bar (V), accumulate uL_bar, gL_bar, uR_bar, gR_bar.
+// Reverse of riemann_roe (physics.cuh), statement by statement backwards:
+// u_bar, s_bar += (dF/d(u, s))^T F_bar for the Roe flux with the Harten-Hyman
+// fix.  The branches of the fix (which of |lambda~| and delta is taken, and
+// which term gives delta) and of |v_n| follow the forward evaluation.
+template <int NK>
+DGFV_HD void riemann_roe_rev(const DevPhys& P, const double* uL, const Prim<NK>& sL, const double* uR,
+                             const Prim<NK>& sR, int d, const double* Fb, double* uLb, PrimBar<NK>& bL, double* uRb,
+                             PrimBar<NK>& bR) {
+    constexpr int V = NK + 4;
+    // ---- forward, keeping the intermediates
+    const double rL = sqrt(sL.rho), rR = sqrt(sR.rho);
+    const double iw = 1.0 / (rL + rR);
+    const double wl = rL * iw, wr = rR * iw;
+    double vt[3], Yt[NK];
+    for (int i = 0; i < 3; ++i) vt[i] = wl * sL.v[i] + wr * sR.v[i];
+    double cvt = 0.0, cpt = 0.0;
+    for (int k = 0; k < NK; ++k) {
+        Yt[k] = wl * sL.Y[k] + wr * sR.Y[k];
+        cvt = fma(Yt[k], P.cv[k], cvt);
+        cpt = fma(Yt[k], P.cp[k], cpt);
+    }
+    const double HL = sL.E + sL.p * sL.irho, HR = sR.E + sR.p * sR.irho;
+    const double Ht = wl * HL + wr * HR;
+    const double kt = cpt / cvt;
+    const double q2 = vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2];
+    const double c2 = (kt - 1.0) * (Ht - 0.5 * q2);
+    const double ct = sqrt(c2);
+    const double ic2 = 1.0 / c2;
+    const double rt = rL * rR;
+    const double vn = vt[d];
+    const double dp = sR.p - sL.p;
+    double dv[3];
+    for (int i = 0; i < 3; ++i) dv[i] = sR.v[i] - sL.v[i];
+    const double Xm = 0.5 * (dp - rt * ct * dv[d]), Xp = 0.5 * (dp + rt * ct * dv[d]);
+    const double am = Xm * ic2, ap = Xp * ic2;
+    // Harten-Hyman: value and the branch taken (0: |lt|, 1: lt - lL, 2: lR - lt)
+    auto hh = [](double lt, double lL, double lR, int& br) {
+        double delta = 0.0;
+        int dbr = 0;
+        if (lt - lL > delta) { delta = lt - lL; dbr = 1; }
+        if (lR - lt > delta) { delta = lR - lt; dbr = 2; }
+        const double a = fabs(lt);
+        br = a < delta ? dbr : 0;
+        return a < delta ? delta : a;
+    };
+    int bm, bp;
+    const double lm = hh(vn - ct, sL.v[d] - sL.c, sR.v[d] - sR.c, bm);
+    const double lp = hh(vn + ct, sL.v[d] + sL.c, sR.v[d] + sR.c, bp);
+    const double l0 = fabs(vn);
+    const double sa = lm * am + lp * ap;
+    const double sd = (lp * ap - lm * am) * ct;
+    const double pt = rt * c2 / kt;
+    const double Dn = (kt - 1.0) * (kt - 1.0) * rt * cvt;
+    const double ecoef = -pt / Dn;
+    double ak[NK], sk[NK], scon = 0.0;
+    for (int k = 0; k < NK; ++k) {
+        ak[k] = (uR[k] - uL[k]) - Yt[k] * dp * ic2;
+        sk[k] = l0 * ak[k];
+        scon += sk[k];
+    }
+    // ---- reverse.  F = (F_L + F_R)/2 - Dis/2
+    double half[V], Db[V];
+    for (int v = 0; v < V; ++v) {
+        half[v] = 0.5 * Fb[v];
+        Db[v] = -0.5 * Fb[v];
+    }
+    flux_conv_rev<NK>(uL, sL, d, half, uLb, bL);
+    flux_conv_rev<NK>(uR, sR, d, half, uRb, bR);
+    double vtb[3] = {0.0, 0.0, 0.0}, Ytb[NK], dvb[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < NK; ++k) Ytb[k] = 0.0;
+    double l0b = 0.0, rtb = 0.0, q2b = 0.0, ktb = 0.0, ecoefb = 0.0, dpb = 0.0, ic2b = 0.0, sab = 0.0, sdb = 0.0;
+    double Htb = 0.0, vnb = 0.0, lmb = 0.0, lpb = 0.0, amb = 0.0, apb = 0.0, ctb = 0.0, c2b = 0.0, cvtb = 0.0;
+    double cptb = 0.0;
+    // shear waves: s = l0 rt dv_i; Dis[m_i] += s; Dis[E] += s vt_i
+    for (int i = 0; i < 3; ++i) {
+        if (i == d) continue;
+        const double sh = l0 * rt * dv[i];
+        const double shb = Db[NK + i] + Db[NK + 3] * vt[i];
+        vtb[i] += Db[NK + 3] * sh;
+        l0b += shb * rt * dv[i];
+        rtb += shb * l0 * dv[i];
+        dvb[i] += shb * l0 * rt;
+    }
+    // contact waves: Dis[m_i] += scon vt_i; Dis[E] += econ
+    double sconb = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        sconb += Db[NK + i] * vt[i];
+        vtb[i] += Db[NK + i] * scon;
+    }
+    const double econb = Db[NK + 3];
+    for (int k = 0; k < NK; ++k) {
+        const double ck = P.cp[k] - kt * P.cv[k];
+        const double skb = Db[k] + sconb + econb * (0.5 * q2 + ecoef * ck);
+        q2b += econb * sk[k] * 0.5;
+        ecoefb += econb * sk[k] * ck;
+        ktb -= econb * sk[k] * ecoef * P.cv[k];
+        l0b += skb * ak[k];
+        const double akb = skb * l0;
+        uRb[k] += akb;
+        uLb[k] -= akb;
+        Ytb[k] -= akb * dp * ic2;
+        dpb -= akb * Yt[k] * ic2;
+        ic2b -= akb * Yt[k] * dp;
+    }
+    // ecoef = -pt / Dn, Dn = (kt - 1)^2 rt cvt;  pt = rt c2 / kt
+    const double ptb = -ecoefb / Dn;
+    const double Dnb = ecoefb * pt / (Dn * Dn);
+    ktb += Dnb * 2.0 * (kt - 1.0) * rt * cvt;
+    rtb += Dnb * (kt - 1.0) * (kt - 1.0) * cvt;
+    cvtb += Dnb * (kt - 1.0) * (kt - 1.0) * rt;
+    rtb += ptb * c2 / kt;
+    c2b += ptb * rt / kt;
+    ktb -= ptb * rt * c2 / (kt * kt);
+    // main waves: Dis[k] = sa Yt_k; Dis[m_i] = sa vt_i (+ sd for i = d); Dis[E] = sa Ht + sd vn
+    for (int k = 0; k < NK; ++k) {
+        sab += Db[k] * Yt[k];
+        Ytb[k] += Db[k] * sa;
+    }
+    for (int i = 0; i < 3; ++i) {
+        sab += Db[NK + i] * vt[i];
+        vtb[i] += Db[NK + i] * sa;
+    }
+    sdb += Db[NK + d];
+    sab += Db[NK + 3] * Ht;
+    Htb += Db[NK + 3] * sa;
+    sdb += Db[NK + 3] * vn;
+    vnb += Db[NK + 3] * sd;
+    // sd = (lp ap - lm am) ct;  sa = lm am + lp ap
+    lpb += sdb * ap * ct + sab * ap;
+    apb += sdb * lp * ct + sab * lp;
+    lmb += -sdb * am * ct + sab * am;
+    amb += -sdb * lm * ct + sab * lm;
+    ctb += sdb * (lp * ap - lm * am);
+    // l0 = |vn|
+    vnb += l0b * (vn > 0.0 ? 1.0 : (vn < 0.0 ? -1.0 : 0.0));
+    // lp = hh(vn + ct, vL + cL, vR + cR);  lm = hh(vn - ct, vL - cL, vR - cR)
+    {
+        double ltb = 0.0, lLb = 0.0, lRb = 0.0;
+        if (bp == 0) ltb = lpb * ((vn + ct) > 0.0 ? 1.0 : ((vn + ct) < 0.0 ? -1.0 : 0.0));
+        else if (bp == 1) { ltb = lpb; lLb = -lpb; }
+        else { lRb = lpb; ltb = -lpb; }
+        vnb += ltb;
+        ctb += ltb;
+        bL.v[d] += lLb;
+        bL.c += lLb;
+        bR.v[d] += lRb;
+        bR.c += lRb;
+    }
+    {
+        double ltb = 0.0, lLb = 0.0, lRb = 0.0;
+        if (bm == 0) ltb = lmb * ((vn - ct) > 0.0 ? 1.0 : ((vn - ct) < 0.0 ? -1.0 : 0.0));
+        else if (bm == 1) { ltb = lmb; lLb = -lmb; }
+        else { lRb = lmb; ltb = -lmb; }
+        vnb += ltb;
+        ctb -= ltb;
+        bL.v[d] += lLb;
+        bL.c -= lLb;
+        bR.v[d] += lRb;
+        bR.c -= lRb;
+    }
+    // am = Xm ic2, ap = Xp ic2;  Xm/p = (dp -/+ rt ct dv_d)/2
+    ic2b += amb * Xm + apb * Xp;
+    const double Xmb = amb * ic2, Xpb = apb * ic2;
+    dpb += 0.5 * (Xmb + Xpb);
+    const double tb = 0.5 * (Xpb - Xmb);  // adjoint of rt ct dv_d
+    rtb += tb * ct * dv[d];
+    ctb += tb * rt * dv[d];
+    dvb[d] += tb * rt * ct;
+    // dv = vR - vL;  dp = pR - pL;  vn = vt_d;  rt = rL rR
+    for (int i = 0; i < 3; ++i) {
+        bR.v[i] += dvb[i];
+        bL.v[i] -= dvb[i];
+    }
+    bR.p += dpb;
+    bL.p -= dpb;
+    vtb[d] += vnb;
+    double rLb = rtb * rR, rRb = rtb * rL;
+    // ic2 = 1/c2;  ct = sqrt(c2);  c2 = (kt - 1)(Ht - q2/2)
+    c2b -= ic2b * ic2 * ic2;
+    c2b += ctb * 0.5 / ct;
+    ktb += c2b * (Ht - 0.5 * q2);
+    Htb += c2b * (kt - 1.0);
+    q2b -= c2b * 0.5 * (kt - 1.0);
+    // q2 = |vt|^2;  kt = cpt / cvt;  Ht = wl HL + wr HR;  H = E + p irho
+    for (int i = 0; i < 3; ++i) vtb[i] += q2b * 2.0 * vt[i];
+    cptb += ktb / cvt;
+    cvtb -= ktb * cpt / (cvt * cvt);
+    double wlb = Htb * HL, wrb = Htb * HR;
+    const double HLb = Htb * wl, HRb = Htb * wr;
+    bL.E += HLb;
+    bL.p += HLb * sL.irho;
+    bL.irho += HLb * sL.p;
+    bR.E += HRb;
+    bR.p += HRb * sR.irho;
+    bR.irho += HRb * sR.p;
+    // cvt, cpt = sum Yt_k c_k;  Yt = wl YL + wr YR;  vt = wl vL + wr vR
+    for (int k = 0; k < NK; ++k) {
+        Ytb[k] += cvtb * P.cv[k] + cptb * P.cp[k];
+        wlb += Ytb[k] * sL.Y[k];
+        wrb += Ytb[k] * sR.Y[k];
+        bL.Y[k] += Ytb[k] * wl;
+        bR.Y[k] += Ytb[k] * wr;
+    }
+    for (int i = 0; i < 3; ++i) {
+        wlb += vtb[i] * sL.v[i];
+        wrb += vtb[i] * sR.v[i];
+        bL.v[i] += vtb[i] * wl;
+        bR.v[i] += vtb[i] * wr;
+    }
+    // wl = rL iw, wr = rR iw, iw = 1/(rL + rR);  r = sqrt(rho)
+    const double iwb = wlb * rL + wrb * rR;
+    rLb += wlb * iw - iwb * iw * iw;
+    rRb += wrb * iw - iwb * iw * iw;
+    bL.rho += rLb * 0.5 / rL;
+    bR.rho += rRb * 0.5 / rR;
+}
+
 template <int NK>
 DGFV_HD void face_point_rev(const DevPhys& P, const double* uL, const double* gL, const double* uR,
                             const double* gR, int d, const double* Fb, double* uLb, double* gLb, double* uRb,
@@ -256,26 +480,31 @@ DGFV_HD void face_point_rev(const DevPhys& P, const double* uL, const double* gL
     PrimBar<NK> bL, bR;
     zero(bL);
     zero(bR);
-    // local Lax-Friedrichs: F = (F_L + F_R)/2 - smax (uR - uL)/2
-    const double aL = fabs(sL.v[d]) + sL.c, aR = fabs(sR.v[d]) + sR.c;
-    const double smax = aL > aR ? aL : aR;
     double half[V];
-    double smaxb = 0.0;
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        half[v] = 0.5 * Fb[v];
-        uRb[v] -= half[v] * smax;
-        uLb[v] += half[v] * smax;
-        smaxb -= half[v] * (uR[v] - uL[v]);
-    }
-    flux_conv_rev<NK>(uL, sL, d, half, uLb, bL);
-    flux_conv_rev<NK>(uR, sR, d, half, uRb, bR);
-    if (aL > aR) {
-        bL.v[d] += smaxb * (sL.v[d] > 0.0 ? 1.0 : (sL.v[d] < 0.0 ? -1.0 : 0.0));
-        bL.c += smaxb;
+    for (int v = 0; v < V; ++v) half[v] = 0.5 * Fb[v];
+    if (use_roe(P, false)) {
+        riemann_roe_rev<NK>(P, uL, sL, uR, sR, d, Fb, uLb, bL, uRb, bR);
     } else {
-        bR.v[d] += smaxb * (sR.v[d] > 0.0 ? 1.0 : (sR.v[d] < 0.0 ? -1.0 : 0.0));
-        bR.c += smaxb;
+        // local Lax-Friedrichs: F = (F_L + F_R)/2 - smax (uR - uL)/2
+        const double aL = fabs(sL.v[d]) + sL.c, aR = fabs(sR.v[d]) + sR.c;
+        const double smax = aL > aR ? aL : aR;
+        double smaxb = 0.0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            uRb[v] -= half[v] * smax;
+            uLb[v] += half[v] * smax;
+            smaxb -= half[v] * (uR[v] - uL[v]);
+        }
+        flux_conv_rev<NK>(uL, sL, d, half, uLb, bL);
+        flux_conv_rev<NK>(uR, sR, d, half, uRb, bR);
+        if (aL > aR) {
+            bL.v[d] += smaxb * (sL.v[d] > 0.0 ? 1.0 : (sL.v[d] < 0.0 ? -1.0 : 0.0));
+            bL.c += smaxb;
+        } else {
+            bR.v[d] += smaxb * (sR.v[d] > 0.0 ? 1.0 : (sR.v[d] < 0.0 ? -1.0 : 0.0));
+            bR.c += smaxb;
+        }
     }
     if (P.viscous) {
         PrimGrad<NK> G;

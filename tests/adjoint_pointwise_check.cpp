@@ -10,10 +10,14 @@
 using namespace dgfv;
 
 template <int NK>
-DevPhys phys(bool visc) {
+DevPhys phys(bool visc, bool suth = false, int riemann = 0) {
     DevPhys P{};
     P.nk = NK;
     P.viscous = visc;
+    P.riemann = riemann;
+    P.sutherland = suth ? 1 : 0;
+    P.T_ref = 1.3;
+    P.S = 0.45;
     const double gam[3] = {1.4, 1.3, 1.67}, R[3] = {1.0 / 29, 1.0 / 44, 1.0 / 4};
     for (int k = 0; k < NK; ++k) {
         P.cv[k] = R[k] / (gam[k] - 1);
@@ -75,11 +79,11 @@ double face_dot(const DevPhys& P, const double* uL, const double* gL, const doub
 }
 
 template <int NK>
-int check(bool visc, int seed) {
+int check(bool visc, int seed, bool suth = false, int riemann = 0) {
     constexpr int V = NK + 4;
     std::mt19937 rng(seed);
     std::normal_distribution<double> N01(0.0, 1.0);
-    DevPhys P = phys<NK>(visc);
+    DevPhys P = phys<NK>(visc, suth, riemann);
     int bad = 0;
     for (int trial = 0; trial < 20; ++trial) {
         double u[V], g[3 * V], Fb[3 * V], du[V], dg[3 * V];
@@ -97,7 +101,7 @@ int check(bool visc, int seed) {
         for (int v = 0; v < V; ++v) ad += ub[v] * du[v];
         for (int x = 0; x < 3 * V; ++x) ad += gb[x] * dg[x];
         if (std::fabs(fd - ad) > 1e-7 + 1e-6 * std::fabs(fd)) {
-            std::printf("volume NK=%d visc=%d trial %d: fd %.12e adjoint %.12e\n", NK, visc, trial, fd, ad);
+            std::printf("volume NK=%d visc=%d suth=%d trial %d: fd %.12e adjoint %.12e\n", NK, visc, suth, trial, fd, ad);
             ++bad;
         }
         // face
@@ -116,7 +120,68 @@ int check(bool visc, int seed) {
         for (int v = 0; v < V; ++v) adf += uLb[v] * du[v] + uRb[v] * duR[v];
         for (int x = 0; x < 3 * V; ++x) adf += gLb[x] * dg[x] + gRb[x] * dgR[x];
         if (std::fabs(fdf - adf) > 1e-7 + 1e-6 * std::fabs(fdf)) {
-            std::printf("face NK=%d visc=%d trial %d: fd %.12e adjoint %.12e\n", NK, visc, trial, fdf, adf);
+            std::printf("face NK=%d visc=%d suth=%d riemann=%d trial %d: fd %.12e adjoint %.12e\n", NK, visc, suth,
+                        riemann, trial, fdf, adf);
+            ++bad;
+        }
+    }
+    return bad;
+}
+
+// Sets the normal velocity of u to f times its sound speed, keeping density,
+// the other velocity components and the temperature.
+template <int NK>
+void set_normal_mach(const DevPhys& P, double* u, int d, double f) {
+    Prim<NK> s;
+    prim<NK>(P, u, s);
+    const double vn = f * s.c;
+    u[NK + 3] += 0.5 * s.rho * (vn * vn - s.v[d] * s.v[d]);
+    u[NK + d] = s.rho * vn;
+}
+
+// Face adjoint of the Roe flux at transonic states, where the Harten-Hyman fix
+// is active on the u - c wave (even trials) or the u + c wave (odd trials).
+template <int NK>
+int check_transonic(bool visc, int seed) {
+    constexpr int V = NK + 4;
+    std::mt19937 rng(seed);
+    std::normal_distribution<double> N01(0.0, 1.0);
+    DevPhys P = phys<NK>(visc, false, 1);
+    int bad = 0;
+    for (int trial = 0; trial < 20; ++trial) {
+        const int d = trial % 3;
+        double uL[V], uR[V], gL[3 * V], gR[3 * V], Fb[V], duL[V], duR[V], dgL[3 * V], dgR[3 * V];
+        state<NK>(rng, P, uL);
+        state<NK>(rng, P, uR);
+        if (trial % 2 == 0) {
+            set_normal_mach<NK>(P, uL, d, 0.8);
+            set_normal_mach<NK>(P, uR, d, 1.2);
+        } else {
+            set_normal_mach<NK>(P, uL, d, -1.2);
+            set_normal_mach<NK>(P, uR, d, -0.8);
+        }
+        for (int x = 0; x < 3 * V; ++x) {
+            gL[x] = 0.3 * N01(rng); gR[x] = 0.3 * N01(rng); dgL[x] = N01(rng); dgR[x] = N01(rng);
+        }
+        for (int v = 0; v < V; ++v) {
+            Fb[v] = N01(rng);
+            duL[v] = 0.05 * N01(rng) * std::fabs(uL[v]);
+            duR[v] = 0.05 * N01(rng) * std::fabs(uR[v]);
+        }
+        double uLb[V] = {}, gLb[3 * V] = {}, uRb[V] = {}, gRb[3 * V] = {};
+        face_point_rev<NK>(P, uL, gL, uR, gR, d, Fb, uLb, gLb, uRb, gRb);
+        const double eps = 1e-6;
+        double a[V], b[V], c[V], e[V], ga[3 * V], gb[3 * V], gc[3 * V], ge[3 * V];
+        for (int v = 0; v < V; ++v) { a[v] = uL[v] + eps * duL[v]; b[v] = uL[v] - eps * duL[v];
+                                      c[v] = uR[v] + eps * duR[v]; e[v] = uR[v] - eps * duR[v]; }
+        for (int x = 0; x < 3 * V; ++x) { ga[x] = gL[x] + eps * dgL[x]; gb[x] = gL[x] - eps * dgL[x];
+                                          gc[x] = gR[x] + eps * dgR[x]; ge[x] = gR[x] - eps * dgR[x]; }
+        const double fd = (face_dot<NK>(P, a, ga, c, gc, d, Fb) - face_dot<NK>(P, b, gb, e, ge, d, Fb)) / (2 * eps);
+        double ad = 0.0;
+        for (int v = 0; v < V; ++v) ad += uLb[v] * duL[v] + uRb[v] * duR[v];
+        for (int x = 0; x < 3 * V; ++x) ad += gLb[x] * dgL[x] + gRb[x] * dgR[x];
+        if (std::fabs(fd - ad) > 1e-7 + 1e-6 * std::fabs(fd)) {
+            std::printf("transonic Roe NK=%d visc=%d trial %d: fd %.12e adjoint %.12e\n", NK, visc, trial, fd, ad);
             ++bad;
         }
     }
@@ -129,6 +194,19 @@ int main() {
         bad += check<1>(visc, 1 + visc);
         bad += check<2>(visc, 3 + visc);
         bad += check<3>(visc, 5 + visc);
+    }
+    // Sutherland viscosity (Sec. 4.3)
+    bad += check<1>(true, 7, true);
+    bad += check<2>(true, 8, true);
+    bad += check<3>(true, 9, true);
+    // Roe flux with the Harten-Hyman fix
+    for (int visc = 0; visc < 2; ++visc) {
+        bad += check<1>(visc, 11 + visc, false, 1);
+        bad += check<2>(visc, 13 + visc, false, 1);
+        bad += check<3>(visc, 15 + visc, false, 1);
+        bad += check_transonic<1>(visc, 21 + visc);
+        bad += check_transonic<2>(visc, 23 + visc);
+        bad += check_transonic<3>(visc, 25 + visc);
     }
     std::printf("%s (%d mismatches)\n", bad ? "FAIL" : "OK", bad);
     return bad ? 1 : 0;

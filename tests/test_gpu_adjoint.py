@@ -14,20 +14,27 @@ pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
 
 
-def _dg_problem(seed, nk=3, nel=(3, 2, 3), Nlo=1, Nhi=5, mu=3e-3, uniform=None, nodes=0):
+def _dg_problem(seed, nk=3, nel=(3, 2, 3), Nlo=1, Nhi=5, mu=3e-3, uniform=None, nodes=0, sutherland=False,
+                riemann=0):
     specs = [W.AIR, W.HELIUM, W.CO2][:nk]
     sp = W.species_set(specs, mu=mu)
     n = nel[0] * nel[1] * nel[2]
     N = np.full(n, uniform, np.int8) if uniform else W.random_degrees(n, Nlo, Nhi, seed)
-    prob = W.make_problem([(nel, (0, 0, 0), (1.0, 0.8, 1.1))], sp, n_fv=8, N=N, riemann=0, nodes=nodes)
+    prob = W.make_problem([(nel, (0, 0, 0), (1.0, 0.8, 1.1))], sp, n_fv=8, N=N, riemann=riemann, nodes=nodes)
+    if sutherland:  # T ~ p / (rho R) ~ 29 in these states; Sutherland constants of air scaled to it
+        prob.update(sutherland=1, T_ref=29.0, S_sutherland=29.0 * 110.4 / 273.15)
     return prob, W.smooth_random_state(prob, seed, amp=0.1)
 
 
-@pytest.mark.parametrize("nk,mu,seed,uniform,nodes", [(3, 3e-3, 1, None, 0), (2, 0.0, 2, None, 0),
-                                                      (1, 1e-3, 3, None, 0), (3, 2e-3, 4, 4, 0),
-                                                      (3, 2e-3, 5, None, 1)])
-def test_rhs_vjp_dot_product_with_oracle_jvp(oracle, nk, mu, seed, uniform, nodes):
-    prob, U = _dg_problem(seed, nk=nk, mu=mu, uniform=uniform, nodes=nodes)
+@pytest.mark.parametrize("nk,mu,seed,uniform,nodes,suth,riemann", [
+    (3, 3e-3, 1, None, 0, False, 0), (2, 0.0, 2, None, 0, False, 0), (1, 1e-3, 3, None, 0, False, 0),
+    (3, 2e-3, 4, 4, 0, False, 0), (3, 2e-3, 5, None, 1, False, 0), (3, 3e-3, 6, None, 0, True, 0),
+    (2, 2e-3, 7, None, 1, True, 0), (3, 3e-3, 8, None, 0, False, 1), (2, 0.0, 9, None, 0, False, 1),
+    (3, 2e-3, 10, None, 1, True, 2)])
+def test_rhs_vjp_dot_product_with_oracle_jvp(oracle, nk, mu, seed, uniform, nodes, suth, riemann):
+    """Constant and Sutherland viscosity (Sec. 4.3), LG and LGL nodes, the LLF
+    and the Roe-HH flux (hybrid = Roe-HH on a DG-only pattern)."""
+    prob, U = _dg_problem(seed, nk=nk, mu=mu, uniform=uniform, nodes=nodes, sutherland=suth, riemann=riemann)
     rng = np.random.default_rng(seed)
     Rbar = rng.standard_normal(U.size)
     ctx = ctx_for(prob, N_min=1, N_max=7)
@@ -74,6 +81,51 @@ def test_rk_step_vjp_against_central_differences(oracle):
         fd = float(np.dot(lam, (up - um) / (2 * eps)))
         ad = float(np.dot(Ubar, v))
         assert abs(fd - ad) <= 1e-6 * abs(fd) + 1e-9 * float(np.abs(lam).sum() * np.abs(v).mean()), (fd, ad)
+    ctx.close()
+
+
+# Carpenter and Kennedy's five-stage 2N-storage RK4 (the published coefficients)
+_LSRK4_A = (0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+            -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0)
+_LSRK4_B = (1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+            1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+            2277821191437.0 / 14882151754819.0)
+
+
+def _lsrk4_step_tangent(oracle, prob, U, v, dt):
+    """One low-storage RK4 step and its exact tangent along v, stage by stage
+    with the oracle's R and its dual-number JVP."""
+    Uc, Vc = U.copy(), v.copy()
+    dU, dV = np.zeros_like(U), np.zeros_like(U)
+    for a, b in zip(_LSRK4_A, _LSRK4_B):
+        R, JR = oracle.eval_rhs_jvp(prob, Uc, Vc)
+        dU = a * dU + dt * R
+        dV = a * dV + dt * JR
+        Uc = Uc + b * dU
+        Vc = Vc + b * dV
+    return Uc, Vc
+
+
+@pytest.mark.parametrize("mu,seed", [(3e-3, 16), (0.0, 17)])
+def test_lsrk4_step_vjp_dot_product(oracle, mu, seed):
+    """Adjoint of one five-stage low-storage RK4 step (Sec. 3.3), stages
+    recomputed: <lambda, (dU1/dU0) v> with the exact stage-by-stage tangent of
+    the oracle equals <(dU1/dU0)^T lambda, v> of the CUDA path.  The step
+    itself is checked against the oracle's integrator first."""
+    prob, U = _dg_problem(seed, nk=2, mu=mu, Nlo=1, Nhi=4)
+    dt = 2e-4
+    ctx = ctx_for(prob, N_min=1, N_max=7, opts={"integrator": 1})
+    rng = np.random.default_rng(seed)
+    lam = rng.standard_normal(U.size)
+    Ubar = ctx.rk_step_vjp(to_dev(U), dt, to_dev(lam)).cpu().numpy()
+    U1, _ = oracle.lsrk4(prob, U, 1, dt_fixed=dt)
+    for _ in range(3):
+        v = rng.standard_normal(U.size) * np.abs(U).mean()
+        Uc, Jv = _lsrk4_step_tangent(oracle, prob, U, v, dt)
+        assert np.abs(Uc - U1).max() <= 1e-13 * np.abs(U1).max()
+        lhs, rhs = float(np.dot(lam, Jv)), float(np.dot(Ubar, v))
+        scale = float(np.abs(lam * Jv).sum())
+        assert abs(lhs - rhs) <= 1e-11 * scale, (lhs, rhs, scale)
     ctx.close()
 
 

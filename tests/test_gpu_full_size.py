@@ -130,3 +130,30 @@ def test_mixing_layer_and_hp_shock_full(oracle, case):
     ctx.autotune()
     assert_rhs_close(oracle, prob, U, ctx.eval_rhs(to_dev(U)).cpu().numpy())
     ctx.close()
+
+
+def test_mortar_half_refined_cube_full(oracle):
+    """The benchmark's non-conforming workload (62k elements, 8M DOFs, type-3
+    mortars on both x interfaces, N in 2..5, 5 % FV): R(U) of the whole mesh and
+    the time step against the FP64 oracle.  Bound as for the turbulence case
+    (4e, at least 2e-12), e the FP64 oracle's own error on the same generator at
+    k = 8, scaled by the ratio of element sizes 24/8: for the same smooth field R
+    stays O(1) while the summed terms grow like 1/h, and so does the rounding
+    relative to R (the oracle's own error at k = 4, 8, 12: 2.0e-13, 6.8e-13,
+    1.1e-12)."""
+    from paper_2502_19342_gb300 import dgfv
+    prob, U = W.half_refined_wave(24)
+    ctx = dgfv.Context(prob, N_min=1, N_max=7, opts=dict(cfl_c=0.5, cfl_v=0.5))
+    ctx.set_state(to_dev(U))
+    R = ctx.eval_rhs(to_dev(U)).cpu().numpy()
+    Ro = oracle.eval_rhs(prob, U)
+    assert np.isfinite(Ro).all()
+    s, Us = W.half_refined_wave(8)
+    e = max(field_errors(s, oracle.eval_rhs(s, Us), oracle.eval_rhs_extended(s, Us)))
+    bound = max(2 * RTOL, 4 * e * 24 / 8)
+    errs = field_errors(prob, R, Ro)
+    assert all(x <= bound for x in errs), f"R: per-field errors {errs}, bound {bound}"
+    dt = ctx.compute_dt(to_dev(U))
+    dto = oracle.dt(prob, U, 0.5, 0.5)
+    assert abs(dt[0] - dto[0]) <= 1e-13 * dto[0]
+    ctx.close()

@@ -2,8 +2,8 @@
 (mortar interfaces of types 1-3, Sec. 3.2.3): the mortar matrices of the
 operator bank, R(U) with random hp/FV patterns (LG, LGL and the split form,
 every flux choice), SSP-RK3 steps on the half-refined cube of Sec. 4.1 with a
-pattern redrawn between steps, free-stream preservation, adaptation, and the
-adjoint's refusal of mortar meshes."""
+pattern redrawn between steps, free-stream preservation, adaptation, the
+adjoint through the mortars, and the refusal of malformed chains."""
 import numpy as np
 import pytest
 
@@ -138,16 +138,54 @@ def test_adapt_on_mortar_chain_matches_oracle(oracle):
     ctx.close()
 
 
-def test_mortar_mesh_errors():
-    """Bad chains are refused at set-up; the adjoint refuses mortar meshes."""
+def test_bad_chains_are_refused():
+    """Neighbouring domains whose ny or nz differ by other than 1:1 or 2:1, or
+    that are finer in y on one side and in z on the other, are refused."""
     from paper_2502_19342_gb300 import dgfv
     prob, U = _all_types(13, fv_frac=0.0, Nhi=4)
-    bad = dict(prob, dims=np.array([[2, 2, 2], [2, 6, 2]], np.int32), lo=prob["lo"][:2], hi=prob["hi"][:2],
-               N=prob["N"][:32], fv=prob["fv"][:32])
-    with pytest.raises(dgfv.DgfvError):
-        ctx_for(bad)
-    ctx = ctx_for(prob)
-    ctx.set_state(to_dev(U))
-    with pytest.raises(dgfv.DgfvError):
-        ctx.rhs_vjp(to_dev(U), to_dev(np.ones_like(U)))
+    for dims in ([[2, 2, 2], [2, 6, 2]], [[2, 4, 2], [2, 2, 4]]):
+        dd = np.array(dims, np.int32)
+        ne = int(np.prod(dd, axis=1).sum())
+        bad = dict(prob, dims=dd, lo=prob["lo"][:2], hi=prob["hi"][:2], N=prob["N"][:ne], fv=prob["fv"][:ne])
+        with pytest.raises(dgfv.DgfvError):
+            ctx_for(bad)
+
+
+@pytest.mark.parametrize("seed,mu,nodes", [(14, 2e-3, 0), (15, 0.0, 0), (16, 3e-3, 1)])
+def test_rhs_vjp_on_mortar_chain_dot_product(oracle, seed, mu, nodes):
+    """The adjoint through the mortars (the interpolation to the virtual sides
+    and the projection back, transposed): <R_bar, J v> with the oracle's exact
+    dual-number JVP equals <J^T R_bar, v> of the CUDA path, DG elements of
+    degrees 1..6 on every mortar type."""
+    prob, U = _all_types(seed, fv_frac=0.0, Nhi=6, mu=mu, nodes=nodes)
+    rng = np.random.default_rng(seed)
+    Rbar = rng.standard_normal(U.size)
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    Ubar = ctx.rhs_vjp(to_dev(U), to_dev(Rbar)).cpu().numpy()
+    for _ in range(3):
+        v = rng.standard_normal(U.size) * 1e-2 * np.abs(U).mean()
+        _, Jv = oracle.eval_rhs_jvp(prob, U, v)
+        lhs, rhs = float(np.dot(Rbar, Jv)), float(np.dot(Ubar, v))
+        scale = float(np.abs(Rbar * Jv).sum())
+        assert abs(lhs - rhs) <= 1e-11 * scale, (lhs, rhs, scale)
+    ctx.close()
+
+
+def test_rhs_vjp_on_mortar_chain_columns(oracle):
+    """A tiny chain (a type-3 mortar each way, 10 elements of degree 1-2): the
+    whole J^T R_bar entry by entry against the oracle's JVP columns."""
+    sp = W.species_set([W.AIR, W.HELIUM], mu=2e-3)
+    doms = W.chain_domains([(1, 2, 2, 0.5), (1, 1, 1, 0.5)])
+    prob = W.make_problem(doms, sp, n_fv=8, N=W.random_degrees(5, 1, 2, 3), chain=1)
+    U = W.smooth_random_state(prob, 3, amp=0.1)
+    rng = np.random.default_rng(3)
+    Rbar = rng.standard_normal(U.size)
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    Ubar = ctx.rhs_vjp(to_dev(U), to_dev(Rbar)).cpu().numpy()
+    ref = np.zeros(U.size)
+    for j in range(U.size):
+        e = np.zeros(U.size)
+        e[j] = 1.0
+        ref[j] = np.dot(Rbar, oracle.eval_rhs_jvp(prob, U, e)[1])
+    np.testing.assert_allclose(Ubar, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
     ctx.close()
