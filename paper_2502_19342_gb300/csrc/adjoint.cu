@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(256) k_adj_vol_a(Params P, Tiles T, const doub
 template <int NK>
 __global__ void __launch_bounds__(128) k_adj_point(Params P, Tiles T, const double* __restrict__ U,
                                                    const double* __restrict__ gf, double* __restrict__ Ub,
-                                                   double* __restrict__ gvol) {
+                                                   double* __restrict__ gvol, int split) {
     constexpr int V = NK + 4;
     const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], n = T.n[blockIdx.x];
     const int n3 = n * n * n, per = 3 * V * n3;
@@ -331,13 +331,110 @@ __global__ void __launch_bounds__(128) k_adj_point(Params P, Tiles T, const doub
             Fb[x] = in[(per + x * n3)];
             g[x] = visc ? in[x * n3] : 0.0;
         }
-        volume_point_rev<NK>(P.ph, u, g, Fb, ub, gb);
+        volume_point_rev<NK>(P.ph, u, g, Fb, ub, gb, !split);  // split form: k_adj_split has the convective part
 #pragma unroll
         for (int v = 0; v < V; ++v) Ub[off + (int64_t)v * n3 + c] = ub[v];
         if (visc)
 #pragma unroll
             for (int x = 0; x < 3 * V; ++x) gvol[3 * off + (int64_t)x * n3 + c] = gb[x];
     }
+}
+
+// k_adj_split (split form on LGL nodes, Sec. 3.5): reverse of the two-point
+// volume term -rh_d sum_m S_im F#(t_i, t_m) of R_i.  Per tile: the tuples of
+// every node; one thread per line (element, direction d, (a, b)) visits every
+// pair i <= m once, F#_bar = -rh_d (S_im R_bar_i + S_mi R_bar_m) (the diagonal
+// -rh_d S_ii R_bar_i), and adds the tuple adjoints of both nodes (shared-memory
+// atomics: the three directions meet at every node); per node the tuple and
+// primitive reverses add to U_bar.
+template <int NK, int NP>
+__device__ __forceinline__ void adj_split_body(const Params& P, const Tiles& T, const double* __restrict__ U,
+                                               const double* __restrict__ Rb, double* __restrict__ Ub) {
+    constexpr int V = NK + 4, NT = 6 + NK;
+    extern __shared__ double sm[];
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x];
+    const int n = NP > 0 ? NP : T.n[blockIdx.x];
+    const int n2 = n * n, n3 = n2 * n;
+    double* sS = sm;                    // n*n split matrix
+    double* sK = sS + n * n;            // count * NT * n3 tuples
+    double* sKb = sK + count * NT * n3; // count * NT * n3 tuple adjoints
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) sS[i] = B(P, P.bi.dsplit[n])[i];
+    for (int idx = threadIdx.x; idx < count * n3; idx += blockDim.x) {
+        const int el = idx / n3, c = idx % n3;
+        const double* src = U + P.t.off[T.items[first + el]] + c;
+        double u[V], t[NT];
+#pragma unroll
+        for (int v = 0; v < V; ++v) u[v] = src[(int64_t)v * n3];
+        Prim<NK> s;
+        prim<NK>(P.ph, u, s);
+        kep_tuple<NK>(s, t);
+#pragma unroll
+        for (int q = 0; q < NT; ++q) {
+            sK[(el * NT + q) * n3 + c] = t[q];
+            sKb[(el * NT + q) * n3 + c] = 0.0;
+        }
+    }
+    __syncthreads();
+    const int lines = 3 * n2;
+    for (int idx = threadIdx.x; idx < count * lines; idx += blockDim.x) {
+        const int el = idx / lines, r = idx % lines, d = r / n2, p = r % n2, a = p % n, b = p / n;
+        const int e = T.items[first + el];
+        const double rh = P.t.rh[3 * e + d];
+        const double* K = sK + el * NT * n3;
+        double* Kb = sKb + el * NT * n3;
+        const double* R = Rb + P.t.off[e];
+        for (int i = 0; i < n; ++i) {
+            const int ci = node_index(n, d, i, a, b);
+            double ti[NT], Ri[V];
+#pragma unroll
+            for (int q = 0; q < NT; ++q) ti[q] = K[q * n3 + ci];
+#pragma unroll
+            for (int v = 0; v < V; ++v) Ri[v] = R[(int64_t)v * n3 + ci];
+            for (int m = i; m < n; ++m) {
+                const int cm = node_index(n, d, m, a, b);
+                double tm[NT], Fb[V], tb[NT];
+#pragma unroll
+                for (int q = 0; q < NT; ++q) {
+                    tm[q] = K[q * n3 + cm];
+                    tb[q] = 0.0;
+                }
+                const double Sim = sS[i * n + m], Smi = sS[m * n + i];
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    Fb[v] = -rh * (m == i ? Sim * Ri[v] : fma(Sim, Ri[v], Smi * R[(int64_t)v * n3 + cm]));
+                kep_flux_rev<NK>(ti, tm, d, Fb, tb);
+#pragma unroll
+                for (int q = 0; q < NT; ++q) {
+                    atomicAdd(&Kb[q * n3 + ci], tb[q]);
+                    atomicAdd(&Kb[q * n3 + cm], tb[q]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < count * n3; idx += blockDim.x) {
+        const int el = idx / n3, c = idx % n3;
+        const int64_t off = P.t.off[T.items[first + el]];
+        double u[V], tb[NT], ub[V] = {};
+#pragma unroll
+        for (int v = 0; v < V; ++v) u[v] = U[off + (int64_t)v * n3 + c];
+#pragma unroll
+        for (int q = 0; q < NT; ++q) tb[q] = sKb[(el * NT + q) * n3 + c];
+        Prim<NK> s;
+        prim<NK>(P.ph, u, s);
+        PrimBar<NK> bb;
+        zero(bb);
+        kep_tuple_rev<NK>(s, tb, bb);
+        prim_rev<NK>(P.ph, u, s, bb, ub);
+#pragma unroll
+        for (int v = 0; v < V; ++v) Ub[off + (int64_t)v * n3 + c] += ub[v];
+    }
+}
+
+template <int NK>
+__global__ void __launch_bounds__(256) k_adj_split(Params P, Tiles T, const double* __restrict__ U,
+                                                   const double* __restrict__ Rb, double* __restrict__ Ub) {
+    adj_split_body<NK, 0>(P, T, U, Rb, Ub);
 }
 
 // k_adj_vol_b (viscous only): g_bar += trace^T of the face gradient adjoints;
@@ -576,11 +673,23 @@ size_t adj_volume_smem_bytes(int nk, int n, int count) {
 }
 
 void launch_adj_vol_a(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
-                      const double* Rb, double* Ub, double* gvol, double* gf, cudaStream_t s) {
+                      const double* Rb, double* Ub, double* gvol, double* gf, cudaStream_t s, int split) {
     if (ntiles <= 0) return;
     DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_adj_vol_a<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                        k_adj_vol_a<NK><<<ntiles, 256, smem, s>>>(P, T, U, Rb, gf),
-                       k_adj_point<NK><<<ntiles, 128, 0, s>>>(P, T, U, gf, Ub, gvol)));
+                       k_adj_point<NK><<<ntiles, 128, 0, s>>>(P, T, U, gf, Ub, gvol, split)));
+}
+
+size_t adj_split_smem_bytes(int nk, int n, int count) {
+    const int NT = 6 + nk, n3 = n * n * n;
+    return sizeof(double) * (size_t)(n * n + 2 * count * NT * n3);
+}
+
+void launch_adj_split(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
+                      const double* Rb, double* Ub, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_adj_split<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       k_adj_split<NK><<<ntiles, 256, smem, s>>>(P, T, U, Rb, Ub)));
 }
 
 void launch_adj_vol_b(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, size_t smem,

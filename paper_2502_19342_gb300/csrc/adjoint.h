@@ -23,7 +23,11 @@ void launch_adj_faces(int nk, const Params& P, const AdjBuffers& A, const Faces&
                       int nconf, const int32_t* mixed, int nmixed, cudaStream_t s);
 size_t adj_volume_smem_bytes(int nk, int n, int count);
 void launch_adj_vol_a(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
-                      const double* Rb, double* Ub, double* gvol, double* gf, cudaStream_t s);
+                      const double* Rb, double* Ub, double* gvol, double* gf, cudaStream_t s, int split = 0);
+// Split form (Sec. 3.5): reverse of the two-point volume term, added to Ub.
+size_t adj_split_smem_bytes(int nk, int n, int count);
+void launch_adj_split(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
+                      const double* Rb, double* Ub, cudaStream_t s);
 void launch_adj_vol_b(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, size_t smem,
                       const double* gvol, double* Ub, cudaStream_t s);
 void launch_adj_lift(int nk, const Params& P, const AdjBuffers& A, const Faces& F, const int32_t* list, int nfaces,

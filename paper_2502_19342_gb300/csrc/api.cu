@@ -141,7 +141,7 @@ struct dgfv_ctx {
     double *d_S1 = nullptr, *d_S2 = nullptr, *d_B1 = nullptr, *d_B2 = nullptr, *d_W = nullptr;
     double* d_gvol = nullptr;  // nodal gradient adjoint, 3 x state
     double* d_gf = nullptr;    // lifted gradient and volume-flux adjoint per node, 6 x state
-    size_t adj_smem = 0;
+    size_t adj_smem = 0, adj_split_smem = 0;
     std::vector<void*> allocs;
 };
 
@@ -374,9 +374,13 @@ int apply_layout(dgfv_ctx* c) {
         }
     c->dg.smem = sm;
     size_t asm_ = 0;
-    for (int t = 0; t < (int)c->dg.first.size(); ++t)
+    size_t ssm = 0;
+    for (int t = 0; t < (int)c->dg.first.size(); ++t) {
         asm_ = std::max(asm_, adj_volume_smem_bytes(c->nk, c->dg.n[t], c->dg.count[t]));
+        ssm = std::max(ssm, adj_split_smem_bytes(c->nk, c->dg.n[t], c->dg.count[t]));
+    }
     c->adj_smem = asm_;
+    c->adj_split_smem = ssm;
     TRY(upload_tiles(c, c->all));
     TRY(upload_tiles(c, c->dg));
     TRY(upload_tiles(c, c->fvt));
@@ -1000,7 +1004,6 @@ int dgfv_compute_dt_noalloc(dgfv_ctx* c, const double* d_U, double* d_out3, void
 
 static int adj_prepare(dgfv_ctx* c) {
     if (c->n_fv_elems) return fail(c, DGFV_ERR_ARG, "the adjoint supports DG elements only (the pattern has FV elements)");
-    if (c->opts.split_form) return fail(c, DGFV_ERR_ARG, "the adjoint supports the standard volume integral only");
     if (c->adj_ready) return DGFV_OK;
     TRY(dalloc(c, &c->d_fbar, c->cap_fpts * c->V));
     TRY(dalloc(c, &c->d_ubar, c->cap_fpts * c->V));
@@ -1034,7 +1037,9 @@ static void enqueue_vjp(dgfv_ctx* c, const double* U, const double* Rb, double* 
     launch_adj_surface(c->nk, P, A, c->dg.view(), c->dg.ntiles, Rb, s);
     launch_adj_mortar_virt(c->nk, P, A, MT, c->n_virt, 0, s);
     // recomputed gradient (and its traces), volume integral^T, nodal reverse
-    launch_adj_vol_a(c->nk, P, c->dg.view(), c->dg.ntiles, c->adj_smem, U, Rb, Ub, c->d_gvol, c->d_gf, s);
+    launch_adj_vol_a(c->nk, P, c->dg.view(), c->dg.ntiles, c->adj_smem, U, Rb, Ub, c->d_gvol, c->d_gf, s,
+                     c->opts.split_form);
+    if (c->opts.split_form) launch_adj_split(c->nk, P, c->dg.view(), c->dg.ntiles, c->adj_split_smem, U, Rb, Ub, s);
     if (c->ph.viscous) launch_mortar_in(c->nk, P, MT, c->n_virt, 1, s);
     launch_adj_faces(c->nk, P, A, F, c->conf.view(), c->conf.ntiles, c->flux.d, c->flux.count, s);
     if (c->ph.viscous) {

@@ -236,15 +236,33 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
     for (int t = threadIdx.x; t < 3 * nif; t += blockDim.x) {
         const int d = t / nif, fidx = t - d * nif;
         const int m = fidx % (n - 1), p = fidx / (n - 1), a = p % n, b = p / n;
-        double uL[V], uR[V], gL[3 * V], gR[3 * V], F[V];
+        // F* = F^c*(uL, uR) + (F^v(uL, gL) + F^v(uR, gR))/2, the two viscous
+        // fluxes one after the other (one gradient live at a time: fewer
+        // registers than the face kernels' interface_flux)
+        double uL[V], uR[V], F[V];
         recon(d, m, a, b, +1, uL);
         recon(d, m + 1, a, b, -1, uR);
-        int i, j, k;
-        coords(d, m, a, b, i, j, k);
-        if (P.ph.viscous) grad(i, j, k, gL);
-        coords(d, m + 1, a, b, i, j, k);
-        if (P.ph.viscous) grad(i, j, k, gR);
-        interface_flux<NK>(P.ph, uL, gL, uR, gR, d, F, true);
+        Prim<NK> sL, sR;
+        prim<NK>(P.ph, uL, sL);
+        prim<NK>(P.ph, uR, sR);
+        if (use_roe(P.ph, true))
+            riemann_roe<NK>(P.ph, uL, sL, uR, sR, d, F);
+        else
+            riemann_llf<NK>(uL, sL, uR, sR, d, F);
+        if (P.ph.viscous) {
+#pragma unroll 1
+            for (int side = 0; side < 2; ++side) {
+                int i, j, k;
+                coords(d, m + side, a, b, i, j, k);
+                double g[3 * V], Fv[V];
+                grad(i, j, k, g);
+                PrimGrad<NK> G;
+                prim_grad<NK>(P.ph, side ? sR : sL, g, G);
+                flux_visc<NK>(P.ph, side ? sR : sL, G, d, Fv);
+#pragma unroll
+                for (int v = 0; v < V; ++v) F[v] = fma(0.5, Fv[v], F[v]);
+            }
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) sF[(d * V + v) * nif + fidx] = F[v];
     }

@@ -230,7 +230,7 @@ DGFV_HD void prim_grad_rev(const DevPhys& P, const Prim<NK>& s, const double* g,
 // given F_bar[d*V + v], accumulate u_bar (V) and g_bar (3V).
 template <int NK>
 DGFV_HD void volume_point_rev(const DevPhys& P, const double* u, const double* g, const double* Fb, double* ub,
-                              double* gb) {
+                              double* gb, bool conv = true) {
     Prim<NK> s;
     prim<NK>(P, u, s);
     PrimBar<NK> b;
@@ -243,11 +243,49 @@ DGFV_HD void volume_point_rev(const DevPhys& P, const double* u, const double* g
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        flux_conv_rev<NK>(u, s, d, Fb + d * (NK + 4), ub, b);
+        if (conv) flux_conv_rev<NK>(u, s, d, Fb + d * (NK + 4), ub, b);
         if (P.viscous) flux_visc_rev<NK>(P, s, G, d, Fb + d * (NK + 4), Gb, b);
     }
     if (P.viscous) prim_grad_rev<NK>(P, s, g, G, Gb, gb, b);
     prim_rev<NK>(P, u, s, b, ub);
+}
+
+// Reverse of kep_flux (physics.cuh): the flux is a function of the arithmetic
+// means of the two tuples, so both tuples receive half of each mean's adjoint;
+// tb += that half (call once per argument).
+template <int NK>
+DGFV_HD void kep_flux_rev(const double* a, const double* b, int d, const double* Fb, double* tb) {
+    const double r = 0.5 * (a[0] + b[0]), vd = 0.5 * (a[1 + d] + b[1 + d]);
+    const double mass = r * vd;
+    double massb = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        massb += Fb[k] * 0.5 * (a[6 + k] + b[6 + k]);
+        tb[6 + k] += 0.5 * Fb[k] * mass;
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        massb += Fb[NK + j] * 0.5 * (a[1 + j] + b[1 + j]);
+        tb[1 + j] += 0.5 * Fb[NK + j] * mass;
+    }
+    tb[4] += 0.5 * Fb[NK + d];
+    massb += Fb[NK + 3] * 0.5 * (a[5] + b[5]);
+    tb[5] += 0.5 * Fb[NK + 3] * mass;
+    tb[0] += 0.5 * massb * vd;
+    tb[1 + d] += 0.5 * massb * r;
+}
+
+// Reverse of kep_tuple: t = (rho, v, p, H = E + p/rho, Y_k).
+template <int NK>
+DGFV_HD void kep_tuple_rev(const Prim<NK>& s, const double* tb, PrimBar<NK>& b) {
+    b.rho += tb[0];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) b.v[i] += tb[1 + i];
+    b.p += tb[4] + tb[5] * s.irho;
+    b.E += tb[5];
+    b.irho += tb[5] * s.p;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) b.Y[k] += tb[6 + k];
 }
 
 // Adjoint of the interface flux F* = LLF(uL, uR) + (F^v(uL,gL) + F^v(uR,gR))/2 in +x_d:

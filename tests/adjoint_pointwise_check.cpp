@@ -1,6 +1,8 @@
 // Host check of the hand-written pointwise adjoints of the CUDA path
 // (physics_adj.cuh) against central finite differences of the forward
-// functions (physics.cuh), compiled for the host by the test suite.
+// functions (physics.cuh), compiled for the host by the test suite: volume
+// node and face point (LLF and Roe-HH, transonic states for the entropy fix,
+// constant and Sutherland viscosity) and the split form's two-point flux.
 #include <cstdio>
 #include <cstdlib>
 #include <random>
@@ -188,6 +190,72 @@ int check_transonic(bool visc, int seed) {
     return bad;
 }
 
+// Split form (Sec. 3.5): the two-point KEP flux of two states through their
+// tuples, reversed with kep_flux_rev (half of each mean's adjoint per tuple),
+// kep_tuple_rev and prim_rev.
+template <int NK>
+int check_kep(int seed) {
+    constexpr int V = NK + 4, NT = 6 + NK;
+    std::mt19937 rng(seed);
+    std::normal_distribution<double> N01(0.0, 1.0);
+    DevPhys P = phys<NK>(false);
+    auto flux = [&](const double* ua, const double* ub, int d, double* F) {
+        Prim<NK> sa, sb;
+        prim<NK>(P, ua, sa);
+        prim<NK>(P, ub, sb);
+        double ta[NT], tb[NT];
+        kep_tuple<NK>(sa, ta);
+        kep_tuple<NK>(sb, tb);
+        kep_flux<NK>(ta, tb, d, F);
+    };
+    int bad = 0;
+    for (int trial = 0; trial < 30; ++trial) {
+        const int d = trial % 3;
+        double ua[V], ub[V], Fb[V], da[V], db[V];
+        state<NK>(rng, P, ua);
+        state<NK>(rng, P, ub);
+        for (int v = 0; v < V; ++v) {
+            Fb[v] = N01(rng);
+            da[v] = 0.05 * N01(rng) * std::fabs(ua[v]);
+            db[v] = 0.05 * N01(rng) * std::fabs(ub[v]);
+        }
+        Prim<NK> sa, sb;
+        prim<NK>(P, ua, sa);
+        prim<NK>(P, ub, sb);
+        double ta[NT], tb[NT], tab[NT] = {}, tbb[NT] = {};
+        kep_tuple<NK>(sa, ta);
+        kep_tuple<NK>(sb, tb);
+        kep_flux_rev<NK>(ta, tb, d, Fb, tab);
+        kep_flux_rev<NK>(ta, tb, d, Fb, tbb);
+        double uab[V] = {}, ubb[V] = {};
+        PrimBar<NK> ba, bb;
+        zero(ba);
+        zero(bb);
+        kep_tuple_rev<NK>(sa, tab, ba);
+        kep_tuple_rev<NK>(sb, tbb, bb);
+        prim_rev<NK>(P, ua, sa, ba, uab);
+        prim_rev<NK>(P, ub, sb, bb, ubb);
+        const double eps = 1e-6;
+        double ap[V], am[V], bp[V], bm[V], Fp[V], Fm[V];
+        for (int v = 0; v < V; ++v) {
+            ap[v] = ua[v] + eps * da[v]; am[v] = ua[v] - eps * da[v];
+            bp[v] = ub[v] + eps * db[v]; bm[v] = ub[v] - eps * db[v];
+        }
+        flux(ap, bp, d, Fp);
+        flux(am, bm, d, Fm);
+        double fd = 0.0, ad = 0.0;
+        for (int v = 0; v < V; ++v) {
+            fd += Fb[v] * (Fp[v] - Fm[v]) / (2 * eps);
+            ad += uab[v] * da[v] + ubb[v] * db[v];
+        }
+        if (std::fabs(fd - ad) > 1e-7 + 1e-6 * std::fabs(fd)) {
+            std::printf("KEP NK=%d trial %d: fd %.12e adjoint %.12e\n", NK, trial, fd, ad);
+            ++bad;
+        }
+    }
+    return bad;
+}
+
 int main() {
     int bad = 0;
     for (int visc = 0; visc < 2; ++visc) {
@@ -208,6 +276,9 @@ int main() {
         bad += check_transonic<2>(visc, 23 + visc);
         bad += check_transonic<3>(visc, 25 + visc);
     }
+    bad += check_kep<1>(31);
+    bad += check_kep<2>(32);
+    bad += check_kep<3>(33);
     std::printf("%s (%d mismatches)\n", bad ? "FAIL" : "OK", bad);
     return bad ? 1 : 0;
 }

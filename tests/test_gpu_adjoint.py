@@ -208,13 +208,23 @@ def test_autograd_function_backward_is_the_adjoint():
     ctx.close()
 
 
-def test_adjoint_rejects_split_form():
-    from paper_2502_19342_gb300 import dgfv
-    prob, U = _dg_problem(12, nk=2, nodes=1)
+@pytest.mark.parametrize("nk,mu,seed,riemann", [(2, 2e-3, 12, 0), (3, 0.0, 13, 1), (1, 1e-3, 14, 0), (3, 3e-3, 15, 2)])
+def test_split_form_rhs_vjp_dot_product(oracle, nk, mu, seed, riemann):
+    """Split form on LGL nodes (Sec. 3.5): the two-point volume term's reverse
+    (k_adj_split) with the standard viscous part, against the oracle's exact
+    dual-number JVP of its split form."""
+    prob, U = _dg_problem(seed, nk=nk, mu=mu, nodes=1, riemann=riemann, Nlo=1, Nhi=6)
     prob["split"] = 1
+    rng = np.random.default_rng(seed)
+    Rbar = rng.standard_normal(U.size)
     ctx = ctx_for(prob, N_min=1, N_max=7)
-    with pytest.raises(dgfv.DgfvError):
-        ctx.rhs_vjp(to_dev(U), to_dev(np.ones_like(U)))
+    Ubar = ctx.rhs_vjp(to_dev(U), to_dev(Rbar)).cpu().numpy()
+    for _ in range(3):
+        v = rng.standard_normal(U.size) * 1e-2 * np.abs(U).mean()
+        _, Jv = oracle.eval_rhs_jvp(prob, U, v)
+        lhs, rhs = float(np.dot(Rbar, Jv)), float(np.dot(Ubar, v))
+        scale = float(np.abs(Rbar * Jv).sum())
+        assert abs(lhs - rhs) <= 1e-11 * scale, (lhs, rhs, scale)
     ctx.close()
 
 
