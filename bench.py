@@ -286,6 +286,70 @@ def adjoint_cost(steps=50):
             "note": "adjoint step = 3 vector-Jacobian products (+2 forward stages when the stages are recomputed)"}
 
 
+def adjoint_hybrid_cost(steps=10):
+    """Cost of the adjoint on a hybrid DG/FV pattern: the hp-mixed shock case
+    after two adaptation cycles (N in 2..6 and FV sub-cells), pattern and dt
+    then frozen; `steps` SSP-RK3 steps forward (plain, and keeping the stage
+    states) against their adjoints from stored and from recomputed stages,
+    with a seeded final-state adjoint.  CUDA events."""
+    import torch
+    from paper_2502_19342_gb300 import dgfv, workloads as W
+    prob, U = W.hp_shock(0, y_bg=0.01)
+    ctx = dgfv.Context(prob, N_min=2, N_max=6, opts=dict(cfl_c=0.5, cfl_v=0.5, thresholds=W.THRESHOLDS))
+    ctx.set_state(torch.from_numpy(U).cuda())
+    for _ in range(2):
+        ctx.adapt()
+        ctx.rk_steps(5, -1.0, want_dt=False)
+    U0 = ctx.get_state()
+    dt = ctx.compute_dt(U0)[0]
+    N_now, fv_now = ctx.get_degrees()
+    ck = [torch.empty_like(U0) for _ in range(steps + 1)]
+    st = [(torch.empty_like(U0), torch.empty_like(U0)) for _ in range(steps)]
+    lam = [torch.empty_like(U0) for _ in range(2)]
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    g = torch.randn(U0.shape, dtype=U0.dtype, device="cuda", generator=gen)
+    ctx.rk_step_vjp_stages((U0, U0, U0), dt, g, lam[0])  # warm-up of the adjoint paths
+    ctx.rk_step_vjp(U0, dt, g, lam[1])
+    s = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+    torch.cuda.synchronize()
+    ev[0].record(s)
+    ctx.set_state(U0)
+    for k in range(steps):
+        ctx.get_state(ck[k])
+        ctx.rk_step(dt, want_dt=False)
+    ev[1].record(s)
+    ctx.set_state(U0)
+    for k in range(steps):
+        ctx.rk_step_save(dt, *st[k])
+    ev[2].record(s)
+    a = g
+    for k in range(steps - 1, -1, -1):
+        b = lam[k % 2]
+        ctx.rk_step_vjp_stages((ck[k], *st[k]), dt, a, b)
+        a = b
+    ev[3].record(s)
+    grad_stored = a.clone()
+    ev[4].record(s)
+    a = g
+    for k in range(steps - 1, -1, -1):
+        b = lam[k % 2]
+        ctx.rk_step_vjp(ck[k], dt, a, b)
+        a = b
+    ev[5].record(s)
+    torch.cuda.synchronize()
+    fwd, fsave, bst, brc = (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]),
+                            ev[4].elapsed_time(ev[5]))
+    same = bool(torch.equal(grad_stored, a))
+    ctx.close()
+    return {"workload": "hp-mixed shock case after 2 adaptation cycles, pattern and dt frozen (hybrid DG/FV)",
+            "steps": steps, "fv_elements": int(fv_now.sum()), "elements": int(len(N_now)),
+            "forward_ms_per_step": fwd / steps, "forward_keeping_stages_ms_per_step": fsave / steps,
+            "adjoint_ms_per_step_stored_stages": bst / steps, "adjoint_over_forward": bst / fwd,
+            "adjoint_ms_per_step_recomputed_stages": brc / steps, "adjoint_over_forward_recomputed": brc / fwd,
+            "gradients_identical": same}
+
+
 def split_form_run(nel, warmup=2, steps=1):
     """The turbulence workload with the jet's scheme (Sec. 5.1): split-form DGSEM
     on LGL nodes with the kinetic-energy-preserving flux, Roe-HH between DG
@@ -668,6 +732,7 @@ def main():
                 "whole_rhs_tflops": per_dof * units / (ms * 1e-3) / 1e12}
         cpu = None if args.no_cpu else cpu_baseline(dict(prob, N=N_now, fv=fv_now))
         adjoint = adjoint_cost()
+        adjoint["hybrid_dg_fv"] = adjoint_hybrid_cost()
         batched = None if args.no_batched else batched_comparison()
         split = None if args.no_split else split_form_run(args.nel)
         tgv = None if args.no_tgv else tgv_run()

@@ -204,11 +204,12 @@ int dgfv_rk_steps(dgfv_ctx* ctx, int n_steps, double dt, double* dt_used, void* 
 
 /* Adjoint (vector-Jacobian product) of the right-hand side:
  * d_Ubar = (dR/dU)^T d_Rbar at the state d_U, with the degree pattern frozen.
- * Supported for patterns without FV elements (DGFV_ERR_ARG otherwise): LG or
- * LGL nodes, the standard or the split-form volume integral, every flux
- * choice (without FV elements the hybrid choice is Roe-HH everywhere),
- * constant or Sutherland viscosity, conforming and mortar meshes (the mortar
- * maps enter transposed).  Device arrays in the current layout;
+ * The hp/FV pattern is frozen: DG and FV sub-cell elements (the minmod
+ * limiter differentiated along the branch the forward evaluation takes), LG
+ * or LGL nodes, the standard or the split-form volume integral, every flux
+ * choice, constant or Sutherland viscosity, conforming meshes and mortar
+ * meshes without FV elements (DGFV_ERR_ARG for FV elements on a mesh with
+ * mortars).  Device arrays in the current layout;
  * d_Ubar must not alias d_U or d_Rbar.  Uses the context's forward face
  * buffers (a later eval_rhs recomputes them).  The first adjoint call
  * allocates the adjoint scratch (face adjoints and four state buffers). */

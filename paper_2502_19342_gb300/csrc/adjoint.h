@@ -32,6 +32,15 @@ void launch_adj_vol_b(int nk, const Params& P, const AdjBuffers& A, const Tiles&
                       const double* gvol, double* Ub, cudaStream_t s);
 void launch_adj_lift(int nk, const Params& P, const AdjBuffers& A, const Faces& F, const int32_t* list, int nfaces,
                      cudaStream_t s);
+// FV sub-cell elements (one tile per element): the surface adjoint, then after
+// the face and lifting adjoints the element reverse and the gather of the
+// neighbour-layer adjoints into the neighbours' U_bar (all elements).
+size_t adj_fv_smem_bytes(int nk, int nfv);
+void launch_adj_surface_fv(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, const double* Rb,
+                           cudaStream_t s);
+void launch_adj_fv_elements(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles,
+                            const double* U, const double* Rb, double* Ub, double* gf, double* gvol, double* fvs,
+                            int64_t cap_state, int n_elem, cudaStream_t s);
 void launch_adj_prolong(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, double* Ub,
                         cudaStream_t s);
 void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);

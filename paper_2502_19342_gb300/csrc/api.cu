@@ -141,6 +141,7 @@ struct dgfv_ctx {
     double *d_S1 = nullptr, *d_S2 = nullptr, *d_B1 = nullptr, *d_B2 = nullptr, *d_W = nullptr;
     double* d_gvol = nullptr;  // nodal gradient adjoint, 3 x state
     double* d_gf = nullptr;    // lifted gradient and volume-flux adjoint per node, 6 x state
+    double* d_fvs = nullptr;   // FV element adjoint scratch (reconstruction-variable and direct adjoints), 2 x state
     size_t adj_smem = 0, adj_split_smem = 0;
     std::vector<void*> allocs;
 };
@@ -1003,7 +1004,8 @@ int dgfv_compute_dt_noalloc(dgfv_ctx* c, const double* d_U, double* d_out3, void
 }
 
 static int adj_prepare(dgfv_ctx* c) {
-    if (c->n_fv_elems) return fail(c, DGFV_ERR_ARG, "the adjoint supports DG elements only (the pattern has FV elements)");
+    if (c->n_fv_elems && c->n_mort)
+        return fail(c, DGFV_ERR_ARG, "the adjoint does not support FV elements on meshes with mortars");
     if (c->adj_ready) return DGFV_OK;
     TRY(dalloc(c, &c->d_fbar, c->cap_fpts * c->V));
     TRY(dalloc(c, &c->d_ubar, c->cap_fpts * c->V));
@@ -1016,6 +1018,7 @@ static int adj_prepare(dgfv_ctx* c) {
     TRY(dalloc(c, &c->d_W, c->cap_state));
     TRY(dalloc(c, &c->d_gvol, 3 * c->cap_state));
     TRY(dalloc(c, &c->d_gf, 6 * c->cap_state));
+    TRY(dalloc(c, &c->d_fvs, 2 * c->cap_state));
     c->adj_ready = true;
     return DGFV_OK;
 }
@@ -1029,12 +1032,14 @@ static void enqueue_vjp(dgfv_ctx* c, const double* U, const double* Rb, double* 
     // forward face values and lifting values of U (mortars: the virtual small
     // sides' values, the big sides' projected lifting values)
     launch_prolong(c->nk, P, c->all.view(), c->all.ntiles, U, s);
+    if (c->n_fv_elems) launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, U, s);  // FV face states and gradients
     launch_mortar_in(c->nk, P, MT, c->n_virt, 0, s);
     if (c->ph.viscous) {
         launch_face_lift(c->nk, P, F, c->lift.d, c->lift.count, s);
         launch_mortar_out(c->nk, P, MT, c->n_mort, 0, s);
     }
     launch_adj_surface(c->nk, P, A, c->dg.view(), c->dg.ntiles, Rb, s);
+    launch_adj_surface_fv(c->nk, P, A, c->fvt.view(), c->fvt.ntiles, Rb, s);
     launch_adj_mortar_virt(c->nk, P, A, MT, c->n_virt, 0, s);
     // recomputed gradient (and its traces), volume integral^T, nodal reverse
     launch_adj_vol_a(c->nk, P, c->dg.view(), c->dg.ntiles, c->adj_smem, U, Rb, Ub, c->d_gvol, c->d_gf, s,
@@ -1049,6 +1054,9 @@ static void enqueue_vjp(dgfv_ctx* c, const double* U, const double* Rb, double* 
         launch_adj_lift(c->nk, P, A, F, c->lift.d, c->lift.count, s);
     }
     launch_adj_mortar_big(c->nk, P, A, MT, c->n_mort, 1, s);
+    if (c->n_fv_elems)
+        launch_adj_fv_elements(c->nk, P, A, c->fvt.view(), c->fvt.ntiles, U, Rb, Ub, c->d_gf, c->d_gvol, c->d_fvs,
+                               c->cap_state, c->n_elem, s);
     launch_adj_prolong(c->nk, P, A, c->dg.view(), c->dg.ntiles, Ub, s);
 }
 

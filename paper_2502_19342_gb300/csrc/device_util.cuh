@@ -104,4 +104,69 @@ __device__ __forceinline__ void face_map2_t(const double* in, int no, double* ou
     __syncthreads();
 }
 
+// The layer of sub-cell means that an FV neighbour sees across face fq of element
+// q, on N_FV x N_FV points: an FV element's boundary sub-cell means (its face
+// values), or a DG element's solution mapped by V^{DG->FV} (boundary row along
+// the face normal, then both face directions).  All threads of the block take
+// part; ends with a barrier.
+template <int NK>
+__device__ __forceinline__ void fv_layer(const Params& P, const double* __restrict__ U, int q, int fq, int n,
+                                         double* dst, double* sT1, double* sT2) {
+    constexpr int V = NK + 4;
+    const int n2 = n * n, d = fq >> 1;
+    if (P.t.fv[q]) {
+        const double* src = P.b.fu + (P.t.fo[q] + (int64_t)fq * n2) * V;
+        for (int i = threadIdx.x; i < V * n2; i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+        return;
+    }
+    const int nq = P.t.n[q], nq2 = nq * nq, nq3 = nq2 * nq;
+    const double* A = B(P, P.bi.d2f[nq]);  // n x nq
+    const int row = (fq & 1) ? n - 1 : 0;   // sub-cell layer next to the shared face
+    const double* src = U + P.t.off[q];
+    for (int i = threadIdx.x; i < V * nq2; i += blockDim.x) {
+        const int v = i / nq2, p = i % nq2, a = p % nq, b = p / nq;
+        double s = 0.0;
+        for (int m = 0; m < nq; ++m)
+            s = fma(__ldg(A + row * nq + m), src[(int64_t)v * nq3 + node_index(nq, d, m, a, b)], s);
+        sT1[i] = s;
+    }
+    __syncthreads();
+    face_map(sT1, nq, dst, n, A, V, sT2);
+}
+
+// Transpose of fv_layer: Ub (the state adjoint of element q) += layer^T lb,
+// lb the adjoint of the N_FV x N_FV layer across face fq.  FV element: the
+// boundary sub-cells; DG element: V^{DG->FV} transposed in both face
+// directions, then the boundary row along the normal.  Ends with a barrier.
+template <int NK>
+__device__ __forceinline__ void fv_layer_t(const Params& P, int q, int fq, int n, const double* lb, double* Ub,
+                                           double* sT1, double* sT2) {
+    constexpr int V = NK + 4;
+    const int n2 = n * n, d = fq >> 1;
+    if (P.t.fv[q]) {
+        const int n3 = n2 * n, m = (fq & 1) ? n - 1 : 0;
+        double* dst = Ub + P.t.off[q];
+        for (int i = threadIdx.x; i < V * n2; i += blockDim.x) {
+            const int v = i / n2, p = i % n2;
+            dst[(int64_t)v * n3 + node_index(n, d, m, p % n, p / n)] += lb[i];
+        }
+        __syncthreads();
+        return;
+    }
+    const int nq = P.t.n[q], nq2 = nq * nq, nq3 = nq2 * nq;
+    const double* A = B(P, P.bi.d2f[nq]);  // n x nq
+    const int row = (fq & 1) ? n - 1 : 0;
+    face_map_t(lb, n, sT1, nq, A, V, sT2);
+    double* dst = Ub + P.t.off[q];
+    for (int i = threadIdx.x; i < V * nq3; i += blockDim.x) {
+        const int v = i / nq3, c = i % nq3;
+        const int ii = c % nq, jj = (c / nq) % nq, kk = c / nq2;
+        const int m = d == 0 ? ii : (d == 1 ? jj : kk);
+        const int a = d == 0 ? jj : ii, b = d == 2 ? jj : kk;
+        dst[(int64_t)v * nq3 + c] += __ldg(A + row * nq + m) * sT1[v * nq2 + a + nq * b];
+    }
+    __syncthreads();
+}
+
 }  // namespace dgfv

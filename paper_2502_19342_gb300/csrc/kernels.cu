@@ -90,38 +90,6 @@ __global__ void __launch_bounds__(256) k_prolong(Params P, Tiles T, const double
 }
 
 // ---------------------------------------------------------------------------------
-// The layer of sub-cell means that an FV neighbour sees across face fq of element
-// q, on N_FV x N_FV points: an FV element's boundary sub-cell means (its face
-// values), or a DG element's solution mapped by V^{DG->FV} (boundary row along
-// the face normal, then both face directions).  All threads of the block take
-// part; ends with a barrier.
-template <int NK>
-__device__ __forceinline__ void fv_layer(const Params& P, const double* __restrict__ U, int q, int fq, int n,
-                                         double* dst, double* sT1, double* sT2) {
-    constexpr int V = NK + 4;
-    const int n2 = n * n, d = fq >> 1;
-    if (P.t.fv[q]) {
-        const double* src = P.b.fu + (P.t.fo[q] + (int64_t)fq * n2) * V;
-        for (int i = threadIdx.x; i < V * n2; i += blockDim.x) dst[i] = src[i];
-        __syncthreads();
-        return;
-    }
-    const int nq = P.t.n[q], nq2 = nq * nq, nq3 = nq2 * nq;
-    const double* A = B(P, P.bi.d2f[nq]);  // n x nq
-    const int row = (fq & 1) ? n - 1 : 0;   // sub-cell layer next to the shared face
-    const double* src = U + P.t.off[q];
-    for (int i = threadIdx.x; i < V * nq2; i += blockDim.x) {
-        const int v = i / nq2, p = i % nq2, a = p % nq, b = p / nq;
-        double s = 0.0;
-        for (int m = 0; m < nq; ++m)
-            s = fma(__ldg(A + row * nq + m), src[(int64_t)v * nq3 + node_index(nq, d, m, a, b)], s);
-        sT1[i] = s;
-    }
-    __syncthreads();
-    face_map(sT1, nq, dst, n, A, V, sT2);
-}
-
-// ---------------------------------------------------------------------------------
 // k_fv: one CTA per FV element (n = N_FV sub-cells per direction).
 //   neighbour value across each face: FV neighbour -> its boundary sub-cell mean;
 //   DG neighbour -> its solution mapped to sub-cell means by V^{DG->FV}, boundary layer.

@@ -250,6 +250,67 @@ DGFV_HD void volume_point_rev(const DevPhys& P, const double* u, const double* g
     prim_rev<NK>(P, u, s, b, ub);
 }
 
+// Reverse of cons_to_w (physics.cuh): u_bar += (dw/du)^T w_bar for the FV
+// reconstruction variables w = (rho_k, v, p).
+template <int NK>
+DGFV_HD void cons_to_w_rev(const DevPhys& P, const double* u, const double* wb, double* ub) {
+    double rho = u[0];
+    for (int k = 1; k < NK; ++k) rho += u[k];
+    const double irho = 1.0 / rho;
+    double cvr = 0.0, cpr = 0.0;
+    for (int k = 0; k < NK; ++k) {
+        cvr = fma(u[k], P.cv[k], cvr);
+        cpr = fma(u[k], P.cp[k], cpr);
+    }
+    double wv[3];
+    for (int i = 0; i < 3; ++i) wv[i] = u[NK + i] * irho;
+    const double ke = 0.5 * (u[NK] * wv[0] + u[NK + 1] * wv[1] + u[NK + 2] * wv[2]);
+    const double q = (cpr - cvr) / cvr;
+    // w_p = q (u_E - ke)
+    const double wpb = wb[NK + 3];
+    const double qb = wpb * (u[NK + 3] - ke);
+    ub[NK + 3] += wpb * q;
+    const double keb = -wpb * q;
+    // ke = 1/2 sum_i u_mi wv_i;  wv_i = u_mi irho
+    double irhob = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        const double wvb = wb[NK + i] + 0.5 * keb * u[NK + i];
+        ub[NK + i] += 0.5 * keb * wv[i] + wvb * irho;
+        irhob += wvb * u[NK + i];
+    }
+    // q = cpr/cvr - 1;  sums;  irho = 1/rho;  rho = sum u_k;  w_k = u_k
+    const double cprb = qb / cvr, cvrb = -qb * cpr / (cvr * cvr);
+    const double rhob = -irhob * irho * irho;
+    for (int k = 0; k < NK; ++k) ub[k] += wb[k] + cvrb * P.cv[k] + cprb * P.cp[k] + rhob;
+}
+
+// Reverse of w_to_cons: w_bar += (du/dw)^T u_bar.
+template <int NK>
+DGFV_HD void w_to_cons_rev(const DevPhys& P, const double* w, const double* ubar, double* wb) {
+    double rho = w[0];
+    for (int k = 1; k < NK; ++k) rho += w[k];
+    double cvr = 0.0, cpr = 0.0;
+    for (int k = 0; k < NK; ++k) {
+        cvr = fma(w[k], P.cv[k], cvr);
+        cpr = fma(w[k], P.cp[k], cpr);
+    }
+    const double Dn = cpr - cvr, r = cvr / Dn;
+    // u_E = w_p r + ke;  ke = 1/2 rho |v|^2;  u_mi = rho v_i
+    const double ueb = ubar[NK + 3];
+    wb[NK + 3] += ueb * r;
+    const double rb = ueb * w[NK + 3];
+    double v2 = 0.0, rhob = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        v2 += w[NK + i] * w[NK + i];
+        wb[NK + i] += ueb * rho * w[NK + i] + ubar[NK + i] * rho;
+        rhob += ubar[NK + i] * w[NK + i];
+    }
+    rhob += 0.5 * ueb * v2;
+    // r = cvr / (cpr - cvr)
+    const double cvrb = rb * cpr / (Dn * Dn), cprb = -rb * cvr / (Dn * Dn);
+    for (int k = 0; k < NK; ++k) wb[k] += ubar[k] + cvrb * P.cv[k] + cprb * P.cp[k] + rhob;
+}
+
 // Reverse of kep_flux (physics.cuh): the flux is a function of the arithmetic
 // means of the two tuples, so both tuples receive half of each mean's adjoint;
 // tb += that half (call once per argument).
@@ -510,7 +571,7 @@ DGFV_HD void riemann_roe_rev(const DevPhys& P, const double* uL, const Prim<NK>&
 template <int NK>
 DGFV_HD void face_point_rev(const DevPhys& P, const double* uL, const double* gL, const double* uR,
                             const double* gR, int d, const double* Fb, double* uLb, double* gLb, double* uRb,
-                            double* gRb) {
+                            double* gRb, bool fv_involved = false) {
     constexpr int V = NK + 4;
     Prim<NK> sL, sR;
     prim<NK>(P, uL, sL);
@@ -521,7 +582,7 @@ DGFV_HD void face_point_rev(const DevPhys& P, const double* uL, const double* gL
     double half[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) half[v] = 0.5 * Fb[v];
-    if (use_roe(P, false)) {
+    if (use_roe(P, fv_involved)) {
         riemann_roe_rev<NK>(P, uL, sL, uR, sR, d, Fb, uLb, bL, uRb, bR);
     } else {
         // local Lax-Friedrichs: F = (F_L + F_R)/2 - smax (uR - uL)/2

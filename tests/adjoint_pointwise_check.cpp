@@ -256,6 +256,54 @@ int check_kep(int seed) {
     return bad;
 }
 
+// FV reconstruction variables (Sec. 3.1.2): cons_to_w and w_to_cons reversed.
+template <int NK>
+int check_fv_maps(int seed) {
+    constexpr int V = NK + 4;
+    std::mt19937 rng(seed);
+    std::normal_distribution<double> N01(0.0, 1.0);
+    DevPhys P = phys<NK>(false);
+    int bad = 0;
+    for (int trial = 0; trial < 30; ++trial) {
+        double u[V], du[V], wb[V], w[V], dw[V], ub_[V];
+        state<NK>(rng, P, u);
+        for (int v = 0; v < V; ++v) {
+            du[v] = 0.05 * N01(rng) * std::fabs(u[v]);
+            wb[v] = N01(rng);
+            ub_[v] = N01(rng);
+        }
+        cons_to_w<NK>(P, u, w);
+        for (int v = 0; v < V; ++v) dw[v] = 0.05 * N01(rng) * std::fabs(w[v]);
+        const double eps = 1e-6;
+        double up[V], um[V], wp[V], wm[V];
+        for (int v = 0; v < V; ++v) { up[v] = u[v] + eps * du[v]; um[v] = u[v] - eps * du[v]; }
+        cons_to_w<NK>(P, up, wp);
+        cons_to_w<NK>(P, um, wm);
+        double fd = 0.0, ad = 0.0, g[V] = {};
+        for (int v = 0; v < V; ++v) fd += wb[v] * (wp[v] - wm[v]) / (2 * eps);
+        cons_to_w_rev<NK>(P, u, wb, g);
+        for (int v = 0; v < V; ++v) ad += g[v] * du[v];
+        if (std::fabs(fd - ad) > 1e-7 + 1e-6 * std::fabs(fd)) {
+            std::printf("cons_to_w NK=%d trial %d: fd %.12e adjoint %.12e\n", NK, trial, fd, ad);
+            ++bad;
+        }
+        double a[V], b[V], ua[V], ubb[V], h[V] = {};
+        for (int v = 0; v < V; ++v) { a[v] = w[v] + eps * dw[v]; b[v] = w[v] - eps * dw[v]; }
+        w_to_cons<NK>(P, a, ua);
+        w_to_cons<NK>(P, b, ubb);
+        fd = 0.0;
+        ad = 0.0;
+        for (int v = 0; v < V; ++v) fd += ub_[v] * (ua[v] - ubb[v]) / (2 * eps);
+        w_to_cons_rev<NK>(P, w, ub_, h);
+        for (int v = 0; v < V; ++v) ad += h[v] * dw[v];
+        if (std::fabs(fd - ad) > 1e-7 + 1e-6 * std::fabs(fd)) {
+            std::printf("w_to_cons NK=%d trial %d: fd %.12e adjoint %.12e\n", NK, trial, fd, ad);
+            ++bad;
+        }
+    }
+    return bad;
+}
+
 int main() {
     int bad = 0;
     for (int visc = 0; visc < 2; ++visc) {
@@ -276,6 +324,9 @@ int main() {
         bad += check_transonic<2>(visc, 23 + visc);
         bad += check_transonic<3>(visc, 25 + visc);
     }
+    bad += check_fv_maps<1>(41);
+    bad += check_fv_maps<2>(42);
+    bad += check_fv_maps<3>(43);
     bad += check_kep<1>(31);
     bad += check_kep<2>(32);
     bad += check_kep<3>(33);

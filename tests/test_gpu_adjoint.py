@@ -1,7 +1,9 @@
 """The hand-written adjoint of the CUDA path (dgfv_rhs_vjp, dgfv_rk_step_vjp)
 against the oracle: the dot-product test <R_bar, J v> (oracle, exact dual
-numbers) = <J^T R_bar (CUDA), v>, central finite differences (eps = 1e-6) of
-the oracle's SSP-RK3 step along seeded directions, and the gradient of a
+numbers) = <J^T R_bar (CUDA), v> on DG and hybrid DG/FV patterns (LG, LGL,
+split form; LLF, Roe-HH, hybrid flux), whole adjoint matrices on tiny meshes,
+the SSP-RK3 and low-storage RK4 step adjoints against exact stage-by-stage
+tangents or central differences, and the gradient of a
 kinetic-energy-plus-species-variance functional after a short rollout."""
 import numpy as np
 import pytest
@@ -228,13 +230,89 @@ def test_split_form_rhs_vjp_dot_product(oracle, nk, mu, seed, riemann):
     ctx.close()
 
 
-def test_adjoint_rejects_fv_patterns():
+def _hybrid_problem(seed, nk=2, nel=(3, 2, 3), Nlo=1, Nhi=5, fv_frac=0.35, n_fv=6, mu=3e-3, riemann=0, nodes=0):
+    specs = [W.AIR, W.HELIUM, W.CO2][:nk]
+    sp = W.species_set(specs, mu=mu)
+    n = nel[0] * nel[1] * nel[2]
+    prob = W.make_problem([(nel, (0, 0, 0), (1.0, 0.8, 1.1))], sp, n_fv=n_fv, N=W.random_degrees(n, Nlo, Nhi, seed),
+                          fv=W.random_fv(n, fv_frac, seed), riemann=riemann, nodes=nodes)
+    return prob, W.smooth_random_state(prob, seed, amp=0.1)
+
+
+@pytest.mark.parametrize("nk,mu,seed,riemann,n_fv,nodes,fv_frac", [
+    (2, 3e-3, 31, 0, 6, 0, 0.35), (3, 0.0, 32, 0, 7, 0, 0.35), (2, 2e-3, 33, 1, 6, 0, 0.35),
+    (3, 3e-3, 34, 2, 8, 0, 0.35), (1, 1e-3, 35, 0, 6, 1, 0.35), (2, 2e-3, 36, 2, 6, 0, 1.0)])
+def test_rhs_vjp_with_fv_elements_dot_product(oracle, nk, mu, seed, riemann, n_fv, nodes, fv_frac):
+    """Hybrid DG/FV patterns frozen in the backward (Sec. 3.1.2, 3.2): the FV
+    sub-cell operator reversed (minmod along the forward's branches, central
+    differences, sub-cell Riemann and viscous fluxes), the DG/FV face and lifting
+    maps transposed, against the oracle's exact dual-number JVP; LLF, Roe-HH
+    and the hybrid flux choice; an all-FV mesh."""
+    prob, U = _hybrid_problem(seed, nk=nk, mu=mu, riemann=riemann, n_fv=n_fv, nodes=nodes, fv_frac=fv_frac)
+    rng = np.random.default_rng(seed)
+    Rbar = rng.standard_normal(U.size)
+    ctx = ctx_for(prob, N_min=1, N_max=int(prob["N"].max()))
+    Ubar = ctx.rhs_vjp(to_dev(U), to_dev(Rbar)).cpu().numpy()
+    for _ in range(3):
+        v = rng.standard_normal(U.size) * 1e-2 * np.abs(U).mean()
+        _, Jv = oracle.eval_rhs_jvp(prob, U, v)
+        lhs, rhs = float(np.dot(Rbar, Jv)), float(np.dot(Ubar, v))
+        scale = float(np.abs(Rbar * Jv).sum())
+        assert abs(lhs - rhs) <= 1e-11 * scale, (lhs, rhs, scale)
+    ctx.close()
+
+
+def test_rhs_vjp_with_fv_elements_columns(oracle):
+    """A 2x1x2 mesh with one FV element (N_FV = 3) among DG elements of degree
+    1-2: the whole J^T R_bar entry by entry against the oracle's JVP columns."""
+    sp = W.species_set([W.AIR, W.HELIUM], mu=2e-3)
+    prob = W.make_problem([((2, 1, 2), (0, 0, 0), (1.0, 0.5, 1.0))], sp, n_fv=3,
+                          N=np.array([2, 1, 2, 1], np.int8), fv=np.array([0, 1, 0, 0], np.uint8))
+    U = W.smooth_random_state(prob, 4, amp=0.1)
+    rng = np.random.default_rng(4)
+    Rbar = rng.standard_normal(U.size)
+    ctx = ctx_for(prob, N_min=1, N_max=2)
+    Ubar = ctx.rhs_vjp(to_dev(U), to_dev(Rbar)).cpu().numpy()
+    ref = np.zeros(U.size)
+    for j in range(U.size):
+        e = np.zeros(U.size)
+        e[j] = 1.0
+        ref[j] = np.dot(Rbar, oracle.eval_rhs_jvp(prob, U, e)[1])
+    np.testing.assert_allclose(Ubar, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+    ctx.close()
+
+
+def test_rk_step_vjp_with_fv_elements_dot_product(oracle):
+    """One SSP-RK3 step of a hybrid pattern, stages recomputed: against the
+    exact stage-by-stage tangent built from the oracle's JVP."""
+    prob, U = _hybrid_problem(37, nk=2, mu=2e-3, n_fv=6)
+    dt = 2e-4
+    ctx = ctx_for(prob, N_min=1, N_max=int(prob["N"].max()))
+    rng = np.random.default_rng(37)
+    lam = rng.standard_normal(U.size)
+    Ubar = ctx.rk_step_vjp(to_dev(U), dt, to_dev(lam)).cpu().numpy()
+    for _ in range(2):
+        v = rng.standard_normal(U.size) * np.abs(U).mean()
+        # U1 = U + dt R(U); U2 = 3/4 U + 1/4 (U1 + dt R(U1)); U3 = 1/3 U + 2/3 (U2 + dt R(U2))
+        R0, J0 = oracle.eval_rhs_jvp(prob, U, v)
+        U1, V1 = U + dt * R0, v + dt * J0
+        R1, J1 = oracle.eval_rhs_jvp(prob, U1, V1)
+        U2, V2 = 0.75 * U + 0.25 * (U1 + dt * R1), 0.75 * v + 0.25 * (V1 + dt * J1)
+        R2, J2 = oracle.eval_rhs_jvp(prob, U2, V2)
+        V3 = v / 3.0 + 2.0 / 3.0 * (V2 + dt * J2)
+        lhs, rhs = float(np.dot(lam, V3)), float(np.dot(Ubar, v))
+        scale = float(np.abs(lam * V3).sum())
+        assert abs(lhs - rhs) <= 1e-11 * scale, (lhs, rhs, scale)
+    ctx.close()
+
+
+def test_adjoint_rejects_fv_elements_on_mortar_meshes():
     from paper_2502_19342_gb300 import dgfv
-    prob, U = _dg_problem(9, nk=2)
-    prob["fv"] = np.zeros(len(prob["N"]), np.uint8)
-    prob["fv"][0] = 1
+    sp = W.species_set([W.AIR, W.HELIUM], mu=2e-3)
+    doms = W.chain_domains([(1, 2, 2, 0.5), (1, 1, 1, 0.5)])
+    prob = W.make_problem(doms, sp, n_fv=6, N=2, fv=np.array([1, 0, 0, 0, 0], np.uint8), chain=1)
     U = W.smooth_random_state(prob, 9)
-    ctx = ctx_for(prob, N_min=1, N_max=7)
+    ctx = ctx_for(prob, N_min=1, N_max=5)
     with pytest.raises(dgfv.DgfvError):
         ctx.rhs_vjp(to_dev(U), to_dev(np.ones_like(U)))
     ctx.close()

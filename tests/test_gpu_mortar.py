@@ -64,6 +64,15 @@ def test_rhs_on_mortar_chain(oracle, nk, riemann, mu, seed, nodes, split, fv_fra
     assert_rhs_close(oracle, prob, U, gpu_rhs(prob, U))
 
 
+@pytest.mark.parametrize("riemann,seed", [(0, 21), (2, 22)])
+def test_rhs_on_mortar_chain_odd_fv_count(oracle, riemann, seed):
+    """N_FV = 7: the middle sub-cell of a big FV side straddles the two halves
+    of the face, so the FV mortar maps split it (half of it on each virtual
+    side); degrees 1..6 and 40 % FV elements."""
+    prob, U = _all_types(seed, n_fv=7, Nhi=6, fv_frac=0.4, riemann=riemann)
+    assert_rhs_close(oracle, prob, U, gpu_rhs(prob, U))
+
+
 def test_rhs_free_stream_on_mortar_chain(oracle):
     """A uniform state gives R = 0 to rounding: on this chain (elements down to
     h = 1/8, degrees up to 7) the FP64 oracle itself reaches ~1e-11, so the
