@@ -340,14 +340,15 @@ def adjoint_hybrid_cost(steps=10):
     torch.cuda.synchronize()
     fwd, fsave, bst, brc = (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]),
                             ev[4].elapsed_time(ev[5]))
-    same = bool(torch.equal(grad_stored, a))
+    # the FV element reverse sums with atomics, so the two gradients agree to rounding, not bit for bit
+    rel = float((grad_stored - a).abs().max() / a.abs().max())
     ctx.close()
     return {"workload": "hp-mixed shock case after 2 adaptation cycles, pattern and dt frozen (hybrid DG/FV)",
             "steps": steps, "fv_elements": int(fv_now.sum()), "elements": int(len(N_now)),
             "forward_ms_per_step": fwd / steps, "forward_keeping_stages_ms_per_step": fsave / steps,
             "adjoint_ms_per_step_stored_stages": bst / steps, "adjoint_over_forward": bst / fwd,
             "adjoint_ms_per_step_recomputed_stages": brc / steps, "adjoint_over_forward_recomputed": brc / fwd,
-            "gradients_identical": same}
+            "gradients_max_rel_diff": rel}
 
 
 def split_form_run(nel, warmup=2, steps=1):

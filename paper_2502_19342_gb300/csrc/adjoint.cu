@@ -651,10 +651,18 @@ __global__ void __launch_bounds__(256) k_adj_fv(Params P, AdjBuffers A, Tiles T,
     for (int i = threadIdx.x; i < 3 * V * n3; i += blockDim.x) gradb[i] = 0.0;
     for (int f = 0; f < 6; ++f) {
         const int q = P.t.nb[6 * e + f];
-        fv_layer<NK>(P, U, q, f ^ 1, n, sNb + f * V * n2, sT1, sT2);
+        int qe = q;
+        if (q < 0) {  // mortar face: the values k_mortar_nb gathered
+            const int sl = -1 - q;
+            const double* src = P.t.mnb + (int64_t)sl * V * n2;
+            for (int i = threadIdx.x; i < V * n2; i += blockDim.x) sNb[f * V * n2 + i] = src[i];
+            qe = P.t.mnbe[sl];
+        } else {
+            fv_layer<NK>(P, U, q, f ^ 1, n, sNb + f * V * n2, sT1, sT2);
+        }
         if (threadIdx.x == 0) {
             const int d = f >> 1;
-            const double dist = 0.5 * l * (1.0 + rh[d] / P.t.rh[3 * q + d]);
+            const double dist = 0.5 * l * (1.0 + rh[d] / P.t.rh[3 * qe + d]);
             sID[f] = 1.0 / dist;
             sGS[f] = rh[d] / (l + dist);
         }
@@ -891,9 +899,10 @@ __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, doubl
 //   k_adj_mortar_big:  which 0: gbar_0 = sum_q M_q^T gbar_q, which 1: ubar_0 = sum_q M_q^T ubar_q
 //                      (one CTA per mortar; no face writes the big side's slot)
 __device__ __forceinline__ const double* adj_mortar_dir(const Params& P, int split, int quad, int dir, int n,
-                                                        bool proj) {
+                                                        bool proj, bool fv = false) {
     if (!((split >> dir) & 1)) return B(P, P.bi.eye[n]);
     const int h = (quad >> dir) & 1;
+    if (fv) return B(P, proj ? P.bi.mfp[h] : P.bi.mfi[h]);
     return B(P, proj ? P.bi.mp[n][h] : P.bi.mi[n][h]);
 }
 
@@ -903,9 +912,11 @@ __global__ void __launch_bounds__(128) k_adj_mortar_virt(Params P, AdjBuffers A,
     __shared__ double tmp[V * MAXP * MAXP];
     const int v = M.n_elem + blockIdx.x, m = M.vmort[blockIdx.x], q = M.vquad[blockIdx.x];
     const int eb = M.big[m], fB = M.fB[m], sp = M.split[m], n = P.t.n[eb], n2 = n * n;
+    const bool fv = P.t.fv[eb];
+    if (which == 1 && fv) return;  // an FV big side has no lifting value
     double* buf = which == 0 ? A.fbar : A.sbar;
     face_map2_t(buf + (P.t.fo[eb] + (int64_t)fB * n2) * V, n, buf + (P.t.fo[v] + (int64_t)fB * n2) * V, n,
-                adj_mortar_dir(P, sp, q, 0, n, true), adj_mortar_dir(P, sp, q, 1, n, true), V, tmp);
+                adj_mortar_dir(P, sp, q, 0, n, true, fv), adj_mortar_dir(P, sp, q, 1, n, true, fv), V, tmp);
 }
 
 template <int NK>
@@ -913,19 +924,54 @@ __global__ void __launch_bounds__(128) k_adj_mortar_big(Params P, AdjBuffers A, 
     constexpr int V = NK + 4;
     __shared__ double tmp[3 * V * MAXP * MAXP], res[3 * V * MAXP * MAXP], acc[3 * V * MAXP * MAXP];
     const int m = blockIdx.x, eb = M.big[m], fB = M.fB[m], sp = M.split[m], n = P.t.n[eb], n2 = n * n;
+    const bool fv = P.t.fv[eb];  // FV big side: the adjoints of its reconstructed state and boundary gradient
     const int w = which == 0 ? 3 * V : V;
     double* buf = which == 0 ? A.gbar : A.ubar;
     for (int i = threadIdx.x; i < w * n2; i += blockDim.x) acc[i] = 0.0;
     for (int vi = M.vfirst[m]; vi < M.vfirst[m + 1]; ++vi) {
         const int v = M.n_elem + vi, q = M.vquad[vi];
-        face_map2_t(buf + (P.t.fo[v] + (int64_t)fB * n2) * w, n, res, n, adj_mortar_dir(P, sp, q, 0, n, false),
-                    adj_mortar_dir(P, sp, q, 1, n, false), w, tmp);
+        face_map2_t(buf + (P.t.fo[v] + (int64_t)fB * n2) * w, n, res, n, adj_mortar_dir(P, sp, q, 0, n, false, fv),
+                    adj_mortar_dir(P, sp, q, 1, n, false, fv), w, tmp);
         for (int i = threadIdx.x; i < w * n2; i += blockDim.x) acc[i] += res[i];
         __syncthreads();
     }
     double* dst = buf + (P.t.fo[eb] + (int64_t)fB * n2) * w;
     for (int i = threadIdx.x; i < w * n2; i += blockDim.x) dst[i] = acc[i];
 }
+
+// k_adj_mortar_nb: one CTA per mortar; the transposes of k_mortar_nb's
+// neighbour values of FV elements (left by k_adj_fv, in conservative
+// variables, in the owner's fbar slot of the mortar face): an FV small side
+// read the big element's layer through M^FV_0q, an FV big side the small
+// elements' layers through M^FV_q0.  The layer adjoints go into the elements'
+// U_bar with atomics (an element can sit on two mortars).
+template <int NK>
+__global__ void __launch_bounds__(128) k_adj_mortar_nb(Params P, AdjBuffers A, MortarTables M, double* __restrict__ Ub) {
+    constexpr int V = NK + 4, PP = MAXP * MAXP;
+    __shared__ double acc[V * PP], res[V * PP], sT1[V * PP], sT2[V * PP];
+    const int m = blockIdx.x, eb = M.big[m], fB = M.fB[m], fS = fB ^ 1, sp = M.split[m];
+    const int n = P.nfv, n2 = n * n;
+    bool any = false;
+    for (int i = threadIdx.x; i < V * n2; i += blockDim.x) acc[i] = 0.0;
+    for (int vi = M.vfirst[m]; vi < M.vfirst[m + 1]; ++vi) {
+        const int q = M.vsmall[vi], qd = M.vquad[vi];
+        if (!P.t.fv[q]) continue;
+        any = true;
+        face_map2_t(A.fbar + (P.t.fo[q] + (int64_t)fS * n2) * V, n, res, n, adj_mortar_dir(P, sp, qd, 0, n, false, true),
+                    adj_mortar_dir(P, sp, qd, 1, n, false, true), V, sT1);
+        for (int i = threadIdx.x; i < V * n2; i += blockDim.x) acc[i] += res[i];
+        __syncthreads();
+    }
+    if (any) fv_layer_t<NK, true>(P, eb, fB, n, acc, Ub, sT1, sT2);
+    if (!P.t.fv[eb]) return;
+    for (int vi = M.vfirst[m]; vi < M.vfirst[m + 1]; ++vi) {
+        const int q = M.vsmall[vi], qd = M.vquad[vi];
+        face_map2_t(A.fbar + (P.t.fo[eb] + (int64_t)fB * n2) * V, n, res, n, adj_mortar_dir(P, sp, qd, 0, n, true, true),
+                    adj_mortar_dir(P, sp, qd, 1, n, true, true), V, sT1);
+        fv_layer_t<NK, true>(P, q, fS, n, res, Ub, sT1, sT2);
+    }
+}
+
 
 #define DGFV_DISPATCH(nk, call)                          \
     switch (nk) {                                        \
@@ -944,6 +990,12 @@ void launch_adj_mortar_big(int nk, const Params& P, const AdjBuffers& A, const M
                            int which, cudaStream_t s) {
     if (n_mort <= 0) return;
     DGFV_DISPATCH(nk, (k_adj_mortar_big<NK><<<n_mort, 128, 0, s>>>(P, A, M, which)));
+}
+
+void launch_adj_mortar_nb(int nk, const Params& P, const AdjBuffers& A, const MortarTables& M, int n_mort,
+                          double* Ub, cudaStream_t s) {
+    if (n_mort <= 0) return;
+    DGFV_DISPATCH(nk, (k_adj_mortar_nb<NK><<<n_mort, 128, 0, s>>>(P, A, M, Ub)));
 }
 
 void launch_adj_surface(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, const double* Rb,

@@ -32,6 +32,9 @@ void launch_adj_vol_b(int nk, const Params& P, const AdjBuffers& A, const Tiles&
                       const double* gvol, double* Ub, cudaStream_t s);
 void launch_adj_lift(int nk, const Params& P, const AdjBuffers& A, const Faces& F, const int32_t* list, int nfaces,
                      cudaStream_t s);
+// Mortar faces of FV elements: the transposes of the neighbour-value gathers.
+void launch_adj_mortar_nb(int nk, const Params& P, const AdjBuffers& A, const MortarTables& M, int n_mort,
+                          double* Ub, cudaStream_t s);
 // FV sub-cell elements (one tile per element): the surface adjoint, then after
 // the face and lifting adjoints the element reverse and the gather of the
 // neighbour-layer adjoints into the neighbours' U_bar (all elements).

@@ -1004,8 +1004,6 @@ int dgfv_compute_dt_noalloc(dgfv_ctx* c, const double* d_U, double* d_out3, void
 }
 
 static int adj_prepare(dgfv_ctx* c) {
-    if (c->n_fv_elems && c->n_mort)
-        return fail(c, DGFV_ERR_ARG, "the adjoint does not support FV elements on meshes with mortars");
     if (c->adj_ready) return DGFV_OK;
     TRY(dalloc(c, &c->d_fbar, c->cap_fpts * c->V));
     TRY(dalloc(c, &c->d_ubar, c->cap_fpts * c->V));
@@ -1032,7 +1030,10 @@ static void enqueue_vjp(dgfv_ctx* c, const double* U, const double* Rb, double* 
     // forward face values and lifting values of U (mortars: the virtual small
     // sides' values, the big sides' projected lifting values)
     launch_prolong(c->nk, P, c->all.view(), c->all.ntiles, U, s);
-    if (c->n_fv_elems) launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, U, s);  // FV face states and gradients
+    if (c->n_fv_elems) {  // FV face states and gradients (with the neighbour values across mortars)
+        launch_mortar_nb(c->nk, P, MT, c->d_s_active, c->n_slot_active, U, c->d_mnb, s);
+        launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, U, s);
+    }
     launch_mortar_in(c->nk, P, MT, c->n_virt, 0, s);
     if (c->ph.viscous) {
         launch_face_lift(c->nk, P, F, c->lift.d, c->lift.count, s);
@@ -1054,9 +1055,11 @@ static void enqueue_vjp(dgfv_ctx* c, const double* U, const double* Rb, double* 
         launch_adj_lift(c->nk, P, A, F, c->lift.d, c->lift.count, s);
     }
     launch_adj_mortar_big(c->nk, P, A, MT, c->n_mort, 1, s);
-    if (c->n_fv_elems)
+    if (c->n_fv_elems) {
         launch_adj_fv_elements(c->nk, P, A, c->fvt.view(), c->fvt.ntiles, U, Rb, Ub, c->d_gf, c->d_gvol, c->d_fvs,
                                c->cap_state, c->n_elem, s);
+        launch_adj_mortar_nb(c->nk, P, A, MT, c->n_mort, Ub, s);
+    }
     launch_adj_prolong(c->nk, P, A, c->dg.view(), c->dg.ntiles, Ub, s);
 }
 

@@ -139,7 +139,7 @@ __device__ __forceinline__ void fv_layer(const Params& P, const double* __restri
 // lb the adjoint of the N_FV x N_FV layer across face fq.  FV element: the
 // boundary sub-cells; DG element: V^{DG->FV} transposed in both face
 // directions, then the boundary row along the normal.  Ends with a barrier.
-template <int NK>
+template <int NK, bool ATOMIC = false>
 __device__ __forceinline__ void fv_layer_t(const Params& P, int q, int fq, int n, const double* lb, double* Ub,
                                            double* sT1, double* sT2) {
     constexpr int V = NK + 4;
@@ -149,7 +149,9 @@ __device__ __forceinline__ void fv_layer_t(const Params& P, int q, int fq, int n
         double* dst = Ub + P.t.off[q];
         for (int i = threadIdx.x; i < V * n2; i += blockDim.x) {
             const int v = i / n2, p = i % n2;
-            dst[(int64_t)v * n3 + node_index(n, d, m, p % n, p / n)] += lb[i];
+            double* t = dst + (int64_t)v * n3 + node_index(n, d, m, p % n, p / n);
+            if (ATOMIC) atomicAdd(t, lb[i]);
+            else *t += lb[i];
         }
         __syncthreads();
         return;
@@ -164,7 +166,9 @@ __device__ __forceinline__ void fv_layer_t(const Params& P, int q, int fq, int n
         const int ii = c % nq, jj = (c / nq) % nq, kk = c / nq2;
         const int m = d == 0 ? ii : (d == 1 ? jj : kk);
         const int a = d == 0 ? jj : ii, b = d == 2 ? jj : kk;
-        dst[(int64_t)v * nq3 + c] += __ldg(A + row * nq + m) * sT1[v * nq2 + a + nq * b];
+        const double x = __ldg(A + row * nq + m) * sT1[v * nq2 + a + nq * b];
+        if (ATOMIC) atomicAdd(dst + (int64_t)v * nq3 + c, x);
+        else dst[(int64_t)v * nq3 + c] += x;
     }
     __syncthreads();
 }

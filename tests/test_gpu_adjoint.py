@@ -306,18 +306,6 @@ def test_rk_step_vjp_with_fv_elements_dot_product(oracle):
     ctx.close()
 
 
-def test_adjoint_rejects_fv_elements_on_mortar_meshes():
-    from paper_2502_19342_gb300 import dgfv
-    sp = W.species_set([W.AIR, W.HELIUM], mu=2e-3)
-    doms = W.chain_domains([(1, 2, 2, 0.5), (1, 1, 1, 0.5)])
-    prob = W.make_problem(doms, sp, n_fv=6, N=2, fv=np.array([1, 0, 0, 0, 0], np.uint8), chain=1)
-    U = W.smooth_random_state(prob, 9)
-    ctx = ctx_for(prob, N_min=1, N_max=5)
-    with pytest.raises(dgfv.DgfvError):
-        ctx.rhs_vjp(to_dev(U), to_dev(np.ones_like(U)))
-    ctx.close()
-
-
 def test_stored_stage_adjoint_matches_recomputed_stages():
     """dgfv_rk_step_save advances the state exactly as dgfv_rk_step and keeps
     U1, U2; the adjoint from those stored stages equals, bit for bit, the

@@ -180,16 +180,37 @@ def test_rhs_vjp_on_mortar_chain_dot_product(oracle, seed, mu, nodes):
     ctx.close()
 
 
-def test_rhs_vjp_on_mortar_chain_columns(oracle):
-    """A tiny chain (a type-3 mortar each way, 10 elements of degree 1-2): the
-    whole J^T R_bar entry by entry against the oracle's JVP columns."""
+@pytest.mark.parametrize("seed,mu,riemann,n_fv", [(24, 2e-3, 0, 6), (25, 0.0, 2, 7), (26, 3e-3, 1, 6)])
+def test_rhs_vjp_on_mortar_chain_with_fv_elements(oracle, seed, mu, riemann, n_fv):
+    """Hybrid DG/FV patterns on every mortar type: the FV big and small sides'
+    maps (M^FV), the neighbour values gathered across mortars, transposed;
+    <R_bar, J v> with the oracle's JVP against <J^T R_bar, v>."""
+    prob, U = _all_types(seed, fv_frac=0.35, Nhi=n_fv - 1, n_fv=n_fv, mu=mu, riemann=riemann)
+    rng = np.random.default_rng(seed)
+    Rbar = rng.standard_normal(U.size)
+    ctx = ctx_for(prob, N_min=1, N_max=n_fv - 1)
+    Ubar = ctx.rhs_vjp(to_dev(U), to_dev(Rbar)).cpu().numpy()
+    for _ in range(3):
+        v = rng.standard_normal(U.size) * 1e-2 * np.abs(U).mean()
+        _, Jv = oracle.eval_rhs_jvp(prob, U, v)
+        lhs, rhs = float(np.dot(Rbar, Jv)), float(np.dot(Ubar, v))
+        scale = float(np.abs(Rbar * Jv).sum())
+        assert abs(lhs - rhs) <= 1e-11 * scale, (lhs, rhs, scale)
+    ctx.close()
+
+
+@pytest.mark.parametrize("fv", [None, [0, 1, 0, 0, 1]])
+def test_rhs_vjp_on_mortar_chain_columns(oracle, fv):
+    """A tiny chain (a type-3 mortar each way, 5 elements of degree 1-2; with
+    FV elements (N_FV = 3) on both the small and the big side): the whole
+    J^T R_bar entry by entry against the oracle's JVP columns."""
     sp = W.species_set([W.AIR, W.HELIUM], mu=2e-3)
     doms = W.chain_domains([(1, 2, 2, 0.5), (1, 1, 1, 0.5)])
-    prob = W.make_problem(doms, sp, n_fv=8, N=W.random_degrees(5, 1, 2, 3), chain=1)
+    prob = W.make_problem(doms, sp, n_fv=3, N=W.random_degrees(5, 1, 2, 3), fv=fv, chain=1)
     U = W.smooth_random_state(prob, 3, amp=0.1)
     rng = np.random.default_rng(3)
     Rbar = rng.standard_normal(U.size)
-    ctx = ctx_for(prob, N_min=1, N_max=7)
+    ctx = ctx_for(prob, N_min=1, N_max=2)
     Ubar = ctx.rhs_vjp(to_dev(U), to_dev(Rbar)).cpu().numpy()
     ref = np.zeros(U.size)
     for j in range(U.size):
