@@ -12,8 +12,8 @@
 //
 //   k_adj_surface    R_bar -> adjoint of the outward face fluxes        (Eq. 22 surface term)^T
 //   k_adj_face_conf  face-flux adjoint, conforming faces               (Eqs. 20, 21)^T
-//   k_adj_face_mixed face-flux adjoint, unequal degrees, with the
-//                    transposed interpolation / projection maps         (Sec. 3.2.1)^T
+//   k_adj_mixed_*    face-flux adjoint of faces that change representation,
+//                    with the transposed maps (three passes)            (Sec. 3.2.1, 3.2.2)^T
 //   k_adj_volume     volume integral^T, nodal-flux adjoint, gradient
 //                    trace^T, lifting^T -> U_bar (part), U*_bar          (Eqs. 22, 23)^T
 //   k_adj_lift       lifting value^T (mean on the lower degree)         (Eq. 19, Sec. 3.2.2)^T
@@ -99,141 +99,116 @@ __global__ void __launch_bounds__(128) k_adj_face_conf(Params P, AdjBuffers A, F
     }
 }
 
-// k_adj_face_mixed: unequal DG degrees, one CTA per face.  Forward: the lower
-// side's u and g traces are interpolated to the higher degree M, the flux is
-// computed there and L2-projected back to the lower side.  Adjoint: project^T
-// the lower side's flux adjoint, combine, reverse the point flux on M points,
-// interpolate^T the lower side's u/g adjoints.
+// Mixed faces in three passes, like the forward (and on its tiles and scratch):
+// k_adj_mixed_in (one CTA per face): the mapped side's forward u, g on the
+// common representation into Sin (4V per point), and the flux adjoint there,
+// F_bar = sgn_direct fbar_direct + sgn_mapped M_out^T fbar_mapped, into Sout;
+// k_adj_mixed_point (one thread per common point): the point-flux reverse, the
+// direct side's ubar/gbar written in place, the mapped side's into Sin;
+// k_adj_mixed_out (one CTA per face): M_in^T back onto the mapped side's slots.
+// M_in / M_out: V^{N->Nc} / its L2 projection back, or V^{DG->FV} / V^{FV->DG}.
 template <int NK>
-struct AdjMixedSmem {
-    static constexpr int V = NK + 4, PP = MAXP * MAXP;
-    double U[2][V * PP];
-    double G[2][3 * V * PP];
-    double F[V * PP];
-    double T[V * PP];      // scratch of one 2-pass map of V variables
-    double S[2 * V * PP];  // staging
-};
+__global__ void __launch_bounds__(128) k_adj_mixed_in(Params P, AdjBuffers A, Faces Fc, const int32_t* __restrict__ mface,
+                                                      const int64_t* __restrict__ mpt, double* __restrict__ Sin,
+                                                      double* __restrict__ Sout) {
+    constexpr int V = NK + 4;
+    __shared__ double tmp[3 * V * MAXP * MAXP], sb[V * MAXP * MAXP];
+    const int k = blockIdx.x, fid = mface[k], d = Fc.d[fid];
+    const MixedFace m = mixed_face(P, Fc, fid);
+    const int em = m.mapL ? m.eL : m.eR, fm = m.mapL ? 2 * d + 1 : 2 * d, n = P.t.n[em], n2 = n * n;
+    const int ed = m.mapL ? m.eR : m.eL, fd = m.mapL ? 2 * d : 2 * d + 1, nc2 = m.nc * m.nc;
+    const int64_t slot = P.t.fo[em] + (int64_t)fm * n2, sd = P.t.fo[ed] + (int64_t)fd * nc2;
+    const double* Min = B(P, m.cfv ? P.bi.d2f[n] : P.bi.vm[n][m.nc]);
+    const double* Mout = B(P, m.cfv ? P.bi.f2d[n] : P.bi.vm[m.nc][n]);
+    double* in = Sin + mpt[k] * 4 * V;
+    face_map(P.b.fu + slot * V, n, in, m.nc, Min, V, tmp);
+    if (P.ph.viscous) face_map(P.b.fg + slot * 3 * V, n, in + V * nc2, m.nc, Min, 3 * V, tmp);
+    // L's slot holds +F, R's slot -F
+    const double sm = m.mapL ? 1.0 : -1.0;
+    face_map_t(A.fbar + slot * V, n, sb, m.nc, Mout, V, tmp);
+    double* out = Sout + mpt[k] * V;
+    for (int i = threadIdx.x; i < V * nc2; i += blockDim.x) out[i] = sm * sb[i] - sm * A.fbar[sd * V + i];
+}
 
 template <int NK, int D>
-__device__ __forceinline__ void adj_mixed_body(const Params& P, const AdjBuffers& A, int eL, int eR,
-                                               AdjMixedSmem<NK>& S) {
+__device__ __forceinline__ void adj_mixed_point_body(const Params& P, const AdjBuffers& A, const Faces& Fc,
+                                                     const int32_t* __restrict__ mface, const int64_t* __restrict__ mpt,
+                                                     double* __restrict__ Sin, const double* __restrict__ Sout,
+                                                     const int32_t* __restrict__ items, int first, int count, int nc) {
     constexpr int V = NK + 4;
-    const int es[2] = {eL, eR};
-    const int fs[2] = {2 * D + 1, 2 * D};
-    // common representation: FV sub-cells if a side is FV (the DG side mapped by
-    // V^{DG->FV}, its flux back by V^{FV->DG}), else the higher degree
-    const bool cfv = P.t.fv[eL] || P.t.fv[eR];
-    const int nc = cfv ? P.nfv : max((int)P.t.n[eL], (int)P.t.n[eR]);
     const int nc2 = nc * nc;
     const bool visc = P.ph.viscous;
-    auto direct = [&](int e) { return P.t.fv[e] || (!cfv && P.t.n[e] == nc); };
-    auto map_in = [&](int n) { return B(P, cfv ? P.bi.d2f[n] : P.bi.vm[n][nc]); };   // nc x n
-    auto map_out = [&](int n) { return B(P, cfv ? P.bi.f2d[n] : P.bi.vm[nc][n]); };  // n x nc
-    // forward states on the common representation
-    for (int side = 0; side < 2; ++side) {
-        const int e = es[side], n = P.t.n[e], n2 = n * n;
-        const int64_t slot = P.t.fo[e] + (int64_t)fs[side] * n2;
-        const double* su = (P.t.fv[e] ? P.b.frec : P.b.fu) + slot * V;
-        const double* sg = P.b.fg + slot * 3 * V;
-        if (direct(e)) {
-            for (int i = threadIdx.x; i < V * nc2; i += blockDim.x) S.U[side][i] = su[i];
-            if (visc)
-                for (int i = threadIdx.x; i < 3 * V * nc2; i += blockDim.x) S.G[side][i] = sg[i];
-        } else {
-            const double* M = map_in(n);
-            for (int i = threadIdx.x; i < V * n2; i += blockDim.x) S.S[i] = su[i];
-            __syncthreads();
-            face_map(S.S, n, S.U[side], nc, M, V, S.T);
-            if (visc) {
-                for (int part = 0; part < 3; ++part) {
-                    for (int i = threadIdx.x; i < V * n2; i += blockDim.x) S.S[i] = sg[part * V * n2 + i];
-                    __syncthreads();
-                    face_map(S.S, n, S.G[side] + part * V * nc2, nc, M, V, S.T);
-                }
-            }
-        }
-    }
-    // flux adjoint on the common degree: F_bar = B_L^T fbar_L - B_R^T fbar_R
-    for (int i = threadIdx.x; i < V * nc2; i += blockDim.x) S.F[i] = 0.0;
-    __syncthreads();
-    for (int side = 0; side < 2; ++side) {
-        const int e = es[side], n = P.t.n[e], n2 = n * n;
-        const double sgn = side == 0 ? 1.0 : -1.0;
-        const double* fb = A.fbar + (P.t.fo[e] + (int64_t)fs[side] * n2) * V;
-        if (direct(e)) {
-            for (int i = threadIdx.x; i < V * nc2; i += blockDim.x) S.F[i] += sgn * fb[i];
-            __syncthreads();
-        } else {
-            for (int i = threadIdx.x; i < V * n2; i += blockDim.x) S.S[i] = fb[i];
-            __syncthreads();
-            face_map_t(S.S, n, S.S + V * MAXP * MAXP, nc, map_out(n), V, S.T);  // (projection or V^{FV->DG})^T
-            for (int i = threadIdx.x; i < V * nc2; i += blockDim.x) S.F[i] += sgn * S.S[V * MAXP * MAXP + i];
-            __syncthreads();
-        }
-    }
-    // reverse of the point flux; the adjoints overwrite the states in place
-    for (int p = threadIdx.x; p < nc2; p += blockDim.x) {
+    for (int t = threadIdx.x; t < count * nc2; t += blockDim.x) {
+        const int k = items[first + t / nc2], p = t % nc2;
+        const MixedFace m = mixed_face(P, Fc, mface[k]);
+        const int ed = m.mapL ? m.eR : m.eL, fd = m.mapL ? 2 * D : 2 * D + 1;
+        const int64_t sd = P.t.fo[ed] + (int64_t)fd * nc2;
+        const double* ud = (P.t.fv[ed] ? P.b.frec : P.b.fu) + sd * V + p;
+        const double* gd = P.b.fg + sd * 3 * V + p;
+        double* um = Sin + mpt[k] * 4 * V + p;
+        double* gm = um + V * nc2;
+        const double* fb = Sout + mpt[k] * V + p;
         double uL[V], uR[V], gL[3 * V], gR[3 * V], Fb[V];
         double uLb[V] = {}, uRb[V] = {}, gLb[3 * V] = {}, gRb[3 * V] = {};
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            uL[v] = S.U[0][v * nc2 + p];
-            uR[v] = S.U[1][v * nc2 + p];
-            Fb[v] = S.F[v * nc2 + p];
+            const double a = um[v * nc2], b = ud[v * nc2];
+            uL[v] = m.mapL ? a : b;
+            uR[v] = m.mapL ? b : a;
+            Fb[v] = fb[v * nc2];
         }
         if (visc) {
 #pragma unroll
             for (int x = 0; x < 3 * V; ++x) {
-                gL[x] = S.G[0][x * nc2 + p];
-                gR[x] = S.G[1][x * nc2 + p];
+                const double a = gm[x * nc2], b = gd[x * nc2];
+                gL[x] = m.mapL ? a : b;
+                gR[x] = m.mapL ? b : a;
             }
         }
-        face_point_rev<NK>(P.ph, uL, gL, uR, gR, D, Fb, uLb, gLb, uRb, gRb, cfv);
+        face_point_rev<NK>(P.ph, uL, gL, uR, gR, D, Fb, uLb, gLb, uRb, gRb, m.cfv);
+        double* ubd = A.ubar + sd * V + p;
+        double* gbd = A.gbar + sd * 3 * V + p;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            S.U[0][v * nc2 + p] = uLb[v];
-            S.U[1][v * nc2 + p] = uRb[v];
+            ubd[v * nc2] = m.mapL ? uRb[v] : uLb[v];
+            um[v * nc2] = m.mapL ? uLb[v] : uRb[v];
         }
+        if (visc) {
 #pragma unroll
-        for (int x = 0; x < 3 * V; ++x) {
-            S.G[0][x * nc2 + p] = visc ? gLb[x] : 0.0;
-            S.G[1][x * nc2 + p] = visc ? gRb[x] : 0.0;
-        }
-    }
-    __syncthreads();
-    // back to each side's degree (interpolation^T for the lower side)
-    for (int side = 0; side < 2; ++side) {
-        const int e = es[side], n = P.t.n[e], n2 = n * n;
-        const int64_t slot = P.t.fo[e] + (int64_t)fs[side] * n2;
-        double* ub = A.ubar + slot * V;
-        double* gb = A.gbar + slot * 3 * V;
-        if (direct(e)) {
-            for (int i = threadIdx.x; i < V * nc2; i += blockDim.x) ub[i] = S.U[side][i];
-            for (int i = threadIdx.x; i < 3 * V * nc2; i += blockDim.x) gb[i] = S.G[side][i];
-        } else {
-            const double* M = map_in(n);
-            face_map_t(S.U[side], nc, S.S, n, M, V, S.T);
-            for (int i = threadIdx.x; i < V * n2; i += blockDim.x) ub[i] = S.S[i];
-            __syncthreads();
-            for (int part = 0; part < 3; ++part) {
-                face_map_t(S.G[side] + part * V * nc2, nc, S.S, n, M, V, S.T);
-                for (int i = threadIdx.x; i < V * n2; i += blockDim.x) gb[part * V * n2 + i] = S.S[i];
-                __syncthreads();
+            for (int x = 0; x < 3 * V; ++x) {
+                gbd[x * nc2] = m.mapL ? gRb[x] : gLb[x];
+                gm[x * nc2] = m.mapL ? gLb[x] : gRb[x];
             }
         }
-        __syncthreads();
     }
 }
 
 template <int NK>
-__global__ void __launch_bounds__(64) k_adj_face_mixed(Params P, AdjBuffers A, Faces Fc, const int32_t* __restrict__ list) {
-    __shared__ AdjMixedSmem<NK> S;
-    const int fid = list[blockIdx.x];
-    switch (Fc.d[fid]) {
-        case 0: adj_mixed_body<NK, 0>(P, A, Fc.L[fid], Fc.R[fid], S); break;
-        case 1: adj_mixed_body<NK, 1>(P, A, Fc.L[fid], Fc.R[fid], S); break;
-        default: adj_mixed_body<NK, 2>(P, A, Fc.L[fid], Fc.R[fid], S); break;
+__global__ void __launch_bounds__(128) k_adj_mixed_point(Params P, AdjBuffers A, Faces Fc, FaceTiles T,
+                                                         const int32_t* __restrict__ mface,
+                                                         const int64_t* __restrict__ mpt, double* __restrict__ Sin,
+                                                         const double* __restrict__ Sout) {
+    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x], nc = T.nc[blockIdx.x];
+    switch (T.d[blockIdx.x]) {
+        case 0: adj_mixed_point_body<NK, 0>(P, A, Fc, mface, mpt, Sin, Sout, T.items, first, count, nc); break;
+        case 1: adj_mixed_point_body<NK, 1>(P, A, Fc, mface, mpt, Sin, Sout, T.items, first, count, nc); break;
+        default: adj_mixed_point_body<NK, 2>(P, A, Fc, mface, mpt, Sin, Sout, T.items, first, count, nc); break;
     }
+}
+
+template <int NK>
+__global__ void __launch_bounds__(128) k_adj_mixed_out(Params P, AdjBuffers A, Faces Fc, const int32_t* __restrict__ mface,
+                                                       const int64_t* __restrict__ mpt, const double* __restrict__ Sin) {
+    constexpr int V = NK + 4;
+    __shared__ double tmp[3 * V * MAXP * MAXP];
+    const int k = blockIdx.x, fid = mface[k], d = Fc.d[fid];
+    const MixedFace m = mixed_face(P, Fc, fid);
+    const int em = m.mapL ? m.eL : m.eR, fm = m.mapL ? 2 * d + 1 : 2 * d, n = P.t.n[em], n2 = n * n;
+    const int64_t slot = P.t.fo[em] + (int64_t)fm * n2;
+    const double* Min = B(P, m.cfv ? P.bi.d2f[n] : P.bi.vm[n][m.nc]);
+    const double* in = Sin + mpt[k] * 4 * V;
+    face_map_t(in, m.nc, A.ubar + slot * V, n, Min, V, tmp);
+    if (P.ph.viscous) face_map_t(in + V * m.nc * m.nc, m.nc, A.gbar + slot * 3 * V, n, Min, 3 * V, tmp);
 }
 
 // Volume adjoint in three kernels around the face adjoint.
@@ -1005,9 +980,17 @@ void launch_adj_surface(int nk, const Params& P, const AdjBuffers& A, const Tile
 }
 
 void launch_adj_faces(int nk, const Params& P, const AdjBuffers& A, const Faces& F, const FaceTiles& conf,
-                      int nconf, const int32_t* mixed, int nmixed, cudaStream_t s) {
+                      int nconf, cudaStream_t s) {
     if (nconf > 0) DGFV_DISPATCH(nk, (k_adj_face_conf<NK><<<nconf, 128, 0, s>>>(P, A, F, conf)));
-    if (nmixed > 0) DGFV_DISPATCH(nk, (k_adj_face_mixed<NK><<<nmixed, 64, 0, s>>>(P, A, F, mixed)));
+}
+
+void launch_adj_mixed_faces(int nk, const Params& P, const AdjBuffers& A, const Faces& F, const FaceTiles& T,
+                            int ntiles, const int32_t* mface, const int64_t* mpt, int nmixed, double* Sin,
+                            double* Sout, cudaStream_t s) {
+    if (nmixed <= 0) return;
+    DGFV_DISPATCH(nk, (k_adj_mixed_in<NK><<<nmixed, 128, 0, s>>>(P, A, F, mface, mpt, Sin, Sout),
+                       k_adj_mixed_point<NK><<<ntiles, 128, 0, s>>>(P, A, F, T, mface, mpt, Sin, Sout),
+                       k_adj_mixed_out<NK><<<nmixed, 128, 0, s>>>(P, A, F, mface, mpt, Sin)));
 }
 
 size_t adj_volume_smem_bytes(int nk, int n, int count) {

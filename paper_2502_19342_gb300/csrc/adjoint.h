@@ -20,7 +20,11 @@ void launch_adj_mortar_virt(int nk, const Params& P, const AdjBuffers& A, const 
 void launch_adj_mortar_big(int nk, const Params& P, const AdjBuffers& A, const MortarTables& M, int n_mort,
                            int which, cudaStream_t s);
 void launch_adj_faces(int nk, const Params& P, const AdjBuffers& A, const Faces& F, const FaceTiles& conf,
-                      int nconf, const int32_t* mixed, int nmixed, cudaStream_t s);
+                      int nconf, cudaStream_t s);
+// Mixed faces in three passes on the forward's mixed-face tiles and scratch.
+void launch_adj_mixed_faces(int nk, const Params& P, const AdjBuffers& A, const Faces& F, const FaceTiles& T,
+                            int ntiles, const int32_t* mface, const int64_t* mpt, int nmixed, double* Sin,
+                            double* Sout, cudaStream_t s);
 size_t adj_volume_smem_bytes(int nk, int n, int count);
 void launch_adj_vol_a(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
                       const double* Rb, double* Ub, double* gvol, double* gf, cudaStream_t s, int split = 0);

@@ -1032,7 +1032,7 @@ static void enqueue_vjp(dgfv_ctx* c, const double* U, const double* Rb, double* 
     launch_prolong(c->nk, P, c->all.view(), c->all.ntiles, U, s);
     if (c->n_fv_elems) {  // FV face states and gradients (with the neighbour values across mortars)
         launch_mortar_nb(c->nk, P, MT, c->d_s_active, c->n_slot_active, U, c->d_mnb, s);
-        launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, U, s);
+        launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, U, s, true);
     }
     launch_mortar_in(c->nk, P, MT, c->n_virt, 0, s);
     if (c->ph.viscous) {
@@ -1047,7 +1047,9 @@ static void enqueue_vjp(dgfv_ctx* c, const double* U, const double* Rb, double* 
                      c->opts.split_form);
     if (c->opts.split_form) launch_adj_split(c->nk, P, c->dg.view(), c->dg.ntiles, c->adj_split_smem, U, Rb, Ub, s);
     if (c->ph.viscous) launch_mortar_in(c->nk, P, MT, c->n_virt, 1, s);
-    launch_adj_faces(c->nk, P, A, F, c->conf.view(), c->conf.ntiles, c->flux.d, c->flux.count, s);
+    launch_adj_faces(c->nk, P, A, F, c->conf.view(), c->conf.ntiles, s);
+    launch_adj_mixed_faces(c->nk, P, A, F, c->mixed.tiles.view(), c->mixed.tiles.ntiles, c->mixed.d_face,
+                           c->mixed.d_pt, c->mixed.n, c->mixed.d_in, c->mixed.d_out, s);
     if (c->ph.viscous) {
         launch_adj_mortar_big(c->nk, P, A, MT, c->n_mort, 0, s);
         launch_adj_vol_b(c->nk, P, A, c->dg.view(), c->dg.ntiles, c->dg.smem, c->d_gvol, Ub, s);

@@ -173,4 +173,23 @@ __device__ __forceinline__ void fv_layer_t(const Params& P, int q, int fq, int n
     __syncthreads();
 }
 
+// A face that changes representation (Sec. 3.2.1, 3.2.2): the common
+// representation (N_FV sub-cells if a side is FV, else the higher degree) and
+// which side is mapped to it (the lower degree, or the DG side of a DG/FV face).
+struct MixedFace {
+    int eL, eR, nc;
+    bool cfv, mapL;
+};
+
+__device__ __forceinline__ MixedFace mixed_face(const Params& P, const Faces& Fc, int fid) {
+    MixedFace m;
+    m.eL = Fc.L[fid];
+    m.eR = Fc.R[fid];
+    m.cfv = P.t.fv[m.eL] || P.t.fv[m.eR];
+    const int nL = P.t.n[m.eL], nR = P.t.n[m.eR];
+    m.nc = m.cfv ? P.nfv : max(nL, nR);
+    m.mapL = m.cfv ? !P.t.fv[m.eL] : nL != m.nc;
+    return m;
+}
+
 }  // namespace dgfv

@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(256) k_prolong(Params P, Tiles T, const double
 //   minmod reconstruction of (rho_k, v, p), conservative central-difference
 //   gradients, interior sub-cell fluxes -> rtmp; element-face states -> frec, fg.
 template <int NK, int NF>
-__device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const double* __restrict__ U) {
+__device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const double* __restrict__ U,
+                                        bool faces_only) {
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
     const int n = NF > 0 ? NF : P.nfv, n2 = n * n, n3 = n2 * n;
@@ -199,8 +200,9 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
     };
     // interior sub-cell faces of all three directions in one pass (better
     // balanced over the CTA than one direction at a time), then the flux
-    // differences of every cell
-    const int nif = (n - 1) * n2;
+    // differences of every cell (skipped when only the element-face states are
+    // wanted: the adjoint's recomputation of the forward face values)
+    const int nif = faces_only ? 0 : (n - 1) * n2;
     for (int t = threadIdx.x; t < 3 * nif; t += blockDim.x) {
         const int d = t / nif, fidx = t - d * nif;
         const int m = fidx % (n - 1), p = fidx / (n - 1), a = p % n, b = p / n;
@@ -235,7 +237,7 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
         for (int v = 0; v < V; ++v) sF[(d * V + v) * nif + fidx] = F[v];
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < n3; c += blockDim.x) {
+    for (int c = threadIdx.x; c < (faces_only ? 0 : n3); c += blockDim.x) {
         const int ijk[3] = {c % n, (c / n) % n, c / n2};
         double acc[V];
 #pragma unroll
@@ -283,11 +285,12 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
 // on an SM (N_FV <= 7), otherwise one CTA of 512 threads (N_FV = 8, up to
 // 180 KB for one element).
 template <int NK, int TPB>
-__global__ void __launch_bounds__(TPB, 512 / TPB) k_fv(Params P, Tiles T, const double* __restrict__ U) {
+__global__ void __launch_bounds__(TPB, 512 / TPB) k_fv(Params P, Tiles T, const double* __restrict__ U,
+                                                       int faces_only) {
     if (P.nfv == 8)
-        fv_body<NK, 8>(P, T, U);
+        fv_body<NK, 8>(P, T, U, faces_only != 0);
     else
-        fv_body<NK, 0>(P, T, U);
+        fv_body<NK, 0>(P, T, U, faces_only != 0);
 }
 
 // ---------------------------------------------------------------------------------
@@ -426,21 +429,6 @@ __global__ void __launch_bounds__(128) k_face_flux_conf(Params P, Faces Fc, Face
 // place, its flux written directly); the mapped side's flux is mapped back
 // (k_mixed_out: L2 projection or V^{FV->DG}).  Mixed face k: face mface[k],
 // scratch at point offset mpt[k] (4V values per point in, V out).
-struct MixedFace {
-    int eL, eR, nc;
-    bool cfv, mapL;
-};
-
-__device__ __forceinline__ MixedFace mixed_face(const Params& P, const Faces& Fc, int fid) {
-    MixedFace m;
-    m.eL = Fc.L[fid];
-    m.eR = Fc.R[fid];
-    m.cfv = P.t.fv[m.eL] || P.t.fv[m.eR];
-    const int nL = P.t.n[m.eL], nR = P.t.n[m.eR];
-    m.nc = m.cfv ? P.nfv : max(nL, nR);
-    m.mapL = m.cfv ? !P.t.fv[m.eL] : nL != m.nc;
-    return m;
-}
 
 template <int NK>
 __global__ void __launch_bounds__(128) k_mixed_in(Params P, Faces Fc, const int32_t* __restrict__ mface,
@@ -1266,16 +1254,16 @@ size_t fv_smem_bytes(int nk, int nfv) {
     return sizeof(double) * (size_t)(2 * V * n3 + 12 * V * n2 + 3 * V * (nfv - 1) * n2 + 2 * V * MAXP * MAXP);
 }
 
-void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s) {
+void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s, bool faces_only) {
     if (ntiles <= 0) return;
     const size_t sm = fv_smem_bytes(nk, P.nfv);
     // 228 KB of shared memory per SM, 1 KB of it reserved per resident CTA
     if (2 * (sm + 1024 + 256) <= 228 * 1024) {
         DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_fv<NK, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
-                           k_fv<NK, 256><<<ntiles, 256, sm, s>>>(P, T, U)));
+                           k_fv<NK, 256><<<ntiles, 256, sm, s>>>(P, T, U, faces_only ? 1 : 0)));
     } else {
         DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_fv<NK, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
-                           k_fv<NK, 512><<<ntiles, 512, sm, s>>>(P, T, U)));
+                           k_fv<NK, 512><<<ntiles, 512, sm, s>>>(P, T, U, faces_only ? 1 : 0)));
     }
 }
 

@@ -12,7 +12,10 @@ namespace dgfv {
 
 void launch_prolong(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s);
 size_t fv_smem_bytes(int nk, int nfv);
-void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s);
+// faces_only: only the element-face states and boundary gradients (frec, fg),
+// not the sub-cell fluxes (the adjoint's recomputation of the forward).
+void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s,
+               bool faces_only = false);
 void launch_face_lift_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s);
 void launch_face_lift(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s);
 size_t volume_smem_bytes(int nk, int n, int count);
