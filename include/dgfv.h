@@ -207,12 +207,13 @@ int dgfv_rk_steps(dgfv_ctx* ctx, int n_steps, double dt, double* dt_used, void* 
  * The hp/FV pattern is frozen: DG and FV sub-cell elements (the minmod
  * limiter differentiated along the branch the forward evaluation takes), LG
  * or LGL nodes, the standard or the split-form volume integral, every flux
- * choice, constant or Sutherland viscosity, conforming meshes and mortar
- * meshes without FV elements (DGFV_ERR_ARG for FV elements on a mesh with
- * mortars).  Device arrays in the current layout;
+ * choice, constant or Sutherland viscosity, conforming and mortar meshes.
+ * Device arrays in the current layout;
  * d_Ubar must not alias d_U or d_Rbar.  Uses the context's forward face
  * buffers (a later eval_rhs recomputes them).  The first adjoint call
- * allocates the adjoint scratch (face adjoints and four state buffers). */
+ * allocates the adjoint scratch (four face-adjoint buffers and sixteen
+ * state-sized buffers: stage states and adjoints, nodal gradient and flux
+ * adjoints, FV scratch). */
 int dgfv_rhs_vjp(dgfv_ctx* ctx, const double* d_U, const double* d_Rbar, double* d_Ubar, void* stream);
 
 /* Adjoint of one step of size dt of the context's integrator from the state
