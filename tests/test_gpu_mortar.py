@@ -108,6 +108,27 @@ def test_rk3_steps_on_half_refined_cube_with_changing_pattern(oracle):
     ctx.close()
 
 
+def test_lsrk4_and_positivity_limiter_on_half_refined_cube(oracle):
+    """The low-storage RK4 (Sec. 3.3) and the Zhang-Shu limiter after every
+    stage (Sec. 3.5) on the mortar mesh: three steps each against the oracle."""
+    prob, U = _half_refined(17, fv_frac=0.2, riemann=2)
+    ctx = ctx_for(prob, N_min=1, N_max=7, opts={"integrator": 1})
+    ctx.set_state(to_dev(U))
+    for _ in range(3):
+        ctx.rk_step(2e-4)
+    Uo, _ = oracle.lsrk4(prob, U, 3, dt_fixed=2e-4)
+    assert_fields_close(prob, ctx.get_state().cpu().numpy(), Uo, what="U(3 LSRK4 steps)")
+    ctx.close()
+    pp = dict(prob, pp_limiter=1, pp_eps=1e-10)
+    ctx = ctx_for(pp, N_min=1, N_max=7)
+    ctx.set_state(to_dev(U))
+    for _ in range(3):
+        ctx.rk_step(2e-4)
+    Uo, _ = oracle.rk3(pp, U, 3, dt_fixed=2e-4)
+    assert_fields_close(pp, ctx.get_state().cpu().numpy(), Uo, what="U(3 limited SSP-RK3 steps)")
+    ctx.close()
+
+
 def test_time_step_and_graph_on_mortar_chain(oracle):
     """CFL time step with the element sizes of both halves, and an RK step replayed
     from a captured graph equals the direct launches."""
