@@ -431,7 +431,8 @@ def tgv_run(nel=32, warmup=2, steps=2):
     N_now, fv_now = ctx.get_degrees()
     ctx.close()
     return {"workload": f"supersonic Taylor-Green vortex, Ma 1.25, Re 1600, {nel}^3 elements on [-pi,pi]^3, "
-                        "N in 2..4 (pressure indicator), FV sub-cells N_FV=8 (density indicator), Sutherland "
+                        f"N in 2..4 (pressure indicator), FV sub-cells N_FV={int(prob['n_fv'])} (density indicator), "
+                        "Sutherland "
                         "viscosity, low-storage RK4, LLF, early time",
             "value": units / (ms * 1e-3), "unit": "DOF-stage/s", "ms_per_step": ms / steps,
             "step": "adapt + 10 low-storage RK4 steps (50 stages), CFL 0.5",

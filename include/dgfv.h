@@ -84,7 +84,9 @@ typedef struct {
     const double* lo;     /* lower corner per domain                    */
     const double* hi;     /* upper corner per domain (hi > lo)          */
     int N_min, N_max;     /* degree bounds, 1 <= N_min <= N_max <= 7    */
-    int N_fv;             /* FV sub-cells per direction, N_max+1 <= N_fv <= 8 */
+    int N_fv;             /* FV sub-cells per direction, N_max+1 <= N_fv <= 9; the
+                             sub-cells of one FV element must fit in one CTA's
+                             shared memory (N_fv = 9: at most 2 species) */
     int chain_x;          /* 0 or 1, see above                          */
 } dgfv_mesh_desc;
 

@@ -115,7 +115,7 @@ struct dgfv_ctx {
     MixedSet mixed;         // the flux faces in three passes
     int n_fv_elems = 0;
     int launch_mode = 0;           // 0: one launch per kernel; 1: one launch per degree bin
-    int vol_per_tile[MAXP + 1] = {};  // elements per volume tile (0: default), set by the autotuner
+    int vol_per_tile[MAXDG + 1] = {};  // elements per volume tile (0: default), set by the autotuner
     int vol_variant = 0;              // volume-kernel launch variant (threads, register budget), autotuned
     bool state_valid = false;
     std::string err;
@@ -629,7 +629,8 @@ int set_pattern(dgfv_ctx* c, const int8_t* N, const uint8_t* fv, bool remap, cud
         const Params P = params(c);
         Timed t(c, K_REMAP, s);
         launch_remap(P, c->d_n_old, c->d_N_old, c->d_fv_old, c->d_off_old, c->d_n, c->d_N, c->d_fv, c->d_off, c->V,
-                     c->n_elem, c->d_U, c->d_Us, s);
+                     c->n_elem, c->d_U, c->d_Us,
+                     std::max(c->N_max + 1, c->nfv), s);
         CK(cudaGetLastError());
         std::swap(c->d_U, c->d_Us);
         CK(cudaStreamSynchronize(s));
@@ -691,6 +692,8 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     if (mesh->n_domains < 1 || !mesh->dims || !mesh->lo || !mesh->hi) return DGFV_ERR_ARG;
     if (mesh->N_min < 1 || mesh->N_max > 7 || mesh->N_min > mesh->N_max) return DGFV_ERR_ARG;
     if (mesh->N_fv < mesh->N_max + 1 || mesh->N_fv > MAXP) return DGFV_ERR_ARG;
+    // one FV element's sub-cell data must fit in the shared memory of one CTA
+    if (fv_smem_bytes(phys->n_species, mesh->N_fv) > 227 * 1024) return DGFV_ERR_ARG;
     if (phys->n_species < 1 || phys->n_species > 3) return DGFV_ERR_ARG;
     int64_t ne = 0;
     for (int d = 0; d < mesh->n_domains; ++d) {
@@ -1321,7 +1324,7 @@ int dgfv_autotune(dgfv_ctx* c, int* per_tile_out, void* stream) {
     CK(cudaEventCreate(&e1));
     // launch variant first, on the whole volume launch with the default tiles
     {
-        for (int n = 0; n <= MAXP; ++n) c->vol_per_tile[n] = 0;
+        for (int n = 0; n <= MAXDG; ++n) c->vol_per_tile[n] = 0;
         TRY(apply_layout(c));
         const Params P = params(c);
         double best_ms = 1e300;
@@ -1341,8 +1344,8 @@ int dgfv_autotune(dgfv_ctx* c, int* per_tile_out, void* stream) {
         }
         c->vol_variant = best;
     }
-    int best_all[MAXP + 1] = {};
-    for (int n = 1; n <= MAXP; ++n) {
+    int best_all[MAXDG + 1] = {};
+    for (int n = 1; n <= MAXDG; ++n) {
         int cnt = 0;
         for (int e = 0; e < c->n_elem; ++e) cnt += (!c->fv[e] && c->npts[e] == n);
         if (cnt == 0) continue;
@@ -1376,7 +1379,7 @@ int dgfv_autotune(dgfv_ctx* c, int* per_tile_out, void* stream) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    for (int n = 1; n <= MAXP; ++n) {
+    for (int n = 1; n <= MAXDG; ++n) {
         c->vol_per_tile[n] = best_all[n];
         if (per_tile_out) per_tile_out[n] = best_all[n];
     }

@@ -14,7 +14,8 @@
 
 namespace dgfv {
 
-constexpr int MAXP = 8;        // points per direction (N <= 7, N_FV <= 8)
+constexpr int MAXP = 9;        // points per direction of any element (DG: N + 1 <= 8; FV: N_FV <= 9)
+constexpr int MAXDG = 8;       // points per direction of a DG element (N <= 7)
 constexpr int NBANK = MAXP + 1;
 
 // Offsets (in doubles) of the reference operators in the device bank, indexed

@@ -614,7 +614,8 @@ __global__ void __launch_bounds__(256) k_surface(Params P, Tiles T, const double
         case 5: surface_body<NK, MODE, 5>(P, T, Uin, U0, out, a, b, dtp, fuse, dU); break;
         case 6: surface_body<NK, MODE, 6>(P, T, Uin, U0, out, a, b, dtp, fuse, dU); break;
         case 7: surface_body<NK, MODE, 7>(P, T, Uin, U0, out, a, b, dtp, fuse, dU); break;
-        default: surface_body<NK, MODE, 8>(P, T, Uin, U0, out, a, b, dtp, fuse, dU); break;
+        case 8: surface_body<NK, MODE, 8>(P, T, Uin, U0, out, a, b, dtp, fuse, dU); break;
+        default: surface_body<NK, MODE, 0>(P, T, Uin, U0, out, a, b, dtp, fuse, dU); break;  // N_FV = 9
     }
 }
 
@@ -911,9 +912,9 @@ struct Thresholds {
 template <int NK>
 __global__ void __launch_bounds__(128) k_indicator(Params P, const double* __restrict__ U, int n_elem,
                                                    double* Ip, double* Ih, uint8_t* dec, Thresholds thr,
-                                                   int N_min, int N_max, int vars) {
+                                                   int N_min, int N_max, int vars, int P3) {
+    // P3: scratch stride, the cube of the context's largest point count
     constexpr int V = NK + 4, NQ = 2 + (NK - 1);  // rho, p, Y_1..Y_{NK-1}
-    constexpr int P3 = MAXP * MAXP * MAXP;
     extern __shared__ double sm[];
     double* sMap = sm;               // V*P3: FV state mapped to the element's degree
     double* sS1 = sMap + V * P3;     // P3 scratch
@@ -1241,12 +1242,15 @@ __global__ void __launch_bounds__(128) k_mortar_nb(Params P, MortarTables M, con
     }
 
 // Shared memory of the tile kernels that stage a tile of states: count * n^3 <= 512
-// nodes per tile (the "all" tiling) and 4 * MAXP bank values.
-static size_t tile_state_smem(int nk) { return sizeof(double) * (size_t)(4 * MAXP + (nk + 4) * 512); }
+// nodes per tile (the "all" tiling; an FV element of N_FV^3 > 512 sub-cells is a
+// tile of its own) and 4 * MAXP bank values.
+static size_t tile_state_smem(int nk, int nfv) {
+    return sizeof(double) * (size_t)(4 * MAXP + (nk + 4) * std::max(512, nfv * nfv * nfv));
+}
 
 void launch_prolong(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s) {
     if (ntiles <= 0) return;
-    DGFV_DISPATCH(nk, (k_prolong<NK><<<ntiles, 256, tile_state_smem(nk), s>>>(P, T, U)));
+    DGFV_DISPATCH(nk, (k_prolong<NK><<<ntiles, 256, tile_state_smem(nk, P.nfv), s>>>(P, T, U)));
 }
 
 size_t fv_smem_bytes(int nk, int nfv) {
@@ -1311,7 +1315,7 @@ void launch_surface(int nk, const Params& P, const Tiles& T, int ntiles, const d
                     cudaStream_t s) {
     if (ntiles <= 0) return;
     const int f = (fuse && mode != 0) ? 1 : 0;
-    const size_t sm = f ? tile_state_smem(nk) : sizeof(double) * 4 * MAXP;
+    const size_t sm = f ? tile_state_smem(nk, P.nfv) : sizeof(double) * 4 * MAXP;
     if (mode == 0) {
         DGFV_DISPATCH(nk, (k_surface<NK, 0><<<ntiles, 256, sm, s>>>(P, T, Uin, U0, out, a, b, dt, f, dU)));
     } else if (mode == 1) {
@@ -1376,16 +1380,19 @@ int launch_dt_noalloc(int nk, const Params& P, const Tiles& T, int ntiles, const
 void launch_indicator(int nk, const Params& P, const double* U, int n_elem, double* Ip, double* Ih, uint8_t* dec,
                       const double thr[4], int N_min, int N_max, int vars, cudaStream_t s) {
     const Thresholds t{thr[0], thr[1], thr[2], thr[3]};
-    const size_t sm = sizeof(double) * (size_t)MAXP * MAXP * MAXP * (nk + 4 + 2 + 2 * (nk + 1));
+    const int nmax = std::max(N_max + 1, P.nfv), p3 = nmax * nmax * nmax;
+    const size_t sm = sizeof(double) * (size_t)p3 * (nk + 4 + 2 + 2 * (nk + 1));
     DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_indicator<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
-                       k_indicator<NK><<<n_elem, 128, sm, s>>>(P, U, n_elem, Ip, Ih, dec, t, N_min, N_max, vars)));
+                       k_indicator<NK><<<n_elem, 128, sm, s>>>(P, U, n_elem, Ip, Ih, dec, t, N_min, N_max, vars,
+                                                                p3)));
 }
 
 void launch_remap(const Params& P, const uint8_t* n_old, const uint8_t* N_old, const uint8_t* fv_old,
                   const int64_t* off_old, const uint8_t* n_new, const uint8_t* N_new, const uint8_t* fv_new,
-                  const int64_t* off_new, int V, int n_elem, const double* Uo, double* Un, cudaStream_t s) {
+                  const int64_t* off_new, int V, int n_elem, const double* Uo, double* Un, int nmax,
+                  cudaStream_t s) {
     RemapSide A{n_old, N_old, fv_old, off_old}, Bn{n_new, N_new, fv_new, off_new};
-    const size_t sm = sizeof(double) * (size_t)(2 * V * MAXP * MAXP * MAXP);
+    const size_t sm = sizeof(double) * (size_t)(2 * V * nmax * nmax * nmax);  // t1 and t2 of the largest element
     cudaFuncSetAttribute(k_remap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_remap<<<n_elem, 128, sm, s>>>(P, A, Bn, V, Uo, Un);
 }

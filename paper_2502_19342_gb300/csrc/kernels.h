@@ -52,7 +52,8 @@ void launch_indicator(int nk, const Params& P, const double* U, int n_elem, doub
                       const double thr[4], int N_min, int N_max, int vars, cudaStream_t s);
 void launch_remap(const Params& P, const uint8_t* n_old, const uint8_t* N_old, const uint8_t* fv_old,
                   const int64_t* off_old, const uint8_t* n_new, const uint8_t* N_new, const uint8_t* fv_new,
-                  const int64_t* off_new, int V, int n_elem, const double* Uo, double* Un, cudaStream_t s);
+                  const int64_t* off_new, int V, int n_elem, const double* Uo, double* Un, int nmax,
+                  cudaStream_t s);
 double probe_dfma(int iters, cudaStream_t s);
 double probe_dmma(int iters, cudaStream_t s);
 

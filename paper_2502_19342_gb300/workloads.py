@@ -478,16 +478,15 @@ TGV_S_OVER_TREF = 110.4 / 273.15
 TGV_THRESHOLDS = (2.0, 3.0, 3.0, 5.0)
 
 
-def tgv(nel=32, N0=3, Ma=1.25, Re=1600.0, n_fv=8, nodes=0, riemann=0, fv=None):
+def tgv(nel=32, N0=3, Ma=1.25, Re=1600.0, n_fv=9, nodes=0, riemann=0, fv=None):
     """Supersonic Taylor-Green vortex on [-pi, pi]^3 (Sec. 4.3): one gas with
     gamma = 1.4, rho_0 = 1, Ma_0 = sqrt(rho_0 / (gamma p_0)) = 1.25, Re_0 =
     rho_0 / mu_0 = 1600, isothermal start at T_0 = T_ref of Sutherland's law,
     v = (sin x cos y cos z, -cos x sin y cos z, 0),
     p = p_0 + rho_0/16 (cos 2x + cos 2y)(2 + cos 2z), rho = p / (R T_0).
     Elements start at degree N0 (a scalar or one per element) and FV flags fv;
-    p-refinement on the pressure indicator, FV on the density indicator.  The
-    paper's N_FV = 9 is above the library's limit of 8 sub-cells per direction:
-    N_FV = 8."""
+    p-refinement on the pressure indicator, FV on the density indicator;
+    N_FV = 9 as in the paper."""
     rho0 = 1.0
     p0 = rho0 / (1.4 * Ma * Ma)
     sp = species_set([AIR], mu=rho0 / Re, Pr=0.71)

@@ -333,6 +333,32 @@ def test_lsrk4_graph_equals_steps_and_stage_adjoint_is_rejected():
     ctx.close()
 
 
+@pytest.mark.parametrize("nk,fv_frac,riemann", [(1, 0.4, 0), (2, 0.3, 2), (2, 1.0, 1)])
+def test_nine_sub_cells_per_direction(oracle, nk, fv_frac, riemann):
+    """N_FV = 9 (the paper's TGV set-up): FV elements of 729 sub-cells next to DG
+    elements of degrees 1..7 (the state tiles of such an element exceed the
+    512-node tiling, the sub-cell kernel runs at its generic size), R(U) and
+    three SSP-RK3 steps against the oracle."""
+    prob, U = _mixed(40 + nk, nk=nk, nel=(3, 3, 2), Nlo=1, Nhi=7, fv_frac=fv_frac, n_fv=9, riemann=riemann)
+    assert_rhs_close(oracle, prob, U, gpu_rhs(prob, U))
+    ctx = ctx_for(prob)
+    ctx.set_state(to_dev(U))
+    for _ in range(3):
+        ctx.rk_step(1e-4)
+    Uo, _ = oracle.rk3(prob, U, 3, dt_fixed=1e-4)
+    assert_fields_close(prob, ctx.get_state().cpu().numpy(), Uo, what="U(3 steps)")
+    ctx.close()
+
+
+def test_nine_sub_cells_with_three_species_is_refused():
+    """One FV element of 9^3 sub-cells and 7 variables needs more shared memory
+    than one CTA has: dgfv_init_mesh refuses the context."""
+    from paper_2502_19342_gb300 import dgfv
+    prob, _ = _mixed(44, nk=3, nel=(2, 2, 2), n_fv=9)
+    with pytest.raises(dgfv.DgfvError):
+        ctx_for(prob)
+
+
 def test_tgv_sutherland_indicator_choice_and_lsrk4(oracle):
     """The supersonic TGV set-up (Sec. 4.3) on 6^3 elements with degrees 2..4 and
     FV elements: R(U) with Sutherland's viscosity, the indicator with
