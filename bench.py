@@ -471,12 +471,16 @@ def hp_shock_run(warmup=2, cycles=4):
     ms = ev0.elapsed_time(ev1)
     N_now, fv_now = ctx.get_degrees()
     ctx.close()
+    value = units / (ms * 1e-3)
+    per_dof, _ = flops_per_dof(dict(prob, N=N_now, fv=fv_now))
     return {"workload": "hp-mixed shock case: 16^3 elements on [0,2]x[0,1]^2, Mach 1.5 shock into a heavy-gas "
                         "bubble (density ratio 3.5), 1 % heavy-gas background, 2 species, N in 2..6 and FV sub-cells "
                         "(N_FV = 7) by the "
                         "indicator every 5 SSP-RK3 steps",
-            "value": units / (ms * 1e-3), "unit": "DOF-stage/s", "ms_per_cycle": ms / cycles,
+            "value": value, "unit": "DOF-stage/s", "ms_per_cycle": ms / cycles,
             "cycle": "adapt + 5 SSP-RK3 steps (15 stages), CFL 0.5",
+            "whole_rhs_tflops": per_dof * value / 1e12, "whole_rhs_frac_of_fp64_peak": per_dof * value / 1e12 / FP64_PEAK_TFLOPS,
+            "flops_per_dof": per_dof,
             "fv_elements": int(fv_now.sum()), "mean_dofs_per_element": st["mean_dofs"],
             "degree_histogram": np.bincount(N_now[fv_now == 0], minlength=7).tolist()}
 
@@ -508,10 +512,14 @@ def mortar_run(k=24, warmup=1, steps=3):
     ctx.sync_status()
     ctx.close()
     ne = W.n_elements(prob)
+    value = dofs * steps * STEPS_PER_CYCLE * STAGES_PER_STEP / (ms * 1e-3)
+    per_dof, _ = flops_per_dof(prob)  # the degree/FV mix on a conforming sample (mortar work not counted)
     return {"workload": f"half-refined unit cube (Sec. 4.1/4.2 layout), {k}x{2 * k}x{2 * k} + {k // 2}x{k}x{k} "
                         "elements, type-3 mortars on both x interfaces, N in 2..5 and 5 % FV (N_FV = 8) at random, "
                         "2 species, viscous, density wave along [1,1,1]",
-            "value": dofs * steps * STEPS_PER_CYCLE * STAGES_PER_STEP / (ms * 1e-3), "unit": "DOF-stage/s",
+            "value": value, "unit": "DOF-stage/s",
+            "whole_rhs_tflops": per_dof * value / 1e12, "whole_rhs_frac_of_fp64_peak": per_dof * value / 1e12 / FP64_PEAK_TFLOPS,
+            "flops_per_dof": per_dof,
             "ms_per_step": ms / (steps * STEPS_PER_CYCLE), "elements": ne, "dofs": dofs,
             "mortars": 2 * k * k, "fv_elements": int(prob["fv"].sum())}
 
