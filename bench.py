@@ -41,7 +41,20 @@ SMS, DFMA_PER_CLK, SM_MHZ_MAX = 152, 2, 2070.0
 # 0.373 + 0.703 GB for 3.13e6 DG DOFs).
 VOLUME_DRAM_BYTES_PER_DG_DOF = 344.0
 FP64_PEAK_TFLOPS = SMS * DFMA_PER_CLK * 2 * SM_MHZ_MAX * 1e6 / 1e12
+# measured copy bandwidth of this GPU type (written beside the repository when
+# it is present); used only to show how far the FP64-bound kernel is from HBM.
+HBM_FALLBACK_GBS = 6800.0
 KERNEL_STEP = {"prolong": 1, "fv": 2, "face_lift": 3, "dg_volume": 4, "face_flux": 5, "surface": 6}
+
+
+def measured_hbm_gbs():
+    """Copy bandwidth measured on this GPU type, else a fallback figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json copy)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback 6.8 TB/s"
 
 
 def parse():
@@ -740,6 +753,11 @@ def main():
                 "dfma_probe_tflops": probe, "dmma_probe_tflops": probe_mma,
                 "flops_per_dof": {"total": per_dof, main_k: per_step[KERNEL_STEP[main_k]]},
                 "whole_rhs_tflops": per_dof * units / (ms * 1e-3) / 1e12}
+        if traffic is not None:
+            hbm_gbs, hbm_src = measured_hbm_gbs()
+            dram_gbs = traffic / (kms / kl * 1e-3) / 1e9
+            roof["hbm_context"] = {"dram_gbs": dram_gbs, "peak_gbs": hbm_gbs, "frac": dram_gbs / hbm_gbs,
+                                   "peak_source": hbm_src}
         cpu = None if args.no_cpu else cpu_baseline(dict(prob, N=N_now, fv=fv_now))
         adjoint = adjoint_cost()
         adjoint["hybrid_dg_fv"] = adjoint_hybrid_cost()

@@ -54,6 +54,8 @@ def lib():
         L.oracle_eval_rhs.argtypes = [P, _dp, _dp]
         L.oracle_eval_rhs_jvp.argtypes = [P, _dp, _dp, _dp, _dp]
         L.oracle_eval_rhs_extended.argtypes = [P, _dp, _dp]
+        L.oracle_eval_rhs_jvp_extended.argtypes = [P, _dp, _dp, _dp, _dp]
+        L.oracle_adjoint_columns.argtypes = [P, _dp, _dp, C.c_int, _dp]
         L.oracle_count_flops.argtypes = [P, _dp, _dp]
         L.oracle_dt.argtypes = [P, _dp, C.c_double, C.c_double, _dp]
         L.oracle_rk3.argtypes = [P, _dp, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
@@ -166,6 +168,30 @@ def eval_rhs_jvp(prob, U, dU):
     dR = np.zeros_like(U)
     _check(lib().oracle_eval_rhs_jvp(b.ref, _ptr(U, _dp), _ptr(dU, _dp), _ptr(R, _dp), _ptr(dR, _dp)), "jvp")
     return R, dR
+
+
+def eval_rhs_jvp_extended(prob, U, dU):
+    """eval_rhs_jvp carried in long double: the FP64 tangent's rounding reference."""
+    b = _Bound(prob)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    dU = np.ascontiguousarray(dU, dtype=np.float64)
+    R = np.zeros_like(U)
+    dR = np.zeros_like(U)
+    _check(lib().oracle_eval_rhs_jvp_extended(b.ref, _ptr(U, _dp), _ptr(dU, _dp), _ptr(R, _dp), _ptr(dR, _dp)),
+           "jvp (extended)")
+    return R, dR
+
+
+def adjoint_columns(prob, U, Rbar, extended=False):
+    """R'(U)^T R_bar entry by entry from tangents along the unit vectors (tiny
+    meshes); extended=True carries tangent and sums in long double."""
+    b = _Bound(prob)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    Rbar = np.ascontiguousarray(Rbar, dtype=np.float64)
+    Ub = np.zeros_like(U)
+    _check(lib().oracle_adjoint_columns(b.ref, _ptr(U, _dp), _ptr(Rbar, _dp), int(extended), _ptr(Ub, _dp)),
+           "adjoint columns")
+    return Ub
 
 
 STEPS = {1: "face values", 2: "FV sub-cells", 3: "lifting value", 4: "DG lifting + volume",

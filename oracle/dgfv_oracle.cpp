@@ -24,6 +24,7 @@
 #include <cstring>
 #include <map>
 #include <stdexcept>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -494,6 +495,13 @@ T minmod(T a, T b) {
     return std::fabs(val(a)) <= std::fabs(val(b)) ? a : b;
 }
 
+// The step being counted, for the operation-counting instantiation only (the
+// other instantiations may run on several threads at once).
+template <class T>
+inline void set_phase(int ph) {
+    if constexpr (std::is_same_v<T, Counted>) flop_counter().phase = ph;
+}
+
 template <class T>
 void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
     const int V = P.V, nfv = P.nfv;
@@ -501,7 +509,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
     vector<ElemWork<T>> W(nel);
 
     // ---- step 1: face values of every element
-    flop_counter().phase = 1;
+    set_phase<T>(1);
 #pragma omp parallel for schedule(dynamic, 16) if (parallel)
     for (int e = 0; e < nel; ++e) {
         const Elem& E = P.el[e];
@@ -528,7 +536,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
             // V^{DG->FV} in all three directions, keeping the sub-cells next to face f
             // (counted with the FV step, which is where it is needed)
             const bool fv_neighbour = fv_across(P, E, f);
-            if (!E.fv && fv_neighbour && !parallel) flop_counter().phase = 2;
+            if (!E.fv && fv_neighbour && !parallel) set_phase<T>(2);
             if (!E.fv && fv_neighbour) {
                 const vector<double>& A = P.ops.d2f.at(E.N);
                 const int row = s ? P.nfv - 1 : 0;
@@ -543,12 +551,12 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
                         }
                 W[e].face_layer[f] = map_face(q, V, n, P.nfv, A);
             }
-            if (!parallel) flop_counter().phase = 1;
+            if (!parallel) set_phase<T>(1);
         }
     }
 
     // ---- step 2: FV sub-cell elements (Sec. 3.1.2)
-    flop_counter().phase = 2;
+    set_phase<T>(2);
 #pragma omp parallel for schedule(dynamic, 1) if (parallel)
     for (int e = 0; e < nel; ++e) {
         const Elem& E = P.el[e];
@@ -692,7 +700,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
     }
 
     // ---- step 3: BR1 lifting interface value U* = (u- + u+)/2 (Eq. 19)
-    flop_counter().phase = 3;
+    set_phase<T>(3);
 #pragma omp parallel for schedule(dynamic, 16) if (parallel)
     for (int e = 0; e < nel; ++e) {
         const Elem& E = P.el[e];
@@ -746,7 +754,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
     }
 
     // ---- step 4: lifting (Eq. 23) and volume integral (Eq. 22) of DG elements.
-    flop_counter().phase = 4;
+    set_phase<T>(4);
     // Cartesian elements: J = hx hy hz / 8, metric terms J dxi_d/dx_d = J (2/h_d),
     // so contravariant quantities divided by J carry the factor 2/h_d.
     // Reading (Eq. 23): the lifted variable is the gradient, g^d = +(1/J)[...].
@@ -829,7 +837,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
 
     // ---- step 5: face fluxes; every conforming face is visited once, from its
     // lower element L, every mortar once, from its big side
-    flop_counter().phase = 5;
+    set_phase<T>(5);
     for (int e = 0; e < nel; ++e)
         for (int f = 0; f < 6; ++f) W[e].flux[f].clear();
     // One side of a face: FV flag, degree, and its face data (DG trace of u or FV
@@ -942,7 +950,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
     }
 
     // ---- step 6: surface integral and -1/J (Eqs. 22, 26)
-    flop_counter().phase = 6;
+    set_phase<T>(6);
 #pragma omp parallel for schedule(dynamic, 16) if (parallel)
     for (int e = 0; e < nel; ++e) {
         const Elem& E = P.el[e];
@@ -976,7 +984,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
         }
         for (int i = 0; i < V * n3; ++i) R[E.off + i] = -div[i];
     }
-    flop_counter().phase = 0;
+    set_phase<T>(0);
 }
 
 // ------------------------------------------------------------------ time step, Sec. 3.3
@@ -1238,6 +1246,24 @@ void indicator(const Problem& P, const double* U, double* Ip, double* Ih) {
     }
 }
 
+// U_bar_j = sum_i R_bar_i (R'(U) e_j)_i for every j: the adjoint by columns of
+// the tangent, the problem set up once.  D carries the tangent, A the sum.
+template <class D, class A>
+static void adjoint_columns_t(const Problem& P, const double* U, const double* Rbar, double* Ubar) {
+#pragma omp parallel
+    {
+        vector<D> u(P.size), r(P.size);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t j = 0; j < P.size; ++j) {
+            for (int64_t i = 0; i < P.size; ++i) u[i] = D(U[i], i == j ? 1.0 : 0.0);
+            eval_rhs_t<D>(P, u.data(), r.data(), false);
+            A s = 0;
+            for (int64_t i = 0; i < P.size; ++i) s += (A)Rbar[i] * r[i].d;
+            Ubar[j] = (double)s;
+        }
+    }
+}
+
 }  // namespace
 
 // ==================================================================== C ABI
@@ -1280,6 +1306,28 @@ int oracle_eval_rhs_jvp(const oracle_problem* p, const double* U, const double* 
         for (int64_t i = 0; i < P.size; ++i) u[i] = Dual(U[i], dU[i]);
         eval_rhs_t<Dual>(P, u.data(), r.data());
         for (int64_t i = 0; i < P.size; ++i) { R[i] = r[i].v; dR[i] = r[i].d; }
+        return 0;
+    } catch (...) { return -1; }
+}
+
+int oracle_eval_rhs_jvp_extended(const oracle_problem* p, const double* U, const double* dU, double* R,
+                                 double* dR) {
+    try {
+        Problem P = make_problem(p);
+        vector<DualL> u(P.size), r(P.size);
+        for (int64_t i = 0; i < P.size; ++i) u[i] = DualL(U[i], dU[i]);
+        eval_rhs_t<DualL>(P, u.data(), r.data());
+        for (int64_t i = 0; i < P.size; ++i) { R[i] = (double)r[i].v; dR[i] = (double)r[i].d; }
+        return 0;
+    } catch (...) { return -1; }
+}
+
+int oracle_adjoint_columns(const oracle_problem* p, const double* U, const double* Rbar, int extended,
+                           double* Ubar) {
+    try {
+        Problem P = make_problem(p);
+        if (extended) adjoint_columns_t<DualL, long double>(P, U, Rbar, Ubar);
+        else adjoint_columns_t<Dual, double>(P, U, Rbar, Ubar);
         return 0;
     } catch (...) { return -1; }
 }

@@ -76,6 +76,18 @@ int oracle_eval_rhs_extended(const oracle_problem* p, const double* U, double* R
 int oracle_eval_rhs_jvp(const oracle_problem* p, const double* U, const double* dU,
                         double* R, double* dR);
 
+/* The same directional derivative with value and derivative carried in long
+   double, rounded to double at the end: the rounding-error reference of the
+   FP64 tangent (and of adjoints checked against it). */
+int oracle_eval_rhs_jvp_extended(const oracle_problem* p, const double* U, const double* dU,
+                                 double* R, double* dR);
+
+/* The whole adjoint U_bar = R'(U)^T R_bar, one entry per tangent along a unit
+   vector (n evaluations: tiny meshes only).  extended = 0: tangent and sum in
+   double; extended = 1: both in long double (the rounding reference). */
+int oracle_adjoint_columns(const oracle_problem* p, const double* U, const double* Rbar,
+                           int extended, double* Ubar);
+
 /* Floating-point operation count of one evaluation of R(U), counted on the
  * oracle's own arithmetic (abs and comparisons are not counted):
  * out[0] add/sub, out[1] mul, out[2] div, out[3] sqrt, out[4] unused, and per

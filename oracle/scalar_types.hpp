@@ -4,7 +4,8 @@
 //
 //   double  - the plain FP64 oracle.
 //   Dual    - forward-mode dual number a + b*eps, eps^2 = 0; gives exact
-//             directional derivatives R'(U)dU for adjoint dot-product tests.
+//             directional derivatives R'(U)dU for adjoint dot-product tests
+//             (DualL: the same in long double, the tangent's rounding reference).
 //   Counted - a double that counts the floating-point operations performed
 //             on it, to state the algorithmic flop count per degree of freedom.
 #ifndef DGFV_ORACLE_SCALAR_TYPES_HPP
@@ -26,32 +27,36 @@ inline long double sqrt_(long double a) { return std::sqrt(a); }
 inline long double abs_(long double a) { return std::fabs(a); }
 
 // ---------------------------------------------------------------- Dual
-struct Dual {
-    double v = 0.0, d = 0.0;
-    Dual() = default;
-    Dual(double x) : v(x), d(0.0) {}
-    Dual(double x, double dx) : v(x), d(dx) {}
+// DualT<R> carries value and derivative in R: Dual (double) for the FP64
+// tangent, DualL (long double) for its rounding-error reference.  The
+// operators are hidden friends so that a double converts implicitly.
+template <class R>
+struct DualT {
+    R v = 0, d = 0;
+    DualT() = default;
+    DualT(R x) : v(x), d(0) {}
+    DualT(R x, R dx) : v(x), d(dx) {}
+    friend DualT operator+(DualT a, DualT b) { return {a.v + b.v, a.d + b.d}; }
+    friend DualT operator-(DualT a, DualT b) { return {a.v - b.v, a.d - b.d}; }
+    friend DualT operator-(DualT a) { return {-a.v, -a.d}; }
+    friend DualT operator*(DualT a, DualT b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+    friend DualT operator/(DualT a, DualT b) { return {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)}; }
+    friend DualT& operator+=(DualT& a, DualT b) { a = a + b; return a; }
+    friend DualT& operator-=(DualT& a, DualT b) { a = a - b; return a; }
+    friend DualT& operator*=(DualT& a, DualT b) { a = a * b; return a; }
+    friend bool operator<(DualT a, DualT b) { return a.v < b.v; }
+    friend bool operator>(DualT a, DualT b) { return a.v > b.v; }
+    friend bool operator<=(DualT a, DualT b) { return a.v <= b.v; }
+    friend bool operator>=(DualT a, DualT b) { return a.v >= b.v; }
+    friend double val(DualT a) { return (double)a.v; }
+    friend DualT sqrt_(DualT a) {
+        R s = std::sqrt(a.v);
+        return {s, a.d / (2 * s)};
+    }
+    friend DualT abs_(DualT a) { return a.v < 0 ? -a : a; }
 };
-inline Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
-inline Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
-inline Dual operator-(Dual a) { return {-a.v, -a.d}; }
-inline Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
-inline Dual operator/(Dual a, Dual b) {
-    return {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)};
-}
-inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
-inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
-inline Dual& operator*=(Dual& a, Dual b) { a = a * b; return a; }
-inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
-inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
-inline bool operator<=(Dual a, Dual b) { return a.v <= b.v; }
-inline bool operator>=(Dual a, Dual b) { return a.v >= b.v; }
-inline double val(Dual a) { return a.v; }
-inline Dual sqrt_(Dual a) {
-    double s = std::sqrt(a.v);
-    return {s, a.d / (2.0 * s)};
-}
-inline Dual abs_(Dual a) { return a.v < 0.0 ? -a : a; }
+using Dual = DualT<double>;
+using DualL = DualT<long double>;
 
 // ---------------------------------------------------------------- Counted
 struct FlopCounter {

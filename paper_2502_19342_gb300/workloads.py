@@ -249,13 +249,17 @@ def _post_shock(gamma, Ms, rho1=1.0, p1=1.0):
     return rho1 * r, p1 * pr, u2
 
 
-def hp_shock(seed=0, nel=(16, 16, 16), riemann=0, mu=1e-4, y_bg=0.0):
+def hp_shock(seed=0, nel=(16, 16, 16), riemann=0, mu=1e-4, y_bg=0.0, perturb=0.0):
     """[0,2]x[0,1]x[0,1], periodic, 16^3 elements, N drawn from {2..6},
     N_FV = 7; a Mach 1.5 planar shock in air at x = 0.4 moving +x towards a
     bubble (r = 0.2, centre (0.8, 0.5, 0.5)) of the heavy species (density
     ratio 3.5), interface smoothed over 2 node spacings of degree 4.  y_bg: a
     background mass fraction of the heavy species (with none, the species'
-    round-off far from the bubble reads as noise to the modal indicator)."""
+    round-off far from the bubble reads as noise to the modal indicator).
+    perturb: relative amplitude of smooth sine perturbations of the partial
+    densities, the velocity and the pressure, so that no two neighbouring
+    values are equal up to rounding (a tangent through minmod slopes is then
+    defined by the data, not by rounding)."""
     sp = species_set([AIR, HEAVY], mu=mu)
     n_elem = nel[0] * nel[1] * nel[2]
     N = random_degrees(n_elem, 2, 6, seed)
@@ -274,6 +278,15 @@ def hp_shock(seed=0, nel=(16, 16, 16), riemann=0, mu=1e-4, y_bg=0.0):
         rho_pre = 1.0 / (Rm * T0)
         rho = rho_pre * (1 - s) + rho2 * s
         vx = s * u2
+        if perturb:
+            tw = 2 * np.pi
+            g1 = np.sin(tw * (0.5 * x + 0.13)) * np.sin(tw * (y + 0.31)) * np.sin(tw * (z + 0.57))
+            g2 = np.cos(tw * (0.5 * x + 0.71)) * np.sin(tw * (y + 0.17)) * np.cos(tw * (z + 0.43))
+            g3 = np.sin(tw * (x + 0.29)) * np.cos(tw * (y + 0.61)) * np.sin(tw * (z + 0.11))
+            p = p * (1 + perturb * g1)
+            rho = rho * (1 + perturb * g2)
+            return ([rho * (1 - Yb), rho * Yb],
+                    (vx + perturb * g3, perturb * g1, perturb * g2), p)
         return [rho * (1 - Yb), rho * Yb], (vx, 0.0 * x, 0.0 * x), p
 
     return prob, build_state(prob, fn)

@@ -62,6 +62,20 @@ def assert_rhs_close(oracle, prob, U, got, factor=3.0):
     return errs, own
 
 
+def assert_adjoint_close(oracle, prob, U, Rbar, got, factor=3.0):
+    """U_bar = R'(U)^T R_bar of the CUDA path against the oracle's adjoint by
+    columns (one exact tangent per unit vector; tiny meshes), with the bar of
+    R(U): per field max(RTOL, factor * e), e the FP64 oracle's own largest
+    per-field deviation from its long-double evaluation."""
+    ref = oracle.adjoint_columns(prob, U, Rbar, extended=True)
+    assert np.isfinite(ref).all(), "the oracle's adjoint is not finite on this input"
+    own = field_errors(prob, oracle.adjoint_columns(prob, U, Rbar), ref)
+    errs = field_errors(prob, got, ref)
+    bound = max(RTOL, factor * max(own))
+    assert all(e <= bound for e in errs), f"U_bar: per-field errors {errs}, bound {bound} (oracle's own {own})"
+    return errs, own
+
+
 def ctx_for(prob, opts=None, N_min=None, N_max=None):
     from paper_2502_19342_gb300 import dgfv
     return dgfv.Context(prob, N_min=N_min, N_max=N_max, opts=opts)

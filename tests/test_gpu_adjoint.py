@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2502_19342_gb300 import workloads as W
-from tests.gpu_helpers import ctx_for, per_field, to_dev
+from tests.gpu_helpers import assert_adjoint_close, ctx_for, per_field, to_dev
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
@@ -59,12 +59,7 @@ def test_rhs_vjp_full_adjoint_against_oracle_columns(oracle):
     Rbar = rng.standard_normal(U.size)
     ctx = ctx_for(prob, N_min=1, N_max=7)
     Ubar = ctx.rhs_vjp(to_dev(U), to_dev(Rbar)).cpu().numpy()
-    ref = np.zeros(U.size)
-    for j in range(U.size):
-        e = np.zeros(U.size)
-        e[j] = 1.0
-        ref[j] = np.dot(Rbar, oracle.eval_rhs_jvp(prob, U, e)[1])
-    np.testing.assert_allclose(Ubar, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+    assert_adjoint_close(oracle, prob, U, Rbar, Ubar)
     ctx.close()
 
 
@@ -273,12 +268,29 @@ def test_rhs_vjp_with_fv_elements_columns(oracle):
     Rbar = rng.standard_normal(U.size)
     ctx = ctx_for(prob, N_min=1, N_max=2)
     Ubar = ctx.rhs_vjp(to_dev(U), to_dev(Rbar)).cpu().numpy()
-    ref = np.zeros(U.size)
-    for j in range(U.size):
-        e = np.zeros(U.size)
-        e[j] = 1.0
-        ref[j] = np.dot(Rbar, oracle.eval_rhs_jvp(prob, U, e)[1])
-    np.testing.assert_allclose(Ubar, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+    assert_adjoint_close(oracle, prob, U, Rbar, Ubar)
+    ctx.close()
+
+
+@pytest.mark.parametrize("nk,riemann,nodes,split,suth,n_fv,seed,fv", [
+    (3, 1, 0, 0, False, 4, 41, [0, 1, 0, 0]), (2, 2, 0, 0, True, 4, 42, [0, 1, 0, 0]),
+    (2, 0, 1, 1, False, 4, 43, [1, 0, 0, 0]), (3, 2, 1, 1, True, 4, 44, [0, 1, 1, 0])])
+def test_rhs_vjp_columns_per_field(oracle, nk, riemann, nodes, split, suth, n_fv, seed, fv):
+    """Small hybrid meshes (2x2x1 elements of degree 1-3, one or two FV):
+    Roe-HH and the hybrid flux, Sutherland viscosity, LG and LGL nodes, the
+    standard and the split-form volume term; the whole U_bar field by field
+    against the oracle's adjoint by columns, with the bar of R(U)."""
+    prob, _ = _hybrid_problem(seed, nk=nk, nel=(2, 2, 1), Nlo=1, Nhi=3, n_fv=n_fv, mu=3e-3, riemann=riemann,
+                              nodes=nodes)
+    prob.update(fv=np.array(fv, np.uint8), split=split)
+    if suth:
+        prob.update(sutherland=1, T_ref=29.0, S_sutherland=29.0 * 110.4 / 273.15)
+    U = W.smooth_random_state(prob, seed, amp=0.1)
+    rng = np.random.default_rng(seed)
+    Rbar = rng.standard_normal(U.size)
+    ctx = ctx_for(prob, N_min=1, N_max=3)
+    Ubar = ctx.rhs_vjp(to_dev(U), to_dev(Rbar)).cpu().numpy()
+    assert_adjoint_close(oracle, prob, U, Rbar, Ubar)
     ctx.close()
 
 

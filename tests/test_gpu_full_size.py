@@ -2,7 +2,8 @@
 benchmark times (one launch per kernel over all degrees, autotuned volume
 tiles, fused face values): the 48^3 turbulence case after one adaptation (the
 decisions, the remapped state, R(U) and the time step), the 256 batched
-domains, the 16^3 mixing layer and the 16^3 hp shock case.
+domains, the 16^3 mixing layer and the 16^3 hp shock case; the adjoint on the
+mixing layer and on a hybrid DG/FV hp shock pattern.
 
 The FP64 oracle runs on the whole mesh (a few seconds on the host cores).  For
 the two large cases the long-double evaluation that fixes the small cases'
@@ -157,3 +158,66 @@ def test_mortar_half_refined_cube_full(oracle):
     dto = oracle.dt(prob, U, 0.5, 0.5)
     assert abs(dt[0] - dto[0]) <= 1e-13 * dto[0]
     ctx.close()
+
+
+def _hybrid_hp_shock(perturb=1e-4):
+    """The hp shock case with the elements on the shock (|x - 0.4| < 0.13) and
+    on the bubble's interface (|r - 0.2| < 0.07) switched to FV sub-cells by
+    the oracle's V^{DG->FV} (668 FV elements of 4,096).  The flow carries
+    smooth perturbations of relative size 1e-4: on the unperturbed state the
+    sub-cell means of the uniform regions differ by rounding only, so the
+    minmod branches there, and with them the tangent, are decided by rounding
+    (a relative change of 1e-15 in U moves the oracle's own <R_bar, J v> by
+    up to 40 %).  Larger perturbations raise the part of the tangent that the
+    LLF wave-speed maximum switches on near-equal sides (spread 3e-13 at
+    1e-4, 2e-11 at 1e-2, relative to the sum of the absolute terms)."""
+    import oracle as O
+    prob, U = W.hp_shock(0, perturb=perturb)
+    _, _, corner, h = W.element_index(prob)
+    xc = corner + 0.5 * h
+    r = np.sqrt(((xc - np.array([0.8, 0.5, 0.5])) ** 2).sum(1))
+    fv = ((np.abs(xc[:, 0] - 0.4) < 0.13) | (np.abs(r - 0.2) < 0.07)).astype(np.uint8)
+    return dict(prob, fv=fv), O.remap(prob, prob["N"], fv, U)
+
+
+@pytest.mark.parametrize("case", ["mixing_layer", "hp_shock_hybrid"])
+def test_rhs_vjp_full_size(oracle, case):
+    """The adjoint at full size: the mixing layer (4,096 elements, N = 4, 3
+    species; the adjoint workload) and the hp shock case with FV elements.
+    (a) <R_bar, J v> of the oracle's exact tangent = <U_bar, v> along two
+    random directions; (b) 16 sampled entries U_bar_j against the oracle's
+    column sum_i R_bar_i (J e_j)_i.  Bar: 1e-12 relative to the sum of the
+    absolute terms of the oracle's dot product, or 4 times the oracle's own
+    spread, whichever is larger: the change of its value when U moves by a
+    relative 1e-15 (the minmod and wave-speed branches make the Jacobian
+    piecewise, and a branch decided within rounding may go either way on
+    either side).  The oracle's own tangent sits ~1e-16 (same measure) from
+    its long-double value here."""
+    import math
+    from paper_2502_19342_gb300 import dgfv
+    prob, U = W.mixing_layer() if case == "mixing_layer" else _hybrid_hp_shock()
+    rng = np.random.default_rng(11)
+    Rbar = rng.standard_normal(U.size)
+    Up = U * (1 + 1e-15 * rng.standard_normal(U.size))
+    ctx = dgfv.Context(prob)
+    ctx.set_state(to_dev(U))
+    Ub = ctx.rhs_vjp(to_dev(U), to_dev(Rbar)).cpu().numpy()
+    ctx.close()
+    assert np.isfinite(Ub).all()
+
+    def bar(t, tp):
+        return max(1e-12 * np.abs(t).sum(), 4 * abs(math.fsum(t) - math.fsum(tp)))
+
+    for _ in range(2):
+        v = rng.standard_normal(U.size) * 1e-2 * np.abs(U).mean()
+        t = Rbar * oracle.eval_rhs_jvp(prob, U, v)[1]
+        tp = Rbar * oracle.eval_rhs_jvp(prob, Up, v)[1]
+        lhs, rhs = math.fsum(t), math.fsum(Ub * v)
+        assert abs(lhs - rhs) <= bar(t, tp), (lhs, rhs, bar(t, tp))
+    for j in rng.choice(U.size, 16, replace=False):
+        e = np.zeros(U.size)
+        e[j] = 1.0
+        t = Rbar * oracle.eval_rhs_jvp(prob, U, e)[1]
+        tp = Rbar * oracle.eval_rhs_jvp(prob, Up, e)[1]
+        ref = math.fsum(t)
+        assert abs(Ub[j] - ref) <= bar(t, tp), (int(j), Ub[j], ref, bar(t, tp))

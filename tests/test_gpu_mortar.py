@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2502_19342_gb300 import workloads as W
-from tests.gpu_helpers import assert_fields_close, assert_rhs_close, ctx_for, gpu_rhs, to_dev
+from tests.gpu_helpers import assert_adjoint_close, assert_fields_close, assert_rhs_close, ctx_for, gpu_rhs, to_dev
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
@@ -233,10 +233,5 @@ def test_rhs_vjp_on_mortar_chain_columns(oracle, fv):
     Rbar = rng.standard_normal(U.size)
     ctx = ctx_for(prob, N_min=1, N_max=2)
     Ubar = ctx.rhs_vjp(to_dev(U), to_dev(Rbar)).cpu().numpy()
-    ref = np.zeros(U.size)
-    for j in range(U.size):
-        e = np.zeros(U.size)
-        e[j] = 1.0
-        ref[j] = np.dot(Rbar, oracle.eval_rhs_jvp(prob, U, e)[1])
-    np.testing.assert_allclose(Ubar, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+    assert_adjoint_close(oracle, prob, U, Rbar, Ubar)
     ctx.close()

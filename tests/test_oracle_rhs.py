@@ -645,6 +645,23 @@ def test_jvp_matches_central_differences(oracle):
     assert np.abs(fd - dR).max() < 1e-6 * np.abs(dR).max()
 
 
+def test_extended_jvp_is_the_tangent_in_long_double(oracle):
+    """The long-double tangent (the rounding reference of adjoint parity) has
+    the extended evaluation's value, agrees with the FP64 tangent to rounding
+    and is linear in the direction (hybrid pattern, Roe-HH, Sutherland)."""
+    prob = _mixed_problem(7, nel=(2, 2, 2), Nlo=1, Nhi=4, fv_frac=0.3, n_fv=5)
+    prob.update(riemann=1, sutherland=1, T_ref=29.0, S_sutherland=11.7)
+    U = W.smooth_random_state(prob, 7, amp=0.1)
+    rng = np.random.default_rng(1)
+    dU = rng.standard_normal(U.size) * 1e-2 * np.abs(U).mean()
+    R, dR = oracle.eval_rhs_jvp(prob, U, dU)
+    Rx, dRx = oracle.eval_rhs_jvp_extended(prob, U, dU)
+    np.testing.assert_array_equal(Rx, oracle.eval_rhs_extended(prob, U))
+    assert np.abs(dRx - dR).max() < 1e-13 * np.abs(dRx).max()
+    _, d3 = oracle.eval_rhs_jvp_extended(prob, U, 3.0 * dU)
+    assert np.abs(d3 - 3.0 * dRx).max() < 1e-15 * np.abs(d3).max()
+
+
 # ---------------------------------------------------------------- split form on LGL nodes (Sec. 3.5)
 def _lgl_derivative_matrix(n):
     """D_ij = l_j'(x_i) on the LGL points from the monomial coefficients of the
