@@ -456,3 +456,26 @@ def test_all_fv_mesh_and_uniform_max_degree(oracle, riemann):
         Uo, _ = oracle.rk3(prob, U, 2, dt_fixed=1e-4)
         assert_fields_close(prob, ctx.get_state().cpu().numpy(), Uo, what=f"U(N={N}, fv={fv})")
         ctx.close()
+
+
+def test_degenerate_calls_leave_the_state_alone():
+    """Zero RK steps, an adaptation whose thresholds can never fire, and the
+    adjoint of a zero R_bar: the state and the pattern stay bitwise as they
+    were and U_bar is exactly zero; a host state of the wrong size is refused."""
+    from paper_2502_19342_gb300 import dgfv
+    prob, U = _mixed(3)
+    ctx = ctx_for(prob, N_min=1, N_max=7, opts=dict(thresholds=(-1e300, 1e300, -1e300, 1e300)))
+    ctx.set_state(to_dev(U))
+    ctx.rk_steps(0, -1.0, want_dt=False)
+    np.testing.assert_array_equal(ctx.get_state().cpu().numpy(), U)
+    N0, f0 = ctx.get_degrees()
+    st = ctx.adapt()
+    assert st["n_changed"] == 0 and st["n_near"] == 0
+    N1, f1 = ctx.get_degrees()
+    assert (N0 == N1).all() and (f0 == f1).all()
+    np.testing.assert_array_equal(ctx.get_state().cpu().numpy(), U)
+    Ub = ctx.rhs_vjp(to_dev(U), torch.zeros(U.size, dtype=torch.float64, device="cuda")).cpu().numpy()
+    assert np.isfinite(Ub).all() and not Ub.any()
+    with pytest.raises(dgfv.DgfvError):
+        ctx.set_state_host(np.zeros(U.size - 1))
+    ctx.close()
