@@ -57,8 +57,8 @@ __device__ __forceinline__ void adj_conf_body(const Params& P, const AdjBuffers&
         const int eL = Fc.L[fid], eR = Fc.R[fid];
         const int64_t sL = P.t.fo[eL] + (int64_t)(2 * D + 1) * nc2;
         const int64_t sR = P.t.fo[eR] + (int64_t)(2 * D) * nc2;
-        double uL[V], uR[V], gL[3 * V], gR[3 * V], Fb[V];
-        double uLb[V] = {}, uRb[V] = {}, gLb[3 * V] = {}, gRb[3 * V] = {};
+        double uL[V], uR[V], Fb[V];
+        double uLb[V] = {}, uRb[V] = {};
         const bool fv = P.t.fv[eL];  // conforming faces: both sides FV or both DG
         const double* us = fv ? P.b.frec : P.b.fu;
 #pragma unroll
@@ -68,24 +68,31 @@ __device__ __forceinline__ void adj_conf_body(const Params& P, const AdjBuffers&
             // L's slot holds +F, R's slot -F
             Fb[v] = A.fbar[sL * V + v * nc2 + p] - A.fbar[sR * V + v * nc2 + p];
         }
-        if (P.ph.viscous) {
+        // the viscous sides one after the other: each side's gradient trace is
+        // read just before its reverse and its adjoint stored right after
+        face_point_rev_seq<NK>(
+            P.ph, uL, uR, D, Fb, uLb, uRb, fv,
+            [&](int side, double* g) {
+                const int64_t sl = side ? sR : sL;
 #pragma unroll
-            for (int x = 0; x < 3 * V; ++x) {
-                gL[x] = P.b.fg[sL * 3 * V + x * nc2 + p];
-                gR[x] = P.b.fg[sR * 3 * V + x * nc2 + p];
-            }
-        }
-        face_point_rev<NK>(P.ph, uL, gL, uR, gR, D, Fb, uLb, gLb, uRb, gRb, fv);
+                for (int x = 0; x < 3 * V; ++x) g[x] = P.b.fg[sl * 3 * V + x * nc2 + p];
+            },
+            [&](int side, const double* gb) {
+                const int64_t sl = side ? sR : sL;
+#pragma unroll
+                for (int x = 0; x < 3 * V; ++x) A.gbar[sl * 3 * V + x * nc2 + p] = gb[x];
+            });
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             A.ubar[sL * V + v * nc2 + p] = uLb[v];
             A.ubar[sR * V + v * nc2 + p] = uRb[v];
         }
+        if (!P.ph.viscous)
 #pragma unroll
-        for (int x = 0; x < 3 * V; ++x) {
-            A.gbar[sL * 3 * V + x * nc2 + p] = gLb[x];
-            A.gbar[sR * 3 * V + x * nc2 + p] = gRb[x];
-        }
+            for (int x = 0; x < 3 * V; ++x) {
+                A.gbar[sL * 3 * V + x * nc2 + p] = 0.0;
+                A.gbar[sR * 3 * V + x * nc2 + p] = 0.0;
+            }
     }
 }
 
@@ -137,7 +144,6 @@ __device__ __forceinline__ void adj_mixed_point_body(const Params& P, const AdjB
                                                      const int32_t* __restrict__ items, int first, int count, int nc) {
     constexpr int V = NK + 4;
     const int nc2 = nc * nc;
-    const bool visc = P.ph.viscous;
     for (int t = threadIdx.x; t < count * nc2; t += blockDim.x) {
         const int k = items[first + t / nc2], p = t % nc2;
         const MixedFace m = mixed_face(P, Fc, mface[k]);
@@ -148,8 +154,8 @@ __device__ __forceinline__ void adj_mixed_point_body(const Params& P, const AdjB
         double* um = Sin + mpt[k] * 4 * V + p;
         double* gm = um + V * nc2;
         const double* fb = Sout + mpt[k] * V + p;
-        double uL[V], uR[V], gL[3 * V], gR[3 * V], Fb[V];
-        double uLb[V] = {}, uRb[V] = {}, gLb[3 * V] = {}, gRb[3 * V] = {};
+        double uL[V], uR[V], Fb[V];
+        double uLb[V] = {}, uRb[V] = {};
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const double a = um[v * nc2], b = ud[v * nc2];
@@ -157,28 +163,26 @@ __device__ __forceinline__ void adj_mixed_point_body(const Params& P, const AdjB
             uR[v] = m.mapL ? b : a;
             Fb[v] = fb[v * nc2];
         }
-        if (visc) {
-#pragma unroll
-            for (int x = 0; x < 3 * V; ++x) {
-                const double a = gm[x * nc2], b = gd[x * nc2];
-                gL[x] = m.mapL ? a : b;
-                gR[x] = m.mapL ? b : a;
-            }
-        }
-        face_point_rev<NK>(P.ph, uL, gL, uR, gR, D, Fb, uLb, gLb, uRb, gRb, m.cfv);
-        double* ubd = A.ubar + sd * V + p;
         double* gbd = A.gbar + sd * 3 * V + p;
+        // viscous sides one after the other; the mapped side's gradient adjoint
+        // replaces its gradient in Sin once that side is done
+        face_point_rev_seq<NK>(
+            P.ph, uL, uR, D, Fb, uLb, uRb, m.cfv,
+            [&](int side, double* g) {
+                const double* src = (side == 0) == m.mapL ? gm : gd;
+#pragma unroll
+                for (int x = 0; x < 3 * V; ++x) g[x] = src[x * nc2];
+            },
+            [&](int side, const double* gb) {
+                double* dst = (side == 0) == m.mapL ? gm : gbd;
+#pragma unroll
+                for (int x = 0; x < 3 * V; ++x) dst[x * nc2] = gb[x];
+            });
+        double* ubd = A.ubar + sd * V + p;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             ubd[v * nc2] = m.mapL ? uRb[v] : uLb[v];
             um[v * nc2] = m.mapL ? uLb[v] : uRb[v];
-        }
-        if (visc) {
-#pragma unroll
-            for (int x = 0; x < 3 * V; ++x) {
-                gbd[x * nc2] = m.mapL ? gRb[x] : gLb[x];
-                gm[x * nc2] = m.mapL ? gLb[x] : gRb[x];
-            }
         }
     }
 }
@@ -649,15 +653,19 @@ __global__ void __launch_bounds__(256) k_adj_fv(Params P, AdjBuffers A, Tiles T,
     __syncthreads();
     for (int c = threadIdx.x; c < n3; c += blockDim.x) {
         double u[V], w[V];
+#pragma unroll
         for (int v = 0; v < V; ++v) u[v] = sU[v * n3 + c];
         cons_to_w<NK>(P.ph, u, w);
+#pragma unroll
         for (int v = 0; v < V; ++v) sW[v * n3 + c] = w[v];
     }
     for (int c = threadIdx.x; c < 6 * n2; c += blockDim.x) {
         const int f = c / n2, p = c % n2;
         double u[V], w[V];
+#pragma unroll
         for (int v = 0; v < V; ++v) u[v] = sNb[(f * V + v) * n2 + p];
         cons_to_w<NK>(P.ph, u, w);
+#pragma unroll
         for (int v = 0; v < V; ++v) sNw[(f * V + v) * n2 + p] = w[v];
     }
     __syncthreads();
@@ -674,6 +682,7 @@ __global__ void __launch_bounds__(256) k_adj_fv(Params P, AdjBuffers A, Tiles T,
     // reconstructed reconstruction variables of cell m at its side (the forward's recon, before w_to_cons)
     auto reconw = [&](int d, int m, int a, int b, int side, double* w) {
         const double ilm = m > 0 ? il : sID[2 * d], ilp = m < n - 1 ? il : sID[2 * d + 1];
+#pragma unroll
         for (int v = 0; v < V; ++v) {
             const double wc = cellW(d, m, a, b, v);
             const double s = minmod((wc - cellW(d, m - 1, a, b, v)) * ilm, (cellW(d, m + 1, a, b, v) - wc) * ilp);
@@ -682,10 +691,12 @@ __global__ void __launch_bounds__(256) k_adj_fv(Params P, AdjBuffers A, Tiles T,
     };
     auto grad = [&](int i, int j, int k, double* g) {
         const int c3[3] = {i, j, k};
+#pragma unroll
         for (int dd = 0; dd < 3; ++dd) {
             const int m = c3[dd];
             const int a = dd == 0 ? j : i, b = dd == 2 ? j : k;
             const double sc = m == 0 ? sGS[2 * dd] : (m == n - 1 ? sGS[2 * dd + 1] : 0.5 * n * 0.5 * rh[dd]);
+#pragma unroll
             for (int v = 0; v < V; ++v)
                 g[dd * V + v] = (cellU(dd, m + 1, a, b, v) - cellU(dd, m - 1, a, b, v)) * sc;
         }
@@ -701,39 +712,47 @@ __global__ void __launch_bounds__(256) k_adj_fv(Params P, AdjBuffers A, Tiles T,
         const int d = t / nif, fidx = t - d * nif;
         const int m = fidx % (n - 1), p = fidx / (n - 1), a = p % n, b = p / n;
         const int cL = node_index(n, d, m, a, b), cR = node_index(n, d, m + 1, a, b);
-        double wL[V], wR[V], uL[V], uR[V], gL[3 * V], gR[3 * V], Fb[V];
-        double uLb[V] = {}, uRb[V] = {}, gLb[3 * V] = {}, gRb[3 * V] = {};
-        reconw(d, m, a, b, +1, wL);
-        reconw(d, m + 1, a, b, -1, wR);
-        w_to_cons<NK>(P.ph, wL, uL);
-        w_to_cons<NK>(P.ph, wR, uR);
-        int i, j, k;
-        if (visc) {
-            coords(d, m, a, b, i, j, k);
-            grad(i, j, k, gL);
-            coords(d, m + 1, a, b, i, j, k);
-            grad(i, j, k, gR);
+        double uL[V], uR[V], Fb[V];
+        double uLb[V] = {}, uRb[V] = {};
+        {
+            double wL[V], wR[V];
+            reconw(d, m, a, b, +1, wL);
+            reconw(d, m + 1, a, b, -1, wR);
+            w_to_cons<NK>(P.ph, wL, uL);
+            w_to_cons<NK>(P.ph, wR, uR);
         }
         const double sc = 0.5 * n * rh[d];
+#pragma unroll
         for (int v = 0; v < V; ++v) Fb[v] = sc * (Rb[off + (int64_t)v * n3 + cR] - Rb[off + (int64_t)v * n3 + cL]);
-        face_point_rev<NK>(P.ph, uL, gL, uR, gR, d, Fb, uLb, gLb, uRb, gRb, true);
+        // viscous sides one after the other: a cell's gradient is formed just
+        // before its reverse and its adjoint summed into gradb right after
+        face_point_rev_seq<NK>(
+            P.ph, uL, uR, d, Fb, uLb, uRb, true,
+            [&](int side, double* g) {
+                int i, j, k;
+                coords(d, m + side, a, b, i, j, k);
+                grad(i, j, k, g);
+            },
+            [&](int side, const double* gb) {
+                const int c = side ? cR : cL;
+#pragma unroll
+                for (int x = 0; x < 3 * V; ++x) atomicAdd(&gradb[x * n3 + c], gb[x]);
+            });
+#pragma unroll
         for (int v = 0; v < V; ++v) {
             recb[((2 * d + 1) * V + v) * n3 + cL] = uLb[v];  // side + of the left cell
             recb[((2 * d) * V + v) * n3 + cR] = uRb[v];      // side - of the right cell
         }
-        if (visc)
-            for (int x = 0; x < 3 * V; ++x) {
-                atomicAdd(&gradb[x * n3 + cL], gLb[x]);
-                atomicAdd(&gradb[x * n3 + cR], gRb[x]);
-            }
     }
     // 2. element faces: the face kernels' adjoints of the reconstructed face state and boundary gradient
     for (int i = threadIdx.x; i < 6 * n2; i += blockDim.x) {
         const int f = i / n2, p = i % n2, d = f >> 1, s = f & 1;
         const int c = node_index(n, d, s ? n - 1 : 0, p % n, p / n);
         const int64_t slot = P.t.fo[e] + (int64_t)f * n2;
+#pragma unroll
         for (int v = 0; v < V; ++v) recb[(f * V + v) * n3 + c] = A.ubar[slot * V + v * n2 + p];
         if (visc)
+#pragma unroll
             for (int x = 0; x < 3 * V; ++x) atomicAdd(&gradb[x * n3 + c], A.gbar[slot * 3 * V + x * n2 + p]);
     }
     __syncthreads();
@@ -757,12 +776,14 @@ __global__ void __launch_bounds__(256) k_adj_fv(Params P, AdjBuffers A, Tiles T,
         double wp[V], wm[V], wpb[V] = {}, wmb[V] = {}, rp[V], rm[V];
         reconw(d, m, a, b, +1, wp);
         reconw(d, m, a, b, -1, wm);
+#pragma unroll
         for (int v = 0; v < V; ++v) {
             rp[v] = recb[((2 * d + 1) * V + v) * n3 + c];
             rm[v] = recb[((2 * d) * V + v) * n3 + c];
         }
         w_to_cons_rev<NK>(P.ph, wp, rp, wpb);
         w_to_cons_rev<NK>(P.ph, wm, rm, wmb);
+#pragma unroll
         for (int v = 0; v < V; ++v) {
             // w+- = wc +- s l/2
             const double sb = 0.5 * l * (wpb[v] - wmb[v]);
@@ -782,6 +803,7 @@ __global__ void __launch_bounds__(256) k_adj_fv(Params P, AdjBuffers A, Tiles T,
         if (visc) {
             // g_d(c) = (u(m+1) - u(m-1)) sc
             const double sc = m == 0 ? sGS[2 * d] : (m == n - 1 ? sGS[2 * d + 1] : 0.5 * n * 0.5 * rh[d]);
+#pragma unroll
             for (int v = 0; v < V; ++v) {
                 const double g = gradb[(d * V + v) * n3 + c] * sc;
                 add_u(d, m + 1, a, b, v, g);
@@ -793,23 +815,27 @@ __global__ void __launch_bounds__(256) k_adj_fv(Params P, AdjBuffers A, Tiles T,
     // 4. cons_to_w^T: the element's U_bar and the neighbour values' adjoints
     for (int c = threadIdx.x; c < n3; c += blockDim.x) {
         double u[V], wb[V], ub[V];
+#pragma unroll
         for (int v = 0; v < V; ++v) {
             u[v] = sU[v * n3 + c];
             wb[v] = wbar[v * n3 + c];
             ub[v] = ubc[v * n3 + c];
         }
         cons_to_w_rev<NK>(P.ph, u, wb, ub);
+#pragma unroll
         for (int v = 0; v < V; ++v) Ub[off + (int64_t)v * n3 + c] = ub[v];
     }
     for (int i = threadIdx.x; i < 6 * n2; i += blockDim.x) {
         const int f = i / n2, p = i % n2;
         double u[V], wb[V], ub[V];
+#pragma unroll
         for (int v = 0; v < V; ++v) {
             u[v] = sNb[(f * V + v) * n2 + p];
             wb[v] = nbwb[(f * V + v) * n2 + p];
             ub[v] = nbub[(f * V + v) * n2 + p];
         }
         cons_to_w_rev<NK>(P.ph, u, wb, ub);
+#pragma unroll
         for (int v = 0; v < V; ++v) nbub[(f * V + v) * n2 + p] = ub[v];
     }
 }

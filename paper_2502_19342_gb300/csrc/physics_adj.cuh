@@ -568,10 +568,13 @@ DGFV_HD void riemann_roe_rev(const DevPhys& P, const double* uL, const Prim<NK>&
     bR.rho += rRb * 0.5 / rR;
 }
 
-template <int NK>
-DGFV_HD void face_point_rev(const DevPhys& P, const double* uL, const double* gL, const double* uR,
-                            const double* gR, int d, const double* Fb, double* uLb, double* gLb, double* uRb,
-                            double* gRb, bool fv_involved = false) {
+// Reverse of the interface flux with the two viscous sides one after the
+// other: getg(side, g) supplies a side's gradient (side 0 = L, 1 = R) just
+// before its reverse and putgb(side, gb) receives its adjoint right after, so
+// only one side's gradient and gradient adjoint are live at a time.
+template <int NK, class GetG, class PutGb>
+DGFV_HD void face_point_rev_seq(const DevPhys& P, const double* uL, const double* uR, int d, const double* Fb,
+                                double* uLb, double* uRb, bool fv_involved, GetG getg, PutGb putgb) {
     constexpr int V = NK + 4;
     Prim<NK> sL, sR;
     prim<NK>(P, uL, sL);
@@ -606,19 +609,46 @@ DGFV_HD void face_point_rev(const DevPhys& P, const double* uL, const double* gL
         }
     }
     if (P.viscous) {
-        PrimGrad<NK> G;
-        PrimGradBar<NK> Gb;
-        prim_grad<NK>(P, sL, gL, G);
-        zero(Gb);
-        flux_visc_rev<NK>(P, sL, G, d, half, Gb, bL);
-        prim_grad_rev<NK>(P, sL, gL, G, Gb, gLb, bL);
-        prim_grad<NK>(P, sR, gR, G);
-        zero(Gb);
-        flux_visc_rev<NK>(P, sR, G, d, half, Gb, bR);
-        prim_grad_rev<NK>(P, sR, gR, G, Gb, gRb, bR);
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const Prim<NK>& s = side ? sR : sL;
+            PrimBar<NK>& b = side ? bR : bL;
+            double g[3 * V], gb[3 * V];
+            getg(side, g);
+#pragma unroll
+            for (int x = 0; x < 3 * V; ++x) gb[x] = 0.0;
+            PrimGrad<NK> G;
+            PrimGradBar<NK> Gb;
+            prim_grad<NK>(P, s, g, G);
+            zero(Gb);
+            flux_visc_rev<NK>(P, s, G, d, half, Gb, b);
+            prim_grad_rev<NK>(P, s, g, G, Gb, gb, b);
+            putgb(side, gb);
+        }
     }
     prim_rev<NK>(P, uL, sL, bL, uLb);
     prim_rev<NK>(P, uR, sR, bR, uRb);
+}
+
+// The same with both gradients given and both gradient adjoints accumulated
+// into gLb, gRb.
+template <int NK>
+DGFV_HD void face_point_rev(const DevPhys& P, const double* uL, const double* gL, const double* uR,
+                            const double* gR, int d, const double* Fb, double* uLb, double* gLb, double* uRb,
+                            double* gRb, bool fv_involved = false) {
+    constexpr int V = NK + 4;
+    face_point_rev_seq<NK>(
+        P, uL, uR, d, Fb, uLb, uRb, fv_involved,
+        [&](int side, double* g) {
+            const double* src = side ? gR : gL;
+#pragma unroll
+            for (int x = 0; x < 3 * V; ++x) g[x] = src[x];
+        },
+        [&](int side, const double* gb) {
+            double* dst = side ? gRb : gLb;
+#pragma unroll
+            for (int x = 0; x < 3 * V; ++x) dst[x] += gb[x];
+        });
 }
 
 }  // namespace dgfv
