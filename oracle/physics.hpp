@@ -163,18 +163,25 @@ void riemann_llf(const Phys& P, const T* uL, const Prim<T>& sL, const T* uR, con
 
 // Roe flux with the Harten-Hyman entropy fix (Sec. 3.1.1, the default
 // convective interface flux), written for the ideal-gas mixture.  The paper
-// does not state the mixture average; this oracle uses:
-//   sqrt(rho)-weighted averages v~, H~ (H = E + p/rho), Y~;  rho~ = sqrt(rho_L rho_R);
-//   kappa~ = c_p,mix(Y~)/c_v,mix(Y~);  c~^2 = (kappa~ - 1)(H~ - |v~|^2/2);  p~ = rho~ c~^2/kappa~.
-// The jump is decomposed on the eigenvectors of the frozen-mixture Jacobian:
+// does not state the mixture average.  This oracle takes the one that makes the
+// linearisation exact (Roe's property U: A~ (u_R - u_L) = F(u_R) - F(u_L)).
+// With p = sum_k rho_k R_k T and rho e = sum_k rho_k c_v,k T, the jump rule
+// d(ab) = a_bar db + b_bar da (arithmetic means) gives exactly
+//   dp = (kappa~ - 1) [d(rho E) - v~.d(rho v) + |v~|^2/2 d rho] + sum_k psi_k d rho_k,
+//   kappa~ - 1 = sum_k R_k rho_k,bar / sum_k c_v,k rho_k,bar,
+//   psi_k = T_bar (c_p,k - kappa~ c_v,k),
+// where rho_k,bar and T_bar are the arithmetic means of the two sides and
+// v~, H~ (H = E + p/rho), Y~ the sqrt(rho)-weighted averages, rho~ = sqrt(rho_L rho_R).
+// The sound speed of that linearisation is
+//   c~^2 = sum_k Y~_k psi_k + (kappa~ - 1)(H~ - |v~|^2/2)
+// (for one species, or species of equal gamma, every psi_k is 0: the textbook
+// Roe average).  The jump is decomposed on the eigenvectors of A~:
 //   acoustic  v_n -+ c:  r = (Y~_k; v~ -+ c~ n; H~ -+ c~ v~_n),  a = (dp -+ rho~ c~ dv_n)/(2 c~^2)
-//   contact, species k:  r = (e_k; v~; |v~|^2/2 + eps_k),       a = d(rho_k) - Y~_k dp/c~^2
+//   contact, species k:  r = (e_k; v~; |v~|^2/2 - psi_k/(kappa~ - 1)),  a = d(rho_k) - Y~_k dp/c~^2
 //   shear, t != n:       r = (0; t; v~_t),                       a = rho~ dv_t
-// with eps_k = d(rho eps)/d(rho_k) at fixed p and v
-//            = -p~ (c_p,k - kappa~ c_v,k) / ((kappa~ - 1)^2 rho~ c_v,mix(Y~)),
-// which vanishes for a single species (the textbook Roe solver).  The
-// Harten-Hyman fix replaces |lambda| by delta = max(0, lambda~ - lambda_L,
-// lambda_R - lambda~) where |lambda| < delta, on the two acoustic waves.
+// (the contact vector carries no pressure change).  The Harten-Hyman fix
+// replaces |lambda| by delta = max(0, lambda~ - lambda_L, lambda_R - lambda~)
+// where |lambda| < delta, on the two acoustic waves.
 template <class T>
 void riemann_roe(const Phys& P, const T* uL, const Prim<T>& sL, const T* uR, const Prim<T>& sR,
                  int d, T* F) {
@@ -189,17 +196,24 @@ void riemann_roe(const Phys& P, const T* uL, const Prim<T>& sL, const T* uR, con
     for (int k = 0; k < nk; ++k) Yt[k] = (rL * sL.Y[k] + rR * sR.Y[k]) / wsum;
     T HL = (uL[nk + 3] + sL.p) / sL.rho, HR = (uR[nk + 3] + sR.p) / sR.rho;
     T Ht = (rL * HL + rR * HR) / wsum;
-    T cvt = Yt[0] * T(P.cv[0]), cpt = Yt[0] * T(P.cp[0]);
+    // kappa~ from the arithmetic-mean partial densities; T_bar the mean temperature
+    T rbar = T(0.5) * (uL[0] + uR[0]);
+    T cvb = rbar * T(P.cv[0]), Rb = rbar * T(P.R[0]);
     for (int k = 1; k < nk; ++k) {
-        cvt = cvt + Yt[k] * T(P.cv[k]);
-        cpt = cpt + Yt[k] * T(P.cp[k]);
+        rbar = T(0.5) * (uL[k] + uR[k]);
+        cvb = cvb + rbar * T(P.cv[k]);
+        Rb = Rb + rbar * T(P.R[k]);
     }
-    T kt = cpt / cvt;
+    T km1 = Rb / cvb;
+    T kt = km1 + T(1.0);
+    T Tbar = T(0.5) * (sL.temp + sR.temp);
+    T psi[MAXSP];
+    for (int k = 0; k < nk; ++k) psi[k] = Tbar * (T(P.cp[k]) - kt * T(P.cv[k]));
     T q2 = vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2];
-    T c2 = (kt - T(1.0)) * (Ht - T(0.5) * q2);
+    T c2 = km1 * (Ht - T(0.5) * q2);
+    for (int k = 0; k < nk; ++k) c2 = c2 + Yt[k] * psi[k];
     T ct = sqrt_(c2);
     T rt = rL * rR;
-    T pt = rt * c2 / kt;
     T vn = vt[d];
     T dp = sR.p - sL.p;
     T dv[3];
@@ -229,7 +243,7 @@ void riemann_roe(const Phys& P, const T* uL, const Prim<T>& sL, const T* uR, con
     // contact waves, one per species
     for (int k = 0; k < nk; ++k) {
         T ak = (uR[k] - uL[k]) - Yt[k] * dp / c2;
-        T epsk = -(pt * (T(P.cp[k]) - kt * T(P.cv[k]))) / ((kt - T(1.0)) * (kt - T(1.0)) * rt * cvt);
+        T epsk = -(psi[k] / km1);
         T s = l0 * ak;
         Dis[k] = Dis[k] + s;
         for (int i = 0; i < 3; ++i) Dis[nk + i] = Dis[nk + i] + s * vt[i];

@@ -270,6 +270,91 @@ def test_llf_textbook_form(oracle):
                                    rtol=1e-14, atol=1e-15)
 
 
+def _euler_flux(prob, u, d):
+    """Convective flux of one state in direction d, written out from Eq. 1 with
+    the ideal-gas mixture law p = (kappa - 1)(rho E - rho|v|^2/2), kappa = c_p/c_v."""
+    nk = len(prob["gamma"])
+    rk = u[:nk]
+    rho = rk.sum()
+    v = u[nk:nk + 3] / rho
+    cv = prob["Rgas"] / (prob["gamma"] - 1)
+    kap = (rk @ (cv * prob["gamma"])) / (rk @ cv)
+    p = (kap - 1) * (u[nk + 3] - 0.5 * rho * v @ v)
+    F = u * v[d]
+    F[nk + d] += p
+    F[nk + 3] += p * v[d]
+    return F, p
+
+
+def _mixture_state(prob, rho_k, v, p):
+    nk = len(rho_k)
+    rho_k = np.asarray(rho_k, float)
+    v = np.asarray(v, float)
+    cv = prob["Rgas"][:nk] / (prob["gamma"][:nk] - 1)
+    kap = (rho_k @ (cv * prob["gamma"][:nk])) / (rho_k @ cv)
+    return np.concatenate([rho_k, rho_k.sum() * v, [p / (kap - 1) + 0.5 * rho_k.sum() * v @ v]])
+
+
+@pytest.mark.parametrize("nk", [2, 3])
+def test_roe_mixture_property_u_supersonic(oracle, nk):
+    """Roe's property U for the mixture average (Sec. 3.1.1): when every wave
+    of the linearisation moves the same way and the entropy fix is inactive,
+    |A~| = +-A~ and A~(u_R - u_L) = F(u_R) - F(u_L) make the Roe flux the
+    upwind flux exactly: F* = F(u_L) for v_n - c > 0 on both sides, F(u_R) for
+    v_n + c < 0.  Species of different gamma and R, unequal compositions and
+    temperatures on the two sides.  (The mixture average with kappa~ taken
+    from the sqrt(rho)-weighted mass fractions misses this by 2e-4 .. 1e-3.)"""
+    prob = _prob(nk, riemann=1)
+    rng = np.random.default_rng(40 + nk)
+    for trial in range(6):
+        rkL = np.array([0.6, 0.3, 0.2][:nk]) * (0.5 + rng.random(nk))
+        rkR = np.array([0.2, 0.7, 0.1][:nk]) * (0.5 + rng.random(nk))
+        for d in range(3):
+            for sign in (1.0, -1.0):
+                vL = rng.standard_normal(3) * 0.2
+                vR = vL + rng.standard_normal(3) * 0.05
+                vL[d] = sign * (3.0 + 0.1 * rng.random())
+                vR[d] = sign * (3.0 + 0.1 * rng.random())
+                uL = _mixture_state(prob, rkL, vL, 1.0 + 0.2 * rng.random())
+                uR = _mixture_state(prob, rkR, vR, 1.0 + 0.2 * rng.random())
+                sL, sR = oracle.primitives(prob, uL), oracle.primitives(prob, uR)
+                if sign > 0:
+                    assert vL[d] - sL["c"] > 0 and vR[d] - sR["c"] > 0
+                else:
+                    assert vL[d] + sL["c"] < 0 and vR[d] + sR["c"] < 0
+                F = oracle.riemann(prob, uL, uR, d)
+                Fup, _ = _euler_flux(prob, uL if sign > 0 else uR, d)
+                np.testing.assert_allclose(F, Fup, rtol=0, atol=1e-14 * np.abs(Fup).max())
+
+
+@pytest.mark.parametrize("nk", [2, 3])
+def test_roe_mixture_contact_discontinuities(oracle, nk):
+    """Contact between two mixtures of different gamma and R at equal pressure
+    and velocity (different compositions and temperatures), Sec. 3.1.1.
+    At rest the exact flux carries no mass, species or energy and the momentum
+    flux is p n; moving with v_n != 0 the jump lies entirely in the contact
+    waves of an exact linearisation, so the Roe flux is the upwind flux."""
+    prob = _prob(nk, riemann=1)
+    rng = np.random.default_rng(60 + nk)
+    for trial in range(6):
+        rkL = np.array([0.9, 0.1, 0.3][:nk]) * (0.5 + rng.random(nk))
+        rkR = np.array([0.1, 0.8, 0.05][:nk]) * (0.5 + rng.random(nk))
+        p = 0.5 + rng.random()
+        for d in range(3):
+            uL = _mixture_state(prob, rkL, (0, 0, 0), p)
+            uR = _mixture_state(prob, rkR, (0, 0, 0), p)
+            F = oracle.riemann(prob, uL, uR, d)
+            expect = np.zeros(nk + 4)
+            expect[nk + d] = p
+            np.testing.assert_allclose(F, expect, rtol=0, atol=1e-14 * p)
+            v = rng.standard_normal(3) * 0.3
+            uL = _mixture_state(prob, rkL, v, p)
+            uR = _mixture_state(prob, rkR, v, p)
+            F = oracle.riemann(prob, uL, uR, d)
+            Fup, _ = _euler_flux(prob, uL if v[d] > 0 else uR, d)
+            np.testing.assert_allclose(F, Fup, rtol=0, atol=1e-14 * np.abs(Fup).max())
+
+
 def _at_temperature(prob, T, rho=1.0):
     """Single-species state at rest with temperature T."""
     cv = prob["Rgas"][0] / (prob["gamma"][0] - 1)
