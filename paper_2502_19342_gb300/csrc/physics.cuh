@@ -200,11 +200,16 @@ DGFV_HD void riemann_llf(const double* uL, const Prim<NK>& sL, const double* uR,
     for (int v = 0; v < V; ++v) F[v] = 0.5 * ((FL[v] + FR[v]) - smax * (uR[v] - uL[v]));
 }
 
-// Roe flux with the Harten-Hyman entropy fix for the ideal-gas mixture:
-// sqrt(rho)-weighted averages of v, H, Y; kappa~ = c_p(Y~)/c_v(Y~);
-// c~^2 = (kappa~ - 1)(H~ - |v~|^2/2); waves v_n - c, v_n (contact per
-// species, shear), v_n + c; contact energy term eps_k = d(rho eps)/d(rho_k)
-// at fixed p and v; Harten-Hyman fix on the acoustic waves.
+// Roe flux with the Harten-Hyman entropy fix for the ideal-gas mixture, with
+// the average that linearises the mixture pressure exactly (Roe's property U,
+// A~ (u_R - u_L) = F(u_R) - F(u_L)): sqrt(rho)-weighted v~, H~, Y~;
+// kappa~ - 1 = sum R_k rho_k,bar / sum c_v,k rho_k,bar and
+// psi_k = T_bar (c_p,k - kappa~ c_v,k) from the arithmetic means of the partial
+// densities and temperatures, so that dp = (kappa~ - 1)(d(rho E) - v~.d(rho v)
+// + |v~|^2/2 d rho) + sum psi_k d rho_k holds exactly;
+// c~^2 = sum Y~_k psi_k + (kappa~ - 1)(H~ - |v~|^2/2); waves v_n - c,
+// v_n (contact per species with energy entry |v~|^2/2 - psi_k/(kappa~ - 1),
+// shear), v_n + c; Harten-Hyman fix on the acoustic waves.
 template <int NK>
 DGFV_HD void riemann_roe(const DevPhys& P, const double* uL, const Prim<NK>& sL,
                                             const double* uR, const Prim<NK>& sR, int d, double* F) {
@@ -218,18 +223,26 @@ DGFV_HD void riemann_roe(const DevPhys& P, const double* uL, const Prim<NK>& sL,
     double vt[3], Yt[NK];
 #pragma unroll
     for (int i = 0; i < 3; ++i) vt[i] = wl * sL.v[i] + wr * sR.v[i];
-    double cvt = 0.0, cpt = 0.0;
 #pragma unroll
-    for (int k = 0; k < NK; ++k) {
-        Yt[k] = wl * sL.Y[k] + wr * sR.Y[k];
-        cvt = fma(Yt[k], P.cv[k], cvt);
-        cpt = fma(Yt[k], P.cp[k], cpt);
-    }
+    for (int k = 0; k < NK; ++k) Yt[k] = wl * sL.Y[k] + wr * sR.Y[k];
     const double HL = sL.E + sL.p * sL.irho, HR = sR.E + sR.p * sR.irho;
     const double Ht = wl * HL + wr * HR;
-    const double kt = cpt / cvt;
+    // kappa~ - 1 from the arithmetic-mean partial densities (the factor 1/2 cancels)
+    double cvb = 0.0, Rb = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const double rs = uL[k] + uR[k];
+        cvb = fma(rs, P.cv[k], cvb);
+        Rb = fma(rs, P.cp[k] - P.cv[k], Rb);
+    }
+    const double km1 = Rb / cvb;
+    const double kt = km1 + 1.0;
+    const double Tbar = 0.5 * (sL.T + sR.T);
+    double ypsi = 0.0;  // sum_k Y~_k (c_p,k - kappa~ c_v,k)
+#pragma unroll
+    for (int k = 0; k < NK; ++k) ypsi = fma(Yt[k], P.cp[k] - kt * P.cv[k], ypsi);
     const double q2 = vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2];
-    const double c2 = (kt - 1.0) * (Ht - 0.5 * q2);
+    const double c2 = km1 * (Ht - 0.5 * q2) + Tbar * ypsi;
     const double ct = sqrt(c2);
     const double ic2 = 1.0 / c2;
     const double rt = rL * rR;
@@ -260,8 +273,7 @@ DGFV_HD void riemann_roe(const DevPhys& P, const double* uL, const Prim<NK>& sL,
     Dis[NK + d] += sd;
     Dis[NK + 3] = sa * Ht + sd * vn;
     // contact waves
-    const double pt = rt * c2 / kt;
-    const double ecoef = -pt / ((kt - 1.0) * (kt - 1.0) * rt * cvt);
+    const double ecoef = -Tbar / km1;
     double scon = 0.0, econ = 0.0;
 #pragma unroll
     for (int k = 0; k < NK; ++k) {

@@ -366,17 +366,25 @@ DGFV_HD void riemann_roe_rev(const DevPhys& P, const double* uL, const Prim<NK>&
     const double wl = rL * iw, wr = rR * iw;
     double vt[3], Yt[NK];
     for (int i = 0; i < 3; ++i) vt[i] = wl * sL.v[i] + wr * sR.v[i];
-    double cvt = 0.0, cpt = 0.0;
-    for (int k = 0; k < NK; ++k) {
-        Yt[k] = wl * sL.Y[k] + wr * sR.Y[k];
-        cvt = fma(Yt[k], P.cv[k], cvt);
-        cpt = fma(Yt[k], P.cp[k], cpt);
-    }
+    for (int k = 0; k < NK; ++k) Yt[k] = wl * sL.Y[k] + wr * sR.Y[k];
     const double HL = sL.E + sL.p * sL.irho, HR = sR.E + sR.p * sR.irho;
     const double Ht = wl * HL + wr * HR;
-    const double kt = cpt / cvt;
+    double cvb = 0.0, Rb = 0.0;
+    for (int k = 0; k < NK; ++k) {
+        const double rs = uL[k] + uR[k];
+        cvb = fma(rs, P.cv[k], cvb);
+        Rb = fma(rs, P.cp[k] - P.cv[k], Rb);
+    }
+    const double km1 = Rb / cvb;
+    const double kt = km1 + 1.0;
+    const double Tbar = 0.5 * (sL.T + sR.T);
+    double ypsi = 0.0, ycv = 0.0;
+    for (int k = 0; k < NK; ++k) {
+        ypsi = fma(Yt[k], P.cp[k] - kt * P.cv[k], ypsi);
+        ycv = fma(Yt[k], P.cv[k], ycv);
+    }
     const double q2 = vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2];
-    const double c2 = (kt - 1.0) * (Ht - 0.5 * q2);
+    const double c2 = km1 * (Ht - 0.5 * q2) + Tbar * ypsi;
     const double ct = sqrt(c2);
     const double ic2 = 1.0 / c2;
     const double rt = rL * rR;
@@ -402,9 +410,7 @@ DGFV_HD void riemann_roe_rev(const DevPhys& P, const double* uL, const Prim<NK>&
     const double l0 = fabs(vn);
     const double sa = lm * am + lp * ap;
     const double sd = (lp * ap - lm * am) * ct;
-    const double pt = rt * c2 / kt;
-    const double Dn = (kt - 1.0) * (kt - 1.0) * rt * cvt;
-    const double ecoef = -pt / Dn;
+    const double ecoef = -Tbar / km1;
     double ak[NK], sk[NK], scon = 0.0;
     for (int k = 0; k < NK; ++k) {
         ak[k] = (uR[k] - uL[k]) - Yt[k] * dp * ic2;
@@ -422,8 +428,8 @@ DGFV_HD void riemann_roe_rev(const DevPhys& P, const double* uL, const Prim<NK>&
     double vtb[3] = {0.0, 0.0, 0.0}, Ytb[NK], dvb[3] = {0.0, 0.0, 0.0};
     for (int k = 0; k < NK; ++k) Ytb[k] = 0.0;
     double l0b = 0.0, rtb = 0.0, q2b = 0.0, ktb = 0.0, ecoefb = 0.0, dpb = 0.0, ic2b = 0.0, sab = 0.0, sdb = 0.0;
-    double Htb = 0.0, vnb = 0.0, lmb = 0.0, lpb = 0.0, amb = 0.0, apb = 0.0, ctb = 0.0, c2b = 0.0, cvtb = 0.0;
-    double cptb = 0.0;
+    double Htb = 0.0, vnb = 0.0, lmb = 0.0, lpb = 0.0, amb = 0.0, apb = 0.0, ctb = 0.0, c2b = 0.0;
+    double km1b = 0.0, Tbarb = 0.0;
     // shear waves: s = l0 rt dv_i; Dis[m_i] += s; Dis[E] += s vt_i
     for (int i = 0; i < 3; ++i) {
         if (i == d) continue;
@@ -455,15 +461,9 @@ DGFV_HD void riemann_roe_rev(const DevPhys& P, const double* uL, const Prim<NK>&
         dpb -= akb * Yt[k] * ic2;
         ic2b -= akb * Yt[k] * dp;
     }
-    // ecoef = -pt / Dn, Dn = (kt - 1)^2 rt cvt;  pt = rt c2 / kt
-    const double ptb = -ecoefb / Dn;
-    const double Dnb = ecoefb * pt / (Dn * Dn);
-    ktb += Dnb * 2.0 * (kt - 1.0) * rt * cvt;
-    rtb += Dnb * (kt - 1.0) * (kt - 1.0) * cvt;
-    cvtb += Dnb * (kt - 1.0) * (kt - 1.0) * rt;
-    rtb += ptb * c2 / kt;
-    c2b += ptb * rt / kt;
-    ktb -= ptb * rt * c2 / (kt * kt);
+    // ecoef = -Tbar / km1
+    Tbarb -= ecoefb / km1;
+    km1b += ecoefb * Tbar / (km1 * km1);
     // main waves: Dis[k] = sa Yt_k; Dis[m_i] = sa vt_i (+ sd for i = d); Dis[E] = sa Ht + sd vn
     for (int k = 0; k < NK; ++k) {
         sab += Db[k] * Yt[k];
@@ -528,16 +528,30 @@ DGFV_HD void riemann_roe_rev(const DevPhys& P, const double* uL, const Prim<NK>&
     bL.p -= dpb;
     vtb[d] += vnb;
     double rLb = rtb * rR, rRb = rtb * rL;
-    // ic2 = 1/c2;  ct = sqrt(c2);  c2 = (kt - 1)(Ht - q2/2)
+    // ic2 = 1/c2;  ct = sqrt(c2);  c2 = km1 (Ht - q2/2) + Tbar ypsi
     c2b -= ic2b * ic2 * ic2;
     c2b += ctb * 0.5 / ct;
-    ktb += c2b * (Ht - 0.5 * q2);
-    Htb += c2b * (kt - 1.0);
-    q2b -= c2b * 0.5 * (kt - 1.0);
-    // q2 = |vt|^2;  kt = cpt / cvt;  Ht = wl HL + wr HR;  H = E + p irho
+    km1b += c2b * (Ht - 0.5 * q2);
+    Htb += c2b * km1;
+    q2b -= c2b * 0.5 * km1;
+    Tbarb += c2b * ypsi;
+    // ypsi = sum_k Yt_k (cp_k - kt cv_k)
+    const double ypsib = c2b * Tbar;
+    for (int k = 0; k < NK; ++k) Ytb[k] += ypsib * (P.cp[k] - kt * P.cv[k]);
+    ktb -= ypsib * ycv;
+    // kt = km1 + 1;  km1 = Rb / cvb;  Rb, cvb = sum_k (uL_k + uR_k) (R_k, cv_k)
+    km1b += ktb;
+    const double Rbb = km1b / cvb, cvbb = -km1b * km1 / cvb;
+    for (int k = 0; k < NK; ++k) {
+        const double rsb = Rbb * (P.cp[k] - P.cv[k]) + cvbb * P.cv[k];
+        uLb[k] += rsb;
+        uRb[k] += rsb;
+    }
+    // Tbar = (TL + TR)/2
+    bL.T += 0.5 * Tbarb;
+    bR.T += 0.5 * Tbarb;
+    // q2 = |vt|^2;  Ht = wl HL + wr HR;  H = E + p irho
     for (int i = 0; i < 3; ++i) vtb[i] += q2b * 2.0 * vt[i];
-    cptb += ktb / cvt;
-    cvtb -= ktb * cpt / (cvt * cvt);
     double wlb = Htb * HL, wrb = Htb * HR;
     const double HLb = Htb * wl, HRb = Htb * wr;
     bL.E += HLb;
@@ -546,9 +560,8 @@ DGFV_HD void riemann_roe_rev(const DevPhys& P, const double* uL, const Prim<NK>&
     bR.E += HRb;
     bR.p += HRb * sR.irho;
     bR.irho += HRb * sR.p;
-    // cvt, cpt = sum Yt_k c_k;  Yt = wl YL + wr YR;  vt = wl vL + wr vR
+    // Yt = wl YL + wr YR;  vt = wl vL + wr vR
     for (int k = 0; k < NK; ++k) {
-        Ytb[k] += cvtb * P.cv[k] + cptb * P.cp[k];
         wlb += Ytb[k] * sL.Y[k];
         wrb += Ytb[k] * sR.Y[k];
         bL.Y[k] += Ytb[k] * wl;
