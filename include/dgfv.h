@@ -28,9 +28,16 @@
  *           default stream) enqueues its work on it and returns without
  *           synchronising, except where a host result is requested.
  * Errors    Every call returns dgfv_status.  Kernels never trap: a detected
- *           problem (non-finite state, a wait that timed out) sets a device
- *           status word that the next synchronising call (or
- *           dgfv_sync_status) reports.  dgfv_last_error gives the message.
+ *           problem sets a device status word (the first one wins) with the
+ *           element it was found in, which the next synchronising call (or
+ *           dgfv_sync_status) reports.  Every Runge-Kutta stage checks the
+ *           new state at every node: NaN or Inf gives DGFV_ERR_NONFINITE,
+ *           rho <= 0 or rho E - |rho v|^2/(2 rho) <= 0 (p <= 0)
+ *           DGFV_ERR_NONPHYSICAL.  The state is left as computed; set a
+ *           valid state to go on.  dgfv_last_error gives the message.
+ * Devices   A context belongs to the device that was current in
+ *           dgfv_init_mesh; every call that touches device memory returns
+ *           DGFV_ERR_ARG, before any CUDA work, when another device is current.
  * Threads   One context is used by one host thread and one stream at a time.
  */
 #ifndef DGFV_H
@@ -184,7 +191,9 @@ int dgfv_compute_dt(dgfv_ctx* ctx, const double* d_U, double* out3, void* stream
  * library.  Same result as dgfv_compute_dt, written to d_out3, a device array
  * of 3 doubles the caller owns ({dt, min dt_c, min dt_v}); nothing is copied
  * to the host and the stream is not synchronised.  The reduction's per-block
- * minima live in one fixed device array of 65536 block pairs (1 MiB) that
+ * maxima of the convective and viscous factors (turned into the minimum step
+ * by the final pass) live in one fixed device array of 65536 block pairs
+ * (1 MiB) that
  * every GPU loading the library holds until the process exits; contexts
  * whose time-step launch needs more blocks get DGFV_ERR_ARG.  The first call
  * on a device looks the array's device address up; make that first call
@@ -290,7 +299,8 @@ int dgfv_set_launch_mode(dgfv_ctx* ctx, int mode);
  * Synchronises. */
 int dgfv_autotune(dgfv_ctx* ctx, int* per_tile_out, void* stream);
 
-/* Device status word: DGFV_OK or the first error a kernel recorded; clears it. */
+/* Device status word: DGFV_OK or the first error a kernel recorded (the
+ * message names the element); clears it.  Synchronises. */
 int dgfv_sync_status(dgfv_ctx* ctx, void* stream);
 
 const char* dgfv_status_string(int status);

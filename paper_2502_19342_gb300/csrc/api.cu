@@ -640,15 +640,28 @@ int set_pattern(dgfv_ctx* c, const int8_t* N, const uint8_t* fv, bool remap, cud
     return DGFV_OK;
 }
 
+// Every device buffer of a context lives on the device that was current in
+// dgfv_init_mesh; a call made while another device is current would launch
+// there on foreign pointers, so it is refused before any CUDA work.
+int check_dev(dgfv_ctx* c) {
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) return fail(c, DGFV_ERR_CUDA, "cudaGetDevice failed");
+    if (d != c->dev)
+        return fail(c, DGFV_ERR_ARG, "the current device (" + std::to_string(d) + ") is not the context's device (" +
+                                         std::to_string(c->dev) + ")");
+    return DGFV_OK;
+}
+
 int read_status(dgfv_ctx* c, cudaStream_t s) {
-    int st = 0;
-    CK(cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int st[2] = {0, 0};
+    CK(cudaMemcpyAsync(st, c->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (st != 0) {
-        const int zero = 0;
-        CK(cudaMemcpyAsync(c->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+    if (st[0] != 0) {
+        const int zero[2] = {0, 0};
+        CK(cudaMemcpyAsync(c->d_status, zero, 2 * sizeof(int), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
-        return fail(c, st, std::string("device reported: ") + dgfv_status_string(st));
+        return fail(c, st[0], std::string("device reported: ") + dgfv_status_string(st[0]) + " (element " +
+                                  std::to_string(st[1]) + ")");
     }
     return DGFV_OK;
 }
@@ -873,7 +886,7 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     A_(c->d_flift, c->cap_fpts * c->V) A_(c->d_frec, c->cap_fpts * c->V)
     A_(c->d_rtmp, c->cap_state) A_(c->d_U, c->cap_state) A_(c->d_Us, c->cap_state)
     A_(c->d_dt3, 4) A_(c->d_partial, 2 * ne + 2) A_(c->d_Ip, ne) A_(c->d_Ih, ne) A_(c->d_dec, ne)
-    A_(c->d_status, 1) A_(c->d_pp_count, 2) A_(c->lift.d, c->n_faces) A_(c->flux.d, c->n_faces)
+    A_(c->d_status, 2) A_(c->d_pp_count, 2) A_(c->lift.d, c->n_faces) A_(c->flux.d, c->n_faces)
     A_(c->conf.d_first, c->n_faces) A_(c->conf.d_count, c->n_faces) A_(c->conf.d_nc, c->n_faces)
     A_(c->conf.d_d, c->n_faces) A_(c->conf.d_items, c->n_faces)
     A_(c->mixed.tiles.d_first, c->n_faces) A_(c->mixed.tiles.d_count, c->n_faces)
@@ -883,7 +896,7 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     if ((r = alloc_tiles(c, c->all)) != DGFV_OK) return cleanup(r);
     if ((r = alloc_tiles(c, c->dg)) != DGFV_OK) return cleanup(r);
     if ((r = alloc_tiles(c, c->fvt)) != DGFV_OK) return cleanup(r);
-    if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) return cleanup(DGFV_ERR_CUDA);
+    if (cudaMemset(c->d_status, 0, 2 * sizeof(int)) != cudaSuccess) return cleanup(DGFV_ERR_CUDA);
     if (cudaMemset(c->d_pp_count, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) return cleanup(DGFV_ERR_CUDA);
     if (cudaMemcpy(c->d_nb, c->nb.data(), c->nb.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->d_rh, c->rh.data(), c->rh.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -923,6 +936,7 @@ int64_t dgfv_num_elements(const dgfv_ctx* c) { return c ? c->n_elem : -1; }
 
 int dgfv_set_degrees(dgfv_ctx* c, const int8_t* N, const uint8_t* is_fv, int remap_state) {
     if (!c || !N) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     return set_pattern(c, N, is_fv, remap_state != 0, nullptr);
 }
 
@@ -945,6 +959,7 @@ int dgfv_state_layout(dgfv_ctx* c, int64_t* n_doubles, const int64_t** d_elem_of
 static int copy_state(dgfv_ctx* c, void* dst, const void* src, int64_t n, cudaMemcpyKind kind, void* stream,
                       bool sync) {
     if (!c || (!dst && n > 0) || (!src && n > 0)) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     if (n != c->n_state) return fail(c, DGFV_ERR_ARG, "state size does not match the layout");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(dst, src, n * sizeof(double), kind, s));
@@ -976,6 +991,7 @@ int dgfv_get_state_host(dgfv_ctx* c, double* h_U, int64_t n, void* stream) {
 
 int dgfv_eval_rhs(dgfv_ctx* c, const double* d_U, double* d_R, void* stream) {
     if (!c || !d_U || !d_R) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     if (d_U == d_R) return fail(c, DGFV_ERR_ARG, "d_U and d_R alias");
     cudaStream_t s = (cudaStream_t)stream;
     enqueue_stage(c, d_U, d_U, d_R, 0, 0.0, 0.0, s);
@@ -985,6 +1001,7 @@ int dgfv_eval_rhs(dgfv_ctx* c, const double* d_U, double* d_R, void* stream) {
 
 int dgfv_compute_dt(dgfv_ctx* c, const double* d_U, double* out3, void* stream) {
     if (!c || !d_U || !out3) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     cudaStream_t s = (cudaStream_t)stream;
     launch_dt(c->nk, params(c), c->all.view(), c->all.ntiles, d_U, c->opts.cfl_c, c->opts.cfl_v, c->d_partial,
               c->d_dt3, s);
@@ -996,6 +1013,7 @@ int dgfv_compute_dt(dgfv_ctx* c, const double* d_U, double* out3, void* stream) 
 
 int dgfv_compute_dt_noalloc(dgfv_ctx* c, const double* d_U, double* d_out3, void* stream) {
     if (!c || !d_U || !d_out3) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     const int r = launch_dt_noalloc(c->nk, params(c), c->all.view(), c->all.ntiles, d_U, c->opts.cfl_c,
                                     c->opts.cfl_v, d_out3, (cudaStream_t)stream);
     if (r == 1)
@@ -1070,6 +1088,7 @@ static void enqueue_vjp(dgfv_ctx* c, const double* U, const double* Rb, double* 
 
 int dgfv_rhs_vjp(dgfv_ctx* c, const double* d_U, const double* d_Rbar, double* d_Ubar, void* stream) {
     if (!c || !d_U || !d_Rbar || !d_Ubar) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     if (d_Ubar == d_U || d_Ubar == d_Rbar) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
     TRY(adj_prepare(c));
     enqueue_vjp(c, d_U, d_Rbar, d_Ubar, (cudaStream_t)stream);
@@ -1127,6 +1146,7 @@ static int lsrk4_step_vjp(dgfv_ctx* c, const double* d_U0, double dt, const doub
 int dgfv_rk_step_vjp(dgfv_ctx* c, const double* d_U0, double dt, const double* d_Ubar_next, double* d_Ubar,
                      void* stream) {
     if (!c || !d_U0 || !d_Ubar_next || !d_Ubar || !(dt > 0.0)) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     if (d_Ubar == d_Ubar_next || d_Ubar == d_U0) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
     if (c->opts.pp_limiter) return fail(c, DGFV_ERR_ARG, "step adjoints do not support the positivity limiter");
     TRY(adj_prepare(c));
@@ -1142,6 +1162,7 @@ int dgfv_rk_step_vjp(dgfv_ctx* c, const double* d_U0, double dt, const double* d
 int dgfv_rk_step_vjp_stages(dgfv_ctx* c, const double* const* d_stages, double dt, const double* d_Ubar_next,
                             double* d_Ubar, void* stream) {
     if (!c || !d_stages || !d_stages[0] || !d_stages[1] || !d_stages[2] || !d_Ubar_next || !d_Ubar || !(dt > 0.0))
+    TRY(check_dev(c));
         return DGFV_ERR_ARG;
     for (int i = 0; i < 3; ++i)
         if (d_Ubar == d_stages[i]) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
@@ -1154,6 +1175,7 @@ int dgfv_rk_step_vjp_stages(dgfv_ctx* c, const double* const* d_stages, double d
 
 int dgfv_rk_step_save(dgfv_ctx* c, double dt, double* d_stage1, double* d_stage2, void* stream) {
     if (!c || !d_stage1 || !d_stage2 || !(dt > 0.0)) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "rk_step_save before set_state");
     if (c->opts.integrator != DGFV_INTEGRATOR_SSPRK3 || c->opts.pp_limiter)
         return fail(c, DGFV_ERR_ARG, "stage adjoints and stage saving support SSP-RK3 without the limiter only");
@@ -1168,6 +1190,7 @@ int dgfv_rk_step_save(dgfv_ctx* c, double dt, double* d_stage1, double* d_stage2
 
 int dgfv_rk_step(dgfv_ctx* c, double dt, double* dt_used, void* stream) {
     if (!c) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "rk_step before set_state");
     cudaStream_t s = (cudaStream_t)stream;
     enqueue_rk_step(c, dt, s);
@@ -1182,6 +1205,7 @@ int dgfv_rk_step(dgfv_ctx* c, double dt, double* dt_used, void* stream) {
 
 int dgfv_rk_steps(dgfv_ctx* c, int n_steps, double dt, double* dt_used, void* stream) {
     if (!c || n_steps < 0) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "rk_steps before set_state");
     cudaStream_t s = (cudaStream_t)stream;
     if (c->prof.on) {
@@ -1219,6 +1243,7 @@ int dgfv_rk_steps(dgfv_ctx* c, int n_steps, double dt, double* dt_used, void* st
 
 int dgfv_indicator(dgfv_ctx* c, const double* d_U, double* d_Ip, double* d_Ih, uint8_t* d_decision, void* stream) {
     if (!c || !d_U) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     const double thr[4] = {c->opts.T_fv_on, c->opts.T_fv_off, c->opts.T_ref, c->opts.T_crs};
     Timed t(c, K_INDICATOR, (cudaStream_t)stream);
     launch_indicator(c->nk, params(c), d_U, c->n_elem, d_Ip, d_Ih, d_decision, thr, c->N_min, c->N_max,
@@ -1230,6 +1255,7 @@ int dgfv_indicator(dgfv_ctx* c, const double* d_U, double* d_Ip, double* d_Ih, u
 
 int dgfv_adapt(dgfv_ctx* c, dgfv_adapt_stats* stats, void* stream) {
     if (!c) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "adapt before set_state");
     cudaStream_t s = (cudaStream_t)stream;
     TRY(dgfv_indicator(c, c->d_U, c->d_Ip, c->d_Ih, c->d_dec, stream));
@@ -1310,6 +1336,7 @@ int dgfv_set_launch_mode(dgfv_ctx* c, int mode) {
 
 int dgfv_autotune(dgfv_ctx* c, int* per_tile_out, void* stream) {
     if (!c) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "autotune before set_state");
     cudaStream_t s = (cudaStream_t)stream;
     const Params P0 = params(c);
@@ -1390,6 +1417,7 @@ int dgfv_autotune(dgfv_ctx* c, int* per_tile_out, void* stream) {
 
 int dgfv_sync_status(dgfv_ctx* c, void* stream) {
     if (!c) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     return read_status(c, (cudaStream_t)stream);
 }
 
@@ -1437,6 +1465,7 @@ int64_t dgfv_bank_entry(dgfv_ctx* c, int which, int N, int M, double* out, int64
 
 int dgfv_pp_limit(dgfv_ctx* c, double* d_U, int64_t* changed, void* stream) {
     if (!c || !d_U) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     cudaStream_t s = (cudaStream_t)stream;
     const double eps = c->opts.pp_eps > 0.0 ? c->opts.pp_eps : 1e-10;
     unsigned long long* cnt = c->d_pp_count + 1;  // scratch counter of this call
@@ -1454,6 +1483,7 @@ int dgfv_pp_limit(dgfv_ctx* c, double* d_U, int64_t* changed, void* stream) {
 
 int dgfv_pp_count(dgfv_ctx* c, int64_t* count, int reset, void* stream) {
     if (!c || !count) return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     cudaStream_t s = (cudaStream_t)stream;
     unsigned long long h = 0;
     CK(cudaMemcpyAsync(&h, c->d_pp_count, sizeof(h), cudaMemcpyDeviceToHost, s));

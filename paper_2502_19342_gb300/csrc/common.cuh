@@ -133,8 +133,10 @@ __device__ __forceinline__ bool nonfinite_bits(double x) {
     return ((__double2hiint(x) >> 20) & 0x7ff) == 0x7ff;
 }
 
-__device__ __forceinline__ void set_status(int* status, int code) {
-    if (status) atomicCAS(status, 0, code);
+// Device status word: status[0] the first error code (first error wins),
+// status[1] the element it was detected in.
+__device__ __forceinline__ void set_status(int* status, int code, int elem) {
+    if (status && atomicCAS(status, 0, code) == 0) atomicExch(status + 1, elem);
 }
 
 }  // namespace dgfv

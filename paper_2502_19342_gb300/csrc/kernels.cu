@@ -570,6 +570,8 @@ __device__ __forceinline__ void surface_body(const Params& P, const Tiles& T, co
             Fm[d] = P.b.flux + (fo + (int64_t)(2 * d) * n2) * V + pt[d];
             Fp[d] = P.b.flux + (fo + (int64_t)(2 * d + 1) * n2) * V + pt[d];
         }
+        // new state of the node, for the positivity check: rho and 2 rho (rho e)
+        double nrho = 0.0, nm2 = 0.0, nE = 0.0;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             double acc = P.b.rtmp[off + (int64_t)v * n3];
@@ -590,11 +592,17 @@ __device__ __forceinline__ void surface_body(const Params& P, const Tiles& T, co
                     dU[off + (int64_t)v * n3] = y;
                     x = fma(b, y, Uin[off + (int64_t)v * n3]);
                 }
-                if (nonfinite_bits(x)) set_status(P.status, -5);
+                if (nonfinite_bits(x)) set_status(P.status, -5, e);
+                if (v < NK) nrho += x;
+                else if (v < NK + 3) nm2 = fma(x, x, nm2);
+                else nE = x;
                 out[off + (int64_t)v * n3] = x;
                 if (fuse) sU[el * V * n3 + v * n3 + c] = x;
             }
         }
+        // rho <= 0 or rho e = rho E - |rho v|^2/(2 rho) <= 0 (p <= 0, as kappa > 1);
+        // false for NaN, which the non-finite check reports
+        if (mode != 0 && (nrho <= 0.0 || fma(2.0 * nrho, nE, -nm2) <= 0.0)) set_status(P.status, -4, e);
     }
     if (fuse) {
         __syncthreads();

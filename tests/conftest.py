@@ -18,3 +18,18 @@ def oracle():
     import oracle as O
     O.lib()
     return O
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """Write the GPU parity margins (achieved per-field errors and bounds of
+    every comparison) to the JSON file DGFV_PARITY_MARGINS names, if any."""
+    out = os.environ.get("DGFV_PARITY_MARGINS")
+    if not out:
+        return
+    try:
+        from tests import gpu_helpers
+    except ImportError:
+        return
+    import json
+    with open(out, "w") as f:
+        json.dump(gpu_helpers.MARGINS, f, indent=1)

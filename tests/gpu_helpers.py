@@ -1,5 +1,9 @@
 """Helpers shared by the GPU parity tests: run the CUDA path through its C ABI
-and compare with the oracle field by field."""
+and compare with the oracle field by field.  Every comparison is also
+recorded (test, what, achieved per-field errors, bound) in MARGINS, which the
+session writes out as JSON when DGFV_PARITY_MARGINS names a file."""
+import os
+
 import numpy as np
 
 from paper_2502_19342_gb300 import workloads as W
@@ -30,6 +34,16 @@ def per_field(prob, x):
 FLOOR = 1e-2
 
 
+MARGINS = []
+
+
+def record(what, errs, bound):
+    """Keep one comparison's achieved errors and bound for the margin report."""
+    test = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+    errs = [float(e) for e in np.atleast_1d(errs)]
+    MARGINS.append(dict(test=test, what=what, max_err=max(errs), errs=errs, bound=float(bound)))
+
+
 def field_errors(prob, got, ref):
     """max |got - ref| / scale for every conserved field (see FLOOR)."""
     g, r = per_field(prob, got), per_field(prob, ref)
@@ -39,6 +53,7 @@ def field_errors(prob, got, ref):
 
 def assert_fields_close(prob, got, ref, rtol=RTOL, what="R"):
     errs = field_errors(prob, got, ref)
+    record(what, errs, rtol)
     assert np.isfinite(ref).all(), f"{what}: the reference is not finite"
     assert all(e <= rtol for e in errs), f"{what}: per-field relative errors {errs}"  # NaN fails too
     return errs
@@ -58,6 +73,7 @@ def assert_rhs_close(oracle, prob, U, got, factor=3.0):
     own = field_errors(prob, oracle.eval_rhs(prob, U), ref)
     errs = field_errors(prob, got, ref)
     bound = [max(RTOL, factor * max(own))] * len(own)
+    record("R", errs, bound[0])
     assert all(e <= b for e, b in zip(errs, bound)), f"R: per-field errors {errs}, bounds {bound}"
     return errs, own
 
@@ -72,6 +88,7 @@ def assert_adjoint_close(oracle, prob, U, Rbar, got, factor=3.0):
     own = field_errors(prob, oracle.adjoint_columns(prob, U, Rbar), ref)
     errs = field_errors(prob, got, ref)
     bound = max(RTOL, factor * max(own))
+    record("U_bar", errs, bound)
     assert all(e <= bound for e in errs), f"U_bar: per-field errors {errs}, bound {bound} (oracle's own {own})"
     return errs, own
 

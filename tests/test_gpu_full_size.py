@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 from paper_2502_19342_gb300 import workloads as W
-from tests.gpu_helpers import RTOL, field_errors, to_dev
+from tests.gpu_helpers import RTOL, field_errors, record, to_dev
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
@@ -49,6 +49,7 @@ def _rhs_parity(oracle, prob, U, ctx):
     assert np.isfinite(Ro).all()
     errs = field_errors(prob, R, Ro)
     bound = _bound(oracle, prob)
+    record("R full size", errs, bound)
     assert all(e <= bound for e in errs), f"R: per-field errors {errs}, bound {bound}"
     return errs
 
@@ -107,6 +108,7 @@ def test_batched_domains_full(oracle):
         ext = oracle.eval_rhs_extended(sub, Us)
         e = max(field_errors(sub, oracle.eval_rhs(sub, Us), ext))
         got = field_errors(sub, R[sl], ext)
+        record(f"R domain {i}", got, max(RTOL, 3 * e))
         assert max(got) <= max(RTOL, 3 * e), (i, got, e)
         own.append(e)
         picked.append(int(sub["N"][0]))
@@ -116,6 +118,7 @@ def test_batched_domains_full(oracle):
     Ro = oracle.eval_rhs(prob, U)
     errs = field_errors(prob, R, Ro)
     bound = max(2 * RTOL, 4 * max(own))
+    record("R whole batch", errs, bound)
     assert all(e <= bound for e in errs), f"R: per-field errors {errs}, bound {bound}"
 
 
@@ -153,6 +156,7 @@ def test_mortar_half_refined_cube_full(oracle):
     e = max(field_errors(s, oracle.eval_rhs(s, Us), oracle.eval_rhs_extended(s, Us)))
     bound = max(2 * RTOL, 4 * e * 24 / 8)
     errs = field_errors(prob, R, Ro)
+    record("R full size", errs, bound)
     assert all(x <= bound for x in errs), f"R: per-field errors {errs}, bound {bound}"
     dt = ctx.compute_dt(to_dev(U))
     dto = oracle.dt(prob, U, 0.5, 0.5)

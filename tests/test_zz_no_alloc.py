@@ -47,4 +47,39 @@ def test_noalloc_time_step_matches_regular_entry_point_twice_in_a_row():
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         np.testing.assert_allclose(got, np.array(ref), rtol=RTOL)
+    # a warm call takes no device memory: the free bytes the driver reports
+    # are the same before and after it
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    rc = L.dgfv_compute_dt_noalloc(ctx.h, ctypes.c_void_p(Ud.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert rc == 0
+    assert torch.cuda.mem_get_info()[0] == free0
+    ctx.close()
+
+
+def test_noalloc_time_step_refuses_more_work_tiles_than_its_scratch():
+    """The fixed scratch holds the partial results of 65536 blocks (one per
+    work tile).  At N = 7 every element is a tile of its own, so 41 x 40 x 40
+    = 65600 elements need more: the call returns DGFV_ERR_ARG with a message
+    and launches nothing; the regular entry point still works."""
+    from paper_2502_19342_gb300 import dgfv
+    L = dgfv.lib()
+    sp = W.species_set([W.AIR], mu=1e-3)
+    prob = W.make_problem([((41, 40, 40), (0, 0, 0), (1.0, 1.0, 1.0))], sp, n_fv=8, N=7)
+    ctx = dgfv.Context(prob, N_min=7, N_max=7)
+    U = torch.zeros(ctx.state_size, dtype=torch.float64, device="cuda")
+    U.view(-1, 5, 512)[:, 0] = 1.0           # rho
+    U.view(-1, 5, 512)[:, 4] = 2.5           # rho E: p = 1 at rest
+    out = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+    rc = L.dgfv_compute_dt_noalloc(ctx.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == -1  # DGFV_ERR_ARG
+    msg = L.dgfv_last_error(ctx.h).decode()
+    assert "65600" in msg and "65536" in msg, msg
+    torch.cuda.synchronize()
+    assert (out.cpu().numpy() == -1.0).all()
+    dt = ctx.compute_dt(U)
+    assert np.isfinite(dt[0]) and dt[0] > 0
     ctx.close()
