@@ -34,17 +34,41 @@ sys.path.insert(0, ROOT)
 
 STEPS_PER_CYCLE = 10
 STAGES_PER_STEP = 3
-# FP64 peak from the unit count and clock of a GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
-SMS, DFMA_PER_CLK, SM_MHZ_MAX = 152, 2, 2070.0
+# FP64 FMA lanes per SM and clock of a GB300 (1.25 TFLOP/s nominal over 152 SMs
+# at 2.07 GHz); the SM count and the maximum SM clock are read from the device.
+DFMA_PER_CLK = 2
 # DRAM bytes per DG DOF of one k_dg_volume launch, from an ncu capture of the
 # turbulence workload at 28^3 elements (dram__bytes_read.sum + write.sum =
 # 0.373 + 0.703 GB for 3.13e6 DG DOFs).
 VOLUME_DRAM_BYTES_PER_DG_DOF = 344.0
-FP64_PEAK_TFLOPS = SMS * DFMA_PER_CLK * 2 * SM_MHZ_MAX * 1e6 / 1e12
 # measured copy bandwidth of this GPU type (written beside the repository when
 # it is present); used only to show how far the FP64-bound kernel is from HBM.
 HBM_FALLBACK_GBS = 6800.0
 KERNEL_STEP = {"prolong": 1, "fv": 2, "face_lift": 3, "dg_volume": 4, "face_flux": 5, "surface": 6}
+
+
+def r4(x):
+    """Four significant digits (keeps the one-line record short)."""
+    if x is None:
+        return None
+    return float(f"{x:.4g}")
+
+
+def fp64_peak(device=0):
+    """FP64 peak of this GPU from its SM count and maximum SM clock:
+    SMs x DFMA_PER_CLK FMA lanes x 2 flop x clock.  Returns (TFLOP/s, source)."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz, src = 2070.0, "2070 MHz (nominal maximum)"
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(device), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        mhz = float(out.stdout.strip().splitlines()[0])
+        src = f"{mhz:.0f} MHz (nvidia-smi clocks.max.sm)"
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        pass
+    tf = sms * DFMA_PER_CLK * 2 * mhz * 1e6 / 1e12
+    return tf, f"{sms} SMs (device properties) x {DFMA_PER_CLK} DFMA/clk x 2 flop x {src}"
 
 
 def measured_hbm_gbs():
@@ -289,14 +313,11 @@ def adjoint_cost(steps=50):
     same = bool(torch.equal(grad_recomputed, a))
     dofs = W.n_dofs(prob)
     ctx.close()
-    return {"workload": "temporal mixing layer, 16^3 elements, N=4, 3 species, viscous, LLF, pattern and dt frozen; "
-                        "gradient of kinetic energy + species variance of the final state",
-            "steps": steps, "dofs": dofs, "stage_state_gb": round(3 * steps * Ud.numel() * 8 / 1e9, 2),
-            "forward_ms_per_step": fwd / steps, "forward_keeping_stages_ms_per_step": fsave / steps,
-            "adjoint_ms_per_step_stored_stages": bwd2 / steps, "adjoint_over_forward": bwd2 / fwd,
-            "adjoint_ms_per_step_recomputed_stages": bwd / steps, "adjoint_over_forward_recomputed": bwd / fwd,
-            "gradients_identical": same,
-            "note": "adjoint step = 3 vector-Jacobian products (+2 forward stages when the stages are recomputed)"}
+    return {"steps": steps, "dofs": dofs, "stage_gb": r4(3 * steps * Ud.numel() * 8 / 1e9),
+            "fwd_ms_step": r4(fwd / steps), "fwd_keep_ms_step": r4(fsave / steps),
+            "adj_ms_step_stored": r4(bwd2 / steps), "adj_over_fwd_stored": r4(bwd2 / fwd),
+            "adj_ms_step_recomputed": r4(bwd / steps), "adj_over_fwd_recomputed": r4(bwd / fwd),
+            "gradients_identical": same}
 
 
 def adjoint_hybrid_cost(steps=10):
@@ -356,19 +377,35 @@ def adjoint_hybrid_cost(steps=10):
     # the FV element reverse sums with atomics, so the two gradients agree to rounding, not bit for bit
     rel = float((grad_stored - a).abs().max() / a.abs().max())
     ctx.close()
-    return {"workload": "hp-mixed shock case after 2 adaptation cycles, pattern and dt frozen (hybrid DG/FV)",
-            "steps": steps, "fv_elements": int(fv_now.sum()), "elements": int(len(N_now)),
-            "forward_ms_per_step": fwd / steps, "forward_keeping_stages_ms_per_step": fsave / steps,
-            "adjoint_ms_per_step_stored_stages": bst / steps, "adjoint_over_forward": bst / fwd,
-            "adjoint_ms_per_step_recomputed_stages": brc / steps, "adjoint_over_forward_recomputed": brc / fwd,
-            "gradients_max_rel_diff": rel}
+    return {"steps": steps, "fv_elements": int(fv_now.sum()), "elements": int(len(N_now)),
+            "fwd_ms_step": r4(fwd / steps), "fwd_keep_ms_step": r4(fsave / steps),
+            "adj_ms_step_stored": r4(bst / steps), "adj_over_fwd_stored": r4(bst / fwd),
+            "adj_ms_step_recomputed": r4(brc / steps), "adj_over_fwd_recomputed": r4(brc / fwd),
+            "grad_max_rel_diff": r4(rel)}
 
 
-def split_form_run(nel, warmup=2, steps=1):
+def kernel_table(prof, per_step, dofs_per_launch, peak):
+    """Per kernel group: [total ms, launches, algorithmic TFLOP/s, fraction of
+    the FP64 peak] from the profiled pass; the algorithmic flops of a launch
+    are the oracle's count of that step per DOF times the DOFs of one stage."""
+    out = {}
+    for k, (ms, nl) in prof.items():
+        if nl <= 0:
+            continue
+        row = [r4(ms), int(nl), None, None]
+        if k in KERNEL_STEP and per_step.get(KERNEL_STEP[k], 0.0) > 0:
+            tf = per_step[KERNEL_STEP[k]] * dofs_per_launch / (ms / nl * 1e-3) / 1e12
+            row[2:] = [r4(tf), r4(tf / peak)]
+        out[k] = row
+    return out
+
+
+def split_form_run(nel, peak, warmup=2, steps=1):
     """The turbulence workload with the jet's scheme (Sec. 5.1): split-form DGSEM
     on LGL nodes with the kinetic-energy-preserving flux, Roe-HH between DG
     elements and LLF where FV data meet; adaptation cycles as in the main
-    measurement.  DOF-stage/s and the roofline of the split volume kernel."""
+    measurement.  DOF-stage/s (CUDA graph replay), then a profiled pass over
+    the same cycles for the roofline of the split volume kernel."""
     import torch
     from paper_2502_19342_gb300 import dgfv, workloads as W
     prob, U = W.turbulence(seed=0, nel=(nel, nel, nel), N0=4, nodes=1, split=1, riemann=2)
@@ -376,11 +413,12 @@ def split_form_run(nel, warmup=2, steps=1):
     ctx.set_state(torch.from_numpy(U).cuda())
     for _ in range(warmup):
         cycle(ctx)
-    tuned = ctx.autotune()  # tile sizes of the split volume kernel, as in the main measurement
+    ctx.autotune()  # tile sizes of the split volume kernel, as in the main measurement
     cycle(ctx)
+    N0, fv0 = ctx.get_degrees()
+    U0 = ctx.get_state()
     s = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ctx.profile_enable(True)
     torch.cuda.synchronize()
     units = 0.0
     ev0.record(s)
@@ -389,6 +427,12 @@ def split_form_run(nel, warmup=2, steps=1):
     ev1.record(s)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
+    ctx.set_degrees(N0, fv0, remap=False)
+    ctx.set_state(U0)
+    ctx.profile_enable(True)
+    for _ in range(steps):
+        cycle(ctx)
+    torch.cuda.synchronize()
     prof = ctx.profile_read()
     ctx.profile_enable(False)
     N_now, fv_now = ctx.get_degrees()
@@ -397,35 +441,31 @@ def split_form_run(nel, warmup=2, steps=1):
     dofs_per_launch = units / (steps * STEPS_PER_CYCLE * STAGES_PER_STEP)
     achieved = per_step[4] * dofs_per_launch / (kms / kl * 1e-3) / 1e12
     ctx.close()
-    return {"workload": f"turbulent multi-component decay, {nel}^3 elements, split-form DGSEM on LGL nodes "
-                        "(kinetic-energy-preserving two-point flux), Roe-HH between DG elements, LLF where FV "
-                        "data meet, N in 1..7 by the indicator, N_FV=8, 3 species, viscous",
-            "value": units / (ms * 1e-3), "unit": "DOF-stage/s", "ms_per_step": ms / steps,
-            "fv_elements": int(fv_now.sum()),
-            "degree_histogram": np.bincount(N_now[fv_now == 0], minlength=8).tolist(),
-            "volume_tiles": {str(k): v for k, v in tuned.items()},
-            "volume_kernel": {"kernel": "k_dg_volume_split", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                              "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                              "flops_per_dof": per_step[4], "share_of_step": kms / sum(v[0] for v in prof.values())},
-            "flops_per_dof_total": per_dof,
-            "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()}}
+    value = units / (ms * 1e-3)
+    return {"value": r4(value), "ms_per_step": r4(ms / steps), "fv_elements": int(fv_now.sum()),
+            "k_dg_volume_split": {"tflops": r4(achieved), "frac": r4(achieved / peak),
+                                  "flops_per_dof": r4(per_step[4]),
+                                  "share": r4(kms / sum(v[0] for v in prof.values()))},
+            "whole_rhs_frac": r4(per_dof * value / 1e12 / peak)}
 
 
-def tgv_run(nel=32, warmup=2, steps=2):
+def tgv_run(nel=32, warmup=30, steps=2):
     """Supersonic Taylor-Green vortex (Sec. 4.3) as a throughput workload: 32^3
     elements, N in 2..4 by the pressure indicator, FV by the density indicator,
     Sutherland viscosity, five-stage low-storage RK4; one step = adaptation +
-    10 RK4 steps (50 stages).  DOF-stage/s (CUDA events)."""
+    10 RK4 steps (50 stages).  `warmup` cycles first carry the flow past its
+    smooth start (shocklets and FV sub-cells appear); DOF-stage/s (CUDA events)."""
     import torch
     from paper_2502_19342_gb300 import dgfv, workloads as W
     prob, U = W.tgv(nel=nel, N0=3)
     ctx = dgfv.Context(prob, N_min=2, N_max=4,
                        opts=dict(cfl_c=0.5, cfl_v=0.5, thresholds=W.TGV_THRESHOLDS, integrator=1))
     ctx.set_state(torch.from_numpy(U).cuda())
+    t = [0.0]
 
     def tgv_cycle():
         st = ctx.adapt()
-        ctx.rk_steps(STEPS_PER_CYCLE, -1.0, want_dt=False)
+        t[0] += STEPS_PER_CYCLE * ctx.rk_steps(STEPS_PER_CYCLE, -1.0, want_dt=True)
         return st["mean_dofs"] * ctx.n_elem * STEPS_PER_CYCLE * 5, st
 
     for _ in range(warmup):
@@ -443,62 +483,51 @@ def tgv_run(nel=32, warmup=2, steps=2):
     ms = ev0.elapsed_time(ev1)
     N_now, fv_now = ctx.get_degrees()
     ctx.close()
-    return {"workload": f"supersonic Taylor-Green vortex, Ma 1.25, Re 1600, {nel}^3 elements on [-pi,pi]^3, "
-                        f"N in 2..4 (pressure indicator), FV sub-cells N_FV={int(prob['n_fv'])} (density indicator), "
-                        "Sutherland "
-                        "viscosity, low-storage RK4, LLF, early time",
-            "value": units / (ms * 1e-3), "unit": "DOF-stage/s", "ms_per_step": ms / steps,
-            "step": "adapt + 10 low-storage RK4 steps (50 stages), CFL 0.5",
-            "fv_elements": int(fv_now.sum()), "mean_dofs_per_element": st["mean_dofs"],
-            "degree_histogram": np.bincount(N_now[fv_now == 0], minlength=5).tolist()}
+    return {"value": r4(units / (ms * 1e-3)), "ms_per_step": r4(ms / steps), "t_end": r4(t[0]),
+            "fv_elements": int(fv_now.sum()), "mean_dofs_per_element": r4(st["mean_dofs"]),
+            "degree_histogram": np.bincount(N_now[fv_now == 0], minlength=5).tolist()[2:]}
 
 
-def hp_shock_run(warmup=2, cycles=4):
-    """The hp-mixed shock case: 16^3 elements on [0,2]x[0,1]^2, N in 2..6 with FV
-    sub-cells (N_FV = 7) chosen by the indicator every 5 SSP-RK3 steps, a Mach
-    1.5 shock into a heavy-gas bubble, 2 species.  DOF-stage/s over `cycles`
-    cycles of (adaptation + 5 steps), CUDA events."""
+def hp_shock_run(peak, cycles=40):
+    """The hp-mixed shock case at its full length: 16^3 elements on
+    [0,2]x[0,1]^2, N in 2..6 with FV sub-cells (N_FV = 7) chosen by the
+    indicator every 5 SSP-RK3 steps, a Mach 1.5 shock into a heavy-gas bubble,
+    2 species; `cycles` x (adaptation + 5 steps) = 200 steps.  CUDA events
+    around each adaptation (indicator, readback, host tables, remap) and
+    around each block of 5 steps (graph replay, recaptured after a pattern
+    change); the RHS rate and its roofline fraction over the steps alone."""
     import torch
     from paper_2502_19342_gb300 import dgfv, workloads as W
     prob, U = W.hp_shock(0, y_bg=0.01)
     ctx = dgfv.Context(prob, N_min=2, N_max=6, opts=dict(cfl_c=0.5, cfl_v=0.5, thresholds=W.THRESHOLDS))
     ctx.set_state(torch.from_numpy(U).cuda())
-
-    def shock_cycle():
-        st = ctx.adapt()
-        ctx.rk_steps(5, -1.0, want_dt=False)
-        return st["mean_dofs"] * ctx.n_elem * 5 * STAGES_PER_STEP, st
-
-    for _ in range(warmup):
-        shock_cycle()
     s = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * cycles + 1)]
+    units, fvs = 0.0, []
     torch.cuda.synchronize()
-    units, st = 0.0, None
-    ev0.record(s)
-    for _ in range(cycles):
-        u, st = shock_cycle()
-        units += u
-    ev1.record(s)
+    ev[0].record(s)
+    for c in range(cycles):
+        st = ctx.adapt()
+        ev[2 * c + 1].record(s)
+        ctx.rk_steps(5, -1.0, want_dt=False)
+        ev[2 * c + 2].record(s)
+        units += st["mean_dofs"] * ctx.n_elem * 5 * STAGES_PER_STEP
+        fvs.append(st["n_fv"])
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
+    adapt_ms = sum(ev[2 * c].elapsed_time(ev[2 * c + 1]) for c in range(cycles))
+    rk_ms = sum(ev[2 * c + 1].elapsed_time(ev[2 * c + 2]) for c in range(cycles))
     N_now, fv_now = ctx.get_degrees()
     ctx.close()
-    value = units / (ms * 1e-3)
     per_dof, _ = flops_per_dof(dict(prob, N=N_now, fv=fv_now))
-    return {"workload": "hp-mixed shock case: 16^3 elements on [0,2]x[0,1]^2, Mach 1.5 shock into a heavy-gas "
-                        "bubble (density ratio 3.5), 1 % heavy-gas background, 2 species, N in 2..6 and FV sub-cells "
-                        "(N_FV = 7) by the "
-                        "indicator every 5 SSP-RK3 steps",
-            "value": value, "unit": "DOF-stage/s", "ms_per_cycle": ms / cycles,
-            "cycle": "adapt + 5 SSP-RK3 steps (15 stages), CFL 0.5",
-            "whole_rhs_tflops": per_dof * value / 1e12, "whole_rhs_frac_of_fp64_peak": per_dof * value / 1e12 / FP64_PEAK_TFLOPS,
-            "flops_per_dof": per_dof,
-            "fv_elements": int(fv_now.sum()), "mean_dofs_per_element": st["mean_dofs"],
-            "degree_histogram": np.bincount(N_now[fv_now == 0], minlength=7).tolist()}
+    rate = units / (rk_ms * 1e-3)
+    return {"steps": 5 * cycles, "value": r4(units / ((adapt_ms + rk_ms) * 1e-3)), "rk_value": r4(rate),
+            "adapt_ms_per_cycle": r4(adapt_ms / cycles), "rk_ms_per_cycle": r4(rk_ms / cycles),
+            "whole_rhs_tflops": r4(per_dof * rate / 1e12), "whole_rhs_frac": r4(per_dof * rate / 1e12 / peak),
+            "flops_per_dof": r4(per_dof), "fv_elements_first_last": [fvs[0], fvs[-1]],
+            "subcell_dof_share": r4(float(fv_now.astype(np.int64).sum() * 343) / float(W.n_dofs(dict(prob, N=N_now, fv=fv_now))))}
 
 
-def mortar_run(k=24, warmup=1, steps=3):
+def mortar_run(peak, k=24, warmup=1, steps=3):
     """Non-conforming mesh (Sec. 3.2.3) at scale: the half-refined unit cube of
     Sec. 4.1 / 4.2 with (k, 2k, 2k) + (k/2, k, k) elements and type-3 mortars on
     both x interfaces, random degrees N in 2..5 and 5 % FV elements (N_FV = 8),
@@ -524,74 +553,89 @@ def mortar_run(k=24, warmup=1, steps=3):
     ms = ev0.elapsed_time(ev1)
     ctx.sync_status()
     ctx.close()
-    ne = W.n_elements(prob)
     value = dofs * steps * STEPS_PER_CYCLE * STAGES_PER_STEP / (ms * 1e-3)
     per_dof, _ = flops_per_dof(prob)  # the degree/FV mix on a conforming sample (mortar work not counted)
-    return {"workload": f"half-refined unit cube (Sec. 4.1/4.2 layout), {k}x{2 * k}x{2 * k} + {k // 2}x{k}x{k} "
-                        "elements, type-3 mortars on both x interfaces, N in 2..5 and 5 % FV (N_FV = 8) at random, "
-                        "2 species, viscous, density wave along [1,1,1]",
-            "value": value, "unit": "DOF-stage/s",
-            "whole_rhs_tflops": per_dof * value / 1e12, "whole_rhs_frac_of_fp64_peak": per_dof * value / 1e12 / FP64_PEAK_TFLOPS,
-            "flops_per_dof": per_dof,
-            "ms_per_step": ms / (steps * STEPS_PER_CYCLE), "elements": ne, "dofs": dofs,
+    return {"value": r4(value), "whole_rhs_frac": r4(per_dof * value / 1e12 / peak),
+            "ms_per_step": r4(ms / (steps * STEPS_PER_CYCLE)), "elements": W.n_elements(prob), "dofs": dofs,
             "mortars": 2 * k * k, "fv_elements": int(prob["fv"].sum())}
 
 
-def batched_comparison(steps=5):
+def batched_comparison(steps=50, rank=0, world=1, dist=None):
     """256 independent periodic domains of 2^3..8^3 elements, one degree
-    N in 1..7 per domain, 3 species: DOF-stage/s of SSP-RK3 steps (fixed dt)
-    in one context with one launch per kernel (as run), the same with the
-    volume tiles autotuned, one launch per degree bin, and one context per
-    domain stepped in a loop."""
+    N in 1..7 per domain, 3 species, 50 SSP-RK3 steps (fixed dt): DOF-stage/s in
+    one context with one launch per kernel (as run), the same with the volume
+    tiles autotuned, one launch per degree bin, and one context per domain
+    stepped in a loop.  With several ranks every rank takes its share of the
+    domains (no exchange) and the figures are all ranks' work over the slowest
+    rank's time."""
     import torch
-    from paper_2502_19342_gb300 import dgfv, workloads as W
+    from paper_2502_19342_gb300 import dgfv, ranks, workloads as W
     prob, U = W.batched_domains()
+    if world > 1:
+        prob, U, _ = W.shard_domains(prob, U, rank, world)
     dofs = W.n_dofs(prob)
     s = torch.cuda.current_stream()
 
     def timed(fn):
         fn()  # warm-up (graph capture, autotuned tiles)
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(s)
         fn()
         b.record(s)
         torch.cuda.synchronize()
-        return a.elapsed_time(b)
+        ms, units = ranks.aggregate(a.elapsed_time(b), dofs * 3 * steps, dist, device="cuda")
+        return units / (ms * 1e-3)
 
     ctx = dgfv.Context(prob, N_min=1, N_max=7)
     Ud = torch.from_numpy(U).cuda()
     dt = 0.5 * ctx.compute_dt(Ud)[0]
+    if dist:  # one step size for every rank's share
+        t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+        dt = float(t.item())
     res = {}
     for name, mode in (("batched", 0), ("per_degree_loop", 1)):
         ctx.set_launch_mode(mode)
-        ctx.set_state(Ud)
-        ms = timed(lambda: ctx.rk_steps(steps, dt, want_dt=False))
-        res[name] = dofs * 3 * steps / (ms * 1e-3)
+
+        def run():
+            ctx.set_state(Ud)
+            ctx.rk_steps(steps, dt, want_dt=False)
+
+        res[name] = timed(run)
     ctx.set_launch_mode(0)
     ctx.set_state(Ud)
     tuned = ctx.autotune()
-    ctx.set_state(Ud)
-    res["batched_autotuned"] = dofs * 3 * steps / (timed(lambda: ctx.rk_steps(steps, dt, want_dt=False)) * 1e-3)
+
+    def run_tuned():
+        ctx.set_state(Ud)
+        ctx.rk_steps(steps, dt, want_dt=False)
+
+    res["batched_autotuned"] = timed(run_tuned)
     ctx.close()
     subs = []
     for sub, sl in W.domain_slices(prob):
         c = dgfv.Context(sub, N_min=1, N_max=7)
-        c.set_state(Ud[sl].contiguous())
-        subs.append(c)
+        subs.append((c, Ud[sl].contiguous()))
 
     def loop():
+        for c, u in subs:
+            c.set_state(u)
         for _ in range(steps):
-            for c in subs:
+            for c, _ in subs:
                 c.rk_step(dt, want_dt=False)
 
-    res["per_domain_loop"] = dofs * 3 * steps / (timed(loop) * 1e-3)
-    for c in subs:
+    res["per_domain_loop"] = timed(loop)
+    for c, _ in subs:
         c.close()
-    return {"workload": "256 periodic domains, 2^3..8^3 elements, N in 1..7 per domain, 3 species, viscous",
-            "dofs": dofs, "steps": steps, "unit": "DOF-stage/s",
-            **{k: round(v, 1) for k, v in res.items()},
-            "autotuned_elements_per_tile": tuned}
+    out = {"steps": steps, "dofs": dofs, **{k: r4(v) for k, v in res.items()},
+           "batched_over_per_degree": r4(res["batched"] / res["per_degree_loop"]),
+           "tiles": {str(k): v for k, v in tuned.items()}}
+    if world > 1:
+        out["domains_sharded"] = f"{world} ranks"
+    return out
 
 
 def run_reference(args, rank, world):
@@ -650,8 +694,9 @@ def main():
     torch.cuda.set_device(local)
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2502_19342_gb300 import dgfv, workloads as W
+    from paper_2502_19342_gb300 import dgfv, ranks, workloads as W
 
+    peak, peak_src = fp64_peak(local)
     prob, U = workload(args.nel, seed=rank)  # every rank its own realisation (weak scaling)
     ctx = dgfv.Context(prob, N_min=1, N_max=7, opts=dict(cfl_c=0.5, cfl_v=0.5, thresholds=W.THRESHOLDS))
     ctx.set_state(torch.from_numpy(U).cuda())
@@ -682,11 +727,17 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ------------------------------------------------------------ timed region (device-resident)
-    # the end-to-end leg repeats the same cycles from the same pattern and state (kept here, untimed)
+    # the profiled pass and the end-to-end leg repeat the timed cycles from the
+    # same pattern and state (kept here, untimed)
     start_N, start_fv = ctx.get_degrees()
-    start_U = None if args.no_e2e else ctx.get_state().cpu()
-    ctx.profile_enable(True)
+    start_U = ctx.get_state()
+
+    def restart():
+        ctx.set_degrees(start_N, start_fv, remap=False)
+        ctx.set_state(start_U)
+        torch.cuda.synchronize()
+
+    # ------------------------------------------------------------ timed region (device-resident, graph replay)
     units = 0.0
     pattern = []
     barrier()
@@ -704,20 +755,32 @@ def main():
         if args.profile_timed:
             torch.cuda.profiler.stop()
     ms = ev0.elapsed_time(ev1)
-    prof = ctx.profile_read()
-    ctx.profile_enable(False)
-    from paper_2502_19342_gb300 import ranks
     ms, tot_units = ranks.aggregate(ms, units, dist, device="cuda")  # slowest rank, all ranks' work
     value = tot_units / (ms * 1e-3)
+
+    # ------------------------------------------------------------ per-kernel times: a separate profiled pass
+    # (one launch per kernel bracketed by CUDA events on the launching stream,
+    # no graph), over the same cycles
+    restart()
+    ctx.profile_enable(True)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        cycle(ctx)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof_ms = p0.elapsed_time(p1)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
 
     # ------------------------------------------------------------ end to end through the C ABI, host buffers
     e2e = None
     if not args.no_e2e:
         cap = ctx.n_elem * ctx.V * 512
         host = torch.empty(cap, dtype=torch.float64).pin_memory()
-        ctx.set_degrees(start_N, start_fv, remap=False)
+        restart()
         n = ctx.state_size
-        host[:n].copy_(start_U)
+        host[:n].copy_(start_U.cpu())
         e_units, h2d, d2h = 0.0, 0, 0
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -734,59 +797,61 @@ def main():
         e1.record(stream)
         barrier()
         ems, e_units = ranks.aggregate(e0.elapsed_time(e1), e_units, dist, device="cuda")
-        e2e = {"value": e_units / (ems * 1e-3), "unit": "DOF-stage/s",
+        e2e = {"value": r4(e_units / (ems * 1e-3)), "unit": "DOF-stage/s",
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)}
 
+    batched = None if args.no_batched else batched_comparison(rank=rank, world=world, dist=dist)
     if rank == 0:
         # roofline of the dominant kernel, with flops per DOF of the pattern the timed steps ran on
         N_now, fv_now = ctx.get_degrees()
         per_dof, per_step = flops_per_dof(dict(prob, N=N_now, fv=fv_now))
+        dofs_per_launch = units / (args.steps * STEPS_PER_CYCLE * STAGES_PER_STEP)
+        kernels = kernel_table(prof, per_step, dofs_per_launch, peak)
         main_k = max((k for k in KERNEL_STEP if prof[k][1] > 0), key=lambda k: prof[k][0])
         kms, kl = prof[main_k]
-        dofs_per_launch = units / (args.steps * STEPS_PER_CYCLE * STAGES_PER_STEP)
         achieved = per_step[KERNEL_STEP[main_k]] * dofs_per_launch / (kms / kl * 1e-3) / 1e12
         probe = dgfv.probe_dfma(1 << 14) / 1e12
         probe_mma = dgfv.probe_dmma(1 << 11) / 1e12
         dg_dofs = float(np.sum((N_now[fv_now == 0].astype(np.int64) + 1) ** 3))
         traffic = VOLUME_DRAM_BYTES_PER_DG_DOF * dg_dofs if main_k == "dg_volume" else None
-        roof = {"bound": "alu", "kernel": main_k, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_dg_volume on the 28^3 "
-                                  "case, 344 B per DG DOF, times the DG DOFs of one launch here",
-                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 1.26 TFLOP/s)",
-                "dfma_probe_tflops": probe, "dmma_probe_tflops": probe_mma,
-                "flops_per_dof": {"total": per_dof, main_k: per_step[KERNEL_STEP[main_k]]},
-                "whole_rhs_tflops": per_dof * units / (ms * 1e-3) / 1e12}
+        roof = {"bound": "alu", "kernel": "k_" + main_k, "achieved": r4(achieved), "peak": r4(peak),
+                "unit": "TFLOP/s", "frac": r4(achieved / peak), "frac_of_dfma_probe": r4(achieved / probe),
+                "traffic": r4(traffic), "peak_source": peak_src,
+                "dfma_probe_tflops": r4(probe), "dmma_probe_tflops": r4(probe_mma),
+                "flops_per_dof": {"total": r4(per_dof), main_k: r4(per_step[KERNEL_STEP[main_k]])},
+                "whole_rhs_tflops": r4(per_dof * units / (ms * 1e-3) / 1e12),
+                "whole_rhs_frac": r4(per_dof * units / (ms * 1e-3) / 1e12 / peak)}
         if traffic is not None:
-            hbm_gbs, hbm_src = measured_hbm_gbs()
+            hbm_gbs, _ = measured_hbm_gbs()
             dram_gbs = traffic / (kms / kl * 1e-3) / 1e9
-            roof["hbm_context"] = {"dram_gbs": dram_gbs, "peak_gbs": hbm_gbs, "frac": dram_gbs / hbm_gbs,
-                                   "peak_source": hbm_src}
+            roof["hbm_frac"] = r4(dram_gbs / hbm_gbs)
         cpu = None if args.no_cpu else cpu_baseline(dict(prob, N=N_now, fv=fv_now))
-        adjoint = adjoint_cost()
-        adjoint["hybrid_dg_fv"] = adjoint_hybrid_cost()
-        batched = None if args.no_batched else batched_comparison()
-        split = None if args.no_split else split_form_run(args.nel)
+        if cpu:
+            cpu = {k: (r4(v) if isinstance(v, float) else v) for k, v in cpu.items()}
+        adjoint = {"mixing_layer": adjoint_cost(), "hybrid_shock": adjoint_hybrid_cost()}
+        shock = None if args.no_shock else hp_shock_run(peak)
+        split = None if args.no_split else split_form_run(args.nel, peak)
         tgv = None if args.no_tgv else tgv_run()
-        shock = None if args.no_shock else hp_shock_run()
-        mortar = None if args.no_mortar else mortar_run()
+        mortar = None if args.no_mortar else mortar_run(peak)
         launches = int(sum(v[1] for v in prof.values()))
         last = pattern[-1]
-        line = {"metric": "DOF-stage updates/s (FP64 RHS, hp-mixed)", "value": value, "unit": "DOF-stage/s",
-                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        line = {"metric": "DOF-stage updates/s (FP64 RHS, hp-mixed)", "value": r4(value), "unit": "DOF-stage/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r4(ms / args.steps),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD_NAME, "elements": ctx.n_elem,
                            "step": "adapt + 10 SSP-RK3 steps (30 stages), CFL 0.5",
                            "dofs_last_step": int(last["mean_dofs"] * ctx.n_elem), "fv_elements": last["n_fv"],
-                           "degree_histogram": last["hist"], "parallelism": f"replicas x{world} (own seed per rank, no exchange)",
+                           "parallelism": f"replicas x{world} (own seed per rank, no exchange); batched domains "
+                                          f"sharded over {world} rank(s)",
+                           "timing": "CUDA graph of the RK step replayed; per-kernel times from a separate "
+                                     f"profiled pass over the same cycles ({r4(prof_ms / args.steps)} ms/step)",
                            "volume_launch": ({str(k): v for k, v in tuned.items()} if tuned else "default"),
                            "l2": "inputs larger than L2 (state ~1.2 GB)"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "adjoint": adjoint,
-                "batched_domains": batched, "split_form": split, "tgv": tgv, "hp_shock": shock, "mortar": mortar,
-                "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
-                "clocks": clk.summary()}
-        print(json.dumps(line))
+                "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary(), "adjoint": adjoint, "batched_domains": batched, "hp_shock": shock,
+                "split_form": split, "tgv": tgv, "mortar": mortar}
+        print(json.dumps(line, separators=(",", ":")))
     ctx.close()
     if dist:
         dist.barrier()

@@ -115,6 +115,7 @@ struct dgfv_ctx {
     MixedSet mixed;         // the flux faces in three passes
     int n_fv_elems = 0;
     int launch_mode = 0;           // 0: one launch per kernel; 1: one launch per degree bin
+    int fv_variant = 0;            // k_fv layout: 0 automatic, 1 gradients recomputed, 2 gradients kept
     int vol_per_tile[MAXDG + 1] = {};  // elements per volume tile (0: default), set by the autotuner
     int vol_variant = 0;              // volume-kernel launch variant (threads, register budget), autotuned
     bool state_valid = false;
@@ -529,7 +530,7 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
     if (c->n_fv_elems) {
         Timed t(c, K_FV, s);
         launch_mortar_nb(c->nk, P, MT, c->d_s_active, c->n_slot_active, Uin, c->d_mnb, s);
-        launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, Uin, s);
+        launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, Uin, s, false, c->fv_variant);
     }
     if (c->n_mort) { Timed t(c, K_LIFT, s); launch_mortar_in(c->nk, P, MT, c->n_virt, 0, s); }
     if (c->ph.viscous) {
@@ -1053,7 +1054,7 @@ static void enqueue_vjp(dgfv_ctx* c, const double* U, const double* Rb, double* 
     launch_prolong(c->nk, P, c->all.view(), c->all.ntiles, U, s);
     if (c->n_fv_elems) {  // FV face states and gradients (with the neighbour values across mortars)
         launch_mortar_nb(c->nk, P, MT, c->d_s_active, c->n_slot_active, U, c->d_mnb, s);
-        launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, U, s, true);
+        launch_fv(c->nk, P, c->fvt.view(), c->fvt.ntiles, U, s, true, c->fv_variant);
     }
     launch_mortar_in(c->nk, P, MT, c->n_virt, 0, s);
     if (c->ph.viscous) {
@@ -1162,8 +1163,8 @@ int dgfv_rk_step_vjp(dgfv_ctx* c, const double* d_U0, double dt, const double* d
 int dgfv_rk_step_vjp_stages(dgfv_ctx* c, const double* const* d_stages, double dt, const double* d_Ubar_next,
                             double* d_Ubar, void* stream) {
     if (!c || !d_stages || !d_stages[0] || !d_stages[1] || !d_stages[2] || !d_Ubar_next || !d_Ubar || !(dt > 0.0))
-    TRY(check_dev(c));
         return DGFV_ERR_ARG;
+    TRY(check_dev(c));
     for (int i = 0; i < 3; ++i)
         if (d_Ubar == d_stages[i]) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
     if (d_Ubar == d_Ubar_next) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
@@ -1334,6 +1335,13 @@ int dgfv_set_launch_mode(dgfv_ctx* c, int mode) {
     return DGFV_OK;
 }
 
+int dgfv_set_fv_variant(dgfv_ctx* c, int variant) {
+    if (!c || variant < 0 || variant > 2) return DGFV_ERR_ARG;
+    c->fv_variant = variant;
+    c->graph_valid = false;
+    return DGFV_OK;
+}
+
 int dgfv_autotune(dgfv_ctx* c, int* per_tile_out, void* stream) {
     if (!c) return DGFV_ERR_ARG;
     TRY(check_dev(c));
@@ -1343,7 +1351,7 @@ int dgfv_autotune(dgfv_ctx* c, int* per_tile_out, void* stream) {
     const Faces F{c->d_faceL, c->d_faceR, c->d_faceD};
     // face values and lifting values of the current state, read by the volume kernel
     launch_prolong(c->nk, P0, c->all.view(), c->all.ntiles, c->d_U, s);
-    if (c->n_fv_elems) launch_fv(c->nk, P0, c->fvt.view(), c->fvt.ntiles, c->d_U, s);
+    if (c->n_fv_elems) launch_fv(c->nk, P0, c->fvt.view(), c->fvt.ntiles, c->d_U, s, false, c->fv_variant);
     if (c->ph.viscous) launch_face_lift(c->nk, P0, F, c->lift.d, c->lift.count, s);
     CK(cudaStreamSynchronize(s));
     cudaEvent_t e0, e1;

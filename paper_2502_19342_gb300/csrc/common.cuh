@@ -123,6 +123,38 @@ struct Faces {
     const uint8_t* d;
 };
 
+// Shared-memory layout of one FV element in k_fv (offsets in doubles); gs = 1
+// keeps the sub-cell gradients (see the kernel).
+struct FvLayout {
+    int u, w, nb, nw, f, g, t, total;
+};
+
+__host__ __device__ __forceinline__ FvLayout fv_layout(int V, int n, int gs) {
+    const int n2 = n * n, n3 = n2 * n, tmp = 2 * V * MAXP * MAXP, fl = 3 * V * (n - 1) * n2;
+    FvLayout L;
+    if (gs) {
+        const int gsz = 3 * V * n3 > tmp ? 3 * V * n3 : tmp;
+        L.g = 0;
+        L.t = 0;
+        L.w = gsz;
+        L.nw = L.w + V * n3;
+        L.f = L.nw + 6 * V * n2;
+        L.u = L.f;
+        L.nb = L.f + V * n3;
+        L.total = L.f + (fl > V * n3 + 6 * V * n2 ? fl : V * n3 + 6 * V * n2);
+    } else {
+        L.u = 0;
+        L.w = V * n3;
+        L.nb = 2 * V * n3;
+        L.nw = L.nb + 6 * V * n2;
+        L.f = L.nw + 6 * V * n2;
+        L.t = L.f;
+        L.g = 0;
+        L.total = L.f + (fl > tmp ? fl : tmp);
+    }
+    return L;
+}
+
 __host__ __device__ __forceinline__ int node_index(int n, int d, int m, int a, int b) {
     return d == 0 ? m + n * (a + n * b) : (d == 1 ? a + n * (m + n * b) : a + n * (b + n * m));
 }

@@ -23,6 +23,7 @@
 // sum-factorised contractions, fused multiply-adds).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cstdint>
 #include <mutex>
@@ -95,24 +96,40 @@ __global__ void __launch_bounds__(256) k_prolong(Params P, Tiles T, const double
 //   DG neighbour -> its solution mapped to sub-cell means by V^{DG->FV}, boundary layer.
 //   minmod reconstruction of (rho_k, v, p), conservative central-difference
 //   gradients, interior sub-cell fluxes -> rtmp; element-face states -> frec, fg.
-template <int NK, int NF>
+// The kernel is bound by its FP64 instruction count, so every reconstructed
+// face value becomes its conservative and mixture state in one step with a
+// single division (face_state), the minmod limiter runs on the integer pipe
+// (minmod_bits), and with GS = 1 the central-difference gradient of every
+// sub-cell is formed once and kept in shared memory (GS = 0: recomputed at
+// each of the cell's faces, for layouts that would not fit).
+//
+// Shared-memory layout (doubles) of one element, see fv_layout:
+//   GS = 1: [gradients 3V n^3 | w V n^3 | neighbour w 6V n^2 | X]; X first holds
+//           the conservative means (V n^3) and neighbour values (6V n^2), after
+//           the gradients are formed the interior face fluxes 3V (n-1) n^2;
+//           the gather's scratch sits in the gradient region.
+//   GS = 0: [u V n^3 | w V n^3 | neighbour u 6V n^2 | neighbour w 6V n^2 | fluxes],
+//           the gather's scratch in the flux region.
+template <int NK, int NF, int GS>
 __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const double* __restrict__ U,
                                         bool faces_only) {
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
     const int n = NF > 0 ? NF : P.nfv, n2 = n * n, n3 = n2 * n;
     const int e = T.items[T.first[blockIdx.x]];
-    double* sU = sm;                 // V*n3 conservative means
-    double* sW = sU + V * n3;        // V*n3 reconstruction variables
-    double* sNb = sW + V * n3;       // 6*V*n2 neighbour values (conservative)
-    double* sNw = sNb + 6 * V * n2;  // 6*V*n2 neighbour reconstruction variables
-    double* sF = sNw + 6 * V * n2;   // 3V*(n-1)*n2 interior face fluxes of the three directions
-    double* sT1 = sF + 3 * V * (n - 1) * n2;   // scratch V*MAXP*MAXP
-    double* sT2 = sT1 + V * MAXP * MAXP;   // scratch V*MAXP*MAXP
+    const FvLayout L = fv_layout(V, n, GS);
+    double* sU = sm + L.u;    // V*n3 conservative means
+    double* sW = sm + L.w;    // V*n3 reconstruction variables
+    double* sNb = sm + L.nb;  // 6*V*n2 neighbour values (conservative)
+    double* sNw = sm + L.nw;  // 6*V*n2 neighbour reconstruction variables
+    double* sF = sm + L.f;    // 3V*(n-1)*n2 interior face fluxes of the three directions
+    double* sG = sm + L.g;    // 3V*n3 gradients (GS = 1)
+    double* sT1 = sm + L.t;   // gather scratch, V*MAXP*MAXP each
+    double* sT2 = sT1 + V * MAXP * MAXP;
     const int64_t off = P.t.off[e];
     const double* rh = P.t.rh + 3 * e;
     __shared__ double sID[6], sGS[6];  // per face: 1/distance to the neighbour's centre, rh/(l + distance)
-    const double l = 2.0 / n;
+    const double l = 2.0 / n, il = 0.5 * n;
     for (int i = threadIdx.x; i < V * n3; i += blockDim.x) sU[i] = U[off + i];
     // neighbour values (across a mortar: gathered beforehand into the slot's values)
     for (int f = 0; f < 6; ++f) {
@@ -137,47 +154,10 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
         }
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < n3; c += blockDim.x) {
-        double u[V], w[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) u[v] = sU[v * n3 + c];
-        cons_to_w<NK>(P.ph, u, w);
-#pragma unroll
-        for (int v = 0; v < V; ++v) sW[v * n3 + c] = w[v];
-    }
-    for (int c = threadIdx.x; c < 6 * n2; c += blockDim.x) {
-        const int f = c / n2, p = c % n2;
-        double u[V], w[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) u[v] = sNb[(f * V + v) * n2 + p];
-        cons_to_w<NK>(P.ph, u, w);
-#pragma unroll
-        for (int v = 0; v < V; ++v) sNw[(f * V + v) * n2 + p] = w[v];
-    }
-    __syncthreads();
-    // value of variable v of cell (m along d, a, b) or of the neighbour beyond
     auto cellU = [&](int d, int m, int a, int b, int v) -> double {
         if (m < 0) return sNb[((2 * d) * V + v) * n2 + a + n * b];
         if (m >= n) return sNb[((2 * d + 1) * V + v) * n2 + a + n * b];
         return sU[v * n3 + node_index(n, d, m, a, b)];
-    };
-    auto cellW = [&](int d, int m, int a, int b, int v) -> double {
-        if (m < 0) return sNw[((2 * d) * V + v) * n2 + a + n * b];
-        if (m >= n) return sNw[((2 * d + 1) * V + v) * n2 + a + n * b];
-        return sW[v * n3 + node_index(n, d, m, a, b)];
-    };
-    // reconstructed conservative state of cell m (along d) at its face side (-1 or +1)
-    auto recon = [&](int d, int m, int a, int b, int side, double* uo) {
-        double w[V];
-        const double il = 1.0 / l;
-        const double ilm = m > 0 ? il : sID[2 * d], ilp = m < n - 1 ? il : sID[2 * d + 1];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const double wc = cellW(d, m, a, b, v);
-            const double s = minmod((wc - cellW(d, m - 1, a, b, v)) * ilm, (cellW(d, m + 1, a, b, v) - wc) * ilp);
-            w[v] = side > 0 ? wc + s * (0.5 * l) : wc - s * (0.5 * l);
-        }
-        w_to_cons<NK>(P.ph, w, uo);
     };
     // central-difference gradient of the conservative variables at a cell (coordinates i,j,k)
     auto grad = [&](int i, int j, int k, double* g) {
@@ -191,6 +171,58 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
 #pragma unroll
             for (int v = 0; v < V; ++v)
                 g[dd * V + v] = (cellU(dd, m + 1, a, b, v) - cellU(dd, m - 1, a, b, v)) * sc;
+        }
+    };
+    for (int c = threadIdx.x; c < n3; c += blockDim.x) {
+        double u[V], w[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) u[v] = sU[v * n3 + c];
+        cons_to_w<NK>(P.ph, u, w);
+#pragma unroll
+        for (int v = 0; v < V; ++v) sW[v * n3 + c] = w[v];
+        if (GS) {
+            double g[3 * V];
+            grad(c % n, (c / n) % n, c / n2, g);
+#pragma unroll
+            for (int x = 0; x < 3 * V; ++x) sG[x * n3 + c] = g[x];
+        }
+    }
+    for (int c = threadIdx.x; c < 6 * n2; c += blockDim.x) {
+        const int f = c / n2, p = c % n2;
+        double u[V], w[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) u[v] = sNb[(f * V + v) * n2 + p];
+        cons_to_w<NK>(P.ph, u, w);
+#pragma unroll
+        for (int v = 0; v < V; ++v) sNw[(f * V + v) * n2 + p] = w[v];
+    }
+    __syncthreads();  // (GS = 1: the means and neighbour values are dead from here on)
+    auto cellW = [&](int d, int m, int a, int b, int v) -> double {
+        if (m < 0) return sNw[((2 * d) * V + v) * n2 + a + n * b];
+        if (m >= n) return sNw[((2 * d + 1) * V + v) * n2 + a + n * b];
+        return sW[v * n3 + node_index(n, d, m, a, b)];
+    };
+    // reconstructed reconstruction variables of cell m (along d) at its face side (-1 or +1):
+    // w +- l/2 minmod(dw-/dist-, dw+/dist+); inside the element both distances are l,
+    // so the half slope is minmod(dw-, dw+)/2
+    auto face_w = [&](int d, int m, int a, int b, int side, double* w) {
+        const bool inner = m > 0 && m < n - 1;
+        const double ilm = m > 0 ? il : sID[2 * d], ilp = m < n - 1 ? il : sID[2 * d + 1];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const double wc = cellW(d, m, a, b, v);
+            const double dm = wc - cellW(d, m - 1, a, b, v), dp = cellW(d, m + 1, a, b, v) - wc;
+            const double h = inner ? 0.5 * minmod_bits(dm, dp) : (0.5 * l) * minmod_bits(dm * ilm, dp * ilp);
+            w[v] = side > 0 ? wc + h : wc - h;
+        }
+    };
+    auto cell_grad = [&](int i, int j, int k, double* g) {
+        if (GS) {
+            const int c = i + n * (j + n * k);
+#pragma unroll
+            for (int x = 0; x < 3 * V; ++x) g[x] = sG[x * n3 + c];
+        } else {
+            grad(i, j, k, g);
         }
     };
     auto coords = [&](int d, int m, int a, int b, int& i, int& j, int& k) {
@@ -207,14 +239,16 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
         const int d = t / nif, fidx = t - d * nif;
         const int m = fidx % (n - 1), p = fidx / (n - 1), a = p % n, b = p / n;
         // F* = F^c*(uL, uR) + (F^v(uL, gL) + F^v(uR, gR))/2, the two viscous
-        // fluxes one after the other (one gradient live at a time: fewer
-        // registers than the face kernels' interface_flux)
+        // fluxes one after the other (one gradient live at a time)
         double uL[V], uR[V], F[V];
-        recon(d, m, a, b, +1, uL);
-        recon(d, m + 1, a, b, -1, uR);
         Prim<NK> sL, sR;
-        prim<NK>(P.ph, uL, sL);
-        prim<NK>(P.ph, uR, sR);
+        {
+            double w[V];
+            face_w(d, m, a, b, +1, w);
+            face_state<NK>(P.ph, w, uL, sL);
+            face_w(d, m + 1, a, b, -1, w);
+            face_state<NK>(P.ph, w, uR, sR);
+        }
         if (use_roe(P.ph, true))
             riemann_roe<NK>(P.ph, uL, sL, uR, sR, d, F);
         else
@@ -225,7 +259,7 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
                 int i, j, k;
                 coords(d, m + side, a, b, i, j, k);
                 double g[3 * V], Fv[V];
-                grad(i, j, k, g);
+                cell_grad(i, j, k, g);
                 PrimGrad<NK> G;
                 prim_grad<NK>(P.ph, side ? sR : sL, g, G);
                 flux_visc<NK>(P.ph, side ? sR : sL, G, d, Fv);
@@ -262,8 +296,9 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
     for (int i = threadIdx.x; i < 6 * n2; i += blockDim.x) {
         const int f = i / n2, p = i % n2, a = p % n, b = p / n, d = f >> 1, s = f & 1;
         const int m = s ? n - 1 : 0;
-        double u[V];
-        recon(d, m, a, b, s ? +1 : -1, u);
+        double w[V], u[V];
+        face_w(d, m, a, b, s ? +1 : -1, w);
+        w_to_cons<NK>(P.ph, w, u);
         const int64_t slot = P.t.fo[e] + (int64_t)f * n2;
 #pragma unroll
         for (int v = 0; v < V; ++v) P.b.frec[slot * V + v * n2 + p] = u[v];
@@ -271,7 +306,7 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
             double g[3 * V];
             int ii, jj, kk;
             coords(d, m, a, b, ii, jj, kk);
-            grad(ii, jj, kk, g);
+            cell_grad(ii, jj, kk, g);
 #pragma unroll
             for (int x = 0; x < 3 * V; ++x) P.b.fg[slot * 3 * V + x * n2 + p] = g[x];
         }
@@ -279,18 +314,19 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
 }
 
 
-// NF: the sub-cell count as a compile-time constant for the common N_FV = 8.
-// 16 warps per SM at 128 registers a thread (the spills of that budget go to
-// L1): two CTAs of 256 threads where the shared memory of two elements fits
-// on an SM (N_FV <= 7), otherwise one CTA of 512 threads (N_FV = 8, up to
-// 180 KB for one element).
-template <int NK, int TPB>
+// NF: the sub-cell count as a compile-time constant for the common N_FV = 8,
+// a runtime one otherwise (the kernel is bound by its FP64 instructions, which
+// a constant count does not change; the integer index work it saves hides
+// behind them).  16 warps per SM at 128
+// registers a thread: two CTAs of 256 threads where the shared memory of two
+// elements fits on an SM, otherwise one CTA of 512 threads.
+template <int NK, int TPB, int GS>
 __global__ void __launch_bounds__(TPB, 512 / TPB) k_fv(Params P, Tiles T, const double* __restrict__ U,
                                                        int faces_only) {
     if (P.nfv == 8)
-        fv_body<NK, 8>(P, T, U, faces_only != 0);
+        fv_body<NK, 8, GS>(P, T, U, faces_only != 0);
     else
-        fv_body<NK, 0>(P, T, U, faces_only != 0);
+        fv_body<NK, 0, GS>(P, T, U, faces_only != 0);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1261,21 +1297,42 @@ void launch_prolong(int nk, const Params& P, const Tiles& T, int ntiles, const d
     DGFV_DISPATCH(nk, (k_prolong<NK><<<ntiles, 256, tile_state_smem(nk, P.nfv), s>>>(P, T, U)));
 }
 
-size_t fv_smem_bytes(int nk, int nfv) {
-    const int V = nk + 4, n2 = nfv * nfv, n3 = n2 * nfv;
-    return sizeof(double) * (size_t)(2 * V * n3 + 12 * V * n2 + 3 * V * (nfv - 1) * n2 + 2 * V * MAXP * MAXP);
+size_t fv_smem_bytes_variant(int nk, int nfv, int gs) {
+    return sizeof(double) * (size_t)fv_layout(nk + 4, nfv, gs).total;
 }
 
-void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s, bool faces_only) {
+// The smaller of the two layouts (the one that has to fit for the FV path to run).
+size_t fv_smem_bytes(int nk, int nfv) {
+    return std::min(fv_smem_bytes_variant(nk, nfv, 0), fv_smem_bytes_variant(nk, nfv, 1));
+}
+
+// 228 KB of shared memory per SM, 1 KB of it reserved per resident CTA
+static bool fits_per_sm(size_t sm, int ctas) { return ctas * (sm + 1024 + 256) <= 228 * 1024; }
+
+int fv_variant_auto(int nk, int nfv) {
+    // gradients kept (GS = 1) when that layout fits one CTA per SM and the
+    // recomputing one would not fit two; else the recomputing layout
+    const size_t s0 = fv_smem_bytes_variant(nk, nfv, 0), s1 = fv_smem_bytes_variant(nk, nfv, 1);
+    if (fits_per_sm(s1, 1) && !fits_per_sm(s0, 2)) return 1;
+    return 0;
+}
+
+void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s, bool faces_only,
+               int variant) {
     if (ntiles <= 0) return;
-    const size_t sm = fv_smem_bytes(nk, P.nfv);
-    // 228 KB of shared memory per SM, 1 KB of it reserved per resident CTA
-    if (2 * (sm + 1024 + 256) <= 228 * 1024) {
-        DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_fv<NK, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
-                           k_fv<NK, 256><<<ntiles, 256, sm, s>>>(P, T, U, faces_only ? 1 : 0)));
+    int gs = variant == 1 ? 0 : (variant == 2 ? 1 : fv_variant_auto(nk, P.nfv));
+    if (gs == 1 && !fits_per_sm(fv_smem_bytes_variant(nk, P.nfv, 1), 1)) gs = 0;
+    const size_t sm = fv_smem_bytes_variant(nk, P.nfv, gs);
+    const int fo = faces_only ? 1 : 0;
+    if (gs == 1) {
+        DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_fv<NK, 512, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                           k_fv<NK, 512, 1><<<ntiles, 512, sm, s>>>(P, T, U, fo)));
+    } else if (fits_per_sm(sm, 2)) {
+        DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_fv<NK, 256, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                           k_fv<NK, 256, 0><<<ntiles, 256, sm, s>>>(P, T, U, fo)));
     } else {
-        DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_fv<NK, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
-                           k_fv<NK, 512><<<ntiles, 512, sm, s>>>(P, T, U, faces_only ? 1 : 0)));
+        DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_fv<NK, 512, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                           k_fv<NK, 512, 0><<<ntiles, 512, sm, s>>>(P, T, U, fo)));
     }
 }
 

@@ -14,8 +14,10 @@ void launch_prolong(int nk, const Params& P, const Tiles& T, int ntiles, const d
 size_t fv_smem_bytes(int nk, int nfv);
 // faces_only: only the element-face states and boundary gradients (frec, fg),
 // not the sub-cell fluxes (the adjoint's recomputation of the forward).
+// variant: 0 automatic, 1 gradients recomputed at each face, 2 gradients kept
+// in shared memory (when that layout fits).
 void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s,
-               bool faces_only = false);
+               bool faces_only = false, int variant = 0);
 void launch_face_lift_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s);
 void launch_face_lift(int nk, const Params& P, const Faces& F, const int32_t* list, int nfaces, cudaStream_t s);
 size_t volume_smem_bytes(int nk, int n, int count);

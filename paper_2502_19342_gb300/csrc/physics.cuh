@@ -402,4 +402,72 @@ DGFV_HD double minmod(double a, double b) {
     return fabs(a) <= fabs(b) ? a : b;
 }
 
+#if defined(__CUDACC__)
+// minmod on the bit patterns, with no FP64 instruction: 0 when the signs
+// differ (a signed zero counts by its sign bit, and a zero argument gives 0
+// either way), else the argument of smaller magnitude, a on ties (for finite
+// doubles |a| <= |b| is the unsigned order of the bits without the sign).
+__device__ __forceinline__ double minmod_bits(double a, double b) {
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    if ((ia ^ ib) < 0) return 0.0;
+    return (unsigned long long)(ia & 0x7fffffffffffffffLL) <= (unsigned long long)(ib & 0x7fffffffffffffffLL) ? a
+                                                                                                          : b;
+}
+#endif
+
+// Conservative state u and mixture state s of a reconstructed FV face value
+// w = (rho_1..rho_NK, v, p), the same quantities as w_to_cons followed by
+// prim, with one division: with A = rho c_v, B = rho c_p, Rr = B - A = rho R_mix
+// and Q = rho Pr_mix, the reciprocals of rho, A, Rr and Q all come from
+// 1/(rho A Rr Q); then rho E = p A/Rr + rho |v|^2/2, T = p/Rr, kappa = B/A,
+// lambda = mu B/Q.
+template <int NK>
+DGFV_HD void face_state(const DevPhys& P, const double* w, double* u, Prim<NK>& s) {
+    double rho = w[0], A = w[0] * P.cv[0], Bc = w[0] * P.cp[0], Mu = w[0] * P.mu[0], Q = w[0] * P.pr[0];
+#pragma unroll
+    for (int k = 1; k < NK; ++k) {
+        rho += w[k];
+        A = fma(w[k], P.cv[k], A);
+        Bc = fma(w[k], P.cp[k], Bc);
+        Mu = fma(w[k], P.mu[k], Mu);
+        Q = fma(w[k], P.pr[k], Q);
+    }
+    const double Rr = Bc - A;
+    const double AR = A * Rr, rQ = rho * Q;
+    const double inv = 1.0 / (AR * rQ);
+    const double irho = AR * Q * inv;
+    const double iAR = rQ * inv;  // 1/(A Rr)
+    const double iA = iAR * Rr, iR = iAR * A;
+    s.rho = rho;
+    s.irho = irho;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        u[k] = w[k];
+        s.Y[k] = w[k] * irho;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        s.v[i] = w[NK + i];
+        u[NK + i] = rho * w[NK + i];
+    }
+    const double p = w[NK + 3];
+    const double q2 = fma(w[NK], w[NK], fma(w[NK + 1], w[NK + 1], w[NK + 2] * w[NK + 2]));
+    const double rE = fma(p * A, iR, 0.5 * rho * q2);
+    u[NK + 3] = rE;
+    s.E = rE * irho;
+    s.cv = A * irho;
+    s.icv = rho * iA;
+    s.cp = Bc * irho;
+    s.kappa = Bc * iA;
+    s.T = p * iR;
+    s.eps = s.cv * s.T;
+    s.p = p;
+    s.c = sqrt(s.kappa * p * irho);
+    double mu = Mu * irho;
+    if (P.sutherland) mu *= sutherland_factor(P, s.T);
+    s.mu = mu;
+    s.pr = Q * irho;
+    s.lam = mu * Bc * (AR * rho * inv);  // mu c_p / Pr = mu B / Q
+}
+
 }  // namespace dgfv

@@ -23,7 +23,8 @@ SYMBOLS = ["dgfv_init_mesh", "dgfv_num_elements", "dgfv_set_degrees", "dgfv_get_
            "dgfv_status_string", "dgfv_last_error", "dgfv_destroy", "dgfv_bank_entry", "dgfv_probe_dfma",
            "dgfv_profile_enable", "dgfv_profile_read", "dgfv_compute_dt_noalloc", "dgfv_rhs_vjp",
            "dgfv_rk_step_vjp", "dgfv_set_launch_mode", "dgfv_autotune", "dgfv_rk_step_save",
-           "dgfv_rk_step_vjp_stages", "dgfv_probe_dmma", "dgfv_pp_limit", "dgfv_pp_count"]
+           "dgfv_rk_step_vjp_stages", "dgfv_probe_dmma", "dgfv_pp_limit", "dgfv_pp_count",
+           "dgfv_set_fv_variant"]
 KERNELS = ["prolong", "fv", "face_lift", "dg_volume", "face_flux", "surface", "dt", "indicator", "remap"]
 
 
@@ -75,6 +76,7 @@ def lib():
         L.dgfv_compute_dt_noalloc.argtypes = [vp, vp, vp, vp]
         L.dgfv_rhs_vjp.argtypes = [vp, vp, vp, vp, vp]
         L.dgfv_set_launch_mode.argtypes = [vp, C.c_int]
+        L.dgfv_set_fv_variant.argtypes = [vp, C.c_int]
         L.dgfv_autotune.argtypes = [vp, C.POINTER(C.c_int), vp]
         L.dgfv_rk_step_vjp.argtypes = [vp, vp, C.c_double, vp, vp, vp]
         L.dgfv_rk_step_save.argtypes = [vp, C.c_double, vp, vp, vp]
@@ -355,6 +357,10 @@ class Context:
 
     def sync_status(self, stream=None):
         self._rc(lib().dgfv_sync_status(self.h, _stream(stream)), "device status")
+
+    def set_fv_variant(self, variant):
+        """FV sub-cell kernel layout: 0 automatic, 1 gradients recomputed at each face, 2 gradients kept."""
+        self._rc(lib().dgfv_set_fv_variant(self.h, int(variant)), "set_fv_variant")
 
     def set_launch_mode(self, per_degree):
         """False: one launch per kernel over all degrees; True: one launch per degree bin."""

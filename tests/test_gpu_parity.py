@@ -64,6 +64,27 @@ def test_rhs_mixed_hp_fv(oracle, nk, riemann, mu, seed, nodes, split):
     assert_rhs_close(oracle, prob, U, gpu_rhs(prob, U))
 
 
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("nk,n_fv,riemann,mu", [(2, 7, 0, 2e-3), (3, 8, 2, 2e-3), (2, 9, 0, 1e-3),
+                                                 (3, 5, 1, 3e-3), (1, 8, 0, 0.0)])
+def test_fv_kernel_layouts_match_oracle(oracle, variant, nk, n_fv, riemann, mu):
+    """Both shared-memory layouts of the FV sub-cell kernel (gradients
+    recomputed at each face / kept per sub-cell) on a hybrid mesh with 40 % FV
+    elements, N_FV = 5, 7, 8, 9: R(U) against the oracle at the bar of R."""
+    sp = W.species_set([W.AIR, W.HELIUM, W.CO2][:nk], mu=mu)
+    n = 3 * 3 * 4
+    N = W.random_degrees(n, 1, min(6, n_fv - 1), 40 + n_fv)
+    prob = W.make_problem([((3, 3, 4), (0, 0, 0), (1.0, 0.9, 1.2))], sp, n_fv=n_fv, N=N,
+                          fv=W.random_fv(n, 0.4, 40 + n_fv), riemann=riemann)
+    U = W.smooth_random_state(prob, 40 + n_fv, amp=0.15)
+    from paper_2502_19342_gb300 import dgfv
+    ctx = dgfv.Context(prob)
+    ctx.set_fv_variant(variant)
+    R = ctx.eval_rhs(to_dev(U)).cpu().numpy()
+    ctx.close()
+    assert_rhs_close(oracle, prob, U, R)
+
+
 def test_rhs_batched_domains(oracle):
     """Several independent periodic domains of uneven size and degree in one context."""
     sp = W.species_set([W.AIR, W.HELIUM, W.CO2], mu=1e-3)
