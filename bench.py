@@ -488,7 +488,7 @@ def tgv_run(nel=32, warmup=30, steps=2):
             "degree_histogram": np.bincount(N_now[fv_now == 0], minlength=5).tolist()[2:]}
 
 
-def hp_shock_run(peak, cycles=40):
+def hp_shock_run(peak, cycles=40, fv_variant=0):
     """The hp-mixed shock case at its full length: 16^3 elements on
     [0,2]x[0,1]^2, N in 2..6 with FV sub-cells (N_FV = 7) chosen by the
     indicator every 5 SSP-RK3 steps, a Mach 1.5 shock into a heavy-gas bubble,
@@ -500,6 +500,7 @@ def hp_shock_run(peak, cycles=40):
     from paper_2502_19342_gb300 import dgfv, workloads as W
     prob, U = W.hp_shock(0, y_bg=0.01)
     ctx = dgfv.Context(prob, N_min=2, N_max=6, opts=dict(cfl_c=0.5, cfl_v=0.5, thresholds=W.THRESHOLDS))
+    ctx.set_fv_variant(fv_variant)
     ctx.set_state(torch.from_numpy(U).cuda())
     s = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * cycles + 1)]
@@ -517,13 +518,24 @@ def hp_shock_run(peak, cycles=40):
     adapt_ms = sum(ev[2 * c].elapsed_time(ev[2 * c + 1]) for c in range(cycles))
     rk_ms = sum(ev[2 * c + 1].elapsed_time(ev[2 * c + 2]) for c in range(cycles))
     N_now, fv_now = ctx.get_degrees()
-    ctx.close()
-    per_dof, _ = flops_per_dof(dict(prob, N=N_now, fv=fv_now))
+    per_dof, per_step = flops_per_dof(dict(prob, N=N_now, fv=fv_now))
     rate = units / (rk_ms * 1e-3)
+    # per-kernel times: 2 more cycles (pattern close to the final one), profiled
+    ctx.profile_enable(True)
+    pu = 0.0
+    for _ in range(2):
+        st = ctx.adapt()
+        ctx.rk_steps(5, -1.0, want_dt=False)
+        pu += st["mean_dofs"] * ctx.n_elem * 5 * STAGES_PER_STEP
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    ctx.close()
+    kernels = kernel_table(prof, per_step, pu / (2 * 5 * STAGES_PER_STEP), peak)
     return {"steps": 5 * cycles, "value": r4(units / ((adapt_ms + rk_ms) * 1e-3)), "rk_value": r4(rate),
             "adapt_ms_per_cycle": r4(adapt_ms / cycles), "rk_ms_per_cycle": r4(rk_ms / cycles),
             "whole_rhs_tflops": r4(per_dof * rate / 1e12), "whole_rhs_frac": r4(per_dof * rate / 1e12 / peak),
-            "flops_per_dof": r4(per_dof), "fv_elements_first_last": [fvs[0], fvs[-1]],
+            "flops_per_dof": r4(per_dof), "fv_elements_first_last": [fvs[0], fvs[-1]], "kernels": kernels,
             "subcell_dof_share": r4(float(fv_now.astype(np.int64).sum() * 343) / float(W.n_dofs(dict(prob, N=N_now, fv=fv_now))))}
 
 

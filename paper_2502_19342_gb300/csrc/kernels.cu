@@ -258,11 +258,22 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
             for (int side = 0; side < 2; ++side) {
                 int i, j, k;
                 coords(d, m + side, a, b, i, j, k);
-                double g[3 * V], Fv[V];
-                cell_grad(i, j, k, g);
-                PrimGrad<NK> G;
-                prim_grad<NK>(P.ph, side ? sR : sL, g, G);
-                flux_visc<NK>(P.ph, side ? sR : sL, G, d, Fv);
+                const int c = i + n * (j + n * k);
+                const int c3[3] = {i, j, k};
+                // d u_v / d x_dd of this cell: kept (GS = 1) or the central difference
+                auto gx = [&](int dd, int v) -> double {
+                    if (GS) return sG[(dd * V + v) * n3 + c];
+                    const int mm = c3[dd];
+                    const int aa = dd == 0 ? c3[1] : c3[0], bb = dd == 2 ? c3[1] : c3[2];
+                    const double sc =
+                        mm == 0 ? sGS[2 * dd] : (mm == n - 1 ? sGS[2 * dd + 1] : 0.5 * n * 0.5 * rh[dd]);
+                    return (cellU(dd, mm + 1, aa, bb, v) - cellU(dd, mm - 1, aa, bb, v)) * sc;
+                };
+                double Fv[V];
+                const Prim<NK>& sx = side ? sR : sL;
+                if (d == 0) flux_visc_dir<NK, 0>(P.ph, sx, gx, Fv);
+                else if (d == 1) flux_visc_dir<NK, 1>(P.ph, sx, gx, Fv);
+                else flux_visc_dir<NK, 2>(P.ph, sx, gx, Fv);
 #pragma unroll
                 for (int v = 0; v < V; ++v) F[v] = fma(0.5, Fv[v], F[v]);
             }
@@ -1310,11 +1321,10 @@ size_t fv_smem_bytes(int nk, int nfv) {
 static bool fits_per_sm(size_t sm, int ctas) { return ctas * (sm + 1024 + 256) <= 228 * 1024; }
 
 int fv_variant_auto(int nk, int nfv) {
-    // gradients kept (GS = 1) when that layout fits one CTA per SM and the
-    // recomputing one would not fit two; else the recomputing layout
-    const size_t s0 = fv_smem_bytes_variant(nk, nfv, 0), s1 = fv_smem_bytes_variant(nk, nfv, 1);
-    if (fits_per_sm(s1, 1) && !fits_per_sm(s0, 2)) return 1;
-    return 0;
+    // gradients kept (GS = 1, one CTA of 512 threads per SM) wherever that
+    // layout fits: at N_FV = 7 and 2 species it measured 4 % faster per cycle of
+    // the hp-mixed shock case than two recomputing CTAs per SM
+    return fits_per_sm(fv_smem_bytes_variant(nk, nfv, 1), 1) ? 1 : 0;
 }
 
 void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s, bool faces_only,

@@ -158,6 +158,60 @@ DGFV_HD void flux_visc(const DevPhys& P, const Prim<NK>& s, const PrimGrad<NK>& 
     F[NK + 3] = -tv - s.lam * G.T[d] + s.T * qd;
 }
 
+// Viscous flux in direction D (a compile-time constant) straight from the
+// conservative gradient, computing only what that direction needs: gx(dd, v)
+// returns d u_v / d x_dd.  Of direction D every variable's gradient is used
+// (species and temperature gradients, the column dv_i/dx_D); of the other two
+// directions A, B only the densities and the momenta along D and along A (B):
+// tau_{D.} needs dv_D/dx_A, dv_D/dx_B and div v the diagonal.  The same
+// formulas as prim_grad + flux_visc (Eqs. 4a-4c, 5), with about two thirds of
+// their FP64 work when the direction is not known before the call.
+template <int NK, int D, class GX>
+DGFV_HD void flux_visc_dir(const DevPhys& P, const Prim<NK>& s, GX gx, double* F) {
+    constexpr int A = D == 0 ? 1 : 0, B = D == 2 ? 1 : 2;
+    double grD = gx(D, 0), grA = gx(A, 0), grB = gx(B, 0);
+#pragma unroll
+    for (int k = 1; k < NK; ++k) {
+        grD += gx(D, k);
+        grA += gx(A, k);
+        grB += gx(B, k);
+    }
+    double vD[3];  // dv_i/dx_D
+#pragma unroll
+    for (int i = 0; i < 3; ++i) vD[i] = (gx(D, NK + i) - s.v[i] * grD) * s.irho;
+    const double vDA = (gx(A, NK + D) - s.v[D] * grA) * s.irho;  // dv_D/dx_A
+    const double vDB = (gx(B, NK + D) - s.v[D] * grB) * s.irho;  // dv_D/dx_B
+    const double vAA = (gx(A, NK + A) - s.v[A] * grA) * s.irho;
+    const double vBB = (gx(B, NK + B) - s.v[B] * grB) * s.irho;
+    const double divv = vD[D] + vAA + vBB;
+    double tau[3];
+    tau[D] = s.mu * (2.0 * vD[D] - (2.0 / 3.0) * divv);
+    tau[A] = s.mu * (vDA + vD[A]);
+    tau[B] = s.mu * (vDB + vD[B]);
+    double GY[NK], corr = 0.0, gcv = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        GY[k] = (gx(D, k) - s.Y[k] * grD) * s.irho;
+        corr = fma(P.D[k], GY[k], corr);
+        gcv = fma(P.cv[k], GY[k], gcv);
+    }
+    double geps = (gx(D, NK + 3) - s.E * grD) * s.irho;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) geps -= s.v[i] * vD[i];
+    const double GT = (geps - s.T * gcv) * s.icv;
+    double qd = 0.0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const double J = s.rho * (s.Y[k] * corr - P.D[k] * GY[k]);
+        F[k] = J;
+        qd = fma(P.cp[k], J, qd);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[NK + i] = -tau[i];
+    const double tv = tau[0] * s.v[0] + tau[1] * s.v[1] + tau[2] * s.v[2];
+    F[NK + 3] = -tv - s.lam * GT + s.T * qd;
+}
+
 // F += F^v_d: the viscous flux of flux_visc added into F with fused
 // multiply-adds (the volume kernel's nodal flux F^c + F^v).
 template <int NK>
