@@ -15,6 +15,8 @@ A *problem* is a plain dict:
     fv    uint8 (n_elem,)          1 for FV sub-cell elements
     chain int (optional)           1: domains glued in order along x, conforming or mortar
                                    interfaces between them (Sec. 3.2.3)
+    fv_own_n int (optional)        1: an FV element of degree N has N+1 sub-cells per direction
+                                   (the per-element variant; n_fv unused; not with chain)
 """
 import ctypes as C
 import os
@@ -38,7 +40,7 @@ class _Problem(C.Structure):
         ("n_species", C.c_int), ("gamma", _dp), ("Rgas", _dp), ("mu", _dp), ("Pr", _dp),
         ("Dk", _dp), ("riemann", C.c_int), ("N", _i8p), ("fv", _u8p), ("nodes", C.c_int), ("split", C.c_int),
         ("sutherland", C.c_int), ("T_ref", C.c_double), ("S_sutherland", C.c_double), ("indicator_vars", C.c_int),
-        ("pp_limiter", C.c_int), ("pp_eps", C.c_double), ("chain_x", C.c_int),
+        ("pp_limiter", C.c_int), ("pp_eps", C.c_double), ("chain_x", C.c_int), ("fv_own_n", C.c_int),
     ]
 
 
@@ -75,6 +77,7 @@ def lib():
         L.oracle_vmap.argtypes = [C.c_int, C.c_int, _dp, C.c_int]
         L.oracle_dg2fv.argtypes = [C.c_int, C.c_int, _dp, C.c_int]
         L.oracle_fv2dg.argtypes = [C.c_int, C.c_int, _dp, C.c_int]
+        L.oracle_fv_overlap.argtypes = [C.c_int, C.c_int, _dp]
         L.oracle_leg_vandermonde.argtypes = [C.c_int, _dp, C.c_int]
         L.oracle_mortar.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, C.c_int]
         L.oracle_flux.argtypes = [P, _dp, _dp, C.c_int, _dp, _dp]
@@ -115,7 +118,7 @@ class _Bound:
             _ptr(self.N, _i8p), _ptr(self.fv, _u8p), int(prob.get("nodes", 0)), int(prob.get("split", 0)),
             int(prob.get("sutherland", 0)), float(prob.get("T_ref", 1.0)), float(prob.get("S_sutherland", 0.0)),
             int(prob.get("indicator_vars", 0)), int(prob.get("pp_limiter", 0)), float(prob.get("pp_eps", 1e-10)),
-            int(prob.get("chain", 0)))
+            int(prob.get("chain", 0)), int(prob.get("fv_own_n", 0)))
 
     @property
     def ref(self):
@@ -327,6 +330,13 @@ def mortar(N, half, proj=False, fv=False, nodes=0):
     n = N if fv else N + 1
     M = np.zeros((n, n))
     _check(lib().oracle_mortar(int(N), int(half), int(bool(proj)), int(bool(fv)), _ptr(M, _dp), int(nodes)), "mortar")
+    return M
+
+
+def fv_overlap(n_from, n_to):
+    """n_to x n_from piecewise-constant L2 projection between uniform sub-cell grids."""
+    M = np.zeros((n_to, n_from))
+    _check(lib().oracle_fv_overlap(n_from, n_to, _ptr(M, _dp)), "fv_overlap")
     return M
 
 

@@ -1,4 +1,5 @@
 // TEST INFRASTRUCTURE ONLY (see dgfv_oracle.h).  Reference-element operators.
+#include <algorithm>
 #include "basis.hpp"
 
 #include <cmath>
@@ -312,6 +313,21 @@ std::vector<double> mortar_proj_fv(int n_fv, int s) {
     std::vector<double> P((size_t)n_fv * n_fv, 0.0);
     for (int i = 0; i < n_fv; ++i) P[(size_t)((s * n_fv + i) / 2) * n_fv + i] = 0.5;
     return P;
+}
+
+std::vector<double> fv_overlap(int n_from, int n_to) {
+    // sub-cell i of n_to spans [i/n_to, (i+1)/n_to], cell j of n_from [j/n_from, (j+1)/n_from]
+    // (unit length): entry = |overlap| / |cell i|, with integer arithmetic on the
+    // common grid of n_from * n_to units (cell i: units [i n_from, (i+1) n_from))
+    if (n_from < 1 || n_to < 1) throw std::runtime_error("bad FV overlap");
+    std::vector<double> M((size_t)n_to * n_from, 0.0);
+    for (int i = 0; i < n_to; ++i)
+        for (int j = 0; j < n_from; ++j) {
+            const long lo = std::max((long)i * n_from, (long)j * n_to);
+            const long hi = std::min((long)(i + 1) * n_from, (long)(j + 1) * n_to);
+            if (hi > lo) M[(size_t)i * n_from + j] = (double)(hi - lo) / (double)n_from;
+        }
+    return M;
 }
 
 std::vector<double> leg_vandermonde_inv(int N, int kind) {

@@ -57,6 +57,10 @@ std::vector<double> mortar_proj(int N, int s, int kind = 0);
 // half s.
 std::vector<double> mortar_interp_fv(int n_fv, int s);
 std::vector<double> mortar_proj_fv(int n_fv, int s);
+// n_to x n_from: the piecewise-constant L2 projection between two uniform
+// sub-cell grids of one face direction (the per-element sub-cell variant's
+// FV/FV faces): entry (i, j) = |cell j of n_from inside cell i of n_to| / |cell i|.
+std::vector<double> fv_overlap(int n_from, int n_to);
 
 }  // namespace ora
 

@@ -68,7 +68,8 @@ struct Mortar {
 struct Ops {  // reference operators, built once per problem before any parallel loop
     std::map<int, Basis1D> basis;
     std::map<std::pair<int, int>, vector<double>> vm;  // (from,to) -> V^{from->to}
-    std::map<int, vector<double>> d2f, f2d;            // per DG degree
+    std::map<std::pair<int, int>, vector<double>> d2f, f2d;  // (DG degree, sub-cells per direction)
+    std::map<std::pair<int, int>, vector<double>> ov;         // (from, to) sub-cell overlap maps
     std::map<int, vector<double>> vleg_inv;
     // mortar maps per (DG degree, half): interpolation to the virtual small side, projection back
     std::map<std::pair<int, int>, vector<double>> mi, mp;
@@ -81,6 +82,7 @@ struct Problem {
     Phys ph;
     int V = 6;
     int nfv = 2;
+    bool fv_own = false;  // per-element variant: an FV element of degree N has N+1 sub-cells
     int riemann = 0;
     int nodes = 0;  // 0 Legendre-Gauss, 1 Legendre-Gauss-Lobatto
     int indicator_vars = 0;  // 0: p-adaptation on rho, FV on min(p, Y_k); 1: p-adaptation on p, FV on rho
@@ -109,6 +111,9 @@ Problem make_problem(const oracle_problem* p, bool need_ops = true) {
     }
     P.V = P.ph.V();
     P.nfv = p->n_fv;
+    P.fv_own = p->fv_own_n != 0;
+    if (p->fv_own_n < 0 || p->fv_own_n > 1 || (P.fv_own && p->chain_x))
+        throw std::runtime_error("bad per-element sub-cell flag (not with chained domains)");
     P.riemann = p->riemann;
     P.nodes = p->nodes;
     P.split = p->split;
@@ -215,7 +220,7 @@ Problem make_problem(const oracle_problem* p, bool need_ops = true) {
         E.N = p->N[e];
         E.fv = p->fv[e] != 0;
         if (E.N < 1 || E.N > 15) throw std::runtime_error("bad degree");
-        E.n = E.fv ? P.nfv : E.N + 1;
+        E.n = E.fv ? (P.fv_own ? E.N + 1 : P.nfv) : E.N + 1;
         E.off = P.size;
         P.size += (int64_t)P.V * E.n * E.n * E.n;
     }
@@ -227,9 +232,16 @@ Problem make_problem(const oracle_problem* p, bool need_ops = true) {
         for (int N : degs) {
             P.ops.basis[N] = make_basis(N, P.nodes);
             P.ops.vleg_inv[N] = leg_vandermonde_inv(N, P.nodes);
-            if (P.nfv >= N + 1) {
-                P.ops.d2f[N] = dg2fv(N, P.nfv, P.nodes);
-                P.ops.f2d[N] = fv2dg(N, P.nfv, P.nodes);
+            // DG <-> FV maps between degree N and every sub-cell count in use
+            // (global: n_fv; per element: N~+1 of every degree N~ present)
+            for (int M : degs) {
+                const int nf = P.fv_own ? M + 1 : P.nfv;
+                if (!P.fv_own && nf < N + 1) continue;
+                if (P.ops.d2f.count({N, nf})) continue;
+                P.ops.d2f[{N, nf}] = dg2fv(N, nf, P.nodes);
+                // V^{FV->DG} (a left inverse) only on grids of at least N+1 sub-cells,
+                // the only ones the coupling maps back from
+                if (nf >= N + 1) P.ops.f2d[{N, nf}] = fv2dg(N, nf, P.nodes);
             }
             for (int M : degs) P.ops.vm[{N, M}] = vmap(N, M, P.nodes);
             for (int h = 0; h < 2; ++h) {
@@ -241,13 +253,16 @@ Problem make_problem(const oracle_problem* p, bool need_ops = true) {
             P.ops.mi_fv[h] = mortar_interp_fv(P.nfv, h);
             P.ops.mp_fv[h] = mortar_proj_fv(P.nfv, h);
         }
+        if (P.fv_own)
+            for (int a : degs)
+                for (int b : degs) P.ops.ov[{a + 1, b + 1}] = fv_overlap(a + 1, b + 1);
         for (int n = 1; n <= 16; ++n) {
             vector<double> I((size_t)n * n, 0.0);
             for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
             P.ops.eye[n] = I;
         }
         for (auto& E : P.el)
-            if (E.fv && P.nfv < E.N + 1) throw std::runtime_error("n_fv < N+1 for an FV element");
+            if (E.fv && E.n < E.N + 1) throw std::runtime_error("n_fv < N+1 for an FV element");
     }
     return P;
 }
@@ -538,8 +553,10 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
             const bool fv_neighbour = fv_across(P, E, f);
             if (!E.fv && fv_neighbour && !parallel) set_phase<T>(2);
             if (!E.fv && fv_neighbour) {
-                const vector<double>& A = P.ops.d2f.at(E.N);
-                const int row = s ? P.nfv - 1 : 0;
+                // on the neighbour's sub-cell grid (per element: its own count)
+                const int nf = (P.fv_own && E.nb[f] >= 0) ? P.el[E.nb[f]].n : P.nfv;
+                const vector<double>& A = P.ops.d2f.at({E.N, nf});
+                const int row = s ? nf - 1 : 0;
                 vector<T> q((size_t)V * n * n, T(0.0));
                 for (int v = 0; v < V; ++v)
                     for (int b = 0; b < n; ++b)
@@ -549,7 +566,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
                                 t = t + T(A[row * n + m]) * u[(size_t)v * n * n * n + node_index(n, d, m, a, b)];
                             q[(size_t)v * n * n + a + n * b] = t;
                         }
-                W[e].face_layer[f] = map_face(q, V, n, P.nfv, A);
+                W[e].face_layer[f] = map_face(q, V, n, nf, A);
             }
             if (!parallel) set_phase<T>(1);
         }
@@ -561,7 +578,7 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
     for (int e = 0; e < nel; ++e) {
         const Elem& E = P.el[e];
         if (!E.fv) continue;
-        const int n = nfv, n3 = n * n * n;
+        const int n = E.n, n3 = n * n * n;
         const double l = 2.0 / n;  // sub-cell size in reference coordinates
         const T* u = U + E.off;
         // Reading: the value beyond the element boundary is the neighbour's
@@ -582,8 +599,18 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
         for (int f = 0; f < 6; ++f) {
             const int d = f / 2;
             if (E.mort[f] < 0) {
+                const Elem& Q = P.el[E.nb[f]];
+                if (Q.fv && Q.n != n) {
+                    // per-element sub-cells, an FV neighbour with another count: its
+                    // boundary layer by the overlap map onto this element's face grid;
+                    // the centre distance l/2 + (h_nb/h)(1/n_nb) in this element's
+                    // reference coordinates
+                    nbval[f] = map_face(layer(E.nb[f], f ^ 1), V, Q.n, n, P.ops.ov.at({Q.n, n}));
+                    nbdist[f] = l / 2 + (Q.h[d] / E.h[d]) / Q.n;
+                    continue;
+                }
                 nbval[f] = layer(E.nb[f], f ^ 1);
-                nbdist[f] = l / 2 * (1.0 + P.el[E.nb[f]].h[d] / E.h[d]);
+                nbdist[f] = l / 2 * (1.0 + Q.h[d] / E.h[d]);
                 continue;
             }
             const Mortar& M = P.mortars[E.mort[f]];
@@ -710,8 +737,14 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
         auto lift_with = [&](const vector<T>& mine, int N, bool ofv, int No, const vector<T>& other) {
             vector<T> us;
             if (ofv) {
-                // Sec. 3.2.2: FV side mapped to the DG element's polynomial data by V^{FV->DG}
-                vector<T> o = map_face(other, V, nfv, N + 1, P.ops.f2d.at(N));
+                // Sec. 3.2.2: FV side mapped to the DG element's polynomial data by
+                // V^{FV->DG}, on the finer of the two sides' sub-cell grids (the FV
+                // side's count, or N+1; per-element sub-cells may be coarser than
+                // N+1, and then enter by their overlaps)
+                const int nfo = P.fv_own ? No + 1 : nfv;
+                const int nc = std::max(nfo, N + 1);
+                vector<T> o = nc == nfo ? other : map_face(other, V, nfo, nc, P.ops.ov.at({nfo, nc}));
+                o = map_face(o, V, nc, N + 1, P.ops.f2d.at({N, nc}));
                 us.resize(mine.size());
                 for (size_t i = 0; i < mine.size(); ++i) us[i] = T(0.5) * (mine[i] + o[i]);
             } else {
@@ -863,21 +896,28 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
             uR = map_face_deg(P, *Rr.u, V, Rr.N, Nc);
             gR = map_face_deg(P, *Rr.g, 3 * V, Rr.N, Nc);
         } else {
-            nc = nfv;
-            if (L.fv) {
-                uL = *L.u;
-                gL = *L.g;
-            } else {
-                uL = map_face(*L.u, V, L.N + 1, nc, P.ops.d2f.at(L.N));
-                gL = map_face(*L.g, 3 * V, L.N + 1, nc, P.ops.d2f.at(L.N));
-            }
-            if (Rr.fv) {
-                uR = *Rr.u;
-                gR = *Rr.g;
-            } else {
-                uR = map_face(*Rr.u, V, Rr.N + 1, nc, P.ops.d2f.at(Rr.N));
-                gR = map_face(*Rr.g, 3 * V, Rr.N + 1, nc, P.ops.d2f.at(Rr.N));
-            }
+            // FV data on the finer of the two sides' sub-cell grids: an FV side's
+            // own count, a DG side's N+1 (with a global count n_fv >= N+1 this is
+            // n_fv).  A coarser FV side enters by the overlap map
+            // (piecewise-constant L2 projection) and gets its flux back by the
+            // overlap map the other way; a DG side by V^{DG->FV} / V^{FV->DG}.
+            const int nL = L.fv ? (P.fv_own ? L.N + 1 : nfv) : L.N + 1;
+            const int nR = Rr.fv ? (P.fv_own ? Rr.N + 1 : nfv) : Rr.N + 1;
+            nc = std::max(nL, nR);
+            auto to_common = [&](const Side& S, int ns, vector<T>& u, vector<T>& g) {
+                if (S.fv && ns == nc) {
+                    u = *S.u;
+                    g = *S.g;
+                } else if (S.fv) {
+                    u = map_face(*S.u, V, ns, nc, P.ops.ov.at({ns, nc}));
+                    g = map_face(*S.g, 3 * V, ns, nc, P.ops.ov.at({ns, nc}));
+                } else {
+                    u = map_face(*S.u, V, S.N + 1, nc, P.ops.d2f.at({S.N, nc}));
+                    g = map_face(*S.g, 3 * V, S.N + 1, nc, P.ops.d2f.at({S.N, nc}));
+                }
+            };
+            to_common(L, nL, uL, gL);
+            to_common(Rr, nR, uR, gR);
         }
         const int np = nc * nc;
         vector<T> Fc((size_t)V * np);
@@ -891,8 +931,11 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
         // back to each side's native representation (projection / V^{FV->DG})
         auto back = [&](const Side& S) -> vector<T> {
             if (!common_fv) return map_face_deg(P, Fc, V, nc - 1, S.N);
-            if (S.fv) return Fc;
-            return map_face(Fc, V, nc, S.N + 1, P.ops.f2d.at(S.N));
+            if (S.fv) {
+                const int ns = P.fv_own ? S.N + 1 : nfv;
+                return ns == nc ? Fc : map_face(Fc, V, nc, ns, P.ops.ov.at({nc, ns}));
+            }
+            return map_face(Fc, V, nc, S.N + 1, P.ops.f2d.at({S.N, nc}));
         };
         FL = back(L);
         FR = back(Rr);
@@ -1003,7 +1046,7 @@ void time_step(const Problem& P, const double* U, double cfl_c, double cfl_v, do
         const int n3 = E.n * E.n * E.n;
         const double fac = E.fv ? 1.0 : (2.0 * E.N + 1.0);
         double dx[3];
-        for (int d = 0; d < 3; ++d) dx[d] = E.fv ? E.h[d] / P.nfv : E.h[d];
+        for (int d = 0; d < 3; ++d) dx[d] = E.fv ? E.h[d] / E.n : E.h[d];
         for (int c = 0; c < n3; ++c) {
             double uc[MAXV];
             for (int v = 0; v < P.V; ++v) uc[v] = U[E.off + (int64_t)v * n3 + c];
@@ -1218,7 +1261,7 @@ void indicator(const Problem& P, const double* U, double* Ip, double* Ih) {
         const int n = E.N + 1, n3 = n * n * n;
         vector<double> u;
         if (E.fv) {
-            u = map_volume(U + E.off, P.V, P.nfv, n, P.ops.f2d.at(E.N));
+            u = map_volume(U + E.off, P.V, E.n, n, P.ops.f2d.at({E.N, E.n}));
         } else {
             u.assign(U + E.off, U + E.off + (int64_t)P.V * n3);
         }
@@ -1481,12 +1524,14 @@ int oracle_remap(const oracle_problem* p_old, const int8_t* N_new, const uint8_t
             vector<double> out;
             if (A.fv == B.fv && A.n == B.n) {
                 out.assign(src, src + (int64_t)V * A.n * A.n * A.n);
+            } else if (A.fv && B.fv) {
+                out = map_volume(src, V, A.n, B.n, fv_overlap(A.n, B.n));  // sub-cell overlaps
             } else if (!A.fv && !B.fv) {
                 out = map_volume(src, V, A.n, B.n, vmap(A.N, B.N, Po.nodes));      // V^{N->N~}
             } else if (!A.fv && B.fv) {
-                out = map_volume(src, V, A.n, B.n, dg2fv(A.N, Po.nfv, Po.nodes));  // V^{DG->FV}
+                out = map_volume(src, V, A.n, B.n, dg2fv(A.N, B.n, Po.nodes));  // V^{DG->FV}
             } else {
-                out = map_volume(src, V, A.n, B.n, fv2dg(B.N, Po.nfv, Po.nodes));  // V^{FV->DG}
+                out = map_volume(src, V, A.n, B.n, fv2dg(B.N, A.n, Po.nodes));  // V^{FV->DG}
             }
             std::copy(out.begin(), out.end(), dst);
         }
@@ -1513,6 +1558,9 @@ int oracle_vmap(int N_from, int N_to, double* M, int nodes) {
 }
 int oracle_dg2fv(int N, int n_fv, double* M, int nodes) {
     try { auto m = dg2fv(N, n_fv, nodes); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }
+}
+int oracle_fv_overlap(int n_from, int n_to, double* M) {
+    try { auto m = fv_overlap(n_from, n_to); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }
 }
 int oracle_fv2dg(int N, int n_fv, double* M, int nodes) {
     try { auto m = fv2dg(N, n_fv, nodes); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }

@@ -59,6 +59,11 @@ typedef struct {
                               z; all share the y and z extents, and neighbouring domains have
                               equal ny, nz (conforming) or twice as many in one or both of them
                               (non-conforming mortar interfaces of types 1-3, Sec. 3.2.3) */
+    int fv_own_n;          /* 0: every FV element has n_fv sub-cells per direction.  1: the
+                              per-element variant (Sec. 1, the common-DOF scheme of Sonntag and
+                              Munz): an FV element of degree N has N+1 sub-cells per direction,
+                              so switching between DG and FV keeps its DOF count; n_fv is then
+                              unused.  Not with chain_x.                    */
 } oracle_problem;
 
 /* 0 on success, negative on a malformed problem. */
@@ -148,6 +153,7 @@ int oracle_basis(int N, double* x, double* w, double* D, double* Dhat,
 int oracle_vmap(int N_from, int N_to, double* M, int nodes);   /* (N_to+1) x (N_from+1) */
 int oracle_dg2fv(int N, int n_fv, double* M, int nodes);       /* n_fv x (N+1)          */
 int oracle_fv2dg(int N, int n_fv, double* M, int nodes);       /* (N+1) x n_fv          */
+int oracle_fv_overlap(int n_from, int n_to, double* M);         /* n_to x n_from: sub-cell overlaps */
 int oracle_leg_vandermonde(int N, double* V, int nodes);       /* V[i][m] = Lhat_m(x_i) */
 /* Mortar operators of Sec. 3.2.3 for half s (0: [-1,0], 1: [0,1]): proj = 0 the
  * interpolation to the virtual small side, 1 the L2 projection back; fv = 0 on

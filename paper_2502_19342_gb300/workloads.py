@@ -40,7 +40,7 @@ def species_set(specs, mu=0.0, Pr=0.72, Sc=1.0, rho_ref=1.0):
     )
 
 
-def make_problem(domains, species, n_fv, N, fv=None, riemann=0, nodes=0, split=0, chain=0):
+def make_problem(domains, species, n_fv, N, fv=None, riemann=0, nodes=0, split=0, chain=0, fv_own_n=0):
     """domains: list of (dims(3), lo(3), hi(3)); species: dict from species_set;
     nodes 0 = Legendre-Gauss, 1 = Legendre-Gauss-Lobatto; split 1 = split-form
     volume integral (LGL only); chain 1 = the domains glued in order along x
@@ -52,7 +52,7 @@ def make_problem(domains, species, n_fv, N, fv=None, riemann=0, nodes=0, split=0
     N = np.broadcast_to(np.asarray(N, np.int8), (n_elem,)).copy()
     fv = np.zeros(n_elem, np.uint8) if fv is None else np.broadcast_to(np.asarray(fv, np.uint8), (n_elem,)).copy()
     p = dict(dims=dims, lo=lo, hi=hi, n_fv=int(n_fv), riemann=int(riemann), N=N, fv=fv, nodes=int(nodes),
-             split=int(split), chain=int(chain))
+             split=int(split), chain=int(chain), fv_own_n=int(fv_own_n))
     p.update({k: np.array(v, float) for k, v in species.items()})
     return p
 
@@ -78,7 +78,10 @@ def n_vars(prob):
 
 
 def points_per_dir(prob):
-    return np.where(prob["fv"] != 0, prob["n_fv"], prob["N"].astype(np.int64) + 1)
+    """Points per direction: N+1 for DG elements; for FV elements n_fv, or N+1
+    when every FV element has its own count (fv_own_n)."""
+    n_fv = prob["N"].astype(np.int64) + 1 if prob.get("fv_own_n", 0) else prob["n_fv"]
+    return np.where(prob["fv"] != 0, n_fv, prob["N"].astype(np.int64) + 1)
 
 
 def offsets(prob):

@@ -1,0 +1,133 @@
+"""Pins of the oracle's per-element sub-cell variant: an FV element of degree N
+has N+1 sub-cells per direction (the common-DOF scheme the paper sets itself
+apart from, Sec. 1), so switching an element between DG and FV keeps its
+number of DOFs.  Faces that touch FV data meet on the finer of the two sides'
+sub-cell grids (an FV side's own count, a DG side's N+1); a coarser FV side
+enters by the exact overlaps of its sub-cells (piecewise-constant L2
+projection).  The 1D brute-force comparison lives with the other brute-force
+checks (tests/test_oracle_rhs.py)."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2502_19342_gb300 import workloads as W
+
+
+def _overlap_exact(n_from, n_to):
+    M = np.zeros((n_to, n_from))
+    for i in range(n_to):
+        for j in range(n_from):
+            lo = max(Fraction(i, n_to), Fraction(j, n_from))
+            hi = min(Fraction(i + 1, n_to), Fraction(j + 1, n_from))
+            if hi > lo:
+                M[i, j] = float((hi - lo) / Fraction(1, n_to))
+    return M
+
+
+@pytest.mark.parametrize("n_from", range(2, 10))
+def test_overlap_maps_are_exact_fractions(oracle, n_from):
+    for n_to in range(2, 10):
+        M = oracle.fv_overlap(n_from, n_to)
+        np.testing.assert_array_equal(M, _overlap_exact(n_from, n_to))
+        # rows are averages (sum 1); the map back preserves integrals
+        np.testing.assert_allclose(M.sum(1), 1.0, rtol=0, atol=1e-15)
+
+
+def _problem(seed, nk=2, dims=(3, 3, 4), Nlo=1, Nhi=5, fv_frac=0.4, riemann=0, mu=2e-3, own=1, n_fv=2):
+    sp = W.species_set([W.AIR, W.HELIUM, W.CO2][:nk], mu=mu)
+    n = int(np.prod(dims))
+    N = W.random_degrees(n, Nlo, Nhi, seed)
+    fv = W.random_fv(n, fv_frac, seed)
+    return W.make_problem([(dims, (0, 0, 0), (1.0, 0.9, 1.2))], sp, n_fv=n_fv, N=N, fv=fv, riemann=riemann,
+                          fv_own_n=own)
+
+
+@pytest.mark.parametrize("riemann", [0, 1, 2])
+def test_uniform_degree_is_the_global_count_bit_for_bit(oracle, riemann):
+    """With one degree N everywhere every FV element has N+1 sub-cells, which is
+    the global variant with n_fv = N+1: R, the time step and the indicator agree
+    bit for bit."""
+    p_own = _problem(3, Nlo=3, Nhi=3, riemann=riemann)
+    p_glob = dict(p_own, fv_own_n=0, n_fv=4)
+    U = W.smooth_random_state(p_glob, 3, amp=0.1)
+    np.testing.assert_array_equal(oracle.eval_rhs(p_own, U), oracle.eval_rhs(p_glob, U))
+    np.testing.assert_array_equal(oracle.dt(p_own, U, 0.5, 0.5), oracle.dt(p_glob, U, 0.5, 0.5))
+    a, b = oracle.indicator(p_own, U), oracle.indicator(p_glob, U)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("seed,nk,riemann", [(1, 2, 0), (2, 3, 1), (3, 2, 2), (4, 1, 0)])
+def test_free_stream_with_per_element_sub_cells(oracle, seed, nk, riemann):
+    """R(const) = 0 to round-off on random degrees 1..6 and FV elements: FV/FV
+    faces between unequal counts and DG/FV faces on either side's grid."""
+    prob = _problem(seed, nk=nk, Nlo=1, Nhi=6, riemann=riemann)
+    rho = [0.5, 0.3, 0.2][:nk]
+    U = W.constant_state(prob, rho, (0.7, -0.4, 0.25), 1.3)
+    R = oracle.eval_rhs(prob, U)
+    assert np.abs(R).max() < 2e-12, np.abs(R).max()
+
+
+def _weights(prob):
+    """Quadrature weight x Jacobian of every DOF (DG: Gauss weights; FV: sub-cell volume)."""
+    off, size = W.offsets(prob)
+    _, _, _, h = W.element_index(prob)
+    V = W.n_vars(prob)
+    n = W.points_per_dir(prob)
+    wts = np.zeros(size)
+    for e in range(W.n_elements(prob)):
+        m = int(n[e])
+        if prob["fv"][e]:
+            w3 = np.full(m ** 3, (2.0 / m) ** 3)
+        else:
+            w = np.polynomial.legendre.leggauss(m)[1]
+            w3 = np.einsum("k,j,i->kji", w, w, w).ravel()
+        J = np.prod(h[e]) / 8.0
+        wts[off[e]:off[e] + V * m ** 3] = np.tile(w3 * J, V)
+    return wts
+
+
+@pytest.mark.parametrize("seed,nk,riemann", [(5, 2, 0), (6, 3, 1), (7, 2, 2)])
+def test_conservation_with_per_element_sub_cells(oracle, seed, nk, riemann):
+    """Every conserved variable's integral of R vanishes on the periodic mesh:
+    the overlap maps and the DG/FV maps on the common grid keep face
+    integrals."""
+    prob = _problem(seed, nk=nk, Nlo=1, Nhi=6, riemann=riemann)
+    U = W.smooth_random_state(prob, seed, amp=0.15)
+    R = oracle.eval_rhs(prob, U)
+    wts = _weights(prob)
+    off, _ = W.offsets(prob)
+    V = W.n_vars(prob)
+    n = W.points_per_dir(prob)
+    for v in range(V):
+        tot, mag = 0.0, 0.0
+        for e in range(W.n_elements(prob)):
+            m3 = int(n[e]) ** 3
+            sl = slice(off[e] + v * m3, off[e] + (v + 1) * m3)
+            tot += float(np.dot(wts[sl], R[sl]))
+            mag += float(np.dot(wts[sl], np.abs(R[sl])))
+        assert abs(tot) <= 1e-13 * mag, (v, tot, mag)
+
+
+def test_switching_keeps_the_dofs_and_round_trips(oracle):
+    """DG -> FV -> DG per element with N+1 sub-cells: the state size does not
+    change, and V^{FV->DG} V^{DG->FV} = I (a square invertible map) returns the
+    DG state."""
+    prob = _problem(8, Nlo=1, Nhi=7, fv_frac=0.0)
+    U = W.smooth_random_state(prob, 8, amp=0.2)
+    rng = np.random.default_rng(8)
+    sel = (rng.random(len(prob["N"])) < 0.5).astype(np.uint8)
+    p_fv = dict(prob, fv=sel)
+    U_fv = oracle.remap(prob, prob["N"], sel, U)
+    assert U_fv.size == U.size == oracle.state_size(p_fv)
+    U_back = oracle.remap(p_fv, prob["N"], np.zeros_like(sel), U_fv)
+    np.testing.assert_allclose(U_back, U, rtol=0, atol=1e-13 * np.abs(U).max())
+
+
+def test_rejected_with_chained_domains(oracle):
+    sp = W.species_set([W.AIR, W.HELIUM], mu=1e-3)
+    doms = W.chain_domains([(2, 2, 2, 0.5), (2, 2, 2, 0.5)])
+    prob = W.make_problem(doms, sp, n_fv=4, N=2, chain=1, fv_own_n=1)
+    with pytest.raises(RuntimeError):
+        oracle.state_size(prob)

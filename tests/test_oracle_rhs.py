@@ -180,13 +180,14 @@ def _minmod(a, b):
     return np.where(a * b <= 0, 0.0, np.where(np.abs(a) <= np.abs(b), a, b))
 
 
-def _rhs_1d(oracle, prob, chain, u, h, axis):
+def _rhs_1d(oracle, prob, chain, u, h, axis, own=False):
     """Brute-force 1D hybrid DG/FV operator on a periodic chain of elements.
-    chain[e] = (N, fv); u[e] is (V, n) nodal values / cell means along `axis`."""
+    chain[e] = (N, fv); u[e] is (V, n) nodal values / cell means along `axis`.
+    own: an FV element of degree N has N+1 sub-cells (else n_fv); the centre
+    distance to an FV neighbour with another count is 1/n + 1/n_nb."""
     K = len(chain)
     V = len(prob["gamma"]) + 4
-    nfv = int(prob["n_fv"])
-    l = 2.0 / nfv
+    nf_of = [(N + 1 if own else int(prob["n_fv"])) for N, _ in chain]
     B = {}
     for N, fv in chain:
         if not fv and N not in B:
@@ -214,10 +215,13 @@ def _rhs_1d(oracle, prob, chain, u, h, axis):
         if not fv:
             continue
         em, ep = (e - 1) % K, (e + 1) % K
+        nfv = nf_of[e]
+        l = 2.0 / nfv
         # neighbour sub-cell mean next to the face: FV cell, or V^{DG->FV} of the DG solution
         wl = right[em] if chain[em][1] else (oracle.dg2fv(chain[em][0], nfv) @ u[em].T)[-1]
         wr = left[ep] if chain[ep][1] else (oracle.dg2fv(chain[ep][0], nfv) @ u[ep].T)[0]
-        dl = dr = l
+        dl = l if not chain[em][1] or nf_of[em] == nfv else 1.0 / nfv + 1.0 / nf_of[em]
+        dr = l if not chain[ep][1] or nf_of[ep] == nfv else 1.0 / nfv + 1.0 / nf_of[ep]
         ext = np.concatenate([wl[:, None], u[e], wr[:, None]], axis=1)
         dist_l = np.array([dl] + [l] * (nfv - 1))
         dist_r = np.array([l] * (nfv - 1) + [dr])
@@ -258,13 +262,13 @@ def _rhs_1d(oracle, prob, chain, u, h, axis):
         uR = rec_l[ep] if chain[ep][1] else left[ep]
         F = oracle.riemann(prob, uL, uR, axis) + 0.5 * (vflux(uL, g_r[e]) + vflux(uR, g_l[ep]))
         if fv:
-            div[e][:, -1] += nfv / h * F
+            div[e][:, -1] += nf_of[e] / h * F
         else:
             b = B[N]
             div[e] += (2.0 / h) * np.outer(F, b["lp"] / b["w"])
         N2, fv2 = chain[ep]
         if fv2:
-            div[ep][:, 0] -= nfv / h * F
+            div[ep][:, 0] -= nf_of[ep] / h * F
         else:
             b = B[N2]
             div[ep] -= (2.0 / h) * np.outer(F, b["lm"] / b["w"])
@@ -327,6 +331,54 @@ def test_matches_brute_force_1d_code(oracle, axis, riemann):
             ref = np.broadcast_to(r1[:, None, :, None], r3[e].shape)
         else:
             ref = np.broadcast_to(r1[:, :, None, None], r3[e].shape)
+        np.testing.assert_allclose(r3[e], ref, atol=1e-11 * scale, rtol=0)
+
+
+@pytest.mark.parametrize("axis", [0, 2])
+@pytest.mark.parametrize("riemann", [0, 1])
+def test_per_element_sub_cells_match_brute_force_1d_code(oracle, axis, riemann):
+    """The per-element sub-cell variant (an FV element of degree N has N+1
+    sub-cells, Sec. 1) with data along one axis: FV/FV faces between unequal
+    counts (centre distance 1/n + 1/n_nb), FV elements coarser and finer than
+    their DG neighbours' N+1, against the 1D brute-force code."""
+    chain = [(3, 0), (2, 1), (5, 1), (4, 0), (1, 1), (2, 1), (6, 0), (3, 1)]
+    K = len(chain)
+    sp = W.species_set([W.AIR, W.HELIUM], mu=3e-3)
+    dims = [1, 1, 1]
+    dims[axis] = K
+    hi = [0.7, 0.7, 0.7]
+    hi[axis] = 1.6
+    N = np.array([c[0] for c in chain], np.int8)
+    fv = np.array([c[1] for c in chain], np.uint8)
+    prob = W.make_problem([(tuple(dims), (0, 0, 0), tuple(hi))], sp, n_fv=2, N=N, fv=fv, riemann=riemann,
+                          fv_own_n=1)
+    L = hi[axis]
+
+    def fn(x, y, z):
+        s = (x, y, z)[axis] / L
+        Y1 = 0.5 + 0.3 * np.sin(2 * np.pi * s)
+        rho = 1.0 + 0.2 * np.cos(2 * np.pi * s + 0.3)
+        v = [0.1 + 0 * s, -0.2 + 0 * s, 0.15 + 0 * s]
+        v[axis] = 0.4 + 0.2 * np.sin(2 * np.pi * s + 1.0)
+        v[(axis + 1) % 3] = 0.3 * np.cos(2 * np.pi * s)
+        return [rho * Y1, rho * (1 - Y1)], v, 1.0 + 0.1 * np.sin(2 * np.pi * s + 2.0)
+
+    U = W.build_state(prob, fn)
+    R = oracle.eval_rhs(prob, U)
+    off, _ = W.offsets(prob)
+    V = 6
+    h = L / K
+    u1, r3 = [], []
+    for e, (Ne, f) in enumerate(chain):
+        n = Ne + 1
+        blk = U[off[e]:off[e] + V * n ** 3].reshape(V, n, n, n)
+        r3.append(R[off[e]:off[e] + V * n ** 3].reshape(V, n, n, n))
+        u1.append(blk[:, 0, 0, :] if axis == 0 else blk[:, :, 0, 0])
+    R1 = _rhs_1d(oracle, prob, chain, u1, h, axis, own=True)
+    scale = max(np.abs(r).max() for r in R1)
+    for e in range(K):
+        r1 = R1[e]
+        ref = np.broadcast_to(r1[:, None, None, :] if axis == 0 else r1[:, :, None, None], r3[e].shape)
         np.testing.assert_allclose(r3[e], ref, atol=1e-11 * scale, rtol=0)
 
 
