@@ -235,6 +235,40 @@ std::vector<double> vmap(int N_from, int N_to, int kind) {
 
 std::vector<double> dg2fv(int N, int n_fv, int kind) { return to_double(dg2fv_ld(N, n_fv, kind)); }
 
+std::vector<double> fv2dg_l2(int N, int n_fv, int kind) {
+    // L2 projection onto degree N of the piecewise constant given by n_fv sub-cell
+    // values on [-1, 1]: M c = b with the exact mass matrix M_ij = int l_i l_j and
+    // b_i(s) = int over sub-cell s of l_i, by Gauss rules exact for the integrands.
+    const int n = N + 1;
+    std::vector<ld> x = nodes_ld(N, kind), q, w;
+    gauss_legendre(n + 1, q, w);  // exact to degree 2N+1
+    std::vector<ld> M(n * n, 0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            ld sum = 0;
+            for (int k = 0; k < n + 1; ++k) sum += w[k] * lagrange(x, i, q[k]) * lagrange(x, j, q[k]);
+            M[i * n + j] = sum;
+        }
+    std::vector<ld> Minv = invert(M, n), Bm(n * n_fv, 0);
+    const ld l = (ld)2 / n_fv;
+    for (int s = 0; s < n_fv; ++s) {
+        const ld a = -1 + s * l;
+        for (int i = 0; i < n; ++i) {
+            ld sum = 0;
+            for (int k = 0; k < n + 1; ++k) sum += w[k] * lagrange(x, i, a + l / 2 * (q[k] + 1));
+            Bm[i * n_fv + s] = sum * l / 2;
+        }
+    }
+    std::vector<ld> P(n * n_fv, 0);
+    for (int i = 0; i < n; ++i)
+        for (int s = 0; s < n_fv; ++s) {
+            ld sum = 0;
+            for (int k = 0; k < n; ++k) sum += Minv[i * n + k] * Bm[k * n_fv + s];
+            P[i * n_fv + s] = sum;
+        }
+    return to_double(P);
+}
+
 std::vector<double> fv2dg(int N, int n_fv, int kind) {
     // Pseudo-inverse through the normal equations, (A^T A)^{-1} A^T; A has full
     // column rank whenever n_fv >= N+1.

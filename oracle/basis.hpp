@@ -61,6 +61,10 @@ std::vector<double> mortar_proj_fv(int n_fv, int s);
 // sub-cell grids of one face direction (the per-element sub-cell variant's
 // FV/FV faces): entry (i, j) = |cell j of n_from inside cell i of n_to| / |cell i|.
 std::vector<double> fv_overlap(int n_from, int n_to);
+// (N+1) x n_fv: L2 projection onto degree N of n_fv sub-cell values (a piecewise
+// constant); the FV -> DG map of the per-element sub-cell variant where n_fv < N+1
+// (the pseudo-inverse of a non-injective V^{DG->FV} would not keep constants).
+std::vector<double> fv2dg_l2(int N, int n_fv, int kind = 0);
 
 }  // namespace ora
 

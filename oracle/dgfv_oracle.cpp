@@ -239,9 +239,11 @@ Problem make_problem(const oracle_problem* p, bool need_ops = true) {
                 if (!P.fv_own && nf < N + 1) continue;
                 if (P.ops.d2f.count({N, nf})) continue;
                 P.ops.d2f[{N, nf}] = dg2fv(N, nf, P.nodes);
-                // V^{FV->DG} (a left inverse) only on grids of at least N+1 sub-cells,
-                // the only ones the coupling maps back from
-                if (nf >= N + 1) P.ops.f2d[{N, nf}] = fv2dg(N, nf, P.nodes);
+                // V^{FV->DG}: the pseudo-inverse (a left inverse) on grids of at least
+                // N+1 sub-cells; on coarser ones (per-element sub-cells only) the L2
+                // projection of the piecewise constant, which keeps constants and
+                // face integrals
+                P.ops.f2d[{N, nf}] = nf >= N + 1 ? fv2dg(N, nf, P.nodes) : fv2dg_l2(N, nf, P.nodes);
             }
             for (int M : degs) P.ops.vm[{N, M}] = vmap(N, M, P.nodes);
             for (int h = 0; h < 2; ++h) {
@@ -737,14 +739,9 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
         auto lift_with = [&](const vector<T>& mine, int N, bool ofv, int No, const vector<T>& other) {
             vector<T> us;
             if (ofv) {
-                // Sec. 3.2.2: FV side mapped to the DG element's polynomial data by
-                // V^{FV->DG}, on the finer of the two sides' sub-cell grids (the FV
-                // side's count, or N+1; per-element sub-cells may be coarser than
-                // N+1, and then enter by their overlaps)
+                // Sec. 3.2.2: FV side mapped to the DG element's polynomial data by V^{FV->DG}
                 const int nfo = P.fv_own ? No + 1 : nfv;
-                const int nc = std::max(nfo, N + 1);
-                vector<T> o = nc == nfo ? other : map_face(other, V, nfo, nc, P.ops.ov.at({nfo, nc}));
-                o = map_face(o, V, nc, N + 1, P.ops.f2d.at({N, nc}));
+                vector<T> o = map_face(other, V, nfo, N + 1, P.ops.f2d.at({N, nfo}));
                 us.resize(mine.size());
                 for (size_t i = 0; i < mine.size(); ++i) us[i] = T(0.5) * (mine[i] + o[i]);
             } else {
@@ -896,13 +893,13 @@ void eval_rhs_t(const Problem& P, const T* U, T* R, bool parallel = true) {
             uR = map_face_deg(P, *Rr.u, V, Rr.N, Nc);
             gR = map_face_deg(P, *Rr.g, 3 * V, Rr.N, Nc);
         } else {
-            // FV data on the finer of the two sides' sub-cell grids: an FV side's
-            // own count, a DG side's N+1 (with a global count n_fv >= N+1 this is
-            // n_fv).  A coarser FV side enters by the overlap map
-            // (piecewise-constant L2 projection) and gets its flux back by the
-            // overlap map the other way; a DG side by V^{DG->FV} / V^{FV->DG}.
-            const int nL = L.fv ? (P.fv_own ? L.N + 1 : nfv) : L.N + 1;
-            const int nR = Rr.fv ? (P.fv_own ? Rr.N + 1 : nfv) : Rr.N + 1;
+            // FV data (Sec. 3.2.1): a DG/FV face on the FV side's sub-cell grid,
+            // the DG side by V^{DG->FV} and back by V^{FV->DG}; two FV sides with
+            // different counts (per-element sub-cells) on the finer grid, the
+            // coarser side by the overlap map (piecewise-constant L2 projection)
+            // and back by the overlap map the other way
+            const int nL = L.fv ? (P.fv_own ? L.N + 1 : nfv) : 0;
+            const int nR = Rr.fv ? (P.fv_own ? Rr.N + 1 : nfv) : 0;
             nc = std::max(nL, nR);
             auto to_common = [&](const Side& S, int ns, vector<T>& u, vector<T>& g) {
                 if (S.fv && ns == nc) {
@@ -1563,7 +1560,11 @@ int oracle_fv_overlap(int n_from, int n_to, double* M) {
     try { auto m = fv_overlap(n_from, n_to); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }
 }
 int oracle_fv2dg(int N, int n_fv, double* M, int nodes) {
-    try { auto m = fv2dg(N, n_fv, nodes); std::copy(m.begin(), m.end(), M); return 0; } catch (...) { return -1; }
+    try {
+        auto m = n_fv >= N + 1 ? fv2dg(N, n_fv, nodes) : fv2dg_l2(N, n_fv, nodes);
+        std::copy(m.begin(), m.end(), M);
+        return 0;
+    } catch (...) { return -1; }
 }
 int oracle_mortar(int N, int s, int proj, int fv, double* M, int nodes) {
     try {

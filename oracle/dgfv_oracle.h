@@ -152,7 +152,9 @@ int oracle_basis(int N, double* x, double* w, double* D, double* Dhat,
                  double* l_minus, double* l_plus, int nodes);
 int oracle_vmap(int N_from, int N_to, double* M, int nodes);   /* (N_to+1) x (N_from+1) */
 int oracle_dg2fv(int N, int n_fv, double* M, int nodes);       /* n_fv x (N+1)          */
-int oracle_fv2dg(int N, int n_fv, double* M, int nodes);       /* (N+1) x n_fv          */
+int oracle_fv2dg(int N, int n_fv, double* M, int nodes);       /* (N+1) x n_fv: pseudo-inverse of
+                                                                   V^{DG->FV} (n_fv >= N+1), else the
+                                                                   L2 projection of the sub-cell values */
 int oracle_fv_overlap(int n_from, int n_to, double* M);         /* n_to x n_from: sub-cell overlaps */
 int oracle_leg_vandermonde(int N, double* V, int nodes);       /* V[i][m] = Lhat_m(x_i) */
 /* Mortar operators of Sec. 3.2.3 for half s (0: [-1,0], 1: [0,1]): proj = 0 the
