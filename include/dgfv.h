@@ -93,7 +93,16 @@ typedef struct {
     int N_min, N_max;     /* degree bounds, 1 <= N_min <= N_max <= 7    */
     int N_fv;             /* FV sub-cells per direction, N_max+1 <= N_fv <= 9; the
                              sub-cells of one FV element must fit in one CTA's
-                             shared memory (N_fv = 9: at most 2 species) */
+                             shared memory (N_fv = 9: at most 2 species).
+                             N_fv = 0: per-element counts, an FV element of degree
+                             N has N+1 sub-cells per direction, so switching between
+                             DG and FV keeps its DOFs (the common-DOF scheme the
+                             paper contrasts with its own in Sec. 1).  A DG/FV face
+                             then couples on the FV side's grid (V^{FV->DG}: the L2
+                             projection where that grid has fewer than N+1
+                             sub-cells); FV/FV faces of unequal counts on the finer
+                             grid, by sub-cell overlaps.  Not with chain_x = 1, and
+                             not with the adjoint calls (DGFV_ERR_ARG). */
     int chain_x;          /* 0 or 1, see above                          */
 } dgfv_mesh_desc;
 
@@ -317,11 +326,13 @@ void dgfv_destroy(dgfv_ctx* ctx);
 
 /* Operator bank entries, for checks against an independent computation:
  * which = 0 nodes, 1 weights, 2 Dhat (n x n), 3 l(-1), 4 l(+1),
- * 5 V^{N->M} ((M+1) x (N+1)), 6 V^{DG->FV} (N_fv x (N+1)),
- * 7 V^{FV->DG} ((N+1) x N_fv), 8 inverse Legendre Vandermonde, 9 D (n x n),
+ * 5 V^{N->M} ((M+1) x (N+1)), 6 V^{DG->FV} (N_fv x (N+1); M >= 1: to M
+ * sub-cells), 7 V^{FV->DG} ((N+1) x N_fv; M >= 1: from M sub-cells, the L2
+ * projection where M < N+1), 8 inverse Legendre Vandermonde, 9 D (n x n),
  * 10 / 11 mortar interpolation to / L2 projection from the virtual small side
  * of half M (0 or 1) ((N+1) x (N+1), Sec. 3.2.3), 12 / 13 the same on the
- * N_fv sub-cells (N_fv x N_fv), all on the context's node family.
+ * N_fv sub-cells (N_fv x N_fv), 14 the sub-cell overlaps from N+1 to M
+ * sub-cells per direction (M x (N+1)), all on the context's node family.
  * Copies the row-major matrix to host memory `out` of `cap` doubles and
  * returns the number of entries, or a negative status. */
 int64_t dgfv_bank_entry(dgfv_ctx* ctx, int which, int N, int M, double* out, int64_t cap);

@@ -121,8 +121,8 @@ __global__ void __launch_bounds__(128) k_adj_mixed_in(Params P, AdjBuffers A, Fa
     const int em = m.mapL ? m.eL : m.eR, fm = m.mapL ? 2 * d + 1 : 2 * d, n = P.t.n[em], n2 = n * n;
     const int ed = m.mapL ? m.eR : m.eL, fd = m.mapL ? 2 * d : 2 * d + 1, nc2 = m.nc * m.nc;
     const int64_t slot = P.t.fo[em] + (int64_t)fm * n2, sd = P.t.fo[ed] + (int64_t)fd * nc2;
-    const double* Min = B(P, m.cfv ? P.bi.d2f[n] : P.bi.vm[n][m.nc]);
-    const double* Mout = B(P, m.cfv ? P.bi.f2d[n] : P.bi.vm[m.nc][n]);
+    const double* Min = B(P, m.cfv ? P.bi.d2f[n][m.nc] : P.bi.vm[n][m.nc]);
+    const double* Mout = B(P, m.cfv ? P.bi.f2d[n][m.nc] : P.bi.vm[m.nc][n]);
     double* in = Sin + mpt[k] * 4 * V;
     face_map(P.b.fu + slot * V, n, in, m.nc, Min, V, tmp);
     if (P.ph.viscous) face_map(P.b.fg + slot * 3 * V, n, in + V * nc2, m.nc, Min, 3 * V, tmp);
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(128) k_adj_mixed_out(Params P, AdjBuffers A, F
     const MixedFace m = mixed_face(P, Fc, fid);
     const int em = m.mapL ? m.eL : m.eR, fm = m.mapL ? 2 * d + 1 : 2 * d, n = P.t.n[em], n2 = n * n;
     const int64_t slot = P.t.fo[em] + (int64_t)fm * n2;
-    const double* Min = B(P, m.cfv ? P.bi.d2f[n] : P.bi.vm[n][m.nc]);
+    const double* Min = B(P, m.cfv ? P.bi.d2f[n][m.nc] : P.bi.vm[n][m.nc]);
     const double* in = Sin + mpt[k] * 4 * V;
     face_map_t(in, m.nc, A.ubar + slot * V, n, Min, V, tmp);
     if (P.ph.viscous) face_map_t(in + V * m.nc * m.nc, m.nc, A.gbar + slot * 3 * V, n, Min, 3 * V, tmp);
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(64) k_adj_lift(Params P, AdjBuffers A, Faces F
             sA[i] = a;
         }
         __syncthreads();
-        face_map_t(sA, nD, sB, nF, B(P, P.bi.f2d[nD]), V, sT);
+        face_map_t(sA, nD, sB, nF, B(P, P.bi.f2d[nD][nF]), V, sT);
         for (int i = threadIdx.x; i < V * nF * nF; i += blockDim.x) A.ubar[sF + i] += sB[i];
         return;
     }

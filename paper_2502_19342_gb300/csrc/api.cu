@@ -80,6 +80,7 @@ struct dgfv_ctx {
     DevPhys ph{};
     dgfv_opts opts{};
     int N_min = 1, N_max = 1, nfv = 2;
+    bool fv_own = false;  // per-element sub-cell counts: an FV element of degree N has N+1
     int n_elem = 0, n_faces = 0;
     std::vector<int32_t> nb;
     std::vector<double> rh;
@@ -242,8 +243,13 @@ int build_bank(dgfv_ctx* c) {
         c->bi.lhm[n] = put(b.lhm);
         c->bi.lhp[n] = put(b.lhp);
         c->bi.vinv[n] = put(b.vinv);
-        c->bi.d2f[n] = put(make_dg2fv(n, c->nfv, kind));
-        c->bi.f2d[n] = put(make_fv2dg(n, c->nfv, kind));
+        // V^{DG->FV} / V^{FV->DG} to the global sub-cell count, or (per-element
+        // counts) to every count an FV element can have
+        for (int m = c->fv_own ? c->N_min + 1 : c->nfv; m <= (c->fv_own ? c->N_max + 1 : c->nfv); ++m) {
+            c->bi.d2f[n][m] = put(make_dg2fv(n, m, kind));
+            c->bi.f2d[n][m] = put(m >= n ? make_fv2dg(n, m, kind) : make_fv2dg_l2(n, m, kind));
+            if (c->fv_own) c->bi.ov[n][m] = put(make_fv_overlap(n, m));
+        }
         for (int m = c->N_min + 1; m <= c->N_max + 1; ++m) c->bi.vm[n][m] = put(make_vmap(n, m, kind));
         for (int h = 0; h < 2; ++h) {
             c->bi.mi[n][h] = put(make_mortar(n, h, false, kind));
@@ -328,7 +334,7 @@ int apply_layout(dgfv_ctx* c) {
     int64_t so = 0, fpo = 0;
     c->n_fv_elems = 0;
     for (int e = 0; e < ne; ++e) {
-        const int n = c->fv[e] ? c->nfv : c->N[e] + 1;
+        const int n = (c->fv[e] && !c->fv_own) ? c->nfv : c->N[e] + 1;
         c->npts[e] = (uint8_t)n;
         c->off[e] = so;
         c->fo[e] = fpo;
@@ -393,7 +399,7 @@ int apply_layout(dgfv_ctx* c) {
     std::vector<int32_t> conf_by[3][MAXP + 1];
     for (int f = 0; f < c->n_faces; ++f) {
         const int L = c->faceL[f], R = c->faceR[f];
-        const bool same = (c->fv[L] && c->fv[R]) || (!c->fv[L] && !c->fv[R] && c->npts[L] == c->npts[R]);
+        const bool same = c->fv[L] == c->fv[R] && c->npts[L] == c->npts[R];
         if (same)
             conf_by[c->faceD[f]][c->npts[L]].push_back(f);
         else
@@ -440,7 +446,9 @@ int apply_layout(dgfv_ctx* c) {
         std::vector<int32_t> by[3][MAXP + 1];
         for (int32_t f : c->flux.ids) {
             const int L = c->faceL[f], R = c->faceR[f];
-            const int nc = (c->fv[L] || c->fv[R]) ? c->nfv : std::max<int>(c->npts[L], c->npts[R]);
+            // as mixed_face: DG/FV on the FV side's sub-cells, else the larger count
+            const int nc = (c->fv[L] != c->fv[R]) ? (c->fv[L] ? c->npts[L] : c->npts[R])
+                                                  : std::max<int>(c->npts[L], c->npts[R]);
             by[c->faceD[f]][nc].push_back(f);
         }
         int64_t pts = 0;
@@ -705,9 +713,14 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     *out = nullptr;
     if (mesh->n_domains < 1 || !mesh->dims || !mesh->lo || !mesh->hi) return DGFV_ERR_ARG;
     if (mesh->N_min < 1 || mesh->N_max > 7 || mesh->N_min > mesh->N_max) return DGFV_ERR_ARG;
-    if (mesh->N_fv < mesh->N_max + 1 || mesh->N_fv > MAXP) return DGFV_ERR_ARG;
+    // N_fv = 0: per-element sub-cell counts (an FV element of degree N has N+1);
+    // not with chained domains (mortars)
+    const bool fv_own = mesh->N_fv == 0;
+    if (fv_own && mesh->chain_x) return DGFV_ERR_ARG;
+    const int nfv_max = fv_own ? mesh->N_max + 1 : mesh->N_fv;
+    if (!fv_own && (mesh->N_fv < mesh->N_max + 1 || mesh->N_fv > MAXP)) return DGFV_ERR_ARG;
     // one FV element's sub-cell data must fit in the shared memory of one CTA
-    if (fv_smem_bytes(phys->n_species, mesh->N_fv) > 227 * 1024) return DGFV_ERR_ARG;
+    if (fv_smem_bytes(phys->n_species, nfv_max) > 227 * 1024) return DGFV_ERR_ARG;
     if (phys->n_species < 1 || phys->n_species > 3) return DGFV_ERR_ARG;
     int64_t ne = 0;
     for (int d = 0; d < mesh->n_domains; ++d) {
@@ -729,7 +742,8 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     c->opts = *opts;
     c->N_min = mesh->N_min;
     c->N_max = mesh->N_max;
-    c->nfv = mesh->N_fv;
+    c->nfv = nfv_max;  // the largest sub-cell count (capacities, shared memory)
+    c->fv_own = fv_own;
     c->ph.nk = c->nk;
     if (opts->riemann < DGFV_RIEMANN_LLF || opts->riemann > DGFV_RIEMANN_HYBRID) return cleanup(DGFV_ERR_ARG);
     if (opts->nodes < 0 || opts->nodes > 1 || opts->split_form < 0 || opts->split_form > 1 ||
@@ -1026,6 +1040,7 @@ int dgfv_compute_dt_noalloc(dgfv_ctx* c, const double* d_U, double* d_out3, void
 }
 
 static int adj_prepare(dgfv_ctx* c) {
+    if (c->fv_own) return fail(c, DGFV_ERR_ARG, "the adjoint does not support per-element sub-cell counts");
     if (c->adj_ready) return DGFV_OK;
     TRY(dalloc(c, &c->d_fbar, c->cap_fpts * c->V));
     TRY(dalloc(c, &c->d_ubar, c->cap_fpts * c->V));
@@ -1447,8 +1462,18 @@ int64_t dgfv_bank_entry(dgfv_ctx* c, int which, int N, int M, double* out, int64
                 if (M < c->N_min || M > c->N_max) return DGFV_ERR_ARG;
                 v = make_vmap(n, m, kind);
                 break;
-            case 6: v = make_dg2fv(n, c->nfv, kind); break;
-            case 7: v = make_fv2dg(n, c->nfv, kind); break;
+            case 6:  // V^{DG->FV} to the context's sub-cell count, or to M sub-cells (M >= 1)
+                v = make_dg2fv(n, M >= 1 ? M : c->nfv, kind);
+                break;
+            case 7: {  // V^{FV->DG} from the context's sub-cell count, or from M sub-cells
+                const int nf = M >= 1 ? M : c->nfv;
+                v = nf >= n ? make_fv2dg(n, nf, kind) : make_fv2dg_l2(n, nf, kind);
+                break;
+            }
+            case 14:  // sub-cell overlaps from N+1 to M sub-cells per direction
+                if (M < 1 || M > MAXP) return DGFV_ERR_ARG;
+                v = make_fv_overlap(n, M);
+                break;
             case 8: v = b.vinv; break;
             case 9: v = b.D; break;
             case 10:  // mortar maps of half M (0 or 1), Sec. 3.2.3

@@ -276,6 +276,43 @@ std::vector<ld> dg2fv_ld(int n, int nfv, int kind) {
 
 std::vector<double> make_dg2fv(int n, int nfv, int kind) { return to_d(dg2fv_ld(n, nfv, kind)); }
 
+std::vector<double> make_fv2dg_l2(int n, int nfv, int kind) {
+    // M c = b: M the exact mass matrix of the node family, b_i = integral of l_i
+    // over each sub-cell (Gauss rules of n + 1 points, exact for both integrands)
+    Nodes g = node_family(n, kind);
+    Nodes q = gauss(n + 1);
+    std::vector<ld> Mc(n * n, 0), Bm(n * nfv, 0);
+    for (size_t k = 0; k < q.x.size(); ++k) {
+        std::vector<ld> lv = lagrange_all(g, q.x[k]);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) Mc[i * n + j] += q.w[k] * lv[i] * lv[j];
+    }
+    const ld l = (ld)2 / nfv;
+    for (int s = 0; s < nfv; ++s)
+        for (size_t k = 0; k < q.x.size(); ++k) {
+            std::vector<ld> lv = lagrange_all(g, -1 + s * l + (q.x[k] + 1) * l / 2);
+            for (int i = 0; i < n; ++i) Bm[i * nfv + s] += q.w[k] * lv[i] * l / 2;
+        }
+    return to_d(chol_solve(Mc, Bm, n, nfv));
+}
+
+std::vector<double> make_fv_overlap(int n_from, int n_to) {
+    // sweep over the merged breakpoints k/n_from and k/n_to of [0, 1]: each
+    // piece between two breakpoints lies in one cell of either grid
+    std::vector<double> M((size_t)n_to * n_from, 0.0);
+    int a = 0, b = 0;  // next breakpoint index on the source / target grid
+    long x = 0;        // current position in units of 1/(n_from n_to)
+    while (a < n_from && b < n_to) {
+        const long xa = (long)(a + 1) * n_to, xb = (long)(b + 1) * n_from;
+        const long x1 = xa < xb ? xa : xb;
+        M[(size_t)b * n_from + a] += (double)(x1 - x) / (double)n_from;  // piece / |target cell|
+        x = x1;
+        if (x == xa) ++a;
+        if (x == xb) ++b;
+    }
+    return M;
+}
+
 std::vector<double> make_fv2dg(int n, int nfv, int kind) {
     if (nfv < n) throw std::runtime_error("N_FV < N+1");
     // Householder QR of A (nfv x n): A = Q R, pinv(A) = R^{-1} Q^T.

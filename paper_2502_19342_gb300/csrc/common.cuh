@@ -27,8 +27,9 @@ struct BankIdx {
     int32_t lm[NBANK], lp[NBANK];    // l_j(-1), l_j(+1)
     int32_t lhm[NBANK], lhp[NBANK];  // l_j(-1)/w_j, l_j(+1)/w_j
     int32_t vinv[NBANK];       // inverse orthonormal-Legendre Vandermonde (n x n)
-    int32_t d2f[NBANK];        // V^{DG->FV}: N_FV x n
-    int32_t f2d[NBANK];        // V^{FV->DG}: n x N_FV
+    int32_t d2f[NBANK][NBANK]; // [n][m] V^{DG->FV}: m sub-cells x n nodes
+    int32_t f2d[NBANK][NBANK]; // [n][m] V^{FV->DG}: n x m (pseudo-inverse; L2 projection where m < n)
+    int32_t ov[NBANK][NBANK];  // [a][b] sub-cell overlaps, b x a (per-element sub-cell counts)
     int32_t vm[NBANK][NBANK];  // V^{n->m}: m x n (interpolation up, L2 projection down)
     int32_t mi[NBANK][2];      // mortar half s: interpolation to the virtual small side, n x n
     int32_t mp[NBANK][2];      // mortar half s: L2 projection back to the big side, n x n

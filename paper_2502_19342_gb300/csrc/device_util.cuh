@@ -114,14 +114,20 @@ __device__ __forceinline__ void fv_layer(const Params& P, const double* __restri
                                          double* dst, double* sT1, double* sT2) {
     constexpr int V = NK + 4;
     const int n2 = n * n, d = fq >> 1;
+    const int nq = P.t.n[q], nq2 = nq * nq, nq3 = nq2 * nq;
     if (P.t.fv[q]) {
-        const double* src = P.b.fu + (P.t.fo[q] + (int64_t)fq * n2) * V;
-        for (int i = threadIdx.x; i < V * n2; i += blockDim.x) dst[i] = src[i];
-        __syncthreads();
+        const double* src = P.b.fu + (P.t.fo[q] + (int64_t)fq * nq2) * V;
+        if (nq == n) {
+            for (int i = threadIdx.x; i < V * n2; i += blockDim.x) dst[i] = src[i];
+            __syncthreads();
+        } else {  // per-element counts: the neighbour's layer by its sub-cell overlaps
+            for (int i = threadIdx.x; i < V * nq2; i += blockDim.x) sT1[i] = src[i];
+            __syncthreads();
+            face_map(sT1, nq, dst, n, B(P, P.bi.ov[nq][n]), V, sT2);
+        }
         return;
     }
-    const int nq = P.t.n[q], nq2 = nq * nq, nq3 = nq2 * nq;
-    const double* A = B(P, P.bi.d2f[nq]);  // n x nq
+    const double* A = B(P, P.bi.d2f[nq][n]);  // n x nq
     const int row = (fq & 1) ? n - 1 : 0;   // sub-cell layer next to the shared face
     const double* src = U + P.t.off[q];
     for (int i = threadIdx.x; i < V * nq2; i += blockDim.x) {
@@ -157,7 +163,7 @@ __device__ __forceinline__ void fv_layer_t(const Params& P, int q, int fq, int n
         return;
     }
     const int nq = P.t.n[q], nq2 = nq * nq, nq3 = nq2 * nq;
-    const double* A = B(P, P.bi.d2f[nq]);  // n x nq
+    const double* A = B(P, P.bi.d2f[nq][n]);  // n x nq
     const int row = (fq & 1) ? n - 1 : 0;
     face_map_t(lb, n, sT1, nq, A, V, sT2);
     double* dst = Ub + P.t.off[q];
@@ -174,8 +180,10 @@ __device__ __forceinline__ void fv_layer_t(const Params& P, int q, int fq, int n
 }
 
 // A face that changes representation (Sec. 3.2.1, 3.2.2): the common
-// representation (N_FV sub-cells if a side is FV, else the higher degree) and
-// which side is mapped to it (the lower degree, or the DG side of a DG/FV face).
+// representation and which side is mapped to it.  DG/DG: the higher degree,
+// the lower side mapped.  DG/FV: the FV side's sub-cells, the DG side mapped
+// (V^{DG->FV}).  FV/FV with different sub-cell counts (per-element counts):
+// the finer grid, the coarser side mapped by its sub-cell overlaps.
 struct MixedFace {
     int eL, eR, nc;
     bool cfv, mapL;
@@ -185,10 +193,19 @@ __device__ __forceinline__ MixedFace mixed_face(const Params& P, const Faces& Fc
     MixedFace m;
     m.eL = Fc.L[fid];
     m.eR = Fc.R[fid];
-    m.cfv = P.t.fv[m.eL] || P.t.fv[m.eR];
+    const bool fL = P.t.fv[m.eL], fR = P.t.fv[m.eR];
+    m.cfv = fL || fR;
     const int nL = P.t.n[m.eL], nR = P.t.n[m.eR];
-    m.nc = m.cfv ? P.nfv : max(nL, nR);
-    m.mapL = m.cfv ? !P.t.fv[m.eL] : nL != m.nc;
+    if (fL && fR) {
+        m.nc = max(nL, nR);
+        m.mapL = nL < nR;
+    } else if (m.cfv) {
+        m.nc = fL ? nL : nR;
+        m.mapL = !fL;
+    } else {
+        m.nc = max(nL, nR);
+        m.mapL = nL != m.nc;
+    }
     return m;
 }
 

@@ -115,7 +115,7 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
                                         bool faces_only) {
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
-    const int n = NF > 0 ? NF : P.nfv, n2 = n * n, n3 = n2 * n;
+    const int n = NF > 0 ? NF : T.n[blockIdx.x], n2 = n * n, n3 = n2 * n;
     const int e = T.items[T.first[blockIdx.x]];
     const FvLayout L = fv_layout(V, n, GS);
     double* sU = sm + L.u;    // V*n3 conservative means
@@ -146,9 +146,13 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
         }
         if (threadIdx.x == 0) {
             // distance between the sub-cell centres in this element's reference
-            // coordinates: l/2 (1 + h_neighbour/h), l when the sizes agree
+            // coordinates: l/2 (1 + h_neighbour/h), l when the sizes agree; to an
+            // FV neighbour with another sub-cell count n_q (per-element counts)
+            // l/2 + (h_neighbour/h)/n_q
             const int d = f >> 1;
-            const double dist = 0.5 * l * (1.0 + rh[d] / P.t.rh[3 * qe + d]);
+            const double hr = rh[d] / P.t.rh[3 * qe + d];
+            const int nq = q >= 0 && P.t.fv[q] ? P.t.n[q] : n;
+            const double dist = nq == n ? 0.5 * l * (1.0 + hr) : 0.5 * l + hr / nq;
             sID[f] = 1.0 / dist;
             sGS[f] = rh[d] / (l + dist);
         }
@@ -334,7 +338,7 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
 template <int NK, int TPB, int GS>
 __global__ void __launch_bounds__(TPB, 512 / TPB) k_fv(Params P, Tiles T, const double* __restrict__ U,
                                                        int faces_only) {
-    if (P.nfv == 8)
+    if (T.n[blockIdx.x] == 8)
         fv_body<NK, 8, GS>(P, T, U, faces_only != 0);
     else
         fv_body<NK, 0, GS>(P, T, U, faces_only != 0);
@@ -403,11 +407,11 @@ __global__ void __launch_bounds__(64) k_face_lift(Params P, Faces Fc, const int3
     }
     if (fvL && fvR) return;
     // DG/FV: FV face state mapped to the DG side's polynomial data by V^{FV->DG}
-    const int nD = fvL ? nR : nL, nF = P.nfv;
+    const int nD = fvL ? nR : nL, nF = fvL ? nL : nR;
     const int64_t sD = fvL ? sR : sL, sF = fvL ? sL : sR;
     for (int i = threadIdx.x; i < V * nF * nF; i += blockDim.x) sA[i] = P.b.frec[sF + i];
     __syncthreads();
-    face_map(sA, nF, sB, nD, B(P, P.bi.f2d[nD]), V, sT);
+    face_map(sA, nF, sB, nD, B(P, P.bi.f2d[nD][nF]), V, sT);
     for (int i = threadIdx.x; i < V * nD * nD; i += blockDim.x) P.b.flift[sD + i] = 0.5 * (P.b.fu[sD + i] + sB[i]);
 }
 
@@ -486,9 +490,10 @@ __global__ void __launch_bounds__(128) k_mixed_in(Params P, Faces Fc, const int3
     const MixedFace m = mixed_face(P, Fc, fid);
     const int e = m.mapL ? m.eL : m.eR, f = m.mapL ? 2 * d + 1 : 2 * d, n = P.t.n[e];
     const int64_t slot = P.t.fo[e] + (int64_t)f * n * n;
-    const double* M = B(P, m.cfv ? P.bi.d2f[n] : P.bi.vm[n][m.nc]);
+    const bool fvs = P.t.fv[e];  // a coarser FV side (per-element counts): its reconstructed states by overlaps
+    const double* M = B(P, fvs ? P.bi.ov[n][m.nc] : (m.cfv ? P.bi.d2f[n][m.nc] : P.bi.vm[n][m.nc]));
     double* out = Sin + mpt[k] * 4 * V;
-    face_map(P.b.fu + slot * V, n, out, m.nc, M, V, tmp);
+    face_map((fvs ? P.b.frec : P.b.fu) + slot * V, n, out, m.nc, M, V, tmp);
     if (P.ph.viscous) face_map(P.b.fg + slot * 3 * V, n, out + V * m.nc * m.nc, m.nc, M, 3 * V, tmp);
 }
 
@@ -556,7 +561,8 @@ __global__ void __launch_bounds__(128) k_mixed_out(Params P, Faces Fc, const int
     const int k = blockIdx.x, fid = mface[k], d = Fc.d[fid];
     const MixedFace m = mixed_face(P, Fc, fid);
     const int e = m.mapL ? m.eL : m.eR, f = m.mapL ? 2 * d + 1 : 2 * d, n = P.t.n[e], n2 = n * n;
-    const double* M = B(P, m.cfv ? P.bi.f2d[n] : P.bi.vm[m.nc][n]);
+    const double* M =
+        B(P, P.t.fv[e] ? P.bi.ov[m.nc][n] : (m.cfv ? P.bi.f2d[n][m.nc] : P.bi.vm[m.nc][n]));
     face_map(Sout + mpt[k] * V, m.nc, res, n, M, V, tmp);
     const double sgn = m.mapL ? 1.0 : -1.0;  // outward normal of the upper element is -x_d
     double* dst = P.b.flux + (P.t.fo[e] + (int64_t)f * n2) * V;
@@ -896,7 +902,7 @@ __global__ void __launch_bounds__(256) k_dt(Params P, Tiles T, const double* __r
             ce = e;
             const bool fv = P.t.fv[e];
             const double fac = fv ? 1.0 : 2.0 * P.t.N[e] + 1.0;
-            const double sub = fv ? (double)P.nfv : 1.0;
+            const double sub = fv ? (double)P.t.n[e] : 1.0;
             double sdx = 0.0;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -985,8 +991,8 @@ __global__ void __launch_bounds__(128) k_indicator(Params P, const double* __res
     const double* src = U + P.t.off[e];
     if (fv) {
         // V^{FV->DG} in three directions, one variable at a time
-        const int nf = P.nfv, nf2 = nf * nf, nf3 = nf2 * nf;
-        const double* X = B(P, P.bi.f2d[n]);  // n x nf
+        const int nf = P.t.n[e], nf2 = nf * nf, nf3 = nf2 * nf;
+        const double* X = B(P, P.bi.f2d[n][nf]);  // n x nf
         for (int v = 0; v < V; ++v) {
             for (int idx = threadIdx.x; idx < n * nf2; idx += blockDim.x) {
                 const int i = idx % n, jk = idx / n;
@@ -1134,8 +1140,9 @@ __global__ void __launch_bounds__(128) k_remap(Params P, RemapSide A, RemapSide 
     }
     const double* M;
     if (!fa && !fb) M = B(P, P.bi.vm[na][nb]);
-    else if (!fa && fb) M = B(P, P.bi.d2f[na]);
-    else M = B(P, P.bi.f2d[nb]);
+    else if (!fa && fb) M = B(P, P.bi.d2f[na][nb]);
+    else if (fa && !fb) M = B(P, P.bi.f2d[nb][na]);
+    else M = B(P, P.bi.ov[na][nb]);  // FV -> FV with another sub-cell count (per-element counts)
     const int a2 = na * na, a3 = a2 * na, b2 = nb * nb, b3 = b2 * nb;
     double* t1 = sm;                 // V * nb*na*na
     double* t2 = t1 + V * nb * a2;   // V * nb*nb*na

@@ -144,7 +144,8 @@ class Context:
         self._keep = (dims, lo, hi)
         mesh = MeshDesc(dims.shape[0], dims.ctypes.data_as(C.POINTER(C.c_int32)),
                         lo.ctypes.data_as(C.POINTER(C.c_double)), hi.ctypes.data_as(C.POINTER(C.c_double)),
-                        N_min, N_max, int(problem["n_fv"]), int(problem.get("chain", 0)))
+                        N_min, N_max, 0 if problem.get("fv_own_n", 0) else int(problem["n_fv"]),
+                        int(problem.get("chain", 0)))
         nk = len(problem["gamma"])
         ph = Phys()
         ph.n_species = nk
