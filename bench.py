@@ -609,7 +609,7 @@ def batched_comparison(steps=50, rank=0, world=1, dist=None):
         dist.all_reduce(t, op=dist.ReduceOp.MIN)
         dt = float(t.item())
     res = {}
-    for name, mode in (("batched", 0), ("per_degree_loop", 1)):
+    for name, mode in (("batched", 0), ("per_degree_loop", 1), ("batched_persistent", 2)):
         ctx.set_launch_mode(mode)
 
         def run():
@@ -644,6 +644,7 @@ def batched_comparison(steps=50, rank=0, world=1, dist=None):
         c.close()
     out = {"steps": steps, "dofs": dofs, **{k: r4(v) for k, v in res.items()},
            "batched_over_per_degree": r4(res["batched"] / res["per_degree_loop"]),
+           "persistent_over_per_degree": r4(res["batched_persistent"] / res["per_degree_loop"]),
            "tiles": {str(k): v for k, v in tuned.items()}}
     if world > 1:
         out["domains_sharded"] = f"{world} ranks"

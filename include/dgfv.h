@@ -295,8 +295,12 @@ int dgfv_profile_read(dgfv_ctx* ctx, double* ms, int64_t* launches, int cap);
 /* Launch organisation of the element and conforming-face kernels: mode 0 (the
  * default) issues one launch per kernel covering every degree (tiles of
  * elements of one degree, the degree read per tile); mode 1 issues one launch
- * per degree bin, the loop a per-degree implementation would run.  Results
- * are identical. */
+ * per degree bin, the loop a per-degree implementation would run; mode 2 is
+ * mode 0 with the volume kernel persistent: as many CTAs as are resident at
+ * once take the tiles of every degree from a work queue, costliest degrees
+ * first (standard volume integral; the split form keeps mode 0).  Modes 0 and
+ * 1 give identical results; mode 2 agrees with them to rounding (the same
+ * element body compiled into another kernel). */
 int dgfv_set_launch_mode(dgfv_ctx* ctx, int mode);
 
 /* Shared-memory layout of the FV sub-cell kernel (Sec. 3.1.2, Eq. 26):

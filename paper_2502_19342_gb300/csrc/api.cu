@@ -115,7 +115,10 @@ struct dgfv_ctx {
     FaceTileSet conf;       // faces with one representation on both sides
     MixedSet mixed;         // the flux faces in three passes
     int n_fv_elems = 0;
-    int launch_mode = 0;           // 0: one launch per kernel; 1: one launch per degree bin
+    int launch_mode = 0;           // 0: one launch per kernel; 1: one launch per degree bin;
+                                   // 2: as 0 with the volume kernel persistent (work queue)
+    int* d_queue = nullptr;        // work-queue counter of the persistent volume kernel
+    int n_sm = 1;                  // SMs of the context's device
     int fv_variant = 0;            // k_fv layout: 0 automatic, 1 gradients recomputed, 2 gradients kept
     int vol_per_tile[MAXDG + 1] = {};  // elements per volume tile (0: default), set by the autotuner
     int vol_variant = 0;              // volume-kernel launch variant (threads, register budget), autotuned
@@ -555,6 +558,9 @@ void enqueue_stage(dgfv_ctx* c, const double* Uin, const double* U0, double* out
             for (size_t bi = 0; bi < c->dg.bin_first.size(); ++bi)
                 launch_volume(c, P, c->dg.view(c->dg.bin_first[bi]), c->dg.bin_count[bi], c->dg.bin_smem[bi], Uin, s,
                               c->vol_variant);
+        else if (c->launch_mode == 2 && !c->opts.split_form)
+            launch_dg_volume_persistent(c->nk, P, c->dg.view(), c->dg.ntiles, c->dg.smem, Uin, s, c->vol_variant,
+                                        c->d_queue, c->n_sm);
         else
             launch_volume(c, P, c->dg.view(), c->dg.ntiles, c->dg.smem, Uin, s, c->vol_variant);
     }
@@ -737,6 +743,8 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
         return r;
     };
     if (cudaGetDevice(&c->dev) != cudaSuccess) return cleanup(DGFV_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess)
+        return cleanup(DGFV_ERR_CUDA);
     c->nk = phys->n_species;
     c->V = c->nk + 4;
     c->opts = *opts;
@@ -901,7 +909,7 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
     A_(c->d_flift, c->cap_fpts * c->V) A_(c->d_frec, c->cap_fpts * c->V)
     A_(c->d_rtmp, c->cap_state) A_(c->d_U, c->cap_state) A_(c->d_Us, c->cap_state)
     A_(c->d_dt3, 4) A_(c->d_partial, 2 * ne + 2) A_(c->d_Ip, ne) A_(c->d_Ih, ne) A_(c->d_dec, ne)
-    A_(c->d_status, 2) A_(c->d_pp_count, 2) A_(c->lift.d, c->n_faces) A_(c->flux.d, c->n_faces)
+    A_(c->d_status, 2) A_(c->d_queue, 1) A_(c->d_pp_count, 2) A_(c->lift.d, c->n_faces) A_(c->flux.d, c->n_faces)
     A_(c->conf.d_first, c->n_faces) A_(c->conf.d_count, c->n_faces) A_(c->conf.d_nc, c->n_faces)
     A_(c->conf.d_d, c->n_faces) A_(c->conf.d_items, c->n_faces)
     A_(c->mixed.tiles.d_first, c->n_faces) A_(c->mixed.tiles.d_count, c->n_faces)
@@ -1344,7 +1352,7 @@ int dgfv_profile_read(dgfv_ctx* c, double* ms, int64_t* launches, int cap) {
 }
 
 int dgfv_set_launch_mode(dgfv_ctx* c, int mode) {
-    if (!c || (mode != 0 && mode != 1)) return DGFV_ERR_ARG;
+    if (!c || mode < 0 || mode > 2) return DGFV_ERR_ARG;
     c->launch_mode = mode;
     c->graph_valid = false;
     return DGFV_OK;

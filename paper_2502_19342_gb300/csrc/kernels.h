@@ -26,6 +26,10 @@ void launch_dg_volume_split(int nk, const Params& P, const Tiles& T, int ntiles,
                             cudaStream_t s);
 void launch_dg_volume(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
                       cudaStream_t s, int variant = 0);
+// Persistent form (one launch over every degree, min(ntiles, resident CTAs)
+// CTAs taking tiles from the counter `queue`, which the launch zeroes).
+void launch_dg_volume_persistent(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
+                                 cudaStream_t s, int variant, int* queue, int n_sm);
 void launch_mixed_faces(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, const int32_t* mface,
                         const int64_t* mpt, int nmixed, double* Sin, double* Sout, cudaStream_t s);
 void launch_face_flux_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s);

@@ -3,6 +3,7 @@
 // kernels.cu so that the point-count instantiations compile in parallel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "common.cuh"
@@ -18,11 +19,12 @@ namespace dgfv {
 // NP > 0: the tile's point count as a compile-time constant (unrolled
 // contractions); NP = 0: read from the tile.
 template <int NK, int NP>
-__device__ __forceinline__ void dg_volume_body(const Params& P, const Tiles& T, const double* __restrict__ U) {
+__device__ __forceinline__ void dg_volume_body(const Params& P, const Tiles& T, const double* __restrict__ U,
+                                               int tile) {
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
-    const int first = T.first[blockIdx.x], count = T.count[blockIdx.x];
-    const int n = NP > 0 ? NP : T.n[blockIdx.x];
+    const int first = T.first[tile], count = T.count[tile];
+    const int n = NP > 0 ? NP : T.n[tile];
     const int n2 = n * n, n3 = n2 * n, q = n2 + 2 * n;
     double* sl = sm;                 // lm, lp (2n)
     double* sS = sl + 2 * n;         // per element and direction: (2/h_d) Dhat, (2/h_d) lhat(-1), (2/h_d) lhat(+1)
@@ -122,16 +124,42 @@ __device__ __forceinline__ void dg_volume_body(const Params& P, const Tiles& T, 
     }
 }
 
+template <int NK>
+__device__ __forceinline__ void dg_volume_tile(const Params& P, const Tiles& T, const double* __restrict__ U,
+                                               int tile) {
+    switch (T.n[tile]) {
+        case 2: dg_volume_body<NK, 2>(P, T, U, tile); break;
+        case 3: dg_volume_body<NK, 3>(P, T, U, tile); break;
+        case 4: dg_volume_body<NK, 4>(P, T, U, tile); break;
+        case 5: dg_volume_body<NK, 5>(P, T, U, tile); break;
+        case 6: dg_volume_body<NK, 6>(P, T, U, tile); break;
+        case 7: dg_volume_body<NK, 7>(P, T, U, tile); break;
+        default: dg_volume_body<NK, 8>(P, T, U, tile); break;
+    }
+}
+
 template <int NK, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_dg_volume(Params P, Tiles T, const double* __restrict__ U) {
-    switch (T.n[blockIdx.x]) {
-        case 2: dg_volume_body<NK, 2>(P, T, U); break;
-        case 3: dg_volume_body<NK, 3>(P, T, U); break;
-        case 4: dg_volume_body<NK, 4>(P, T, U); break;
-        case 5: dg_volume_body<NK, 5>(P, T, U); break;
-        case 6: dg_volume_body<NK, 6>(P, T, U); break;
-        case 7: dg_volume_body<NK, 7>(P, T, U); break;
-        default: dg_volume_body<NK, 8>(P, T, U); break;
+    dg_volume_tile<NK>(P, T, U, blockIdx.x);
+}
+
+// Persistent form: as many CTAs as fit on the GPU at once, each taking tiles
+// (of one degree each, every degree in the one launch) from a work queue, the
+// costliest degrees first (the tiles are stored by increasing point count and
+// taken from the end).  The queue is a counter the launch sets to zero; every
+// CTA stops once the counter passes the last tile, so the loop runs at most
+// ntiles times and never waits on another CTA.
+template <int NK, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_dg_volume_persistent(Params P, Tiles T, const double* __restrict__ U,
+                                                                    int ntiles, int* __restrict__ queue) {
+    __shared__ int s_next;
+    for (int it = 0; it < ntiles; ++it) {
+        if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
+        __syncthreads();
+        const int t = s_next;
+        if (t >= ntiles) break;
+        dg_volume_tile<NK>(P, T, U, ntiles - 1 - t);
+        __syncthreads();  // the tile's shared memory and s_next are reused
     }
 }
 
@@ -341,6 +369,29 @@ void launch_dg_volume(int nk, const Params& P, const Tiles& T, int ntiles, size_
         DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_dg_volume<NK, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)smem),
                            k_dg_volume<NK, 2><<<ntiles, threads, smem, s>>>(P, T, U)));
+    }
+}
+
+void launch_dg_volume_persistent(int nk, const Params& P, const Tiles& T, int ntiles, size_t smem, const double* U,
+                                 cudaStream_t s, int variant, int* queue, int n_sm) {
+    if (ntiles <= 0) return;
+    const int threads = (variant & 1) ? 128 : 256;
+    cudaMemsetAsync(queue, 0, sizeof(int), s);
+    int per_sm = 1;
+    if (variant & 2) {
+        DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_dg_volume_persistent<NK, 3>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dg_volume_persistent<NK, 3>,
+                                                                         threads, smem),
+                           k_dg_volume_persistent<NK, 3><<<std::min(ntiles, std::max(1, per_sm) * n_sm), threads,
+                                                           smem, s>>>(P, T, U, ntiles, queue)));
+    } else {
+        DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_dg_volume_persistent<NK, 2>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dg_volume_persistent<NK, 2>,
+                                                                         threads, smem),
+                           k_dg_volume_persistent<NK, 2><<<std::min(ntiles, std::max(1, per_sm) * n_sm), threads,
+                                                           smem, s>>>(P, T, U, ntiles, queue)));
     }
 }
 

@@ -363,9 +363,10 @@ class Context:
         """FV sub-cell kernel layout: 0 automatic, 1 gradients recomputed at each face, 2 gradients kept."""
         self._rc(lib().dgfv_set_fv_variant(self.h, int(variant)), "set_fv_variant")
 
-    def set_launch_mode(self, per_degree):
-        """False: one launch per kernel over all degrees; True: one launch per degree bin."""
-        self._rc(lib().dgfv_set_launch_mode(self.h, int(bool(per_degree))), "set_launch_mode")
+    def set_launch_mode(self, mode):
+        """0 (or False): one launch per kernel over all degrees; 1 (or True): one
+        launch per degree bin; 2: as 0 with the persistent volume kernel."""
+        self._rc(lib().dgfv_set_launch_mode(self.h, int(mode)), "set_launch_mode")
 
     def autotune(self, stream=None):
         """Time launch variants and tile sizes of the volume kernel on the current

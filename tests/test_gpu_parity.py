@@ -278,8 +278,23 @@ def test_launch_modes_and_autotuned_tiles_give_identical_results(oracle):
     assert tuned.pop("variant") in range(4)
     assert set(tuned) == set(int(x) for x in np.unique(prob["N"]))
     R2 = ctx.eval_rhs(Ud).cpu().numpy()
+    # persistent volume kernel (work queue over the tiles of every degree), with
+    # the tuned tiles and with many more tiles than resident CTAs
+    ctx.set_launch_mode(2)
+    R3 = ctx.eval_rhs(Ud).cpu().numpy()
+    ctx.set_state(Ud)
+    ctx.rk_steps(2, 1e-4, want_dt=False)  # graph capture of the persistent launch (queue reset inside)
+    S3 = ctx.get_state().cpu().numpy()
+    ctx.set_launch_mode(0)
+    ctx.set_state(Ud)
+    ctx.rk_steps(2, 1e-4, want_dt=False)
+    S0 = ctx.get_state().cpu().numpy()
     np.testing.assert_array_equal(R1, R0)
     np.testing.assert_array_equal(R2, R0)
+    # the persistent kernel is the same tile body compiled into another kernel:
+    # the compiler may contract multiply-adds differently, so it agrees to rounding
+    np.testing.assert_allclose(R3, R0, rtol=1e-12, atol=1e-12 * np.abs(R0).max())
+    np.testing.assert_allclose(S3, S0, rtol=1e-13, atol=0)
     assert_rhs_close(oracle, prob, U, R0)
     ctx.close()
 
