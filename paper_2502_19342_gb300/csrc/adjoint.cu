@@ -78,7 +78,7 @@ __device__ __forceinline__ void adj_conf_body(const Params& P, const AdjBuffers&
                 gR[x] = P.b.fg[sR * 3 * V + x * nc2 + p];
             }
         }
-        face_point_rev<NK>(P.ph, uL, gL, uR, gR, D, Fb, uLb, gLb, uRb, gRb, fv);
+        face_point_rev<NK, D>(P.ph, uL, gL, uR, gR, D, Fb, uLb, gLb, uRb, gRb, fv);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             A.ubar[sL * V + v * nc2 + p] = uLb[v];
@@ -162,7 +162,7 @@ __device__ __forceinline__ void adj_mixed_point_body(const Params& P, const AdjB
         double* gbd = A.gbar + sd * 3 * V + p;
         // viscous sides one after the other; the mapped side's gradient adjoint
         // replaces its gradient in Sin once that side is done
-        face_point_rev_seq<NK>(
+        face_point_rev_seq<NK, D>(
             P.ph, uL, uR, D, Fb, uLb, uRb, m.cfv,
             [&](int side, double* g) {
                 const double* src = (side == 0) == m.mapL ? gm : gd;
@@ -722,18 +722,24 @@ __global__ void __launch_bounds__(256) k_adj_fv(Params P, AdjBuffers A, Tiles T,
         for (int v = 0; v < V; ++v) Fb[v] = sc * (Rb[off + (int64_t)v * n3 + cR] - Rb[off + (int64_t)v * n3 + cL]);
         // viscous sides one after the other: a cell's gradient is formed just
         // before its reverse and its adjoint summed into gradb right after
-        face_point_rev_seq<NK>(
-            P.ph, uL, uR, d, Fb, uLb, uRb, true,
-            [&](int side, double* g) {
-                int i, j, k;
-                coords(d, m + side, a, b, i, j, k);
-                grad(i, j, k, g);
-            },
-            [&](int side, const double* gb) {
-                const int c = side ? cR : cL;
+        auto getg = [&](int side, double* g) {
+            int i, j, k;
+            coords(d, m + side, a, b, i, j, k);
+            grad(i, j, k, g);
+        };
+        auto putgb = [&](int side, const double* gb) {
+            const int c = side ? cR : cL;
 #pragma unroll
-                for (int x = 0; x < 3 * V; ++x) atomicAdd(&gradb[x * n3 + c], gb[x]);
-            });
+            for (int x = 0; x < 3 * V; ++x) atomicAdd(&gradb[x * n3 + c], gb[x]);
+        };
+        // the face direction as a compile-time constant: the viscous reverse of
+        // the other two directions' gradient entries reduces to the nonzero ones
+        if (d == 0)
+            face_point_rev_seq<NK, 0>(P.ph, uL, uR, 0, Fb, uLb, uRb, true, getg, putgb);
+        else if (d == 1)
+            face_point_rev_seq<NK, 1>(P.ph, uL, uR, 1, Fb, uLb, uRb, true, getg, putgb);
+        else
+            face_point_rev_seq<NK, 2>(P.ph, uL, uR, 2, Fb, uLb, uRb, true, getg, putgb);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             recb[((2 * d + 1) * V + v) * n3 + cL] = uLb[v];  // side + of the left cell
@@ -882,6 +888,26 @@ __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, doubl
                         double* __restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = fma(a, x[i], b * y[i]);
+}
+
+// The stage combinations of the SSP-RK3 step adjoint, one pass each:
+//   mode 0: o1 = c1 (x + dt y), o2 = c2 x          (after the VJP at U2)
+//   mode 1: o1 = c1 (x + dt y), o2 += c2 x         (after the VJP at U1)
+//   mode 2: o2 += x + dt y                         (after the VJP at U0)
+__global__ void k_rk3_adj_combine(int64_t n, int mode, double c1, double c2, double dt, const double* __restrict__ x,
+                                  const double* __restrict__ y, double* __restrict__ o1, double* __restrict__ o2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double xi = x[i], t = fma(dt, y[i], xi);
+        if (mode == 0) {
+            o1[i] = c1 * t;
+            o2[i] = c2 * xi;
+        } else if (mode == 1) {
+            o1[i] = c1 * t;
+            o2[i] = fma(c2, xi, o2[i]);
+        } else {
+            o2[i] += t;
+        }
+    }
 }
 
 // ================================================================= launchers
@@ -1084,6 +1110,13 @@ void launch_axpby(int64_t n, double a, const double* x, double b, const double* 
     if (n <= 0) return;
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 32);
     k_axpby<<<blocks, 256, 0, s>>>(n, a, x, b, y, out);
+}
+
+void launch_rk3_adj_combine(int64_t n, int mode, double c1, double c2, double dt, const double* x, const double* y,
+                            double* o1, double* o2, cudaStream_t s) {
+    if (n <= 0) return;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    k_rk3_adj_combine<<<blocks, 256, 0, s>>>(n, mode, c1, c2, dt, x, y, o1, o2);
 }
 
 }  // namespace dgfv

@@ -51,5 +51,8 @@ void launch_adj_fv_elements(int nk, const Params& P, const AdjBuffers& A, const 
 void launch_adj_prolong(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, double* Ub,
                         cudaStream_t s);
 void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);
+// SSP-RK3 step-adjoint combinations (see k_rk3_adj_combine).
+void launch_rk3_adj_combine(int64_t n, int mode, double c1, double c2, double dt, const double* x, const double* y,
+                            double* o1, double* o2, cudaStream_t s);
 
 }  // namespace dgfv

@@ -1123,16 +1123,16 @@ int dgfv_rhs_vjp(dgfv_ctx* c, const double* d_U, const double* d_Rbar, double* d
 static int rk_step_vjp_impl(dgfv_ctx* c, const double* d_U0, const double* d_U1, const double* d_U2, double dt,
                             const double* d_Ubar_next, double* d_Ubar, cudaStream_t s) {
     const int64_t n = c->n_state;
-    // U3 = 1/3 U0 + 2/3 (U2 + dt R(U2)), backwards:
+    // U3 = 1/3 U0 + 2/3 (U2 + dt R(U2)), backwards (W = J^T of the stage's adjoint):
     enqueue_vjp(c, d_U2, d_Ubar_next, c->d_W, s);
-    launch_axpby(n, 2.0 / 3.0, d_Ubar_next, 2.0 / 3.0 * dt, c->d_W, c->d_B2, s);   // U2_bar
-    launch_axpby(n, 1.0 / 3.0, d_Ubar_next, 0.0, d_Ubar_next, d_Ubar, s);          // U0_bar  = 1/3 U3_bar
+    // U2_bar = 2/3 (U3_bar + dt W);  U0_bar = 1/3 U3_bar
+    launch_rk3_adj_combine(n, 0, 2.0 / 3.0, 1.0 / 3.0, dt, d_Ubar_next, c->d_W, c->d_B2, d_Ubar, s);
     enqueue_vjp(c, d_U1, c->d_B2, c->d_W, s);
-    launch_axpby(n, 0.25, c->d_B2, 0.25 * dt, c->d_W, c->d_B1, s);                  // U1_bar
-    launch_axpby(n, 1.0, d_Ubar, 0.75, c->d_B2, d_Ubar, s);                         // U0_bar += 3/4 U2_bar
+    // U1_bar = 1/4 (U2_bar + dt W);  U0_bar += 3/4 U2_bar
+    launch_rk3_adj_combine(n, 1, 0.25, 0.75, dt, c->d_B2, c->d_W, c->d_B1, d_Ubar, s);
     enqueue_vjp(c, d_U0, c->d_B1, c->d_W, s);
-    launch_axpby(n, 1.0, d_Ubar, 1.0, c->d_B1, d_Ubar, s);                          // += U1_bar
-    launch_axpby(n, 1.0, d_Ubar, dt, c->d_W, d_Ubar, s);                            // += dt J^T U1_bar
+    // U0_bar += U1_bar + dt W
+    launch_rk3_adj_combine(n, 2, 0.0, 0.0, dt, c->d_B1, c->d_W, nullptr, d_Ubar, s);
     CK(cudaGetLastError());
     return DGFV_OK;
 }

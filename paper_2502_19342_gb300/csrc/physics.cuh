@@ -49,7 +49,7 @@ DGFV_HD double sutherland_factor(const DevPhys& P, double T) {
 
 template <int NK>
 struct Prim {
-    double rho, irho, Y[NK], v[3], E, eps, cv, icv, cp, kappa, T, p, c, mu, pr, lam;
+    double rho, irho, Y[NK], v[3], E, eps, cv, icv, cp, kappa, T, p, c, mu, pr, ipr, lam;
 };
 
 // Mixture state of a conserved vector.  3 divisions and 1 square root; terms
@@ -85,7 +85,8 @@ DGFV_HD void prim(const DevPhys& P, const double* u, Prim<NK>& s) {
     s.c = sqrt(s.kappa * s.p * s.irho);
     if (P.sutherland) mu *= sutherland_factor(P, s.T);
     s.mu = mu;
-    s.lam = mu * cp / pr;
+    s.ipr = 1.0 / pr;  // kept for the adjoint (its reverse of lambda needs 1/Pr)
+    s.lam = mu * cp * s.ipr;
 }
 
 // Convective flux in direction d.
@@ -521,7 +522,9 @@ DGFV_HD void face_state(const DevPhys& P, const double* w, double* u, Prim<NK>& 
     if (P.sutherland) mu *= sutherland_factor(P, s.T);
     s.mu = mu;
     s.pr = Q * irho;
-    s.lam = mu * Bc * (AR * rho * inv);  // mu c_p / Pr = mu B / Q
+    const double iQ = AR * rho * inv;  // 1/Q
+    s.ipr = rho * iQ;
+    s.lam = mu * Bc * iQ;  // mu c_p / Pr = mu B / Q
 }
 
 }  // namespace dgfv

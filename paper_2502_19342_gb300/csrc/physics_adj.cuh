@@ -27,9 +27,10 @@ DGFV_HD void zero(PrimBar<NK>& b) {
 template <int NK>
 DGFV_HD void prim_rev(const DevPhys& P, const double* u, const Prim<NK>& s, PrimBar<NK> b, double* ub) {
     // lam = mu cp / pr
-    b.mu += b.lam * s.cp / s.pr;
-    b.cp += b.lam * s.mu / s.pr;
-    b.pr -= b.lam * s.lam / s.pr;
+    const double lb = b.lam * s.ipr;
+    b.mu += lb * s.cp;
+    b.cp += lb * s.mu;
+    b.pr -= lb * s.lam;
     // Sutherland (Sec. 4.3): mu = mu_mix f(T), f = (T/T_ref)^{3/2} (T_ref + S)/(T + S),
     // f'/f = 3/(2T) - 1/(T + S); b.mu becomes the adjoint of mu_mix
     if (P.sutherland) {
@@ -224,6 +225,101 @@ DGFV_HD void prim_grad_rev(const DevPhys& P, const Prim<NK>& s, const double* g,
 #pragma unroll
         for (int k = 0; k < NK; ++k) gbd[k] += grb;
     }
+}
+
+// prim_grad_rev after the viscous flux reverse of a face in direction D (a
+// compile-time constant): flux_visc_rev leaves nonzero adjoints only on
+// direction D's entries, on dv_D/dx_dd and on the diagonal dv_dd/dx_dd, so for
+// the two other directions dd only those two velocity entries are reversed
+// (the products with the zero adjoints of the rest are not formed; the
+// compiler may not drop a product with 0.0 by itself).
+template <int NK, int D>
+DGFV_HD void prim_grad_rev_dir(const DevPhys& P, const Prim<NK>& s, const double* g, const PrimGrad<NK>& G,
+                               const PrimGradBar<NK>& Gb, double* gb, PrimBar<NK>& b) {
+    constexpr int V = NK + 4;
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+        if (dd == D) continue;
+        const double* gd = g + dd * V;
+        double* gbd = gb + dd * V;
+        double gr = gd[0];
+#pragma unroll
+        for (int k = 1; k < NK; ++k) gr += gd[k];
+        double grb = 0.0;
+        auto vrev = [&](int i) {
+            // Gv_i = (g_{m_i} - v_i gr) irho
+            const double Gvb = Gb.v[i][dd];
+            gbd[NK + i] += Gvb * s.irho;
+            b.v[i] -= Gvb * gr * s.irho;
+            grb -= Gvb * s.v[i] * s.irho;
+            b.irho += Gvb * (gd[NK + i] - s.v[i] * gr);
+        };
+        vrev(D);
+        vrev(dd);
+#pragma unroll
+        for (int k = 0; k < NK; ++k) gbd[k] += grb;
+    }
+    // direction D itself: every entry, as prim_grad_rev
+    PrimGradBar<NK> GbD;
+    zero(GbD);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) GbD.v[i][D] = Gb.v[i][D];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) GbD.Y[k][D] = Gb.Y[k][D];
+    GbD.T[D] = Gb.T[D];
+    {
+        const double* gd = g + D * V;
+        double* gbd = gb + D * V;
+        double gr = gd[0];
+#pragma unroll
+        for (int k = 1; k < NK; ++k) gr += gd[k];
+        double gcv = 0.0;
+#pragma unroll
+        for (int k = 0; k < NK; ++k) gcv = fma(P.cv[k], G.Y[k][D], gcv);
+        double geps = (gd[NK + 3] - s.E * gr) * s.irho;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) geps -= s.v[i] * G.v[i][D];
+        const double GTb = GbD.T[D];
+        const double gepsb = GTb * s.icv;
+        b.T -= GTb * gcv * s.icv;
+        const double gcvb = -GTb * s.T * s.icv;
+        b.icv += GTb * (geps - s.T * gcv);
+        double grb = 0.0;
+        gbd[NK + 3] += gepsb * s.irho;
+        b.E -= gepsb * gr * s.irho;
+        grb -= gepsb * s.E * s.irho;
+        b.irho += gepsb * (gd[NK + 3] - s.E * gr);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            b.v[i] -= gepsb * G.v[i][D];
+            const double Gvb = GbD.v[i][D] - gepsb * s.v[i];
+            gbd[NK + i] += Gvb * s.irho;
+            b.v[i] -= Gvb * gr * s.irho;
+            grb -= Gvb * s.v[i] * s.irho;
+            b.irho += Gvb * (gd[NK + i] - s.v[i] * gr);
+        }
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const double GYb = GbD.Y[k][D] + gcvb * P.cv[k];
+            gbd[k] += GYb * s.irho;
+            b.Y[k] -= GYb * gr * s.irho;
+            grb -= GYb * s.Y[k] * s.irho;
+            b.irho += GYb * (gd[k] - s.Y[k] * gr);
+        }
+#pragma unroll
+        for (int k = 0; k < NK; ++k) gbd[k] += grb;
+    }
+}
+
+// The gradient reverse of a face in direction d: specialised when the caller
+// knows d at compile time (DC = d), the general one otherwise (DC = -1).
+template <int NK, int DC>
+DGFV_HD void prim_grad_rev_face(const DevPhys& P, const Prim<NK>& s, const double* g, const PrimGrad<NK>& G,
+                                const PrimGradBar<NK>& Gb, double* gb, PrimBar<NK>& b) {
+    if constexpr (DC >= 0)
+        prim_grad_rev_dir<NK, DC>(P, s, g, G, Gb, gb, b);
+    else
+        prim_grad_rev<NK>(P, s, g, G, Gb, gb, b);
 }
 
 // Adjoint of the nodal volume fluxes F_d = F^c_d(u) + F^v_d(u, g), d = 0..2:
@@ -585,7 +681,7 @@ DGFV_HD void riemann_roe_rev(const DevPhys& P, const double* uL, const Prim<NK>&
 // other: getg(side, g) supplies a side's gradient (side 0 = L, 1 = R) just
 // before its reverse and putgb(side, gb) receives its adjoint right after, so
 // only one side's gradient and gradient adjoint are live at a time.
-template <int NK, class GetG, class PutGb>
+template <int NK, int DC = -1, class GetG, class PutGb>
 DGFV_HD void face_point_rev_seq(const DevPhys& P, const double* uL, const double* uR, int d, const double* Fb,
                                 double* uLb, double* uRb, bool fv_involved, GetG getg, PutGb putgb) {
     constexpr int V = NK + 4;
@@ -635,7 +731,7 @@ DGFV_HD void face_point_rev_seq(const DevPhys& P, const double* uL, const double
             prim_grad<NK>(P, s, g, G);
             zero(Gb);
             flux_visc_rev<NK>(P, s, G, d, half, Gb, b);
-            prim_grad_rev<NK>(P, s, g, G, Gb, gb, b);
+            prim_grad_rev_face<NK, DC>(P, s, g, G, Gb, gb, b);
             putgb(side, gb);
         }
     }
@@ -645,12 +741,12 @@ DGFV_HD void face_point_rev_seq(const DevPhys& P, const double* uL, const double
 
 // The same with both gradients given and both gradient adjoints accumulated
 // into gLb, gRb.
-template <int NK>
+template <int NK, int DC = -1>
 DGFV_HD void face_point_rev(const DevPhys& P, const double* uL, const double* gL, const double* uR,
                             const double* gR, int d, const double* Fb, double* uLb, double* gLb, double* uRb,
                             double* gRb, bool fv_involved = false) {
     constexpr int V = NK + 4;
-    face_point_rev_seq<NK>(
+    face_point_rev_seq<NK, DC>(
         P, uL, uR, d, Fb, uLb, uRb, fv_involved,
         [&](int side, double* g) {
             const double* src = side ? gR : gL;
