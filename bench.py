@@ -449,7 +449,7 @@ def split_form_run(nel, peak, warmup=2, steps=1):
             "whole_rhs_frac": r4(per_dof * value / 1e12 / peak)}
 
 
-def tgv_run(nel=32, warmup=30, steps=2):
+def tgv_run(nel=32, warmup=60, steps=2):
     """Supersonic Taylor-Green vortex (Sec. 4.3) as a throughput workload: 32^3
     elements, N in 2..4 by the pressure indicator, FV by the density indicator,
     Sutherland viscosity, five-stage low-storage RK4; one step = adaptation +
