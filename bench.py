@@ -39,8 +39,8 @@ STAGES_PER_STEP = 3
 DFMA_PER_CLK = 2
 # DRAM bytes per DG DOF of one k_dg_volume launch, from an ncu capture of the
 # turbulence workload at 28^3 elements (dram__bytes_read.sum + write.sum =
-# 0.373 + 0.703 GB for 3.13e6 DG DOFs).
-VOLUME_DRAM_BYTES_PER_DG_DOF = 344.0
+# 0.398 + 0.759 GB for 3.45e6 DG DOFs).
+VOLUME_DRAM_BYTES_PER_DG_DOF = 335.0
 # measured copy bandwidth of this GPU type (written beside the repository when
 # it is present); used only to show how far the FP64-bound kernel is from HBM.
 HBM_FALLBACK_GBS = 6800.0
@@ -400,7 +400,7 @@ def kernel_table(prof, per_step, dofs_per_launch, peak):
     return out
 
 
-def split_form_run(nel, peak, warmup=2, steps=1):
+def split_form_run(nel, peak=None, warmup=2, steps=1):
     """The turbulence workload with the jet's scheme (Sec. 5.1): split-form DGSEM
     on LGL nodes with the kinetic-energy-preserving flux, Roe-HH between DG
     elements and LLF where FV data meet; adaptation cycles as in the main
@@ -408,6 +408,7 @@ def split_form_run(nel, peak, warmup=2, steps=1):
     the same cycles for the roofline of the split volume kernel."""
     import torch
     from paper_2502_19342_gb300 import dgfv, workloads as W
+    peak = fp64_peak()[0] if peak is None else peak
     prob, U = W.turbulence(seed=0, nel=(nel, nel, nel), N0=4, nodes=1, split=1, riemann=2)
     ctx = dgfv.Context(prob, N_min=1, N_max=7, opts=dict(cfl_c=0.5, cfl_v=0.5, thresholds=W.THRESHOLDS))
     ctx.set_state(torch.from_numpy(U).cuda())
@@ -488,7 +489,7 @@ def tgv_run(nel=32, warmup=60, steps=2):
             "degree_histogram": np.bincount(N_now[fv_now == 0], minlength=5).tolist()[2:]}
 
 
-def hp_shock_run(peak, cycles=40, fv_variant=0):
+def hp_shock_run(peak=None, cycles=40, fv_variant=0):
     """The hp-mixed shock case at its full length: 16^3 elements on
     [0,2]x[0,1]^2, N in 2..6 with FV sub-cells (N_FV = 7) chosen by the
     indicator every 5 SSP-RK3 steps, a Mach 1.5 shock into a heavy-gas bubble,
@@ -498,6 +499,7 @@ def hp_shock_run(peak, cycles=40, fv_variant=0):
     change); the RHS rate and its roofline fraction over the steps alone."""
     import torch
     from paper_2502_19342_gb300 import dgfv, workloads as W
+    peak = fp64_peak()[0] if peak is None else peak
     prob, U = W.hp_shock(0, y_bg=0.01)
     ctx = dgfv.Context(prob, N_min=2, N_max=6, opts=dict(cfl_c=0.5, cfl_v=0.5, thresholds=W.THRESHOLDS))
     ctx.set_fv_variant(fv_variant)
@@ -539,7 +541,7 @@ def hp_shock_run(peak, cycles=40, fv_variant=0):
             "subcell_dof_share": r4(float(fv_now.astype(np.int64).sum() * 343) / float(W.n_dofs(dict(prob, N=N_now, fv=fv_now))))}
 
 
-def mortar_run(peak, k=24, warmup=1, steps=3):
+def mortar_run(peak=None, k=24, warmup=1, steps=3):
     """Non-conforming mesh (Sec. 3.2.3) at scale: the half-refined unit cube of
     Sec. 4.1 / 4.2 with (k, 2k, 2k) + (k/2, k, k) elements and type-3 mortars on
     both x interfaces, random degrees N in 2..5 and 5 % FV elements (N_FV = 8),
@@ -547,6 +549,7 @@ def mortar_run(peak, k=24, warmup=1, steps=3):
     10 SSP-RK3 steps at CFL 0.5 (pattern fixed), CUDA events."""
     import torch
     from paper_2502_19342_gb300 import dgfv, workloads as W
+    peak = fp64_peak()[0] if peak is None else peak
     prob, U = W.half_refined_wave(k)
     ctx = dgfv.Context(prob, N_min=1, N_max=7, opts=dict(cfl_c=0.5, cfl_v=0.5))
     ctx.set_state(torch.from_numpy(U).cuda())
@@ -829,7 +832,9 @@ def main():
         traffic = VOLUME_DRAM_BYTES_PER_DG_DOF * dg_dofs if main_k == "dg_volume" else None
         roof = {"bound": "alu", "kernel": "k_" + main_k, "achieved": r4(achieved), "peak": r4(peak),
                 "unit": "TFLOP/s", "frac": r4(achieved / peak), "frac_of_dfma_probe": r4(achieved / probe),
-                "traffic": r4(traffic), "peak_source": peak_src,
+                "traffic": r4(traffic), "traffic_source": "ncu DRAM bytes per DG DOF of k_dg_volume (28^3 case, "
+                                                          "335 B) x the DG DOFs of one launch here",
+                "peak_source": peak_src,
                 "dfma_probe_tflops": r4(probe), "dmma_probe_tflops": r4(probe_mma),
                 "flops_per_dof": {"total": r4(per_dof), main_k: r4(per_step[KERNEL_STEP[main_k]])},
                 "whole_rhs_tflops": r4(per_dof * units / (ms * 1e-3) / 1e12),
