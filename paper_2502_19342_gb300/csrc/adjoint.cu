@@ -572,292 +572,6 @@ __global__ void __launch_bounds__(128) k_adj_surface_fv(Params P, AdjBuffers A, 
     }
 }
 
-// k_adj_fv: one CTA per FV element, after the face and lifting adjoints (which
-// leave the adjoints of the element's reconstructed face states in ubar and of
-// its boundary-cell gradients in gbar).  Recomputes the forward quantities of
-// k_fv (neighbour values, reconstruction variables, slopes, gradients) and
-// runs its steps backwards:
-//   1. interior sub-cell faces: F_bar = (n/h_d)(R_bar(c_R) - R_bar(c_L)), the
-//      point-flux reverse gives the adjoints of the two reconstructed states and
-//      of the two cells' gradients;
-//   2. element faces: the reconstructed-state and gradient adjoints from ubar, gbar;
-//   3. reconstruction^T per cell and direction (w_to_cons^T, the slope, minmod
-//      along the branch the forward took) and gradient^T (central differences);
-//      contributions beyond the element go to the neighbour values;
-//   4. cons_to_w^T: the element's U_bar (written), and the neighbour values'
-//      adjoints in conservative variables, left in the element's fbar slots for
-//      k_adj_fv_gather.
-// Scratch in global memory, in the element's own regions of the adjoint
-// buffers the DG kernels do not use for FV elements: rec_bar (6V n^3) in gf,
-// grad_bar (3V n^3) in gvol, w_bar and the direct u_bar (2 x V n^3) in fvs; the
-// neighbour adjoints in the element's sbar (reconstruction variables) and fbar
-// (conservative) face slots.  Sums over several writers use atomics.
-template <int NK>
-__global__ void __launch_bounds__(256) k_adj_fv(Params P, AdjBuffers A, Tiles T, const double* __restrict__ U,
-                                               const double* __restrict__ Rb, double* __restrict__ Ub,
-                                               double* __restrict__ gf, double* __restrict__ gvol,
-                                               double* __restrict__ fvs, int64_t cap_state) {
-    constexpr int V = NK + 4;
-    extern __shared__ double sm[];
-    const int n = P.nfv, n2 = n * n, n3 = n2 * n;
-    const int e = T.items[T.first[blockIdx.x]];
-    double* sU = sm;                 // V n3
-    double* sW = sU + V * n3;        // V n3
-    double* sNb = sW + V * n3;       // 6 V n2
-    double* sNw = sNb + 6 * V * n2;  // 6 V n2
-    double* sT1 = sNw + 6 * V * n2;  // V MAXP^2
-    double* sT2 = sT1 + V * MAXP * MAXP;
-    __shared__ double sID[6], sGS[6];
-    const int64_t off = P.t.off[e];
-    const double* rh = P.t.rh + 3 * e;
-    const double l = 2.0 / n, il = 1.0 / l;
-    const bool visc = P.ph.viscous;
-    double* recb = gf + 6 * off;             // [d][side][v][c]: 6 V n3
-    double* gradb = gvol + 3 * off;          // [x][c]: 3V n3
-    double* wbar = fvs + off;                // V n3
-    double* ubc = fvs + cap_state + off;     // V n3
-    double* nbwb = A.sbar + P.t.fo[e] * V;   // 6 slots of V n2
-    double* nbub = A.fbar + P.t.fo[e] * V;   // 6 slots of V n2
-    for (int i = threadIdx.x; i < V * n3; i += blockDim.x) {
-        sU[i] = U[off + i];
-        wbar[i] = 0.0;
-        ubc[i] = 0.0;
-    }
-    for (int i = threadIdx.x; i < 3 * V * n3; i += blockDim.x) gradb[i] = 0.0;
-    for (int f = 0; f < 6; ++f) {
-        const int q = P.t.nb[6 * e + f];
-        int qe = q;
-        if (q < 0) {  // mortar face: the values k_mortar_nb gathered
-            const int sl = -1 - q;
-            const double* src = P.t.mnb + (int64_t)sl * V * n2;
-            for (int i = threadIdx.x; i < V * n2; i += blockDim.x) sNb[f * V * n2 + i] = src[i];
-            qe = P.t.mnbe[sl];
-        } else {
-            fv_layer<NK>(P, U, q, f ^ 1, n, sNb + f * V * n2, sT1, sT2);
-        }
-        if (threadIdx.x == 0) {
-            const int d = f >> 1;
-            const double dist = 0.5 * l * (1.0 + rh[d] / P.t.rh[3 * qe + d]);
-            sID[f] = 1.0 / dist;
-            sGS[f] = rh[d] / (l + dist);
-        }
-    }
-    for (int i = threadIdx.x; i < 6 * V * n2; i += blockDim.x) {
-        nbwb[i] = 0.0;
-        nbub[i] = 0.0;
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < n3; c += blockDim.x) {
-        double u[V], w[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) u[v] = sU[v * n3 + c];
-        cons_to_w<NK>(P.ph, u, w);
-#pragma unroll
-        for (int v = 0; v < V; ++v) sW[v * n3 + c] = w[v];
-    }
-    for (int c = threadIdx.x; c < 6 * n2; c += blockDim.x) {
-        const int f = c / n2, p = c % n2;
-        double u[V], w[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) u[v] = sNb[(f * V + v) * n2 + p];
-        cons_to_w<NK>(P.ph, u, w);
-#pragma unroll
-        for (int v = 0; v < V; ++v) sNw[(f * V + v) * n2 + p] = w[v];
-    }
-    __syncthreads();
-    auto cellU = [&](int d, int m, int a, int b, int v) -> double {
-        if (m < 0) return sNb[((2 * d) * V + v) * n2 + a + n * b];
-        if (m >= n) return sNb[((2 * d + 1) * V + v) * n2 + a + n * b];
-        return sU[v * n3 + node_index(n, d, m, a, b)];
-    };
-    auto cellW = [&](int d, int m, int a, int b, int v) -> double {
-        if (m < 0) return sNw[((2 * d) * V + v) * n2 + a + n * b];
-        if (m >= n) return sNw[((2 * d + 1) * V + v) * n2 + a + n * b];
-        return sW[v * n3 + node_index(n, d, m, a, b)];
-    };
-    // reconstructed reconstruction variables of cell m at its side (the forward's recon, before w_to_cons)
-    auto reconw = [&](int d, int m, int a, int b, int side, double* w) {
-        const double ilm = m > 0 ? il : sID[2 * d], ilp = m < n - 1 ? il : sID[2 * d + 1];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const double wc = cellW(d, m, a, b, v);
-            const double s = minmod((wc - cellW(d, m - 1, a, b, v)) * ilm, (cellW(d, m + 1, a, b, v) - wc) * ilp);
-            w[v] = side > 0 ? wc + s * (0.5 * l) : wc - s * (0.5 * l);
-        }
-    };
-    auto grad = [&](int i, int j, int k, double* g) {
-        const int c3[3] = {i, j, k};
-#pragma unroll
-        for (int dd = 0; dd < 3; ++dd) {
-            const int m = c3[dd];
-            const int a = dd == 0 ? j : i, b = dd == 2 ? j : k;
-            const double sc = m == 0 ? sGS[2 * dd] : (m == n - 1 ? sGS[2 * dd + 1] : 0.5 * n * 0.5 * rh[dd]);
-#pragma unroll
-            for (int v = 0; v < V; ++v)
-                g[dd * V + v] = (cellU(dd, m + 1, a, b, v) - cellU(dd, m - 1, a, b, v)) * sc;
-        }
-    };
-    auto coords = [&](int d, int m, int a, int b, int& i, int& j, int& k) {
-        if (d == 0) { i = m; j = a; k = b; }
-        else if (d == 1) { i = a; j = m; k = b; }
-        else { i = a; j = b; k = m; }
-    };
-    // 1. interior sub-cell faces
-    const int nif = (n - 1) * n2;
-    for (int t = threadIdx.x; t < 3 * nif; t += blockDim.x) {
-        const int d = t / nif, fidx = t - d * nif;
-        const int m = fidx % (n - 1), p = fidx / (n - 1), a = p % n, b = p / n;
-        const int cL = node_index(n, d, m, a, b), cR = node_index(n, d, m + 1, a, b);
-        double uL[V], uR[V], Fb[V];
-        double uLb[V] = {}, uRb[V] = {};
-        {
-            double wL[V], wR[V];
-            reconw(d, m, a, b, +1, wL);
-            reconw(d, m + 1, a, b, -1, wR);
-            w_to_cons<NK>(P.ph, wL, uL);
-            w_to_cons<NK>(P.ph, wR, uR);
-        }
-        const double sc = 0.5 * n * rh[d];
-#pragma unroll
-        for (int v = 0; v < V; ++v) Fb[v] = sc * (Rb[off + (int64_t)v * n3 + cR] - Rb[off + (int64_t)v * n3 + cL]);
-        // viscous sides one after the other: a cell's gradient is formed just
-        // before its reverse and its adjoint summed into gradb right after
-        auto getg = [&](int side, double* g) {
-            int i, j, k;
-            coords(d, m + side, a, b, i, j, k);
-            grad(i, j, k, g);
-        };
-        auto putgb = [&](int side, const double* gb) {
-            const int c = side ? cR : cL;
-#pragma unroll
-            for (int x = 0; x < 3 * V; ++x) atomicAdd(&gradb[x * n3 + c], gb[x]);
-        };
-        // the face direction as a compile-time constant: the viscous reverse of
-        // the other two directions' gradient entries reduces to the nonzero ones
-        if (d == 0)
-            face_point_rev_seq<NK, 0>(P.ph, uL, uR, 0, Fb, uLb, uRb, true, getg, putgb);
-        else if (d == 1)
-            face_point_rev_seq<NK, 1>(P.ph, uL, uR, 1, Fb, uLb, uRb, true, getg, putgb);
-        else
-            face_point_rev_seq<NK, 2>(P.ph, uL, uR, 2, Fb, uLb, uRb, true, getg, putgb);
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            recb[((2 * d + 1) * V + v) * n3 + cL] = uLb[v];  // side + of the left cell
-            recb[((2 * d) * V + v) * n3 + cR] = uRb[v];      // side - of the right cell
-        }
-    }
-    // 2. element faces: the face kernels' adjoints of the reconstructed face state and boundary gradient
-    for (int i = threadIdx.x; i < 6 * n2; i += blockDim.x) {
-        const int f = i / n2, p = i % n2, d = f >> 1, s = f & 1;
-        const int c = node_index(n, d, s ? n - 1 : 0, p % n, p / n);
-        const int64_t slot = P.t.fo[e] + (int64_t)f * n2;
-#pragma unroll
-        for (int v = 0; v < V; ++v) recb[(f * V + v) * n3 + c] = A.ubar[slot * V + v * n2 + p];
-        if (visc)
-#pragma unroll
-            for (int x = 0; x < 3 * V; ++x) atomicAdd(&gradb[x * n3 + c], A.gbar[slot * 3 * V + x * n2 + p]);
-    }
-    __syncthreads();
-    // 3. reconstruction^T and gradient^T, per cell and direction
-    auto add_w = [&](int d, int m, int a, int b, int v, double x) {
-        if (m < 0) atomicAdd(&nbwb[((2 * d) * V + v) * n2 + a + n * b], x);
-        else if (m >= n) atomicAdd(&nbwb[((2 * d + 1) * V + v) * n2 + a + n * b], x);
-        else atomicAdd(&wbar[v * n3 + node_index(n, d, m, a, b)], x);
-    };
-    auto add_u = [&](int d, int m, int a, int b, int v, double x) {
-        if (m < 0) atomicAdd(&nbub[((2 * d) * V + v) * n2 + a + n * b], x);
-        else if (m >= n) atomicAdd(&nbub[((2 * d + 1) * V + v) * n2 + a + n * b], x);
-        else atomicAdd(&ubc[v * n3 + node_index(n, d, m, a, b)], x);
-    };
-    for (int t = threadIdx.x; t < 3 * n3; t += blockDim.x) {
-        const int d = t / n3, c = t % n3;
-        const int ijk[3] = {c % n, (c / n) % n, c / n2};
-        const int m = ijk[d];
-        const int a = d == 0 ? ijk[1] : ijk[0], b = d == 2 ? ijk[1] : ijk[2];
-        const double ilm = m > 0 ? il : sID[2 * d], ilp = m < n - 1 ? il : sID[2 * d + 1];
-        double wp[V], wm[V], wpb[V] = {}, wmb[V] = {}, rp[V], rm[V];
-        reconw(d, m, a, b, +1, wp);
-        reconw(d, m, a, b, -1, wm);
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            rp[v] = recb[((2 * d + 1) * V + v) * n3 + c];
-            rm[v] = recb[((2 * d) * V + v) * n3 + c];
-        }
-        w_to_cons_rev<NK>(P.ph, wp, rp, wpb);
-        w_to_cons_rev<NK>(P.ph, wm, rm, wmb);
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            // w+- = wc +- s l/2
-            const double sb = 0.5 * l * (wpb[v] - wmb[v]);
-            add_w(d, m, a, b, v, wpb[v] + wmb[v]);
-            const double wc = cellW(d, m, a, b, v);
-            const double ga = (wc - cellW(d, m - 1, a, b, v)) * ilm, gb = (cellW(d, m + 1, a, b, v) - wc) * ilp;
-            if (ga * gb > 0.0) {
-                if (fabs(ga) <= fabs(gb)) {
-                    add_w(d, m, a, b, v, sb * ilm);
-                    add_w(d, m - 1, a, b, v, -sb * ilm);
-                } else {
-                    add_w(d, m + 1, a, b, v, sb * ilp);
-                    add_w(d, m, a, b, v, -sb * ilp);
-                }
-            }
-        }
-        if (visc) {
-            // g_d(c) = (u(m+1) - u(m-1)) sc
-            const double sc = m == 0 ? sGS[2 * d] : (m == n - 1 ? sGS[2 * d + 1] : 0.5 * n * 0.5 * rh[d]);
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const double g = gradb[(d * V + v) * n3 + c] * sc;
-                add_u(d, m + 1, a, b, v, g);
-                add_u(d, m - 1, a, b, v, -g);
-            }
-        }
-    }
-    __syncthreads();
-    // 4. cons_to_w^T: the element's U_bar and the neighbour values' adjoints
-    for (int c = threadIdx.x; c < n3; c += blockDim.x) {
-        double u[V], wb[V], ub[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            u[v] = sU[v * n3 + c];
-            wb[v] = wbar[v * n3 + c];
-            ub[v] = ubc[v * n3 + c];
-        }
-        cons_to_w_rev<NK>(P.ph, u, wb, ub);
-#pragma unroll
-        for (int v = 0; v < V; ++v) Ub[off + (int64_t)v * n3 + c] = ub[v];
-    }
-    for (int i = threadIdx.x; i < 6 * n2; i += blockDim.x) {
-        const int f = i / n2, p = i % n2;
-        double u[V], wb[V], ub[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            u[v] = sNb[(f * V + v) * n2 + p];
-            wb[v] = nbwb[(f * V + v) * n2 + p];
-            ub[v] = nbub[(f * V + v) * n2 + p];
-        }
-        cons_to_w_rev<NK>(P.ph, u, wb, ub);
-#pragma unroll
-        for (int v = 0; v < V; ++v) nbub[(f * V + v) * n2 + p] = ub[v];
-    }
-}
-
-// k_adj_fv_gather: one CTA per element q; for every face of q with an FV
-// element e across, U_bar(q) += layer^T (the adjoint of the layer e read from q,
-// left by k_adj_fv in e's fbar slot facing q).
-template <int NK>
-__global__ void __launch_bounds__(128) k_adj_fv_gather(Params P, AdjBuffers A, double* __restrict__ Ub) {
-    constexpr int V = NK + 4;
-    __shared__ double sT1[V * MAXP * MAXP], sT2[V * MAXP * MAXP];
-    const int q = blockIdx.x, n = P.nfv, n2 = n * n;
-    for (int fq = 0; fq < 6; ++fq) {
-        const int e = P.t.nb[6 * q + fq];
-        if (e < 0 || !P.t.fv[e]) continue;
-        const double* lb = A.fbar + (P.t.fo[e] + (int64_t)(fq ^ 1) * n2) * V;
-        fv_layer_t<NK>(P, q, fq, n, lb, Ub, sT1, sT2);
-    }
-}
-
 // k_adj_prolong: U_bar += trace^T of the face-value adjoints.
 template <int NK>
 __global__ void __launch_bounds__(256) k_adj_prolong(Params P, AdjBuffers A, Tiles T, double* __restrict__ Ub) {
@@ -1079,25 +793,10 @@ void launch_adj_lift(int nk, const Params& P, const AdjBuffers& A, const Faces& 
     DGFV_DISPATCH(nk, (k_adj_lift<NK><<<nfaces, 64, 0, s>>>(P, A, F, list)));
 }
 
-size_t adj_fv_smem_bytes(int nk, int nfv) {
-    const int V = nk + 4, n2 = nfv * nfv, n3 = n2 * nfv;
-    return sizeof(double) * (size_t)(2 * V * n3 + 12 * V * n2 + 2 * V * MAXP * MAXP);
-}
-
 void launch_adj_surface_fv(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, const double* Rb,
                            cudaStream_t s) {
     if (ntiles <= 0) return;
     DGFV_DISPATCH(nk, (k_adj_surface_fv<NK><<<ntiles, 128, 0, s>>>(P, A, T, Rb)));
-}
-
-void launch_adj_fv_elements(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles,
-                            const double* U, const double* Rb, double* Ub, double* gf, double* gvol, double* fvs,
-                            int64_t cap_state, int n_elem, cudaStream_t s) {
-    if (ntiles <= 0) return;
-    const size_t sm = adj_fv_smem_bytes(nk, P.nfv);
-    DGFV_DISPATCH(nk, (cudaFuncSetAttribute(k_adj_fv<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
-                       k_adj_fv<NK><<<ntiles, 256, sm, s>>>(P, A, T, U, Rb, Ub, gf, gvol, fvs, cap_state),
-                       k_adj_fv_gather<NK><<<n_elem, 128, 0, s>>>(P, A, Ub)));
 }
 
 void launch_adj_prolong(int nk, const Params& P, const AdjBuffers& A, const Tiles& T, int ntiles, double* Ub,

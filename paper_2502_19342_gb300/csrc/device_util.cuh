@@ -141,6 +141,113 @@ __device__ __forceinline__ void fv_layer(const Params& P, const double* __restri
     face_map(sT1, nq, dst, n, A, V, sT2);
 }
 
+// The six neighbour layers of FV element e (n sub-cells per direction) into
+// sNb (6 x V n^2 conservative values, face-major), with the per-face
+// geometry: sID[f] = 1/distance and sGS[f] = rh_d/(l + distance), the
+// distance between the boundary sub-cell's centre and the neighbour layer's,
+// in e's reference coordinates (l = 2/n).  All six faces at once in three
+// passes separated by block barriers:
+//   (1) an FV neighbour of the same count: its boundary sub-cell means
+//       (its face values) straight into sNb; of another count (per-element
+//       counts): its layer into the scratch, mapped by its sub-cell overlaps;
+//       a DG neighbour: the boundary row of V^{DG->FV} along the face normal
+//       into the scratch, then V^{DG->FV} in both face directions; across a
+//       mortar: the values gathered beforehand into the slot;
+//   (2), (3) the two face directions of those maps (as face_map).
+// sT: 6 V (MAXP^2 + n MAXP) doubles of scratch; sMap, sNq: 6 entries of
+// shared memory each.  All threads of the block take part; ends with a
+// barrier.
+template <int NK>
+__device__ __forceinline__ void fv_gather_neighbours(const Params& P, const double* __restrict__ U, int e, int n,
+                                                     double* sNb, double* sT, double* sID, double* sGS,
+                                                     const double** sMap, int* sNq) {
+    constexpr int V = NK + 4;
+    const int n2 = n * n;
+    const double l = 2.0 / n;
+    const double* rh = P.t.rh + 3 * e;
+    if (threadIdx.x < 6) {
+        const int f = threadIdx.x, q = P.t.nb[6 * e + f];
+        int qe = q, nq = n;
+        const double* M = nullptr;
+        if (q < 0) {
+            qe = P.t.mnbe[-1 - q];
+        } else if (P.t.fv[q]) {
+            nq = P.t.n[q];
+            if (nq != n) M = B(P, P.bi.ov[nq][n]);
+        } else {
+            nq = P.t.n[q];
+            M = B(P, P.bi.d2f[nq][n]);
+        }
+        sMap[f] = M;
+        sNq[f] = nq;
+        // l/2 (1 + h_neighbour/h), l when the sizes agree; to an FV neighbour
+        // with another sub-cell count n_q (per-element counts) l/2 + (h_neighbour/h)/n_q
+        const int d = f >> 1;
+        const double hr = rh[d] / P.t.rh[3 * qe + d];
+        const int nqd = q >= 0 && P.t.fv[q] ? nq : n;
+        const double dist = nqd == n ? 0.5 * l * (1.0 + hr) : 0.5 * l + hr / nqd;
+        sID[f] = 1.0 / dist;
+        sGS[f] = rh[d] / (l + dist);
+    }
+    __syncthreads();
+    const int per_face = V * (MAXP * MAXP + n * MAXP);
+    for (int f = 0; f < 6; ++f) {
+        const int q = P.t.nb[6 * e + f], fq = f ^ 1, d = f >> 1, nq = sNq[f], nq2 = nq * nq;
+        double* dst = sNb + f * V * n2;
+        double* lay = sT + f * per_face;
+        if (q < 0) {
+            const double* src = P.t.mnb + (int64_t)(-1 - q) * V * n2;
+            for (int i = threadIdx.x; i < V * n2; i += blockDim.x) dst[i] = src[i];
+        } else if (P.t.fv[q]) {
+            const double* src = P.b.fu + (P.t.fo[q] + (int64_t)fq * nq2) * V;
+            double* to = sMap[f] ? lay : dst;
+            for (int i = threadIdx.x; i < V * nq2; i += blockDim.x) to[i] = src[i];
+        } else {
+            const int nq3 = nq2 * nq, row = (fq & 1) ? n - 1 : 0;  // sub-cell layer next to the shared face
+            const double* A = sMap[f];                                // n x nq
+            const double* src = U + P.t.off[q];
+            for (int i = threadIdx.x; i < V * nq2; i += blockDim.x) {
+                const int v = i / nq2, p = i % nq2, a = p % nq, b = p / nq;
+                double s = 0.0;
+                for (int m = 0; m < nq; ++m)
+                    s = fma(__ldg(A + row * nq + m), src[(int64_t)v * nq3 + node_index(nq, d, m, a, b)], s);
+                lay[i] = s;
+            }
+        }
+    }
+    __syncthreads();
+    for (int f = 0; f < 6; ++f) {  // first face direction of the maps: n x nq per variable
+        const double* M = sMap[f];
+        if (!M) continue;
+        const int nq = sNq[f], n1 = n * nq;
+        const double* lay = sT + f * per_face;
+        double* half = sT + f * per_face + V * MAXP * MAXP;
+        for (int i = threadIdx.x; i < V * n1; i += blockDim.x) {
+            const int x = i / n1, r = i % n1, ao = r % n, bi = r / n;
+            const double* in = lay + x * nq * nq + nq * bi;
+            double s = 0.0;
+            for (int ai = 0; ai < nq; ++ai) s = fma(__ldg(M + ao * nq + ai), in[ai], s);
+            half[x * n1 + ao + n * bi] = s;
+        }
+    }
+    __syncthreads();
+    for (int f = 0; f < 6; ++f) {  // second face direction, into the neighbour values
+        const double* M = sMap[f];
+        if (!M) continue;
+        const int nq = sNq[f], n1 = n * nq;
+        const double* half = sT + f * per_face + V * MAXP * MAXP;
+        double* dst = sNb + f * V * n2;
+        for (int i = threadIdx.x; i < V * n2; i += blockDim.x) {
+            const int x = i / n2, r = i % n2, ao = r % n, bo = r / n;
+            const double* in = half + x * n1 + ao;
+            double s = 0.0;
+            for (int bi = 0; bi < nq; ++bi) s = fma(__ldg(M + bo * nq + bi), in[n * bi], s);
+            dst[x * n2 + r] = s;
+        }
+    }
+    __syncthreads();
+}
+
 // Transpose of fv_layer: Ub (the state adjoint of element q) += layer^T lb,
 // lb the adjoint of the N_FV x N_FV layer across face fq.  FV element: the
 // boundary sub-cells; DG element: V^{DG->FV} transposed in both face

@@ -128,101 +128,11 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
     const int64_t off = P.t.off[e];
     const double* rh = P.t.rh + 3 * e;
     __shared__ double sID[6], sGS[6];  // per face: 1/distance to the neighbour's centre, rh/(l + distance)
-    __shared__ const double* sMap[6];  // per face: the map of the neighbour layer (null: copied as is)
-    __shared__ int sNq[6];             // per face: the layer's points per direction
+    __shared__ const double* sMap[6];
+    __shared__ int sNq[6];
     const double l = 2.0 / n, il = 0.5 * n;
     for (int i = threadIdx.x; i < V * n3; i += blockDim.x) sU[i] = U[off + i];
-    // neighbour values (across a mortar: gathered beforehand into the slot's values),
-    // all six faces at once in three passes:
-    //   (1) an FV neighbour of the same count: its boundary sub-cell means straight
-    //       into sNb; of another count (per-element counts): its layer into the
-    //       scratch, mapped by its sub-cell overlaps; a DG neighbour: the boundary
-    //       row of V^{DG->FV} along the face normal into the scratch, then
-    //       V^{DG->FV} in both face directions;
-    //   (2), (3) the two face directions of those maps.
-    if (threadIdx.x < 6) {
-        const int f = threadIdx.x, q = P.t.nb[6 * e + f];
-        int qe = q, nq = n;
-        const double* M = nullptr;
-        if (q < 0) {
-            qe = P.t.mnbe[-1 - q];
-        } else if (P.t.fv[q]) {
-            nq = P.t.n[q];
-            if (nq != n) M = B(P, P.bi.ov[nq][n]);
-        } else {
-            nq = P.t.n[q];
-            M = B(P, P.bi.d2f[nq][n]);
-        }
-        sMap[f] = M;
-        sNq[f] = nq;
-        // distance between the sub-cell centres in this element's reference
-        // coordinates: l/2 (1 + h_neighbour/h), l when the sizes agree; to an
-        // FV neighbour with another sub-cell count n_q (per-element counts)
-        // l/2 + (h_neighbour/h)/n_q
-        const int d = f >> 1;
-        const double hr = rh[d] / P.t.rh[3 * qe + d];
-        const int nqd = q >= 0 && P.t.fv[q] ? nq : n;
-        const double dist = nqd == n ? 0.5 * l * (1.0 + hr) : 0.5 * l + hr / nqd;
-        sID[f] = 1.0 / dist;
-        sGS[f] = rh[d] / (l + dist);
-    }
-    __syncthreads();
-    const int per_face = V * (MAXP * MAXP + n * MAXP);
-    for (int f = 0; f < 6; ++f) {
-        const int q = P.t.nb[6 * e + f], fq = f ^ 1, d = f >> 1, nq = sNq[f], nq2 = nq * nq;
-        double* dst = sNb + f * V * n2;
-        double* lay = sT + f * per_face;
-        if (q < 0) {
-            const double* src = P.t.mnb + (int64_t)(-1 - q) * V * n2;
-            for (int i = threadIdx.x; i < V * n2; i += blockDim.x) dst[i] = src[i];
-        } else if (P.t.fv[q]) {
-            const double* src = P.b.fu + (P.t.fo[q] + (int64_t)fq * nq2) * V;
-            double* to = sMap[f] ? lay : dst;
-            for (int i = threadIdx.x; i < V * nq2; i += blockDim.x) to[i] = src[i];
-        } else {
-            const int nq3 = nq2 * nq, row = (fq & 1) ? n - 1 : 0;  // sub-cell layer next to the shared face
-            const double* A = sMap[f];                                // n x nq
-            const double* src = U + P.t.off[q];
-            for (int i = threadIdx.x; i < V * nq2; i += blockDim.x) {
-                const int v = i / nq2, p = i % nq2, a = p % nq, b = p / nq;
-                double sacc = 0.0;
-                for (int m = 0; m < nq; ++m)
-                    sacc = fma(__ldg(A + row * nq + m), src[(int64_t)v * nq3 + node_index(nq, d, m, a, b)], sacc);
-                lay[i] = sacc;
-            }
-        }
-    }
-    __syncthreads();
-    for (int f = 0; f < 6; ++f) {  // first face direction of the maps: n x nq per variable
-        const double* M = sMap[f];
-        if (!M) continue;
-        const int nq = sNq[f], n1 = n * nq;
-        const double* lay = sT + f * per_face;
-        double* half = sT + f * per_face + V * MAXP * MAXP;
-        for (int i = threadIdx.x; i < V * n1; i += blockDim.x) {
-            const int x = i / n1, r = i % n1, ao = r % n, bi = r / n;
-            const double* in = lay + x * nq * nq + nq * bi;
-            double sacc = 0.0;
-            for (int ai = 0; ai < nq; ++ai) sacc = fma(__ldg(M + ao * nq + ai), in[ai], sacc);
-            half[x * n1 + ao + n * bi] = sacc;
-        }
-    }
-    __syncthreads();
-    for (int f = 0; f < 6; ++f) {  // second face direction, into the neighbour values
-        const double* M = sMap[f];
-        if (!M) continue;
-        const int nq = sNq[f], n1 = n * nq;
-        const double* half = sT + f * per_face + V * MAXP * MAXP;
-        double* dst = sNb + f * V * n2;
-        for (int i = threadIdx.x; i < V * n2; i += blockDim.x) {
-            const int x = i / n2, r = i % n2, ao = r % n, bo = r / n;
-            const double* in = half + x * n1 + ao;
-            double sacc = 0.0;
-            for (int bi = 0; bi < nq; ++bi) sacc = fma(__ldg(M + bo * nq + bi), in[n * bi], sacc);
-            dst[x * n2 + r] = sacc;
-        }
-    }
-    __syncthreads();
+    fv_gather_neighbours<NK>(P, U, e, n, sNb, sT, sID, sGS, sMap, sNq);
     auto cellU = [&](int d, int m, int a, int b, int v) -> double {
         if (m < 0) return sNb[((2 * d) * V + v) * n2 + a + n * b];
         if (m >= n) return sNb[((2 * d + 1) * V + v) * n2 + a + n * b];

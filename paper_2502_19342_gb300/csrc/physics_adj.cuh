@@ -361,7 +361,7 @@ DGFV_HD void cons_to_w_rev(const DevPhys& P, const double* u, const double* wb, 
     double wv[3];
     for (int i = 0; i < 3; ++i) wv[i] = u[NK + i] * irho;
     const double ke = 0.5 * (u[NK] * wv[0] + u[NK + 1] * wv[1] + u[NK + 2] * wv[2]);
-    const double q = (cpr - cvr) / cvr;
+    const double icvr = 1.0 / cvr, q = (cpr - cvr) * icvr;  // one division for q and its derivatives
     // w_p = q (u_E - ke)
     const double wpb = wb[NK + 3];
     const double qb = wpb * (u[NK + 3] - ke);
@@ -375,7 +375,7 @@ DGFV_HD void cons_to_w_rev(const DevPhys& P, const double* u, const double* wb, 
         irhob += wvb * u[NK + i];
     }
     // q = cpr/cvr - 1;  sums;  irho = 1/rho;  rho = sum u_k;  w_k = u_k
-    const double cprb = qb / cvr, cvrb = -qb * cpr / (cvr * cvr);
+    const double cprb = qb * icvr, cvrb = -qb * cpr * (icvr * icvr);
     const double rhob = -irhob * irho * irho;
     for (int k = 0; k < NK; ++k) ub[k] += wb[k] + cvrb * P.cv[k] + cprb * P.cp[k] + rhob;
 }
@@ -390,7 +390,7 @@ DGFV_HD void w_to_cons_rev(const DevPhys& P, const double* w, const double* ubar
         cvr = fma(w[k], P.cv[k], cvr);
         cpr = fma(w[k], P.cp[k], cpr);
     }
-    const double Dn = cpr - cvr, r = cvr / Dn;
+    const double Dn = cpr - cvr, iDn = 1.0 / Dn, r = cvr * iDn;  // one division for r and its derivatives
     // u_E = w_p r + ke;  ke = 1/2 rho |v|^2;  u_mi = rho v_i
     const double ueb = ubar[NK + 3];
     wb[NK + 3] += ueb * r;
@@ -403,7 +403,7 @@ DGFV_HD void w_to_cons_rev(const DevPhys& P, const double* w, const double* ubar
     }
     rhob += 0.5 * ueb * v2;
     // r = cvr / (cpr - cvr)
-    const double cvrb = rb * cpr / (Dn * Dn), cprb = -rb * cvr / (Dn * Dn);
+    const double rbD = rb * (iDn * iDn), cvrb = rbD * cpr, cprb = -rbD * cvr;
     for (int k = 0; k < NK; ++k) wb[k] += ubar[k] + cvrb * P.cv[k] + cprb * P.cp[k] + rhob;
 }
 
