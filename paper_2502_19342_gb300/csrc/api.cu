@@ -283,13 +283,15 @@ int upload_tiles(dgfv_ctx* c, TileSet& t) {
     return DGFV_OK;
 }
 
-// Group items by their point count n (ascending) and cut each group into tiles
-// of at most per_tile(n) items.
+// Group items by their point count n and cut each group into tiles of at most
+// per_tile(n) items.  The groups go in descending n: the block scheduler
+// dispatches tiles in order, so the heaviest tiles start first and the light
+// ones fill the tail of a mixed-degree launch (longest first).
 template <class Sel, class Per>
 void make_tiles(const dgfv_ctx* c, TileSet& t, Sel sel, Per per_tile) {
     t.first.clear(); t.count.clear(); t.items.clear(); t.n.clear();
     t.bin_first.clear(); t.bin_count.clear();
-    for (int n = 1; n <= MAXP; ++n) {
+    for (int n = MAXP; n >= 1; --n) {
         std::vector<int32_t> group;
         for (int e = 0; e < c->n_elem; ++e)
             if (c->npts[e] == n && sel(e)) group.push_back(e);
@@ -414,7 +416,7 @@ int apply_layout(dgfv_ctx* c) {
         t.first.clear(); t.count.clear(); t.items.clear(); t.nc.clear(); t.d.clear();
         t.bin_first.clear(); t.bin_count.clear();
         for (int d = 0; d < 3; ++d)
-            for (int n = 1; n <= MAXP; ++n) {
+            for (int n = MAXP; n >= 1; --n) {  // descending, as the element tiles
                 const auto& g = conf_by[d][n];
                 const int per = std::max(1, 256 / (n * n));
                 if (!g.empty()) {
