@@ -236,13 +236,17 @@ def _hybrid_problem(seed, nk=2, nel=(3, 2, 3), Nlo=1, Nhi=5, fv_frac=0.35, n_fv=
 
 @pytest.mark.parametrize("nk,mu,seed,riemann,n_fv,nodes,fv_frac", [
     (2, 3e-3, 31, 0, 6, 0, 0.35), (3, 0.0, 32, 0, 7, 0, 0.35), (2, 2e-3, 33, 1, 6, 0, 0.35),
-    (3, 3e-3, 34, 2, 8, 0, 0.35), (1, 1e-3, 35, 0, 6, 1, 0.35), (2, 2e-3, 36, 2, 6, 0, 1.0)])
+    (3, 3e-3, 34, 2, 8, 0, 0.35), (1, 1e-3, 35, 0, 6, 1, 0.35), (2, 2e-3, 36, 2, 6, 0, 1.0),
+    (2, 2e-3, 38, 0, 9, 0, 0.35)])
 def test_rhs_vjp_with_fv_elements_dot_product(oracle, nk, mu, seed, riemann, n_fv, nodes, fv_frac):
     """Hybrid DG/FV patterns frozen in the backward (Sec. 3.1.2, 3.2): the FV
     sub-cell operator reversed (minmod along the forward's branches, central
     differences, sub-cell Riemann and viscous fluxes), the DG/FV face and lifting
     maps transposed, against the oracle's exact dual-number JVP; LLF, Roe-HH
-    and the hybrid flux choice; an all-FV mesh."""
+    and the hybrid flux choice; an all-FV mesh.  N_FV = 6, 7 run the FV reverse
+    with the sub-cell gradients kept in shared memory, 8 and 9 with the
+    gradients formed at each face (two CTAs of 128 threads per SM, and one of
+    256)."""
     prob, U = _hybrid_problem(seed, nk=nk, mu=mu, riemann=riemann, n_fv=n_fv, nodes=nodes, fv_frac=fv_frac)
     rng = np.random.default_rng(seed)
     Rbar = rng.standard_normal(U.size)

@@ -201,7 +201,8 @@ def test_rhs_vjp_on_mortar_chain_dot_product(oracle, seed, mu, nodes):
     ctx.close()
 
 
-@pytest.mark.parametrize("seed,mu,riemann,n_fv", [(24, 2e-3, 0, 6), (25, 0.0, 2, 7), (26, 3e-3, 1, 6)])
+@pytest.mark.parametrize("seed,mu,riemann,n_fv", [(24, 2e-3, 0, 6), (25, 0.0, 2, 7), (26, 3e-3, 1, 6),
+                                                (27, 2e-3, 1, 8)])
 def test_rhs_vjp_on_mortar_chain_with_fv_elements(oracle, seed, mu, riemann, n_fv):
     """Hybrid DG/FV patterns on every mortar type: the FV big and small sides'
     maps (M^FV), the neighbour values gathered across mortars, transposed;
