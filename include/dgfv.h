@@ -176,7 +176,11 @@ int dgfv_state_layout(dgfv_ctx* ctx, int64_t* n_doubles, const int64_t** d_elem_
 
 /* Copies n doubles (must equal the layout size) into / out of the context's
  * state.  d_U is device memory, or host memory for the *_host variants
- * (which synchronise the stream). */
+ * (which synchronise the stream).  Page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister, a pinned torch tensor) is copied by a kernel on every SM
+ * through its device mapping (full C2C bandwidth also on the first copy after
+ * heavy GPU work, when the copy engines first refill the address translations
+ * of the buffer's pages); pageable host memory by cudaMemcpyAsync. */
 int dgfv_set_state(dgfv_ctx* ctx, const double* d_U, int64_t n, void* stream);
 int dgfv_get_state(dgfv_ctx* ctx, double* d_U, int64_t n, void* stream);
 int dgfv_set_state_host(dgfv_ctx* ctx, const double* h_U, int64_t n, void* stream);

@@ -981,13 +981,42 @@ int dgfv_state_layout(dgfv_ctx* c, int64_t* n_doubles, const int64_t** d_elem_of
     return DGFV_OK;
 }
 
+// The device address of page-locked host memory (cudaHostAlloc,
+// cudaHostRegister), or null for pageable memory.
+static void* host_device_view(const void* h) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+        cudaGetLastError();  // clear: an unknown pointer is pageable memory here
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// State copies.  Host buffers in page-locked memory are copied by a kernel on
+// every SM through their device mapping, pageable ones by cudaMemcpyAsync.
+// Measured on a GB300 (Grace host, 64 KB pages, 715 MB of state): after a
+// cycle of GPU work the copy engines took 24-43 ms for the first copy of the
+// buffer and 3.6-4.0 ms when it was repeated at once (the device's
+// translations of the buffer's host pages are refilled in sequence), the SM
+// copy 3.8-4.5 ms in both cases.
 static int copy_state(dgfv_ctx* c, void* dst, const void* src, int64_t n, cudaMemcpyKind kind, void* stream,
                       bool sync) {
     if (!c || (!dst && n > 0) || (!src && n > 0)) return DGFV_ERR_ARG;
     TRY(check_dev(c));
     if (n != c->n_state) return fail(c, DGFV_ERR_ARG, "state size does not match the layout");
     cudaStream_t s = (cudaStream_t)stream;
-    CK(cudaMemcpyAsync(dst, src, n * sizeof(double), kind, s));
+    void* hv = nullptr;
+    if (n > 0 && kind == cudaMemcpyHostToDevice) hv = host_device_view(src);
+    if (n > 0 && kind == cudaMemcpyDeviceToHost) hv = host_device_view(dst);
+    if (hv) {
+        if (kind == cudaMemcpyHostToDevice)
+            launch_copy_state(static_cast<double*>(dst), static_cast<const double*>(hv), n, c->n_sm, s);
+        else
+            launch_copy_state(static_cast<double*>(hv), static_cast<const double*>(src), n, c->n_sm, s);
+        CK(cudaGetLastError());
+    } else {
+        CK(cudaMemcpyAsync(dst, src, n * sizeof(double), kind, s));
+    }
     if (sync) CK(cudaStreamSynchronize(s));
     return DGFV_OK;
 }

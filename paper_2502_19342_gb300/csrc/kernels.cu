@@ -938,6 +938,27 @@ __global__ void k_dt_final(const double* __restrict__ partial, int nb, int visco
 
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
+// Copy of n doubles by every thread of a grid-stride loop, 16 bytes per
+// access (both pointers 16-byte aligned; the odd last element by thread 0),
+// for the state copies between device memory and page-locked host memory
+// seen through its device mapping.
+__global__ void __launch_bounds__(256) k_copy_state2(double* __restrict__ dst, const double* __restrict__ src,
+                                                     int64_t n) {
+    const int64_t n2 = n >> 1;
+    double2* d2 = reinterpret_cast<double2*>(dst);
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
+        d2[i] = s2[i];
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) dst[n - 1] = src[n - 1];
+}
+
+// The same, 8 bytes per access (a pointer not 16-byte aligned).
+__global__ void __launch_bounds__(256) k_copy_state1(double* __restrict__ dst, const double* __restrict__ src,
+                                                     int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
 // Decision thresholds of Sec. 3.4: FV on / FV off (on I_h), refine / coarsen (on I_rho).
 struct Thresholds {
     double fv_on, fv_off, ref, crs;
@@ -1389,6 +1410,17 @@ void launch_dt(int nk, const Params& P, const Tiles& T, int ntiles, const double
 }
 
 void launch_set_scalar(double* p, double v, cudaStream_t s) { k_set_scalar<<<1, 1, 0, s>>>(p, v); }
+
+void launch_copy_state(double* dst, const double* src, int64_t n, int n_sm, cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t per = ((((uintptr_t)dst | (uintptr_t)src) & 15) == 0) ? 2 : 1;
+    const int64_t need = (n / per + 255) / 256;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)n_sm * 8));
+    if (per == 2)
+        k_copy_state2<<<blocks, 256, 0, s>>>(dst, src, n);
+    else
+        k_copy_state1<<<blocks, 256, 0, s>>>(dst, src, n);
+}
 
 void launch_pp_limit(int nk, const Params& P, const int32_t* items, int n_dg, double* U, double eps,
                      unsigned long long* count, bool write_faces, cudaStream_t s) {

@@ -48,6 +48,9 @@ void launch_dt(int nk, const Params& P, const Tiles& T, int ntiles, const double
 void launch_pp_limit(int nk, const Params& P, const int32_t* items, int n_dg, double* U, double eps,
                      unsigned long long* count, bool write_faces, cudaStream_t s);
 void launch_set_scalar(double* p, double v, cudaStream_t s);
+// n doubles from src to dst by a grid-stride kernel on every SM (device
+// memory, or page-locked host memory through its device mapping).
+void launch_copy_state(double* dst, const double* src, int64_t n, int n_sm, cudaStream_t s);
 // Time step with the per-block minima in a fixed device array (no allocation).
 // Returns 0, 1 when ntiles exceeds DT_NOALLOC_MAX_BLOCKS, 2 on a CUDA error.
 constexpr int DT_NOALLOC_MAX_BLOCKS = 65536;
