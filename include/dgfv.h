@@ -308,11 +308,15 @@ int dgfv_profile_read(dgfv_ctx* ctx, double* ms, int64_t* launches, int cap);
 int dgfv_set_launch_mode(dgfv_ctx* ctx, int mode);
 
 /* Shared-memory layout of the FV sub-cell kernel (Sec. 3.1.2, Eq. 26):
- * variant 0 (the default) chooses by the shared memory one element needs;
- * 1 recomputes the central-difference gradient of a sub-cell at each of its
- * faces; 2 keeps every sub-cell's gradient in shared memory (one CTA per SM;
- * falls back to 1 where that layout does not fit).  Results agree to
- * rounding.  Errors: DGFV_ERR_ARG for another value. */
+ * variant 0 (the default) chooses by the shared memory one element needs
+ * (3 where it fits, else 2, else 1); 1 recomputes the central-difference
+ * gradient of a sub-cell at each of its faces; 2 keeps every sub-cell's
+ * gradient in shared memory (one CTA of 512 threads per SM; falls back to 1
+ * where that layout does not fit); 3 keeps them and runs the z faces in a
+ * second pass, so that two CTAs of 256 threads fit per SM (N_FV != 8 only;
+ * falls back to the automatic choice elsewhere).  2 and 3 give identical
+ * results, 1 agrees with them to rounding.  Errors: DGFV_ERR_ARG for another
+ * value. */
 int dgfv_set_fv_variant(dgfv_ctx* ctx, int variant);
 
 /* Chooses the launch variant of the volume kernel (bit 0: 128 instead of 256

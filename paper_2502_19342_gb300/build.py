@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libdgfv.so")
-SOURCES = ["kernels.cu", "volume.cu", "adjoint.cu", "adjoint_fv.cu", "api.cu", "bank.cpp"]
+SOURCES = ["kernels.cu", "fv.cu", "volume.cu", "adjoint.cu", "adjoint_fv.cu", "api.cu", "bank.cpp"]
 DEPS = SOURCES + ["kernels.h", "adjoint.h", "common.cuh", "device_util.cuh", "physics.cuh", "physics_adj.cuh", "bank.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -119,7 +119,7 @@ struct dgfv_ctx {
                                    // 2: as 0 with the volume kernel persistent (work queue)
     int* d_queue = nullptr;        // work-queue counter of the persistent volume kernel
     int n_sm = 1;                  // SMs of the context's device
-    int fv_variant = 0;            // k_fv layout: 0 automatic, 1 gradients recomputed, 2 gradients kept
+    int fv_variant = 0;            // k_fv layout: 0 automatic, 1 gradients recomputed, 2 kept, 3 kept + two face passes
     int vol_per_tile[MAXDG + 1] = {};  // elements per volume tile (0: default), set by the autotuner
     int vol_variant = 0;              // volume-kernel launch variant (threads, register budget), autotuned
     bool state_valid = false;
@@ -1390,7 +1390,7 @@ int dgfv_set_launch_mode(dgfv_ctx* c, int mode) {
 }
 
 int dgfv_set_fv_variant(dgfv_ctx* c, int variant) {
-    if (!c || variant < 0 || variant > 2) return DGFV_ERR_ARG;
+    if (!c || variant < 0 || variant > 3) return DGFV_ERR_ARG;
     c->fv_variant = variant;
     c->graph_valid = false;
     return DGFV_OK;

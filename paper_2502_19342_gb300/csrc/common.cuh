@@ -133,7 +133,10 @@ struct FvLayout {
 __host__ __device__ __forceinline__ FvLayout fv_layout(int V, int n, int gs) {
     // tmp: the neighbour gather's scratch, per face a layer of at most MAXP^2
     // points and its half-mapped form (n x MAXP) for all six faces at once
-    const int n2 = n * n, n3 = n2 * n, tmp = 6 * V * (MAXP * MAXP + n * MAXP), fl = 3 * V * (n - 1) * n2;
+    // fl: the interior face fluxes of the three directions (of two with gs = 2,
+    // which runs the z faces in a second pass)
+    const int n2 = n * n, n3 = n2 * n, tmp = 6 * V * (MAXP * MAXP + n * MAXP),
+              fl = (gs == 2 ? 2 : 3) * V * (n - 1) * n2;
     FvLayout L;
     if (gs) {
         const int gsz = 3 * V * n3 > tmp ? 3 * V * n3 : tmp;

@@ -360,7 +360,8 @@ class Context:
         self._rc(lib().dgfv_sync_status(self.h, _stream(stream)), "device status")
 
     def set_fv_variant(self, variant):
-        """FV sub-cell kernel layout: 0 automatic, 1 gradients recomputed at each face, 2 gradients kept."""
+        """FV sub-cell kernel layout: 0 automatic, 1 gradients recomputed at each face, 2 gradients kept,
+        3 gradients kept with the z faces in a second pass (two CTAs per SM)."""
         self._rc(lib().dgfv_set_fv_variant(self.h, int(variant)), "set_fv_variant")
 
     def set_launch_mode(self, mode):

@@ -64,12 +64,13 @@ def test_rhs_mixed_hp_fv(oracle, nk, riemann, mu, seed, nodes, split):
     assert_rhs_close(oracle, prob, U, gpu_rhs(prob, U))
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("nk,n_fv,riemann,mu", [(2, 7, 0, 2e-3), (3, 8, 2, 2e-3), (2, 9, 0, 1e-3),
                                                  (3, 5, 1, 3e-3), (1, 8, 0, 0.0)])
 def test_fv_kernel_layouts_match_oracle(oracle, variant, nk, n_fv, riemann, mu):
-    """Both shared-memory layouts of the FV sub-cell kernel (gradients
-    recomputed at each face / kept per sub-cell) on a hybrid mesh with 40 % FV
+    """The shared-memory layouts of the FV sub-cell kernel (gradients
+    recomputed at each face / kept per sub-cell / kept, with the z faces in a
+    second pass where two CTAs then fit per SM) on a hybrid mesh with 40 % FV
     elements, N_FV = 5, 7, 8, 9: R(U) against the oracle at the bar of R."""
     sp = W.species_set([W.AIR, W.HELIUM, W.CO2][:nk], mu=mu)
     n = 3 * 3 * 4
@@ -83,6 +84,32 @@ def test_fv_kernel_layouts_match_oracle(oracle, variant, nk, n_fv, riemann, mu):
     R = ctx.eval_rhs(to_dev(U)).cpu().numpy()
     ctx.close()
     assert_rhs_close(oracle, prob, U, R)
+
+
+@pytest.mark.parametrize("nk,n_fv", [(2, 7), (3, 5), (1, 6)])
+def test_fv_two_pass_layout_is_the_kept_gradient_layout_bit_for_bit(nk, n_fv):
+    """The z faces in a second pass, the first pass's flux differences kept in
+    the cell's row: the same sums in the same order as one pass, so R(U) and
+    an SSP-RK3 step are bitwise those of the one-pass layout."""
+    sp = W.species_set([W.AIR, W.HELIUM, W.CO2][:nk], mu=2e-3)
+    n = 3 * 3 * 4
+    N = W.random_degrees(n, 1, n_fv - 1, 60 + n_fv)
+    prob = W.make_problem([((3, 3, 4), (0, 0, 0), (1.0, 0.9, 1.2))], sp, n_fv=n_fv, N=N,
+                          fv=W.random_fv(n, 0.5, 60 + n_fv))
+    U = to_dev(W.smooth_random_state(prob, 60 + n_fv, amp=0.15))
+    from paper_2502_19342_gb300 import dgfv
+    out = []
+    for variant in (2, 3):
+        ctx = dgfv.Context(prob)
+        ctx.set_fv_variant(variant)
+        R = ctx.eval_rhs(U)
+        ctx.set_state(U)
+        dt = 0.5 * ctx.compute_dt(U)[0]
+        ctx.rk_step(dt, want_dt=False)
+        out.append((R, ctx.get_state()))
+        ctx.close()
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
 
 
 def test_rhs_batched_domains(oracle):
