@@ -307,17 +307,42 @@ def adjoint_cost(steps=50):
         ctx.rk_step_vjp_stages((ck[k], *st[k]), dt, a, b)
         a = b
     ev[6].record(s)
+    grad_stored = a.clone()
+    # segment checkpoints: every K-th state of the plain forward (ck[0], ck[K],
+    # ...); the backward pass steps each segment forward again from its
+    # checkpoint into K buffers, then runs its step adjoints
+    K = max(1, int(round(steps ** 0.5)))
+    seg = [torch.empty_like(Ud) for _ in range(K)]
+    ev7, ev8 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev7.record(s)
+    a = g
+    for sg in range((steps - 1) // K, -1, -1):
+        first, last = sg * K, min(sg * K + K, steps)
+        seg[0].copy_(ck[first])
+        ctx.set_state(seg[0])
+        for j in range(1, last - first):
+            ctx.rk_step(dt, want_dt=False)
+            ctx.get_state(seg[j])
+        for kk in range(last - 1, first - 1, -1):
+            b = lam[kk % 2]
+            ctx.rk_step_vjp(seg[kk - first], dt, a, b)
+            a = b
+    ev8.record(s)
     torch.cuda.synchronize()
     fwd, bwd, fsave, bwd2 = (ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3]), ev[4].elapsed_time(ev[5]),
                              ev[5].elapsed_time(ev[6]))
-    same = bool(torch.equal(grad_recomputed, a))
+    bwd3 = ev7.elapsed_time(ev8)
+    same = bool(torch.equal(grad_recomputed, grad_stored) and torch.equal(grad_recomputed, a))
     dofs = W.n_dofs(prob)
+    gb = Ud.numel() * 8 / 1e9
     ctx.close()
-    return {"steps": steps, "dofs": dofs, "stage_gb": r4(3 * steps * Ud.numel() * 8 / 1e9),
+    return {"steps": steps, "dofs": dofs, "stage_gb": r4(3 * steps * gb), "ckpt_gb": r4(steps * gb),
             "fwd_ms_step": r4(fwd / steps), "fwd_keep_ms_step": r4(fsave / steps),
             "adj_ms_step_stored": r4(bwd2 / steps), "adj_over_fwd_stored": r4(bwd2 / fwd),
             "adj_ms_step_recomputed": r4(bwd / steps), "adj_over_fwd_recomputed": r4(bwd / fwd),
-            "gradients_identical": same}
+            "segment_every": K, "segment_gb": r4(((steps + K - 1) // K + K) * gb),
+            "adj_over_fwd_segments": r4(bwd3 / fwd), "gradients_identical": same}
 
 
 def adjoint_hybrid_cost(steps=10):

@@ -433,27 +433,50 @@ def rhs_function():
     return RHS
 
 
-def rollout_gradient(ctx, U0, n_steps, dt, loss_grad, keep_stages=False):
+def rollout_gradient(ctx, U0, n_steps, dt, loss_grad, keep_stages=False, checkpoint_every=1):
     """Gradient of a loss of the state after n_steps SSP-RK3 steps of size dt
     with respect to the initial state, by the adjoint of every step.
-    keep_stages=False keeps one checkpoint per step (the stage states are
-    recomputed in the backward pass); True keeps all three stage states per
-    step (three times the memory, no recomputation).
-    loss_grad(U_final) returns dLoss/dU_final."""
+    keep_stages=False keeps one checkpoint every `checkpoint_every` steps: with
+    1 (the default) the state at the start of every step, whose stage states
+    the backward pass recomputes; with k > 1 every k-th state, the backward
+    pass stepping each segment forward again from its checkpoint to recover
+    its step states (n_steps/k + k states in memory instead of n_steps, for one
+    more forward pass; the forward is deterministic, so the gradient is bitwise
+    the same).  keep_stages=True keeps all three stage states per step (three
+    times the memory of k = 1, no recomputation).
+    loss_grad(U_final) returns dLoss/dU_final.  Returns (gradient, U_final);
+    the context's state is U_final afterwards."""
     import torch
+    k = int(checkpoint_every)
+    if k < 1 or (keep_stages and k != 1):
+        raise ValueError("checkpoint_every must be >= 1 (and 1 with keep_stages)")
     ctx.set_state(U0)
     ckpt = []
-    for _ in range(n_steps):
-        U = ctx.get_state()
+    for s in range(n_steps):
         if keep_stages:
+            U = ctx.get_state()
             s1, s2 = torch.empty_like(U), torch.empty_like(U)
             ctx.rk_step_save(dt, s1, s2)
             ckpt.append((U, s1, s2))
         else:
+            if s % k == 0:
+                ckpt.append(ctx.get_state())
             ctx.rk_step(dt, want_dt=False)
-            ckpt.append(U)
     Uf = ctx.get_state()
     lam = loss_grad(Uf)
-    for k in range(n_steps - 1, -1, -1):
-        lam = ctx.rk_step_vjp_stages(ckpt[k], dt, lam) if keep_stages else ctx.rk_step_vjp(ckpt[k], dt, lam)
+    if keep_stages:
+        for s in range(n_steps - 1, -1, -1):
+            lam = ctx.rk_step_vjp_stages(ckpt[s], dt, lam)
+    else:
+        for seg in range((n_steps - 1) // k if n_steps else -1, -1, -1):
+            first, last = seg * k, min(seg * k + k, n_steps)
+            states = [ckpt[seg]]
+            if last - first > 1:
+                ctx.set_state(ckpt[seg])
+                for _ in range(first, last - 1):
+                    ctx.rk_step(dt, want_dt=False)
+                    states.append(ctx.get_state())
+            for s in range(last - 1, first - 1, -1):
+                lam = ctx.rk_step_vjp(states[s - first], dt, lam)
+    ctx.set_state(Uf)
     return lam, Uf

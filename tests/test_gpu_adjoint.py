@@ -325,7 +325,9 @@ def test_rk_step_vjp_with_fv_elements_dot_product(oracle):
 def test_stored_stage_adjoint_matches_recomputed_stages():
     """dgfv_rk_step_save advances the state exactly as dgfv_rk_step and keeps
     U1, U2; the adjoint from those stored stages equals, bit for bit, the
-    adjoint that recomputes them (same kernels on the same inputs)."""
+    adjoint that recomputes them (same kernels on the same inputs); so does a
+    rollout gradient from segment checkpoints (every k-th state kept, the
+    others stepped again in the backward pass)."""
     from paper_2502_19342_gb300 import dgfv
     prob, U = _dg_problem(10, nk=3, nel=(3, 2, 2), uniform=None, mu=2e-3)
     dt = 2e-4
@@ -347,4 +349,14 @@ def test_stored_stage_adjoint_matches_recomputed_stages():
     g1, _ = dgfv.rollout_gradient(ctx, U0, 3, dt, lambda Uf: torch.ones_like(Uf))
     g2, _ = dgfv.rollout_gradient(ctx, U0, 3, dt, lambda Uf: torch.ones_like(Uf), keep_stages=True)
     assert torch.equal(g1, g2)
+    # segment checkpoints (every 2nd, every 3rd state, one for the whole
+    # rollout): the step states recomputed bitwise, so the same gradient
+    w = to_dev(np.random.default_rng(11).standard_normal(U.size))
+    ref, Uf = dgfv.rollout_gradient(ctx, U0, 7, dt, lambda X: w * X)
+    for k in (2, 3, 7, 9):
+        g, Ufk = dgfv.rollout_gradient(ctx, U0, 7, dt, lambda X: w * X, checkpoint_every=k)
+        assert torch.equal(g, ref), k
+        assert torch.equal(Ufk, Uf) and torch.equal(ctx.get_state(), Uf)
+    with pytest.raises(ValueError):
+        dgfv.rollout_gradient(ctx, U0, 3, dt, lambda X: X, keep_stages=True, checkpoint_every=2)
     ctx.close()
