@@ -90,14 +90,21 @@ DGFV_HD void prim(const DevPhys& P, const double* u, Prim<NK>& s) {
 }
 
 // Convective flux in direction d.
+// x[d] of a 3-vector by selects: indexed with a direction known only at run
+// time, an array (and the structure holding it) would be placed in local
+// memory; with a compile-time d this is x[d].
+DGFV_HD double pick3(const double* x, int d) { return d == 0 ? x[0] : (d == 1 ? x[1] : x[2]); }
+
 template <int NK>
 DGFV_HD void flux_conv(const double* u, const Prim<NK>& s, int d, double* F) {
-    const double vd = s.v[d];
+    const double vd = pick3(s.v, d);
 #pragma unroll
     for (int k = 0; k < NK; ++k) F[k] = u[k] * vd;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) F[NK + i] = u[NK + i] * vd;
-    F[NK + d] += s.p;
+    for (int i = 0; i < 3; ++i) {
+        F[NK + i] = u[NK + i] * vd;
+        if (i == d) F[NK + i] += s.p;
+    }
     F[NK + 3] = (u[NK + 3] + s.p) * vd;
 }
 
@@ -249,7 +256,7 @@ DGFV_HD void riemann_llf(const double* uL, const Prim<NK>& sL, const double* uR,
     double FL[V], FR[V];
     flux_conv<NK>(uL, sL, d, FL);
     flux_conv<NK>(uR, sR, d, FR);
-    const double aL = fabs(sL.v[d]) + sL.c, aR = fabs(sR.v[d]) + sR.c;
+    const double aL = fabs(pick3(sL.v, d)) + sL.c, aR = fabs(pick3(sR.v, d)) + sR.c;
     const double smax = aL > aR ? aL : aR;
 #pragma unroll
     for (int v = 0; v < V; ++v) F[v] = 0.5 * ((FL[v] + FR[v]) - smax * (uR[v] - uL[v]));
@@ -301,13 +308,14 @@ DGFV_HD void riemann_roe(const DevPhys& P, const double* uL, const Prim<NK>& sL,
     const double ct = sqrt(c2);
     const double ic2 = 1.0 / c2;
     const double rt = rL * rR;
-    const double vn = vt[d];
+    const double vn = pick3(vt, d);
     const double dp = sR.p - sL.p;
     double dv[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) dv[i] = sR.v[i] - sL.v[i];
-    const double am = 0.5 * (dp - rt * ct * dv[d]) * ic2;
-    const double ap = 0.5 * (dp + rt * ct * dv[d]) * ic2;
+    const double dvn = pick3(dv, d);
+    const double am = 0.5 * (dp - rt * ct * dvn) * ic2;
+    const double ap = 0.5 * (dp + rt * ct * dvn) * ic2;
     auto hh = [](double lt, double lL, double lR) {
         double delta = 0.0;
         delta = fmax(delta, lt - lL);
@@ -315,8 +323,9 @@ DGFV_HD void riemann_roe(const DevPhys& P, const double* uL, const Prim<NK>& sL,
         const double a = fabs(lt);
         return a < delta ? delta : a;
     };
-    const double lm = hh(vn - ct, sL.v[d] - sL.c, sR.v[d] - sR.c);
-    const double lp = hh(vn + ct, sL.v[d] + sL.c, sR.v[d] + sR.c);
+    const double vLn = pick3(sL.v, d), vRn = pick3(sR.v, d);
+    const double lm = hh(vn - ct, vLn - sL.c, vRn - sR.c);
+    const double lp = hh(vn + ct, vLn + sL.c, vRn + sR.c);
     const double l0 = fabs(vn);
     const double sa = lm * am + lp * ap;
     const double sd = (lp * ap - lm * am) * ct;
@@ -324,8 +333,10 @@ DGFV_HD void riemann_roe(const DevPhys& P, const double* uL, const Prim<NK>& sL,
 #pragma unroll
     for (int k = 0; k < NK; ++k) Dis[k] = sa * Yt[k];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) Dis[NK + i] = sa * vt[i];
-    Dis[NK + d] += sd;
+    for (int i = 0; i < 3; ++i) {
+        Dis[NK + i] = sa * vt[i];
+        if (i == d) Dis[NK + i] += sd;
+    }
     Dis[NK + 3] = sa * Ht + sd * vn;
     // contact waves
     const double ecoef = -Tbar / km1;
