@@ -4,12 +4,12 @@
 //   k_prolong    face values: DG traces u(+-1) (Sec. 3.1.1), FV boundary sub-cell means
 //                (fused into the previous stage's k_surface within a step)
 //   k_fv         FV sub-cell elements (Sec. 3.1.2): minmod reconstruction, central
-//                gradients, interior sub-cell fluxes, element-face states
+//                gradients, interior sub-cell fluxes, element-face states (fv.cu)
 //   k_face_lift* BR1 lifting value U* = (u- + u+)/2 (Eq. 19) on the lower degree /
 //                on DG data at DG/FV faces (Sec. 3.2.2)
 //   k_dg_volume  lifting (Eq. 23) -> gradient in shared memory -> fluxes at the nodes
 //                -> volume integral (Eq. 22); traces of the gradient
-//                (k_dg_volume_split: the split form on LGL nodes, Sec. 3.5)
+//                (k_dg_volume_split: the split form on LGL nodes, Sec. 3.5; volume.cu)
 //   k_face_flux_conf, k_mixed_*
 //                F* = F^c* + (F^v- + F^v+)/2 (Eqs. 20, 21) on the higher degree / on
 //                FV data (Sec. 3.2.1), mapped back to both sides

@@ -1,4 +1,5 @@
-// Host-side launchers of the kernels in kernels.cu (no torch types).
+// Host-side launchers of the forward kernels (kernels.cu, fv.cu, volume.cu; no
+// torch types).
 #pragma once
 
 #include <cuda_runtime.h>
