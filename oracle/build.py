@@ -3,6 +3,7 @@
 TEST INFRASTRUCTURE ONLY: the oracle is the reference the CUDA path is checked
 against; nothing in the product path loads it.
 """
+import fcntl
 import os
 import subprocess
 import sys
@@ -22,18 +23,26 @@ def _stale() -> bool:
 
 
 def build(force: bool = False) -> str:
-    """Build the oracle library if it is missing or older than its sources."""
+    """Build the oracle library if it is missing or older than its sources
+    (concurrent callers serialise on a lock file)."""
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
-    tmp = LIB + f".tmp{os.getpid()}"
-    # -ffp-contract=off: no fused multiply-add contraction, so x86 and Arm hosts
-    # round identically.
-    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-           "-o", tmp] + [os.path.join(HERE, s) for s in SOURCES]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    with open(os.path.join(OUT_DIR, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and not _stale():
+                return LIB
+            tmp = LIB + f".tmp{os.getpid()}"
+            # -ffp-contract=off: no fused multiply-add contraction, so x86 and Arm
+            # hosts round identically.
+            cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                   "-o", tmp] + [os.path.join(HERE, s) for s in SOURCES]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, LIB)
+            return LIB
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
 
 
 if __name__ == "__main__":

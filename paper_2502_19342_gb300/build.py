@@ -3,6 +3,7 @@
 Compiles for sm_103a only (GB300), translation units in parallel, no cmake.
 """
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -46,11 +47,23 @@ def _compile(src, extra):
 
 
 def build(force=False, verbose=False, extra=()):
-    """Compile the library if it is missing or older than its sources; returns its path."""
+    """Compile the library if it is missing or older than its sources; returns its path.
+    Concurrent callers (one process per rank) serialise on a lock file, and a
+    caller that waited finds the library built."""
     if not force and not _stale():
         return LIB
     os.makedirs(OUT, exist_ok=True)
-    extra = list(extra)
+    with open(os.path.join(OUT, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and not _stale():
+                return LIB
+            return _build_locked(verbose, list(extra))
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose, extra):
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         results = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     if verbose:
