@@ -68,10 +68,11 @@ __host__ __device__ inline AdjFvLayout adj_fv_layout(int V, int n, int gs) {
 //   4. cons_to_w^T: the element's U_bar (written), and the neighbour values'
 //      adjoints in conservative variables, left in the element's fbar slots for
 //      k_adj_fv_gather.
-// The reconstructed values follow k_fv's arithmetic (a half slope
-// minmod(dw-, dw+)/2 inside the element, l/2 minmod(dw-/dist-, dw+/dist+) in
-// the boundary sub-cells).  Scratch in global memory, in the element's own
-// regions of the adjoint buffers the DG kernels do not use for FV elements:
+// The reconstructed values and their states follow k_fv's arithmetic (a half
+// slope minmod(dw-, dw+)/2 inside the element, l/2 minmod(dw-/dist-,
+// dw+/dist+) in the boundary sub-cells; face_state).  Scratch in global
+// memory, in the element's own regions of the adjoint buffers the DG kernels
+// do not use for FV elements:
 // rec_bar (6V n^3) in gf, grad_bar (3V n^3) in gvol, w_bar and the direct
 // u_bar (2 x V n^3) in fvs; the neighbour adjoints in the element's sbar
 // (reconstruction variables) and fbar (conservative) face slots.  Sums over
@@ -191,12 +192,13 @@ __global__ void __launch_bounds__(256) k_adj_fv(Params P, AdjBuffers A, Tiles T,
         const int cL = node_index(n, d, m, a, b), cR = node_index(n, d, m + 1, a, b);
         double uL[V], uR[V], Fb[V];
         double uLb[V] = {}, uRb[V] = {};
+        Prim<NK> sL, sR;  // as k_fv forms them (face_state: one division each)
         {
-            double wL[V], wR[V];
-            reconw(d, m, a, b, +1, wL);
-            reconw(d, m + 1, a, b, -1, wR);
-            w_to_cons<NK>(P.ph, wL, uL);
-            w_to_cons<NK>(P.ph, wR, uR);
+            double w[V];
+            reconw(d, m, a, b, +1, w);
+            face_state<NK>(P.ph, w, uL, sL);
+            reconw(d, m + 1, a, b, -1, w);
+            face_state<NK>(P.ph, w, uR, sR);
         }
         const double sc = 0.5 * n * rh[d];
 #pragma unroll
@@ -223,11 +225,11 @@ __global__ void __launch_bounds__(256) k_adj_fv(Params P, AdjBuffers A, Tiles T,
         // the face direction as a compile-time constant: the viscous reverse of
         // the other two directions' gradient entries reduces to the nonzero ones
         if (d == 0)
-            face_point_rev_seq<NK, 0>(P.ph, uL, uR, 0, Fb, uLb, uRb, true, getg, putgb);
+            face_point_rev_seq_s<NK, 0>(P.ph, uL, sL, uR, sR, 0, Fb, uLb, uRb, true, getg, putgb);
         else if (d == 1)
-            face_point_rev_seq<NK, 1>(P.ph, uL, uR, 1, Fb, uLb, uRb, true, getg, putgb);
+            face_point_rev_seq_s<NK, 1>(P.ph, uL, sL, uR, sR, 1, Fb, uLb, uRb, true, getg, putgb);
         else
-            face_point_rev_seq<NK, 2>(P.ph, uL, uR, 2, Fb, uLb, uRb, true, getg, putgb);
+            face_point_rev_seq_s<NK, 2>(P.ph, uL, sL, uR, sR, 2, Fb, uLb, uRb, true, getg, putgb);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             recb[((2 * d + 1) * V + v) * n3 + cL] = uLb[v];  // side + of the left cell

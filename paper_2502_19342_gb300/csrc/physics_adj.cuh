@@ -681,13 +681,13 @@ DGFV_HD void riemann_roe_rev(const DevPhys& P, const double* uL, const Prim<NK>&
 // other: getg(side, g) supplies a side's gradient (side 0 = L, 1 = R) just
 // before its reverse and putgb(side, gb) receives its adjoint right after, so
 // only one side's gradient and gradient adjoint are live at a time.
+// The same with the two mixture states given (sL, sR the states of uL, uR,
+// e.g. built by face_state from reconstructed variables).
 template <int NK, int DC = -1, class GetG, class PutGb>
-DGFV_HD void face_point_rev_seq(const DevPhys& P, const double* uL, const double* uR, int d, const double* Fb,
-                                double* uLb, double* uRb, bool fv_involved, GetG getg, PutGb putgb) {
+DGFV_HD void face_point_rev_seq_s(const DevPhys& P, const double* uL, const Prim<NK>& sL, const double* uR,
+                                  const Prim<NK>& sR, int d, const double* Fb, double* uLb, double* uRb,
+                                  bool fv_involved, GetG getg, PutGb putgb) {
     constexpr int V = NK + 4;
-    Prim<NK> sL, sR;
-    prim<NK>(P, uL, sL);
-    prim<NK>(P, uR, sR);
     PrimBar<NK> bL, bR;
     zero(bL);
     zero(bR);
@@ -737,6 +737,15 @@ DGFV_HD void face_point_rev_seq(const DevPhys& P, const double* uL, const double
     }
     prim_rev<NK>(P, uL, sL, bL, uLb);
     prim_rev<NK>(P, uR, sR, bR, uRb);
+}
+
+template <int NK, int DC = -1, class GetG, class PutGb>
+DGFV_HD void face_point_rev_seq(const DevPhys& P, const double* uL, const double* uR, int d, const double* Fb,
+                                double* uLb, double* uRb, bool fv_involved, GetG getg, PutGb putgb) {
+    Prim<NK> sL, sR;
+    prim<NK>(P, uL, sL);
+    prim<NK>(P, uR, sR);
+    face_point_rev_seq_s<NK, DC>(P, uL, sL, uR, sR, d, Fb, uLb, uRb, fv_involved, getg, putgb);
 }
 
 // The same with both gradients given and both gradient adjoints accumulated
