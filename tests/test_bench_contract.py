@@ -21,3 +21,21 @@ def test_reference_arm_prints_the_contract_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["dtype"] == "f64"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_kernel_table_and_rounding():
+    """The per-kernel rows of the bench line: [total ms, launches, algorithmic
+    TFLOP/s, fraction of the peak], the flops being the oracle's per-DOF count
+    of the kernel's step times the DOFs of one launch; kernels without a step
+    count (time step, indicator) carry times only; idle ones are left out."""
+    sys.path.insert(0, ROOT)
+    import bench
+    prof = {"dg_volume": (10.0, 5), "face_flux": (3.0, 5), "dt": (1.0, 2), "remap": (0.0, 0)}
+    per_step = {bench.KERNEL_STEP["dg_volume"]: 1000.0, bench.KERNEL_STEP["face_flux"]: 0.0}
+    t = bench.kernel_table(prof, per_step, 1.0e6, 1.25)
+    # 1000 flop per DOF x 1e6 DOFs in 2 ms per launch: 0.5 TFLOP/s, 0.4 of 1.25
+    assert t["dg_volume"] == [10.0, 5, 0.5, 0.4]
+    assert t["face_flux"] == [3.0, 5, None, None]
+    assert t["dt"] == [1.0, 2, None, None]
+    assert "remap" not in t
+    assert bench.r4(123456.0) == 123500.0 and bench.r4(0.000123456) == 0.0001235 and bench.r4(None) is None
