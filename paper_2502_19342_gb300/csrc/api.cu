@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dgfv.h"
 #include "adjoint.h"
 #include "bank.h"
@@ -19,6 +21,15 @@
 using namespace dgfv;
 
 namespace {
+
+// A named range on the host timeline of a profiler attached through NVTX
+// (header-only NVTX 3; without a tool the push and pop return at once).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct TileSet {
     std::vector<int32_t> first, count, items;
@@ -960,6 +971,7 @@ int dgfv_init_mesh(dgfv_ctx** out, const dgfv_mesh_desc* mesh, const dgfv_phys* 
 int64_t dgfv_num_elements(const dgfv_ctx* c) { return c ? c->n_elem : -1; }
 
 int dgfv_set_degrees(dgfv_ctx* c, const int8_t* N, const uint8_t* is_fv, int remap_state) {
+    const NvtxRange nvtx_range("dgfv_set_degrees");
     if (!c || !N) return DGFV_ERR_ARG;
     TRY(check_dev(c));
     return set_pattern(c, N, is_fv, remap_state != 0, nullptr);
@@ -1044,6 +1056,7 @@ int dgfv_get_state_host(dgfv_ctx* c, double* h_U, int64_t n, void* stream) {
 }
 
 int dgfv_eval_rhs(dgfv_ctx* c, const double* d_U, double* d_R, void* stream) {
+    const NvtxRange nvtx_range("dgfv_eval_rhs");
     if (!c || !d_U || !d_R) return DGFV_ERR_ARG;
     TRY(check_dev(c));
     if (d_U == d_R) return fail(c, DGFV_ERR_ARG, "d_U and d_R alias");
@@ -1054,6 +1067,7 @@ int dgfv_eval_rhs(dgfv_ctx* c, const double* d_U, double* d_R, void* stream) {
 }
 
 int dgfv_compute_dt(dgfv_ctx* c, const double* d_U, double* out3, void* stream) {
+    const NvtxRange nvtx_range("dgfv_compute_dt");
     if (!c || !d_U || !out3) return DGFV_ERR_ARG;
     TRY(check_dev(c));
     cudaStream_t s = (cudaStream_t)stream;
@@ -1142,6 +1156,7 @@ static void enqueue_vjp(dgfv_ctx* c, const double* U, const double* Rb, double* 
 }
 
 int dgfv_rhs_vjp(dgfv_ctx* c, const double* d_U, const double* d_Rbar, double* d_Ubar, void* stream) {
+    const NvtxRange nvtx_range("dgfv_rhs_vjp");
     if (!c || !d_U || !d_Rbar || !d_Ubar) return DGFV_ERR_ARG;
     TRY(check_dev(c));
     if (d_Ubar == d_U || d_Ubar == d_Rbar) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
@@ -1200,6 +1215,7 @@ static int lsrk4_step_vjp(dgfv_ctx* c, const double* d_U0, double dt, const doub
 
 int dgfv_rk_step_vjp(dgfv_ctx* c, const double* d_U0, double dt, const double* d_Ubar_next, double* d_Ubar,
                      void* stream) {
+    const NvtxRange nvtx_range("dgfv_rk_step_vjp");
     if (!c || !d_U0 || !d_Ubar_next || !d_Ubar || !(dt > 0.0)) return DGFV_ERR_ARG;
     TRY(check_dev(c));
     if (d_Ubar == d_Ubar_next || d_Ubar == d_U0) return fail(c, DGFV_ERR_ARG, "d_Ubar aliases an input");
@@ -1216,6 +1232,7 @@ int dgfv_rk_step_vjp(dgfv_ctx* c, const double* d_U0, double dt, const double* d
 
 int dgfv_rk_step_vjp_stages(dgfv_ctx* c, const double* const* d_stages, double dt, const double* d_Ubar_next,
                             double* d_Ubar, void* stream) {
+    const NvtxRange nvtx_range("dgfv_rk_step_vjp_stages");
     if (!c || !d_stages || !d_stages[0] || !d_stages[1] || !d_stages[2] || !d_Ubar_next || !d_Ubar || !(dt > 0.0))
         return DGFV_ERR_ARG;
     TRY(check_dev(c));
@@ -1229,6 +1246,7 @@ int dgfv_rk_step_vjp_stages(dgfv_ctx* c, const double* const* d_stages, double d
 }
 
 int dgfv_rk_step_save(dgfv_ctx* c, double dt, double* d_stage1, double* d_stage2, void* stream) {
+    const NvtxRange nvtx_range("dgfv_rk_step_save");
     if (!c || !d_stage1 || !d_stage2 || !(dt > 0.0)) return DGFV_ERR_ARG;
     TRY(check_dev(c));
     if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "rk_step_save before set_state");
@@ -1244,6 +1262,7 @@ int dgfv_rk_step_save(dgfv_ctx* c, double dt, double* d_stage1, double* d_stage2
 }
 
 int dgfv_rk_step(dgfv_ctx* c, double dt, double* dt_used, void* stream) {
+    const NvtxRange nvtx_range("dgfv_rk_step");
     if (!c) return DGFV_ERR_ARG;
     TRY(check_dev(c));
     if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "rk_step before set_state");
@@ -1259,6 +1278,7 @@ int dgfv_rk_step(dgfv_ctx* c, double dt, double* dt_used, void* stream) {
 }
 
 int dgfv_rk_steps(dgfv_ctx* c, int n_steps, double dt, double* dt_used, void* stream) {
+    const NvtxRange nvtx_range("dgfv_rk_steps");
     if (!c || n_steps < 0) return DGFV_ERR_ARG;
     TRY(check_dev(c));
     if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "rk_steps before set_state");
@@ -1309,6 +1329,7 @@ int dgfv_indicator(dgfv_ctx* c, const double* d_U, double* d_Ip, double* d_Ih, u
 }
 
 int dgfv_adapt(dgfv_ctx* c, dgfv_adapt_stats* stats, void* stream) {
+    const NvtxRange nvtx_range("dgfv_adapt");
     if (!c) return DGFV_ERR_ARG;
     TRY(check_dev(c));
     if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "adapt before set_state");
@@ -1397,6 +1418,7 @@ int dgfv_set_fv_variant(dgfv_ctx* c, int variant) {
 }
 
 int dgfv_autotune(dgfv_ctx* c, int* per_tile_out, void* stream) {
+    const NvtxRange nvtx_range("dgfv_autotune");
     if (!c) return DGFV_ERR_ARG;
     TRY(check_dev(c));
     if (!c->state_valid) return fail(c, DGFV_ERR_STATE, "autotune before set_state");

@@ -542,3 +542,36 @@ def test_degenerate_calls_leave_the_state_alone():
     with pytest.raises(dgfv.DgfvError):
         ctx.set_state_host(np.zeros(U.size - 1))
     ctx.close()
+
+
+def test_checkpoint_and_resume_is_bitwise():
+    """Checkpoint/resume: the state with its degrees and FV flags, saved after
+    two adaptation cycles and loaded into a new context of the same mesh,
+    continues bit for bit like the context that kept running (adaptation, CFL
+    time steps and stages included)."""
+    from paper_2502_19342_gb300 import dgfv
+    prob, U = _mixed(21, nk=3, fv_frac=0.3)
+    opts = dict(thresholds=W.THRESHOLDS, cfl_c=0.5, cfl_v=0.5)
+    a = dgfv.Context(prob, N_min=1, N_max=7, opts=opts)
+    a.set_state(to_dev(U))
+    for _ in range(2):
+        a.adapt()
+        a.rk_steps(3, -1.0, want_dt=False)
+    N, fv = a.get_degrees()
+    saved = a.get_state()
+    for _ in range(2):
+        a.adapt()
+        a.rk_steps(3, -1.0, want_dt=False)
+    b = dgfv.Context(prob, N_min=1, N_max=7, opts=opts)
+    b.set_degrees(N, fv, remap=False)
+    b.set_state(saved)
+    for _ in range(2):
+        b.adapt()
+        b.rk_steps(3, -1.0, want_dt=False)
+    Na, fva = a.get_degrees()
+    Nb, fvb = b.get_degrees()
+    np.testing.assert_array_equal(Na, Nb)
+    np.testing.assert_array_equal(fva, fvb)
+    assert torch.equal(a.get_state(), b.get_state())
+    a.close()
+    b.close()
