@@ -39,6 +39,11 @@
  *           dgfv_init_mesh; every call that touches device memory returns
  *           DGFV_ERR_ARG, before any CUDA work, when another device is current.
  * Threads   One context is used by one host thread and one stream at a time.
+ * Tracing   The calls that enqueue work (set_degrees, eval_rhs, compute_dt,
+ *           rk_step, rk_steps, rk_step_save, adapt, autotune and the VJPs)
+ *           open an NVTX range named after the call on the host timeline of
+ *           a profiler that attaches through NVTX; per-kernel device times
+ *           come from dgfv_profile_enable / dgfv_profile_read.
  */
 #ifndef DGFV_H
 #define DGFV_H
