@@ -66,12 +66,14 @@ def test_rhs_mixed_hp_fv(oracle, nk, riemann, mu, seed, nodes, split):
 
 @pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("nk,n_fv,riemann,mu", [(2, 7, 0, 2e-3), (3, 8, 2, 2e-3), (2, 9, 0, 1e-3),
-                                                 (3, 5, 1, 3e-3), (1, 8, 0, 0.0)])
+                                                 (3, 5, 1, 3e-3), (1, 8, 0, 0.0), (2, 2, 0, 2e-3), (3, 3, 1, 1e-3)])
 def test_fv_kernel_layouts_match_oracle(oracle, variant, nk, n_fv, riemann, mu):
     """The shared-memory layouts of the FV sub-cell kernel (gradients
     recomputed at each face / kept per sub-cell / kept, with the z faces in a
     second pass where two CTAs then fit per SM) on a hybrid mesh with 40 % FV
-    elements, N_FV = 5, 7, 8, 9: R(U) against the oracle at the bar of R."""
+    elements, N_FV = 2, 3, 5, 7, 8, 9 (two sub-cells: one interior face per
+    line, every cell a boundary cell): R(U) against the oracle at the bar of
+    R."""
     sp = W.species_set([W.AIR, W.HELIUM, W.CO2][:nk], mu=mu)
     n = 3 * 3 * 4
     N = W.random_degrees(n, 1, min(6, n_fv - 1), 40 + n_fv)
