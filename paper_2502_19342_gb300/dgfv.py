@@ -433,6 +433,33 @@ def rhs_function():
     return RHS
 
 
+def rk_step_function():
+    """torch.autograd.Function of one SSP-RK3 step of fixed size on the CUDA
+    path: forward U1 = step(U0) through the context, backward the step's
+    hand-written adjoint with its stage states recomputed from the saved U0
+    (degree pattern frozen).  A rollout is a chain of applications, so autograd
+    keeps one state per step.  Usage: U1 = rk_step_function().apply(U0, ctx, dt).
+    The context's state is U1 after the forward."""
+    import torch
+
+    class RKStep(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, U0, ctx, dt):
+            fctx.ctx, fctx.dt = ctx, float(dt)
+            U0 = U0.detach().contiguous()
+            fctx.save_for_backward(U0)
+            ctx.set_state(U0)
+            ctx.rk_step(float(dt), want_dt=False)
+            return ctx.get_state()
+
+        @staticmethod
+        def backward(fctx, U1bar):
+            (U0,) = fctx.saved_tensors
+            return fctx.ctx.rk_step_vjp(U0, fctx.dt, U1bar.contiguous()), None, None
+
+    return RKStep
+
+
 def rollout_gradient(ctx, U0, n_steps, dt, loss_grad, keep_stages=False, checkpoint_every=1):
     """Gradient of a loss of the state after n_steps SSP-RK3 steps of size dt
     with respect to the initial state, by the adjoint of every step.

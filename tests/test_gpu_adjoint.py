@@ -360,3 +360,26 @@ def test_stored_stage_adjoint_matches_recomputed_stages():
     with pytest.raises(ValueError):
         dgfv.rollout_gradient(ctx, U0, 3, dt, lambda X: X, keep_stages=True, checkpoint_every=2)
     ctx.close()
+
+
+def test_rk_step_autograd_function_matches_rollout_gradient():
+    """The RK step behind torch.autograd.Function: a chain of four steps and a
+    torch loss on the final state backpropagate, step by step through the
+    hand-written step adjoint, to the same gradient as rollout_gradient (bit for
+    bit: the same adjoints on the same states); the forward chain reproduces
+    the context's own rollout."""
+    from paper_2502_19342_gb300 import dgfv
+    prob, U = _dg_problem(12, nk=2, nel=(2, 3, 2), uniform=None, mu=2e-3)
+    dt = 2e-4
+    ctx = ctx_for(prob, N_min=1, N_max=7)
+    w = to_dev(np.random.default_rng(12).standard_normal(U.size))
+    step = dgfv.rk_step_function()
+    X = to_dev(U).requires_grad_(True)
+    Y = X
+    for _ in range(4):
+        Y = step.apply(Y, ctx, dt)
+    (0.5 * (w * Y * Y).sum()).backward()
+    g_ref, Uf = dgfv.rollout_gradient(ctx, to_dev(U), 4, dt, lambda Z: w * Z)
+    assert torch.equal(Y.detach(), Uf)
+    assert torch.equal(X.grad, g_ref)
+    ctx.close()
