@@ -434,10 +434,11 @@ def rhs_function():
 
 
 def rk_step_function():
-    """torch.autograd.Function of one SSP-RK3 step of fixed size on the CUDA
-    path: forward U1 = step(U0) through the context, backward the step's
-    hand-written adjoint with its stage states recomputed from the saved U0
-    (degree pattern frozen).  A rollout is a chain of applications, so autograd
+    """torch.autograd.Function of one Runge-Kutta step of fixed size on the
+    CUDA path, in the context's scheme (SSP-RK3, or the low-storage RK4 with
+    opts integrator 1): forward U1 = step(U0) through the context, backward
+    the step's hand-written adjoint with its stage states recomputed from the
+    saved U0 (degree pattern frozen).  A rollout is a chain of applications, so autograd
     keeps one state per step.  Usage: U1 = rk_step_function().apply(U0, ctx, dt).
     The context's state is U1 after the forward."""
     import torch
@@ -461,8 +462,9 @@ def rk_step_function():
 
 
 def rollout_gradient(ctx, U0, n_steps, dt, loss_grad, keep_stages=False, checkpoint_every=1):
-    """Gradient of a loss of the state after n_steps SSP-RK3 steps of size dt
-    with respect to the initial state, by the adjoint of every step.
+    """Gradient of a loss of the state after n_steps Runge-Kutta steps of size
+    dt (the context's scheme; keep_stages needs SSP-RK3) with respect to the
+    initial state, by the adjoint of every step.
     keep_stages=False keeps one checkpoint every `checkpoint_every` steps: with
     1 (the default) the state at the start of every step, whose stage states
     the backward pass recomputes; with k > 1 every k-th state, the backward

@@ -362,16 +362,17 @@ def test_stored_stage_adjoint_matches_recomputed_stages():
     ctx.close()
 
 
-def test_rk_step_autograd_function_matches_rollout_gradient():
-    """The RK step behind torch.autograd.Function: a chain of four steps and a
-    torch loss on the final state backpropagate, step by step through the
-    hand-written step adjoint, to the same gradient as rollout_gradient (bit for
-    bit: the same adjoints on the same states); the forward chain reproduces
-    the context's own rollout."""
+@pytest.mark.parametrize("integrator", [0, 1])
+def test_rk_step_autograd_function_matches_rollout_gradient(integrator):
+    """The RK step behind torch.autograd.Function (SSP-RK3, low-storage RK4):
+    a chain of four steps and a torch loss on the final state backpropagate,
+    step by step through the hand-written step adjoint, to the same gradient as
+    rollout_gradient (bit for bit: the same adjoints on the same states); the
+    forward chain reproduces the context's own rollout."""
     from paper_2502_19342_gb300 import dgfv
     prob, U = _dg_problem(12, nk=2, nel=(2, 3, 2), uniform=None, mu=2e-3)
     dt = 2e-4
-    ctx = ctx_for(prob, N_min=1, N_max=7)
+    ctx = ctx_for(prob, opts=dict(integrator=integrator), N_min=1, N_max=7)
     w = to_dev(np.random.default_rng(12).standard_normal(U.size))
     step = dgfv.rk_step_function()
     X = to_dev(U).requires_grad_(True)
