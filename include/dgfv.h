@@ -106,8 +106,8 @@ typedef struct {
                              then couples on the FV side's grid (V^{FV->DG}: the L2
                              projection where that grid has fewer than N+1
                              sub-cells); FV/FV faces of unequal counts on the finer
-                             grid, by sub-cell overlaps.  Not with chain_x = 1, and
-                             not with the adjoint calls (DGFV_ERR_ARG). */
+                             grid, by sub-cell overlaps.  Not with chain_x = 1
+                             (DGFV_ERR_ARG). */
     int chain_x;          /* 0 or 1, see above                          */
 } dgfv_mesh_desc;
 

@@ -121,10 +121,13 @@ __global__ void __launch_bounds__(128) k_adj_mixed_in(Params P, AdjBuffers A, Fa
     const int em = m.mapL ? m.eL : m.eR, fm = m.mapL ? 2 * d + 1 : 2 * d, n = P.t.n[em], n2 = n * n;
     const int ed = m.mapL ? m.eR : m.eL, fd = m.mapL ? 2 * d : 2 * d + 1, nc2 = m.nc * m.nc;
     const int64_t slot = P.t.fo[em] + (int64_t)fm * n2, sd = P.t.fo[ed] + (int64_t)fd * nc2;
-    const double* Min = B(P, m.cfv ? P.bi.d2f[n][m.nc] : P.bi.vm[n][m.nc]);
-    const double* Mout = B(P, m.cfv ? P.bi.f2d[n][m.nc] : P.bi.vm[m.nc][n]);
+    // a coarser FV side (per-element counts) enters by its sub-cell overlaps,
+    // from its reconstructed face states, as in k_mixed_in / k_mixed_out
+    const bool fvs = P.t.fv[em];
+    const double* Min = B(P, fvs ? P.bi.ov[n][m.nc] : (m.cfv ? P.bi.d2f[n][m.nc] : P.bi.vm[n][m.nc]));
+    const double* Mout = B(P, fvs ? P.bi.ov[m.nc][n] : (m.cfv ? P.bi.f2d[n][m.nc] : P.bi.vm[m.nc][n]));
     double* in = Sin + mpt[k] * 4 * V;
-    face_map(P.b.fu + slot * V, n, in, m.nc, Min, V, tmp);
+    face_map((fvs ? P.b.frec : P.b.fu) + slot * V, n, in, m.nc, Min, V, tmp);
     if (P.ph.viscous) face_map(P.b.fg + slot * 3 * V, n, in + V * nc2, m.nc, Min, 3 * V, tmp);
     // L's slot holds +F, R's slot -F
     const double sm = m.mapL ? 1.0 : -1.0;
@@ -205,7 +208,8 @@ __global__ void __launch_bounds__(128) k_adj_mixed_out(Params P, AdjBuffers A, F
     const MixedFace m = mixed_face(P, Fc, fid);
     const int em = m.mapL ? m.eL : m.eR, fm = m.mapL ? 2 * d + 1 : 2 * d, n = P.t.n[em], n2 = n * n;
     const int64_t slot = P.t.fo[em] + (int64_t)fm * n2;
-    const double* Min = B(P, m.cfv ? P.bi.d2f[n][m.nc] : P.bi.vm[n][m.nc]);
+    const double* Min =
+        B(P, P.t.fv[em] ? P.bi.ov[n][m.nc] : (m.cfv ? P.bi.d2f[n][m.nc] : P.bi.vm[n][m.nc]));
     const double* in = Sin + mpt[k] * 4 * V;
     face_map_t(in, m.nc, A.ubar + slot * V, n, Min, V, tmp);
     if (P.ph.viscous) face_map_t(in + V * m.nc * m.nc, m.nc, A.gbar + slot * 3 * V, n, Min, 3 * V, tmp);
@@ -518,7 +522,7 @@ __global__ void __launch_bounds__(64) k_adj_lift(Params P, AdjBuffers A, Faces F
     if (fvL || fvR) {
         // U*_DG = (u_DG + V^{FV->DG} rec_FV)/2: u_DG_bar += U*_bar/2, and the FV
         // reconstructed face state's adjoint += V^{FV->DG}^T U*_bar/2
-        const int nD = fvL ? nR : nL, nF = P.nfv;
+        const int nD = fvL ? nR : nL, nF = fvL ? nL : nR;  // the FV side's own count
         const int64_t sD = fvL ? sR : sL, sF = fvL ? sL : sR;
         for (int i = threadIdx.x; i < V * nD * nD; i += blockDim.x) {
             const double a = 0.5 * A.sbar[sD + i];
@@ -563,7 +567,7 @@ __global__ void __launch_bounds__(64) k_adj_lift(Params P, AdjBuffers A, Faces F
 template <int NK>
 __global__ void __launch_bounds__(128) k_adj_surface_fv(Params P, AdjBuffers A, Tiles T, const double* __restrict__ Rb) {
     constexpr int V = NK + 4;
-    const int e = T.items[T.first[blockIdx.x]], n = P.nfv, n2 = n * n, n3 = n2 * n;
+    const int e = T.items[T.first[blockIdx.x]], n = P.t.n[e], n2 = n * n, n3 = n2 * n;
     for (int i = threadIdx.x; i < 6 * V * n2; i += blockDim.x) {
         const int f = i / (V * n2), r = i % (V * n2), v = r / n2, p = r % n2, d = f >> 1;
         const int c = node_index(n, d, (f & 1) ? n - 1 : 0, p % n, p / n);

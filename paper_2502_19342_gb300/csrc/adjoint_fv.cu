@@ -85,8 +85,8 @@ __global__ void __launch_bounds__(256) k_adj_fv(Params P, AdjBuffers A, Tiles T,
                                                double* __restrict__ fvs, int64_t cap_state) {
     constexpr int V = NK + 4;
     extern __shared__ double sm[];
-    const int n = P.nfv, n2 = n * n, n3 = n2 * n;
     const int e = T.items[T.first[blockIdx.x]];
+    const int n = P.t.n[e], n2 = n * n, n3 = n2 * n;  // this element's sub-cells (the shared memory fits the largest)
     const AdjFvLayout L = adj_fv_layout(V, n, GS);
     double* sU = sm + L.u;    // V n3 conservative means (GS = 1: turned into sW in place)
     double* sW = sm + L.w;    // V n3 reconstruction variables
@@ -353,11 +353,12 @@ template <int NK>
 __global__ void __launch_bounds__(128) k_adj_fv_gather(Params P, AdjBuffers A, double* __restrict__ Ub) {
     constexpr int V = NK + 4;
     __shared__ double sT1[V * MAXP * MAXP], sT2[V * MAXP * MAXP];
-    const int q = blockIdx.x, n = P.nfv, n2 = n * n;
+    const int q = blockIdx.x;
     for (int fq = 0; fq < 6; ++fq) {
         const int e = P.t.nb[6 * q + fq];
         if (e < 0 || !P.t.fv[e]) continue;
-        const double* lb = A.fbar + (P.t.fo[e] + (int64_t)(fq ^ 1) * n2) * V;
+        const int n = P.t.n[e];  // the layer is on e's sub-cell grid
+        const double* lb = A.fbar + (P.t.fo[e] + (int64_t)(fq ^ 1) * n * n) * V;
         fv_layer_t<NK>(P, q, fq, n, lb, Ub, sT1, sT2);
     }
 }

@@ -1093,7 +1093,6 @@ int dgfv_compute_dt_noalloc(dgfv_ctx* c, const double* d_U, double* d_out3, void
 }
 
 static int adj_prepare(dgfv_ctx* c) {
-    if (c->fv_own) return fail(c, DGFV_ERR_ARG, "the adjoint does not support per-element sub-cell counts");
     if (c->adj_ready) return DGFV_OK;
     TRY(dalloc(c, &c->d_fbar, c->cap_fpts * c->V));
     TRY(dalloc(c, &c->d_ubar, c->cap_fpts * c->V));

@@ -248,23 +248,30 @@ __device__ __forceinline__ void fv_gather_neighbours(const Params& P, const doub
     __syncthreads();
 }
 
-// Transpose of fv_layer: Ub (the state adjoint of element q) += layer^T lb,
-// lb the adjoint of the N_FV x N_FV layer across face fq.  FV element: the
-// boundary sub-cells; DG element: V^{DG->FV} transposed in both face
+// Transpose of the neighbour layer an FV element of n sub-cells per direction
+// reads across face fq of element q: Ub (the state adjoint of q) += layer^T
+// lb, lb the adjoint of the n x n layer.  FV element: its boundary sub-cells
+// (with another sub-cell count, per-element counts, the transpose of the
+// overlap map first); DG element: V^{DG->FV} transposed in both face
 // directions, then the boundary row along the normal.  Ends with a barrier.
 template <int NK, bool ATOMIC = false>
 __device__ __forceinline__ void fv_layer_t(const Params& P, int q, int fq, int n, const double* lb, double* Ub,
                                            double* sT1, double* sT2) {
     constexpr int V = NK + 4;
-    const int n2 = n * n, d = fq >> 1;
+    const int d = fq >> 1;
     if (P.t.fv[q]) {
-        const int n3 = n2 * n, m = (fq & 1) ? n - 1 : 0;
+        const int nq = P.t.n[q], nq2 = nq * nq, nq3 = nq2 * nq, m = (fq & 1) ? nq - 1 : 0;
+        const double* src = lb;
+        if (nq != n) {  // the layer was mapped from q's grid by its overlaps (n x nq)
+            face_map_t(lb, n, sT1, nq, B(P, P.bi.ov[nq][n]), V, sT2);
+            src = sT1;
+        }
         double* dst = Ub + P.t.off[q];
-        for (int i = threadIdx.x; i < V * n2; i += blockDim.x) {
-            const int v = i / n2, p = i % n2;
-            double* t = dst + (int64_t)v * n3 + node_index(n, d, m, p % n, p / n);
-            if (ATOMIC) atomicAdd(t, lb[i]);
-            else *t += lb[i];
+        for (int i = threadIdx.x; i < V * nq2; i += blockDim.x) {
+            const int v = i / nq2, p = i % nq2;
+            double* t = dst + (int64_t)v * nq3 + node_index(nq, d, m, p % nq, p / nq);
+            if (ATOMIC) atomicAdd(t, src[i]);
+            else *t += src[i];
         }
         __syncthreads();
         return;
