@@ -514,18 +514,22 @@ def tgv_run(nel=32, warmup=60, steps=2):
             "degree_histogram": np.bincount(N_now[fv_now == 0], minlength=5).tolist()[2:]}
 
 
-def hp_shock_run(peak=None, cycles=40, fv_variant=0):
+def hp_shock_run(peak=None, cycles=40, fv_variant=0, own=False):
     """The hp-mixed shock case at its full length: 16^3 elements on
     [0,2]x[0,1]^2, N in 2..6 with FV sub-cells (N_FV = 7) chosen by the
     indicator every 5 SSP-RK3 steps, a Mach 1.5 shock into a heavy-gas bubble,
     2 species; `cycles` x (adaptation + 5 steps) = 200 steps.  CUDA events
     around each adaptation (indicator, readback, host tables, remap) and
     around each block of 5 steps (graph replay, recaptured after a pattern
-    change); the RHS rate and its roofline fraction over the steps alone."""
+    change); the RHS rate and its roofline fraction over the steps alone.
+    own: the per-element sub-cell variant (N_fv = 0: an FV element of degree N
+    has N+1 sub-cells; the start has no FV element, so the same state)."""
     import torch
     from paper_2502_19342_gb300 import dgfv, workloads as W
     peak = fp64_peak()[0] if peak is None else peak
     prob, U = W.hp_shock(0, y_bg=0.01)
+    if own:
+        prob = dict(prob, fv_own_n=1)
     ctx = dgfv.Context(prob, N_min=2, N_max=6, opts=dict(cfl_c=0.5, cfl_v=0.5, thresholds=W.THRESHOLDS))
     ctx.set_fv_variant(fv_variant)
     ctx.set_state(torch.from_numpy(U).cuda())
@@ -563,7 +567,13 @@ def hp_shock_run(peak=None, cycles=40, fv_variant=0):
             "adapt_ms_per_cycle": r4(adapt_ms / cycles), "rk_ms_per_cycle": r4(rk_ms / cycles),
             "whole_rhs_tflops": r4(per_dof * rate / 1e12), "whole_rhs_frac": r4(per_dof * rate / 1e12 / peak),
             "flops_per_dof": r4(per_dof), "fv_elements_first_last": [fvs[0], fvs[-1]], "kernels": kernels,
-            "subcell_dof_share": r4(float(fv_now.astype(np.int64).sum() * 343) / float(W.n_dofs(dict(prob, N=N_now, fv=fv_now))))}
+            "subcell_dof_share": r4(subcell_share(W, dict(prob, N=N_now, fv=fv_now)))}
+
+
+def subcell_share(W, prob):
+    """Fraction of the DOFs that are FV sub-cells."""
+    n = W.points_per_dir(prob).astype(np.int64)
+    return float((n[prob["fv"] != 0] ** 3).sum()) / float((n ** 3).sum())
 
 
 def mortar_run(peak=None, k=24, warmup=1, steps=3):
@@ -873,6 +883,15 @@ def main():
             cpu = {k: (r4(v) if isinstance(v, float) else v) for k, v in cpu.items()}
         adjoint = {"mixing_layer": adjoint_cost(), "hybrid_shock": adjoint_hybrid_cost()}
         shock = None if args.no_shock else hp_shock_run(peak)
+        shock_own = None
+        if not args.no_shock:
+            # one timed cycle and the two profiled ones: with N+1 sub-cells the
+            # shock case's state turns non-physical in the fourth cycle, in the
+            # oracle alike
+            o = hp_shock_run(peak, cycles=1, own=True)
+            shock_own = {k: o[k] for k in ("value", "rk_value", "whole_rhs_frac", "fv_elements_first_last",
+                                           "subcell_dof_share")}
+            shock_own["fv"] = o["kernels"].get("fv")
         split = None if args.no_split else split_form_run(args.nel, peak)
         tgv = None if args.no_tgv else tgv_run()
         mortar = None if args.no_mortar else mortar_run(peak)
@@ -893,6 +912,7 @@ def main():
                            "l2": "inputs larger than L2 (state ~1.2 GB)"},
                 "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary(), "adjoint": adjoint, "batched_domains": batched, "hp_shock": shock,
+                "hp_shock_own": shock_own,
                 "split_form": split, "tgv": tgv, "mortar": mortar}
         print(json.dumps(line, separators=(",", ":")))
     ctx.close()

@@ -16,7 +16,8 @@ size_t fv_smem_bytes(int nk, int nfv);
 // faces_only: only the element-face states and boundary gradients (frec, fg),
 // not the sub-cell fluxes (the adjoint's recomputation of the forward).
 // variant: 0 automatic, 1 gradients recomputed at each face, 2 gradients kept
-// in shared memory (when that layout fits).
+// in shared memory, 3 kept with the z faces in a second pass (when that layout
+// fits).
 void launch_fv(int nk, const Params& P, const Tiles& T, int ntiles, const double* U, cudaStream_t s,
                bool faces_only = false, int variant = 0);
 void launch_face_lift_conf(int nk, const Params& P, const Faces& F, const FaceTiles& T, int ntiles, cudaStream_t s);
