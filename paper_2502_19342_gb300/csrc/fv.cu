@@ -108,16 +108,29 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
     };
     // reconstructed reconstruction variables of cell m (along d) at its face side (-1 or +1):
     // w +- l/2 minmod(dw-/dist-, dw+/dist+); inside the element both distances are l,
-    // so the half slope is minmod(dw-, dw+)/2
+    // so the half slope is minmod(dw-, dw+)/2 and w = fma(+-1/2, minmod, w_c) (the
+    // same value: halving is exact).  The branch is uniform in the warps of the
+    // face pass, which takes the faces between two inner cells first.
     auto face_w = [&](int d, int m, int a, int b, int side, double* w) {
-        const bool inner = m > 0 && m < n - 1;
+        if (m > 0 && m < n - 1) {
+            const int st = d == 0 ? 1 : (d == 1 ? n : n2);  // stride of direction d
+            const double* c = sW + node_index(n, d, m, a, b);
+            const double hs = side > 0 ? 0.5 : -0.5;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const double wc = c[v * n3];
+                const double dm = wc - c[v * n3 - st], dp = c[v * n3 + st] - wc;
+                w[v] = fma(hs, minmod_bits(dm, dp), wc);
+            }
+            return;
+        }
         const double ilm = m > 0 ? il : sID[2 * d], ilp = m < n - 1 ? il : sID[2 * d + 1];
+        const double hl = side > 0 ? 0.5 * l : -0.5 * l;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const double wc = cellW(d, m, a, b, v);
             const double dm = wc - cellW(d, m - 1, a, b, v), dp = cellW(d, m + 1, a, b, v) - wc;
-            const double h = inner ? 0.5 * minmod_bits(dm, dp) : (0.5 * l) * minmod_bits(dm * ilm, dp * ilp);
-            w[v] = side > 0 ? wc + h : wc - h;
+            w[v] = fma(hl, minmod_bits(dm * ilm, dp * ilp), wc);
         }
     };
     auto cell_grad = [&](int i, int j, int k, double* g) {
@@ -142,6 +155,7 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
     // flux differences of the first pass kept in the cell's row of rtmp in
     // between (the same sums in the same order, so the same result as GS = 1)
     const int nif = faces_only ? 0 : (n - 1) * n2;
+    const int ninner = n > 3 ? (n - 3) * n2 : 0;  // faces m = 1..n-3 of a direction: both cells inner
     constexpr int NPASS = GS == 2 ? 2 : 1;
 #pragma unroll 1
     for (int pass = 0; pass < NPASS; ++pass) {
@@ -149,8 +163,17 @@ __device__ __forceinline__ void fv_body(const Params& P, const Tiles& T, const d
         const int nd = GS == 2 ? (pass == 0 ? 2 : 1) : 3;  // directions in the pass
         if (pass > 0) __syncthreads();                      // the first pass's fluxes have been read
         for (int t = threadIdx.x; t < nd * nif; t += blockDim.x) {
-            const int dl = t / nif, fidx = t - dl * nif, d = d0 + dl;
-            const int m = fidx % (n - 1), p = fidx / (n - 1), a = p % n, b = p / n;
+            const int dl = t / nif, r = t - dl * nif, d = d0 + dl;
+            // work order in a direction: the faces between two inner cells, then
+            // the faces m = 0 and m = n-2 (next to a boundary cell)
+            int m, p;
+            if (r < ninner) {
+                m = 1 + r % (n - 3), p = r / (n - 3);
+            } else {
+                const int q = r - ninner;
+                m = q < n2 ? 0 : n - 2, p = q < n2 ? q : q - n2;
+            }
+            const int a = p % n, b = p / n, fidx = m + (n - 1) * p;
             // F* = F^c*(uL, uR) + (F^v(uL, gL) + F^v(uR, gR))/2, the two viscous
             // fluxes one after the other (one gradient live at a time)
             double uL[V], uR[V], F[V];

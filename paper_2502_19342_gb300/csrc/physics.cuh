@@ -101,10 +101,7 @@ DGFV_HD void flux_conv(const double* u, const Prim<NK>& s, int d, double* F) {
 #pragma unroll
     for (int k = 0; k < NK; ++k) F[k] = u[k] * vd;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        F[NK + i] = u[NK + i] * vd;
-        if (i == d) F[NK + i] += s.p;
-    }
+    for (int i = 0; i < 3; ++i) F[NK + i] = fma(u[NK + i], vd, i == d ? s.p : 0.0);
     F[NK + 3] = (u[NK + 3] + s.p) * vd;
 }
 
@@ -173,7 +170,11 @@ DGFV_HD void flux_visc(const DevPhys& P, const Prim<NK>& s, const PrimGrad<NK>& 
 // directions A, B only the densities and the momenta along D and along A (B):
 // tau_{D.} needs dv_D/dx_A, dv_D/dx_B and div v the diagonal.  The same
 // formulas as prim_grad + flux_visc (Eqs. 4a-4c, 5), with about two thirds of
-// their FP64 work when the direction is not known before the call.
+// their FP64 work when the direction is not known before the call.  Every
+// primitive gradient of the chain rule carries the factor 1/rho; it is kept
+// out of the gradients below (they are rho times the primitive gradients) and
+// applied once each in the viscosity (mu/rho), in the temperature gradient and,
+// as rho/rho = 1, not at all in the diffusion fluxes.
 template <int NK, int D, class GX>
 DGFV_HD void flux_visc_dir(const DevPhys& P, const Prim<NK>& s, GX gx, double* F) {
     constexpr int A = D == 0 ? 1 : 0, B = D == 2 ? 1 : 2;
@@ -184,40 +185,41 @@ DGFV_HD void flux_visc_dir(const DevPhys& P, const Prim<NK>& s, GX gx, double* F
         grA += gx(A, k);
         grB += gx(B, k);
     }
-    double vD[3];  // dv_i/dx_D
+    double vD[3];  // rho dv_i/dx_D
 #pragma unroll
-    for (int i = 0; i < 3; ++i) vD[i] = (gx(D, NK + i) - s.v[i] * grD) * s.irho;
-    const double vDA = (gx(A, NK + D) - s.v[D] * grA) * s.irho;  // dv_D/dx_A
-    const double vDB = (gx(B, NK + D) - s.v[D] * grB) * s.irho;  // dv_D/dx_B
-    const double vAA = (gx(A, NK + A) - s.v[A] * grA) * s.irho;
-    const double vBB = (gx(B, NK + B) - s.v[B] * grB) * s.irho;
+    for (int i = 0; i < 3; ++i) vD[i] = fma(-s.v[i], grD, gx(D, NK + i));
+    const double vDA = fma(-s.v[D], grA, gx(A, NK + D));  // rho dv_D/dx_A
+    const double vDB = fma(-s.v[D], grB, gx(B, NK + D));  // rho dv_D/dx_B
+    const double vAA = fma(-s.v[A], grA, gx(A, NK + A));
+    const double vBB = fma(-s.v[B], grB, gx(B, NK + B));
     const double divv = vD[D] + vAA + vBB;
+    const double mr = s.mu * s.irho;
     double tau[3];
-    tau[D] = s.mu * (2.0 * vD[D] - (2.0 / 3.0) * divv);
-    tau[A] = s.mu * (vDA + vD[A]);
-    tau[B] = s.mu * (vDB + vD[B]);
-    double GY[NK], corr = 0.0, gcv = 0.0;
+    tau[D] = mr * fma(-2.0 / 3.0, divv, 2.0 * vD[D]);
+    tau[A] = mr * (vDA + vD[A]);
+    tau[B] = mr * (vDB + vD[B]);
+    double GY[NK], corr = 0.0, gcv = 0.0;  // rho dY_k/dx_D and its sums
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
-        GY[k] = (gx(D, k) - s.Y[k] * grD) * s.irho;
+        GY[k] = fma(-s.Y[k], grD, gx(D, k));
         corr = fma(P.D[k], GY[k], corr);
         gcv = fma(P.cv[k], GY[k], gcv);
     }
-    double geps = (gx(D, NK + 3) - s.E * grD) * s.irho;
+    double geps = fma(-s.E, grD, gx(D, NK + 3));  // rho d(eps)/dx_D, eps = E - |v|^2/2
 #pragma unroll
-    for (int i = 0; i < 3; ++i) geps -= s.v[i] * vD[i];
-    const double GT = (geps - s.T * gcv) * s.icv;
+    for (int i = 0; i < 3; ++i) geps = fma(-s.v[i], vD[i], geps);
+    const double GT = fma(-s.T, gcv, geps) * (s.irho * s.icv);
     double qd = 0.0;
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
-        const double J = s.rho * (s.Y[k] * corr - P.D[k] * GY[k]);
+        const double J = fma(s.Y[k], corr, -P.D[k] * GY[k]);  // rho (Y_k corr - D_k dY_k/dx_D)
         F[k] = J;
         qd = fma(P.cp[k], J, qd);
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) F[NK + i] = -tau[i];
-    const double tv = tau[0] * s.v[0] + tau[1] * s.v[1] + tau[2] * s.v[2];
-    F[NK + 3] = -tv - s.lam * GT + s.T * qd;
+    const double tv = fma(tau[2], s.v[2], fma(tau[1], s.v[1], tau[0] * s.v[0]));
+    F[NK + 3] = fma(s.T, qd, fma(-s.lam, GT, -tv));
 }
 
 // F += F^v_d: the viscous flux of flux_visc added into F with fused
@@ -259,7 +261,7 @@ DGFV_HD void riemann_llf(const double* uL, const Prim<NK>& sL, const double* uR,
     const double aL = fabs(pick3(sL.v, d)) + sL.c, aR = fabs(pick3(sR.v, d)) + sR.c;
     const double smax = aL > aR ? aL : aR;
 #pragma unroll
-    for (int v = 0; v < V; ++v) F[v] = 0.5 * ((FL[v] + FR[v]) - smax * (uR[v] - uL[v]));
+    for (int v = 0; v < V; ++v) F[v] = 0.5 * fma(-smax, uR[v] - uL[v], FL[v] + FR[v]);
 }
 
 // Roe flux with the Harten-Hyman entropy fix for the ideal-gas mixture, with
@@ -440,7 +442,7 @@ DGFV_HD void cons_to_w(const DevPhys& P, const double* u, double* w) {
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) w[NK + i] = u[NK + i] * irho;
-    const double ke = 0.5 * (u[NK] * w[NK] + u[NK + 1] * w[NK + 1] + u[NK + 2] * w[NK + 2]);
+    const double ke = 0.5 * fma(u[NK + 2], w[NK + 2], fma(u[NK + 1], w[NK + 1], u[NK] * w[NK]));
     w[NK + 3] = ((cpr - cvr) / cvr) * (u[NK + 3] - ke);
 }
 
@@ -458,9 +460,9 @@ DGFV_HD void w_to_cons(const DevPhys& P, const double* w, double* u) {
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) u[NK + i] = rho * w[NK + i];
-    const double ke = 0.5 * rho * (w[NK] * w[NK] + w[NK + 1] * w[NK + 1] + w[NK + 2] * w[NK + 2]);
+    const double ke = 0.5 * rho * fma(w[NK + 2], w[NK + 2], fma(w[NK + 1], w[NK + 1], w[NK] * w[NK]));
     // rho E = p / (kappa - 1) + rho |v|^2 / 2,  1/(kappa - 1) = c_v / (c_p - c_v)
-    u[NK + 3] = w[NK + 3] * (cvr / (cpr - cvr)) + ke;
+    u[NK + 3] = fma(w[NK + 3], cvr / (cpr - cvr), ke);
 }
 
 DGFV_HD double minmod(double a, double b) {
