@@ -39,3 +39,20 @@ def test_kernel_table_and_rounding():
     assert t["dt"] == [1.0, 2, None, None]
     assert "remap" not in t
     assert bench.r4(123456.0) == 123500.0 and bench.r4(0.000123456) == 0.0001235 and bench.r4(None) is None
+
+
+def test_target_summary_reads_the_legs_and_tolerates_missing_ones():
+    """The closing `targets` object of the bench line takes each ratio from its
+    leg (kernel-table rows by position) and gives None where a leg was
+    skipped."""
+    sys.path.insert(0, ROOT)
+    import bench
+    line = {"roofline": {"frac": 0.8, "whole_rhs_frac": 0.79},
+            "hp_shock": {"whole_rhs_frac": 0.52, "kernels": {"fv": [12.0, 30, 0.6, 0.48]}},
+            "adjoint": {"mixing_layer": {"adj_over_fwd_stored": 2.2, "adj_over_fwd_recomputed": 2.9}},
+            "batched_domains": None}
+    t = bench.target_summary(line)
+    assert t == {"dominant_frac": 0.8, "whole_rhs_frac": 0.79, "hp_shock_whole_rhs_frac": 0.52,
+                 "hp_shock_fv_frac": 0.48, "adj_over_fwd_stored": 2.2, "adj_over_fwd_recomputed": 2.9,
+                 "batched_over_per_degree": None}
+    assert all(v is None for v in bench.target_summary({}).values())
