@@ -37,13 +37,6 @@ STAGES_PER_STEP = 3
 # FP64 FMA lanes per SM and clock of a GB300 (1.25 TFLOP/s nominal over 152 SMs
 # at 2.07 GHz); the SM count and the maximum SM clock are read from the device.
 DFMA_PER_CLK = 2
-# DRAM bytes per DG DOF of one k_dg_volume launch, from an ncu capture of the
-# turbulence workload at 28^3 elements (dram__bytes_read.sum + write.sum =
-# 0.398 + 0.759 GB for 3.45e6 DG DOFs).
-VOLUME_DRAM_BYTES_PER_DG_DOF = 335.0
-# measured copy bandwidth of this GPU type (written beside the repository when
-# it is present); used only to show how far the FP64-bound kernel is from HBM.
-HBM_FALLBACK_GBS = 6800.0
 KERNEL_STEP = {"prolong": 1, "fv": 2, "face_lift": 3, "dg_volume": 4, "face_flux": 5, "surface": 6}
 
 
@@ -69,16 +62,6 @@ def fp64_peak(device=0):
         pass
     tf = sms * DFMA_PER_CLK * 2 * mhz * 1e6 / 1e12
     return tf, f"{sms} SMs (device properties) x {DFMA_PER_CLK} DFMA/clk x 2 flop x {src}"
-
-
-def measured_hbm_gbs():
-    """Copy bandwidth measured on this GPU type, else a fallback figure."""
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    try:
-        with open(path) as f:
-            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json copy)"
-    except (OSError, KeyError, ValueError):
-        return HBM_FALLBACK_GBS, "fallback 6.8 TB/s"
 
 
 def parse():
@@ -887,21 +870,18 @@ def main():
         achieved = per_step[KERNEL_STEP[main_k]] * dofs_per_launch / (kms / kl * 1e-3) / 1e12
         probe = dgfv.probe_dfma(1 << 14) / 1e12
         probe_mma = dgfv.probe_dmma(1 << 11) / 1e12
-        dg_dofs = float(np.sum((N_now[fv_now == 0].astype(np.int64) + 1) ** 3))
-        traffic = VOLUME_DRAM_BYTES_PER_DG_DOF * dg_dofs if main_k == "dg_volume" else None
+        # DRAM counters of k_dg_volume exist only from a capture (335 B per DG
+        # DOF, 28^3 case) taken before later register-level edits of the flux
+        # functions the kernel inlines, so the traffic stays null
         roof = {"bound": "alu", "kernel": "k_" + main_k, "achieved": r4(achieved), "peak": r4(peak),
                 "unit": "TFLOP/s", "frac": r4(achieved / peak), "frac_of_dfma_probe": r4(achieved / probe),
-                "traffic": r4(traffic), "traffic_source": "ncu DRAM bytes per DG DOF of k_dg_volume (28^3 case, "
-                                                          "335 B) x the DG DOFs of one launch here",
+                "traffic": None, "traffic_source": "null: the last ncu DRAM capture of k_dg_volume predates "
+                                                   "edits of the flux functions it inlines",
                 "peak_source": peak_src,
                 "dfma_probe_tflops": r4(probe), "dmma_probe_tflops": r4(probe_mma),
                 "flops_per_dof": {"total": r4(per_dof), main_k: r4(per_step[KERNEL_STEP[main_k]])},
                 "whole_rhs_tflops": r4(per_dof * units / (ms * 1e-3) / 1e12),
                 "whole_rhs_frac": r4(per_dof * units / (ms * 1e-3) / 1e12 / peak)}
-        if traffic is not None:
-            hbm_gbs, _ = measured_hbm_gbs()
-            dram_gbs = traffic / (kms / kl * 1e-3) / 1e9
-            roof["hbm_frac"] = r4(dram_gbs / hbm_gbs)
         cpu = None if args.no_cpu else cpu_baseline(dict(prob, N=N_now, fv=fv_now))
         if cpu:
             cpu = {k: (r4(v) if isinstance(v, float) else v) for k, v in cpu.items()}
