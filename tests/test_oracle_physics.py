@@ -393,3 +393,136 @@ def test_indicator_variable_choice_swaps_the_roles(oracle):
     Ip1, Ih1 = oracle.indicator(dict(prob, indicator_vars=1), U)
     np.testing.assert_array_equal(Ip1, Ih0)
     np.testing.assert_array_equal(Ih1, Ip0)
+
+
+# ---------------------------------------------------------------- sensitivity of the Roe pins
+def _roe_matrix(prob, uL, uR, d, average):
+    """Roe matrix A~ of the mixture Euler flux in direction d, written from
+    the product rule for jumps: with sqrt(rho)-weighted v~, H~, Y~,
+      d(rho_k v_d)  = Y~_k dm_d + v~_d drho_k - Y~_k v~_d drho,
+      d(m_i v_d)    = v~_i dm_d + v~_d dm_i - v~_i v~_d drho,
+      d(rho H v_d)  = H~ dm_d + v~_d (d(rho E) + dp) - H~ v~_d drho,
+    and the pressure jump
+      dp = (kappa~ - 1)[d(rho E) - v~.dm + |v~|^2/2 drho] + sum_k psi_k drho_k.
+    `average` picks kappa~ and psi_k:
+      "exact"  - kappa~ - 1 = sum R_k rhobar_k / sum c_v,k rhobar_k (arithmetic
+                 means of the partial densities), psi_k = Tbar (c_p,k - kappa~ c_v,k);
+                 the product rule applied to p = sum rho_k R_k T and
+                 rho e = sum rho_k c_v,k T makes dp exact;
+      "frozen" - kappa~ = c_p(Y~)/c_v(Y~), psi_k = 0: the single-gas average with
+                 the species carried as passive scalars."""
+    nk = len(prob["gamma"])
+    Rk = prob["Rgas"]
+    cv = Rk / (prob["gamma"] - 1)
+    cp = cv + Rk
+
+    def parts(u):
+        rk = u[:nk]
+        rho = rk.sum()
+        v = u[nk:nk + 3] / rho
+        T = (u[nk + 3] - 0.5 * rho * v @ v) / (rk @ cv)
+        p = T * (rk @ Rk)
+        return rk, rho, v, T, p, (u[nk + 3] + p) / rho
+
+    rkL, rL, vL, TL, pL, HL = parts(uL)
+    rkR, rR, vR, TR, pR, HR = parts(uR)
+    wL, wR = np.sqrt(rL), np.sqrt(rR)
+    avg = lambda a, b: (wL * a + wR * b) / (wL + wR)
+    v, H, Y = avg(vL, vR), avg(HL, HR), avg(rkL / rL, rkR / rR)
+    if average == "exact":
+        rbar = 0.5 * (rkL + rkR)
+        km1 = (rbar @ Rk) / (rbar @ cv)
+        psi = 0.5 * (TL + TR) * (cp - (1.0 + km1) * cv)
+    else:
+        km1 = (Y @ cp) / (Y @ cv) - 1.0
+        psi = np.zeros(nk)
+    V = nk + 4
+    iM, iE = nk, nk + 3
+    # pressure row: dp = P . du
+    P = np.zeros(V)
+    P[:nk] = km1 * 0.5 * (v @ v) + psi
+    P[iM:iM + 3] = -km1 * v
+    P[iE] = km1
+    drho = np.zeros(V)
+    drho[:nk] = 1.0
+    A = np.zeros((V, V))
+    for k in range(nk):
+        A[k, k] += v[d]
+        A[k] -= Y[k] * v[d] * drho
+        A[k, iM + d] += Y[k]
+    for i in range(3):
+        A[iM + i, iM + d] += v[i]
+        A[iM + i, iM + i] += v[d]
+        A[iM + i] -= v[i] * v[d] * drho
+        if i == d:
+            A[iM + i] += P
+    A[iE, iM + d] += H
+    A[iE, iE] += v[d]
+    A[iE] += v[d] * P
+    A[iE] -= H * v[d] * drho
+    return A
+
+
+def _abs_matrix(A, at_rest):
+    """|A~| in the two cases the pins use.  Supersonic: every eigenvalue
+    positive, so |A~| = A~.  At rest: the eigenvalues are 0 (the species,
+    shear and contact waves) and +-c~, so |A~| = A~^2 / c~ on every
+    eigenvector."""
+    lam = np.linalg.eigvals(A)
+    assert np.abs(lam.imag).max() < 1e-8 * np.abs(lam).max()
+    lam = np.sort(lam.real)
+    if not at_rest:
+        assert lam[0] > 0
+        return A
+    c = lam[-1]
+    assert abs(lam[0] + c) < 1e-12 * c and np.abs(lam[1:-1]).max() < 1e-6 * c
+    return A @ A / c
+
+
+def test_roe_pins_reject_the_frozen_kappa_average():
+    """The property-U and resting-contact pins above would catch a Roe flux
+    built on the single-gas average: for species of different gamma its
+    matrix misses A~ du = dF, so in every supersonic case its flux
+    (F_L + F_R)/2 - |A~| du/2 differs from F(u_L) (by 0.5-2 % here, against
+    the pin's 1e-14), and at every resting contact it carries mass (2-12 % of
+    the partial densities); the exact mixture linearisation meets both to
+    round-off.  For species of equal gamma both averages coincide."""
+    rng = np.random.default_rng(81)
+    for nk, specs in ((2, [W.AIR, W.HELIUM]), (3, [W.AIR, W.CO2, W.HELIUM]), (2, [W.AIR, dict(W.AIR, M=4.0)])):
+        prob = W.species_set(specs)
+        same_gamma = len({s["gamma"] for s in specs}) == 1
+        best_frozen = np.inf
+        for trial in range(4):
+            rkL = np.array([0.6, 0.3, 0.2][:nk]) * (0.5 + rng.random(nk))
+            rkR = np.array([0.2, 0.7, 0.1][:nk]) * (0.5 + rng.random(nk))
+            for d in range(3):
+                # supersonic: every wave to the right, the Roe flux must be F(u_L)
+                vL = rng.standard_normal(3) * 0.2
+                vR = vL + rng.standard_normal(3) * 0.05
+                vL[d], vR[d] = 3.0 + 0.1 * rng.random(), 3.0 + 0.1 * rng.random()
+                uL = _mixture_state(prob, rkL, vL, 1.0 + 0.2 * rng.random())
+                uR = _mixture_state(prob, rkR, vR, 1.0 + 0.2 * rng.random())
+                FL, _ = _euler_flux(prob, uL, d)
+                FR, _ = _euler_flux(prob, uR, d)
+                du, dF = uR - uL, FR - FL
+                for average in ("exact", "frozen"):
+                    Ab = _abs_matrix(_roe_matrix(prob, uL, uR, d, average), at_rest=False)
+                    err = np.abs(0.5 * (FL + FR) - 0.5 * Ab @ du - FL).max() / np.abs(FL).max()
+                    if average == "exact" or same_gamma:
+                        assert err < 1e-13, (nk, average, err)
+                    else:
+                        best_frozen = min(best_frozen, err)
+                # resting contact at equal pressure: no mass, species or energy flux
+                p = 0.5 + rng.random()
+                uL = _mixture_state(prob, rkL, (0, 0, 0), p)
+                uR = _mixture_state(prob, rkR, (0, 0, 0), p)
+                for average in ("exact", "frozen"):
+                    Ab = _abs_matrix(_roe_matrix(prob, uL, uR, d, average), at_rest=True)
+                    diss = 0.5 * Ab @ (uR - uL)
+                    mass = np.abs(diss[:nk]).max() / np.abs(uL[:nk]).max()
+                    if average == "exact" or same_gamma:
+                        assert mass < 1e-13, (nk, average, mass)
+                    else:
+                        best_frozen = min(best_frozen, mass)
+        if not same_gamma:
+            assert best_frozen > 1e-3, (nk, best_frozen)  # every case fails its pin
