@@ -889,9 +889,10 @@ def main():
         shock = None if args.no_shock else hp_shock_run(peak)
         shock_own = None
         if not args.no_shock:
-            # one timed cycle and the two profiled ones: with N+1 sub-cells the
-            # shock case's state turns non-physical in the fourth cycle, in the
-            # oracle alike
+            # one timed cycle and the two profiled ones: with N+1 sub-cells and
+            # no limiter the shock case's state turns non-physical in the fourth
+            # cycle, in the oracle alike (at the expansion of the periodic wrap,
+            # in DG elements fed by L2 projections from coarser FV neighbours)
             o = hp_shock_run(peak, cycles=1, own=True)
             shock_own = {k: o[k] for k in ("value", "rk_value", "whole_rhs_frac", "fv_elements_first_last",
                                            "subcell_dof_share")}
