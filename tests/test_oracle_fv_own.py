@@ -165,3 +165,56 @@ def test_rejected_with_chained_domains(oracle):
     prob = W.make_problem(doms, sp, n_fv=4, N=2, chain=1, fv_own_n=1)
     with pytest.raises(RuntimeError):
         oracle.state_size(prob)
+
+
+def _physical(prob, U):
+    """Every density positive and every internal energy positive, at the nodes
+    and sub-cells, and no value non-finite."""
+    import oracle
+    nk = len(prob["gamma"])
+    V = nk + 4
+    if not np.isfinite(U).all():
+        return False
+    off = [int(o) for o in oracle.elem_offsets(prob)] + [U.size]
+    for e in range(len(prob["N"])):
+        u = U[off[e]:off[e + 1]].reshape(V, -1)
+        rho = u[:nk].sum(0)
+        if (rho <= 0).any() or (u[nk + 3] - 0.5 * (u[nk:nk + 3] ** 2).sum(0) / rho <= 0).any():
+            return False
+    return True
+
+
+def _shock_cycles(oracle, limiter, cycles, own=True):
+    """The hp-mixed shock case (16^3 elements, N in 2..6, Mach 1.5 shock into a
+    heavy-gas bubble) with per-element sub-cell counts: `cycles` times the
+    indicator's adaptation and 5 SSP-RK3 steps at CFL 0.5.  Returns the number
+    of steps that ended in a physical state."""
+    prob, U = W.hp_shock(0, y_bg=0.01)
+    prob = dict(prob, fv_own_n=int(own), pp_limiter=int(limiter))
+    done = 0
+    for _ in range(cycles):
+        Ip, Ih = oracle.indicator(prob, U)
+        N, fv = oracle.adapt_decide(prob, Ip, Ih, W.THRESHOLDS, 2, 6)
+        U = oracle.remap(prob, N, fv, U)
+        prob = dict(prob, N=N, fv=fv)
+        for _ in range(5):
+            U, _ = oracle.rk3(prob, U, 1, cfl_c=0.5, cfl_v=0.5)
+            if not _physical(prob, U):
+                return done
+            done += 1
+    return done
+
+
+def test_shock_case_with_per_element_sub_cells_needs_the_positivity_limiter(oracle):
+    """Per-element sub-cell counts let a DG element of degree N meet FV
+    neighbours of fewer than N+1 sub-cells, whose coupling fluxes reach it as
+    L2 projections of piecewise constants.  On the shock case a DG element at
+    the expansion of the periodic wrap, fed so, gets face traces of negative
+    pressure and the run turns non-finite within the first five cycles; the
+    Zhang-Shu limiter (nodal and face-point positivity, Sec. 3.5) carries the
+    same run through them.  With the global sub-cell count, N_FV = 7 >=
+    N_max + 1, no such projection occurs and the case runs without the
+    limiter."""
+    assert _shock_cycles(oracle, limiter=False, cycles=5) < 25
+    assert _shock_cycles(oracle, limiter=True, cycles=5) == 25
+    assert _shock_cycles(oracle, limiter=False, cycles=5, own=False) == 25
