@@ -882,7 +882,8 @@ def main():
                 "flops_per_dof": {"total": r4(per_dof), main_k: r4(per_step[KERNEL_STEP[main_k]])},
                 "whole_rhs_tflops": r4(per_dof * units / (ms * 1e-3) / 1e12),
                 "whole_rhs_frac": r4(per_dof * units / (ms * 1e-3) / 1e12 / peak)}
-        cpu = None if args.no_cpu else cpu_baseline(dict(prob, N=N_now, fv=fv_now))
+        # the oracle baseline runs at N = 1 only (rank 0)
+        cpu = None if args.no_cpu or world > 1 else cpu_baseline(dict(prob, N=N_now, fv=fv_now))
         if cpu:
             cpu = {k: (r4(v) if isinstance(v, float) else v) for k, v in cpu.items()}
         adjoint = {"mixing_layer": adjoint_cost(), "hybrid_shock": adjoint_hybrid_cost()}
